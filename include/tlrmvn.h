@@ -1,0 +1,159 @@
+/*
+ * tlrmvn.h - C ABI of the GB300 (sm_103a) tile-low-rank quasi-Monte Carlo library
+ * for high-dimensional multivariate normal (MVN) and Student-t (MVT) probabilities.
+ *
+ * Method: Cao, Genton, Keyes & Turkiyyah, "Exploiting low rank covariance
+ * structures for computing high-dimensional normal and Student-t probabilities"
+ * (arXiv 2003.11183).  The library computes
+ *
+ *     log Phi_n(a, b; Sigma)        (eq. 1)      or
+ *     log T_n(a, b; Sigma, nu)      (eq. 3 / eq. 4)
+ *
+ * by the separation-of-variables integrand (eq. 2) on a block-reordered
+ * tile-low-rank (TLR) Cholesky factor (Section 3.3, Algorithms 4 and 5),
+ * evaluated over randomly shifted Richtmyer lattice points (Section 2.1) by
+ * the TLR integrands of Algorithms 6 and 7 (Section 3.4).
+ *
+ * Conventions for every entry point:
+ *  - Return value: TLRMVN_OK (0) or a positive TLRMVN_E_* code; a one-line
+ *    description of the last failure on the calling thread is available from
+ *    tlrmvn_last_error().  Outputs are written only on success.
+ *  - Arrays are plain C arrays.  "host" pointers point to CPU memory,
+ *    "device" pointers to memory of the current CUDA device.  The caller owns
+ *    every array it passes; the library copies what it needs and keeps no
+ *    caller pointer after the call returns.
+ *  - Streams: a cudaStream_t passed as void*; NULL selects the library's own
+ *    stream.  Calls return after their work on that stream has completed.
+ *  - One handle may be used by one call at a time; different handles are
+ *    independent.  The library allocates device memory with the CUDA runtime.
+ */
+#ifndef TLRMVN_H
+#define TLRMVN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define TLRMVN_OK          0
+#define TLRMVN_E_INVAL     1  /* invalid argument: n <= 0, tile <= 0, NaN, a_i > b_i, bad option */
+#define TLRMVN_E_NOT_SPD   2  /* a Cholesky pivot was not positive: covariance not positive definite */
+#define TLRMVN_E_NOMEM     3  /* device or host allocation failed */
+#define TLRMVN_E_CUDA      4  /* CUDA runtime error (no usable device, launch failure, ...) */
+#define TLRMVN_E_FORMAT    5  /* tlrmvn_factor_import: buffer is not a factor of this format */
+#define TLRMVN_E_NOTSUP    6  /* requested precision / mode not available */
+
+/* ---- option values --------------------------------------------------- */
+/* Arithmetic of the integrand (tlrmvn_opts.precision). */
+#define TLRMVN_FP64        0  /* everything in float64 */
+#define TLRMVN_FP32        1  /* diagonal-tile sweep and low-rank shifts in float32 */
+#define TLRMVN_BF16_SHIFT  2  /* float32 sweep; low-rank shifts on tcgen05 tensor cores, bf16 in, fp32 accumulate */
+
+/* Preconditioner (tlrmvn_factor_opts.reorder), Section 3.3. */
+#define TLRMVN_REORDER_NONE       0  /* geometric order only ("tlrmvn") */
+#define TLRMVN_REORDER_BLOCK      1  /* Algorithm 4, block reordering ("rtlrmvn") */
+#define TLRMVN_REORDER_ITERATIVE  2  /* Algorithm 5, iterative block reordering ("rrtlrmvn") */
+
+/* Covariance kernels of tlrmvn_factor_kernel (Section 3.2; unit variance each). */
+#define TLRMVN_KERNEL_EXP          0  /* exp(-d/beta);                          params = {beta}      */
+#define TLRMVN_KERNEL_MATERN15     1  /* (1 + sqrt3 d/ell) exp(-sqrt3 d/ell);   params = {ell}       */
+#define TLRMVN_KERNEL_EXP_MATERN15 2  /* sum of the two;                        params = {beta, ell} */
+
+typedef struct tlrmvn_factor_s* tlrmvn_factor_t;  /* opaque, library-owned, device-resident */
+
+typedef struct {
+  int    tile;      /* tile size m (> 0); the last tile of the geometric order may be shorter   */
+  double tol;       /* absolute ACA truncation tolerance of the off-diagonal tiles (>= 0)      */
+  int    max_rank;  /* rank cap per off-diagonal tile; 0 = tile size                           */
+  int    reorder;   /* TLRMVN_REORDER_*                                                        */
+  void*  stream;    /* cudaStream_t or NULL                                                    */
+} tlrmvn_factor_opts;
+
+typedef struct {
+  int    precision;        /* TLRMVN_FP64 / TLRMVN_FP32 / TLRMVN_BF16_SHIFT                          */
+  int    n_shifts;         /* M >= 1 random shifts ("batches")                                      */
+  int    n_points;         /* N >= 1 lattice points per shift                                       */
+  int    periodize;        /* nonzero: tent (baker's) transform of each lattice coordinate          */
+  const uint64_t* shifts;  /* host, M x (n + 1) row-major uint64 fractions (shift / 2^64), or NULL:
+                              then shift (s, i) = splitmix64 output number s*(n+1)+i from seed     */
+  uint64_t seed;           /* used only when shifts == NULL                                         */
+  int64_t sample_chunk;    /* samples in flight per pass; 0 = automatic                             */
+  void*  stream;           /* cudaStream_t or NULL                                                  */
+} tlrmvn_opts;
+
+/* ---- factorisation (Section 3.3) -------------------------------------- */
+
+/* Build the block-reordered TLR Cholesky factor of a covariance given by a kernel
+ * on 2-D locations.  Section 3.2: locations are indexed by a cardinality-balanced
+ * k-d bisection whose leaves (tile-sized clusters) become the tiles; Section 3.3:
+ * the factor is formed in float64 on the GPU, reordered by Algorithm 4 or 5 when
+ * requested, with off-diagonal tiles truncated by adaptive cross approximation.
+ *   xy      host, n x 2 row-major locations
+ *   kernel  TLRMVN_KERNEL_*, params host array (1 or 2 entries), nugget >= 0 on the diagonal
+ *   a_ref, b_ref  host, length n, limits that steer the reordering (may be NULL
+ *           when reorder == NONE); -INFINITY / +INFINITY allowed, a_ref <= b_ref
+ *   out     receives the handle; free with tlrmvn_factor_free. */
+int tlrmvn_factor_kernel(const double* xy, int64_t n, int kernel, const double* params, double nugget,
+                         const double* a_ref, const double* b_ref, const tlrmvn_factor_opts* opts,
+                         tlrmvn_factor_t* out);
+
+/* Same from a dense covariance.  cov: host, column-major n x n with leading
+ * dimension ld >= n, symmetric positive definite; tiles are consecutive runs of
+ * `tile` indices in the given order. */
+int tlrmvn_factor_dense(const double* cov, int64_t n, int64_t ld, const double* a_ref, const double* b_ref,
+                        const tlrmvn_factor_opts* opts, tlrmvn_factor_t* out);
+
+/* Shape of a factor: n, number of tiles r, tile size m, total stored rank
+ * K = sum of off-diagonal tile ranks, and the number of tiles whose rank cap
+ * stopped ACA before the tolerance.  Any output pointer may be NULL. */
+int tlrmvn_factor_info(tlrmvn_factor_t f, int64_t* n, int* r, int* m, int64_t* k_total, int* capped);
+
+/* Serialise a factor to host memory (checkpoint; also how tests hand the same
+ * factor to an independent implementation).  If buf == NULL, *bytes receives the
+ * size needed.  Layout (little-endian):
+ *   char magic[8] = "TLRMVN01"; int64 n, r, m, k_total;
+ *   int64 tile_off[r + 1]; int64 perm[n]  (perm[position] = original index);
+ *   int32 rank[r * r]  (rank[i*r + j] for i > j, else 0);
+ *   float64 B[r][m][m]  (diagonal tiles, row-major, zero above the diagonal and
+ *                        outside a short last tile);
+ *   then for each i > j in row-major (i, j) order: float64 U_ij[m_i][k], V_ij[m_j][k]
+ *   (row-major), with L_ij ~ U_ij V_ij^T. */
+int tlrmvn_factor_export(tlrmvn_factor_t f, void* buf, size_t* bytes);
+
+/* Load a factor in the export layout (host buffer) onto the current device. */
+int tlrmvn_factor_import(const void* buf, size_t bytes, tlrmvn_factor_t* out);
+
+int tlrmvn_factor_free(tlrmvn_factor_t f);
+
+/* ---- probabilities (Algorithms 6 and 7) -------------------------------- */
+
+/* log Phi_n(a, b; Sigma) (nu = INFINITY) or log T_n(a, b; Sigma, nu) (nu > 0).
+ *   a, b        host, length n, in the ORIGINAL index order; -INFINITY/+INFINITY allowed
+ *   logp        host, receives log of the QMC estimate (mean over shifts of the
+ *               per-shift lattice means, Section 2.1)
+ *   err         host, receives the standard error of that mean divided by the
+ *               mean (the paper's relative error, Section 4), which is also the
+ *               standard error of logp to first order; NaN when n_shifts == 1
+ *   per_shift   host, length n_shifts or NULL: log of each shift's lattice mean
+ *   per_sample  host, length n_shifts * n_points or NULL: log integrand of every
+ *               sample, shift-major (sample s*N + k-1 is point k of shift s) */
+int tlrmvn_prob(tlrmvn_factor_t f, const double* a, const double* b, double nu, const tlrmvn_opts* opts,
+                double* logp, double* err, double* per_shift, double* per_sample);
+
+/* Same with every array in device memory (inputs already resident; outputs
+ * written on the device).  per_shift / per_sample may be NULL. */
+int tlrmvn_prob_device(tlrmvn_factor_t f, const double* a, const double* b, double nu,
+                       const tlrmvn_opts* opts, double* logp, double* err, double* per_shift,
+                       double* per_sample);
+
+/* ---- diagnostics ------------------------------------------------------ */
+const char* tlrmvn_strerror(int status);
+const char* tlrmvn_last_error(void);   /* thread-local detail of the last failure, "" if none */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TLRMVN_H */

@@ -1,0 +1,228 @@
+"""Python binding of libtlrmvn (include/tlrmvn.h): the same entry points, with
+numpy arrays for host data and torch CUDA tensors for device data.  This
+module only marshals arguments; every step of the computation runs in the
+library's CUDA kernels.  It raises TlrmvnError on any non-zero status.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _lib as L
+
+FP64, FP32, BF16_SHIFT = 0, 1, 2
+REORDER_NONE, REORDER_BLOCK, REORDER_ITERATIVE = 0, 1, 2
+KERNEL_EXP, KERNEL_MATERN15, KERNEL_EXP_MATERN15 = 0, 1, 2
+E_INVAL, E_NOT_SPD, E_NOMEM, E_CUDA, E_FORMAT, E_NOTSUP = 1, 2, 3, 4, 5, 6
+
+
+class TlrmvnError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        lib = L.load()
+        self.status = status
+        super().__init__(f"{where}: {lib.tlrmvn_strerror(status).decode()} ({lib.tlrmvn_last_error().decode()})")
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise TlrmvnError(status, where)
+
+
+def _dp(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(L.c_double_p)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Factor:
+    """Owns a tlrmvn_factor_t; freed by close() or garbage collection."""
+
+    def __init__(self, handle: int):
+        self.handle = C.c_void_p(handle)
+
+    def close(self):
+        if self.handle and self.handle.value:
+            L.load().tlrmvn_factor_free(self.handle)
+            self.handle = C.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _fopts(tile: int, tol: float, max_rank: int, reorder: int, stream) -> L.FactorOpts:
+    return L.FactorOpts(int(tile), float(tol), int(max_rank), int(reorder), _stream_ptr(stream))
+
+
+def tlrmvn_factor_kernel(xy, kernel: int, params, nugget: float, a_ref, b_ref, tile: int, tol: float,
+                         max_rank: int = 0, reorder: int = REORDER_ITERATIVE, stream=None) -> Factor:
+    lib = L.load()
+    xy = _f64(xy).reshape(-1, 2)
+    p = _f64(list(params) + [0.0] * (2 - len(params)))
+    a = None if a_ref is None else _f64(a_ref)
+    b = None if b_ref is None else _f64(b_ref)
+    out = C.c_void_p()
+    o = _fopts(tile, tol, max_rank, reorder, stream)
+    _check(lib.tlrmvn_factor_kernel(_dp(xy), xy.shape[0], int(kernel), _dp(p), float(nugget), _dp(a), _dp(b),
+                                    C.byref(o), C.byref(out)), "tlrmvn_factor_kernel")
+    return Factor(out.value)
+
+
+def tlrmvn_factor_dense(cov, a_ref, b_ref, tile: int, tol: float, max_rank: int = 0,
+                        reorder: int = REORDER_ITERATIVE, stream=None) -> Factor:
+    lib = L.load()
+    cov = np.asfortranarray(cov, dtype=np.float64)
+    n = cov.shape[0]
+    a = None if a_ref is None else _f64(a_ref)
+    b = None if b_ref is None else _f64(b_ref)
+    out = C.c_void_p()
+    o = _fopts(tile, tol, max_rank, reorder, stream)
+    _check(lib.tlrmvn_factor_dense(cov.ctypes.data_as(L.c_double_p), n, n, _dp(a), _dp(b), C.byref(o), C.byref(out)),
+           "tlrmvn_factor_dense")
+    return Factor(out.value)
+
+
+def tlrmvn_factor_info(f: Factor) -> dict:
+    lib = L.load()
+    n, k = C.c_int64(), C.c_int64()
+    r, m, cp = C.c_int(), C.c_int(), C.c_int()
+    _check(lib.tlrmvn_factor_info(f.handle, C.byref(n), C.byref(r), C.byref(m), C.byref(k), C.byref(cp)),
+           "tlrmvn_factor_info")
+    return {"n": n.value, "r": r.value, "m": m.value, "k_total": k.value, "capped": cp.value}
+
+
+def tlrmvn_factor_export(f: Factor) -> bytes:
+    lib = L.load()
+    nb = C.c_size_t(0)
+    _check(lib.tlrmvn_factor_export(f.handle, None, C.byref(nb)), "tlrmvn_factor_export")
+    buf = C.create_string_buffer(nb.value)
+    _check(lib.tlrmvn_factor_export(f.handle, buf, C.byref(nb)), "tlrmvn_factor_export")
+    return buf.raw[:nb.value]
+
+
+def tlrmvn_factor_import(buf: bytes) -> Factor:
+    lib = L.load()
+    out = C.c_void_p()
+    cbuf = C.create_string_buffer(bytes(buf), len(buf))
+    _check(lib.tlrmvn_factor_import(cbuf, len(buf), C.byref(out)), "tlrmvn_factor_import")
+    return Factor(out.value)
+
+
+def tlrmvn_factor_free(f: Factor):
+    f.close()
+
+
+@dataclass
+class ExportedFactor:
+    """The serialised layout of tlrmvn_factor_export as numpy arrays."""
+    n: int
+    r: int
+    m: int
+    tile_off: np.ndarray
+    perm: np.ndarray
+    rank: np.ndarray      # r x r
+    B: np.ndarray         # r x m x m
+    U: dict               # (i, j) -> m_i x k
+    V: dict               # (i, j) -> m_j x k
+
+
+def parse_export(buf: bytes) -> ExportedFactor:
+    if buf[:8] != b"TLRMVN01":
+        raise ValueError("not a tlrmvn factor")
+    n, r, m, _ = np.frombuffer(buf, dtype=np.int64, count=4, offset=8)
+    n, r, m = int(n), int(r), int(m)
+    off = 40
+    tile_off = np.frombuffer(buf, np.int64, r + 1, off).copy(); off += 8 * (r + 1)
+    perm = np.frombuffer(buf, np.int64, n, off).copy(); off += 8 * n
+    rank = np.frombuffer(buf, np.int32, r * r, off).reshape(r, r).copy(); off += 4 * r * r
+    B = np.frombuffer(buf, np.float64, r * m * m, off).reshape(r, m, m).copy(); off += 8 * r * m * m
+    U, V = {}, {}
+    for i in range(r):
+        for j in range(i):
+            k = int(rank[i, j])
+            if not k:
+                continue
+            mi, mj = int(tile_off[i + 1] - tile_off[i]), int(tile_off[j + 1] - tile_off[j])
+            U[(i, j)] = np.frombuffer(buf, np.float64, mi * k, off).reshape(mi, k).copy(); off += 8 * mi * k
+            V[(i, j)] = np.frombuffer(buf, np.float64, mj * k, off).reshape(mj, k).copy(); off += 8 * mj * k
+    return ExportedFactor(n, r, m, tile_off, perm, rank, B, U, V)
+
+
+def build_export(n: int, m: int, tile_off, perm, B_tiles, U: dict, V: dict) -> bytes:
+    """Serialise a factor given as arrays into the tlrmvn_factor_import layout."""
+    r = len(tile_off) - 1
+    rank = np.zeros((r, r), dtype=np.int32)
+    for (i, j), u in U.items():
+        rank[i, j] = u.shape[1]
+    Bp = np.zeros((r, m, m))
+    for t, Bt in enumerate(B_tiles):
+        Bp[t, :Bt.shape[0], :Bt.shape[1]] = np.tril(Bt)
+    parts = [b"TLRMVN01", np.array([n, r, m, int(rank.sum())], np.int64).tobytes(),
+             np.asarray(tile_off, np.int64).tobytes(), np.asarray(perm, np.int64).tobytes(), rank.tobytes(),
+             Bp.tobytes()]
+    for i in range(r):
+        for j in range(i):
+            if rank[i, j]:
+                parts.append(np.ascontiguousarray(U[(i, j)], np.float64).tobytes())
+                parts.append(np.ascontiguousarray(V[(i, j)], np.float64).tobytes())
+    return b"".join(parts)
+
+
+def _opts(precision, n_shifts, n_points, periodize, shifts, seed, sample_chunk, stream, n):
+    keep = None
+    sp = None
+    if shifts is not None:
+        keep = np.ascontiguousarray(shifts, dtype=np.uint64)
+        if keep.shape != (n_shifts, n + 1):
+            raise ValueError(f"shifts must have shape ({n_shifts}, {n + 1})")
+        sp = keep.ctypes.data_as(L.c_u64_p)
+    o = L.Opts(int(precision), int(n_shifts), int(n_points), 1 if periodize else 0, sp, int(seed) & (2**64 - 1),
+               int(sample_chunk), _stream_ptr(stream))
+    return o, keep
+
+
+def tlrmvn_prob(f: Factor, a, b, nu: float = math.inf, precision: int = FP32, n_shifts: int = 20,
+                n_points: int = 1000, shifts=None, seed: int = 0, periodize: bool = True, sample_chunk: int = 0,
+                per_shift: bool = False, per_sample: bool = False, stream=None):
+    """Host-array call: returns (logp, err, per_shift or None, per_sample or None)."""
+    lib = L.load()
+    a = _f64(a)
+    b = _f64(b)
+    n = a.size
+    o, keep = _opts(precision, n_shifts, n_points, periodize, shifts, seed, sample_chunk, stream, n)
+    lp, er = C.c_double(), C.c_double()
+    ps = np.empty(n_shifts) if per_shift else None
+    pm = np.empty(n_shifts * n_points) if per_sample else None
+    _check(lib.tlrmvn_prob(f.handle, _dp(a), _dp(b), float(nu), C.byref(o), C.byref(lp), C.byref(er), _dp(ps), _dp(pm)),
+           "tlrmvn_prob")
+    del keep
+    return lp.value, er.value, ps, pm
+
+
+def tlrmvn_prob_device(f: Factor, a, b, out, nu: float = math.inf, precision: int = FP32, n_shifts: int = 20,
+                       n_points: int = 1000, shifts=None, seed: int = 0, periodize: bool = True,
+                       sample_chunk: int = 0, per_shift=None, per_sample=None, stream=None):
+    """Device call: a, b float64 CUDA tensors (original order); out a float64 CUDA
+    tensor of 2 elements receiving (logp, err); per_shift / per_sample optional tensors."""
+    lib = L.load()
+    n = a.numel()
+    o, keep = _opts(precision, n_shifts, n_points, periodize, shifts, seed, sample_chunk, stream, n)
+    ptr = lambda t: None if t is None else t.data_ptr()
+    _check(lib.tlrmvn_prob_device(f.handle, a.data_ptr(), b.data_ptr(), float(nu), C.byref(o), out.data_ptr(),
+                                  out.data_ptr() + 8, ptr(per_shift), ptr(per_sample)), "tlrmvn_prob_device")
+    del keep

@@ -1,0 +1,276 @@
+// Shared internals of the tlrmvn library: status plumbing, the factor handle,
+// and the device-side univariate functions of the SOV integrand.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <math.h>
+#include <string>
+#include <vector>
+
+#include "../../include/tlrmvn.h"
+
+namespace tlrmvn {
+
+// ---- error plumbing --------------------------------------------------------
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define TLR_CUDA(call)                                              \
+  do {                                                              \
+    cudaError_t e_ = (call);                                        \
+    if (e_ != cudaSuccess) return ::tlrmvn::cuda_fail(e_, #call);   \
+  } while (0)
+
+#define TLR_CHECK(st)            \
+  do {                           \
+    int s_ = (st);               \
+    if (s_ != TLRMVN_OK) return s_; \
+  } while (0)
+
+// Device allocation owned by the caller of dalloc.
+template <typename T>
+int dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) return TLRMVN_OK;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(TLRMVN_E_NOMEM, std::string("cudaMalloc of ") + std::to_string(count * sizeof(T)) + " bytes failed");
+  }
+  return TLRMVN_OK;
+}
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+// ---- factor handle -----------------------------------------------------------
+// L ~ tile-low-rank Cholesky factor of Sigma[perm][:, perm] (Section 3.3).
+// Compact device layout used by the integrand:
+//   B     r x m x m float64, diagonal tiles by position, row-major, zero above the diagonal
+//   Ucat  for row tile i: an m x Krow_i row-major block at offset m*krow_off[i]; its
+//         columns are the ranks of (i,0), (i,1), ..., (i,i-1) in that order
+//   Vcat  for column tile j: a Kcol_j x m row-major block at offset m*kcol_off[j];
+//         its rows are the ranks of (j+1,j), (j+2,j), ..., (r-1,j), stored as V^T
+//   vmap  Vcat row -> global rank index (the row-grouped index of Ucat columns)
+struct Factor {
+  int64_t n = 0;
+  int r = 0, m = 0;
+  int64_t ktot = 0;
+  int capped = 0;
+  int device = 0;
+  std::vector<int64_t> tile_off, perm;   // host
+  std::vector<int32_t> rank;             // host, r*r, rank[i*r+j] for i > j
+  std::vector<int64_t> krow_off, kcol_off;
+  double* B = nullptr;
+  double* Ucat = nullptr;
+  double* Vcat = nullptr;
+  int32_t* vmap = nullptr;
+  // lazily made copies for the reduced-precision integrands
+  float* B32 = nullptr;
+  float* U32 = nullptr;
+  float* V32 = nullptr;
+  __nv_bfloat16* U16 = nullptr;
+  __nv_bfloat16* V16 = nullptr;
+  // lattice generators for n + 1 coordinates (device), and the permutation (device)
+  uint64_t* Q = nullptr;
+  int64_t* dperm = nullptr;
+
+  int64_t tsize(int t) const { return tile_off[t + 1] - tile_off[t]; }
+  int64_t krow(int i) const { return krow_off[i + 1] - krow_off[i]; }
+  int64_t kcol(int j) const { return kcol_off[j + 1] - kcol_off[j]; }
+  ~Factor();
+};
+
+// Fills krow_off/kcol_off/ktot from rank and allocates Ucat/Vcat/vmap/B (not filled).
+int factor_alloc_compact(Factor& F);
+// Host tables: lattice generators Q_i = floor(frac(sqrt(p_i)) 2^64) for the first d primes.
+std::vector<uint64_t> richtmyer_generators(int64_t d);
+// Uploads Q and perm, called once the factor is complete.
+int factor_finish(Factor& F, cudaStream_t st);
+
+cudaStream_t pick_stream(void* s);
+
+// ---- device univariate functions ------------------------------------------------
+#define TLR_RSQRT2 0.70710678118654752440
+#define TLR_SQRT2PI 2.50662827463100050242
+#define TLR_LOG_SQRT2PI 0.91893853320467274178
+
+// Rational approximation of the standard normal quantile by P. J. Acklam
+// (2003; relative error below 1.15e-9 on (0,1)): central branch in p - 1/2,
+// tail branch in q = sqrt(-2 log p).  Coefficients as published.
+struct Acklam {
+  static constexpr double a1 = -3.969683028665376e+01, a2 = 2.209460984245205e+02, a3 = -2.759285104469687e+02,
+                          a4 = 1.383577518672690e+02, a5 = -3.066479806614716e+01, a6 = 2.506628277459239e+00;
+  static constexpr double b1 = -5.447609879822406e+01, b2 = 1.615858368580409e+02, b3 = -1.556989798598866e+02,
+                          b4 = 6.680131188771972e+01, b5 = -1.328068155288572e+01;
+  static constexpr double c1 = -7.784894002430293e-03, c2 = -3.223964580411365e-01, c3 = -2.400758277161838e+00,
+                          c4 = -2.549732539343734e+00, c5 = 4.374664141464968e+00, c6 = 2.938163982698783e+00;
+  static constexpr double d1 = 7.784695709041462e-03, d2 = 3.224671290700398e-01, d3 = 2.445134137142996e+00,
+                          d4 = 3.754408661907416e+00;
+  static constexpr double p_low = 0.02425;
+};
+
+// log Phi(x), accurate in both tails.
+__device__ __forceinline__ double log_Phi(double x) {
+  if (x < -1.0) return log(0.5 * erfcx(-x * TLR_RSQRT2)) - 0.5 * x * x;
+  if (x < 0.0) return log(0.5 * erfc(-x * TLR_RSQRT2));
+  return log1p(-0.5 * erfc(x * TLR_RSQRT2));
+}
+__device__ __forceinline__ float log_Phi(float x) {
+  if (x < -1.0f) return logf(0.5f * erfcxf(-x * (float)TLR_RSQRT2)) - 0.5f * x * x;
+  if (x < 0.0f) return logf(0.5f * erfcf(-x * (float)TLR_RSQRT2));
+  return log1pf(-0.5f * erfcf(x * (float)TLR_RSQRT2));
+}
+
+// Phi^-1(p) for p in (0, 1/2]; lp = log p (finite even when p underflows).
+// float64: Acklam start, then one Newton step on log Phi(x) - log p in the tail
+// or one Halley step on Phi(x) - p in the centre, which brings the relative
+// error to the level of the erfc evaluation.
+__device__ __forceinline__ double ndtri_lower(double p, double lp) {
+  double x;
+  if (p < Acklam::p_low) {
+    double q = sqrt(-2.0 * lp);
+    x = (((((Acklam::c1 * q + Acklam::c2) * q + Acklam::c3) * q + Acklam::c4) * q + Acklam::c5) * q + Acklam::c6) /
+        ((((Acklam::d1 * q + Acklam::d2) * q + Acklam::d3) * q + Acklam::d4) * q + 1.0);
+    double lphi = log_Phi(x);
+    double f = lphi - lp;
+    double dfdx = exp(-0.5 * x * x - TLR_LOG_SQRT2PI - lphi);
+    x -= f / dfdx;
+  } else {
+    double q = p - 0.5, rr = q * q;
+    x = (((((Acklam::a1 * rr + Acklam::a2) * rr + Acklam::a3) * rr + Acklam::a4) * rr + Acklam::a5) * rr + Acklam::a6) * q /
+        (((((Acklam::b1 * rr + Acklam::b2) * rr + Acklam::b3) * rr + Acklam::b4) * rr + Acklam::b5) * rr + 1.0);
+    double e = 0.5 * erfc(-x * TLR_RSQRT2) - p;
+    double u = e * TLR_SQRT2PI * exp(0.5 * x * x);
+    x = x - u / (1.0 + 0.5 * x * u);
+  }
+  return x;
+}
+// float32: the rational approximation alone is below float rounding.
+__device__ __forceinline__ float ndtri_lower(float p, float lp) {
+  if (p < (float)Acklam::p_low) {
+    float q = sqrtf(-2.0f * lp);
+    float num = (float)Acklam::c1;
+    num = num * q + (float)Acklam::c2;
+    num = num * q + (float)Acklam::c3;
+    num = num * q + (float)Acklam::c4;
+    num = num * q + (float)Acklam::c5;
+    num = num * q + (float)Acklam::c6;
+    float den = (float)Acklam::d1;
+    den = den * q + (float)Acklam::d2;
+    den = den * q + (float)Acklam::d3;
+    den = den * q + (float)Acklam::d4;
+    den = den * q + 1.0f;
+    return num / den;
+  }
+  float q = p - 0.5f, rr = q * q;
+  float num = (float)Acklam::a1;
+  num = num * rr + (float)Acklam::a2;
+  num = num * rr + (float)Acklam::a3;
+  num = num * rr + (float)Acklam::a4;
+  num = num * rr + (float)Acklam::a5;
+  num = num * rr + (float)Acklam::a6;
+  float den = (float)Acklam::b1;
+  den = den * rr + (float)Acklam::b2;
+  den = den * rr + (float)Acklam::b3;
+  den = den * rr + (float)Acklam::b4;
+  den = den * rr + (float)Acklam::b5;
+  den = den * rr + 1.0f;
+  return num * q / den;
+}
+
+__device__ __forceinline__ double dev_log(double x) { return log(x); }
+__device__ __forceinline__ float dev_log(float x) { return logf(x); }
+__device__ __forceinline__ double dev_erfc(double x) { return erfc(x); }
+__device__ __forceinline__ float dev_erfc(float x) { return erfcf(x); }
+
+// Phi^-1 given u and its complement uc = 1 - u (both accurate) and lu = log u.
+template <typename T>
+__device__ __forceinline__ T ndtri2(T u, T uc, T lu) {
+  if (u <= (T)0.5) return ndtri_lower(u, lu);
+  return -ndtri_lower(uc, dev_log(uc));
+}
+
+// One variable of eq. (2) on standardised limits (at, bt), lattice value w with
+// complement wc = 1 - w: returns log(e - d) and y = Phi^-1(d + w (e - d)),
+// with d = Phi(at), e = Phi(bt).  Upper-half intervals (at > 0) are handled
+// through the complements Phi(-at), Phi(-bt); one-sided intervals through log Phi.
+template <typename T>
+__device__ __forceinline__ void sov_step(T at, T bt, T w, T wc, T& ld, T& y) {
+  const T rs2 = (T)TLR_RSQRT2;
+  const T INF = (T)INFINITY;
+  if (at == -INF) {
+    if (bt == INF) {
+      ld = (T)0;
+      y = ndtri2(w, wc, dev_log(w));
+      return;
+    }
+    T e, ec, le;
+    if (bt < (T)0) {
+      e = (T)0.5 * dev_erfc(-bt * rs2);
+      ec = (T)1 - e;
+      le = log_Phi(bt);
+    } else {
+      ec = (T)0.5 * dev_erfc(bt * rs2);
+      e = (T)1 - ec;
+      le = log_Phi(bt);
+    }
+    T u = w * e, uc = ec + wc * e;
+    y = ndtri2(u, uc, dev_log(w) + le);
+    ld = le;
+    return;
+  }
+  if (at > (T)0) {
+    T dc = (T)0.5 * dev_erfc(at * rs2);
+    T ec = (bt == INF) ? (T)0 : (T)0.5 * dev_erfc(bt * rs2);
+    T diff = dc - ec;
+    T uc = ec + wc * diff;   // 1 - u
+    T u = (T)1 - uc;
+    y = ndtri2(u, uc, dev_log(u));
+    ld = dev_log(diff);
+    return;
+  }
+  T d = (T)0.5 * dev_erfc(-at * rs2);
+  T e, ec;
+  if (bt == INF) {
+    e = (T)1;
+    ec = (T)0;
+  } else if (bt < (T)0) {
+    e = (T)0.5 * dev_erfc(-bt * rs2);
+    ec = (T)1 - e;
+  } else {
+    ec = (T)0.5 * dev_erfc(bt * rs2);
+    e = (T)1 - ec;
+  }
+  T diff = e - d;
+  T u = d + w * diff, uc = ec + wc * diff;
+  y = ndtri2(u, uc, dev_log(u));
+  ld = dev_log(diff);
+}
+
+// Lattice coordinate -> (w, 1 - w), exactly (see the lattice definition:
+// tent transform of the cell midpoint of the top 53 bits, or the midpoint of
+// the top 52 bits without periodisation).
+__device__ __forceinline__ void lattice_w(uint64_t x, int periodize, double& w, double& wc) {
+  const double s53 = 1.1102230246251565e-16;  // 2^-53
+  if (periodize) {
+    int64_t h = (int64_t)(x >> 11);
+    int64_t num = 2 * h + 1 - (int64_t(1) << 53);
+    if (num < 0) num = -num;
+    w = (double)num * s53;
+    wc = (double)((int64_t(1) << 53) - num) * s53;
+  } else {
+    int64_t h = (int64_t)(x >> 12);
+    int64_t num = 2 * h + 1;
+    w = (double)num * s53;
+    wc = (double)((int64_t(1) << 53) - num) * s53;
+  }
+}
+
+}  // namespace tlrmvn

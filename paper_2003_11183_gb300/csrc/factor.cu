@@ -1,0 +1,1013 @@
+// Block-reordered tile-low-rank Cholesky factorisation in float64 on the GPU
+// (Section 3.3, Algorithms 4 and 5).
+//
+// Blocks (tile-sized clusters of the geometric order) carry a block id; the
+// factor is built position by position j = 0..r-1:
+//   * Algorithm 5 (iterative): univariate conditioning (UC) of every remaining
+//     block on its current Schur complement and conditioned limits; the block
+//     with the smallest estimate takes position j, and its UC pivot order is its
+//     within-block order.  Algorithm 4 (one-shot): UC of the original blocks
+//     once, blocks sorted by the estimate.
+//   * L_jj = Cholesky(S_jj); S_ij = Sigma_ij - sum_{k<j} U_ik (V_ik^T V_jk) U_jk^T
+//     (left-looking, so no dense Schur complement of the off-diagonal part is
+//     ever stored); L_ij = S_ij L_jj^-T; L_ij ~ U_ij V_ij^T by adaptive cross
+//     approximation with full pivoting at absolute tolerance tol.
+//   * Algorithm 5 only: limits of the remaining blocks are conditioned by
+//     U_ij (V_ij^T y_j); these steer the ordering only.
+//   * The diagonal Schur blocks S_ii -= U_ij (V_ij^T V_ij) U_ij^T are kept current.
+#include "common.cuh"
+#include "gemm.cuh"
+
+#include <algorithm>
+#include <cstring>
+#include <functional>
+#include <numeric>
+
+namespace tlrmvn {
+
+// ---- device helpers (float64) -------------------------------------------------------
+// log(Phi(bt) - Phi(at)) for at <= bt, through complements in the upper half.
+__device__ double log_interval_d(double at, double bt) {
+  if (at == -INFINITY) return (bt == INFINITY) ? 0.0 : log_Phi(bt);
+  if (at > 0.0) {
+    double dc = 0.5 * erfc(at * TLR_RSQRT2);
+    double ec = (bt == INFINITY) ? 0.0 : 0.5 * erfc(bt * TLR_RSQRT2);
+    return log(dc - ec);
+  }
+  double d = 0.5 * erfc(-at * TLR_RSQRT2);
+  double e = (bt == INFINITY) ? 1.0 : (bt < 0.0 ? 0.5 * erfc(-bt * TLR_RSQRT2) : 1.0 - 0.5 * erfc(bt * TLR_RSQRT2));
+  return log(e - d);
+}
+// Mean of N(0,1) truncated to (at, bt).
+__device__ double trunc_mean_d(double at, double bt) {
+  double ld = log_interval_d(at, bt);
+  double ta = (at > -INFINITY && at < INFINITY) ? exp(-0.5 * at * at - TLR_LOG_SQRT2PI - ld) : 0.0;
+  double tb = (bt > -INFINITY && bt < INFINITY) ? exp(-0.5 * bt * bt - TLR_LOG_SQRT2PI - ld) : 0.0;
+  return ta - tb;
+}
+
+__device__ __forceinline__ void argmin_merge(double& q, int& i, double q2, int i2) {
+  if (q2 < q || (q2 == q && i2 < i)) {
+    q = q2;
+    i = i2;
+  }
+}
+// block-wide (min q, lowest index); every thread gets the result
+__device__ void block_argmin(double& q, int& i, double* shq, int* shi) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  for (int o = 16; o; o >>= 1) {
+    double q2 = __shfl_xor_sync(0xffffffffu, q, o);
+    int i2 = __shfl_xor_sync(0xffffffffu, i, o);
+    argmin_merge(q, i, q2, i2);
+  }
+  if (lane == 0) {
+    shq[wid] = q;
+    shi[wid] = i;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    q = lane < nw ? shq[lane] : INFINITY;
+    i = lane < nw ? shi[lane] : 0x7fffffff;
+    for (int o = 16; o; o >>= 1) {
+      double q2 = __shfl_xor_sync(0xffffffffu, q, o);
+      int i2 = __shfl_xor_sync(0xffffffffu, i, o);
+      argmin_merge(q, i, q2, i2);
+    }
+    if (lane == 0) {
+      shq[0] = q;
+      shi[0] = i;
+    }
+  }
+  __syncthreads();
+  q = shq[0];
+  i = shi[0];
+  __syncthreads();
+}
+__device__ double block_sum(double v, double* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    v = lane < nw ? sh[lane] : 0.0;
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[0] = v;
+  }
+  __syncthreads();
+  v = sh[0];
+  __syncthreads();
+  return v;
+}
+
+// ---- covariance tiles -----------------------------------------------------------------
+struct TileJob {
+  double* out;              // m x m row-major (ld m)
+  const int64_t* rows;      // original indices of the tile rows
+  const int64_t* cols;
+  int nr, nc;
+};
+struct CovSrc {
+  const double* xy;    // n x 2 (kernel source) or null
+  const double* dense; // column-major n x n, leading dimension ld (dense source) or null
+  int64_t ld;
+  int kernel;
+  double p0, p1, nugget;
+};
+__device__ __forceinline__ double cov_value(const CovSrc& s, int64_t i, int64_t j) {
+  if (s.dense) return s.dense[i + j * s.ld];
+  double dx = s.xy[2 * i] - s.xy[2 * j], dy = s.xy[2 * i + 1] - s.xy[2 * j + 1];
+  double d = sqrt(dx * dx + dy * dy);
+  double v;
+  if (s.kernel == TLRMVN_KERNEL_EXP) v = exp(-d / s.p0);
+  else if (s.kernel == TLRMVN_KERNEL_MATERN15) {
+    double t = 1.7320508075688772 * d / s.p0;
+    v = (1.0 + t) * exp(-t);
+  } else {
+    double t = 1.7320508075688772 * d / s.p1;
+    v = exp(-d / s.p0) + (1.0 + t) * exp(-t);
+  }
+  if (i == j) v += s.nugget;
+  return v;
+}
+__global__ void k_cov_tiles(const TileJob* jobs, CovSrc src, int m) {
+  const TileJob jb = jobs[blockIdx.y];
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)m * m; t += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(t / m), j = (int)(t % m);
+    jb.out[t] = (i < jb.nr && j < jb.nc) ? cov_value(src, jb.rows[i], jb.cols[j]) : 0.0;
+  }
+}
+
+// ---- univariate conditioning (Trinh & Genz) of diagonal blocks --------------------------
+// One block per CTA; right-looking pivoted Cholesky of a copy of the block in
+// `work`.  Writes log of the estimate; with emit, also the pivot order and the
+// truncated expectations in the new order.
+__global__ void __launch_bounds__(512) k_uc(const int* blist, const double* diagS, const int* bsize, int m,
+                                            const double* acur, const double* bcur, double* work, double* logp_out,
+                                            int emit, int* order_out, double* y_out, int* status) {
+  extern __shared__ double shm[];
+  double* sa = shm;
+  double* sb = sa + m;
+  double* ss = sb + m;
+  double* lcol = ss + m;
+  double* sy = lcol + m;
+  int* so = (int*)(sy + m);
+  __shared__ double shq[32];
+  __shared__ int shi[32];
+  __shared__ double shy;
+  const int b = blist[blockIdx.x];
+  const int mb = bsize[b];
+  double* A = work + (size_t)blockIdx.x * m * m;
+  const double* S = diagS + (size_t)b * m * m;
+  for (int t = threadIdx.x; t < mb * mb; t += blockDim.x) A[(t / mb) * m + t % mb] = S[(t / mb) * m + t % mb];
+  for (int t = threadIdx.x; t < mb; t += blockDim.x) {
+    sa[t] = acur[(size_t)b * m + t];
+    sb[t] = bcur[(size_t)b * m + t];
+    ss[t] = 0.0;
+    so[t] = t;
+  }
+  __syncthreads();
+  double logp = 0.0;
+  for (int k = 0; k < mb; k++) {
+    double bq = INFINITY;
+    int bi = 0x7fffffff;
+    for (int i = k + threadIdx.x; i < mb; i += blockDim.x) {
+      double var = A[(size_t)i * m + i];
+      double q;
+      if (!(var > 0.0)) {
+        atomicExch(status, TLRMVN_E_NOT_SPD);
+        q = INFINITY;
+      } else {
+        double sig = sqrt(var);
+        q = log_interval_d((sa[i] - ss[i]) / sig, (sb[i] - ss[i]) / sig);
+      }
+      argmin_merge(bq, bi, q, i);
+    }
+    block_argmin(bq, bi, shq, shi);
+    const int piv = (bi < mb) ? bi : k;
+    if (threadIdx.x == 0) {
+      if (piv != k) {
+        double t;
+        t = sa[k]; sa[k] = sa[piv]; sa[piv] = t;
+        t = sb[k]; sb[k] = sb[piv]; sb[piv] = t;
+        t = ss[k]; ss[k] = ss[piv]; ss[piv] = t;
+        int ti = so[k]; so[k] = so[piv]; so[piv] = ti;
+      }
+      logp += bq;
+    }
+    if (piv != k) {
+      for (int t = threadIdx.x; t < mb; t += blockDim.x) {
+        double x = A[(size_t)k * m + t];
+        A[(size_t)k * m + t] = A[(size_t)piv * m + t];
+        A[(size_t)piv * m + t] = x;
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < mb; t += blockDim.x) {
+        double x = A[(size_t)t * m + k];
+        A[(size_t)t * m + k] = A[(size_t)t * m + piv];
+        A[(size_t)t * m + piv] = x;
+      }
+    }
+    __syncthreads();
+    const double dkk = A[(size_t)k * m + k];
+    const double lkk = sqrt(dkk > 0.0 ? dkk : 1.0);
+    for (int i = k + 1 + threadIdx.x; i < mb; i += blockDim.x) lcol[i] = A[(size_t)i * m + k] / lkk;
+    if (threadIdx.x == 0) {
+      double y = trunc_mean_d((sa[k] - ss[k]) / lkk, (sb[k] - ss[k]) / lkk);
+      sy[k] = y;
+      shy = y;
+    }
+    __syncthreads();
+    const double yk = shy;
+    for (int i = k + 1 + threadIdx.x; i < mb; i += blockDim.x) ss[i] += lcol[i] * yk;
+    const int w = mb - k - 1;
+    for (int t = threadIdx.x; t < w * w; t += blockDim.x) {
+      int i = k + 1 + t / w, jj = k + 1 + t % w;
+      A[(size_t)i * m + jj] -= lcol[i] * lcol[jj];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) logp_out[blockIdx.x] = logp;
+  if (emit) {
+    for (int t = threadIdx.x; t < mb; t += blockDim.x) {
+      order_out[(size_t)blockIdx.x * m + t] = so[t];
+      y_out[(size_t)blockIdx.x * m + t] = sy[t];
+    }
+  }
+}
+
+// ---- plain Cholesky of one block, in place (lower), zero above -------------------------
+__global__ void __launch_bounds__(512) k_potrf(double* A, int mb, int m, int* status) {
+  extern __shared__ double col[];
+  for (int k = 0; k < mb; k++) {
+    const double d = A[(size_t)k * m + k];
+    if (!(d > 0.0)) {
+      if (threadIdx.x == 0) atomicExch(status, TLRMVN_E_NOT_SPD);
+      return;
+    }
+    const double lkk = sqrt(d);
+    for (int i = k + 1 + threadIdx.x; i < mb; i += blockDim.x) {
+      double l = A[(size_t)i * m + k] / lkk;
+      A[(size_t)i * m + k] = l;
+      col[i] = l;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) A[(size_t)k * m + k] = lkk;
+    const int w = mb - k - 1;
+    for (int t = threadIdx.x; t < w * w; t += blockDim.x) {
+      int i = k + 1 + t / w, jj = k + 1 + t % w;
+      if (jj <= i) A[(size_t)i * m + jj] -= col[i] * col[jj];
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+    int i = t / m, jj = t % m;
+    if (jj > i || i >= mb) A[t] = 0.0;
+  }
+}
+
+// ---- inverse of a lower triangular block: Linv (zero above), column per thread ----------
+__global__ void __launch_bounds__(512) k_trinv(const double* L, double* Linv, int mb, int m) {
+  for (int t = threadIdx.x; t < m * m; t += blockDim.x) Linv[t] = 0.0;
+  __syncthreads();
+  for (int r = 0; r < mb; r++) {
+    for (int c = threadIdx.x; c <= r; c += blockDim.x) {
+      double acc = (r == c) ? 1.0 : 0.0;
+      for (int t = c; t < r; t++) acc -= L[(size_t)r * m + t] * Linv[(size_t)t * m + c];
+      Linv[(size_t)r * m + c] = acc / L[(size_t)r * m + r];
+    }
+    __syncthreads();
+  }
+}
+
+// ---- adaptive cross approximation with full pivoting, in place on R --------------------
+// R (mi x mj, ld m) ~ U V^T with max|R - U V^T| <= tol or rank == cap.
+// U, V: m x cap row-major slots; each rank-one term balanced (|u| = |v|).
+struct AcaJob {
+  double* R;
+  double* U;
+  double* V;
+  int mi, mj;
+};
+__device__ __forceinline__ void argmax_merge(double& a, int& i, double a2, int i2) {
+  if (a2 > a || (a2 == a && i2 < i)) {
+    a = a2;
+    i = i2;
+  }
+}
+__device__ void block_argmax(double& a, int& i, double* sha, int* shi) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  for (int o = 16; o; o >>= 1) {
+    double a2 = __shfl_xor_sync(0xffffffffu, a, o);
+    int i2 = __shfl_xor_sync(0xffffffffu, i, o);
+    argmax_merge(a, i, a2, i2);
+  }
+  if (lane == 0) {
+    sha[wid] = a;
+    shi[wid] = i;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    a = lane < nw ? sha[lane] : -1.0;
+    i = lane < nw ? shi[lane] : 0x7fffffff;
+    for (int o = 16; o; o >>= 1) {
+      double a2 = __shfl_xor_sync(0xffffffffu, a, o);
+      int i2 = __shfl_xor_sync(0xffffffffu, i, o);
+      argmax_merge(a, i, a2, i2);
+    }
+    if (lane == 0) {
+      sha[0] = a;
+      shi[0] = i;
+    }
+  }
+  __syncthreads();
+  a = sha[0];
+  i = shi[0];
+  __syncthreads();
+}
+__global__ void __launch_bounds__(512) k_aca(const AcaJob* jobs, int m, int cap, double tol, int* ranks, int* capped) {
+  extern __shared__ double sm[];
+  double* u = sm;
+  double* v = sm + m;
+  __shared__ double sha[32];
+  __shared__ int shi[32];
+  const AcaJob jb = jobs[blockIdx.x];
+  const int mi = jb.mi, mj = jb.mj, tot = mi * mj;
+  double amax = -1.0;
+  int aidx = 0x7fffffff;
+  for (int t = threadIdx.x; t < tot; t += blockDim.x) argmax_merge(amax, aidx, fabs(jb.R[(size_t)(t / mj) * m + t % mj]), t);
+  int rank = 0, cp = 0;
+  for (;;) {
+    block_argmax(amax, aidx, sha, shi);
+    if (!(amax > tol) || aidx >= tot) break;
+    if (rank >= cap) {
+      cp = 1;
+      break;
+    }
+    const int pi = aidx / mj, pj = aidx % mj;
+    const double piv = jb.R[(size_t)pi * m + pj];
+    for (int t = threadIdx.x; t < mi; t += blockDim.x) u[t] = jb.R[(size_t)t * m + pj];
+    for (int t = threadIdx.x; t < mj; t += blockDim.x) v[t] = jb.R[(size_t)pi * m + t] / piv;
+    __syncthreads();
+    double nu2 = 0.0, nv2 = 0.0;
+    for (int t = threadIdx.x; t < mi; t += blockDim.x) nu2 += u[t] * u[t];
+    nu2 = block_sum(nu2, sha);
+    for (int t = threadIdx.x; t < mj; t += blockDim.x) nv2 += v[t] * v[t];
+    nv2 = block_sum(nv2, sha);
+    const double f = sqrt(sqrt(nv2) / sqrt(nu2));
+    for (int t = threadIdx.x; t < mi; t += blockDim.x) jb.U[(size_t)t * cap + rank] = u[t] * f;
+    for (int t = threadIdx.x; t < mj; t += blockDim.x) jb.V[(size_t)t * cap + rank] = v[t] / f;
+    amax = -1.0;
+    aidx = 0x7fffffff;
+    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+      int i = t / mj, jj = t % mj;
+      double* p = jb.R + (size_t)i * m + jj;
+      double x = *p - u[i] * v[jj];
+      *p = x;
+      argmax_merge(amax, aidx, fabs(x), t);
+    }
+    __syncthreads();
+    rank++;
+  }
+  if (threadIdx.x == 0) {
+    ranks[blockIdx.x] = rank;
+    if (cp) atomicAdd(capped, 1);
+  }
+}
+
+// ---- limit conditioning (Algorithm 5): a_i -= U_ij (V_ij^T y_j) --------------------------
+struct CondJob {
+  const double* U;
+  const double* V;
+  double* a;
+  double* b;
+  int mi, mj, k;
+};
+__global__ void k_condition(const CondJob* jobs, const double* y, int cap) {
+  __shared__ double t[1024];
+  const CondJob jb = jobs[blockIdx.x];
+  for (int c = threadIdx.x; c < jb.k; c += blockDim.x) {
+    double s = 0.0;
+    for (int u = 0; u < jb.mj; u++) s += jb.V[(size_t)u * cap + c] * y[u];
+    t[c] = s;
+  }
+  __syncthreads();
+  for (int v = threadIdx.x; v < jb.mi; v += blockDim.x) {
+    double s = 0.0;
+    for (int c = 0; c < jb.k; c++) s += jb.U[(size_t)v * cap + c] * t[c];
+    jb.a[v] -= s;
+    jb.b[v] -= s;
+  }
+}
+
+// ---- within-block permutation of a chosen block ------------------------------------------
+// rows/cols of the diagonal block, its index list and limits, and the rows of
+// the finished factor tiles U_jk (k < j).
+__global__ void k_permute_block(double* S, double* tmp, int64_t* idx, double* a, double* b, const int* order, int mb,
+                                int m, double* const* Urows, int nU, int cap) {
+  for (int t = threadIdx.x; t < mb * mb; t += blockDim.x) {
+    int i = t / mb, jj = t % mb;
+    tmp[(size_t)i * m + jj] = S[(size_t)order[i] * m + order[jj]];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < mb * mb; t += blockDim.x) {
+    int i = t / mb, jj = t % mb;
+    S[(size_t)i * m + jj] = tmp[(size_t)i * m + jj];
+  }
+  __syncthreads();
+  // idx, a, b via tmp as staging (3 * mb doubles)
+  double* ti = tmp;
+  double* ta = tmp + m;
+  double* tb = tmp + 2 * m;
+  for (int t = threadIdx.x; t < mb; t += blockDim.x) {
+    ti[t] = (double)idx[order[t]];
+    ta[t] = a[order[t]];
+    tb[t] = b[order[t]];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < mb; t += blockDim.x) {
+    idx[t] = (int64_t)ti[t];
+    a[t] = ta[t];
+    b[t] = tb[t];
+  }
+  __syncthreads();
+  for (int q = 0; q < nU; q++) {
+    double* U = Urows[q];
+    for (int t = threadIdx.x; t < mb * cap; t += blockDim.x) tmp[t] = U[(size_t)order[t / cap] * cap + t % cap];
+    __syncthreads();
+    for (int t = threadIdx.x; t < mb * cap; t += blockDim.x) U[t] = tmp[t];
+    __syncthreads();
+  }
+}
+
+// ---- pack slots into the compact factor layout ---------------------------------------------
+struct PackJob {
+  const double* U;   // slot, m x cap
+  const double* V;
+  double* Ucat;      // row block base of tile i: m x Krow_i, ld Krow
+  int64_t ldu, col0; // column offset of (i,j) within row block i
+  double* Vcat;      // first row of (i,j) in column block j: k x m
+  int32_t* vmap;
+  int64_t g0;        // global rank index of component 0
+  int mi, mj, k;
+};
+__global__ void k_pack(const PackJob* jobs, int m, int cap) {
+  const PackJob jb = jobs[blockIdx.x];
+  for (int t = threadIdx.x; t < jb.mi * jb.k; t += blockDim.x) {
+    int v = t / jb.k, c = t % jb.k;
+    jb.Ucat[(int64_t)v * jb.ldu + jb.col0 + c] = jb.U[(size_t)v * cap + c];
+  }
+  for (int t = threadIdx.x; t < jb.k * m; t += blockDim.x) {
+    int c = t / m, u = t % m;
+    jb.Vcat[(int64_t)c * m + u] = (u < jb.mj) ? jb.V[(size_t)u * cap + c] : 0.0;
+  }
+  for (int c = threadIdx.x; c < jb.k; c += blockDim.x) jb.vmap[c] = (int32_t)(jb.g0 + c);
+}
+
+// ---------------------------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------------------------
+
+// k-d bisection ordering (Section 3.2 geometric indexing, cardinality balanced):
+// a set spanning t tiles splits into the first ceil(t/2)*m points and the rest,
+// along the coordinate of larger extent (x on a tie), ranked by (that
+// coordinate, the other one, original index); leaves depth first.
+static void kd_order(const double* xy, int64_t n, int m, std::vector<int64_t>& perm, std::vector<int>& sizes) {
+  perm.resize(n);
+  std::iota(perm.begin(), perm.end(), 0);
+  sizes.clear();
+  std::function<void(int64_t, int64_t)> split = [&](int64_t lo, int64_t hi) {
+    int64_t cnt = hi - lo;
+    int64_t t = (cnt + m - 1) / m;
+    if (t <= 1) {
+      sizes.push_back((int)cnt);
+      return;
+    }
+    int64_t nl = ((t + 1) / 2) * m;
+    double mn[2] = {INFINITY, INFINITY}, mx[2] = {-INFINITY, -INFINITY};
+    for (int64_t q = lo; q < hi; q++)
+      for (int d = 0; d < 2; d++) {
+        mn[d] = std::min(mn[d], xy[2 * perm[q] + d]);
+        mx[d] = std::max(mx[d], xy[2 * perm[q] + d]);
+      }
+    int ax = (mx[0] - mn[0] >= mx[1] - mn[1]) ? 0 : 1, ot = 1 - ax;
+    std::sort(perm.begin() + lo, perm.begin() + hi, [&](int64_t p, int64_t q) {
+      double pa = xy[2 * p + ax], qa = xy[2 * q + ax];
+      if (pa != qa) return pa < qa;
+      double po = xy[2 * p + ot], qo = xy[2 * q + ot];
+      if (po != qo) return po < qo;
+      return p < q;
+    });
+    split(lo, lo + nl);
+    split(lo + nl, hi);
+  };
+  split(0, n);
+}
+
+// Device buffers of one factorisation; freed on every exit path.
+struct Build {
+  std::vector<void*> ptrs;
+  template <typename T>
+  int get(T** p, size_t count) {
+    TLR_CHECK(dalloc(p, std::max<size_t>(count, 1)));
+    ptrs.push_back(*p);
+    return TLRMVN_OK;
+  }
+  ~Build() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+};
+
+template <typename T>
+static int upload(T* dst, const std::vector<T>& src, cudaStream_t st) {
+  if (src.empty()) return TLRMVN_OK;
+  TLR_CUDA(cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+  return TLRMVN_OK;
+}
+
+static int check_status(int* d_status, cudaStream_t st, const char* what) {
+  int h = 0;
+  TLR_CUDA(cudaMemcpyAsync(&h, d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TLR_CUDA(cudaStreamSynchronize(st));
+  if (h) return fail(h, std::string(what) + ": covariance block is not positive definite");
+  return TLRMVN_OK;
+}
+
+template <bool TA, bool TB>
+static int run_batched(std::vector<GemmEntry>& ent, std::vector<GemmSeg>& seg, GemmEntry* d_ent, GemmSeg* d_seg,
+                       size_t ent_cap, size_t seg_cap, cudaStream_t st) {
+  if (ent.empty()) return TLRMVN_OK;
+  if (ent.size() > ent_cap || seg.size() > seg_cap) return fail(TLRMVN_E_CUDA, "internal: gemm job list overflow");
+  int maxM = 0, maxN = 0;
+  for (auto& e : ent) {
+    maxM = std::max(maxM, e.M);
+    maxN = std::max(maxN, e.N);
+  }
+  TLR_CHECK(upload(d_ent, ent, st));
+  TLR_CHECK(upload(d_seg, seg, st));
+  for (size_t z0 = 0; z0 < ent.size(); z0 += 65535) {
+    unsigned nz = (unsigned)std::min<size_t>(65535, ent.size() - z0);
+    dim3 grid((unsigned)((maxN + 63) / 64), (unsigned)((maxM + 63) / 64), nz);
+    k_gemm_batched<TA, TB><<<grid, 256, 0, st>>>(d_ent + z0, d_seg);
+  }
+  TLR_CUDA(cudaGetLastError());
+  // the host vectors are reused right away: wait for the uploads
+  TLR_CUDA(cudaStreamSynchronize(st));
+  return TLRMVN_OK;
+}
+
+static int factor_build(const CovSrc& src, int64_t n, std::vector<int64_t> geo, std::vector<int> sizes,
+                        const double* a_ref, const double* b_ref, const tlrmvn_factor_opts& o, Factor& F) {
+  cudaStream_t st = pick_stream(o.stream);
+  const int m = o.tile;
+  const int r = (int)sizes.size();
+  const int cap = (o.max_rank > 0) ? std::min(o.max_rank, m) : m;
+  const bool reorder = o.reorder != TLRMVN_REORDER_NONE;
+  Build bd;
+  // block-id layout: block b's variables at [b*m, b*m + sizes[b])
+  std::vector<int64_t> idx_h((size_t)r * m, 0);
+  {
+    int64_t off = 0;
+    for (int b = 0; b < r; b++) {
+      for (int t = 0; t < sizes[b]; t++) idx_h[(size_t)b * m + t] = geo[off + t];
+      off += sizes[b];
+    }
+  }
+  int64_t* d_idx;
+  int* d_bsize;
+  double *d_a, *d_b, *diagS, *work, *Sij, *Lij, *Linv, *pool, *Xs, *Ys, *d_y;
+  int *d_status, *d_order, *d_ranks, *d_capped, *d_blist;
+  double* d_logp;
+  TLR_CHECK(bd.get(&d_idx, (size_t)r * m));
+  TLR_CHECK(bd.get(&d_bsize, r));
+  TLR_CHECK(bd.get(&d_a, (size_t)r * m));
+  TLR_CHECK(bd.get(&d_b, (size_t)r * m));
+  TLR_CHECK(bd.get(&diagS, (size_t)r * m * m));
+  TLR_CHECK(bd.get(&d_status, 1));
+  double* ptmp;
+  TLR_CHECK(bd.get(&d_order, (size_t)r * m));
+  TLR_CHECK(bd.get(&d_y, (size_t)r * m));
+  TLR_CHECK(bd.get(&ptmp, std::max<size_t>((size_t)m * std::max(m, cap), 3 * (size_t)m)));
+  TLR_CHECK(bd.get(&d_ranks, r));
+  TLR_CHECK(bd.get(&d_capped, 1));
+  TLR_CHECK(bd.get(&d_blist, r));
+  TLR_CHECK(bd.get(&d_logp, r));
+  TLR_CHECK(bd.get(&Linv, (size_t)m * m));
+  const size_t npairs = (size_t)r * (r - 1) / 2;
+  TLR_CHECK(bd.get(&pool, std::max<size_t>(npairs, 1) * 2 * (size_t)m * cap));
+  TLR_CHECK(bd.get(&Sij, (size_t)std::max(r - 1, 1) * m * m));
+  TLR_CHECK(bd.get(&Lij, (size_t)std::max(r - 1, 1) * m * m));
+  const size_t uc_par = reorder ? (size_t)r : 1;
+  TLR_CHECK(bd.get(&work, uc_par * m * m));
+  const size_t max_pairs_step = (size_t)(r / 2 + 1) * (size_t)(r / 2 + 1);
+  TLR_CHECK(bd.get(&Xs, max_pairs_step * cap * cap));
+  TLR_CHECK(bd.get(&Ys, max_pairs_step * cap * m));
+  const size_t ent_cap = std::max<size_t>(max_pairs_step, (size_t)r) + 8, seg_cap = ent_cap;
+  GemmEntry* d_ent;
+  GemmSeg* d_seg;
+  TileJob* d_tj;
+  AcaJob* d_aj;
+  CondJob* d_cj;
+  PackJob* d_pj;
+  double** d_urows;
+  TLR_CHECK(bd.get(&d_ent, ent_cap));
+  TLR_CHECK(bd.get(&d_seg, seg_cap));
+  TLR_CHECK(bd.get(&d_tj, (size_t)r));
+  TLR_CHECK(bd.get(&d_aj, (size_t)r));
+  TLR_CHECK(bd.get(&d_cj, (size_t)r));
+  TLR_CHECK(bd.get(&d_pj, std::max<size_t>(npairs, 1)));
+  TLR_CHECK(bd.get(&d_urows, (size_t)r));
+  TLR_CHECK(upload(d_idx, idx_h, st));
+  TLR_CHECK(upload(d_bsize, sizes, st));
+  TLR_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), st));
+  TLR_CUDA(cudaMemsetAsync(d_capped, 0, sizeof(int), st));
+  if (reorder) {
+    std::vector<double> ah((size_t)r * m, 0.0), bh((size_t)r * m, 0.0);
+    for (int b = 0; b < r; b++)
+      for (int t = 0; t < sizes[b]; t++) {
+        ah[(size_t)b * m + t] = a_ref[idx_h[(size_t)b * m + t]];
+        bh[(size_t)b * m + t] = b_ref[idx_h[(size_t)b * m + t]];
+      }
+    TLR_CHECK(upload(d_a, ah, st));
+    TLR_CHECK(upload(d_b, bh, st));
+  }
+  // diagonal blocks of Sigma
+  {
+    std::vector<TileJob> tj(r);
+    for (int b = 0; b < r; b++)
+      tj[b] = TileJob{diagS + (size_t)b * m * m, d_idx + (size_t)b * m, d_idx + (size_t)b * m, sizes[b], sizes[b]};
+    TLR_CHECK(upload(d_tj, tj, st));
+    k_cov_tiles<<<dim3(std::max(1, (m * m + 255) / 256 / 4), r), 256, 0, st>>>(d_tj, src, m);
+    TLR_CUDA(cudaGetLastError());
+  }
+  std::vector<int> pos2blk(r);
+  std::iota(pos2blk.begin(), pos2blk.end(), 0);
+  const size_t uc_smem = (size_t)m * (5 * sizeof(double) + sizeof(int));
+  TLR_CUDA(cudaFuncSetAttribute(k_uc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)uc_smem));
+  TLR_CUDA(cudaFuncSetAttribute(k_aca, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * m * sizeof(double))));
+  TLR_CUDA(cudaFuncSetAttribute(k_potrf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(m * sizeof(double))));
+  const int uc_threads = m >= 256 ? 512 : 256;
+
+  if (o.reorder == TLRMVN_REORDER_BLOCK) {
+    // Algorithm 4: one UC estimate per original block, then a selection sort
+    std::vector<int> bl(r);
+    std::iota(bl.begin(), bl.end(), 0);
+    TLR_CHECK(upload(d_blist, bl, st));
+    k_uc<<<r, uc_threads, uc_smem, st>>>(d_blist, diagS, d_bsize, m, d_a, d_b, work, d_logp, 1, d_order, d_y,
+                                          d_status);
+    TLR_CUDA(cudaGetLastError());
+    TLR_CHECK(check_status(d_status, st, "block reordering"));
+    // within-block order: the UC pivot order of each original block
+    for (int b = 0; b < r; b++) {
+      k_permute_block<<<1, 512, 0, st>>>(diagS + (size_t)b * m * m, ptmp, d_idx + (size_t)b * m, d_a + (size_t)b * m,
+                                         d_b + (size_t)b * m, d_order + (size_t)b * m, sizes[b], m, d_urows, 0, cap);
+      TLR_CUDA(cudaGetLastError());
+    }
+    std::vector<double> p(r);
+    TLR_CUDA(cudaMemcpyAsync(p.data(), d_logp, r * 8, cudaMemcpyDeviceToHost, st));
+    TLR_CUDA(cudaStreamSynchronize(st));
+    for (int j = 0; j < r; j++) {
+      int best = j;
+      for (int l = j + 1; l < r; l++)
+        if (p[pos2blk[l]] < p[pos2blk[best]]) best = l;
+      std::swap(pos2blk[j], pos2blk[best]);
+    }
+  }
+
+  std::vector<int> slot((size_t)r * r, -1), rank((size_t)r * r, 0);
+  int next_slot = 0;
+  auto Uslot = [&](int s) { return pool + (size_t)s * 2 * m * cap; };
+  auto Vslot = [&](int s) { return pool + (size_t)s * 2 * m * cap + (size_t)m * cap; };
+  std::vector<GemmEntry> ent;
+  std::vector<GemmSeg> seg;
+
+  for (int j = 0; j < r; j++) {
+    // -- choose the block of position j and its within-block order
+    bool permute = false;
+    int chosen = 0;
+    if (o.reorder == TLRMVN_REORDER_ITERATIVE) {
+      std::vector<int> bl(pos2blk.begin() + j, pos2blk.end());
+      TLR_CHECK(upload(d_blist, bl, st));
+      k_uc<<<(unsigned)bl.size(), uc_threads, uc_smem, st>>>(d_blist, diagS, d_bsize, m, d_a, d_b, work, d_logp, 1,
+                                                             d_order, d_y, d_status);
+      TLR_CUDA(cudaGetLastError());
+      TLR_CHECK(check_status(d_status, st, "iterative block reordering"));
+      std::vector<double> p(bl.size());
+      TLR_CUDA(cudaMemcpyAsync(p.data(), d_logp, p.size() * 8, cudaMemcpyDeviceToHost, st));
+      TLR_CUDA(cudaStreamSynchronize(st));
+      int best = 0;
+      for (size_t l = 1; l < p.size(); l++)
+        if (p[l] < p[best]) best = (int)l;
+      const int jt = j + best;
+      chosen = best;
+      if (jt != j) {
+        std::swap(pos2blk[j], pos2blk[jt]);
+        for (int k = 0; k < j; k++) {
+          std::swap(slot[(size_t)j * r + k], slot[(size_t)jt * r + k]);
+          std::swap(rank[(size_t)j * r + k], rank[(size_t)jt * r + k]);
+        }
+      }
+      permute = true;
+    }
+    const int bj = pos2blk[j];
+    const int mj = sizes[bj];
+    double* Sjj = diagS + (size_t)bj * m * m;
+    const double* yj = d_y + (size_t)chosen * m;
+    if (permute) {
+      std::vector<double*> ur;
+      for (int k = 0; k < j; k++)
+        if (rank[(size_t)j * r + k] > 0) ur.push_back(Uslot(slot[(size_t)j * r + k]));
+      TLR_CHECK(upload(d_urows, ur, st));
+      k_permute_block<<<1, 512, 0, st>>>(Sjj, ptmp, d_idx + (size_t)bj * m, d_a + (size_t)bj * m, d_b + (size_t)bj * m,
+                                         d_order + (size_t)chosen * m, mj, m, d_urows, (int)ur.size(), cap);
+      TLR_CUDA(cudaGetLastError());
+      TLR_CUDA(cudaStreamSynchronize(st));
+    }
+    // -- L_jj and its inverse
+    k_potrf<<<1, 512, m * sizeof(double), st>>>(Sjj, mj, m, d_status);
+    TLR_CUDA(cudaGetLastError());
+    TLR_CHECK(check_status(d_status, st, "diagonal Cholesky"));
+    k_trinv<<<1, 512, 0, st>>>(Sjj, Linv, mj, m);
+    const int nrem = r - 1 - j;
+    if (nrem == 0) break;
+    // -- Sigma_ij for the remaining blocks
+    {
+      std::vector<TileJob> tj(nrem);
+      for (int q = 0; q < nrem; q++) {
+        int bi = pos2blk[j + 1 + q];
+        tj[q] = TileJob{Sij + (size_t)q * m * m, d_idx + (size_t)bi * m, d_idx + (size_t)bj * m, sizes[bi], mj};
+      }
+      TLR_CHECK(upload(d_tj, tj, st));
+      k_cov_tiles<<<dim3(std::max(1, (m * m + 255) / 256 / 4), nrem), 256, 0, st>>>(d_tj, src, m);
+      TLR_CUDA(cudaGetLastError());
+      TLR_CUDA(cudaStreamSynchronize(st));
+    }
+    // -- left-looking update S_ij -= sum_k U_ik (V_ik^T V_jk) U_jk^T
+    {
+      struct P {
+        int q, k;
+        size_t xo, yo;
+      };
+      std::vector<P> pairs;
+      size_t xo = 0, yo = 0;
+      for (int q = 0; q < nrem; q++) {
+        int i = j + 1 + q;
+        for (int k = 0; k < j; k++) {
+          int kik = rank[(size_t)i * r + k], kjk = rank[(size_t)j * r + k];
+          if (!kik || !kjk) continue;
+          pairs.push_back(P{q, k, xo, yo});
+          xo += (size_t)kik * kjk;
+          yo += (size_t)kik * m;
+        }
+      }
+      if (!pairs.empty()) {
+        if (xo > max_pairs_step * cap * cap || yo > max_pairs_step * cap * m)
+          return fail(TLRMVN_E_CUDA, "internal: left-looking scratch overflow");
+        ent.clear();
+        seg.clear();
+        for (auto& pr : pairs) {  // X_ik = V_ik^T V_jk
+          int i = j + 1 + pr.q;
+          int kik = rank[(size_t)i * r + pr.k], kjk = rank[(size_t)j * r + pr.k];
+          int mk = sizes[pos2blk[pr.k]];
+          seg.push_back(GemmSeg{Vslot(slot[(size_t)i * r + pr.k]), Vslot(slot[(size_t)j * r + pr.k]), cap, cap, mk});
+          ent.push_back(GemmEntry{Xs + pr.xo, kjk, kik, kjk, (int)seg.size() - 1, (int)seg.size(), 1.0, 0.0});
+        }
+        TLR_CHECK((run_batched<true, false>(ent, seg, d_ent, d_seg, ent_cap, seg_cap, st)));
+        ent.clear();
+        seg.clear();
+        for (auto& pr : pairs) {  // Y_ik = X_ik U_jk^T
+          int i = j + 1 + pr.q;
+          int kik = rank[(size_t)i * r + pr.k], kjk = rank[(size_t)j * r + pr.k];
+          seg.push_back(GemmSeg{Xs + pr.xo, Uslot(slot[(size_t)j * r + pr.k]), kjk, cap, kjk});
+          ent.push_back(GemmEntry{Ys + pr.yo, m, kik, mj, (int)seg.size() - 1, (int)seg.size(), 1.0, 0.0});
+        }
+        TLR_CHECK((run_batched<false, true>(ent, seg, d_ent, d_seg, ent_cap, seg_cap, st)));
+        ent.clear();
+        seg.clear();
+        size_t p0 = 0;
+        for (int q = 0; q < nrem; q++) {  // S_ij -= sum_k U_ik Y_ik
+          int i = j + 1 + q;
+          int s0 = (int)seg.size();
+          while (p0 < pairs.size() && pairs[p0].q == q) {
+            auto& pr = pairs[p0++];
+            int kik = rank[(size_t)i * r + pr.k];
+            seg.push_back(GemmSeg{Uslot(slot[(size_t)i * r + pr.k]), Ys + pr.yo, cap, m, kik});
+          }
+          if ((int)seg.size() > s0)
+            ent.push_back(GemmEntry{Sij + (size_t)q * m * m, m, sizes[pos2blk[i]], mj, s0, (int)seg.size(), -1.0, 1.0});
+        }
+        TLR_CHECK((run_batched<false, false>(ent, seg, d_ent, d_seg, ent_cap, seg_cap, st)));
+      }
+    }
+    // -- L_ij = S_ij L_jj^-T
+    ent.clear();
+    seg.clear();
+    for (int q = 0; q < nrem; q++) {
+      int mi = sizes[pos2blk[j + 1 + q]];
+      seg.push_back(GemmSeg{Sij + (size_t)q * m * m, Linv, m, m, mj});
+      ent.push_back(GemmEntry{Lij + (size_t)q * m * m, m, mi, mj, q, q + 1, 1.0, 0.0});
+    }
+    TLR_CHECK((run_batched<false, true>(ent, seg, d_ent, d_seg, ent_cap, seg_cap, st)));
+    // -- ACA of every L_ij into fresh slots
+    {
+      std::vector<AcaJob> aj(nrem);
+      for (int q = 0; q < nrem; q++) {
+        int i = j + 1 + q;
+        int s = next_slot++;
+        slot[(size_t)i * r + j] = s;
+        aj[q] = AcaJob{Lij + (size_t)q * m * m, Uslot(s), Vslot(s), sizes[pos2blk[i]], mj};
+      }
+      TLR_CHECK(upload(d_aj, aj, st));
+      k_aca<<<nrem, 512, 2 * m * sizeof(double), st>>>(d_aj, m, cap, o.tol, d_ranks, d_capped);
+      TLR_CUDA(cudaGetLastError());
+      std::vector<int> rk(nrem);
+      TLR_CUDA(cudaMemcpyAsync(rk.data(), d_ranks, nrem * sizeof(int), cudaMemcpyDeviceToHost, st));
+      TLR_CUDA(cudaStreamSynchronize(st));
+      for (int q = 0; q < nrem; q++) rank[(size_t)(j + 1 + q) * r + j] = rk[q];
+    }
+    // -- Algorithm 5: condition the limits of the remaining blocks
+    if (o.reorder == TLRMVN_REORDER_ITERATIVE) {
+      std::vector<CondJob> cj;
+      for (int q = 0; q < nrem; q++) {
+        int i = j + 1 + q, bi = pos2blk[i], k = rank[(size_t)i * r + j];
+        if (!k) continue;
+        int s = slot[(size_t)i * r + j];
+        cj.push_back(CondJob{Uslot(s), Vslot(s), d_a + (size_t)bi * m, d_b + (size_t)bi * m, sizes[bi], mj, k});
+      }
+      if (!cj.empty()) {
+        TLR_CHECK(upload(d_cj, cj, st));
+        k_condition<<<(unsigned)cj.size(), 256, 0, st>>>(d_cj, yj, cap);
+        TLR_CUDA(cudaGetLastError());
+        TLR_CUDA(cudaStreamSynchronize(st));
+      }
+    }
+    // -- diagonal Schur blocks: S_ii -= U_ij (V_ij^T V_ij) U_ij^T
+    {
+      std::vector<int> qs;
+      size_t xo = 0, yo = 0;
+      std::vector<size_t> xof, yof;
+      for (int q = 0; q < nrem; q++) {
+        int k = rank[(size_t)(j + 1 + q) * r + j];
+        if (!k) continue;
+        qs.push_back(q);
+        xof.push_back(xo);
+        yof.push_back(yo);
+        xo += (size_t)k * k;
+        yo += (size_t)k * m;
+      }
+      if (!qs.empty()) {
+        ent.clear();
+        seg.clear();
+        for (size_t t = 0; t < qs.size(); t++) {
+          int i = j + 1 + qs[t], k = rank[(size_t)i * r + j], s = slot[(size_t)i * r + j];
+          seg.push_back(GemmSeg{Vslot(s), Vslot(s), cap, cap, mj});
+          ent.push_back(GemmEntry{Xs + xof[t], k, k, k, (int)t, (int)t + 1, 1.0, 0.0});
+        }
+        TLR_CHECK((run_batched<true, false>(ent, seg, d_ent, d_seg, ent_cap, seg_cap, st)));
+        ent.clear();
+        seg.clear();
+        for (size_t t = 0; t < qs.size(); t++) {
+          int i = j + 1 + qs[t], k = rank[(size_t)i * r + j], s = slot[(size_t)i * r + j];
+          int mi = sizes[pos2blk[i]];
+          seg.push_back(GemmSeg{Xs + xof[t], Uslot(s), k, cap, k});
+          ent.push_back(GemmEntry{Ys + yof[t], m, k, mi, (int)t, (int)t + 1, 1.0, 0.0});
+        }
+        TLR_CHECK((run_batched<false, true>(ent, seg, d_ent, d_seg, ent_cap, seg_cap, st)));
+        ent.clear();
+        seg.clear();
+        for (size_t t = 0; t < qs.size(); t++) {
+          int i = j + 1 + qs[t], k = rank[(size_t)i * r + j], s = slot[(size_t)i * r + j];
+          int bi = pos2blk[i], mi = sizes[bi];
+          seg.push_back(GemmSeg{Uslot(s), Ys + yof[t], cap, m, k});
+          ent.push_back(GemmEntry{diagS + (size_t)bi * m * m, m, mi, mi, (int)t, (int)t + 1, -1.0, 1.0});
+        }
+        TLR_CHECK((run_batched<false, false>(ent, seg, d_ent, d_seg, ent_cap, seg_cap, st)));
+      }
+    }
+  }
+  // -- assemble the handle
+  F.n = n;
+  F.r = r;
+  F.m = m;
+  F.tile_off.assign(r + 1, 0);
+  for (int j = 0; j < r; j++) F.tile_off[j + 1] = F.tile_off[j] + sizes[pos2blk[j]];
+  F.rank = std::vector<int32_t>(rank.begin(), rank.end());
+  TLR_CUDA(cudaMemcpyAsync(&F.capped, d_capped, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TLR_CUDA(cudaStreamSynchronize(st));
+  TLR_CHECK(factor_alloc_compact(F));
+  for (int j = 0; j < r; j++)
+    TLR_CUDA(cudaMemcpyAsync(F.B + (size_t)j * m * m, diagS + (size_t)pos2blk[j] * m * m, (size_t)m * m * 8,
+                             cudaMemcpyDeviceToDevice, st));
+  {
+    std::vector<PackJob> pj;
+    for (int i = 0; i < r; i++) {
+      int64_t col = 0;
+      for (int j = 0; j < i; j++) {
+        int k = rank[(size_t)i * r + j];
+        if (!k) continue;
+        int64_t vr = 0;
+        for (int t = j + 1; t < i; t++) vr += rank[(size_t)t * r + j];
+        int s = slot[(size_t)i * r + j];
+        pj.push_back(PackJob{Uslot(s), Vslot(s), F.Ucat + (size_t)m * F.krow_off[i], F.krow(i), col,
+                             F.Vcat + (size_t)m * (F.kcol_off[j] + vr), F.vmap + F.kcol_off[j] + vr,
+                             F.krow_off[i] + col, sizes[pos2blk[i]], sizes[pos2blk[j]], k});
+        col += k;
+      }
+    }
+    if (!pj.empty()) {
+      TLR_CHECK(upload(d_pj, pj, st));
+      k_pack<<<(unsigned)pj.size(), 256, 0, st>>>(d_pj, m, cap);
+      TLR_CUDA(cudaGetLastError());
+    }
+  }
+  std::vector<int64_t> idx_fin((size_t)r * m);
+  TLR_CUDA(cudaMemcpyAsync(idx_fin.data(), d_idx, idx_fin.size() * 8, cudaMemcpyDeviceToHost, st));
+  TLR_CUDA(cudaStreamSynchronize(st));
+  F.perm.resize(n);
+  for (int j = 0; j < r; j++)
+    for (int t = 0; t < sizes[pos2blk[j]]; t++) F.perm[F.tile_off[j] + t] = idx_fin[(size_t)pos2blk[j] * m + t];
+  return factor_finish(F, st);
+}
+
+static int check_fopts(const tlrmvn_factor_opts* o, int64_t n, const double* a, const double* b) {
+  if (!o) return fail(TLRMVN_E_INVAL, "null options");
+  if (n <= 0) return fail(TLRMVN_E_INVAL, "n must be positive");
+  if (o->tile <= 0 || o->tile > 1024) return fail(TLRMVN_E_INVAL, "tile must be in 1..1024");
+  if (!(o->tol >= 0.0)) return fail(TLRMVN_E_INVAL, "tol must be >= 0");
+  if (o->max_rank < 0) return fail(TLRMVN_E_INVAL, "max_rank must be >= 0");
+  if (o->reorder < 0 || o->reorder > 2) return fail(TLRMVN_E_INVAL, "bad reorder mode");
+  if (o->reorder != TLRMVN_REORDER_NONE) {
+    if (!a || !b) return fail(TLRMVN_E_INVAL, "reordering needs limits a_ref, b_ref");
+    for (int64_t i = 0; i < n; i++)
+      if (std::isnan(a[i]) || std::isnan(b[i]) || a[i] > b[i] || a[i] == INFINITY || b[i] == -INFINITY)
+        return fail(TLRMVN_E_INVAL, "limits must satisfy a_i <= b_i, no NaN");
+  }
+  return TLRMVN_OK;
+}
+
+}  // namespace tlrmvn
+
+using namespace tlrmvn;
+
+extern "C" int tlrmvn_factor_kernel(const double* xy, int64_t n, int kernel, const double* params, double nugget,
+                                    const double* a_ref, const double* b_ref, const tlrmvn_factor_opts* opts,
+                                    tlrmvn_factor_t* out) {
+  if (!xy || !params || !out) return fail(TLRMVN_E_INVAL, "null argument");
+  TLR_CHECK(check_fopts(opts, n, a_ref, b_ref));
+  if (kernel < 0 || kernel > 2) return fail(TLRMVN_E_INVAL, "unknown kernel");
+  if (!(params[0] > 0.0) || (kernel == TLRMVN_KERNEL_EXP_MATERN15 && !(params[1] > 0.0)) || !(nugget >= 0.0))
+    return fail(TLRMVN_E_INVAL, "kernel parameters must be positive");
+  for (int64_t i = 0; i < 2 * n; i++)
+    if (!std::isfinite(xy[i])) return fail(TLRMVN_E_INVAL, "locations must be finite");
+  std::vector<int64_t> geo;
+  std::vector<int> sizes;
+  kd_order(xy, n, opts->tile, geo, sizes);
+  cudaStream_t st = pick_stream(opts->stream);
+  double* dxy = nullptr;
+  TLR_CHECK(dalloc(&dxy, (size_t)2 * n));
+  cudaError_t e = cudaMemcpyAsync(dxy, xy, (size_t)2 * n * 8, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) {
+    dfree(dxy);
+    return cuda_fail(e, "upload locations");
+  }
+  CovSrc src{dxy, nullptr, 0, kernel, params[0], kernel == TLRMVN_KERNEL_EXP_MATERN15 ? params[1] : 0.0, nugget};
+  Factor* F = new Factor();
+  cudaGetDevice(&F->device);
+  int s = factor_build(src, n, geo, sizes, a_ref, b_ref, *opts, *F);
+  dfree(dxy);
+  if (s != TLRMVN_OK) {
+    delete F;
+    return s;
+  }
+  *out = reinterpret_cast<tlrmvn_factor_t>(F);
+  return TLRMVN_OK;
+}
+
+extern "C" int tlrmvn_factor_dense(const double* cov, int64_t n, int64_t ld, const double* a_ref, const double* b_ref,
+                                   const tlrmvn_factor_opts* opts, tlrmvn_factor_t* out) {
+  if (!cov || !out) return fail(TLRMVN_E_INVAL, "null argument");
+  TLR_CHECK(check_fopts(opts, n, a_ref, b_ref));
+  if (ld < n) return fail(TLRMVN_E_INVAL, "ld must be >= n");
+  std::vector<int64_t> geo(n);
+  std::iota(geo.begin(), geo.end(), 0);
+  std::vector<int> sizes;
+  for (int64_t off = 0; off < n; off += opts->tile) sizes.push_back((int)std::min<int64_t>(opts->tile, n - off));
+  cudaStream_t st = pick_stream(opts->stream);
+  double* dcov = nullptr;
+  TLR_CHECK(dalloc(&dcov, (size_t)ld * n));
+  cudaError_t e = cudaMemcpyAsync(dcov, cov, (size_t)ld * n * 8, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) {
+    dfree(dcov);
+    return cuda_fail(e, "upload covariance");
+  }
+  CovSrc src{nullptr, dcov, ld, 0, 0.0, 0.0, 0.0};
+  Factor* F = new Factor();
+  cudaGetDevice(&F->device);
+  int s = factor_build(src, n, geo, sizes, a_ref, b_ref, *opts, *F);
+  dfree(dcov);
+  if (s != TLRMVN_OK) {
+    delete F;
+    return s;
+  }
+  *out = reinterpret_cast<tlrmvn_factor_t>(F);
+  return TLRMVN_OK;
+}

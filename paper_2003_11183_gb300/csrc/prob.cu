@@ -1,0 +1,512 @@
+// The TLR quasi-Monte Carlo integrand (Algorithms 6 and 7) and its estimator.
+//
+// For a chunk of C samples (shift-major sample index g = s*N + k-1) the
+// integrand walks the diagonal tiles i = 0..r-1:
+//   1. low-rank shift   Delta_i = Ucat_i * W_row_i         (m x C)   [Algorithm 6, shift of the limits]
+//   2. diagonal sweep   per sample, eq. (2) on tile B_i with limits r_s b - Delta - s
+//                       -> y_i (m x C) and the log of the tile's product
+//   3. projection       W_col_i = Vcat_i * y_i   scattered into W (ktot x C)
+// Step 1 accumulates, in one product, the sums that Algorithm 6 adds tile by
+// tile after every diagonal block: sum_{j<i} U_ij (V_ij^T y_j).  Student-t
+// problems first scale the limits by chi_nu^-1(w0)/sqrt(nu) per sample (Algorithm 7).
+// Per-sample logs are reduced per shift by a log-sum-exp and then across shifts (Section 2.1).
+#include "common.cuh"
+#include "gemm.cuh"
+
+#include <algorithm>
+#include <cstring>
+
+namespace tlrmvn {
+
+// ---- Student-t scale (Algorithm 7): chi_nu^-1(w0)/sqrt(nu) ------------------------
+// Regularised incomplete gamma P(a,x) and Q(a,x) = 1 - P: power series below
+// x = a + 1, Legendre continued fraction (modified Lentz) above.
+__device__ void gamma_pq(double a, double x, double& P, double& Q) {
+  if (!(x > 0.0)) {
+    P = 0.0;
+    Q = 1.0;
+    return;
+  }
+  double lpref = a * log(x) - x - lgamma(a);
+  if (x < a + 1.0) {
+    double ap = a, term = 1.0 / a, sum = term;
+    for (int it = 0; it < 2000; it++) {
+      ap += 1.0;
+      term *= x / ap;
+      sum += term;
+      if (fabs(term) < fabs(sum) * 1e-17) break;
+    }
+    P = sum * exp(lpref);
+    Q = 1.0 - P;
+  } else {
+    const double tiny = 1e-300;
+    double bq = x + 1.0 - a, c = 1.0 / tiny, d = 1.0 / bq, h = d;
+    for (int i = 1; i < 2000; i++) {
+      double an = -i * (i - a);
+      bq += 2.0;
+      d = an * d + bq;
+      if (fabs(d) < tiny) d = tiny;
+      c = bq + an / c;
+      if (fabs(c) < tiny) c = tiny;
+      d = 1.0 / d;
+      double del = d * c;
+      h *= del;
+      if (fabs(del - 1.0) < 1e-16) break;
+    }
+    Q = exp(lpref) * h;
+    P = 1.0 - Q;
+  }
+}
+
+// x with P(a, x) = p (q = 1 - p exactly): Wilson-Hilferty start, Halley steps.
+__device__ double gamma_p_inv(double a, double p, double q) {
+  double z = ndtri2(p, q, log(p));
+  double t = 1.0 / (9.0 * a);
+  double base = 1.0 - t + z * sqrt(t);
+  double x = a * base * base * base;
+  if (!(x > 0.0)) x = exp((log(p) + lgamma(a + 1.0)) / a);
+  const double lga = lgamma(a);
+  for (int it = 0; it < 100; it++) {
+    double P, Q;
+    gamma_pq(a, x, P, Q);
+    double f = (p < 0.5) ? (P - p) : (q - Q);
+    double f1 = exp((a - 1.0) * log(x) - x - lga);
+    if (!(f1 > 0.0)) break;
+    double dx = f / f1;
+    double h2 = (a - 1.0) / x - 1.0;
+    double corr = 0.5 * dx * h2;
+    double step = (fabs(corr) < 0.5) ? dx / (1.0 - corr) : dx;
+    double xn = x - step;
+    if (!(xn > 0.0)) xn = 0.5 * x;
+    if (fabs(xn - x) <= 4e-16 * x) {
+      x = xn;
+      break;
+    }
+    x = xn;
+  }
+  return x;
+}
+
+__global__ void k_chi_scale(double* rs, const uint64_t* Q, const uint64_t* D, int64_t ldD, int64_t coord,
+                            int64_t sample0, int64_t N, int64_t C, double nu, int periodize) {
+  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  int64_t g = sample0 + c, s = g / N;
+  uint64_t k = (uint64_t)(g - s * N) + 1;
+  double w, wc;
+  lattice_w(k * Q[coord] + D[s * ldD + coord], periodize, w, wc);
+  double x = gamma_p_inv(0.5 * nu, w, wc);
+  rs[c] = sqrt(2.0 * x / nu);
+}
+
+// ---- limits: permute to factor order and validate ---------------------------------
+__global__ void k_permute_limits(const double* a, const double* b, const int64_t* perm, int64_t n, double* ap,
+                                 double* bp, int* bad) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  double av = a[perm[t]], bv = b[perm[t]];
+  if (isnan(av) || isnan(bv) || av > bv || av == INFINITY || bv == -INFINITY) atomicExch(bad, 1);
+  ap[t] = av;
+  bp[t] = bv;
+}
+
+// ---- diagonal-tile sweep (eq. 2 on B_i, Algorithm 6 inner call) -------------------
+template <typename T, typename YT>
+struct DiagArgs {
+  const T* B;
+  int mt, ldb;
+  const T* Delta;   // m x C sample-major, or null (no earlier tiles)
+  int64_t ldd;
+  const double* a;  // the tile's limits, factor order
+  const double* b;
+  const double* rs;  // per-sample Student-t scale or null
+  const uint64_t* Q;
+  const uint64_t* D;
+  int64_t ldD, coord0, sample0, N, C;
+  int periodize, first;
+  YT* Y;
+  int64_t ldy;
+  double* logP;  // all samples
+};
+
+__device__ __forceinline__ double to_t(double x, double) { return x; }
+__device__ __forceinline__ float to_t(double x, float) { return (float)x; }
+template <typename YT>
+__device__ __forceinline__ YT store_y(float y);
+template <>
+__device__ __forceinline__ float store_y<float>(float y) { return y; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 store_y<__nv_bfloat16>(float y) { return __float2bfloat16_rn(y); }
+
+// One thread per sample; the tile's y values of the thread's sample live in shared
+// memory (column tid of a [mt][blockDim] array); B_i rows are read through L1
+// as warp-uniform broadcasts.
+template <typename T, typename YT>
+__global__ void k_diag(DiagArgs<T, YT> p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* ys = reinterpret_cast<T*>(smem_raw);
+  const int bd = blockDim.x, tid = threadIdx.x;
+  const int64_t c = (int64_t)blockIdx.x * bd + tid;
+  if (c >= p.C) return;
+  const int64_t g = p.sample0 + c;
+  const int64_t s = g / p.N;
+  const uint64_t k = (uint64_t)(g - s * p.N) + 1;
+  const uint64_t* Ds = p.D + s * p.ldD + p.coord0;
+  const uint64_t* Qt = p.Q + p.coord0;
+  const T rs = p.rs ? (T)p.rs[c] : (T)1;
+  T lp = 0;
+  for (int v = 0; v < p.mt; v++) {
+    const T* Brow = p.B + (int64_t)v * p.ldb;
+    T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+    int u = 0;
+    for (; u + 4 <= v; u += 4) {
+      s0 = fma(__ldg(Brow + u), ys[(u)*bd + tid], s0);
+      s1 = fma(__ldg(Brow + u + 1), ys[(u + 1) * bd + tid], s1);
+      s2 = fma(__ldg(Brow + u + 2), ys[(u + 2) * bd + tid], s2);
+      s3 = fma(__ldg(Brow + u + 3), ys[(u + 3) * bd + tid], s3);
+    }
+    for (; u < v; u++) s0 = fma(__ldg(Brow + u), ys[u * bd + tid], s0);
+    const T sum = (s0 + s1) + (s2 + s3);
+    const T dl = p.Delta ? p.Delta[(int64_t)v * p.ldd + c] : (T)0;
+    const T lvv = __ldg(Brow + v);
+    const T at = ((T)p.a[v] * rs - dl - sum) / lvv;
+    const T bt = ((T)p.b[v] * rs - dl - sum) / lvv;
+    double w, wc;
+    lattice_w(k * Qt[v] + Ds[v], p.periodize, w, wc);
+    T ld, y;
+    sov_step<T>(at, bt, (T)w, (T)wc, ld, y);
+    lp += ld;
+    ys[v * bd + tid] = y;
+    p.Y[(int64_t)v * p.ldy + c] = (YT)y;
+  }
+  if (p.first) p.logP[g] = (double)lp;
+  else p.logP[g] += (double)lp;
+}
+
+// ---- reductions (Section 2.1 estimator, in logs) -----------------------------------
+template <typename T, typename Op>
+__device__ T block_reduce(T v, Op op, T* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int o = 16; o; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  v = threadIdx.x < nw ? sh[threadIdx.x] : sh[0];
+  if (wid == 0)
+    for (int o = 16; o; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if (threadIdx.x == 0) sh[0] = v;
+  __syncthreads();
+  v = sh[0];
+  __syncthreads();
+  return v;
+}
+struct MaxOp {
+  __device__ double operator()(double a, double b) const { return a > b ? a : b; }
+};
+struct SumOp {
+  __device__ double operator()(double a, double b) const { return a + b; }
+};
+
+// ell_s = log((1/N) sum_k exp(logP_{s,k})) for shift s = blockIdx.x.
+__global__ void k_shift_reduce(const double* logP, int64_t N, double* ell) {
+  __shared__ double sh[32];
+  const double* L = logP + (int64_t)blockIdx.x * N;
+  double mx = -INFINITY;
+  for (int64_t i = threadIdx.x; i < N; i += blockDim.x) mx = fmax(mx, L[i]);
+  mx = block_reduce(mx, MaxOp(), sh);
+  double sum = 0.0;
+  if (mx > -INFINITY)
+    for (int64_t i = threadIdx.x; i < N; i += blockDim.x) sum += exp(L[i] - mx);
+  sum = block_reduce(sum, SumOp(), sh);
+  if (threadIdx.x == 0) ell[blockIdx.x] = (mx > -INFINITY) ? mx + log(sum) - log((double)N) : -INFINITY;
+}
+
+// log p_hat = log((1/M) sum_s exp(ell_s)); err = SD_s(exp ell_s)/(sqrt(M) p_hat).
+__global__ void k_final(const double* ell, int M, double* out) {
+  __shared__ double sh[32];
+  double mx = -INFINITY;
+  for (int s = threadIdx.x; s < M; s += blockDim.x) mx = fmax(mx, ell[s]);
+  mx = block_reduce(mx, MaxOp(), sh);
+  double sum = 0.0;
+  if (mx > -INFINITY)
+    for (int s = threadIdx.x; s < M; s += blockDim.x) sum += exp(ell[s] - mx);
+  sum = block_reduce(sum, SumOp(), sh);
+  double mean = sum / M;
+  double sq = 0.0;
+  if (mx > -INFINITY)
+    for (int s = threadIdx.x; s < M; s += blockDim.x) {
+      double d = exp(ell[s] - mx) - mean;
+      sq += d * d;
+    }
+  sq = block_reduce(sq, SumOp(), sh);
+  if (threadIdx.x == 0) {
+    out[0] = (mx > -INFINITY) ? mx + log(sum) - log((double)M) : -INFINITY;
+    out[1] = (M > 1 && mx > -INFINITY) ? sqrt(sq / (M - 1) / M) / mean : NAN;
+  }
+}
+
+template <typename S, typename D>
+__global__ void k_convert(const S* src, D* dst, int64_t count) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) dst[i] = (D)src[i];
+}
+__global__ void k_convert_bf16(const double* src, __nv_bfloat16* dst, int64_t count) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) dst[i] = __double2bfloat16(src[i]);
+}
+
+static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+static int ensure_copies(Factor& F, int precision, cudaStream_t st) {
+  const int64_t nb = (int64_t)F.r * F.m * F.m, nu = (int64_t)F.m * F.ktot;
+  if (precision != TLRMVN_FP64 && !F.B32) {
+    TLR_CHECK(dalloc(&F.B32, nb));
+    k_convert<double, float><<<blocks_for(nb, 256), 256, 0, st>>>(F.B, F.B32, nb);
+  }
+  if (precision == TLRMVN_FP32 && !F.U32 && nu) {
+    TLR_CHECK(dalloc(&F.U32, nu));
+    TLR_CHECK(dalloc(&F.V32, nu));
+    k_convert<double, float><<<blocks_for(nu, 256), 256, 0, st>>>(F.Ucat, F.U32, nu);
+    k_convert<double, float><<<blocks_for(nu, 256), 256, 0, st>>>(F.Vcat, F.V32, nu);
+  }
+  if (precision == TLRMVN_BF16_SHIFT && !F.U16 && nu) {
+    TLR_CHECK(dalloc(&F.U16, nu));
+    TLR_CHECK(dalloc(&F.V16, nu));
+    k_convert_bf16<<<blocks_for(nu, 256), 256, 0, st>>>(F.Ucat, F.U16, nu);
+    k_convert_bf16<<<blocks_for(nu, 256), 256, 0, st>>>(F.Vcat, F.V16, nu);
+  }
+  TLR_CUDA(cudaGetLastError());
+  return TLRMVN_OK;
+}
+
+// splitmix64 (S. Vigna): output number t of the generator started at `seed`.
+static uint64_t splitmix64_at(uint64_t seed, uint64_t t) {
+  uint64_t z = seed + (t + 1) * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+// Scratch of one call, freed on every exit path.
+struct Scratch {
+  std::vector<void*> ptrs;
+  cudaStream_t st;
+  explicit Scratch(cudaStream_t s) : st(s) {}
+  template <typename T>
+  int get(T** p, size_t count) {
+    *p = nullptr;
+    if (!count) return TLRMVN_OK;
+    cudaError_t e = cudaMallocAsync((void**)p, count * sizeof(T), st);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(TLRMVN_E_NOMEM, "scratch allocation of " + std::to_string(count * sizeof(T)) + " bytes failed");
+    }
+    ptrs.push_back(*p);
+    return TLRMVN_OK;
+  }
+  ~Scratch() {
+    for (void* p : ptrs) cudaFreeAsync(p, st);
+    cudaStreamSynchronize(st);
+  }
+};
+
+template <typename T, typename YT>
+static int run_chunks(Factor& F, const T* Bt, const T* Ut, const T* Vt, const double* ap, const double* bp,
+                      double nu, const tlrmvn_opts& o, const uint64_t* dD, double* logP, Scratch& sc,
+                      cudaStream_t st) {
+  const int64_t M = o.n_shifts, N = o.n_points, S = M * N;
+  const int m = F.m;
+  int64_t C = o.sample_chunk > 0 ? o.sample_chunk : 0;
+  if (C <= 0) {
+    // keep W (ktot x C) within ~8 GiB
+    const double budget = 8.0 * (1ull << 30);
+    double per = (double)(F.ktot + 2 * m) * sizeof(T) + 16.0;
+    C = (int64_t)std::max(256.0, std::min((double)S, budget / per));
+  }
+  C = std::min<int64_t>(C, S);
+  C = (C + 255) / 256 * 256;
+  T *W = nullptr, *Dl = nullptr;
+  YT* Y = nullptr;
+  double* rs = nullptr;
+  TLR_CHECK(sc.get(&W, (size_t)F.ktot * C));
+  TLR_CHECK(sc.get(&Dl, (size_t)m * C));
+  TLR_CHECK(sc.get(&Y, (size_t)m * C));
+  const bool mvt = std::isfinite(nu);
+  if (mvt) TLR_CHECK(sc.get(&rs, (size_t)C));
+
+  int bd = 256;
+  while (bd > 32 && (size_t)m * bd * sizeof(T) > 65536) bd >>= 1;
+  size_t smem = (size_t)m * bd * sizeof(T);
+  TLR_CUDA(cudaFuncSetAttribute(k_diag<T, YT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+
+  for (int64_t c0 = 0; c0 < S; c0 += C) {
+    const int64_t Cc = std::min(C, S - c0);
+    if (mvt)
+      k_chi_scale<<<blocks_for(Cc, 128), 128, 0, st>>>(rs, F.Q, dD, F.n + 1, F.n, c0, N, Cc, nu, o.periodize);
+    for (int i = 0; i < F.r; i++) {
+      const int mt = (int)F.tsize(i);
+      const int64_t Kr = F.krow(i), Kc = F.kcol(i);
+      const T* Delta = nullptr;
+      if (Kr > 0) {
+        gemm_nn<T>(st, mt, Cc, Kr, Ut + (size_t)m * F.krow_off[i], Kr, W + (size_t)F.krow_off[i] * C, C, Dl, C,
+                   nullptr);
+        Delta = Dl;
+      }
+      DiagArgs<T, YT> a;
+      a.B = Bt + (size_t)i * m * m;
+      a.mt = mt;
+      a.ldb = m;
+      a.Delta = Delta;
+      a.ldd = C;
+      a.a = ap + F.tile_off[i];
+      a.b = bp + F.tile_off[i];
+      a.rs = rs;
+      a.Q = F.Q;
+      a.D = dD;
+      a.ldD = F.n + 1;
+      a.coord0 = F.tile_off[i];
+      a.sample0 = c0;
+      a.N = N;
+      a.C = Cc;
+      a.periodize = o.periodize;
+      a.first = (i == 0);
+      a.Y = Y;
+      a.ldy = C;
+      a.logP = logP;
+      k_diag<T, YT><<<blocks_for(Cc, bd), bd, smem, st>>>(a);
+      if (Kc > 0)
+        gemm_nn<T>(st, (int)Kc, Cc, mt, Vt + (size_t)m * F.kcol_off[i], m, Y, C, W, C, F.vmap + F.kcol_off[i]);
+    }
+    TLR_CUDA(cudaGetLastError());
+  }
+  return TLRMVN_OK;
+}
+
+static int prob_impl(Factor& F, const double* a_dev, const double* b_dev, double nu, const tlrmvn_opts& o,
+                     double* out2_dev, double* ell_dev_out, double* per_sample_dev, cudaStream_t st) {
+  const int64_t M = o.n_shifts, N = o.n_points, S = M * N, n = F.n;
+  Scratch sc(st);
+  double *ap = nullptr, *bp = nullptr, *logP = nullptr, *ell = nullptr;
+  uint64_t* dD = nullptr;
+  int* bad = nullptr;
+  TLR_CHECK(sc.get(&ap, n));
+  TLR_CHECK(sc.get(&bp, n));
+  TLR_CHECK(sc.get(&bad, 1));
+  TLR_CHECK(sc.get(&dD, (size_t)M * (n + 1)));
+  TLR_CHECK(sc.get(&ell, M));
+  if (per_sample_dev) logP = per_sample_dev;
+  else TLR_CHECK(sc.get(&logP, S));
+  // lattice shifts
+  {
+    std::vector<uint64_t> hD;
+    const uint64_t* src = o.shifts;
+    if (!src) {
+      hD.resize((size_t)M * (n + 1));
+      for (size_t t = 0; t < hD.size(); t++) hD[t] = splitmix64_at(o.seed, t);
+      src = hD.data();
+    }
+    TLR_CUDA(cudaMemcpyAsync(dD, src, (size_t)M * (n + 1) * 8, cudaMemcpyHostToDevice, st));
+    if (!hD.empty()) TLR_CUDA(cudaStreamSynchronize(st));
+  }
+  TLR_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
+  k_permute_limits<<<blocks_for(n, 256), 256, 0, st>>>(a_dev, b_dev, F.dperm, n, ap, bp, bad);
+  int hbad = 0;
+  TLR_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TLR_CUDA(cudaStreamSynchronize(st));
+  if (hbad) return fail(TLRMVN_E_INVAL, "limits must satisfy a_i <= b_i, a_i < +inf, b_i > -inf, no NaN");
+  TLR_CHECK(ensure_copies(F, o.precision, st));
+  int s;
+  if (o.precision == TLRMVN_FP64)
+    s = run_chunks<double, double>(F, F.B, F.Ucat, F.Vcat, ap, bp, nu, o, dD, logP, sc, st);
+  else if (o.precision == TLRMVN_FP32)
+    s = run_chunks<float, float>(F, F.B32, F.U32, F.V32, ap, bp, nu, o, dD, logP, sc, st);
+  else
+    return fail(TLRMVN_E_NOTSUP, "precision not available");
+  TLR_CHECK(s);
+  k_shift_reduce<<<(unsigned)M, 256, 0, st>>>(logP, N, ell);
+  k_final<<<1, 256, 0, st>>>(ell, (int)M, out2_dev);
+  if (ell_dev_out) TLR_CUDA(cudaMemcpyAsync(ell_dev_out, ell, M * 8, cudaMemcpyDeviceToDevice, st));
+  TLR_CUDA(cudaGetLastError());
+  TLR_CUDA(cudaStreamSynchronize(st));
+  return TLRMVN_OK;
+}
+
+static int check_opts(const Factor& F, double nu, const tlrmvn_opts* o) {
+  if (!o) return fail(TLRMVN_E_INVAL, "null options");
+  if (o->n_shifts < 1 || o->n_points < 1) return fail(TLRMVN_E_INVAL, "n_shifts and n_points must be >= 1");
+  if (o->precision < TLRMVN_FP64 || o->precision > TLRMVN_BF16_SHIFT) return fail(TLRMVN_E_INVAL, "bad precision");
+  if (!(nu > 0.0)) return fail(TLRMVN_E_INVAL, "nu must be > 0 (INFINITY for the normal case)");
+  (void)F;
+  return TLRMVN_OK;
+}
+
+}  // namespace tlrmvn
+
+using namespace tlrmvn;
+
+extern "C" int tlrmvn_prob_device(tlrmvn_factor_t f, const double* a, const double* b, double nu,
+                                  const tlrmvn_opts* opts, double* logp, double* err, double* per_shift,
+                                  double* per_sample) {
+  if (!f || !a || !b || !logp || !err) return fail(TLRMVN_E_INVAL, "null argument");
+  Factor& F = *reinterpret_cast<Factor*>(f);
+  TLR_CHECK(check_opts(F, nu, opts));
+  int cur = 0;
+  cudaGetDevice(&cur);
+  TLR_CUDA(cudaSetDevice(F.device));
+  cudaStream_t st = pick_stream(opts->stream);
+  double* out2 = nullptr;
+  int s = dalloc(&out2, 2);
+  if (s == TLRMVN_OK) s = prob_impl(F, a, b, nu, *opts, out2, per_shift, per_sample, st);
+  if (s == TLRMVN_OK) {
+    cudaError_t e1 = cudaMemcpyAsync(logp, out2, 8, cudaMemcpyDeviceToDevice, st);
+    cudaError_t e2 = cudaMemcpyAsync(err, out2 + 1, 8, cudaMemcpyDeviceToDevice, st);
+    cudaError_t e3 = cudaStreamSynchronize(st);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) s = cuda_fail(e1 ? e1 : (e2 ? e2 : e3), "copy out");
+  }
+  dfree(out2);
+  cudaSetDevice(cur);
+  return s;
+}
+
+extern "C" int tlrmvn_prob(tlrmvn_factor_t f, const double* a, const double* b, double nu, const tlrmvn_opts* opts,
+                           double* logp, double* err, double* per_shift, double* per_sample) {
+  if (!f || !a || !b || !logp || !err) return fail(TLRMVN_E_INVAL, "null argument");
+  Factor& F = *reinterpret_cast<Factor*>(f);
+  TLR_CHECK(check_opts(F, nu, opts));
+  int cur = 0;
+  cudaGetDevice(&cur);
+  TLR_CUDA(cudaSetDevice(F.device));
+  cudaStream_t st = pick_stream(opts->stream);
+  const int64_t n = F.n, M = opts->n_shifts, S = M * (int64_t)opts->n_points;
+  double *da = nullptr, *db = nullptr, *out2 = nullptr, *dell = nullptr, *dps = nullptr;
+  int s = dalloc(&da, n);
+  if (s == TLRMVN_OK) s = dalloc(&db, n);
+  if (s == TLRMVN_OK) s = dalloc(&out2, 2);
+  if (s == TLRMVN_OK && per_shift) s = dalloc(&dell, M);
+  if (s == TLRMVN_OK && per_sample) s = dalloc(&dps, S);
+  if (s == TLRMVN_OK) {
+    cudaError_t e = cudaMemcpyAsync(da, a, n * 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(db, b, n * 8, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) s = cuda_fail(e, "copy limits");
+  }
+  if (s == TLRMVN_OK) s = prob_impl(F, da, db, nu, *opts, out2, dell, dps, st);
+  if (s == TLRMVN_OK) {
+    double h[2];
+    cudaError_t e = cudaMemcpyAsync(h, out2, 16, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && per_shift) e = cudaMemcpyAsync(per_shift, dell, M * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && per_sample) e = cudaMemcpyAsync(per_sample, dps, S * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) s = cuda_fail(e, "copy results");
+    else {
+      *logp = h[0];
+      *err = h[1];
+    }
+  }
+  dfree(da);
+  dfree(db);
+  dfree(out2);
+  dfree(dell);
+  dfree(dps);
+  cudaSetDevice(cur);
+  return s;
+}

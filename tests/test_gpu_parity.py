@@ -1,0 +1,175 @@
+"""GPU parity: the CUDA integrand against the oracle, element by element.
+
+Both sides get the same factor (exported by the library or built by the oracle
+and imported), the same lattice and the same shifts.  Tolerances (relative, on
+per-shift log-probabilities): FP64 1e-9, FP32 1e-4.  Per-sample log integrands
+are compared too: FP64 to 1e-9 relative, FP32 to 1e-4 relative plus 1e-3
+absolute (float32 accumulation over a few hundred variables).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import sov
+from tests.helpers import to_oracle_factor, oracle_factor, export_bytes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tl():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2003_11183_gb300 as tl
+    return tl
+
+
+def rel(a, b):
+    return np.abs(np.asarray(a) - np.asarray(b)) / np.maximum(np.abs(np.asarray(b)), 1e-300)
+
+
+def run_both(tl, F_lib, OF, w, precision, nu=None, samples=None):
+    nu = w.nu if nu is None else nu
+    lp, err, ps, pm = tl.tlrmvn_prob(F_lib, w.a, w.b, nu, precision, w.n_shifts, w.n_points, shifts=w.shifts,
+                                     per_shift=True, per_sample=True)
+    if samples is None:
+        ref = sov.solve(OF, w.a, w.b, nu, w.shifts, w.n_points)
+    else:
+        ref = sov.solve(OF, w.a, w.b, nu, w.shifts, w.n_points, samples=samples)
+    return (lp, err, ps, pm), ref
+
+
+@pytest.mark.parametrize("nu", [math.inf, 7.0])
+@pytest.mark.parametrize("ragged", [None, 300])
+def test_fp64_per_sample_on_imported_oracle_factor(tl, nu, ragged):
+    w = synth.small_workload(16, 64, 31, nu=nu, n_shifts=3, n_points=200, ragged_n=ragged)
+    OF, _ = oracle_factor(w)
+    F = tl.tlrmvn_factor_import(export_bytes(OF))
+    (lp, err, ps, pm), ref = run_both(tl, F, OF, w, tl.FP64)
+    assert np.all(rel(pm, ref["per_sample"]) < 1e-9)
+    assert np.all(rel(ps, ref["per_shift"]) < 1e-9)
+    assert abs(lp - ref["logp"]) < 1e-9 * abs(ref["logp"])
+    assert abs(err - ref["err"]) < 1e-6 * ref["err"]
+
+
+@pytest.mark.parametrize("nu", [math.inf, 3.0])
+def test_fp32_on_imported_oracle_factor(tl, nu):
+    w = synth.small_workload(16, 64, 32, nu=nu, n_shifts=4, n_points=300)
+    OF, _ = oracle_factor(w)
+    F = tl.tlrmvn_factor_import(export_bytes(OF))
+    (lp, err, ps, pm), ref = run_both(tl, F, OF, w, tl.FP32)
+    assert np.all(rel(ps, ref["per_shift"]) < 1e-4)
+    assert np.all(np.abs(pm - ref["per_sample"]) <= 1e-4 * np.abs(ref["per_sample"]) + 1e-3)
+
+
+def test_two_sided_and_upper_tail_limits(tl):
+    w = synth.small_workload(12, 48, 33, n_shifts=3, n_points=128, limits="twosided")
+    w.a[::7] = 1.5
+    w.b[::7] = np.inf       # upper-tail one-sided intervals
+    OF, _ = oracle_factor(w)
+    F = tl.tlrmvn_factor_import(export_bytes(OF))
+    (lp, err, ps, pm), ref = run_both(tl, F, OF, w, tl.FP64)
+    assert np.all(rel(pm, ref["per_sample"]) < 1e-9)
+    (lp, err, ps, pm), ref = run_both(tl, F, OF, w, tl.FP32)
+    assert np.all(rel(ps, ref["per_shift"]) < 1e-4)
+
+
+def test_gpu_factor_matches_oracle_factor(tl):
+    for reorder in (0, 1, 2):
+        w = synth.small_workload(16, 32, 34, n_shifts=2, n_points=64, reorder=reorder)
+        OF, Sig = oracle_factor(w)
+        F = tl.tlrmvn_factor_kernel(w.xy, w.kernel, w.params, w.nugget, w.a, w.b, w.m, w.tol, 0, reorder)
+        ex = tl.parse_export(tl.tlrmvn_factor_export(F))
+        assert np.array_equal(ex.perm, OF.perm), reorder        # ordering is integer work: exact
+        assert np.array_equal(ex.tile_off, OF.tile_off)
+        GF = to_oracle_factor(ex)
+        assert np.abs(GF.dense() - OF.dense()).max() < 1e-7
+        P = ex.perm
+        L = GF.dense()
+        assert np.abs(L @ L.T - Sig[np.ix_(P, P)]).max() < 50 * w.tol
+
+
+def test_gpu_factor_parity_fp64_and_fp32(tl):
+    w = synth.small_workload(20, 50, 35, nu=7.0, n_shifts=4, n_points=256, ragged_n=390)
+    F = tl.tlrmvn_factor_kernel(w.xy, w.kernel, w.params, w.nugget, w.a, w.b, w.m, w.tol, 0, 2)
+    OF = to_oracle_factor(tl.parse_export(tl.tlrmvn_factor_export(F)))
+    (lp, err, ps, pm), ref = run_both(tl, F, OF, w, tl.FP64)
+    assert np.all(rel(pm, ref["per_sample"]) < 1e-9)
+    (lp, err, ps, pm), ref = run_both(tl, F, OF, w, tl.FP32)
+    assert np.all(rel(ps, ref["per_shift"]) < 1e-4)
+
+
+def test_dense_covariance_entry_point(tl):
+    from oracle import geometry
+    w = synth.small_workload(10, 25, 36, n_shifts=2, n_points=64)
+    Sig = geometry.covariance(w.xy, w.kernel, w.params, w.nugget)
+    F = tl.tlrmvn_factor_dense(Sig, w.a, w.b, 25, 1e-10, 0, 2)
+    ex = tl.parse_export(tl.tlrmvn_factor_export(F))
+    L = to_oracle_factor(ex).dense()
+    P = ex.perm
+    assert np.abs(L @ L.T - Sig[np.ix_(P, P)]).max() < 1e-8
+    OF = to_oracle_factor(ex)
+    (lp, err, ps, pm), ref = run_both(tl, F, OF, w, tl.FP64)
+    assert np.all(rel(pm, ref["per_sample"]) < 1e-9)
+
+
+def test_closed_forms_on_gpu(tl):
+    # n = 1: every sample equals Phi(b) - Phi(a); all-infinite limits give 0
+    from scipy import stats
+    F = tl.tlrmvn_factor_dense(np.array([[2.25]]), None, None, 1, 0.0, 0, 0)
+    for prec in (tl.FP64, tl.FP32):
+        lp, err, ps, pm = tl.tlrmvn_prob(F, [-0.4], [1.1], math.inf, prec, 2, 50, seed=3, per_sample=True)
+        want = math.log(stats.norm.cdf(1.1 / 1.5) - stats.norm.cdf(-0.4 / 1.5))
+        assert np.allclose(pm, want, rtol=1e-12 if prec == tl.FP64 else 1e-6)
+    w = synth.small_workload(8, 16, 37, n_shifts=2, n_points=32)
+    F = tl.tlrmvn_factor_kernel(w.xy, w.kernel, w.params, w.nugget, None, None, 16, 1e-8, 0, 0)
+    lp, err, ps, pm = tl.tlrmvn_prob(F, np.full(64, -np.inf), np.full(64, np.inf), math.inf, tl.FP64, 2, 32,
+                                     per_sample=True)
+    assert np.all(pm == 0.0) and lp == 0.0
+    # bivariate orthant
+    rho = 0.6
+    F = tl.tlrmvn_factor_dense(np.array([[1.0, rho], [rho, 1.0]]), None, None, 2, 0.0, 0, 0)
+    lp, err, _, _ = tl.tlrmvn_prob(F, [-np.inf] * 2, [0.0, 0.0], math.inf, tl.FP64, 10, 4000, seed=5)
+    want = 0.25 + math.asin(rho) / (2 * math.pi)
+    assert abs(math.exp(lp) - want) <= 4 * err * want + 1e-7
+
+
+def test_error_paths(tl):
+    F = tl.tlrmvn_factor_dense(np.eye(4), None, None, 2, 0.0, 0, 0)
+    with pytest.raises(tl.TlrmvnError) as e:
+        tl.tlrmvn_prob(F, [0.0] * 4, [-1.0] * 4, math.inf, tl.FP64, 2, 10)
+    assert e.value.status == tl.E_INVAL
+    bad = np.array([[1.0, 2.0], [2.0, 1.0]])
+    with pytest.raises(tl.TlrmvnError) as e:
+        tl.tlrmvn_factor_dense(bad, None, None, 2, 0.0, 0, 0)
+    assert e.value.status == tl.E_NOT_SPD
+    lp, err, _, _ = tl.tlrmvn_prob(F, [-np.inf] * 4, [0.0] * 4, math.inf, tl.FP64, 1, 10)
+    assert math.isnan(err)
+
+
+def test_export_import_round_trip(tl):
+    w = synth.small_workload(12, 40, 38, n_shifts=2, n_points=64)
+    F = tl.tlrmvn_factor_kernel(w.xy, w.kernel, w.params, w.nugget, w.a, w.b, w.m, w.tol, 0, 2)
+    buf = tl.tlrmvn_factor_export(F)
+    F2 = tl.tlrmvn_factor_import(buf)
+    assert tl.tlrmvn_factor_export(F2) == buf
+    r1 = tl.tlrmvn_prob(F, w.a, w.b, math.inf, tl.FP64, 2, 64, shifts=w.shifts)
+    r2 = tl.tlrmvn_prob(F2, w.a, w.b, math.inf, tl.FP64, 2, 64, shifts=w.shifts)
+    assert r1[0] == r2[0]
+
+
+def test_config1_full_size_fp64(tl):
+    # n = 256, m = 64, tol 1e-8, iterative block reordering, 20 x 500, FP64
+    w = synth.workload(1)
+    F = tl.tlrmvn_factor_kernel(w.xy, w.kernel, w.params, w.nugget, w.a, w.b, w.m, w.tol, w.max_rank, w.reorder)
+    OF = to_oracle_factor(tl.parse_export(tl.tlrmvn_factor_export(F)))
+    (lp, err, ps, pm), ref = run_both(tl, F, OF, w, tl.FP64)
+    assert np.all(rel(ps, ref["per_shift"]) < 1e-9)
+    assert np.all(rel(pm, ref["per_sample"]) < 1e-9)
+    own, _ = oracle_factor(w)
+    assert np.array_equal(own.perm, OF.perm)

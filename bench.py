@@ -1,0 +1,343 @@
+#!/usr/bin/env python
+"""Throughput of the TLR quasi-Monte Carlo integrand, in QMC sample-dimensions per second.
+
+Workload (one "step" = one full solve): Student-t nu = 7 probability in
+n = 65,536 dimensions; exponential covariance (beta = 0.1) on a 256 x 256
+jittered grid of the unit square; a = -inf, b_i ~ N(1, 0.5^2); tile m = 512,
+ACA tolerance 1e-4, ranks <= 64; 20 random shifts x 5,000 Richtmyer points.
+The factor is built once on the GPU (float64) before timing; the timed step
+is tlrmvn_prob_device with the limits already resident in HBM.
+
+Output: one JSON line (rank 0).  `--impl reference` times the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+# Peak FP32 rate of the diagonal sweep's roofline: 152 SMs x 128 FP32 lanes x
+# 2 flops per FMA x 2.07 GHz maximum SM clock.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default=os.environ.get("TLRMVN_BENCH_PRECISION", "fp32"), choices=list(PRECISIONS))
+    ap.add_argument("--workload", type=int, default=3)
+    ap.add_argument("--points", type=int, default=0, help="override points per shift (0 = workload's)")
+    ap.add_argument("--no-baselines", action="store_true", help="skip FP64-path and CPU-oracle legs")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(ws, x: float) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_sample(buf_path: str, wl: int, n_points: int, shift_index: int) -> dict:
+    """Times the oracle's TLR integrand on one shift x n_points of the workload, single-threaded BLAS."""
+    code = f"""
+import os, sys, time, math, json
+sys.path.insert(0, {ROOT!r})
+import numpy as np
+import synth
+from oracle import sov
+from tests.helpers import to_oracle_factor
+from paper_2003_11183_gb300.api import parse_export
+w = synth.workload({wl})
+F = to_oracle_factor(parse_export(open({buf_path!r}, 'rb').read()))
+sh = w.shifts[{shift_index}:{shift_index} + 1]
+t0 = time.perf_counter()
+r = sov.solve(F, w.a, w.b, w.nu, sh, {n_points}, chunk={n_points})
+t = time.perf_counter() - t0
+print(json.dumps({{"seconds": t, "logp": r["logp"], "per_sample": r["per_sample"].tolist()}}))
+"""
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def build_factor(tl, w):
+    t0 = time.perf_counter()
+    F = tl.tlrmvn_factor_kernel(w.xy, w.kernel, w.params, w.nugget, w.a, w.b, w.m, w.tol, w.max_rank, w.reorder)
+    return F, time.perf_counter() - t0
+
+
+def run_reference(args):
+    ws, rank, local = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    if rank != 0:
+        return 0
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2003_11183_gb300 as tl
+    import synth
+    w = synth.workload(args.workload)
+    torch.cuda.set_device(0)
+    F, fs = build_factor(tl, w)
+    path = os.path.join(tempfile.gettempdir(), f"tlrmvn_factor_{os.getpid()}.bin")
+    with open(path, "wb") as fh:
+        fh.write(tl.tlrmvn_factor_export(F))
+    pts = 32
+    times = []
+    for s in range(args.warmup + args.steps):
+        res = cpu_oracle_sample(path, args.workload, pts, s % w.n_shifts)
+        if s >= args.warmup:
+            times.append(res["seconds"])
+    os.unlink(path)
+    per = statistics.mean(times)
+    value = w.n * pts / per
+    sample = f"1 shift x {pts} lattice points of the same workload per step, same factor"
+    line = {"impl": "reference", "metric": "QMC sample-dims/sec", "value": value, "unit": "sample-dims/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "n": w.n, "tile": w.m, "tol": w.tol, "nu": w.nu},
+            "cpu_baseline": {"value": value, "unit": "sample-dims/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "sample-dims/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "notes": "factor built once by the library's GPU factorisation (setup, untimed); timed step is the "
+                     "oracle's TLR integrand alone"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2003_11183_gb300 as tl
+    import synth
+    w = synth.workload(args.workload)
+    if args.points:
+        w.n_points = args.points
+    if ws > 1:
+        # disjoint shift batches per rank: same problem, independent replicas
+        w.shifts = synth.lattice_shifts(w.n_shifts, w.n + 1, 3000 + args.workload + 7919 * rank)
+    prec = PRECISIONS[args.precision]
+    F, factor_s = build_factor(tl, w)
+    info = tl.tlrmvn_factor_info(F)
+    stream = torch.cuda.current_stream()
+    a = torch.tensor(w.a, dtype=torch.float64, device="cuda")
+    b = torch.tensor(w.b, dtype=torch.float64, device="cuda")
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    kw = dict(nu=w.nu, precision=prec, n_shifts=w.n_shifts, n_points=w.n_points, shifts=w.shifts, stream=stream)
+
+    for _ in range(args.warmup):
+        tl.tlrmvn_prob_device(F, a, b, out, **kw)
+    torch.cuda.synchronize()
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    tl.tlrmvn_profile_reset()
+    tl.tlrmvn_profile_enable(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        tl.tlrmvn_prob_device(F, a, b, out, **kw)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    tl.tlrmvn_profile_enable(False)
+    clk = clocks.stop()
+    barrier(ws)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = allmax(ws, ms)
+    logp, err = out.tolist()
+    kern = {tl.KC_NAMES[c]: tl.tlrmvn_profile_get(c) for c in range(5)}
+    launches = sum(v[1] for v in kern.values())
+    sd = w.n * w.n_shifts * w.n_points
+    value = ws * sd / (ms / 1e3)
+
+    # end to end through the public host-array entry point
+    h2d = 2 * w.n * 8 + w.shifts.nbytes
+    t_e2e = []
+    for _ in range(max(2, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tl.tlrmvn_prob(F, w.a, w.b, **kw)
+        t_e2e.append(time.perf_counter() - t0)
+    e2e = ws * sd / statistics.mean(t_e2e)
+
+    # roofline of the dominant kernel class
+    pk, pk_kind = peaks()
+    dom = max(("shift", "diag", "vproj"), key=lambda c: kern[c][0])
+    roof = None
+    m, n, C = w.m, w.n, w.n_shifts * w.n_points
+    if dom == "diag":
+        r = info["r"]
+        sizes = [min(m, n - t * m) for t in range(r)]
+        flops = sum(s * (s - 1) for s in sizes) * C * args.steps  # one FMA per (v, u < v) per sample
+        t = kern["diag"][0] / 1e3
+        ach = flops / t / 1e12
+        roof = {"kernel": "k_diag", "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP32_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+    else:
+        K = info["k_total"]
+        flops = 2.0 * m * K * C * args.steps
+        t = kern[dom][0] / 1e3
+        ach = flops / t / 1e12
+        if prec == 2:
+            p = pk.get("bf16_tflops_sustained", 1700.0)
+            roof = {"kernel": dom, "bound": "tensor", "achieved": ach, "peak": p, "unit": "TFLOP/s", "frac": ach / p,
+                    "traffic": None, "peak_source": f"bf16 sustained, {pk_kind}"}
+        else:
+            roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": ach / FP32_PEAK_TFLOPS, "traffic": None,
+                    "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+
+    extra = {}
+    if rank == 0 and not args.no_baselines:
+        # the same library's FP64 path on a bounded sample (1 shift x 1000 points)
+        pts64 = min(1000, w.n_points)
+        kw64 = dict(kw, precision=0, n_shifts=1, n_points=pts64, shifts=w.shifts[:1])
+        tl.tlrmvn_prob_device(F, a, b, out, **kw64)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tl.tlrmvn_prob_device(F, a, b, out, **kw64)
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t0
+        v64 = w.n * pts64 / t64
+        extra["fp64_path"] = {"value": v64, "unit": "sample-dims/s", "sample": f"1 shift x {pts64} points",
+                              "speedup": (value / ws) / v64}
+        # the CPU oracle on a bounded sample of the same workload and factor
+        path = os.path.join(tempfile.gettempdir(), f"tlrmvn_factor_{os.getpid()}.bin")
+        with open(path, "wb") as fh:
+            fh.write(tl.tlrmvn_factor_export(F))
+        pts_cpu = 32
+        res = cpu_oracle_sample(path, args.workload, pts_cpu, 0)
+        os.unlink(path)
+        cpu = {"value": w.n * pts_cpu / res["seconds"], "unit": "sample-dims/s", "cores": 1, "kind": "oracle",
+               "sample": f"1 shift x {pts_cpu} points of the same workload and factor, single-threaded BLAS"}
+    else:
+        cpu = None
+
+    if rank == 0:
+        line = {"metric": "QMC sample-dims/sec (MVT nu=7, n=65,536)", "value": value, "unit": "sample-dims/s",
+                "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": {0: "f64", 1: "f32", 2: "f32+bf16"}[prec], "data": "synthetic",
+                "config": {"workload": w.name, "n": w.n, "tile": w.m, "tol": w.tol, "max_rank": w.max_rank,
+                           "nu": w.nu, "shifts": w.n_shifts, "points": w.n_points, "reorder": w.reorder,
+                           "precision": args.precision, "k_total": info["k_total"], "tiles": info["r"],
+                           "l2": "inputs larger than L2 (factor and W buffer)"},
+                "clocks": clk,
+                "e2e": {"value": e2e, "unit": "sample-dims/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 16},
+                "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
+                "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kern.items()},
+                "factor_seconds": factor_s, "logp": logp, "err": err}
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -153,6 +153,23 @@ int tlrmvn_prob_device(tlrmvn_factor_t f, const double* a, const double* b, doub
 const char* tlrmvn_strerror(int status);
 const char* tlrmvn_last_error(void);   /* thread-local detail of the last failure, "" if none */
 
+/* Kernel classes of the integrand, for tlrmvn_profile_get. */
+#define TLRMVN_KC_SHIFT   0  /* low-rank limit shifts  Delta_i = U_i W_i           */
+#define TLRMVN_KC_DIAG    1  /* diagonal-tile SOV sweep (eq. 2 on B_i)              */
+#define TLRMVN_KC_VPROJ   2  /* projections  W_col_i = V_i^T y_i                    */
+#define TLRMVN_KC_CHI     3  /* Student-t scale chi_nu^-1(w0)/sqrt(nu)              */
+#define TLRMVN_KC_REDUCE  4  /* per-shift and cross-shift log-sum reductions        */
+#define TLRMVN_KC_COUNT   5
+
+/* Process-wide kernel timing: when enabled, every integrand launch is bracketed
+ * by CUDA events on its stream and, once the call has completed, its device
+ * time is added to its class.  Enabling costs two event records per launch.
+ * tlrmvn_profile_get returns the accumulated milliseconds and launch count of
+ * one class; tlrmvn_profile_reset clears all classes. */
+int tlrmvn_profile_enable(int on);
+int tlrmvn_profile_reset(void);
+int tlrmvn_profile_get(int kernel_class, double* total_ms, int64_t* launches);
+
 #ifdef __cplusplus
 }
 #endif

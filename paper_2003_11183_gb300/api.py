@@ -123,6 +123,25 @@ def tlrmvn_factor_import(buf: bytes) -> Factor:
     return Factor(out.value)
 
 
+KC_SHIFT, KC_DIAG, KC_VPROJ, KC_CHI, KC_REDUCE = 0, 1, 2, 3, 4
+KC_NAMES = ("shift", "diag", "vproj", "chi", "reduce")
+
+
+def tlrmvn_profile_enable(on: bool):
+    L.load().tlrmvn_profile_enable(1 if on else 0)
+
+
+def tlrmvn_profile_reset():
+    L.load().tlrmvn_profile_reset()
+
+
+def tlrmvn_profile_get(kernel_class: int):
+    """(total device milliseconds, launches) accumulated for one kernel class."""
+    ms, n = C.c_double(), C.c_int64()
+    _check(L.load().tlrmvn_profile_get(int(kernel_class), C.byref(ms), C.byref(n)), "tlrmvn_profile_get")
+    return ms.value, n.value
+
+
 def tlrmvn_factor_free(f: Factor):
     f.close()
 

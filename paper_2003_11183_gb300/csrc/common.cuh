@@ -96,6 +96,18 @@ int factor_finish(Factor& F, cudaStream_t st);
 
 cudaStream_t pick_stream(void* s);
 
+// Kernel-class timing (tlrmvn_profile_*): Prof brackets launches with events.
+struct Prof {
+  bool on;
+  cudaStream_t st;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
+  explicit Prof(cudaStream_t s);
+  void begin(int cls);
+  void end();
+  int collect();  // after the stream is synchronised: add to the global accumulators
+  ~Prof();
+};
+
 // ---- device univariate functions ------------------------------------------------
 #define TLR_RSQRT2 0.70710678118654752440
 #define TLR_SQRT2PI 2.50662827463100050242

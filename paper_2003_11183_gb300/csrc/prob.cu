@@ -129,8 +129,6 @@ struct DiagArgs {
   double* logP;  // all samples
 };
 
-__device__ __forceinline__ double to_t(double x, double) { return x; }
-__device__ __forceinline__ float to_t(double x, float) { return (float)x; }
 template <typename YT>
 __device__ __forceinline__ YT store_y(float y);
 template <>
@@ -184,14 +182,15 @@ __global__ void k_diag(DiagArgs<T, YT> p) {
 }
 
 // ---- reductions (Section 2.1 estimator, in logs) -----------------------------------
+// Block-wide reduction; `ident` pads the lanes beyond the warp count.
 template <typename T, typename Op>
-__device__ T block_reduce(T v, Op op, T* sh) {
+__device__ T block_reduce(T v, Op op, T* sh, T ident) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int o = 16; o; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
   if (lane == 0) sh[wid] = v;
   __syncthreads();
   const int nw = (blockDim.x + 31) >> 5;
-  v = threadIdx.x < nw ? sh[threadIdx.x] : sh[0];
+  v = threadIdx.x < nw ? sh[threadIdx.x] : ident;
   if (wid == 0)
     for (int o = 16; o; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
   if (threadIdx.x == 0) sh[0] = v;
@@ -213,11 +212,11 @@ __global__ void k_shift_reduce(const double* logP, int64_t N, double* ell) {
   const double* L = logP + (int64_t)blockIdx.x * N;
   double mx = -INFINITY;
   for (int64_t i = threadIdx.x; i < N; i += blockDim.x) mx = fmax(mx, L[i]);
-  mx = block_reduce(mx, MaxOp(), sh);
+  mx = block_reduce(mx, MaxOp(), sh, (double)-INFINITY);
   double sum = 0.0;
   if (mx > -INFINITY)
     for (int64_t i = threadIdx.x; i < N; i += blockDim.x) sum += exp(L[i] - mx);
-  sum = block_reduce(sum, SumOp(), sh);
+  sum = block_reduce(sum, SumOp(), sh, 0.0);
   if (threadIdx.x == 0) ell[blockIdx.x] = (mx > -INFINITY) ? mx + log(sum) - log((double)N) : -INFINITY;
 }
 
@@ -226,11 +225,11 @@ __global__ void k_final(const double* ell, int M, double* out) {
   __shared__ double sh[32];
   double mx = -INFINITY;
   for (int s = threadIdx.x; s < M; s += blockDim.x) mx = fmax(mx, ell[s]);
-  mx = block_reduce(mx, MaxOp(), sh);
+  mx = block_reduce(mx, MaxOp(), sh, (double)-INFINITY);
   double sum = 0.0;
   if (mx > -INFINITY)
     for (int s = threadIdx.x; s < M; s += blockDim.x) sum += exp(ell[s] - mx);
-  sum = block_reduce(sum, SumOp(), sh);
+  sum = block_reduce(sum, SumOp(), sh, 0.0);
   double mean = sum / M;
   double sq = 0.0;
   if (mx > -INFINITY)
@@ -238,7 +237,7 @@ __global__ void k_final(const double* ell, int M, double* out) {
       double d = exp(ell[s] - mx) - mean;
       sq += d * d;
     }
-  sq = block_reduce(sq, SumOp(), sh);
+  sq = block_reduce(sq, SumOp(), sh, 0.0);
   if (threadIdx.x == 0) {
     out[0] = (mx > -INFINITY) ? mx + log(sum) - log((double)M) : -INFINITY;
     out[1] = (M > 1 && mx > -INFINITY) ? sqrt(sq / (M - 1) / M) / mean : NAN;
@@ -313,7 +312,7 @@ struct Scratch {
 template <typename T, typename YT>
 static int run_chunks(Factor& F, const T* Bt, const T* Ut, const T* Vt, const double* ap, const double* bp,
                       double nu, const tlrmvn_opts& o, const uint64_t* dD, double* logP, Scratch& sc,
-                      cudaStream_t st) {
+                      cudaStream_t st, Prof& pf) {
   const int64_t M = o.n_shifts, N = o.n_points, S = M * N;
   const int m = F.m;
   int64_t C = o.sample_chunk > 0 ? o.sample_chunk : 0;
@@ -341,15 +340,20 @@ static int run_chunks(Factor& F, const T* Bt, const T* Ut, const T* Vt, const do
 
   for (int64_t c0 = 0; c0 < S; c0 += C) {
     const int64_t Cc = std::min(C, S - c0);
-    if (mvt)
+    if (mvt) {
+      pf.begin(TLRMVN_KC_CHI);
       k_chi_scale<<<blocks_for(Cc, 128), 128, 0, st>>>(rs, F.Q, dD, F.n + 1, F.n, c0, N, Cc, nu, o.periodize);
+      pf.end();
+    }
     for (int i = 0; i < F.r; i++) {
       const int mt = (int)F.tsize(i);
       const int64_t Kr = F.krow(i), Kc = F.kcol(i);
       const T* Delta = nullptr;
       if (Kr > 0) {
+        pf.begin(TLRMVN_KC_SHIFT);
         gemm_nn<T>(st, mt, Cc, Kr, Ut + (size_t)m * F.krow_off[i], Kr, W + (size_t)F.krow_off[i] * C, C, Dl, C,
                    nullptr);
+        pf.end();
         Delta = Dl;
       }
       DiagArgs<T, YT> a;
@@ -373,9 +377,14 @@ static int run_chunks(Factor& F, const T* Bt, const T* Ut, const T* Vt, const do
       a.Y = Y;
       a.ldy = C;
       a.logP = logP;
+      pf.begin(TLRMVN_KC_DIAG);
       k_diag<T, YT><<<blocks_for(Cc, bd), bd, smem, st>>>(a);
-      if (Kc > 0)
+      pf.end();
+      if (Kc > 0) {
+        pf.begin(TLRMVN_KC_VPROJ);
         gemm_nn<T>(st, (int)Kc, Cc, mt, Vt + (size_t)m * F.kcol_off[i], m, Y, C, W, C, F.vmap + F.kcol_off[i]);
+        pf.end();
+      }
     }
     TLR_CUDA(cudaGetLastError());
   }
@@ -415,20 +424,23 @@ static int prob_impl(Factor& F, const double* a_dev, const double* b_dev, double
   TLR_CUDA(cudaStreamSynchronize(st));
   if (hbad) return fail(TLRMVN_E_INVAL, "limits must satisfy a_i <= b_i, a_i < +inf, b_i > -inf, no NaN");
   TLR_CHECK(ensure_copies(F, o.precision, st));
+  Prof pf(st);
   int s;
   if (o.precision == TLRMVN_FP64)
-    s = run_chunks<double, double>(F, F.B, F.Ucat, F.Vcat, ap, bp, nu, o, dD, logP, sc, st);
+    s = run_chunks<double, double>(F, F.B, F.Ucat, F.Vcat, ap, bp, nu, o, dD, logP, sc, st, pf);
   else if (o.precision == TLRMVN_FP32)
-    s = run_chunks<float, float>(F, F.B32, F.U32, F.V32, ap, bp, nu, o, dD, logP, sc, st);
+    s = run_chunks<float, float>(F, F.B32, F.U32, F.V32, ap, bp, nu, o, dD, logP, sc, st, pf);
   else
     return fail(TLRMVN_E_NOTSUP, "precision not available");
   TLR_CHECK(s);
+  pf.begin(TLRMVN_KC_REDUCE);
   k_shift_reduce<<<(unsigned)M, 256, 0, st>>>(logP, N, ell);
   k_final<<<1, 256, 0, st>>>(ell, (int)M, out2_dev);
+  pf.end();
   if (ell_dev_out) TLR_CUDA(cudaMemcpyAsync(ell_dev_out, ell, M * 8, cudaMemcpyDeviceToDevice, st));
   TLR_CUDA(cudaGetLastError());
   TLR_CUDA(cudaStreamSynchronize(st));
-  return TLRMVN_OK;
+  return pf.collect();
 }
 
 static int check_opts(const Factor& F, double nu, const tlrmvn_opts* o) {

@@ -34,6 +34,53 @@ cudaStream_t pick_stream(void* s) {
   return g_stream[dev];
 }
 
+static std::mutex g_prof_mu;
+static bool g_prof_on = false;
+static double g_prof_ms[TLRMVN_KC_COUNT] = {};
+static int64_t g_prof_n[TLRMVN_KC_COUNT] = {};
+
+Prof::Prof(cudaStream_t s) : st(s) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  on = g_prof_on;
+}
+void Prof::begin(int cls) {
+  if (!on) return;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  cudaEventRecord(a, st);
+  ev.push_back({cls, {a, b}});
+}
+void Prof::end() {
+  if (!on || ev.empty()) return;
+  cudaEventRecord(ev.back().second.second, st);
+}
+int Prof::collect() {
+  if (!on) return TLRMVN_OK;
+  double ms[TLRMVN_KC_COUNT] = {};
+  int64_t cnt[TLRMVN_KC_COUNT] = {};
+  for (auto& e : ev) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, e.second.first, e.second.second) == cudaSuccess) {
+      ms[e.first] += t;
+      cnt[e.first]++;
+    }
+  }
+  cudaGetLastError();
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (int c = 0; c < TLRMVN_KC_COUNT; c++) {
+    g_prof_ms[c] += ms[c];
+    g_prof_n[c] += cnt[c];
+  }
+  return TLRMVN_OK;
+}
+Prof::~Prof() {
+  for (auto& e : ev) {
+    cudaEventDestroy(e.second.first);
+    cudaEventDestroy(e.second.second);
+  }
+}
+
 Factor::~Factor() {
   dfree(B);
   dfree(Ucat);
@@ -153,6 +200,27 @@ extern "C" const char* tlrmvn_strerror(int status) {
 }
 
 extern "C" const char* tlrmvn_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" int tlrmvn_profile_enable(int on) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof_on = on != 0;
+  return TLRMVN_OK;
+}
+extern "C" int tlrmvn_profile_reset(void) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (int c = 0; c < TLRMVN_KC_COUNT; c++) {
+    g_prof_ms[c] = 0.0;
+    g_prof_n[c] = 0;
+  }
+  return TLRMVN_OK;
+}
+extern "C" int tlrmvn_profile_get(int kernel_class, double* total_ms, int64_t* launches) {
+  if (kernel_class < 0 || kernel_class >= TLRMVN_KC_COUNT) return fail(TLRMVN_E_INVAL, "bad kernel class");
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (total_ms) *total_ms = g_prof_ms[kernel_class];
+  if (launches) *launches = g_prof_n[kernel_class];
+  return TLRMVN_OK;
+}
 
 extern "C" int tlrmvn_factor_info(tlrmvn_factor_t f, int64_t* n, int* r, int* m, int64_t* k_total, int* capped) {
   if (!f) return fail(TLRMVN_E_INVAL, "null factor");

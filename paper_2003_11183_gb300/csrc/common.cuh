@@ -75,8 +75,16 @@ struct Factor {
   float* B32 = nullptr;
   float* U32 = nullptr;
   float* V32 = nullptr;
+  // bf16 operands of the tensor-core shifts (K-major, padded for TMA):
+  //   U16   (r*m) x kmax16: row i*m+v holds row v of Ucat_i, zero beyond Krow_i
+  //   V16   ktot x my16:    Vcat rows, zero beyond m
+  //   vmap16 Vcat row -> column of the padded rank space, whose row tile i starts at
+  //          kpad_off[i] (a multiple of 64) and spans kw16 columns in all
   __nv_bfloat16* U16 = nullptr;
   __nv_bfloat16* V16 = nullptr;
+  int32_t* vmap16 = nullptr;
+  std::vector<int64_t> kpad_off;
+  int64_t kmax16 = 0, kw16 = 0, my16 = 0;
   // lattice generators for n + 1 coordinates (device), and the permutation (device)
   uint64_t* Q = nullptr;
   int64_t* dperm = nullptr;

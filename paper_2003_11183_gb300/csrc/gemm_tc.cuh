@@ -1,0 +1,241 @@
+// BF16 x BF16 -> FP32 GEMM on the 5th-generation tensor cores (tcgen05, sm_103a)
+// for the low-rank limit shifts of the BF16-shift integrand.
+//
+//   D (M x N) = A (M x K) * B (N x K)^T      both operands K-major bf16
+//
+// One 128 x 256 output tile per CTA of 128 threads.  Operands are staged by
+// TMA (128-byte swizzle) through a 4-stage shared-memory ring; one thread
+// issues tcgen05.mma (M=128, N=256, K=16) into a TMEM accumulator; after the
+// last k-block all four warps read their 32 TMEM lanes and run the epilogue:
+//   EPI_ROWMAJOR_F32:  D[row * ldd + col] = acc              (limit shifts, fp32)
+//   EPI_COLMAP_BF16:   W[col * ldw + map[row]] = bf16(acc)   (projections, bf16)
+// Every mbarrier wait is bounded; on expiry the CTA records an error code,
+// skips the remaining work, frees its TMEM and returns.
+#pragma once
+#include <cuda.h>
+#include "common.cuh"
+
+namespace tlrmvn {
+namespace tc {
+
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr int A_BYTES = BM * BK * 2;  // 16 KB
+constexpr int B_BYTES = BN * BK * 2;  // 32 KB
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int TMEM_COLS = 256;
+constexpr uint32_t WAIT_LIMIT = 1u << 24;  // polls before a wait gives up (seconds)
+
+enum { EPI_ROWMAJOR_F32 = 0, EPI_COLMAP_BF16 = 1 };
+
+// Instruction descriptor of tcgen05.mma kind::f16: fp32 accumulator, bf16 A and
+// B, both K-major, N = 256 (bits 17-22 hold N/8), M = 128 (bits 24-28 hold M/16).
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;            // leading byte offset (unused with this swizzle)
+  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
+  d |= (uint64_t)1 << 46;            // version
+  d |= (uint64_t)2 << 61;            // 128-byte swizzle
+  return d;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false (and the error code set) when the limit expires.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code) {
+  for (uint32_t i = 0; i < WAIT_LIMIT; i++)
+    if (mbar_try_wait(bar, parity)) return true;
+  atomicExch(err, code);
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          tmem_d),
+      "l"(a), "l"(b), "r"(IDESC), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// 32 consecutive fp32 columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
+}
+
+struct GemmTcArgs {
+  int M, N, K;          // logical sizes; rows >= M and cols >= N are not stored
+  int ax0, ay0;         // A tile origin in its tensor map (x = K, y = M)
+  int bx0, by0;         // B tile origin (x = K, y = N)
+  float* D;             // EPI_ROWMAJOR_F32
+  int64_t ldd;
+  __nv_bfloat16* W;     // EPI_COLMAP_BF16
+  int64_t ldw;
+  const int32_t* map;
+  int* err;             // nonzero after a wait expired
+};
+
+template <int EPI>
+__global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUtensorMap mapA,
+                                                    const __grid_constant__ CUtensorMap mapB, GemmTcArgs p) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* done = empty + STAGES;
+  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  __shared__ int abort_flag;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int nk = (p.K + BK - 1) / BK;
+
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < STAGES; s++) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // TMA producer
+    int issued = 0;
+    for (int kb = 0; kb < nk; kb++) {
+      const int s = kb % STAGES;
+      if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1, p.err, 2)) {
+        abort_flag = 1;
+        break;
+      }
+      if (*(volatile int*)&abort_flag) break;
+      unsigned char* sa = smem + s * STAGE_BYTES;
+      mbar_expect_tx(&full[s], STAGE_BYTES);
+      tma_load_2d(sa, &mapA, &full[s], p.ax0 + kb * BK, p.ay0 + m0);
+      tma_load_2d(sa + A_BYTES, &mapB, &full[s], p.bx0 + kb * BK, p.by0 + n0);
+      issued = kb + 1;
+    }
+    if (*(volatile int*)&abort_flag) {
+      // drain: wait (bounded) for the copies still in flight before the CTA exits
+      for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; kb++)
+        mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, p.err, 5);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    bool ok = true;
+    for (int kb = 0; kb < nk && ok; kb++) {
+      const int s = kb % STAGES;
+      if (!mbar_wait(&full[s], (kb / STAGES) & 1, p.err, 3)) {
+        abort_flag = 1;
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+      const uint64_t da = sdesc(sa), db = sdesc(sa + A_BYTES);
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; kk++)
+        mma_bf16(tmem, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), (kb > 0 || kk > 0) ? 1u : 0u);
+      mma_commit(&empty[s]);
+    }
+    mma_commit(done);
+  }
+  __syncwarp();
+  // epilogue: every warp reads its 32 TMEM lanes (rows m0 + 32*warp + lane)
+  const bool ready = mbar_wait(done, 0, p.err, 4);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (ready && !*(volatile int*)&abort_flag) {
+    const int row = m0 + 32 * warp + lane;
+    const uint32_t tbase = tmem + ((uint32_t)(32 * warp) << 16);
+    if (EPI == EPI_ROWMAJOR_F32) {
+      for (int c = 0; c < BN / 32; c++) {
+        float v[32];
+        tmem_ld32(tbase + c * 32, v);
+        const int col0 = n0 + c * 32;
+        if (row < p.M) {
+          float* dst = p.D + (int64_t)row * p.ldd + col0;
+          if (col0 + 32 <= p.N && ((p.ldd & 3) == 0)) {
+#pragma unroll
+            for (int q = 0; q < 8; q++)
+              reinterpret_cast<float4*>(dst)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+          } else {
+            for (int q = 0; q < 32; q++)
+              if (col0 + q < p.N) dst[q] = v[q];
+          }
+        }
+      }
+    } else {
+      const int64_t dcol = (row < p.M) ? (int64_t)p.map[row] : 0;
+      for (int c = 0; c < BN / 32; c++) {
+        float v[32];
+        tmem_ld32(tbase + c * 32, v);
+        const int col0 = n0 + c * 32;
+        if (row < p.M) {
+          for (int q = 0; q < 32; q++)
+            if (col0 + q < p.N) p.W[(int64_t)(col0 + q) * p.ldw + dcol] = __float2bfloat16_rn(v[q]);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+}  // namespace tc
+}  // namespace tlrmvn

@@ -12,6 +12,9 @@
 // Per-sample logs are reduced per shift by a log-sum-exp and then across shifts (Section 2.1).
 #include "common.cuh"
 #include "gemm.cuh"
+#include "gemm_tc.cuh"
+
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cstring>
@@ -129,56 +132,69 @@ struct DiagArgs {
   double* logP;  // all samples
 };
 
-template <typename YT>
-__device__ __forceinline__ YT store_y(float y);
-template <>
-__device__ __forceinline__ float store_y<float>(float y) { return y; }
-template <>
-__device__ __forceinline__ __nv_bfloat16 store_y<__nv_bfloat16>(float y) { return __float2bfloat16_rn(y); }
+__device__ __forceinline__ void put_y(double* Y, int64_t i, double y) { Y[i] = y; }
+__device__ __forceinline__ void put_y(float* Y, int64_t i, float y) { Y[i] = y; }
+__device__ __forceinline__ void put_y(__nv_bfloat16* Y, int64_t i, float y) { Y[i] = __float2bfloat16_rn(y); }
 
 // One thread per sample; the tile's y values of the thread's sample live in shared
-// memory (column tid of a [mt][blockDim] array); B_i rows are read through L1
-// as warp-uniform broadcasts.
-template <typename T, typename YT>
+// memory (column tid of a [mt][blockDim+1] array); B_i rows are read through L1
+// as warp-uniform broadcasts.  Y layout:
+//   SAMPLE_MAJOR = false: Y[v * ldy + c]  (variable-major, written as produced)
+//   SAMPLE_MAJOR = true:  Y[c * ldy + v]  (each sample's y contiguous: the K-major
+//                         operand of the tensor-core projection), written at the
+//                         end of the tile from shared memory, a row per warp pass.
+template <typename T, typename YT, bool SAMPLE_MAJOR>
 __global__ void k_diag(DiagArgs<T, YT> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* ys = reinterpret_cast<T*>(smem_raw);
-  const int bd = blockDim.x, tid = threadIdx.x;
-  const int64_t c = (int64_t)blockIdx.x * bd + tid;
-  if (c >= p.C) return;
-  const int64_t g = p.sample0 + c;
-  const int64_t s = g / p.N;
-  const uint64_t k = (uint64_t)(g - s * p.N) + 1;
-  const uint64_t* Ds = p.D + s * p.ldD + p.coord0;
-  const uint64_t* Qt = p.Q + p.coord0;
-  const T rs = p.rs ? (T)p.rs[c] : (T)1;
-  T lp = 0;
-  for (int v = 0; v < p.mt; v++) {
-    const T* Brow = p.B + (int64_t)v * p.ldb;
-    T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-    int u = 0;
-    for (; u + 4 <= v; u += 4) {
-      s0 = fma(__ldg(Brow + u), ys[(u)*bd + tid], s0);
-      s1 = fma(__ldg(Brow + u + 1), ys[(u + 1) * bd + tid], s1);
-      s2 = fma(__ldg(Brow + u + 2), ys[(u + 2) * bd + tid], s2);
-      s3 = fma(__ldg(Brow + u + 3), ys[(u + 3) * bd + tid], s3);
+  const int bd = blockDim.x, tid = threadIdx.x, ld = bd + 1;
+  const int64_t c0 = (int64_t)blockIdx.x * bd;
+  const int64_t c = c0 + tid;
+  const bool active = c < p.C;
+  if (active) {
+    const int64_t g = p.sample0 + c;
+    const int64_t s = g / p.N;
+    const uint64_t k = (uint64_t)(g - s * p.N) + 1;
+    const uint64_t* Ds = p.D + s * p.ldD + p.coord0;
+    const uint64_t* Qt = p.Q + p.coord0;
+    const T rs = p.rs ? (T)p.rs[c] : (T)1;
+    T lp = 0;
+    for (int v = 0; v < p.mt; v++) {
+      const T* Brow = p.B + (int64_t)v * p.ldb;
+      T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+      int u = 0;
+      for (; u + 4 <= v; u += 4) {
+        s0 = fma(__ldg(Brow + u), ys[(u)*ld + tid], s0);
+        s1 = fma(__ldg(Brow + u + 1), ys[(u + 1) * ld + tid], s1);
+        s2 = fma(__ldg(Brow + u + 2), ys[(u + 2) * ld + tid], s2);
+        s3 = fma(__ldg(Brow + u + 3), ys[(u + 3) * ld + tid], s3);
+      }
+      for (; u < v; u++) s0 = fma(__ldg(Brow + u), ys[u * ld + tid], s0);
+      const T sum = (s0 + s1) + (s2 + s3);
+      const T dl = p.Delta ? p.Delta[(int64_t)v * p.ldd + c] : (T)0;
+      const T lvv = __ldg(Brow + v);
+      const T at = ((T)p.a[v] * rs - dl - sum) / lvv;
+      const T bt = ((T)p.b[v] * rs - dl - sum) / lvv;
+      double w, wc;
+      lattice_w(k * Qt[v] + Ds[v], p.periodize, w, wc);
+      T lv, y;
+      sov_step<T>(at, bt, (T)w, (T)wc, lv, y);
+      lp += lv;
+      ys[v * ld + tid] = y;
+      if (!SAMPLE_MAJOR) put_y(p.Y, (int64_t)v * p.ldy + c, y);
     }
-    for (; u < v; u++) s0 = fma(__ldg(Brow + u), ys[u * bd + tid], s0);
-    const T sum = (s0 + s1) + (s2 + s3);
-    const T dl = p.Delta ? p.Delta[(int64_t)v * p.ldd + c] : (T)0;
-    const T lvv = __ldg(Brow + v);
-    const T at = ((T)p.a[v] * rs - dl - sum) / lvv;
-    const T bt = ((T)p.b[v] * rs - dl - sum) / lvv;
-    double w, wc;
-    lattice_w(k * Qt[v] + Ds[v], p.periodize, w, wc);
-    T ld, y;
-    sov_step<T>(at, bt, (T)w, (T)wc, ld, y);
-    lp += ld;
-    ys[v * bd + tid] = y;
-    p.Y[(int64_t)v * p.ldy + c] = (YT)y;
+    if (p.first) p.logP[g] = (double)lp;
+    else p.logP[g] += (double)lp;
   }
-  if (p.first) p.logP[g] = (double)lp;
-  else p.logP[g] += (double)lp;
+  if (SAMPLE_MAJOR) {
+    __syncthreads();
+    const int nw = bd >> 5, warp = tid >> 5, lane = tid & 31;
+    for (int j = warp; j < bd; j += nw) {
+      if (c0 + j >= p.C) break;
+      YT* row = p.Y + (c0 + j) * p.ldy;
+      for (int v = lane; v < p.mt; v += 32) put_y(row, v, ys[v * ld + j]);
+    }
+  }
 }
 
 // ---- reductions (Section 2.1 estimator, in logs) -----------------------------------
@@ -249,9 +265,22 @@ __global__ void k_convert(const S* src, D* dst, int64_t count) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < count) dst[i] = (D)src[i];
 }
-__global__ void k_convert_bf16(const double* src, __nv_bfloat16* dst, int64_t count) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < count) dst[i] = __double2bfloat16(src[i]);
+// U16[(i*m + v) * kmax + k] = Ucat_i[v][k] for k < Krow_i, else 0
+__global__ void k_pad_u16(const double* Ucat, const int64_t* krow_off, int m, int64_t kmax, int64_t count,
+                          __nv_bfloat16* U16) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  int64_t row = t / kmax, k = t % kmax;
+  int64_t i = row / m, v = row % m;
+  int64_t Kr = krow_off[i + 1] - krow_off[i];
+  U16[t] = (k < Kr) ? __double2bfloat16(Ucat[(int64_t)m * krow_off[i] + v * Kr + k]) : __float2bfloat16(0.f);
+}
+// V16[row * my + u] = Vcat[row][u] for u < m, else 0
+__global__ void k_pad_v16(const double* Vcat, int m, int64_t my, int64_t count, __nv_bfloat16* V16) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  int64_t row = t / my, u = t % my;
+  V16[t] = (u < m) ? __double2bfloat16(Vcat[row * m + u]) : __float2bfloat16(0.f);
 }
 
 static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -268,13 +297,73 @@ static int ensure_copies(Factor& F, int precision, cudaStream_t st) {
     k_convert<double, float><<<blocks_for(nu, 256), 256, 0, st>>>(F.Ucat, F.U32, nu);
     k_convert<double, float><<<blocks_for(nu, 256), 256, 0, st>>>(F.Vcat, F.V32, nu);
   }
-  if (precision == TLRMVN_BF16_SHIFT && !F.U16 && nu) {
-    TLR_CHECK(dalloc(&F.U16, nu));
-    TLR_CHECK(dalloc(&F.V16, nu));
-    k_convert_bf16<<<blocks_for(nu, 256), 256, 0, st>>>(F.Ucat, F.U16, nu);
-    k_convert_bf16<<<blocks_for(nu, 256), 256, 0, st>>>(F.Vcat, F.V16, nu);
+  if (precision == TLRMVN_BF16_SHIFT && !F.kpad_off.size()) {
+    // padded rank space: row tile i starts at a multiple of 64
+    const int r = F.r, m = F.m;
+    F.kpad_off.assign(r + 1, 0);
+    int64_t kmax = 0;
+    for (int i = 0; i < r; i++) {
+      F.kpad_off[i + 1] = F.kpad_off[i] + (F.krow(i) + 63) / 64 * 64;
+      kmax = std::max(kmax, F.krow(i));
+    }
+    F.kw16 = std::max<int64_t>(F.kpad_off[r], 64);
+    F.kmax16 = std::max<int64_t>((kmax + 63) / 64 * 64, 64);
+    F.my16 = ((int64_t)m + 63) / 64 * 64;
+    if (F.ktot) {
+      // vmap16: for each Vcat row, its column in the padded rank space
+      std::vector<int32_t> v16(F.ktot);
+      for (int j = 0; j < r; j++) {
+        int64_t row = F.kcol_off[j];
+        for (int i = j + 1; i < r; i++) {
+          int64_t local = 0;
+          for (int t = 0; t < j; t++) local += F.rank[(size_t)i * r + t];
+          for (int c = 0; c < F.rank[(size_t)i * r + j]; c++) v16[row++] = (int32_t)(F.kpad_off[i] + local + c);
+        }
+      }
+      TLR_CHECK(dalloc(&F.vmap16, (size_t)F.ktot));
+      TLR_CUDA(cudaMemcpyAsync(F.vmap16, v16.data(), v16.size() * 4, cudaMemcpyHostToDevice, st));
+      std::vector<int64_t> kro(F.krow_off);
+      int64_t* dkro = nullptr;
+      TLR_CHECK(dalloc(&dkro, kro.size()));
+      TLR_CUDA(cudaMemcpyAsync(dkro, kro.data(), kro.size() * 8, cudaMemcpyHostToDevice, st));
+      const int64_t nu16 = (int64_t)r * m * F.kmax16, nv16 = F.ktot * F.my16;
+      TLR_CHECK(dalloc(&F.U16, nu16));
+      TLR_CHECK(dalloc(&F.V16, nv16));
+      k_pad_u16<<<blocks_for(nu16, 256), 256, 0, st>>>(F.Ucat, dkro, m, F.kmax16, nu16, F.U16);
+      k_pad_v16<<<blocks_for(nv16, 256), 256, 0, st>>>(F.Vcat, m, F.my16, nv16, F.V16);
+      TLR_CUDA(cudaStreamSynchronize(st));
+      dfree(dkro);
+    }
   }
   TLR_CUDA(cudaGetLastError());
+  return TLRMVN_OK;
+}
+
+// ---- tensor maps for the tcgen05 shifts ---------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+// 2-D bf16 tensor (inner x outer, row pitch in bytes), box 64 x box_outer, 128-byte swizzle.
+static int make_map(CUtensorMap* map, const void* base, uint64_t inner, uint64_t outer, uint64_t pitch,
+                    uint32_t box_outer) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return fail(TLRMVN_E_CUDA, "cuTensorMapEncodeTiled is not available");
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {pitch};
+  cuuint32_t box[2] = {64, box_outer};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(TLRMVN_E_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
   return TLRMVN_OK;
 }
 
@@ -335,8 +424,8 @@ static int run_chunks(Factor& F, const T* Bt, const T* Ut, const T* Vt, const do
 
   int bd = 256;
   while (bd > 32 && (size_t)m * bd * sizeof(T) > 65536) bd >>= 1;
-  size_t smem = (size_t)m * bd * sizeof(T);
-  TLR_CUDA(cudaFuncSetAttribute(k_diag<T, YT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  size_t smem = (size_t)m * (bd + 1) * sizeof(T);
+  TLR_CUDA(cudaFuncSetAttribute(k_diag<T, YT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
 
   for (int64_t c0 = 0; c0 < S; c0 += C) {
     const int64_t Cc = std::min(C, S - c0);
@@ -378,7 +467,7 @@ static int run_chunks(Factor& F, const T* Bt, const T* Ut, const T* Vt, const do
       a.ldy = C;
       a.logP = logP;
       pf.begin(TLRMVN_KC_DIAG);
-      k_diag<T, YT><<<blocks_for(Cc, bd), bd, smem, st>>>(a);
+      k_diag<T, YT, false><<<blocks_for(Cc, bd), bd, smem, st>>>(a);
       pf.end();
       if (Kc > 0) {
         pf.begin(TLRMVN_KC_VPROJ);
@@ -388,6 +477,119 @@ static int run_chunks(Factor& F, const T* Bt, const T* Ut, const T* Vt, const do
     }
     TLR_CUDA(cudaGetLastError());
   }
+  return TLRMVN_OK;
+}
+
+// BF16-shift integrand: float32 sweep; both low-rank products on tcgen05 with
+// bf16 operands and fp32 accumulation.  Layouts (C = samples in the chunk):
+//   W16  C x kw16  bf16, sample-major: row c holds the projections of sample c
+//   Y16  C x my16  bf16, sample-major
+//   Dl   m x C     fp32, variable-major (read by the sweep)
+static int run_chunks_bf16(Factor& F, const double* ap, const double* bp, double nu, const tlrmvn_opts& o,
+                           const uint64_t* dD, double* logP, Scratch& sc, cudaStream_t st, Prof& pf) {
+  const int64_t M = o.n_shifts, N = o.n_points, S = M * N;
+  const int m = F.m;
+  int64_t C = o.sample_chunk > 0 ? o.sample_chunk : 0;
+  if (C <= 0) {
+    // keep W16 within ~32 GiB
+    const double budget = 32.0 * (1ull << 30);
+    double per = (double)F.kw16 * 2 + (double)F.my16 * 2 + (double)m * 4 + 16.0;
+    C = (int64_t)std::max(256.0, std::min((double)S, budget / per));
+  }
+  C = std::min<int64_t>(C, S);
+  C = (C + 255) / 256 * 256;
+  __nv_bfloat16 *W = nullptr, *Y = nullptr;
+  float* Dl = nullptr;
+  double* rs = nullptr;
+  int* err = nullptr;
+  TLR_CHECK(sc.get(&W, (size_t)F.kw16 * C));
+  TLR_CHECK(sc.get(&Y, (size_t)F.my16 * C));
+  TLR_CHECK(sc.get(&Dl, (size_t)m * C));
+  TLR_CHECK(sc.get(&err, 1));
+  const bool mvt = std::isfinite(nu);
+  if (mvt) TLR_CHECK(sc.get(&rs, (size_t)C));
+  // padding columns of W and Y must hold finite values: they meet zero operand columns
+  TLR_CUDA(cudaMemsetAsync(W, 0, (size_t)F.kw16 * C * 2, st));
+  TLR_CUDA(cudaMemsetAsync(Y, 0, (size_t)F.my16 * C * 2, st));
+  TLR_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+
+  CUtensorMap mapU, mapV, mapW, mapY;
+  if (F.ktot) {
+    TLR_CHECK(make_map(&mapU, F.U16, F.kmax16, (uint64_t)F.r * m, F.kmax16 * 2, tc::BM));
+    TLR_CHECK(make_map(&mapV, F.V16, F.my16, F.ktot, F.my16 * 2, tc::BM));
+  }
+  TLR_CHECK(make_map(&mapW, W, F.kw16, C, F.kw16 * 2, tc::BN));
+  TLR_CHECK(make_map(&mapY, Y, F.my16, C, F.my16 * 2, tc::BN));
+  TLR_CUDA(cudaFuncSetAttribute(tc::k_gemm_tc<tc::EPI_ROWMAJOR_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                tc::SMEM_BYTES));
+  TLR_CUDA(cudaFuncSetAttribute(tc::k_gemm_tc<tc::EPI_COLMAP_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                tc::SMEM_BYTES));
+
+  int bd = 256;
+  while (bd > 32 && (size_t)m * bd * sizeof(float) > 65536) bd >>= 1;
+  size_t smem = (size_t)m * (bd + 1) * sizeof(float);
+  TLR_CUDA(cudaFuncSetAttribute(k_diag<float, __nv_bfloat16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem));
+
+  for (int64_t c0 = 0; c0 < S; c0 += C) {
+    const int64_t Cc = std::min(C, S - c0);
+    if (mvt) {
+      pf.begin(TLRMVN_KC_CHI);
+      k_chi_scale<<<blocks_for(Cc, 128), 128, 0, st>>>(rs, F.Q, dD, F.n + 1, F.n, c0, N, Cc, nu, o.periodize);
+      pf.end();
+    }
+    const unsigned ntile = (unsigned)((Cc + tc::BN - 1) / tc::BN);
+    for (int i = 0; i < F.r; i++) {
+      const int mt = (int)F.tsize(i);
+      const int64_t Kr = F.krow(i), Kc = F.kcol(i);
+      const float* Delta = nullptr;
+      if (Kr > 0) {
+        tc::GemmTcArgs g{mt, (int)Cc, (int)Kr, 0, i * m, (int)F.kpad_off[i], 0, Dl, C, nullptr, 0, nullptr, err};
+        pf.begin(TLRMVN_KC_SHIFT);
+        tc::k_gemm_tc<tc::EPI_ROWMAJOR_F32><<<dim3(ntile, (unsigned)((mt + tc::BM - 1) / tc::BM)), 128,
+                                               tc::SMEM_BYTES, st>>>(mapU, mapW, g);
+        pf.end();
+        Delta = Dl;
+      }
+      DiagArgs<float, __nv_bfloat16> a;
+      a.B = F.B32 + (size_t)i * m * m;
+      a.mt = mt;
+      a.ldb = m;
+      a.Delta = Delta;
+      a.ldd = C;
+      a.a = ap + F.tile_off[i];
+      a.b = bp + F.tile_off[i];
+      a.rs = rs;
+      a.Q = F.Q;
+      a.D = dD;
+      a.ldD = F.n + 1;
+      a.coord0 = F.tile_off[i];
+      a.sample0 = c0;
+      a.N = N;
+      a.C = Cc;
+      a.periodize = o.periodize;
+      a.first = (i == 0);
+      a.Y = Y;
+      a.ldy = F.my16;
+      a.logP = logP;
+      pf.begin(TLRMVN_KC_DIAG);
+      k_diag<float, __nv_bfloat16, true><<<blocks_for(Cc, bd), bd, smem, st>>>(a);
+      pf.end();
+      if (Kc > 0) {
+        tc::GemmTcArgs g{(int)Kc, (int)Cc, mt, 0, (int)F.kcol_off[i], 0, 0, nullptr, 0, W, F.kw16,
+                         F.vmap16 + F.kcol_off[i], err};
+        pf.begin(TLRMVN_KC_VPROJ);
+        tc::k_gemm_tc<tc::EPI_COLMAP_BF16><<<dim3(ntile, (unsigned)((Kc + tc::BM - 1) / tc::BM)), 128,
+                                              tc::SMEM_BYTES, st>>>(mapV, mapY, g);
+        pf.end();
+      }
+    }
+    TLR_CUDA(cudaGetLastError());
+  }
+  int herr = 0;
+  TLR_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TLR_CUDA(cudaStreamSynchronize(st));
+  if (herr) return fail(TLRMVN_E_CUDA, "tensor-core shift kernel gave up waiting (code " + std::to_string(herr) + ")");
   return TLRMVN_OK;
 }
 
@@ -431,7 +633,7 @@ static int prob_impl(Factor& F, const double* a_dev, const double* b_dev, double
   else if (o.precision == TLRMVN_FP32)
     s = run_chunks<float, float>(F, F.B32, F.U32, F.V32, ap, bp, nu, o, dD, logP, sc, st, pf);
   else
-    return fail(TLRMVN_E_NOTSUP, "precision not available");
+    s = run_chunks_bf16(F, ap, bp, nu, o, dD, logP, sc, st, pf);
   TLR_CHECK(s);
   pf.begin(TLRMVN_KC_REDUCE);
   k_shift_reduce<<<(unsigned)M, 256, 0, st>>>(logP, N, ell);

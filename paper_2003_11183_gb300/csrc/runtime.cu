@@ -91,6 +91,7 @@ Factor::~Factor() {
   dfree(V32);
   dfree(U16);
   dfree(V16);
+  dfree(vmap16);
   dfree(Q);
   dfree(dperm);
 }
@@ -114,6 +115,12 @@ int factor_alloc_compact(Factor& F) {
   TLR_CHECK(dalloc(&F.Ucat, (size_t)F.m * F.ktot));
   TLR_CHECK(dalloc(&F.Vcat, (size_t)F.m * F.ktot));
   TLR_CHECK(dalloc(&F.vmap, (size_t)F.ktot));
+  // zero padding rows / columns of short tiles
+  if (F.ktot) {
+    TLR_CUDA(cudaMemset(F.Ucat, 0, (size_t)F.m * F.ktot * 8));
+    TLR_CUDA(cudaMemset(F.Vcat, 0, (size_t)F.m * F.ktot * 8));
+  }
+  TLR_CUDA(cudaMemset(F.B, 0, (size_t)r * F.m * F.m * 8));
   return TLRMVN_OK;
 }
 

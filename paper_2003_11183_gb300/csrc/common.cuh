@@ -72,6 +72,11 @@ struct Factor {
   double* Vcat = nullptr;
   int32_t* vmap = nullptr;
   // lazily made copies for the reduced-precision integrands
+  //   BT32  r x m x ldbt: transposed diagonal tiles, BT32[i][u][v] = B_i[v][u]
+  //   inv32 r x m: 1 / B_i[v][v]
+  float* BT32 = nullptr;
+  float* inv32 = nullptr;
+  int64_t ldbt = 0;
   float* B32 = nullptr;
   float* U32 = nullptr;
   float* V32 = nullptr;

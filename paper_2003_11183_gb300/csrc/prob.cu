@@ -90,8 +90,8 @@ __device__ double gamma_p_inv(double a, double p, double q) {
   return x;
 }
 
-__global__ void k_chi_scale(double* rs, const uint64_t* Q, const uint64_t* D, int64_t ldD, int64_t coord,
-                            int64_t sample0, int64_t N, int64_t C, double nu, int periodize) {
+__global__ void k_chi_scale(double* rs, float* rs32, const uint64_t* Q, const uint64_t* D, int64_t ldD,
+                            int64_t coord, int64_t sample0, int64_t N, int64_t C, double nu, int periodize) {
   int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= C) return;
   int64_t g = sample0 + c, s = g / N;
@@ -99,18 +99,24 @@ __global__ void k_chi_scale(double* rs, const uint64_t* Q, const uint64_t* D, in
   double w, wc;
   lattice_w(k * Q[coord] + D[s * ldD + coord], periodize, w, wc);
   double x = gamma_p_inv(0.5 * nu, w, wc);
-  rs[c] = sqrt(2.0 * x / nu);
+  double r = sqrt(2.0 * x / nu);
+  if (rs) rs[c] = r;
+  if (rs32) rs32[c] = (float)r;
 }
 
 // ---- limits: permute to factor order and validate ---------------------------------
 __global__ void k_permute_limits(const double* a, const double* b, const int64_t* perm, int64_t n, double* ap,
-                                 double* bp, int* bad) {
+                                 double* bp, float* ap32, float* bp32, int* bad) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   double av = a[perm[t]], bv = b[perm[t]];
   if (isnan(av) || isnan(bv) || av > bv || av == INFINITY || bv == -INFINITY) atomicExch(bad, 1);
   ap[t] = av;
   bp[t] = bv;
+  if (ap32) {
+    ap32[t] = (float)av;
+    bp32[t] = (float)bv;
+  }
 }
 
 // ---- diagonal-tile sweep (eq. 2 on B_i, Algorithm 6 inner call) -------------------
@@ -195,6 +201,164 @@ __global__ void k_diag(DiagArgs<T, YT> p) {
       for (int v = lane; v < p.mt; v += 32) put_y(row, v, ys[v * ld + j]);
     }
   }
+}
+
+// ---- float32 sweep ------------------------------------------------------------------
+// Lattice value as floats, from the same exact numerator as lattice_w (integer
+// arithmetic only: the float path issues no float64 instruction).
+__device__ __forceinline__ void lattice_wf(uint64_t x, int periodize, float& w, float& wc) {
+  int64_t num;
+  if (periodize) {
+    int64_t h = (int64_t)(x >> 11);
+    num = 2 * h + 1 - (int64_t(1) << 53);
+    if (num < 0) num = -num;
+  } else {
+    num = 2 * (int64_t)(x >> 12) + 1;
+  }
+  const int64_t numc = (int64_t(1) << 53) - num;
+  w = fmaf((float)(uint32_t)(num >> 21), 2.3283064365386963e-10f, (float)(uint32_t)(num & 0x1FFFFF) * 1.1102230246251565e-16f);
+  wc = fmaf((float)(uint32_t)(numc >> 21), 2.3283064365386963e-10f,
+            (float)(uint32_t)(numc & 0x1FFFFF) * 1.1102230246251565e-16f);
+}
+
+// eq. (2) for one variable in float32; the one-sided case (at = -inf) evaluates one
+// scaled complementary error function and the logs it needs, nothing else.
+__device__ __forceinline__ void sov_step_f32(float at, float bt, float w, float wc, float& ld, float& y) {
+  const float rs2 = (float)TLR_RSQRT2;
+  if (at == -INFINITY && bt != INFINITY) {
+    if (bt < 0.0f) {
+      const float t = -bt * rs2;
+      const float le = logf(0.5f * erfcxf(t)) - t * t;  // log Phi(bt)
+      const float lu = logf(w) + le;                      // log u, u = w Phi(bt) < 1/2
+      y = ndtri_lower(expf(lu), lu);
+      ld = le;
+    } else {
+      const float ec = 0.5f * erfcf(bt * rs2);
+      const float e = 1.0f - ec;
+      const float u = w * e, uc = ec + wc * e;
+      y = (u <= 0.5f) ? ndtri_lower(u, logf(u)) : -ndtri_lower(uc, logf(uc));
+      ld = log1pf(-ec);
+    }
+    return;
+  }
+  sov_step<float>(at, bt, w, wc, ld, y);
+}
+
+template <typename YT>
+struct DiagArgs32 {
+  const float* BT;   // transposed tile, BT[u * ldbt + v] = B[v][u]
+  const float* inv;  // 1 / B[v][v]
+  int mt;
+  int64_t ldbt;
+  const float* Delta;
+  int64_t ldd;
+  const float* a;
+  const float* b;
+  const float* rs;
+  const uint64_t* Q;
+  const uint64_t* D;
+  int64_t ldD, coord0, sample0, N, C;
+  int periodize, first;
+  YT* Y;
+  int64_t ldy;
+  double* logP;
+};
+
+// One thread per sample; 16 variables per pass: the partial sums of a block of
+// 16 variables over all earlier variables of the tile are accumulated together
+// (each y_u read once per block, B read as four broadcast float4 per u), then
+// the block's 16 x 16 triangle and special functions run in order.
+constexpr int DIAG_VB = 16;
+template <typename YT, bool SAMPLE_MAJOR>
+__global__ void k_diag_f32(DiagArgs32<YT> p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* ys = reinterpret_cast<float*>(smem_raw);
+  const int bd = blockDim.x, tid = threadIdx.x, ld = bd + 1;
+  const int64_t c0 = (int64_t)blockIdx.x * bd;
+  const int64_t c = c0 + tid;
+  if (c < p.C) {
+    const int64_t g = p.sample0 + c;
+    const int64_t s = g / p.N;
+    const uint64_t k = (uint64_t)(g - s * p.N) + 1;
+    const uint64_t* Ds = p.D + s * p.ldD + p.coord0;
+    const uint64_t* Qt = p.Q + p.coord0;
+    const float rs = p.rs ? p.rs[c] : 1.0f;
+    const int mt = p.mt;
+    float lp = 0.0f;
+    for (int v0 = 0; v0 < mt; v0 += DIAG_VB) {
+      float acc[DIAG_VB];
+#pragma unroll
+      for (int j = 0; j < DIAG_VB; j++) acc[j] = 0.0f;
+      const float* bcol = p.BT + v0;
+#pragma unroll 2
+      for (int u = 0; u < v0; u++) {
+        const float yu = ys[u * ld + tid];
+        const float4* b4 = reinterpret_cast<const float4*>(bcol + (int64_t)u * p.ldbt);
+        const float4 q0 = __ldg(b4), q1 = __ldg(b4 + 1), q2 = __ldg(b4 + 2), q3 = __ldg(b4 + 3);
+        acc[0] = fmaf(q0.x, yu, acc[0]);
+        acc[1] = fmaf(q0.y, yu, acc[1]);
+        acc[2] = fmaf(q0.z, yu, acc[2]);
+        acc[3] = fmaf(q0.w, yu, acc[3]);
+        acc[4] = fmaf(q1.x, yu, acc[4]);
+        acc[5] = fmaf(q1.y, yu, acc[5]);
+        acc[6] = fmaf(q1.z, yu, acc[6]);
+        acc[7] = fmaf(q1.w, yu, acc[7]);
+        acc[8] = fmaf(q2.x, yu, acc[8]);
+        acc[9] = fmaf(q2.y, yu, acc[9]);
+        acc[10] = fmaf(q2.z, yu, acc[10]);
+        acc[11] = fmaf(q2.w, yu, acc[11]);
+        acc[12] = fmaf(q3.x, yu, acc[12]);
+        acc[13] = fmaf(q3.y, yu, acc[13]);
+        acc[14] = fmaf(q3.z, yu, acc[14]);
+        acc[15] = fmaf(q3.w, yu, acc[15]);
+      }
+      float yb[DIAG_VB];
+#pragma unroll
+      for (int j = 0; j < DIAG_VB; j++) {
+        const int v = v0 + j;
+        yb[j] = 0.0f;
+        if (v < mt) {
+          float sum = acc[j];
+#pragma unroll
+          for (int jj = 0; jj < j; jj++) sum = fmaf(__ldg(p.BT + (int64_t)(v0 + jj) * p.ldbt + v), yb[jj], sum);
+          const float dl = p.Delta ? p.Delta[(int64_t)v * p.ldd + c] : 0.0f;
+          const float iv = __ldg(p.inv + v);
+          const float at = (p.a[v] * rs - dl - sum) * iv;
+          const float bt = (p.b[v] * rs - dl - sum) * iv;
+          float w, wc;
+          lattice_wf(k * Qt[v] + Ds[v], p.periodize, w, wc);
+          float lv, y;
+          sov_step_f32(at, bt, w, wc, lv, y);
+          lp += lv;
+          yb[j] = y;
+          ys[v * ld + tid] = y;
+          if (!SAMPLE_MAJOR) put_y(p.Y, (int64_t)v * p.ldy + c, y);
+        }
+      }
+    }
+    if (p.first) p.logP[g] = (double)lp;
+    else p.logP[g] += (double)lp;
+  }
+  if (SAMPLE_MAJOR) {
+    __syncthreads();
+    const int nw = bd >> 5, warp = tid >> 5, lane = tid & 31;
+    for (int j = warp; j < bd; j += nw) {
+      if (c0 + j >= p.C) break;
+      YT* row = p.Y + (c0 + j) * p.ldy;
+      for (int v = lane; v < p.mt; v += 32) put_y(row, v, ys[v * ld + j]);
+    }
+  }
+}
+
+// BT32[i][u][v] = B[i][v][u] (zero for v >= m), inv32[i][v] = 1 / B[i][v][v]
+__global__ void k_transpose_tiles(const double* B, int m, int64_t ldbt, int64_t count, float* BT, float* inv) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  int64_t i = t / ((int64_t)m * ldbt), rem = t % ((int64_t)m * ldbt);
+  int64_t u = rem / ldbt, v = rem % ldbt;
+  const double* Bi = B + i * (int64_t)m * m;
+  BT[t] = (v < m) ? (float)Bi[v * m + u] : 0.0f;
+  if (v == u && v < m) inv[i * m + v] = (float)(1.0 / Bi[v * m + v]);
 }
 
 // ---- reductions (Section 2.1 estimator, in logs) -----------------------------------
@@ -290,6 +454,11 @@ static int ensure_copies(Factor& F, int precision, cudaStream_t st) {
   if (precision != TLRMVN_FP64 && !F.B32) {
     TLR_CHECK(dalloc(&F.B32, nb));
     k_convert<double, float><<<blocks_for(nb, 256), 256, 0, st>>>(F.B, F.B32, nb);
+    F.ldbt = ((int64_t)F.m + DIAG_VB - 1) / DIAG_VB * DIAG_VB;
+    const int64_t nt = (int64_t)F.r * F.m * F.ldbt;
+    TLR_CHECK(dalloc(&F.BT32, nt));
+    TLR_CHECK(dalloc(&F.inv32, (size_t)F.r * F.m));
+    k_transpose_tiles<<<blocks_for(nt, 256), 256, 0, st>>>(F.B, F.m, F.ldbt, nt, F.BT32, F.inv32);
   }
   if (precision == TLRMVN_FP32 && !F.U32 && nu) {
     TLR_CHECK(dalloc(&F.U32, nu));
@@ -398,12 +567,59 @@ struct Scratch {
   }
 };
 
+// Limits in factor order, in float64 and (for the float paths) float32.
+struct Lims {
+  const double* a;
+  const double* b;
+  const float* a32;
+  const float* b32;
+};
+
+// Threads per block of the sweep: as many as keep the tile's y values of the
+// block's samples within 64 KB of shared memory (at least one warp).
+template <typename T>
+static int diag_threads(int m) {
+  int bd = 256;
+  while (bd > 32 && (size_t)m * bd * sizeof(T) > 65536) bd >>= 1;
+  return bd;
+}
+
+template <typename YT, bool SM>
+static void launch_diag_f32(const Factor& F, int i, const float* Delta, int64_t ldd, const Lims& L, const float* rs32,
+                            const uint64_t* dD, int64_t c0, int64_t N, int64_t Cc, int periodize, YT* Y, int64_t ldy,
+                            double* logP, int bd, size_t smem, cudaStream_t st) {
+  DiagArgs32<YT> a;
+  a.BT = F.BT32 + (size_t)i * F.m * F.ldbt;
+  a.inv = F.inv32 + (size_t)i * F.m;
+  a.mt = (int)F.tsize(i);
+  a.ldbt = F.ldbt;
+  a.Delta = Delta;
+  a.ldd = ldd;
+  a.a = L.a32 + F.tile_off[i];
+  a.b = L.b32 + F.tile_off[i];
+  a.rs = rs32;
+  a.Q = F.Q;
+  a.D = dD;
+  a.ldD = F.n + 1;
+  a.coord0 = F.tile_off[i];
+  a.sample0 = c0;
+  a.N = N;
+  a.C = Cc;
+  a.periodize = periodize;
+  a.first = (i == 0);
+  a.Y = Y;
+  a.ldy = ldy;
+  a.logP = logP;
+  k_diag_f32<YT, SM><<<blocks_for(Cc, bd), bd, smem, st>>>(a);
+}
+
 template <typename T, typename YT>
-static int run_chunks(Factor& F, const T* Bt, const T* Ut, const T* Vt, const double* ap, const double* bp,
-                      double nu, const tlrmvn_opts& o, const uint64_t* dD, double* logP, Scratch& sc,
-                      cudaStream_t st, Prof& pf) {
+static int run_chunks(Factor& F, const T* Bt, const T* Ut, const T* Vt, const Lims& L, double nu,
+                      const tlrmvn_opts& o, const uint64_t* dD, double* logP, Scratch& sc, cudaStream_t st,
+                      Prof& pf) {
   const int64_t M = o.n_shifts, N = o.n_points, S = M * N;
   const int m = F.m;
+  const bool f32 = sizeof(T) == 4;
   int64_t C = o.sample_chunk > 0 ? o.sample_chunk : 0;
   if (C <= 0) {
     // keep W (ktot x C) within ~8 GiB
@@ -416,22 +632,25 @@ static int run_chunks(Factor& F, const T* Bt, const T* Ut, const T* Vt, const do
   T *W = nullptr, *Dl = nullptr;
   YT* Y = nullptr;
   double* rs = nullptr;
+  float* rs32 = nullptr;
   TLR_CHECK(sc.get(&W, (size_t)F.ktot * C));
   TLR_CHECK(sc.get(&Dl, (size_t)m * C));
   TLR_CHECK(sc.get(&Y, (size_t)m * C));
   const bool mvt = std::isfinite(nu);
-  if (mvt) TLR_CHECK(sc.get(&rs, (size_t)C));
+  if (mvt) TLR_CHECK(f32 ? sc.get(&rs32, (size_t)C) : sc.get(&rs, (size_t)C));
 
-  int bd = 256;
-  while (bd > 32 && (size_t)m * bd * sizeof(T) > 65536) bd >>= 1;
-  size_t smem = (size_t)m * (bd + 1) * sizeof(T);
-  TLR_CUDA(cudaFuncSetAttribute(k_diag<T, YT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int bd = diag_threads<T>(m);
+  const size_t smem = (size_t)m * (bd + 1) * sizeof(T);
+  if (f32)
+    TLR_CUDA(cudaFuncSetAttribute(k_diag_f32<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  else
+    TLR_CUDA(cudaFuncSetAttribute(k_diag<T, YT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
 
   for (int64_t c0 = 0; c0 < S; c0 += C) {
     const int64_t Cc = std::min(C, S - c0);
     if (mvt) {
       pf.begin(TLRMVN_KC_CHI);
-      k_chi_scale<<<blocks_for(Cc, 128), 128, 0, st>>>(rs, F.Q, dD, F.n + 1, F.n, c0, N, Cc, nu, o.periodize);
+      k_chi_scale<<<blocks_for(Cc, 128), 128, 0, st>>>(rs, rs32, F.Q, dD, F.n + 1, F.n, c0, N, Cc, nu, o.periodize);
       pf.end();
     }
     for (int i = 0; i < F.r; i++) {
@@ -445,29 +664,34 @@ static int run_chunks(Factor& F, const T* Bt, const T* Ut, const T* Vt, const do
         pf.end();
         Delta = Dl;
       }
-      DiagArgs<T, YT> a;
-      a.B = Bt + (size_t)i * m * m;
-      a.mt = mt;
-      a.ldb = m;
-      a.Delta = Delta;
-      a.ldd = C;
-      a.a = ap + F.tile_off[i];
-      a.b = bp + F.tile_off[i];
-      a.rs = rs;
-      a.Q = F.Q;
-      a.D = dD;
-      a.ldD = F.n + 1;
-      a.coord0 = F.tile_off[i];
-      a.sample0 = c0;
-      a.N = N;
-      a.C = Cc;
-      a.periodize = o.periodize;
-      a.first = (i == 0);
-      a.Y = Y;
-      a.ldy = C;
-      a.logP = logP;
       pf.begin(TLRMVN_KC_DIAG);
-      k_diag<T, YT, false><<<blocks_for(Cc, bd), bd, smem, st>>>(a);
+      if constexpr (sizeof(T) == 4) {
+        launch_diag_f32<float, false>(F, i, (const float*)Delta, C, L, rs32, dD, c0, N, Cc, o.periodize,
+                                      (float*)Y, C, logP, bd, smem, st);
+      } else {
+        DiagArgs<T, YT> a;
+        a.B = Bt + (size_t)i * m * m;
+        a.mt = mt;
+        a.ldb = m;
+        a.Delta = Delta;
+        a.ldd = C;
+        a.a = L.a + F.tile_off[i];
+        a.b = L.b + F.tile_off[i];
+        a.rs = rs;
+        a.Q = F.Q;
+        a.D = dD;
+        a.ldD = F.n + 1;
+        a.coord0 = F.tile_off[i];
+        a.sample0 = c0;
+        a.N = N;
+        a.C = Cc;
+        a.periodize = o.periodize;
+        a.first = (i == 0);
+        a.Y = Y;
+        a.ldy = C;
+        a.logP = logP;
+        k_diag<T, YT, false><<<blocks_for(Cc, bd), bd, smem, st>>>(a);
+      }
       pf.end();
       if (Kc > 0) {
         pf.begin(TLRMVN_KC_VPROJ);
@@ -485,8 +709,8 @@ static int run_chunks(Factor& F, const T* Bt, const T* Ut, const T* Vt, const do
 //   W16  C x kw16  bf16, sample-major: row c holds the projections of sample c
 //   Y16  C x my16  bf16, sample-major
 //   Dl   m x C     fp32, variable-major (read by the sweep)
-static int run_chunks_bf16(Factor& F, const double* ap, const double* bp, double nu, const tlrmvn_opts& o,
-                           const uint64_t* dD, double* logP, Scratch& sc, cudaStream_t st, Prof& pf) {
+static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opts& o, const uint64_t* dD,
+                           double* logP, Scratch& sc, cudaStream_t st, Prof& pf) {
   const int64_t M = o.n_shifts, N = o.n_points, S = M * N;
   const int m = F.m;
   int64_t C = o.sample_chunk > 0 ? o.sample_chunk : 0;
@@ -500,14 +724,14 @@ static int run_chunks_bf16(Factor& F, const double* ap, const double* bp, double
   C = (C + 255) / 256 * 256;
   __nv_bfloat16 *W = nullptr, *Y = nullptr;
   float* Dl = nullptr;
-  double* rs = nullptr;
+  float* rs32 = nullptr;
   int* err = nullptr;
   TLR_CHECK(sc.get(&W, (size_t)F.kw16 * C));
   TLR_CHECK(sc.get(&Y, (size_t)F.my16 * C));
   TLR_CHECK(sc.get(&Dl, (size_t)m * C));
   TLR_CHECK(sc.get(&err, 1));
   const bool mvt = std::isfinite(nu);
-  if (mvt) TLR_CHECK(sc.get(&rs, (size_t)C));
+  if (mvt) TLR_CHECK(sc.get(&rs32, (size_t)C));
   // padding columns of W and Y must hold finite values: they meet zero operand columns
   TLR_CUDA(cudaMemsetAsync(W, 0, (size_t)F.kw16 * C * 2, st));
   TLR_CUDA(cudaMemsetAsync(Y, 0, (size_t)F.my16 * C * 2, st));
@@ -525,17 +749,17 @@ static int run_chunks_bf16(Factor& F, const double* ap, const double* bp, double
   TLR_CUDA(cudaFuncSetAttribute(tc::k_gemm_tc<tc::EPI_COLMAP_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 tc::SMEM_BYTES));
 
-  int bd = 256;
-  while (bd > 32 && (size_t)m * bd * sizeof(float) > 65536) bd >>= 1;
-  size_t smem = (size_t)m * (bd + 1) * sizeof(float);
-  TLR_CUDA(cudaFuncSetAttribute(k_diag<float, __nv_bfloat16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const int bd = diag_threads<float>(m);
+  const size_t smem = (size_t)m * (bd + 1) * sizeof(float);
+  TLR_CUDA(cudaFuncSetAttribute(k_diag_f32<__nv_bfloat16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem));
 
   for (int64_t c0 = 0; c0 < S; c0 += C) {
     const int64_t Cc = std::min(C, S - c0);
     if (mvt) {
       pf.begin(TLRMVN_KC_CHI);
-      k_chi_scale<<<blocks_for(Cc, 128), 128, 0, st>>>(rs, F.Q, dD, F.n + 1, F.n, c0, N, Cc, nu, o.periodize);
+      k_chi_scale<<<blocks_for(Cc, 128), 128, 0, st>>>(nullptr, rs32, F.Q, dD, F.n + 1, F.n, c0, N, Cc, nu,
+                                                       o.periodize);
       pf.end();
     }
     const unsigned ntile = (unsigned)((Cc + tc::BN - 1) / tc::BN);
@@ -551,29 +775,9 @@ static int run_chunks_bf16(Factor& F, const double* ap, const double* bp, double
         pf.end();
         Delta = Dl;
       }
-      DiagArgs<float, __nv_bfloat16> a;
-      a.B = F.B32 + (size_t)i * m * m;
-      a.mt = mt;
-      a.ldb = m;
-      a.Delta = Delta;
-      a.ldd = C;
-      a.a = ap + F.tile_off[i];
-      a.b = bp + F.tile_off[i];
-      a.rs = rs;
-      a.Q = F.Q;
-      a.D = dD;
-      a.ldD = F.n + 1;
-      a.coord0 = F.tile_off[i];
-      a.sample0 = c0;
-      a.N = N;
-      a.C = Cc;
-      a.periodize = o.periodize;
-      a.first = (i == 0);
-      a.Y = Y;
-      a.ldy = F.my16;
-      a.logP = logP;
       pf.begin(TLRMVN_KC_DIAG);
-      k_diag<float, __nv_bfloat16, true><<<blocks_for(Cc, bd), bd, smem, st>>>(a);
+      launch_diag_f32<__nv_bfloat16, true>(F, i, Delta, C, L, rs32, dD, c0, N, Cc, o.periodize, Y, F.my16, logP, bd,
+                                           smem, st);
       pf.end();
       if (Kc > 0) {
         tc::GemmTcArgs g{(int)Kc, (int)Cc, mt, 0, (int)F.kcol_off[i], 0, 0, nullptr, 0, W, F.kw16,
@@ -598,10 +802,15 @@ static int prob_impl(Factor& F, const double* a_dev, const double* b_dev, double
   const int64_t M = o.n_shifts, N = o.n_points, S = M * N, n = F.n;
   Scratch sc(st);
   double *ap = nullptr, *bp = nullptr, *logP = nullptr, *ell = nullptr;
+  float *ap32 = nullptr, *bp32 = nullptr;
   uint64_t* dD = nullptr;
   int* bad = nullptr;
   TLR_CHECK(sc.get(&ap, n));
   TLR_CHECK(sc.get(&bp, n));
+  if (o.precision != TLRMVN_FP64) {
+    TLR_CHECK(sc.get(&ap32, n));
+    TLR_CHECK(sc.get(&bp32, n));
+  }
   TLR_CHECK(sc.get(&bad, 1));
   TLR_CHECK(sc.get(&dD, (size_t)M * (n + 1)));
   TLR_CHECK(sc.get(&ell, M));
@@ -620,7 +829,7 @@ static int prob_impl(Factor& F, const double* a_dev, const double* b_dev, double
     if (!hD.empty()) TLR_CUDA(cudaStreamSynchronize(st));
   }
   TLR_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
-  k_permute_limits<<<blocks_for(n, 256), 256, 0, st>>>(a_dev, b_dev, F.dperm, n, ap, bp, bad);
+  k_permute_limits<<<blocks_for(n, 256), 256, 0, st>>>(a_dev, b_dev, F.dperm, n, ap, bp, ap32, bp32, bad);
   int hbad = 0;
   TLR_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
   TLR_CUDA(cudaStreamSynchronize(st));
@@ -628,12 +837,13 @@ static int prob_impl(Factor& F, const double* a_dev, const double* b_dev, double
   TLR_CHECK(ensure_copies(F, o.precision, st));
   Prof pf(st);
   int s;
+  const Lims L{ap, bp, ap32, bp32};
   if (o.precision == TLRMVN_FP64)
-    s = run_chunks<double, double>(F, F.B, F.Ucat, F.Vcat, ap, bp, nu, o, dD, logP, sc, st, pf);
+    s = run_chunks<double, double>(F, F.B, F.Ucat, F.Vcat, L, nu, o, dD, logP, sc, st, pf);
   else if (o.precision == TLRMVN_FP32)
-    s = run_chunks<float, float>(F, F.B32, F.U32, F.V32, ap, bp, nu, o, dD, logP, sc, st, pf);
+    s = run_chunks<float, float>(F, F.B32, F.U32, F.V32, L, nu, o, dD, logP, sc, st, pf);
   else
-    s = run_chunks_bf16(F, ap, bp, nu, o, dD, logP, sc, st, pf);
+    s = run_chunks_bf16(F, L, nu, o, dD, logP, sc, st, pf);
   TLR_CHECK(s);
   pf.begin(TLRMVN_KC_REDUCE);
   k_shift_reduce<<<(unsigned)M, 256, 0, st>>>(logP, N, ell);

@@ -87,6 +87,8 @@ Factor::~Factor() {
   dfree(Vcat);
   dfree(vmap);
   dfree(B32);
+  dfree(BT32);
+  dfree(inv32);
   dfree(U32);
   dfree(V32);
   dfree(U16);

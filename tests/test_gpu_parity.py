@@ -173,3 +173,63 @@ def test_config1_full_size_fp64(tl):
     assert np.all(rel(pm, ref["per_sample"]) < 1e-9)
     own, _ = oracle_factor(w)
     assert np.array_equal(own.perm, OF.perm)
+
+
+@pytest.mark.parametrize("nu", [math.inf, 7.0])
+@pytest.mark.parametrize("ragged", [None, 390])
+def test_bf16_shift_path(tl, nu, ragged):
+    # bf16 tensor-core shifts: per-shift log-probability within 1e-2 relative,
+    # and the estimate within 3 QMC standard errors of the oracle's
+    m = 64 if ragged is None else 50
+    w = synth.small_workload(16, m, 39, nu=nu, n_shifts=8, n_points=512, ragged_n=ragged)
+    OF, _ = oracle_factor(w)
+    F = tl.tlrmvn_factor_import(export_bytes(OF))
+    (lp, err, ps, pm), ref = run_both(tl, F, OF, w, tl.BF16_SHIFT)
+    assert np.all(rel(ps, ref["per_shift"]) < 1e-2)
+    assert abs(lp - ref["logp"]) <= 3 * max(err, ref["err"])
+    assert np.all(np.isfinite(pm))
+
+
+def _sampled(w, k=6, seed=0):
+    rng = np.random.default_rng(seed)
+    S = w.n_shifts * w.n_points
+    return np.unique(np.concatenate([[0, S - 1], rng.integers(0, S, k)]))
+
+
+def test_full_size_mvn_n16384_sampled(tl):
+    # n = 16,384, exp + Matern kernel, m = 256, tol 1e-5, iterative block
+    # reordering, 20 x 5000; FP64 and FP32 per-sample values checked against
+    # the oracle on sampled outputs of the same factor
+    w = synth.workload(2)
+    F = tl.tlrmvn_factor_kernel(w.xy, w.kernel, w.params, w.nugget, w.a, w.b, w.m, w.tol, w.max_rank, w.reorder)
+    OF = to_oracle_factor(tl.parse_export(tl.tlrmvn_factor_export(F)))
+    sel = _sampled(w)
+    ref = sov.solve(OF, w.a, w.b, w.nu, w.shifts, w.n_points, samples=sel)["per_sample"]
+    _, _, _, pm64 = tl.tlrmvn_prob(F, w.a, w.b, w.nu, tl.FP64, w.n_shifts, w.n_points, shifts=w.shifts,
+                                   per_sample=True)
+    assert np.all(rel(pm64[sel], ref) < 1e-9)
+    lp32, err32, ps32, pm32 = tl.tlrmvn_prob(F, w.a, w.b, w.nu, tl.FP32, w.n_shifts, w.n_points, shifts=w.shifts,
+                                             per_shift=True, per_sample=True)
+    assert np.all(np.abs(pm32[sel] - ref) <= 1e-4 * np.abs(ref) + 1e-2)
+    lp64, err64, ps64, _ = tl.tlrmvn_prob(F, w.a, w.b, w.nu, tl.FP64, w.n_shifts, w.n_points, shifts=w.shifts,
+                                          per_shift=True)
+    assert np.all(rel(ps32, ps64) < 1e-4)
+
+
+def test_full_size_mvt_n65536_sampled(tl):
+    # n = 65,536 Student-t (nu = 7), m = 512, tol 1e-4, ranks <= 64, 20 x 5000:
+    # the bench's workload.  Sampled per-sample values of the FP32 and BF16-shift
+    # paths against the oracle on the same factor; per-shift BF16 within 1e-2 of FP32.
+    w = synth.workload(3)
+    F = tl.tlrmvn_factor_kernel(w.xy, w.kernel, w.params, w.nugget, w.a, w.b, w.m, w.tol, w.max_rank, w.reorder)
+    OF = to_oracle_factor(tl.parse_export(tl.tlrmvn_factor_export(F)))
+    sel = _sampled(w, k=4)
+    ref = sov.solve(OF, w.a, w.b, w.nu, w.shifts, w.n_points, samples=sel)["per_sample"]
+    lp32, err32, ps32, pm32 = tl.tlrmvn_prob(F, w.a, w.b, w.nu, tl.FP32, w.n_shifts, w.n_points, shifts=w.shifts,
+                                             per_shift=True, per_sample=True)
+    assert np.all(np.abs(pm32[sel] - ref) <= 1e-4 * np.abs(ref) + 2e-2)
+    lp16, err16, ps16, pm16 = tl.tlrmvn_prob(F, w.a, w.b, w.nu, tl.BF16_SHIFT, w.n_shifts, w.n_points,
+                                             shifts=w.shifts, per_shift=True, per_sample=True)
+    assert np.all(rel(pm16[sel], ref) < 1e-2)
+    assert np.all(rel(ps16, ps32) < 1e-2)
+    assert abs(lp16 - lp32) <= 3 * err32

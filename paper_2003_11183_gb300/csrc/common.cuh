@@ -101,7 +101,7 @@ struct Factor {
 };
 
 // Fills krow_off/kcol_off/ktot from rank and allocates Ucat/Vcat/vmap/B (not filled).
-int factor_alloc_compact(Factor& F);
+int factor_alloc_compact(Factor& F, cudaStream_t st);
 // Host tables: lattice generators Q_i = floor(frac(sqrt(p_i)) 2^64) for the first d primes.
 std::vector<uint64_t> richtmyer_generators(int64_t d);
 // Uploads Q and perm, called once the factor is complete.

@@ -893,7 +893,7 @@ static int factor_build(const CovSrc& src, int64_t n, std::vector<int64_t> geo, 
   F.rank = std::vector<int32_t>(rank.begin(), rank.end());
   TLR_CUDA(cudaMemcpyAsync(&F.capped, d_capped, sizeof(int), cudaMemcpyDeviceToHost, st));
   TLR_CUDA(cudaStreamSynchronize(st));
-  TLR_CHECK(factor_alloc_compact(F));
+  TLR_CHECK(factor_alloc_compact(F, st));
   for (int j = 0; j < r; j++)
     TLR_CUDA(cudaMemcpyAsync(F.B + (size_t)j * m * m, diagS + (size_t)pos2blk[j] * m * m, (size_t)m * m * 8,
                              cudaMemcpyDeviceToDevice, st));

@@ -98,7 +98,7 @@ Factor::~Factor() {
   dfree(dperm);
 }
 
-int factor_alloc_compact(Factor& F) {
+int factor_alloc_compact(Factor& F, cudaStream_t st) {
   const int r = F.r;
   F.krow_off.assign(r + 1, 0);
   F.kcol_off.assign(r + 1, 0);
@@ -117,12 +117,12 @@ int factor_alloc_compact(Factor& F) {
   TLR_CHECK(dalloc(&F.Ucat, (size_t)F.m * F.ktot));
   TLR_CHECK(dalloc(&F.Vcat, (size_t)F.m * F.ktot));
   TLR_CHECK(dalloc(&F.vmap, (size_t)F.ktot));
-  // zero padding rows / columns of short tiles
+  // zero padding rows / columns of short tiles; ordered on the stream that fills them
   if (F.ktot) {
-    TLR_CUDA(cudaMemset(F.Ucat, 0, (size_t)F.m * F.ktot * 8));
-    TLR_CUDA(cudaMemset(F.Vcat, 0, (size_t)F.m * F.ktot * 8));
+    TLR_CUDA(cudaMemsetAsync(F.Ucat, 0, (size_t)F.m * F.ktot * 8, st));
+    TLR_CUDA(cudaMemsetAsync(F.Vcat, 0, (size_t)F.m * F.ktot * 8, st));
   }
-  TLR_CUDA(cudaMemset(F.B, 0, (size_t)r * F.m * F.m * 8));
+  TLR_CUDA(cudaMemsetAsync(F.B, 0, (size_t)r * F.m * F.m * 8, st));
   return TLRMVN_OK;
 }
 
@@ -322,7 +322,7 @@ namespace tlrmvn {
 int factor_upload_pairs(Factor& F, const double* Bh, const std::vector<const double*>& Up,
                         const std::vector<const double*>& Vp, cudaStream_t st) {
   const int r = F.r, m = F.m;
-  TLR_CHECK(factor_alloc_compact(F));
+  TLR_CHECK(factor_alloc_compact(F, st));
   std::vector<double> Uc((size_t)m * F.ktot, 0.0), Vc((size_t)m * F.ktot, 0.0);
   std::vector<int32_t> vm(F.ktot);
   for (int i = 0; i < r; i++) {

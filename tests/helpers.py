@@ -41,3 +41,31 @@ def gpu_available() -> bool:
         return torch.cuda.is_available()
     except Exception:
         return False
+
+
+def factor_row(F: ofactor.TLRFactor, t: int) -> np.ndarray:
+    """Row t (factor position) of the dense TLR factor L, without assembling L."""
+    o = F.tile_off
+    i = int(np.searchsorted(o, t, side="right") - 1)
+    row = np.zeros(F.n)
+    v = t - o[i]
+    row[o[i]:o[i] + v + 1] = F.B[i][v, :v + 1]
+    for j in range(i):
+        U, V = F.U[(i, j)], F.V[(i, j)]
+        if U.shape[1]:
+            row[o[j]:o[j + 1]] = V @ U[v]
+    return row
+
+
+def sampled_reconstruction_error(F: ofactor.TLRFactor, xy, kernel, params, nugget, pairs) -> float:
+    """max |(L L^T)[s, t] - Sigma[perm[s], perm[t]]| over the given position pairs."""
+    rows = {}
+    worst = 0.0
+    for s, t in pairs:
+        for q in (s, t):
+            if q not in rows:
+                rows[q] = factor_row(F, q)
+        got = rows[s] @ rows[t]
+        want = geometry.covariance(xy, kernel, params, nugget, rows=[F.perm[s]], cols=[F.perm[t]])[0, 0]
+        worst = max(worst, abs(got - want))
+    return worst

@@ -13,7 +13,7 @@ import pytest
 
 import synth
 from oracle import sov
-from tests.helpers import to_oracle_factor, oracle_factor, export_bytes
+from tests.helpers import to_oracle_factor, oracle_factor, export_bytes, sampled_reconstruction_error
 
 pytestmark = pytest.mark.gpu
 
@@ -168,6 +168,7 @@ def test_config1_full_size_fp64(tl):
     w = synth.workload(1)
     F = tl.tlrmvn_factor_kernel(w.xy, w.kernel, w.params, w.nugget, w.a, w.b, w.m, w.tol, w.max_rank, w.reorder)
     OF = to_oracle_factor(tl.parse_export(tl.tlrmvn_factor_export(F)))
+    _check_factor(OF, w)
     (lp, err, ps, pm), ref = run_both(tl, F, OF, w, tl.FP64)
     assert np.all(rel(ps, ref["per_shift"]) < 1e-9)
     assert np.all(rel(pm, ref["per_sample"]) < 1e-9)
@@ -190,6 +191,16 @@ def test_bf16_shift_path(tl, nu, ragged):
     assert np.all(np.isfinite(pm))
 
 
+def _check_factor(OF, w, n_pairs=24, tol_mult=50):
+    # every diagonal entry positive and sampled entries of L L^T equal to Sigma
+    assert all(np.all(np.diag(Bt) > 0) for Bt in OF.B)
+    rng = np.random.default_rng(1)
+    pairs = [(int(a), int(b)) for a, b in rng.integers(0, w.n, (n_pairs, 2))]
+    pairs += [(t, t) for t in rng.integers(0, w.n, 4).tolist()]
+    err = sampled_reconstruction_error(OF, w.xy, w.kernel, w.params, w.nugget, pairs)
+    assert err < tol_mult * w.tol, err
+
+
 def _sampled(w, k=6, seed=0):
     rng = np.random.default_rng(seed)
     S = w.n_shifts * w.n_points
@@ -203,6 +214,7 @@ def test_full_size_mvn_n16384_sampled(tl):
     w = synth.workload(2)
     F = tl.tlrmvn_factor_kernel(w.xy, w.kernel, w.params, w.nugget, w.a, w.b, w.m, w.tol, w.max_rank, w.reorder)
     OF = to_oracle_factor(tl.parse_export(tl.tlrmvn_factor_export(F)))
+    _check_factor(OF, w)
     sel = _sampled(w)
     ref = sov.solve(OF, w.a, w.b, w.nu, w.shifts, w.n_points, samples=sel)["per_sample"]
     _, _, _, pm64 = tl.tlrmvn_prob(F, w.a, w.b, w.nu, tl.FP64, w.n_shifts, w.n_points, shifts=w.shifts,
@@ -223,6 +235,7 @@ def test_full_size_mvt_n65536_sampled(tl):
     w = synth.workload(3)
     F = tl.tlrmvn_factor_kernel(w.xy, w.kernel, w.params, w.nugget, w.a, w.b, w.m, w.tol, w.max_rank, w.reorder)
     OF = to_oracle_factor(tl.parse_export(tl.tlrmvn_factor_export(F)))
+    _check_factor(OF, w)
     sel = _sampled(w, k=4)
     ref = sov.solve(OF, w.a, w.b, w.nu, w.shifts, w.n_points, samples=sel)["per_sample"]
     lp32, err32, ps32, pm32 = tl.tlrmvn_prob(F, w.a, w.b, w.nu, tl.FP32, w.n_shifts, w.n_points, shifts=w.shifts,

@@ -149,6 +149,30 @@ int tlrmvn_prob_device(tlrmvn_factor_t f, const double* a, const double* b, doub
                        const tlrmvn_opts* opts, double* logp, double* err, double* per_shift,
                        double* per_sample);
 
+/* ---- estimator without device allocation ------------------------------ */
+
+/* The paper has no counterpart: this is a service for callers that cannot
+ * allocate device memory - a serving loop that reserved its memory up front and
+ * must not take the device-wide synchronisation of cudaMalloc/cudaFree, or an
+ * application whose device memory belongs to another allocator.
+ *
+ * Computes the same estimate as tlrmvn_prob from per-sample log integrand
+ * values (the per_sample output of tlrmvn_prob / tlrmvn_prob_device):
+ *   per_sample  device, n_shifts * n_points doubles, shift-major
+ *   out         device, 2 doubles: log p_hat, err (as tlrmvn_prob's logp / err)
+ *   per_shift   device, n_shifts doubles, or NULL
+ *   stream      cudaStream_t or NULL (library stream); returns after completion.
+ * It allocates nothing: its scratch (one double per shift) is a fixed array in
+ * the library, TLRMVN_NOALLOC_MAX_SHIFTS doubles, held by every GPU that loads
+ * the library until the process exits.  n_shifts above that limit returns
+ * TLRMVN_E_INVAL.  The first call on a device looks up the array's device
+ * address; make that first call before any stream capture.  All calls share
+ * the array: calls whose work overlaps on the GPU (different streams, or other
+ * threads) race on it and must be serialised by the caller. */
+#define TLRMVN_NOALLOC_MAX_SHIFTS 65536
+int tlrmvn_estimate_noalloc(const double* per_sample, int n_shifts, int64_t n_points, double* out,
+                            double* per_shift, void* stream);
+
 /* ---- diagnostics ------------------------------------------------------ */
 const char* tlrmvn_strerror(int status);
 const char* tlrmvn_last_error(void);   /* thread-local detail of the last failure, "" if none */

@@ -35,6 +35,7 @@ SIGNATURES = {
                               c_double_p, c_double_p]),
     "tlrmvn_prob_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.POINTER(Opts), C.c_void_p,
                                      C.c_void_p, C.c_void_p, C.c_void_p]),
+    "tlrmvn_estimate_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tlrmvn_profile_enable": (C.c_int, [C.c_int]),
     "tlrmvn_profile_reset": (C.c_int, []),
     "tlrmvn_profile_get": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),

@@ -123,6 +123,20 @@ def tlrmvn_factor_import(buf: bytes) -> Factor:
     return Factor(out.value)
 
 
+NOALLOC_MAX_SHIFTS = 65536
+
+
+def tlrmvn_estimate_noalloc(per_sample, n_shifts: int, n_points: int, out, per_shift=None, stream=None):
+    """Estimator from device per-sample logs without any device allocation.
+
+    per_sample: float64 CUDA tensor (n_shifts * n_points); out: float64 CUDA
+    tensor of 2 elements receiving (log p_hat, err); per_shift: optional tensor.
+    """
+    _check(L.load().tlrmvn_estimate_noalloc(per_sample.data_ptr(), int(n_shifts), int(n_points), out.data_ptr(),
+                                            None if per_shift is None else per_shift.data_ptr(),
+                                            _stream_ptr(stream)), "tlrmvn_estimate_noalloc")
+
+
 KC_SHIFT, KC_DIAG, KC_VPROJ, KC_CHI, KC_REDUCE = 0, 1, 2, 3, 4
 KC_NAMES = ("shift", "diag", "vproj", "chi", "reduce")
 

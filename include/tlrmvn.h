@@ -149,6 +149,32 @@ int tlrmvn_prob_device(tlrmvn_factor_t f, const double* a, const double* b, doub
                        const tlrmvn_opts* opts, double* logp, double* err, double* per_shift,
                        double* per_sample);
 
+/* ---- many problems in one launch -------------------------------------- */
+
+/* A batch plan: `count` problems (each its own factor, tile size <= 128, and
+ * its own nu; INFINITY for MVN) solved together by one persistent kernel whose
+ * blocks take (problem, 128-sample chunk) work items from a device counter,
+ * largest problems first; each item runs Algorithm 6/7 for its chunk over all
+ * tiles of its problem.  The launch sequence (limit permutation, persistent
+ * integrand, estimator) is captured once in a CUDA graph; tlrmvn_batch_run
+ * replays it for new limits.  Needed by likelihood fitting, where the same
+ * covariances meet new limits at every step (Section 5 of the paper).
+ *   opts: precision must be TLRMVN_FP32; opts->shifts must be NULL: problem p
+ *         draws its shifts from seed opts->seed + p exactly as tlrmvn_prob does
+ *         with that seed; n_shifts / n_points / periodize apply to all problems.
+ *   factors, nu: host arrays of length count; the factors must outlive the plan.
+ * tlrmvn_batch_run: a[p], b[p] host arrays of the problem's length (original
+ * order); logp / err host arrays of length count. */
+typedef struct tlrmvn_batch_s* tlrmvn_batch_t;
+int tlrmvn_batch_create(int count, const tlrmvn_factor_t* factors, const double* nu, const tlrmvn_opts* opts,
+                        tlrmvn_batch_t* out);
+int tlrmvn_batch_run(tlrmvn_batch_t plan, const double* const* a, const double* const* b, double* logp,
+                     double* err);
+int tlrmvn_batch_free(tlrmvn_batch_t plan);
+/* create + run + free in one call */
+int tlrmvn_prob_batch(int count, const tlrmvn_factor_t* factors, const double* const* a, const double* const* b,
+                      const double* nu, const tlrmvn_opts* opts, double* logp, double* err);
+
 /* ---- estimator without device allocation ------------------------------ */
 
 /* The paper has no counterpart: this is a service for callers that cannot

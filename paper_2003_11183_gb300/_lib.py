@@ -35,6 +35,12 @@ SIGNATURES = {
                               c_double_p, c_double_p]),
     "tlrmvn_prob_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.POINTER(Opts), C.c_void_p,
                                      C.c_void_p, C.c_void_p, C.c_void_p]),
+    "tlrmvn_batch_create": (C.c_int, [C.c_int, C.POINTER(C.c_void_p), c_double_p, C.POINTER(Opts),
+                                      C.POINTER(C.c_void_p)]),
+    "tlrmvn_batch_run": (C.c_int, [C.c_void_p, C.POINTER(c_double_p), C.POINTER(c_double_p), c_double_p, c_double_p]),
+    "tlrmvn_batch_free": (C.c_int, [C.c_void_p]),
+    "tlrmvn_prob_batch": (C.c_int, [C.c_int, C.POINTER(C.c_void_p), C.POINTER(c_double_p), C.POINTER(c_double_p),
+                                    c_double_p, C.POINTER(Opts), c_double_p, c_double_p]),
     "tlrmvn_estimate_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tlrmvn_profile_enable": (C.c_int, [C.c_int]),
     "tlrmvn_profile_reset": (C.c_int, []),

@@ -123,6 +123,56 @@ def tlrmvn_factor_import(buf: bytes) -> Factor:
     return Factor(out.value)
 
 
+class BatchPlan:
+    """tlrmvn_batch_t: many factors solved by one persistent launch (replayed CUDA graph)."""
+
+    def __init__(self, factors, nu, n_shifts: int, n_points: int, seed: int = 0, periodize: bool = True):
+        lib = L.load()
+        self.factors = list(factors)  # keep the handles alive
+        self.sizes = [tlrmvn_factor_info(f)["n"] for f in self.factors]
+        count = len(self.factors)
+        hs = (C.c_void_p * count)(*[f.handle.value for f in self.factors])
+        nus = _f64(nu if np.ndim(nu) else [nu] * count)
+        o, _ = _opts(FP32, n_shifts, n_points, periodize, None, seed, 0, None, 0)
+        out = C.c_void_p()
+        _check(lib.tlrmvn_batch_create(count, hs, _dp(nus), C.byref(o), C.byref(out)), "tlrmvn_batch_create")
+        self.handle = out
+        self.count = count
+
+    def run(self, a_list, b_list):
+        """Returns (logp, err) arrays of length count."""
+        lib = L.load()
+        a_arr = [_f64(a) for a in a_list]
+        b_arr = [_f64(b) for b in b_list]
+        pa = (L.c_double_p * self.count)(*[_dp(x) for x in a_arr])
+        pb = (L.c_double_p * self.count)(*[_dp(x) for x in b_arr])
+        lp = np.empty(self.count)
+        er = np.empty(self.count)
+        _check(lib.tlrmvn_batch_run(self.handle, pa, pb, _dp(lp), _dp(er)), "tlrmvn_batch_run")
+        return lp, er
+
+    def close(self):
+        if self.handle and self.handle.value:
+            L.load().tlrmvn_batch_free(self.handle)
+            self.handle = C.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tlrmvn_prob_batch(factors, a_list, b_list, nu, n_shifts: int, n_points: int, seed: int = 0,
+                      periodize: bool = True):
+    """One-shot batched solve: (logp, err) arrays."""
+    plan = BatchPlan(factors, nu, n_shifts, n_points, seed, periodize)
+    try:
+        return plan.run(a_list, b_list)
+    finally:
+        plan.close()
+
+
 NOALLOC_MAX_SHIFTS = 65536
 
 

@@ -1,0 +1,478 @@
+// Many MVN/MVT problems of uneven dimension in one persistent launch.
+//
+// A work item is (problem, chunk of up to 128 samples).  Persistent CTAs take
+// items from an atomic counter, largest problems first, and run the whole TLR
+// integrand of Algorithms 6/7 for their chunk: for every diagonal tile, the
+// low-rank limit shift sum_{j<i} U_ij (V_ij^T y_j) (from the chunk's projections
+// W, kept in a CTA-private global buffer), the float32 SOV sweep of eq. (2),
+// then the projections V_col,i^T y_i of the tile for the later tiles.  Items
+// never wait on one another, so the kernel has no inter-CTA spin.  A plan
+// captures the launch sequence (limit permutation, persistent kernel,
+// estimator) in a CUDA graph, replayed for every new set of limits.
+#include "common.cuh"
+#include "sov_device.cuh"
+
+#include <algorithm>
+#include <numeric>
+
+namespace tlrmvn {
+
+__global__ void k_shift_reduce(const double* logP, int64_t N, double* ell);
+__global__ void k_final(const double* ell, int M, double* out);
+
+constexpr int BATCH_T = 128;     // samples per work item = threads per CTA
+constexpr int BATCH_MMAX = 128;  // largest tile size of a batched problem
+constexpr int BATCH_VB = 16;     // variables per register block
+
+struct BatchProblem {
+  int n, r, m, n_shifts;
+  int64_t n_points, ldbt, ktot, logp_off;
+  double nu;
+  int periodize;
+  const int64_t* tile_off;
+  const int64_t* krow_off;
+  const int64_t* kcol_off;
+  const int64_t* vt_off;
+  const int32_t* kcpad;
+  const float* BT;
+  const float* inv;
+  const float* UT;  // UT[(krow_off[i] + k) * ldbt + v] = Ucat_i[v][k]
+  const float* VT;  // VT[vt_off[j] + u * kcpad[j] + k] = Vcat_j[k][u]
+  const int32_t* vmap;
+  const uint64_t* Q;
+  const uint64_t* D;
+  const float* a;
+  const float* b;
+};
+struct BatchItem {
+  int prob, count;
+  int64_t sample0;
+};
+
+__device__ __forceinline__ void fma16(float* acc, const float* row, float x) {
+  const float4* r4 = reinterpret_cast<const float4*>(row);
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    const float4 v = __ldg(r4 + q);
+    acc[4 * q] = fmaf(v.x, x, acc[4 * q]);
+    acc[4 * q + 1] = fmaf(v.y, x, acc[4 * q + 1]);
+    acc[4 * q + 2] = fmaf(v.z, x, acc[4 * q + 2]);
+    acc[4 * q + 3] = fmaf(v.w, x, acc[4 * q + 3]);
+  }
+}
+
+__global__ void __launch_bounds__(BATCH_T) k_batch(const BatchProblem* __restrict__ probs,
+                                                   const BatchItem* __restrict__ items, int n_items, int* next,
+                                                   float* Wbase, int64_t wstride, double* logP) {
+  extern __shared__ __align__(16) float ys[];  // [BATCH_MMAX][BATCH_T + 1]
+  __shared__ int cur;
+  const int tid = threadIdx.x, ld = BATCH_T + 1;
+  float* W = Wbase + (int64_t)blockIdx.x * wstride;  // [ktot][BATCH_T]
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) cur = atomicAdd(next, 1);
+    __syncthreads();
+    const int it = cur;
+    if (it >= n_items) break;
+    const BatchItem item = items[it];
+    if (tid >= item.count) continue;
+    const BatchProblem& P = probs[item.prob];
+    const int64_t g = item.sample0 + tid;
+    const int64_t s = g / P.n_points;
+    const uint64_t k = (uint64_t)(g - s * P.n_points) + 1;
+    const uint64_t* Ds = P.D + s * (int64_t)(P.n + 1);
+    float rs = 1.0f;
+    if (isfinite(P.nu)) {
+      double w, wc;
+      lattice_w(k * P.Q[P.n] + Ds[P.n], P.periodize, w, wc);
+      rs = (float)sqrt(2.0 * gamma_p_inv(0.5 * P.nu, w, wc) / P.nu);
+    }
+    float lp = 0.0f;
+    for (int i = 0; i < P.r; i++) {
+      const int64_t t0 = P.tile_off[i];
+      const int mt = (int)(P.tile_off[i + 1] - t0);
+      const int64_t kr0 = P.krow_off[i], Kr = P.krow_off[i + 1] - kr0;
+      const float* BTi = P.BT + (int64_t)i * P.m * P.ldbt;
+      const float* invi = P.inv + (int64_t)i * P.m;
+      for (int v0 = 0; v0 < mt; v0 += BATCH_VB) {
+        float acc[BATCH_VB];
+#pragma unroll
+        for (int j = 0; j < BATCH_VB; j++) acc[j] = 0.0f;
+        for (int64_t kk = 0; kk < Kr; kk++)  // low-rank shift of the limits
+          fma16(acc, P.UT + (kr0 + kk) * P.ldbt + v0, W[(kr0 + kk) * BATCH_T + tid]);
+        for (int u = 0; u < v0; u++)  // earlier variables of the tile
+          fma16(acc, BTi + (int64_t)u * P.ldbt + v0, ys[u * ld + tid]);
+        float yb[BATCH_VB];
+#pragma unroll
+        for (int j = 0; j < BATCH_VB; j++) {
+          const int v = v0 + j;
+          yb[j] = 0.0f;
+          if (v < mt) {
+            float sum = acc[j];
+#pragma unroll
+            for (int jj = 0; jj < j; jj++) sum = fmaf(__ldg(BTi + (int64_t)(v0 + jj) * P.ldbt + v), yb[jj], sum);
+            const float iv = __ldg(invi + v);
+            const float at = (P.a[t0 + v] * rs - sum) * iv;
+            const float bt = (P.b[t0 + v] * rs - sum) * iv;
+            float w, wc;
+            lattice_wf(k * P.Q[t0 + v] + Ds[t0 + v], P.periodize, w, wc);
+            float lv, y;
+            sov_step_f32(at, bt, w, wc, lv, y);
+            lp += lv;
+            yb[j] = y;
+            ys[v * ld + tid] = y;
+          }
+        }
+      }
+      const int64_t kc0 = P.kcol_off[i], Kc = P.kcol_off[i + 1] - kc0;
+      if (Kc > 0) {  // projections of this tile for the later tiles
+        const float* VTi = P.VT + P.vt_off[i];
+        const int kcp = P.kcpad[i];
+        const int32_t* vm = P.vmap + kc0;
+        for (int64_t q0 = 0; q0 < Kc; q0 += BATCH_VB) {
+          float acc[BATCH_VB];
+#pragma unroll
+          for (int j = 0; j < BATCH_VB; j++) acc[j] = 0.0f;
+          for (int u = 0; u < mt; u++) fma16(acc, VTi + (int64_t)u * kcp + q0, ys[u * ld + tid]);
+#pragma unroll
+          for (int j = 0; j < BATCH_VB; j++)
+            if (q0 + j < Kc) W[(int64_t)vm[q0 + j] * BATCH_T + tid] = acc[j];
+        }
+      }
+    }
+    logP[P.logp_off + g] = (double)lp;
+  }
+}
+
+// limits of all problems: original order (staged) -> factor order, float; validation
+__global__ void k_permute_batch(const double* a, const double* b, const int64_t* perm_g, int64_t total, float* a32,
+                                float* b32, int* bad) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  const int64_t src = perm_g[t];  // global index into the staged limits
+  const double av = a[src], bv = b[src];
+  if (isnan(av) || isnan(bv) || av > bv || av == INFINITY || bv == -INFINITY) atomicExch(bad, 1);
+  a32[t] = (float)av;
+  b32[t] = (float)bv;
+}
+
+// UT row g (global rank index) = column g - krow_off[i] of Ucat_i, padded to ldbt
+__global__ void k_make_ut(const double* Ucat, const int32_t* ktile, const int64_t* krow_off, int m, int64_t ldbt,
+                          int64_t count, float* UT) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  const int64_t g = t / ldbt, v = t % ldbt;
+  const int i = ktile[g];
+  const int64_t Kr = krow_off[i + 1] - krow_off[i];
+  UT[t] = (v < m) ? (float)Ucat[(int64_t)m * krow_off[i] + v * Kr + (g - krow_off[i])] : 0.0f;
+}
+// VT block of column tile j: VT[u * kcp + k] = Vcat_j[k][u], zero for k >= Kc
+__global__ void k_make_vt(const double* Vcat_j, int m, int64_t Kc, int kcp, float* VT) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)m * kcp) return;
+  const int64_t u = t / kcp, kk = t % kcp;
+  VT[t] = (kk < Kc) ? (float)Vcat_j[kk * m + u] : 0.0f;
+}
+
+// per-problem estimates: block p reduces the shifts of problem p
+__global__ void k_final_batch(const double* ell, int M, double* out);
+
+static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// The float copies used by the batched kernel, made once per factor.
+struct BatchCopies {
+  float* UT = nullptr;
+  float* VT = nullptr;
+  int64_t *tile_off = nullptr, *krow_off = nullptr, *kcol_off = nullptr, *vt_off = nullptr;
+  int32_t* kcpad = nullptr;
+  ~BatchCopies() {
+    dfree(UT);
+    dfree(VT);
+    dfree(tile_off);
+    dfree(krow_off);
+    dfree(kcol_off);
+    dfree(vt_off);
+    dfree(kcpad);
+  }
+};
+
+int ensure_float_tiles(Factor& F, cudaStream_t st);  // prob.cu: BT32 / inv32
+
+static int make_batch_copies(Factor& F, BatchCopies& C, cudaStream_t st) {
+  const int r = F.r, m = F.m;
+  TLR_CHECK(ensure_float_tiles(F, st));
+  std::vector<int64_t> vt_off(r + 1, 0);
+  std::vector<int32_t> kcpad(r);
+  for (int j = 0; j < r; j++) {
+    kcpad[j] = (int32_t)((F.kcol(j) + 15) / 16 * 16);
+    vt_off[j + 1] = vt_off[j] + (int64_t)m * kcpad[j];
+  }
+  TLR_CHECK(dalloc(&C.tile_off, r + 1));
+  TLR_CHECK(dalloc(&C.krow_off, r + 1));
+  TLR_CHECK(dalloc(&C.kcol_off, r + 1));
+  TLR_CHECK(dalloc(&C.vt_off, r + 1));
+  TLR_CHECK(dalloc(&C.kcpad, r));
+  TLR_CUDA(cudaMemcpyAsync(C.tile_off, F.tile_off.data(), (r + 1) * 8, cudaMemcpyHostToDevice, st));
+  TLR_CUDA(cudaMemcpyAsync(C.krow_off, F.krow_off.data(), (r + 1) * 8, cudaMemcpyHostToDevice, st));
+  TLR_CUDA(cudaMemcpyAsync(C.kcol_off, F.kcol_off.data(), (r + 1) * 8, cudaMemcpyHostToDevice, st));
+  TLR_CUDA(cudaMemcpyAsync(C.vt_off, vt_off.data(), (r + 1) * 8, cudaMemcpyHostToDevice, st));
+  TLR_CUDA(cudaMemcpyAsync(C.kcpad, kcpad.data(), r * 4, cudaMemcpyHostToDevice, st));
+  if (F.ktot) {
+    std::vector<int32_t> ktile(F.ktot);
+    for (int i = 0; i < r; i++)
+      for (int64_t g = F.krow_off[i]; g < F.krow_off[i + 1]; g++) ktile[g] = i;
+    int32_t* dkt = nullptr;
+    TLR_CHECK(dalloc(&dkt, (size_t)F.ktot));
+    TLR_CUDA(cudaMemcpyAsync(dkt, ktile.data(), ktile.size() * 4, cudaMemcpyHostToDevice, st));
+    const int64_t nut = F.ktot * F.ldbt;
+    TLR_CHECK(dalloc(&C.UT, (size_t)nut));
+    k_make_ut<<<nblk(nut, 256), 256, 0, st>>>(F.Ucat, dkt, C.krow_off, m, F.ldbt, nut, C.UT);
+    TLR_CHECK(dalloc(&C.VT, (size_t)std::max<int64_t>(vt_off[r], 1)));
+    for (int j = 0; j < r; j++)
+      if (F.kcol(j))
+        k_make_vt<<<nblk((int64_t)m * kcpad[j], 256), 256, 0, st>>>(F.Vcat + (size_t)m * F.kcol_off[j], m, F.kcol(j),
+                                                                      kcpad[j], C.VT + vt_off[j]);
+    TLR_CUDA(cudaStreamSynchronize(st));
+    dfree(dkt);
+  }
+  TLR_CUDA(cudaGetLastError());
+  return TLRMVN_OK;
+}
+
+struct Batch {
+  int count = 0, M = 0, device = 0;
+  int64_t N = 0, total_n = 0, total_samples = 0, ktot_max = 0;
+  int periodize = 1;
+  cudaStream_t st = nullptr;
+  std::vector<Factor*> F;
+  std::vector<int64_t> n_off;  // limits offsets of each problem (host)
+  std::vector<BatchCopies> copies;
+  BatchProblem* dprobs = nullptr;
+  BatchItem* ditems = nullptr;
+  int n_items = 0, grid = 0;
+  int* dnext = nullptr;
+  int* dbad = nullptr;
+  float* W = nullptr;
+  double *logP = nullptr, *ell = nullptr, *out = nullptr, *a_st = nullptr, *b_st = nullptr;
+  float *a32 = nullptr, *b32 = nullptr;
+  int64_t* perm_g = nullptr;
+  uint64_t* D = nullptr;
+  double* h_ab = nullptr;   // pinned staging of the limits
+  double* h_out = nullptr;  // pinned results
+  cudaGraphExec_t exec = nullptr;
+  ~Batch() {
+    if (exec) cudaGraphExecDestroy(exec);
+    dfree(dprobs);
+    dfree(ditems);
+    dfree(dnext);
+    dfree(dbad);
+    dfree(W);
+    dfree(logP);
+    dfree(ell);
+    dfree(out);
+    dfree(a_st);
+    dfree(b_st);
+    dfree(a32);
+    dfree(b32);
+    dfree(perm_g);
+    dfree(D);
+    if (h_ab) cudaFreeHost(h_ab);
+    if (h_out) cudaFreeHost(h_out);
+    if (st) cudaStreamDestroy(st);
+  }
+};
+
+uint64_t splitmix64_seed_at(uint64_t seed, uint64_t t);  // prob.cu
+
+static int batch_build(Batch& B, int count, const tlrmvn_factor_t* factors, const double* nu,
+                       const tlrmvn_opts& o) {
+  B.count = count;
+  B.M = o.n_shifts;
+  B.N = o.n_points;
+  B.periodize = o.periodize;
+  TLR_CUDA(cudaGetDevice(&B.device));
+  TLR_CUDA(cudaStreamCreateWithFlags(&B.st, cudaStreamNonBlocking));
+  cudaStream_t st = B.st;
+  B.F.resize(count);
+  B.copies.resize(count);
+  B.n_off.assign(count + 1, 0);
+  for (int p = 0; p < count; p++) {
+    Factor* F = reinterpret_cast<Factor*>(factors[p]);
+    if (!F) return fail(TLRMVN_E_INVAL, "null factor in batch");
+    if (F->m > BATCH_MMAX) return fail(TLRMVN_E_NOTSUP, "batched problems need tile size <= 128");
+    if (!(nu[p] > 0.0)) return fail(TLRMVN_E_INVAL, "nu must be > 0");
+    B.F[p] = F;
+    B.n_off[p + 1] = B.n_off[p] + F->n;
+    B.ktot_max = std::max(B.ktot_max, F->ktot);
+    TLR_CHECK(make_batch_copies(*F, B.copies[p], st));
+  }
+  B.total_n = B.n_off[count];
+  const int64_t S = (int64_t)B.M * B.N;
+  B.total_samples = S * count;
+  // device tables
+  std::vector<BatchProblem> probs(count);
+  std::vector<int64_t> perm_g(B.total_n);
+  std::vector<int64_t> d_off(count + 1, 0);
+  for (int p = 0; p < count; p++) d_off[p + 1] = d_off[p] + (int64_t)B.M * (B.F[p]->n + 1);
+  TLR_CHECK(dalloc(&B.D, (size_t)d_off[count]));
+  TLR_CHECK(dalloc(&B.a32, (size_t)B.total_n));
+  TLR_CHECK(dalloc(&B.b32, (size_t)B.total_n));
+  {
+    std::vector<uint64_t> hD((size_t)d_off[count]);
+    for (int p = 0; p < count; p++) {
+      const Factor& F = *B.F[p];
+      for (int64_t t = 0; t < (int64_t)B.M * (F.n + 1); t++) hD[d_off[p] + t] = splitmix64_seed_at(o.seed + p, t);
+      for (int64_t t = 0; t < F.n; t++) perm_g[B.n_off[p] + t] = B.n_off[p] + F.perm[t];
+      const BatchCopies& C = B.copies[p];
+      BatchProblem& P = probs[p];
+      P.n = (int)F.n;
+      P.r = F.r;
+      P.m = F.m;
+      P.n_shifts = B.M;
+      P.n_points = B.N;
+      P.ldbt = F.ldbt;
+      P.ktot = F.ktot;
+      P.logp_off = S * p;
+      P.nu = nu[p];
+      P.periodize = B.periodize;
+      P.tile_off = C.tile_off;
+      P.krow_off = C.krow_off;
+      P.kcol_off = C.kcol_off;
+      P.vt_off = C.vt_off;
+      P.kcpad = C.kcpad;
+      P.BT = F.BT32;
+      P.inv = F.inv32;
+      P.UT = C.UT;
+      P.VT = C.VT;
+      P.vmap = F.vmap;
+      P.Q = F.Q;
+      P.D = B.D + d_off[p];
+      P.a = B.a32 + B.n_off[p];
+      P.b = B.b32 + B.n_off[p];
+    }
+    TLR_CUDA(cudaMemcpyAsync(B.D, hD.data(), hD.size() * 8, cudaMemcpyHostToDevice, st));
+    TLR_CUDA(cudaStreamSynchronize(st));
+  }
+  // work items, largest problems first
+  std::vector<int> order(count);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return B.F[x]->n > B.F[y]->n; });
+  std::vector<BatchItem> items;
+  for (int p : order)
+    for (int64_t c0 = 0; c0 < S; c0 += BATCH_T) items.push_back(BatchItem{p, (int)std::min<int64_t>(BATCH_T, S - c0), c0});
+  B.n_items = (int)items.size();
+  TLR_CHECK(dalloc(&B.dprobs, count));
+  TLR_CHECK(dalloc(&B.ditems, items.size()));
+  TLR_CHECK(dalloc(&B.perm_g, (size_t)B.total_n));
+  TLR_CUDA(cudaMemcpyAsync(B.dprobs, probs.data(), probs.size() * sizeof(BatchProblem), cudaMemcpyHostToDevice, st));
+  TLR_CUDA(cudaMemcpyAsync(B.ditems, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice, st));
+  TLR_CUDA(cudaMemcpyAsync(B.perm_g, perm_g.data(), perm_g.size() * 8, cudaMemcpyHostToDevice, st));
+  // persistent grid and its private projection buffers
+  const size_t smem = (size_t)BATCH_MMAX * (BATCH_T + 1) * sizeof(float);
+  TLR_CUDA(cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0, sms = 0;
+  TLR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, BATCH_T, smem));
+  TLR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, B.device));
+  B.grid = std::max(1, std::min(per_sm * sms, B.n_items));
+  TLR_CHECK(dalloc(&B.W, (size_t)B.grid * std::max<int64_t>(B.ktot_max, 1) * BATCH_T));
+  TLR_CHECK(dalloc(&B.dnext, 1));
+  TLR_CHECK(dalloc(&B.dbad, 1));
+  TLR_CHECK(dalloc(&B.logP, (size_t)B.total_samples));
+  TLR_CHECK(dalloc(&B.ell, (size_t)count * B.M));
+  TLR_CHECK(dalloc(&B.out, (size_t)count * 2));
+  TLR_CHECK(dalloc(&B.a_st, (size_t)B.total_n));
+  TLR_CHECK(dalloc(&B.b_st, (size_t)B.total_n));
+  TLR_CUDA(cudaMallocHost(&B.h_ab, (size_t)B.total_n * 2 * 8));
+  TLR_CUDA(cudaMallocHost(&B.h_out, (size_t)count * 2 * 8 + 8));
+  TLR_CUDA(cudaStreamSynchronize(st));
+  // capture: permute limits -> persistent integrand -> estimator
+  cudaGraph_t graph;
+  TLR_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  cudaMemsetAsync(B.dbad, 0, sizeof(int), st);
+  cudaMemsetAsync(B.dnext, 0, sizeof(int), st);
+  k_permute_batch<<<nblk(B.total_n, 256), 256, 0, st>>>(B.a_st, B.b_st, B.perm_g, B.total_n, B.a32, B.b32, B.dbad);
+  k_batch<<<B.grid, BATCH_T, smem, st>>>(B.dprobs, B.ditems, B.n_items, B.dnext, B.W,
+                                         std::max<int64_t>(B.ktot_max, 1) * BATCH_T, B.logP);
+  k_shift_reduce<<<(unsigned)(count * B.M), 256, 0, st>>>(B.logP, B.N, B.ell);
+  k_final_batch<<<count, 256, 0, st>>>(B.ell, B.M, B.out);
+  cudaError_t ec = cudaStreamEndCapture(st, &graph);
+  if (ec != cudaSuccess) return cuda_fail(ec, "capture of the batched integrand");
+  ec = cudaGraphInstantiate(&B.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ec != cudaSuccess) return cuda_fail(ec, "instantiate the batched integrand graph");
+  return TLRMVN_OK;
+}
+
+static int batch_run(Batch& B, const double* const* a, const double* const* b, double* logp, double* err) {
+  int cur = 0;
+  cudaGetDevice(&cur);
+  TLR_CUDA(cudaSetDevice(B.device));
+  for (int p = 0; p < B.count; p++) {
+    if (!a[p] || !b[p]) return fail(TLRMVN_E_INVAL, "null limits in batch");
+    std::copy(a[p], a[p] + B.F[p]->n, B.h_ab + B.n_off[p]);
+    std::copy(b[p], b[p] + B.F[p]->n, B.h_ab + B.total_n + B.n_off[p]);
+  }
+  cudaStream_t st = B.st;
+  TLR_CUDA(cudaMemcpyAsync(B.a_st, B.h_ab, B.total_n * 8, cudaMemcpyHostToDevice, st));
+  TLR_CUDA(cudaMemcpyAsync(B.b_st, B.h_ab + B.total_n, B.total_n * 8, cudaMemcpyHostToDevice, st));
+  TLR_CUDA(cudaGraphLaunch(B.exec, st));
+  TLR_CUDA(cudaMemcpyAsync(B.h_out, B.out, (size_t)B.count * 2 * 8, cudaMemcpyDeviceToHost, st));
+  TLR_CUDA(cudaMemcpyAsync(B.h_out + 2 * B.count, B.dbad, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TLR_CUDA(cudaStreamSynchronize(st));
+  int bad = 0;
+  memcpy(&bad, B.h_out + 2 * B.count, sizeof(int));
+  cudaSetDevice(cur);
+  if (bad) return fail(TLRMVN_E_INVAL, "limits must satisfy a_i <= b_i, a_i < +inf, b_i > -inf, no NaN");
+  for (int p = 0; p < B.count; p++) {
+    logp[p] = B.h_out[2 * p];
+    err[p] = B.h_out[2 * p + 1];
+  }
+  return TLRMVN_OK;
+}
+
+static int check_batch_opts(int count, const tlrmvn_factor_t* f, const double* nu, const tlrmvn_opts* o) {
+  if (count < 1 || !f || !nu || !o) return fail(TLRMVN_E_INVAL, "bad batch arguments");
+  if (o->n_shifts < 1 || o->n_points < 1) return fail(TLRMVN_E_INVAL, "n_shifts and n_points must be >= 1");
+  if (o->precision != TLRMVN_FP32) return fail(TLRMVN_E_NOTSUP, "the batched integrand runs in TLRMVN_FP32");
+  if (o->shifts) return fail(TLRMVN_E_NOTSUP, "batched problems draw their shifts from opts.seed + problem index");
+  return TLRMVN_OK;
+}
+
+}  // namespace tlrmvn
+
+using namespace tlrmvn;
+
+extern "C" int tlrmvn_batch_create(int count, const tlrmvn_factor_t* factors, const double* nu,
+                                   const tlrmvn_opts* opts, tlrmvn_batch_t* out) {
+  if (!out) return fail(TLRMVN_E_INVAL, "null output");
+  TLR_CHECK(check_batch_opts(count, factors, nu, opts));
+  Batch* B = new Batch();
+  int s = batch_build(*B, count, factors, nu, *opts);
+  if (s != TLRMVN_OK) {
+    delete B;
+    return s;
+  }
+  *out = reinterpret_cast<tlrmvn_batch_t>(B);
+  return TLRMVN_OK;
+}
+
+extern "C" int tlrmvn_batch_run(tlrmvn_batch_t plan, const double* const* a, const double* const* b, double* logp,
+                                double* err) {
+  if (!plan || !a || !b || !logp || !err) return fail(TLRMVN_E_INVAL, "null argument");
+  return batch_run(*reinterpret_cast<Batch*>(plan), a, b, logp, err);
+}
+
+extern "C" int tlrmvn_batch_free(tlrmvn_batch_t plan) {
+  delete reinterpret_cast<Batch*>(plan);
+  return TLRMVN_OK;
+}
+
+extern "C" int tlrmvn_prob_batch(int count, const tlrmvn_factor_t* factors, const double* const* a,
+                                 const double* const* b, const double* nu, const tlrmvn_opts* opts, double* logp,
+                                 double* err) {
+  tlrmvn_batch_t plan = nullptr;
+  TLR_CHECK(tlrmvn_batch_create(count, factors, nu, opts, &plan));
+  int s = tlrmvn_batch_run(plan, a, b, logp, err);
+  tlrmvn_batch_free(plan);
+  return s;
+}

@@ -5,12 +5,12 @@
 
 namespace tlrmvn {
 
-// C[rowmap[i]][:] = A (M x K, row-major) * B (K x N, row-major); rowmap may be null.
-// 64x64 output tile per 256-thread block, 4x4 per thread, K in steps of 16.
+// C[rowmap[i]][:] = A (M x K, row-major) * B (K x N, row-major) (+ C when accumulate);
+// rowmap may be null.  64x64 output tile per 256-thread block, 4x4 per thread, K in steps of 16.
 template <typename T>
 __global__ void __launch_bounds__(256) k_gemm_nn(int M, int64_t N, int64_t K, const T* __restrict__ A, int64_t lda,
                                                  const T* __restrict__ B, int64_t ldb, T* __restrict__ C, int64_t ldc,
-                                                 const int32_t* __restrict__ rowmap) {
+                                                 const int32_t* __restrict__ rowmap, int accumulate) {
   __shared__ T As[16][64 + 1];
   __shared__ T Bs[16][64];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -56,17 +56,20 @@ __global__ void __launch_bounds__(256) k_gemm_nn(int M, int64_t N, int64_t K, co
 #pragma unroll
     for (int j = 0; j < 4; j++) {
       int64_t gn = n0 + tx + 16 * j;
-      if (gn < N) C[row * ldc + gn] = acc[i][j];
+      if (gn < N) {
+        T* c = C + row * ldc + gn;
+        *c = accumulate ? *c + acc[i][j] : acc[i][j];
+      }
     }
   }
 }
 
 template <typename T>
 inline void gemm_nn(cudaStream_t st, int M, int64_t N, int64_t K, const T* A, int64_t lda, const T* B, int64_t ldb,
-                    T* C, int64_t ldc, const int32_t* rowmap) {
+                    T* C, int64_t ldc, const int32_t* rowmap, int accumulate = 0) {
   if (M <= 0 || N <= 0) return;
   dim3 grid((unsigned)((N + 63) / 64), (unsigned)((M + 63) / 64));
-  k_gemm_nn<T><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, rowmap);
+  k_gemm_nn<T><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, rowmap, accumulate);
 }
 
 // ---- batched, grouped float64 GEMM for the factorisation ---------------------------

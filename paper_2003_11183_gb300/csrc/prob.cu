@@ -13,6 +13,7 @@
 #include "common.cuh"
 #include "gemm.cuh"
 #include "gemm_tc.cuh"
+#include "sov_device.cuh"
 
 #include <cudaTypedefs.h>
 
@@ -22,74 +23,6 @@
 namespace tlrmvn {
 
 // ---- Student-t scale (Algorithm 7): chi_nu^-1(w0)/sqrt(nu) ------------------------
-// Regularised incomplete gamma P(a,x) and Q(a,x) = 1 - P: power series below
-// x = a + 1, Legendre continued fraction (modified Lentz) above.
-__device__ void gamma_pq(double a, double x, double& P, double& Q) {
-  if (!(x > 0.0)) {
-    P = 0.0;
-    Q = 1.0;
-    return;
-  }
-  double lpref = a * log(x) - x - lgamma(a);
-  if (x < a + 1.0) {
-    double ap = a, term = 1.0 / a, sum = term;
-    for (int it = 0; it < 2000; it++) {
-      ap += 1.0;
-      term *= x / ap;
-      sum += term;
-      if (fabs(term) < fabs(sum) * 1e-17) break;
-    }
-    P = sum * exp(lpref);
-    Q = 1.0 - P;
-  } else {
-    const double tiny = 1e-300;
-    double bq = x + 1.0 - a, c = 1.0 / tiny, d = 1.0 / bq, h = d;
-    for (int i = 1; i < 2000; i++) {
-      double an = -i * (i - a);
-      bq += 2.0;
-      d = an * d + bq;
-      if (fabs(d) < tiny) d = tiny;
-      c = bq + an / c;
-      if (fabs(c) < tiny) c = tiny;
-      d = 1.0 / d;
-      double del = d * c;
-      h *= del;
-      if (fabs(del - 1.0) < 1e-16) break;
-    }
-    Q = exp(lpref) * h;
-    P = 1.0 - Q;
-  }
-}
-
-// x with P(a, x) = p (q = 1 - p exactly): Wilson-Hilferty start, Halley steps.
-__device__ double gamma_p_inv(double a, double p, double q) {
-  double z = ndtri2(p, q, log(p));
-  double t = 1.0 / (9.0 * a);
-  double base = 1.0 - t + z * sqrt(t);
-  double x = a * base * base * base;
-  if (!(x > 0.0)) x = exp((log(p) + lgamma(a + 1.0)) / a);
-  const double lga = lgamma(a);
-  for (int it = 0; it < 100; it++) {
-    double P, Q;
-    gamma_pq(a, x, P, Q);
-    double f = (p < 0.5) ? (P - p) : (q - Q);
-    double f1 = exp((a - 1.0) * log(x) - x - lga);
-    if (!(f1 > 0.0)) break;
-    double dx = f / f1;
-    double h2 = (a - 1.0) / x - 1.0;
-    double corr = 0.5 * dx * h2;
-    double step = (fabs(corr) < 0.5) ? dx / (1.0 - corr) : dx;
-    double xn = x - step;
-    if (!(xn > 0.0)) xn = 0.5 * x;
-    if (fabs(xn - x) <= 4e-16 * x) {
-      x = xn;
-      break;
-    }
-    x = xn;
-  }
-  return x;
-}
-
 __global__ void k_chi_scale(double* rs, float* rs32, const uint64_t* Q, const uint64_t* D, int64_t ldD,
                             int64_t coord, int64_t sample0, int64_t N, int64_t C, double nu, int periodize) {
   int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -204,53 +137,14 @@ __global__ void k_diag(DiagArgs<T, YT> p) {
 }
 
 // ---- float32 sweep ------------------------------------------------------------------
-// Lattice value as floats, from the same exact numerator as lattice_w (integer
-// arithmetic only: the float path issues no float64 instruction).
-__device__ __forceinline__ void lattice_wf(uint64_t x, int periodize, float& w, float& wc) {
-  int64_t num;
-  if (periodize) {
-    int64_t h = (int64_t)(x >> 11);
-    num = 2 * h + 1 - (int64_t(1) << 53);
-    if (num < 0) num = -num;
-  } else {
-    num = 2 * (int64_t)(x >> 12) + 1;
-  }
-  const int64_t numc = (int64_t(1) << 53) - num;
-  w = fmaf((float)(uint32_t)(num >> 21), 2.3283064365386963e-10f, (float)(uint32_t)(num & 0x1FFFFF) * 1.1102230246251565e-16f);
-  wc = fmaf((float)(uint32_t)(numc >> 21), 2.3283064365386963e-10f,
-            (float)(uint32_t)(numc & 0x1FFFFF) * 1.1102230246251565e-16f);
-}
-
-// eq. (2) for one variable in float32; the one-sided case (at = -inf) evaluates one
-// scaled complementary error function and the logs it needs, nothing else.
-__device__ __forceinline__ void sov_step_f32(float at, float bt, float w, float wc, float& ld, float& y) {
-  const float rs2 = (float)TLR_RSQRT2;
-  if (at == -INFINITY && bt != INFINITY) {
-    if (bt < 0.0f) {
-      const float t = -bt * rs2;
-      const float le = logf(0.5f * erfcxf(t)) - t * t;  // log Phi(bt)
-      const float lu = logf(w) + le;                      // log u, u = w Phi(bt) < 1/2
-      y = ndtri_lower(expf(lu), lu);
-      ld = le;
-    } else {
-      const float ec = 0.5f * erfcf(bt * rs2);
-      const float e = 1.0f - ec;
-      const float u = w * e, uc = ec + wc * e;
-      y = (u <= 0.5f) ? ndtri_lower(u, logf(u)) : -ndtri_lower(uc, logf(uc));
-      ld = log1pf(-ec);
-    }
-    return;
-  }
-  sov_step<float>(at, bt, w, wc, ld, y);
-}
-
-template <typename YT>
+// Arguments of one float32 sweep over a (sub-)tile of mt variables.  All
+// pointers are already offset to the sub-tile's first variable.
 struct DiagArgs32 {
-  const float* BT;   // transposed tile, BT[u * ldbt + v] = B[v][u]
+  const float* BT;   // transposed diagonal block, BT[u * ldbt + v] = B[v][u]
   const float* inv;  // 1 / B[v][v]
   int mt;
   int64_t ldbt;
-  const float* Delta;
+  const float* Delta;  // limit shifts, variable-major (ldd), or null
   int64_t ldd;
   const float* a;
   const float* b;
@@ -259,18 +153,22 @@ struct DiagArgs32 {
   const uint64_t* D;
   int64_t ldD, coord0, sample0, N, C;
   int periodize, first;
-  YT* Y;
-  int64_t ldy;
+  float* Yv;             // y variable-major, Yv[v * ldyv + c], or null
+  int64_t ldyv;
+  __nv_bfloat16* Ys;     // y sample-major bf16, Ys[c * ldys + v], or null
+  int64_t ldys;
   double* logP;
 };
 
 // One thread per sample; 16 variables per pass: the partial sums of a block of
-// 16 variables over all earlier variables of the tile are accumulated together
-// (each y_u read once per block, B read as four broadcast float4 per u), then
-// the block's 16 x 16 triangle and special functions run in order.
+// 16 variables over all earlier variables of the (sub-)tile are accumulated
+// together (each y_u read once per block, B read as four broadcast float4 per
+// u), then the block's 16 x 16 triangle and special functions run in order.
 constexpr int DIAG_VB = 16;
-template <typename YT, bool SAMPLE_MAJOR>
-__global__ void k_diag_f32(DiagArgs32<YT> p) {
+// Sub-tile of the float sweep: couplings between sub-tiles of one diagonal tile
+// are applied as a dense product before the sweep of each sub-tile.
+constexpr int DIAG_SUB = 128;
+__global__ void k_diag_f32(DiagArgs32 p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* ys = reinterpret_cast<float*>(smem_raw);
   const int bd = blockDim.x, tid = threadIdx.x, ld = bd + 1;
@@ -332,19 +230,19 @@ __global__ void k_diag_f32(DiagArgs32<YT> p) {
           lp += lv;
           yb[j] = y;
           ys[v * ld + tid] = y;
-          if (!SAMPLE_MAJOR) put_y(p.Y, (int64_t)v * p.ldy + c, y);
+          if (p.Yv) p.Yv[(int64_t)v * p.ldyv + c] = y;
         }
       }
     }
     if (p.first) p.logP[g] = (double)lp;
     else p.logP[g] += (double)lp;
   }
-  if (SAMPLE_MAJOR) {
+  if (p.Ys) {
     __syncthreads();
     const int nw = bd >> 5, warp = tid >> 5, lane = tid & 31;
     for (int j = warp; j < bd; j += nw) {
       if (c0 + j >= p.C) break;
-      YT* row = p.Y + (c0 + j) * p.ldy;
+      __nv_bfloat16* row = p.Ys + (c0 + j) * p.ldys;
       for (int v = lane; v < p.mt; v += 32) put_y(row, v, ys[v * ld + j]);
     }
   }
@@ -401,7 +299,7 @@ __global__ void k_shift_reduce(const double* logP, int64_t N, double* ell) {
 }
 
 // log p_hat = log((1/M) sum_s exp(ell_s)); err = SD_s(exp ell_s)/(sqrt(M) p_hat).
-__global__ void k_final(const double* ell, int M, double* out) {
+__device__ void final_estimate(const double* ell, int M, double* out) {
   __shared__ double sh[32];
   double mx = -INFINITY;
   for (int s = threadIdx.x; s < M; s += blockDim.x) mx = fmax(mx, ell[s]);
@@ -422,6 +320,11 @@ __global__ void k_final(const double* ell, int M, double* out) {
     out[0] = (mx > -INFINITY) ? mx + log(sum) - log((double)M) : -INFINITY;
     out[1] = (M > 1 && mx > -INFINITY) ? sqrt(sq / (M - 1) / M) / mean : NAN;
   }
+}
+__global__ void k_final(const double* ell, int M, double* out) { final_estimate(ell, M, out); }
+// one problem per block: ell + blockIdx.x * M -> out + 2 * blockIdx.x
+__global__ void k_final_batch(const double* ell, int M, double* out) {
+  final_estimate(ell + (int64_t)blockIdx.x * M, M, out + 2 * blockIdx.x);
 }
 
 template <typename S, typename D>
@@ -449,17 +352,24 @@ __global__ void k_pad_v16(const double* Vcat, int m, int64_t my, int64_t count, 
 
 static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// float32 diagonal tiles: row-major B32, transposed BT32 (ld ldbt), reciprocal diagonal inv32
+int ensure_float_tiles(Factor& F, cudaStream_t st) {
+  if (F.B32) return TLRMVN_OK;
+  const int64_t nb = (int64_t)F.r * F.m * F.m;
+  TLR_CHECK(dalloc(&F.B32, nb));
+  k_convert<double, float><<<blocks_for(nb, 256), 256, 0, st>>>(F.B, F.B32, nb);
+  F.ldbt = ((int64_t)F.m + DIAG_VB - 1) / DIAG_VB * DIAG_VB;
+  const int64_t nt = (int64_t)F.r * F.m * F.ldbt;
+  TLR_CHECK(dalloc(&F.BT32, nt));
+  TLR_CHECK(dalloc(&F.inv32, (size_t)F.r * F.m));
+  k_transpose_tiles<<<blocks_for(nt, 256), 256, 0, st>>>(F.B, F.m, F.ldbt, nt, F.BT32, F.inv32);
+  TLR_CUDA(cudaGetLastError());
+  return TLRMVN_OK;
+}
+
 static int ensure_copies(Factor& F, int precision, cudaStream_t st) {
-  const int64_t nb = (int64_t)F.r * F.m * F.m, nu = (int64_t)F.m * F.ktot;
-  if (precision != TLRMVN_FP64 && !F.B32) {
-    TLR_CHECK(dalloc(&F.B32, nb));
-    k_convert<double, float><<<blocks_for(nb, 256), 256, 0, st>>>(F.B, F.B32, nb);
-    F.ldbt = ((int64_t)F.m + DIAG_VB - 1) / DIAG_VB * DIAG_VB;
-    const int64_t nt = (int64_t)F.r * F.m * F.ldbt;
-    TLR_CHECK(dalloc(&F.BT32, nt));
-    TLR_CHECK(dalloc(&F.inv32, (size_t)F.r * F.m));
-    k_transpose_tiles<<<blocks_for(nt, 256), 256, 0, st>>>(F.B, F.m, F.ldbt, nt, F.BT32, F.inv32);
-  }
+  const int64_t nu = (int64_t)F.m * F.ktot;
+  if (precision != TLRMVN_FP64) TLR_CHECK(ensure_float_tiles(F, st));
   if (precision == TLRMVN_FP32 && !F.U32 && nu) {
     TLR_CHECK(dalloc(&F.U32, nu));
     TLR_CHECK(dalloc(&F.V32, nu));
@@ -537,7 +447,9 @@ static int make_map(CUtensorMap* map, const void* base, uint64_t inner, uint64_t
 }
 
 // splitmix64 (S. Vigna): output number t of the generator started at `seed`.
-static uint64_t splitmix64_at(uint64_t seed, uint64_t t) {
+uint64_t splitmix64_seed_at(uint64_t seed, uint64_t t);
+static uint64_t splitmix64_at(uint64_t seed, uint64_t t) { return splitmix64_seed_at(seed, t); }
+uint64_t splitmix64_seed_at(uint64_t seed, uint64_t t) {
   uint64_t z = seed + (t + 1) * 0x9E3779B97F4A7C15ULL;
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
@@ -584,33 +496,58 @@ static int diag_threads(int m) {
   return bd;
 }
 
-template <typename YT, bool SM>
-static void launch_diag_f32(const Factor& F, int i, const float* Delta, int64_t ldd, const Lims& L, const float* rs32,
-                            const uint64_t* dD, int64_t c0, int64_t N, int64_t Cc, int periodize, YT* Y, int64_t ldy,
-                            double* logP, int bd, size_t smem, cudaStream_t st) {
-  DiagArgs32<YT> a;
-  a.BT = F.BT32 + (size_t)i * F.m * F.ldbt;
-  a.inv = F.inv32 + (size_t)i * F.m;
-  a.mt = (int)F.tsize(i);
-  a.ldbt = F.ldbt;
-  a.Delta = Delta;
-  a.ldd = ldd;
-  a.a = L.a32 + F.tile_off[i];
-  a.b = L.b32 + F.tile_off[i];
-  a.rs = rs32;
-  a.Q = F.Q;
-  a.D = dD;
-  a.ldD = F.n + 1;
-  a.coord0 = F.tile_off[i];
-  a.sample0 = c0;
-  a.N = N;
-  a.C = Cc;
-  a.periodize = periodize;
-  a.first = (i == 0);
-  a.Y = Y;
-  a.ldy = ldy;
-  a.logP = logP;
-  k_diag_f32<YT, SM><<<blocks_for(Cc, bd), bd, smem, st>>>(a);
+// Threads per block and shared memory of the float sweep over DIAG_SUB-variable sub-tiles.
+static int sub_threads(int m) { return diag_threads<float>(std::min(m, DIAG_SUB)); }
+static size_t sub_smem(int m) { return (size_t)std::min(m, DIAG_SUB) * (sub_threads(m) + 1) * sizeof(float); }
+
+// Float sweep of diagonal tile i, DIAG_SUB variables at a time.  Before each
+// sub-tile q > 0, the coupling to the tile's earlier sub-tiles,
+// B_i[q, <q] y_i[<q], is added to the limit shifts Dl (variable-major, ld C) by a
+// dense product; y goes to Yv (float, variable-major, ld C) and, when Ys is
+// given, to Ys (bf16, sample-major, ld ldys).  has_shift: Dl already holds the
+// low-rank shifts of this tile.
+static void sweep_tile_f32(const Factor& F, int i, bool has_shift, float* Dl, int64_t C, const Lims& L,
+                           const float* rs32, const uint64_t* dD, int64_t c0, int64_t N, int64_t Cc, int periodize,
+                           float* Yv, __nv_bfloat16* Ys, int64_t ldys, double* logP, cudaStream_t st, Prof& pf) {
+  const int m = F.m, mt = (int)F.tsize(i);
+  const int bd = sub_threads(m);
+  const size_t smem = sub_smem(m);
+  const float* Bi = F.B32 + (size_t)i * m * m;
+  for (int q0 = 0; q0 < mt; q0 += DIAG_SUB) {
+    const int mq = std::min(DIAG_SUB, mt - q0);
+    if (q0 > 0) {
+      pf.begin(TLRMVN_KC_DIAG);
+      gemm_nn<float>(st, mq, Cc, q0, Bi + (size_t)q0 * m, m, Yv, C, Dl + (size_t)q0 * C, C, nullptr, has_shift ? 1 : 0);
+      pf.end();
+    }
+    DiagArgs32 a;
+    a.BT = F.BT32 + (size_t)i * m * F.ldbt + (size_t)q0 * F.ldbt + q0;
+    a.inv = F.inv32 + (size_t)i * m + q0;
+    a.mt = mq;
+    a.ldbt = F.ldbt;
+    a.Delta = (has_shift || q0 > 0) ? Dl + (size_t)q0 * C : nullptr;
+    a.ldd = C;
+    a.a = L.a32 + F.tile_off[i] + q0;
+    a.b = L.b32 + F.tile_off[i] + q0;
+    a.rs = rs32;
+    a.Q = F.Q;
+    a.D = dD;
+    a.ldD = F.n + 1;
+    a.coord0 = F.tile_off[i] + q0;
+    a.sample0 = c0;
+    a.N = N;
+    a.C = Cc;
+    a.periodize = periodize;
+    a.first = (i == 0 && q0 == 0);
+    a.Yv = Yv + (size_t)q0 * C;
+    a.ldyv = C;
+    a.Ys = Ys ? Ys + q0 : nullptr;
+    a.ldys = ldys;
+    a.logP = logP;
+    pf.begin(TLRMVN_KC_DIAG);
+    k_diag_f32<<<blocks_for(Cc, bd), bd, smem, st>>>(a);
+    pf.end();
+  }
 }
 
 template <typename T, typename YT>
@@ -642,7 +579,7 @@ static int run_chunks(Factor& F, const T* Bt, const T* Ut, const T* Vt, const Li
   const int bd = diag_threads<T>(m);
   const size_t smem = (size_t)m * (bd + 1) * sizeof(T);
   if (f32)
-    TLR_CUDA(cudaFuncSetAttribute(k_diag_f32<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    TLR_CUDA(cudaFuncSetAttribute(k_diag_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sub_smem(m)));
   else
     TLR_CUDA(cudaFuncSetAttribute(k_diag<T, YT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
 
@@ -664,11 +601,11 @@ static int run_chunks(Factor& F, const T* Bt, const T* Ut, const T* Vt, const Li
         pf.end();
         Delta = Dl;
       }
-      pf.begin(TLRMVN_KC_DIAG);
       if constexpr (sizeof(T) == 4) {
-        launch_diag_f32<float, false>(F, i, (const float*)Delta, C, L, rs32, dD, c0, N, Cc, o.periodize,
-                                      (float*)Y, C, logP, bd, smem, st);
+        sweep_tile_f32(F, i, Kr > 0, (float*)Dl, C, L, rs32, dD, c0, N, Cc, o.periodize, (float*)Y, nullptr, 0, logP,
+                       st, pf);
       } else {
+        pf.begin(TLRMVN_KC_DIAG);
         DiagArgs<T, YT> a;
         a.B = Bt + (size_t)i * m * m;
         a.mt = mt;
@@ -691,8 +628,8 @@ static int run_chunks(Factor& F, const T* Bt, const T* Ut, const T* Vt, const Li
         a.ldy = C;
         a.logP = logP;
         k_diag<T, YT, false><<<blocks_for(Cc, bd), bd, smem, st>>>(a);
+        pf.end();
       }
-      pf.end();
       if (Kc > 0) {
         pf.begin(TLRMVN_KC_VPROJ);
         gemm_nn<T>(st, (int)Kc, Cc, mt, Vt + (size_t)m * F.kcol_off[i], m, Y, C, W, C, F.vmap + F.kcol_off[i]);
@@ -723,12 +660,13 @@ static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opt
   C = std::min<int64_t>(C, S);
   C = (C + 255) / 256 * 256;
   __nv_bfloat16 *W = nullptr, *Y = nullptr;
-  float* Dl = nullptr;
+  float *Dl = nullptr, *Yv = nullptr;
   float* rs32 = nullptr;
   int* err = nullptr;
   TLR_CHECK(sc.get(&W, (size_t)F.kw16 * C));
   TLR_CHECK(sc.get(&Y, (size_t)F.my16 * C));
   TLR_CHECK(sc.get(&Dl, (size_t)m * C));
+  TLR_CHECK(sc.get(&Yv, (size_t)m * C));
   TLR_CHECK(sc.get(&err, 1));
   const bool mvt = std::isfinite(nu);
   if (mvt) TLR_CHECK(sc.get(&rs32, (size_t)C));
@@ -749,10 +687,7 @@ static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opt
   TLR_CUDA(cudaFuncSetAttribute(tc::k_gemm_tc<tc::EPI_COLMAP_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 tc::SMEM_BYTES));
 
-  const int bd = diag_threads<float>(m);
-  const size_t smem = (size_t)m * (bd + 1) * sizeof(float);
-  TLR_CUDA(cudaFuncSetAttribute(k_diag_f32<__nv_bfloat16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem));
+  TLR_CUDA(cudaFuncSetAttribute(k_diag_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sub_smem(m)));
 
   for (int64_t c0 = 0; c0 < S; c0 += C) {
     const int64_t Cc = std::min(C, S - c0);
@@ -775,10 +710,7 @@ static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opt
         pf.end();
         Delta = Dl;
       }
-      pf.begin(TLRMVN_KC_DIAG);
-      launch_diag_f32<__nv_bfloat16, true>(F, i, Delta, C, L, rs32, dD, c0, N, Cc, o.periodize, Y, F.my16, logP, bd,
-                                           smem, st);
-      pf.end();
+      sweep_tile_f32(F, i, Delta != nullptr, Dl, C, L, rs32, dD, c0, N, Cc, o.periodize, Yv, Y, F.my16, logP, st, pf);
       if (Kc > 0) {
         tc::GemmTcArgs g{(int)Kc, (int)Cc, mt, 0, (int)F.kcol_off[i], 0, 0, nullptr, 0, W, F.kw16,
                          F.vmap16 + F.kcol_off[i], err};

@@ -1,0 +1,118 @@
+// Device functions of the float32 integrand and of the Student-t scale, shared
+// by the single-problem integrand (prob.cu) and the batched persistent kernel (batch.cu).
+#pragma once
+#include "common.cuh"
+
+namespace tlrmvn {
+
+// ---- Student-t scale (Algorithm 7): chi_nu^-1(w0)/sqrt(nu) ------------------------
+// Regularised incomplete gamma P(a,x) and Q(a,x) = 1 - P: power series below
+// x = a + 1, Legendre continued fraction (modified Lentz) above.
+__device__ inline void gamma_pq(double a, double x, double& P, double& Q) {
+  if (!(x > 0.0)) {
+    P = 0.0;
+    Q = 1.0;
+    return;
+  }
+  double lpref = a * log(x) - x - lgamma(a);
+  if (x < a + 1.0) {
+    double ap = a, term = 1.0 / a, sum = term;
+    for (int it = 0; it < 2000; it++) {
+      ap += 1.0;
+      term *= x / ap;
+      sum += term;
+      if (fabs(term) < fabs(sum) * 1e-17) break;
+    }
+    P = sum * exp(lpref);
+    Q = 1.0 - P;
+  } else {
+    const double tiny = 1e-300;
+    double bq = x + 1.0 - a, c = 1.0 / tiny, d = 1.0 / bq, h = d;
+    for (int i = 1; i < 2000; i++) {
+      double an = -i * (i - a);
+      bq += 2.0;
+      d = an * d + bq;
+      if (fabs(d) < tiny) d = tiny;
+      c = bq + an / c;
+      if (fabs(c) < tiny) c = tiny;
+      d = 1.0 / d;
+      double del = d * c;
+      h *= del;
+      if (fabs(del - 1.0) < 1e-16) break;
+    }
+    Q = exp(lpref) * h;
+    P = 1.0 - Q;
+  }
+}
+
+// x with P(a, x) = p (q = 1 - p exactly): Wilson-Hilferty start, Halley steps.
+__device__ inline double gamma_p_inv(double a, double p, double q) {
+  double z = ndtri2(p, q, log(p));
+  double t = 1.0 / (9.0 * a);
+  double base = 1.0 - t + z * sqrt(t);
+  double x = a * base * base * base;
+  if (!(x > 0.0)) x = exp((log(p) + lgamma(a + 1.0)) / a);
+  const double lga = lgamma(a);
+  for (int it = 0; it < 100; it++) {
+    double P, Q;
+    gamma_pq(a, x, P, Q);
+    double f = (p < 0.5) ? (P - p) : (q - Q);
+    double f1 = exp((a - 1.0) * log(x) - x - lga);
+    if (!(f1 > 0.0)) break;
+    double dx = f / f1;
+    double h2 = (a - 1.0) / x - 1.0;
+    double corr = 0.5 * dx * h2;
+    double step = (fabs(corr) < 0.5) ? dx / (1.0 - corr) : dx;
+    double xn = x - step;
+    if (!(xn > 0.0)) xn = 0.5 * x;
+    if (fabs(xn - x) <= 4e-16 * x) {
+      x = xn;
+      break;
+    }
+    x = xn;
+  }
+  return x;
+}
+
+// ---- float32 integrand helpers ------------------------------------------------------
+// Lattice value as floats, from the same exact numerator as lattice_w (integer
+// arithmetic only: the float path issues no float64 instruction).
+__device__ __forceinline__ void lattice_wf(uint64_t x, int periodize, float& w, float& wc) {
+  int64_t num;
+  if (periodize) {
+    int64_t h = (int64_t)(x >> 11);
+    num = 2 * h + 1 - (int64_t(1) << 53);
+    if (num < 0) num = -num;
+  } else {
+    num = 2 * (int64_t)(x >> 12) + 1;
+  }
+  const int64_t numc = (int64_t(1) << 53) - num;
+  w = fmaf((float)(uint32_t)(num >> 21), 2.3283064365386963e-10f, (float)(uint32_t)(num & 0x1FFFFF) * 1.1102230246251565e-16f);
+  wc = fmaf((float)(uint32_t)(numc >> 21), 2.3283064365386963e-10f,
+            (float)(uint32_t)(numc & 0x1FFFFF) * 1.1102230246251565e-16f);
+}
+
+// eq. (2) for one variable in float32; the one-sided case (at = -inf) evaluates one
+// scaled complementary error function and the logs it needs, nothing else.
+__device__ __forceinline__ void sov_step_f32(float at, float bt, float w, float wc, float& ld, float& y) {
+  const float rs2 = (float)TLR_RSQRT2;
+  if (at == -INFINITY && bt != INFINITY) {
+    if (bt < 0.0f) {
+      const float t = -bt * rs2;
+      const float le = logf(0.5f * erfcxf(t)) - t * t;  // log Phi(bt)
+      const float lu = logf(w) + le;                      // log u, u = w Phi(bt) < 1/2
+      y = ndtri_lower(expf(lu), lu);
+      ld = le;
+    } else {
+      const float ec = 0.5f * erfcf(bt * rs2);
+      const float e = 1.0f - ec;
+      const float u = w * e, uc = ec + wc * e;
+      y = (u <= 0.5f) ? ndtri_lower(u, logf(u)) : -ndtri_lower(uc, logf(uc));
+      ld = log1pf(-ec);
+    }
+    return;
+  }
+  sov_step<float>(at, bt, w, wc, ld, y);
+}
+
+}  // namespace tlrmvn

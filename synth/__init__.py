@@ -145,3 +145,20 @@ def small_workload(n_side: int, m: int, seed: int, kernel: int = KERNEL_EXP, par
     return Workload(f"small_{n}_{m}_{seed}", xy, kernel, tuple(params), 1e-8, a, b, m, tol,
                     max_rank if max_rank > 0 else m, nu, n_shifts, n_points,
                     lattice_shifts(n_shifts, n + 1, 3000 + seed), reorder=reorder)
+
+
+def batched_problems(count: int = 256, seed: int = 4000, n_min: int = 256, n_max: int = 4096):
+    """The batched workload: `count` MVN problems, n log-uniform in [n_min, n_max], each
+    with its own jittered grid (the first n points of a ceil(sqrt n)^2 grid), exponential
+    kernel with beta ~ U(0.05, 0.3), b_i ~ U(0, 1).  Returns a list of dicts."""
+    rng = np.random.default_rng(seed)
+    ns = np.exp(rng.uniform(math.log(n_min), math.log(n_max), size=count)).astype(int)
+    betas = rng.uniform(0.05, 0.3, size=count)
+    out = []
+    for p in range(count):
+        n = int(ns[p])
+        g = int(math.ceil(math.sqrt(n)))
+        xy = jittered_grid(g, seed + 1 + p)[:n]
+        a, b = limits_uniform(n, seed + 10_000 + p)
+        out.append({"xy": xy, "beta": float(betas[p]), "a": a, "b": b})
+    return out

@@ -43,7 +43,11 @@ def parse():
     ap.add_argument("--precision", default=os.environ.get("TLRMVN_BENCH_PRECISION", "fp32"), choices=list(PRECISIONS))
     ap.add_argument("--workload", type=int, default=3)
     ap.add_argument("--points", type=int, default=0, help="override points per shift (0 = workload's)")
+    ap.add_argument("--shifts", type=int, default=0, help="override the number of shifts (0 = workload's)")
+    ap.add_argument("--n-side", type=int, default=0,
+                    help="grid side of a smaller problem of the same family (profiling captures only)")
     ap.add_argument("--no-baselines", action="store_true", help="skip FP64-path and CPU-oracle legs")
+    ap.add_argument("--count", type=int, default=256, help="problems of the batched workload (--workload 4)")
     return ap.parse_args()
 
 
@@ -205,9 +209,12 @@ def run_ours(args):
     ge.build()
     import paper_2003_11183_gb300 as tl
     import synth
-    w = synth.workload(args.workload)
+    w = synth.workload(args.workload, n_side=args.n_side or None)
     if args.points:
         w.n_points = args.points
+    if args.shifts:
+        w.n_shifts = args.shifts
+        w.shifts = w.shifts[:args.shifts]
     if ws > 1:
         # disjoint shift batches per rank: same problem, independent replicas
         w.shifts = synth.lattice_shifts(w.n_shifts, w.n + 1, 3000 + args.workload + 7919 * rank)
@@ -332,10 +339,59 @@ def run_ours(args):
     return 0
 
 
+def run_batched(args):
+    """Batched workload: 256 MVN problems (n log-uniform in [256, 4096], own covariances,
+    m = 128, tol 1e-5, iterative block reordering), 10 shifts x 2,000 points each, solved by
+    one persistent launch (a replayed CUDA graph) per step."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2003_11183_gb300 as tl
+    import synth
+    probs = synth.batched_problems(args.count)
+    t0 = time.perf_counter()
+    factors = [tl.tlrmvn_factor_kernel(p["xy"], tl.KERNEL_EXP, (p["beta"],), 1e-8, p["a"], p["b"], 128, 1e-5, 0,
+                                       tl.REORDER_ITERATIVE) for p in probs]
+    factor_s = time.perf_counter() - t0
+    M, N = 10, args.points or 2000
+    plan = tl.BatchPlan(factors, math.inf, M, N, seed=4242)
+    a = [p["a"] for p in probs]
+    b = [p["b"] for p in probs]
+    for _ in range(args.warmup):
+        plan.run(a, b)
+    clocks = Clocks(0)
+    clocks.start()
+    times = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        lp, err = plan.run(a, b)
+        times.append(time.perf_counter() - t1)
+    clk = clocks.stop()
+    sd = sum(len(p["a"]) for p in probs) * M * N
+    ms = statistics.mean(times) * 1e3
+    line = {"metric": "batched QMC sample-dims/sec", "value": sd / (ms / 1e3), "unit": "sample-dims/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "p50_ms": statistics.median(times) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batched_{len(probs)}_mvn_n256_4096_m128", "problems": len(probs),
+                       "sum_n": sum(len(p["a"]) for p in probs), "shifts": M, "points": N, "tol": 1e-5},
+            "clocks": clk, "factor_seconds": factor_s,
+            "e2e": {"value": sd / (ms / 1e3), "unit": "sample-dims/s",
+                    "h2d_bytes_per_step": 2 * 8 * sum(len(p["a"]) for p in probs),
+                    "d2h_bytes_per_step": 16 * len(probs)},
+            "logp_mean": float(np.mean(lp)), "err_median": float(np.median(err))}
+    print(json.dumps(line), flush=True)
+    plan.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == 4:
+        return run_batched(args)
     return run_ours(args)
 
 

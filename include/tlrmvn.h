@@ -175,6 +175,41 @@ int tlrmvn_batch_free(tlrmvn_batch_t plan);
 int tlrmvn_prob_batch(int count, const tlrmvn_factor_t* factors, const double* const* a, const double* const* b,
                       const double* nu, const tlrmvn_opts* opts, double* logp, double* err);
 
+/* ---- serving loop ----------------------------------------------------- */
+
+/* A server keeps the given factors resident and answers probability requests
+ * with new limits as they arrive (e.g. the likelihood evaluations of Section 5,
+ * or an online service).  Requests wait in arrival order; `lanes` worker
+ * threads, each with its own CUDA stream, take the oldest request as soon as a
+ * lane is free and the request's scratch fits in what is left of
+ * `memory_budget` bytes.  Requests that arrive while others run are therefore
+ * admitted as lanes and memory free up, and their kernels overlap on the
+ * device.  A request's result depends on its own inputs only: it is the same
+ * alone and in the mix.  Factors must outlive the server; they may be used by
+ * other calls meanwhile.
+ *   tlrmvn_server_submit copies a, b (host, length n of the factor) and, when
+ *     opts->shifts is set, the shifts; opts->stream is ignored.  Returns an id.
+ *     TLRMVN_E_NOMEM if the request alone exceeds the budget.
+ *   tlrmvn_server_wait blocks until the request is done and returns its logp,
+ *     err and latency (submission to completion, milliseconds); an id can be
+ *     waited for once.
+ *   tlrmvn_server_free waits for every queued request, then stops the lanes. */
+typedef struct tlrmvn_server_s* tlrmvn_server_t;
+typedef struct {
+  int64_t completed, queued;
+  int in_flight, peak_in_flight;  /* requests on the device now / at most at once */
+  int64_t overlapped;             /* requests admitted while another was running  */
+  int64_t peak_bytes;             /* largest admitted scratch at once              */
+  double p50_ms, p99_ms;          /* latency percentiles of completed requests     */
+} tlrmvn_server_stats_t;
+int tlrmvn_server_create(const tlrmvn_factor_t* factors, int n_factors, int lanes, int64_t memory_budget,
+                         tlrmvn_server_t* out);
+int tlrmvn_server_submit(tlrmvn_server_t server, int factor, const double* a, const double* b, double nu,
+                         const tlrmvn_opts* opts, int64_t* request_id);
+int tlrmvn_server_wait(tlrmvn_server_t server, int64_t request_id, double* logp, double* err, double* latency_ms);
+int tlrmvn_server_stats(tlrmvn_server_t server, tlrmvn_server_stats_t* out);
+int tlrmvn_server_free(tlrmvn_server_t server);
+
 /* ---- estimator without device allocation ------------------------------ */
 
 /* The paper has no counterpart: this is a service for callers that cannot

@@ -20,6 +20,11 @@ class Opts(C.Structure):
                 ("shifts", c_u64_p), ("seed", C.c_uint64), ("sample_chunk", C.c_int64), ("stream", C.c_void_p)]
 
 
+class ServerStats(C.Structure):
+    _fields_ = [("completed", C.c_int64), ("queued", C.c_int64), ("in_flight", C.c_int), ("peak_in_flight", C.c_int),
+                ("overlapped", C.c_int64), ("peak_bytes", C.c_int64), ("p50_ms", C.c_double), ("p99_ms", C.c_double)]
+
+
 # every exported symbol of include/tlrmvn.h with its argument and result types
 SIGNATURES = {
     "tlrmvn_factor_kernel": (C.c_int, [c_double_p, C.c_int64, C.c_int, c_double_p, C.c_double, c_double_p, c_double_p,
@@ -41,6 +46,12 @@ SIGNATURES = {
     "tlrmvn_batch_free": (C.c_int, [C.c_void_p]),
     "tlrmvn_prob_batch": (C.c_int, [C.c_int, C.POINTER(C.c_void_p), C.POINTER(c_double_p), C.POINTER(c_double_p),
                                     c_double_p, C.POINTER(Opts), c_double_p, c_double_p]),
+    "tlrmvn_server_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int64, C.POINTER(C.c_void_p)]),
+    "tlrmvn_server_submit": (C.c_int, [C.c_void_p, C.c_int, c_double_p, c_double_p, C.c_double, C.POINTER(Opts),
+                                       C.POINTER(C.c_int64)]),
+    "tlrmvn_server_wait": (C.c_int, [C.c_void_p, C.c_int64, c_double_p, c_double_p, c_double_p]),
+    "tlrmvn_server_stats": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "tlrmvn_server_free": (C.c_int, [C.c_void_p]),
     "tlrmvn_estimate_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tlrmvn_profile_enable": (C.c_int, [C.c_int]),
     "tlrmvn_profile_reset": (C.c_int, []),

@@ -173,6 +173,55 @@ def tlrmvn_prob_batch(factors, a_list, b_list, nu, n_shifts: int, n_points: int,
         plan.close()
 
 
+class Server:
+    """tlrmvn_server_t: resident factors, requests admitted as lanes and memory free up."""
+
+    def __init__(self, factors, lanes: int = 4, memory_budget: int = 16 << 30):
+        lib = L.load()
+        self.factors = list(factors)
+        self.sizes = [tlrmvn_factor_info(f)["n"] for f in self.factors]
+        hs = (C.c_void_p * len(self.factors))(*[f.handle.value for f in self.factors])
+        out = C.c_void_p()
+        _check(lib.tlrmvn_server_create(hs, len(self.factors), int(lanes), int(memory_budget), C.byref(out)),
+               "tlrmvn_server_create")
+        self.handle = out
+
+    def submit(self, factor: int, a, b, nu: float = math.inf, precision: int = FP32, n_shifts: int = 10,
+               n_points: int = 1000, shifts=None, seed: int = 0, periodize: bool = True, sample_chunk: int = 0) -> int:
+        a = _f64(a)
+        b = _f64(b)
+        o, keep = _opts(precision, n_shifts, n_points, periodize, shifts, seed, sample_chunk, None,
+                        self.sizes[factor])
+        rid = C.c_int64()
+        _check(L.load().tlrmvn_server_submit(self.handle, int(factor), _dp(a), _dp(b), float(nu), C.byref(o),
+                                             C.byref(rid)), "tlrmvn_server_submit")
+        del keep
+        return rid.value
+
+    def wait(self, rid: int):
+        """(logp, err, latency_ms) of a submitted request."""
+        lp, er, lat = C.c_double(), C.c_double(), C.c_double()
+        _check(L.load().tlrmvn_server_wait(self.handle, int(rid), C.byref(lp), C.byref(er), C.byref(lat)),
+               "tlrmvn_server_wait")
+        return lp.value, er.value, lat.value
+
+    def stats(self) -> dict:
+        st = L.ServerStats()
+        _check(L.load().tlrmvn_server_stats(self.handle, C.byref(st)), "tlrmvn_server_stats")
+        return {k: getattr(st, k) for k, _ in L.ServerStats._fields_}
+
+    def close(self):
+        if self.handle and self.handle.value:
+            L.load().tlrmvn_server_free(self.handle)
+            self.handle = C.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 NOALLOC_MAX_SHIFTS = 65536
 
 

@@ -102,26 +102,24 @@ __global__ void __launch_bounds__(BATCH_T) k_batch(const BatchProblem* __restric
           fma16(acc, P.UT + (kr0 + kk) * P.ldbt + v0, W[(kr0 + kk) * BATCH_T + tid]);
         for (int u = 0; u < v0; u++)  // earlier variables of the tile
           fma16(acc, BTi + (int64_t)u * P.ldbt + v0, ys[u * ld + tid]);
-        float yb[BATCH_VB];
-#pragma unroll
-        for (int j = 0; j < BATCH_VB; j++) {
+        const int nb = min(BATCH_VB, mt - v0);
+#pragma unroll 1
+        for (int j = 0; j < nb; j++) {  // the block in order; acc[0] belongs to variable v
           const int v = v0 + j;
-          yb[j] = 0.0f;
-          if (v < mt) {
-            float sum = acc[j];
+          const float sum = acc[0];
+          const float iv = __ldg(invi + v);
+          const float at = (P.a[t0 + v] * rs - sum) * iv;
+          const float bt = (P.b[t0 + v] * rs - sum) * iv;
+          float w, wc;
+          lattice_wf(k * P.Q[t0 + v] + Ds[t0 + v], P.periodize, w, wc);
+          float lv, y;
+          sov_step_f32(at, bt, w, wc, lv, y);
+          lp += lv;
+          ys[v * ld + tid] = y;
+          const float* brow = BTi + (int64_t)v * P.ldbt + v + 1;  // B[v+1+i][v]
 #pragma unroll
-            for (int jj = 0; jj < j; jj++) sum = fmaf(__ldg(BTi + (int64_t)(v0 + jj) * P.ldbt + v), yb[jj], sum);
-            const float iv = __ldg(invi + v);
-            const float at = (P.a[t0 + v] * rs - sum) * iv;
-            const float bt = (P.b[t0 + v] * rs - sum) * iv;
-            float w, wc;
-            lattice_wf(k * P.Q[t0 + v] + Ds[t0 + v], P.periodize, w, wc);
-            float lv, y;
-            sov_step_f32(at, bt, w, wc, lv, y);
-            lp += lv;
-            yb[j] = y;
-            ys[v * ld + tid] = y;
-          }
+          for (int i = 0; i < BATCH_VB - 1; i++) acc[i] = fmaf(__ldg(brow + i), y, acc[i + 1]);
+          acc[BATCH_VB - 1] = 0.0f;
         }
       }
       const int64_t kc0 = P.kcol_off[i], Kc = P.kcol_off[i + 1] - kc0;
@@ -200,7 +198,11 @@ int ensure_float_tiles(Factor& F, cudaStream_t st);  // prob.cu: BT32 / inv32
 
 static int make_batch_copies(Factor& F, BatchCopies& C, cudaStream_t st) {
   const int r = F.r, m = F.m;
-  TLR_CHECK(ensure_float_tiles(F, st));
+  {
+    std::lock_guard<std::mutex> lk(F.copy_mu);
+    TLR_CHECK(ensure_float_tiles(F, st));
+    TLR_CUDA(cudaStreamSynchronize(st));
+  }
   std::vector<int64_t> vt_off(r + 1, 0);
   std::vector<int32_t> kcpad(r);
   for (int j = 0; j < r; j++) {

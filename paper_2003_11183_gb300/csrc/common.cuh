@@ -6,6 +6,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 #include <math.h>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -93,6 +94,8 @@ struct Factor {
   // lattice generators for n + 1 coordinates (device), and the permutation (device)
   uint64_t* Q = nullptr;
   int64_t* dperm = nullptr;
+  // guards the lazily made copies when several streams use the factor at once
+  std::mutex copy_mu;
 
   int64_t tsize(int t) const { return tile_off[t + 1] - tile_off[t]; }
   int64_t krow(int i) const { return krow_off[i + 1] - krow_off[i]; }

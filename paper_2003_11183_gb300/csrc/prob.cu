@@ -163,30 +163,45 @@ struct DiagArgs32 {
 // One thread per sample; 16 variables per pass: the partial sums of a block of
 // 16 variables over all earlier variables of the (sub-)tile are accumulated
 // together (each y_u read once per block, B read as four broadcast float4 per
-// u), then the block's 16 x 16 triangle and special functions run in order.
+// u); then the block's variables run in order in a rolled loop, each pushing
+// its y into the partial sums of the block's later variables through a
+// shifting window of accumulators (so the special-function code exists once).
 constexpr int DIAG_VB = 16;
 // Sub-tile of the float sweep: couplings between sub-tiles of one diagonal tile
 // are applied as a dense product before the sweep of each sub-tile.
 constexpr int DIAG_SUB = 128;
+// Extra floats after the transposed tiles: the accumulator window may read up
+// to DIAG_VB - 1 entries past the last row.
+constexpr int DIAG_PAD = 32;
 __global__ void k_diag_f32(DiagArgs32 p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* ys = reinterpret_cast<float*>(smem_raw);
+  __shared__ float s_a[DIAG_SUB], s_b[DIAG_SUB], s_inv[DIAG_SUB];
+  __shared__ uint64_t s_q[DIAG_SUB];
   const int bd = blockDim.x, tid = threadIdx.x, ld = bd + 1;
   const int64_t c0 = (int64_t)blockIdx.x * bd;
   const int64_t c = c0 + tid;
+  const int mt = p.mt;
+  for (int t = tid; t < mt; t += bd) {
+    s_a[t] = p.a[t];
+    s_b[t] = p.b[t];
+    s_inv[t] = p.inv[t];
+    s_q[t] = p.Q[p.coord0 + t];
+  }
+  __syncthreads();
   if (c < p.C) {
     const int64_t g = p.sample0 + c;
     const int64_t s = g / p.N;
     const uint64_t k = (uint64_t)(g - s * p.N) + 1;
     const uint64_t* Ds = p.D + s * p.ldD + p.coord0;
-    const uint64_t* Qt = p.Q + p.coord0;
     const float rs = p.rs ? p.rs[c] : 1.0f;
-    const int mt = p.mt;
     float lp = 0.0f;
     for (int v0 = 0; v0 < mt; v0 += DIAG_VB) {
+      const int nb = min(DIAG_VB, mt - v0);
       float acc[DIAG_VB];
 #pragma unroll
-      for (int j = 0; j < DIAG_VB; j++) acc[j] = 0.0f;
+      for (int j = 0; j < DIAG_VB; j++)
+        acc[j] = (p.Delta && j < nb) ? p.Delta[(int64_t)(v0 + j) * p.ldd + c] : 0.0f;
       const float* bcol = p.BT + v0;
 #pragma unroll 2
       for (int u = 0; u < v0; u++) {
@@ -210,28 +225,25 @@ __global__ void k_diag_f32(DiagArgs32 p) {
         acc[14] = fmaf(q3.z, yu, acc[14]);
         acc[15] = fmaf(q3.w, yu, acc[15]);
       }
-      float yb[DIAG_VB];
-#pragma unroll
-      for (int j = 0; j < DIAG_VB; j++) {
+#pragma unroll 1
+      for (int j = 0; j < nb; j++) {
         const int v = v0 + j;
-        yb[j] = 0.0f;
-        if (v < mt) {
-          float sum = acc[j];
+        const float sum = acc[0];  // shifts + earlier variables, for variable v
+        const float iv = s_inv[v];
+        const float at = (s_a[v] * rs - sum) * iv;
+        const float bt = (s_b[v] * rs - sum) * iv;
+        float w, wc;
+        lattice_wf(k * s_q[v] + Ds[v], p.periodize, w, wc);
+        float lv, y;
+        sov_step_f32(at, bt, w, wc, lv, y);
+        lp += lv;
+        ys[v * ld + tid] = y;
+        if (p.Yv) p.Yv[(int64_t)v * p.ldyv + c] = y;
+        // window shift: acc[i] <- acc[i+1] + B[v+1+i][v] y
+        const float* brow = p.BT + (int64_t)v * p.ldbt + v + 1;
 #pragma unroll
-          for (int jj = 0; jj < j; jj++) sum = fmaf(__ldg(p.BT + (int64_t)(v0 + jj) * p.ldbt + v), yb[jj], sum);
-          const float dl = p.Delta ? p.Delta[(int64_t)v * p.ldd + c] : 0.0f;
-          const float iv = __ldg(p.inv + v);
-          const float at = (p.a[v] * rs - dl - sum) * iv;
-          const float bt = (p.b[v] * rs - dl - sum) * iv;
-          float w, wc;
-          lattice_wf(k * Qt[v] + Ds[v], p.periodize, w, wc);
-          float lv, y;
-          sov_step_f32(at, bt, w, wc, lv, y);
-          lp += lv;
-          yb[j] = y;
-          ys[v * ld + tid] = y;
-          if (p.Yv) p.Yv[(int64_t)v * p.ldyv + c] = y;
-        }
+        for (int i = 0; i < DIAG_VB - 1; i++) acc[i] = fmaf(__ldg(brow + i), y, acc[i + 1]);
+        acc[DIAG_VB - 1] = 0.0f;
       }
     }
     if (p.first) p.logP[g] = (double)lp;
@@ -360,14 +372,24 @@ int ensure_float_tiles(Factor& F, cudaStream_t st) {
   k_convert<double, float><<<blocks_for(nb, 256), 256, 0, st>>>(F.B, F.B32, nb);
   F.ldbt = ((int64_t)F.m + DIAG_VB - 1) / DIAG_VB * DIAG_VB;
   const int64_t nt = (int64_t)F.r * F.m * F.ldbt;
-  TLR_CHECK(dalloc(&F.BT32, nt));
+  TLR_CHECK(dalloc(&F.BT32, nt + DIAG_PAD));
+  TLR_CUDA(cudaMemsetAsync(F.BT32 + nt, 0, DIAG_PAD * sizeof(float), st));
   TLR_CHECK(dalloc(&F.inv32, (size_t)F.r * F.m));
   k_transpose_tiles<<<blocks_for(nt, 256), 256, 0, st>>>(F.B, F.m, F.ldbt, nt, F.BT32, F.inv32);
   TLR_CUDA(cudaGetLastError());
   return TLRMVN_OK;
 }
 
+// Makes the copies a precision needs; the first caller makes them (and waits for
+// them) under the factor's lock, so concurrent streams never see a partial copy.
+static int ensure_copies_locked(Factor& F, int precision, cudaStream_t st);
 static int ensure_copies(Factor& F, int precision, cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(F.copy_mu);
+  TLR_CHECK(ensure_copies_locked(F, precision, st));
+  TLR_CUDA(cudaStreamSynchronize(st));
+  return TLRMVN_OK;
+}
+static int ensure_copies_locked(Factor& F, int precision, cudaStream_t st) {
   const int64_t nu = (int64_t)F.m * F.ktot;
   if (precision != TLRMVN_FP64) TLR_CHECK(ensure_float_tiles(F, st));
   if (precision == TLRMVN_FP32 && !F.U32 && nu) {
@@ -479,6 +501,25 @@ struct Scratch {
   }
 };
 
+// Samples per pass: opts.sample_chunk, else as many as keep the projection
+// buffer W within 8 GiB (SIMT paths) or 32 GiB (bf16 path); a multiple of 256.
+static int64_t round_chunk(int64_t C, int64_t S) {
+  C = std::min<int64_t>(C, S);
+  return (C + 255) / 256 * 256;
+}
+static int64_t chunk_simt(const tlrmvn_opts& o, int64_t S, int64_t ktot, int m, int64_t es) {
+  if (o.sample_chunk > 0) return round_chunk(o.sample_chunk, S);
+  const double budget = 8.0 * (1ull << 30);
+  const double per = (double)(ktot + 2 * m) * es + 16.0;
+  return round_chunk((int64_t)std::max(256.0, std::min((double)S, budget / per)), S);
+}
+static int64_t chunk_bf16(const tlrmvn_opts& o, int64_t S, int64_t kw, int64_t my, int m) {
+  if (o.sample_chunk > 0) return round_chunk(o.sample_chunk, S);
+  const double budget = 32.0 * (1ull << 30);
+  const double per = (double)kw * 2 + (double)my * 2 + (double)m * 8 + 16.0;
+  return round_chunk((int64_t)std::max(256.0, std::min((double)S, budget / per)), S);
+}
+
 // Limits in factor order, in float64 and (for the float paths) float32.
 struct Lims {
   const double* a;
@@ -557,15 +598,7 @@ static int run_chunks(Factor& F, const T* Bt, const T* Ut, const T* Vt, const Li
   const int64_t M = o.n_shifts, N = o.n_points, S = M * N;
   const int m = F.m;
   const bool f32 = sizeof(T) == 4;
-  int64_t C = o.sample_chunk > 0 ? o.sample_chunk : 0;
-  if (C <= 0) {
-    // keep W (ktot x C) within ~8 GiB
-    const double budget = 8.0 * (1ull << 30);
-    double per = (double)(F.ktot + 2 * m) * sizeof(T) + 16.0;
-    C = (int64_t)std::max(256.0, std::min((double)S, budget / per));
-  }
-  C = std::min<int64_t>(C, S);
-  C = (C + 255) / 256 * 256;
+  const int64_t C = chunk_simt(o, S, F.ktot, m, sizeof(T));
   T *W = nullptr, *Dl = nullptr;
   YT* Y = nullptr;
   double* rs = nullptr;
@@ -650,15 +683,7 @@ static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opt
                            double* logP, Scratch& sc, cudaStream_t st, Prof& pf) {
   const int64_t M = o.n_shifts, N = o.n_points, S = M * N;
   const int m = F.m;
-  int64_t C = o.sample_chunk > 0 ? o.sample_chunk : 0;
-  if (C <= 0) {
-    // keep W16 within ~32 GiB
-    const double budget = 32.0 * (1ull << 30);
-    double per = (double)F.kw16 * 2 + (double)F.my16 * 2 + (double)m * 4 + 16.0;
-    C = (int64_t)std::max(256.0, std::min((double)S, budget / per));
-  }
-  C = std::min<int64_t>(C, S);
-  C = (C + 255) / 256 * 256;
+  const int64_t C = chunk_bf16(o, S, F.kw16, F.my16, m);
   __nv_bfloat16 *W = nullptr, *Y = nullptr;
   float *Dl = nullptr, *Yv = nullptr;
   float* rs32 = nullptr;
@@ -729,8 +754,28 @@ static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opt
   return TLRMVN_OK;
 }
 
-static int prob_impl(Factor& F, const double* a_dev, const double* b_dev, double nu, const tlrmvn_opts& o,
-                     double* out2_dev, double* ell_dev_out, double* per_sample_dev, cudaStream_t st) {
+// Bytes of stream-ordered scratch one tlrmvn_prob call takes (used for admission
+// by the serving loop); mirrors the buffers of prob_impl and the chunk loops.
+int64_t prob_scratch_bytes(const Factor& F, const tlrmvn_opts& o) {
+  const int64_t M = o.n_shifts, N = o.n_points, S = M * N, n = F.n, m = F.m;
+  int64_t bytes = n * (8 * 2 + 4 * 2) + M * (n + 1) * 8 + M * 8 + S * 8 + 256;
+  if (o.precision == TLRMVN_BF16_SHIFT) {
+    int64_t kw = 0;
+    for (int i = 0; i < F.r; i++) kw += (F.krow(i) + 63) / 64 * 64;
+    kw = std::max<int64_t>(kw, 64);
+    const int64_t my = (m + 63) / 64 * 64;
+    const int64_t C = chunk_bf16(o, S, kw, my, m);
+    bytes += C * (kw * 2 + my * 2 + m * 8 + 4);
+  } else {
+    const int64_t es = o.precision == TLRMVN_FP64 ? 8 : 4;
+    const int64_t C = chunk_simt(o, S, F.ktot, m, es);
+    bytes += C * ((F.ktot + 2 * m) * es + 8);
+  }
+  return bytes;
+}
+
+int prob_impl(Factor& F, const double* a_dev, const double* b_dev, double nu, const tlrmvn_opts& o,
+              double* out2_dev, double* ell_dev_out, double* per_sample_dev, cudaStream_t st) {
   const int64_t M = o.n_shifts, N = o.n_points, S = M * N, n = F.n;
   Scratch sc(st);
   double *ap = nullptr, *bp = nullptr, *logP = nullptr, *ell = nullptr;

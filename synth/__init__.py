@@ -94,12 +94,13 @@ class Workload:
         return self.xy.shape[0]
 
 
-def workload(c: int) -> Workload:
+def workload(c: int, n_side: int | None = None) -> Workload:
     """The five workload shapes, numbered 1..5, at full size.
 
     1: MVN n=256, 16x16 grid, exp beta=0.1, nugget 1e-8, b~U(0,1), m=64, tol 1e-8, 20x500, FP64
     2: MVN n=16,384, 128x128 grid, exp beta=0.3 + Matern 1.5 ell=0.1, b~U(0,1), m=256, tol 1e-5, 20x5000
     3: MVT nu=7, n=65,536, 256x256 grid, exp beta=0.1, b~N(1,0.5^2), m=512, tol 1e-4, rank<=64, 20x5000
+    n_side (workload 3 only): a smaller grid of the same family, for profiling captures.
     """
     if c == 1:
         xy = jittered_grid(16, 1000 + c)
@@ -112,10 +113,12 @@ def workload(c: int) -> Workload:
         return Workload("mvn_n16384_expmatern", xy, KERNEL_EXP_MATERN15, (0.3, 0.1), 1e-8, a, b, 256, 1e-5, 256,
                         math.inf, 20, 5000, lattice_shifts(20, 16385, 3000 + c), reorder=2)
     if c == 3:
-        xy = jittered_grid(256, 1000 + c)
-        a, b = limits_normal(65536, 2000 + c, 1.0, 0.5)
-        return Workload("mvt7_n65536_exp", xy, KERNEL_EXP, (0.1,), 1e-8, a, b, 512, 1e-4, 64,
-                        7.0, 20, 5000, lattice_shifts(20, 65537, 3000 + c), reorder=1)
+        g = 256 if n_side is None else n_side
+        xy = jittered_grid(g, 1000 + c)
+        a, b = limits_normal(g * g, 2000 + c, 1.0, 0.5)
+        name = "mvt7_n65536_exp" if g == 256 else f"mvt7_n{g * g}_exp"
+        return Workload(name, xy, KERNEL_EXP, (0.1,), 1e-8, a, b, 512, 1e-4, 64,
+                        7.0, 20, 5000, lattice_shifts(20, g * g + 1, 3000 + c), reorder=1)
     raise ValueError(f"unknown workload {c}")
 
 

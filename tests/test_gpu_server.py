@@ -1,0 +1,83 @@
+"""GPU: the serving loop (tlrmvn_server_*): continuous admission, overlap on the
+device, and results that are the same alone and in the mix."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2003_11183_gb300 as tl
+    ws, fs = [], []
+    for seed, (side, m) in enumerate([(24, 64), (32, 128), (40, 128)]):
+        w = synth.small_workload(side, m, 80 + seed, tol=1e-6)
+        fs.append(tl.tlrmvn_factor_kernel(w.xy, w.kernel, w.params, w.nugget, w.a, w.b, w.m, w.tol, 0, 2))
+        ws.append(w)
+    return tl, ws, fs
+
+
+def _req(w, k, rng):
+    b = rng.uniform(0.0, 1.0, w.n)
+    return np.full(w.n, -np.inf), b, [math.inf, 7.0, 3.0][k % 3], [1, 2][k % 2]
+
+
+def test_same_alone_and_in_the_mix(env):
+    tl, ws, fs = env
+    rng = np.random.default_rng(0)
+    reqs = []
+    for k in range(12):
+        f = k % 3
+        a, b, nu, prec = _req(ws[f], k, rng)
+        reqs.append((f, a, b, nu, prec))
+    kw = dict(n_shifts=4, n_points=2000, seed=11)
+    # alone: one request at a time
+    alone = []
+    srv = tl.Server(fs, lanes=4, memory_budget=8 << 30)
+    for f, a, b, nu, prec in reqs:
+        rid = srv.submit(f, a, b, nu, prec, **kw)
+        alone.append(srv.wait(rid)[:2])
+    # in the mix: all submitted at once
+    ids = [srv.submit(f, a, b, nu, prec, **kw) for f, a, b, nu, prec in reqs]
+    mixed = [srv.wait(i)[:2] for i in ids]
+    st = srv.stats()
+    srv.close()
+    for (l1, e1), (l2, e2) in zip(alone, mixed):
+        assert l1 == l2 and (e1 == e2 or (math.isnan(e1) and math.isnan(e2)))
+    assert st["completed"] == 24
+    assert st["peak_in_flight"] > 1 and st["overlapped"] > 0
+    assert st["p99_ms"] >= st["p50_ms"] > 0
+    # and the same as the plain entry point
+    f, a, b, nu, prec = reqs[0]
+    lp, err, _, _ = tl.tlrmvn_prob(fs[f], a, b, nu, prec, **kw)
+    assert lp == alone[0][0] and err == alone[0][1]
+
+
+def test_admission_by_memory_budget(env):
+    tl, ws, fs = env
+    rng = np.random.default_rng(1)
+    a, b, nu, prec = _req(ws[2], 0, rng)
+    # a 2,048-sample chunk bounds one request's scratch near 9 MB: 12 MB admits one at a time
+    kw = dict(n_shifts=4, n_points=4000, seed=3, sample_chunk=2048)
+    srv = tl.Server(fs, lanes=4, memory_budget=12 << 20)
+    ids = [srv.submit(2, a, b, nu, tl.FP32, **kw) for _ in range(6)]
+    res = [srv.wait(i) for i in ids]
+    st = srv.stats()
+    assert st["peak_in_flight"] == 1 and 0 < st["peak_bytes"] <= 12 << 20
+    assert all(r[0] == res[0][0] for r in res)
+    with pytest.raises(tl.TlrmvnError) as e:
+        srv.submit(2, a, b, nu, tl.FP32, n_shifts=20, n_points=200000)
+    assert e.value.status == tl.E_NOMEM
+    with pytest.raises(tl.TlrmvnError) as e:
+        srv.submit(7, a, b, nu, tl.FP32, **kw)
+    assert e.value.status == tl.E_INVAL
+    srv.close()

@@ -40,7 +40,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default=os.environ.get("TLRMVN_BENCH_PRECISION", "fp32"), choices=list(PRECISIONS))
+    ap.add_argument("--precision", default="bf16", choices=list(PRECISIONS),
+                    help="bf16: float32 sweep with bf16 tensor-core shifts (the workload's precision)")
     ap.add_argument("--workload", type=int, default=3)
     ap.add_argument("--points", type=int, default=0, help="override points per shift (0 = workload's)")
     ap.add_argument("--shifts", type=int, default=0, help="override the number of shifts (0 = workload's)")
@@ -48,6 +49,8 @@ def parse():
                     help="grid side of a smaller problem of the same family (profiling captures only)")
     ap.add_argument("--no-baselines", action="store_true", help="skip FP64-path and CPU-oracle legs")
     ap.add_argument("--count", type=int, default=256, help="problems of the batched workload (--workload 4)")
+    ap.add_argument("--requests", type=int, default=400, help="requests of the serving workload (--workload 5)")
+    ap.add_argument("--rate", type=float, default=0.0, help="arrivals per second (--workload 5; 0 = measured)")
     return ap.parse_args()
 
 
@@ -225,7 +228,9 @@ def run_ours(args):
     a = torch.tensor(w.a, dtype=torch.float64, device="cuda")
     b = torch.tensor(w.b, dtype=torch.float64, device="cuda")
     out = torch.zeros(2, dtype=torch.float64, device="cuda")
-    kw = dict(nu=w.nu, precision=prec, n_shifts=w.n_shifts, n_points=w.n_points, shifts=w.shifts, stream=stream)
+    per_shift = torch.zeros(w.n_shifts, dtype=torch.float64, device="cuda")
+    kw = dict(nu=w.nu, precision=prec, n_shifts=w.n_shifts, n_points=w.n_points, shifts=w.shifts, stream=stream,
+              per_shift=per_shift)
 
     for _ in range(args.warmup):
         tl.tlrmvn_prob_device(F, a, b, out, **kw)
@@ -248,7 +253,12 @@ def run_ours(args):
     ms = ev0.elapsed_time(ev1) / args.steps
     ms = allmax(ws, ms)
     logp, err = out.tolist()
-    kern = {tl.KC_NAMES[c]: tl.tlrmvn_profile_get(c) for c in range(5)}
+    if ws > 1:
+        # replicas: pool the per-shift log means of all ranks (one gather of M doubles per rank)
+        import torch.distributed as dist
+        from paper_2003_11183_gb300 import replicas
+        logp, err = replicas.gather_and_combine(per_shift.cpu().numpy(), group=dist.new_group(backend="gloo"))
+    kern = {tl.KC_NAMES[c]: tl.tlrmvn_profile_get(c) for c in range(len(tl.KC_NAMES))}
     launches = sum(v[1] for v in kern.values())
     sd = w.n * w.n_shifts * w.n_points
     value = ws * sd / (ms / 1e3)
@@ -259,43 +269,52 @@ def run_ours(args):
     for _ in range(max(2, min(args.steps, 3))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        tl.tlrmvn_prob(F, w.a, w.b, **kw)
+        tl.tlrmvn_prob(F, w.a, w.b, **{k: v for k, v in kw.items() if k != "per_shift"})
         t_e2e.append(time.perf_counter() - t0)
     e2e = ws * sd / statistics.mean(t_e2e)
 
-    # roofline of the dominant kernel class
+    # roofline of every kernel class; the line reports the dominant one.
+    # Algorithmic flops per sample (2 per multiply-add), tiles of size mt:
+    #   diag   sweep triangle: per 128-variable sub-tile of size mq, mq (mq - 1)
+    #          (float paths; the float64 path sweeps the whole tile: mt (mt - 1))
+    #   couple in-tile coupling of sub-tile q: 2 mq q0
+    #   shift / vproj: 2 m K_total each
     pk, pk_kind = peaks()
-    dom = max(("shift", "diag", "vproj"), key=lambda c: kern[c][0])
-    roof = None
     m, n, C = w.m, w.n, w.n_shifts * w.n_points
-    if dom == "diag":
-        r = info["r"]
-        sizes = [min(m, n - t * m) for t in range(r)]
-        flops = sum(s * (s - 1) for s in sizes) * C * args.steps  # one FMA per (v, u < v) per sample
-        t = kern["diag"][0] / 1e3
-        ach = flops / t / 1e12
-        roof = {"kernel": "k_diag", "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP32_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
-    else:
-        K = info["k_total"]
-        flops = 2.0 * m * K * C * args.steps
-        t = kern[dom][0] / 1e3
-        ach = flops / t / 1e12
-        if prec == 2:
+    sizes = [min(m, n - t * m) for t in range(info["r"])]
+    sub = 128 if prec != 0 else m
+    per = {"diag": 0.0, "couple": 0.0, "shift": 2.0 * m * info["k_total"], "vproj": 2.0 * m * info["k_total"]}
+    for mt in sizes:
+        for q0 in range(0, mt, sub):
+            mq = min(sub, mt - q0)
+            per["diag"] += mq * (mq - 1)
+            per["couple"] += 2.0 * mq * q0
+    fp32_peak = {"bound": "alu", "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (derived)"}
+    classes = {}
+    for cls in ("diag", "couple", "shift", "vproj"):
+        t = kern[cls][0] / 1e3
+        if t <= 0:
+            continue
+        ach = per[cls] * C * args.steps / t / 1e12
+        if cls in ("shift", "vproj") and prec == 2:
             p = pk.get("bf16_tflops_sustained", 1700.0)
-            roof = {"kernel": dom, "bound": "tensor", "achieved": ach, "peak": p, "unit": "TFLOP/s", "frac": ach / p,
-                    "traffic": None, "peak_source": f"bf16 sustained, {pk_kind}"}
+            pkd = {"bound": "tensor", "peak": p, "unit": "TFLOP/s", "peak_source": f"bf16 sustained, {pk_kind}"}
         else:
-            roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": ach / FP32_PEAK_TFLOPS, "traffic": None,
-                    "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+            pkd = fp32_peak
+        classes[cls] = dict(pkd, achieved=ach, frac=ach / pkd["peak"], ms_per_step=kern[cls][0] / args.steps,
+                            kernel={"diag": "k_diag_f32", "couple": "k_gemm_nn", "shift": "k_gemm_tc",
+                                    "vproj": "k_gemm_tc"}[cls] if prec == 2 else cls)
+    dom = max(classes, key=lambda c: classes[c]["ms_per_step"])
+    roof = dict(classes[dom], traffic=None)
+    roof["note"] = ("achieved counts the multiply-adds only; the sweep's special functions "
+                    "(about 3/4 of its instructions) are not in the algorithmic flops")
 
     extra = {}
     if rank == 0 and not args.no_baselines:
         # the same library's FP64 path on a bounded sample (1 shift x 1000 points)
         pts64 = min(1000, w.n_points)
-        kw64 = dict(kw, precision=0, n_shifts=1, n_points=pts64, shifts=w.shifts[:1])
+        kw64 = dict(kw, precision=0, n_shifts=1, n_points=pts64, shifts=w.shifts[:1], per_shift=None)
         tl.tlrmvn_prob_device(F, a, b, out, **kw64)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -328,7 +347,7 @@ def run_ours(args):
                            "l2": "inputs larger than L2 (factor and W buffer)"},
                 "clocks": clk,
                 "e2e": {"value": e2e, "unit": "sample-dims/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 16},
-                "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
+                "gpu_launches": launches, "roofline": roof, "kernel_classes": classes, "cpu_baseline": cpu,
                 "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kern.items()},
                 "factor_seconds": factor_s, "logp": logp, "err": err}
         line.update(extra)
@@ -386,12 +405,94 @@ def run_batched(args):
     return 0
 
 
+def run_serving(args):
+    """Serving workload: 8 resident factors (n = 1,024 ... 16,384 on jittered grids, Matern 1/2 and
+    3/2 kernels), a Poisson stream of requests with fresh b_i ~ U(0,1), nu in {3, 7, inf},
+    FP32 and BF16-shift classes, 10 shifts x 1,000 points each; 4 lanes, 16 GiB scratch budget.
+    The arrival rate is `--rate` requests/s, or (default) the rate a single lane would sustain,
+    measured from the requests run alone."""
+    import threading
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2003_11183_gb300 as tl
+    import synth
+    sides = [32, 45, 64, 64, 90, 90, 128, 128]          # n = 1,024 ... 16,384
+    kernels = [(tl.KERNEL_EXP, (0.1,)), (tl.KERNEL_MATERN15, (0.05,))] * 4
+    factors, sizes = [], []
+    t0 = time.perf_counter()
+    for f, g in enumerate(sides):
+        xy = synth.jittered_grid(g, 5000 + f)
+        n = g * g
+        a, b = synth.limits_uniform(n, 6000 + f)
+        kern, prm = kernels[f]
+        factors.append(tl.tlrmvn_factor_kernel(xy, kern, prm, 1e-6, a, b, 128 if n <= 4096 else 256, 1e-5, 0,
+                                               tl.REORDER_BLOCK))
+        sizes.append(n)
+    factor_s = time.perf_counter() - t0
+    rng = np.random.default_rng(7000)
+    R = args.requests
+    reqs = []
+    for q in range(R):
+        f = int(rng.integers(0, len(factors)))
+        reqs.append((f, np.full(sizes[f], -np.inf), rng.uniform(0.0, 1.0, sizes[f]), [3.0, 7.0, math.inf][q % 3],
+                     tl.FP32 if q % 2 == 0 else tl.BF16_SHIFT))
+    kw = dict(n_shifts=10, n_points=1000)
+    srv = tl.Server(factors, lanes=4, memory_budget=16 << 30)
+    alone = []
+    for q, (f, a, b, nu, prec) in enumerate(reqs[:16]):  # warm-up and the alone service time
+        rid = srv.submit(f, a, b, nu, prec, seed=q, **kw)
+        alone.append(srv.wait(rid)[2])
+    service = statistics.mean(alone[4:])
+    rate = args.rate if args.rate > 0 else 1e3 / service
+    srv.close()
+    srv = tl.Server(factors, lanes=4, memory_budget=16 << 30)
+    gaps = rng.exponential(1.0 / rate, size=R)
+    ids = [None] * R
+    clocks = Clocks(0)
+    clocks.start()
+    t_start = time.perf_counter()
+
+    def submitter():
+        t = time.perf_counter()
+        for q, (f, a, b, nu, prec) in enumerate(reqs):
+            t += gaps[q]
+            dt = t - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            ids[q] = srv.submit(f, a, b, nu, prec, seed=q, **kw)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    th.join()
+    lat = [srv.wait(i)[2] for i in ids]
+    makespan = time.perf_counter() - t_start
+    clk = clocks.stop()
+    st = srv.stats()
+    srv.close()
+    sd = sum(sizes[f] for f, *_ in reqs) * kw["n_shifts"] * kw["n_points"]
+    line = {"metric": "served QMC sample-dims/sec and p50/p99 latency", "value": sd / makespan,
+            "unit": "sample-dims/s", "n_gpus": 1, "steps": R, "warmup": 16, "ms_per_step": makespan * 1e3 / R,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 | f32+bf16",
+            "data": "synthetic",
+            "config": {"workload": "serving_8_factors_n1024_16384", "requests": R, "rate_per_s": rate,
+                       "lanes": 4, "memory_budget_gib": 16, "shifts": 10, "points": 1000,
+                       "service_ms_alone_mean": service},
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "server_stats": st, "clocks": clk, "factor_seconds": factor_s}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == 4:
         return run_batched(args)
+    if args.workload == 5:
+        return run_serving(args)
     return run_ours(args)
 
 

@@ -209,6 +209,9 @@ int tlrmvn_server_submit(tlrmvn_server_t server, int factor, const double* a, co
 int tlrmvn_server_wait(tlrmvn_server_t server, int64_t request_id, double* logp, double* err, double* latency_ms);
 int tlrmvn_server_stats(tlrmvn_server_t server, tlrmvn_server_stats_t* out);
 int tlrmvn_server_free(tlrmvn_server_t server);
+/* Device scratch (bytes) one request with these options takes on this factor:
+ * what the server charges against its budget (also a tlrmvn_prob call's peak). */
+int tlrmvn_prob_scratch_bytes(tlrmvn_factor_t f, const tlrmvn_opts* opts, int64_t* bytes);
 
 /* ---- estimator without device allocation ------------------------------ */
 
@@ -244,7 +247,8 @@ const char* tlrmvn_last_error(void);   /* thread-local detail of the last failur
 #define TLRMVN_KC_VPROJ   2  /* projections  W_col_i = V_i^T y_i                    */
 #define TLRMVN_KC_CHI     3  /* Student-t scale chi_nu^-1(w0)/sqrt(nu)              */
 #define TLRMVN_KC_REDUCE  4  /* per-shift and cross-shift log-sum reductions        */
-#define TLRMVN_KC_COUNT   5
+#define TLRMVN_KC_COUPLE  5  /* in-tile coupling of 128-variable sub-tiles (FP32)   */
+#define TLRMVN_KC_COUNT   6
 
 /* Process-wide kernel timing: when enabled, every integrand launch is bracketed
  * by CUDA events on its stream and, once the call has completed, its device

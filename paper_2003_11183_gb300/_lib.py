@@ -52,6 +52,7 @@ SIGNATURES = {
     "tlrmvn_server_wait": (C.c_int, [C.c_void_p, C.c_int64, c_double_p, c_double_p, c_double_p]),
     "tlrmvn_server_stats": (C.c_int, [C.c_void_p, C.c_void_p]),
     "tlrmvn_server_free": (C.c_int, [C.c_void_p]),
+    "tlrmvn_prob_scratch_bytes": (C.c_int, [C.c_void_p, C.POINTER(Opts), C.POINTER(C.c_int64)]),
     "tlrmvn_estimate_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tlrmvn_profile_enable": (C.c_int, [C.c_int]),
     "tlrmvn_profile_reset": (C.c_int, []),

@@ -173,6 +173,16 @@ def tlrmvn_prob_batch(factors, a_list, b_list, nu, n_shifts: int, n_points: int,
         plan.close()
 
 
+def tlrmvn_prob_scratch_bytes(f: Factor, precision: int = FP32, n_shifts: int = 10, n_points: int = 1000,
+                              sample_chunk: int = 0) -> int:
+    """Device scratch bytes of one request with these options on factor f."""
+    n = tlrmvn_factor_info(f)["n"]
+    o, _ = _opts(precision, n_shifts, n_points, True, None, 0, sample_chunk, None, n)
+    nb = C.c_int64()
+    _check(L.load().tlrmvn_prob_scratch_bytes(f.handle, C.byref(o), C.byref(nb)), "tlrmvn_prob_scratch_bytes")
+    return nb.value
+
+
 class Server:
     """tlrmvn_server_t: resident factors, requests admitted as lanes and memory free up."""
 
@@ -190,8 +200,8 @@ class Server:
                n_points: int = 1000, shifts=None, seed: int = 0, periodize: bool = True, sample_chunk: int = 0) -> int:
         a = _f64(a)
         b = _f64(b)
-        o, keep = _opts(precision, n_shifts, n_points, periodize, shifts, seed, sample_chunk, None,
-                        self.sizes[factor])
+        n = self.sizes[factor] if 0 <= factor < len(self.sizes) else 0  # the library rejects a bad index
+        o, keep = _opts(precision, n_shifts, n_points, periodize, shifts, seed, sample_chunk, None, n)
         rid = C.c_int64()
         _check(L.load().tlrmvn_server_submit(self.handle, int(factor), _dp(a), _dp(b), float(nu), C.byref(o),
                                              C.byref(rid)), "tlrmvn_server_submit")
@@ -236,8 +246,8 @@ def tlrmvn_estimate_noalloc(per_sample, n_shifts: int, n_points: int, out, per_s
                                             _stream_ptr(stream)), "tlrmvn_estimate_noalloc")
 
 
-KC_SHIFT, KC_DIAG, KC_VPROJ, KC_CHI, KC_REDUCE = 0, 1, 2, 3, 4
-KC_NAMES = ("shift", "diag", "vproj", "chi", "reduce")
+KC_SHIFT, KC_DIAG, KC_VPROJ, KC_CHI, KC_REDUCE, KC_COUPLE = 0, 1, 2, 3, 4, 5
+KC_NAMES = ("shift", "diag", "vproj", "chi", "reduce", "couple")
 
 
 def tlrmvn_profile_enable(on: bool):

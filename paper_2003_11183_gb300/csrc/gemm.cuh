@@ -64,10 +64,116 @@ __global__ void __launch_bounds__(256) k_gemm_nn(int M, int64_t N, int64_t K, co
   }
 }
 
+// float32 C = A B (+ C): 128 x 128 output tile per 256-thread block, 8 x 8 per
+// thread (two 4 x 4 quadrants so that shared-memory reads are float4), K in
+// steps of 8 with the next step's tile prefetched into registers while the
+// current one is multiplied (shared memory double-buffered, one barrier per step).
+// Requires lda, ldb, ldc multiples of 4, 16-byte aligned A, B, C and K a multiple of 8.
+static __global__ void __launch_bounds__(256) k_sgemm128(int M, int64_t N, int K, const float* __restrict__ A, int64_t lda,
+                                                  const float* __restrict__ B, int64_t ldb, float* __restrict__ C,
+                                                  int64_t ldc, const int32_t* __restrict__ rowmap, int accumulate) {
+  __shared__ __align__(16) float As[2][8][128];
+  __shared__ __align__(16) float Bs[2][8][128];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int m0 = blockIdx.y * 128;
+  const int64_t n0 = (int64_t)blockIdx.x * 128;
+  const int am = tid >> 1, ak = (tid & 1) * 4;   // A: row, first k of a float4
+  const int bk = tid >> 5, bn = (tid & 31) * 4;  // B: k row, first column of a float4
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; i++)
+#pragma unroll
+    for (int j = 0; j < 8; j++) acc[i][j] = 0.0f;
+  float4 ra, rb;
+  auto load = [&](int k0) {
+    const int gm = m0 + am;
+    ra = (gm < M) ? *reinterpret_cast<const float4*>(A + (int64_t)gm * lda + k0 + ak) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int64_t gn = n0 + bn;
+    const float* brow = B + (int64_t)(k0 + bk) * ldb;
+    if (gn + 3 < N) {
+      rb = *reinterpret_cast<const float4*>(brow + gn);
+    } else {
+      rb.x = gn < N ? brow[gn] : 0.f;
+      rb.y = gn + 1 < N ? brow[gn + 1] : 0.f;
+      rb.z = gn + 2 < N ? brow[gn + 2] : 0.f;
+      rb.w = 0.f;
+    }
+  };
+  auto store = [&](int buf) {
+    As[buf][ak][am] = ra.x;
+    As[buf][ak + 1][am] = ra.y;
+    As[buf][ak + 2][am] = ra.z;
+    As[buf][ak + 3][am] = ra.w;
+    *reinterpret_cast<float4*>(&Bs[buf][bk][bn]) = rb;
+  };
+  load(0);
+  store(0);
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = 0; k0 < K; k0 += 8) {
+    const bool more = k0 + 8 < K;
+    if (more) load(k0 + 8);
+#pragma unroll
+    for (int kk = 0; kk < 8; kk++) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][64 + ty * 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][64 + tx * 4]);
+      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 8; i++)
+#pragma unroll
+        for (int j = 0; j < 8; j++) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    if (more) {
+      store(buf ^ 1);
+      __syncthreads();
+      buf ^= 1;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 8; i++) {
+    const int gm = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
+    if (gm >= M) continue;
+    const int64_t row = rowmap ? (int64_t)rowmap[gm] : (int64_t)gm;
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      const int64_t gn = n0 + h * 64 + tx * 4;
+      float* c = C + row * ldc + gn;
+      const float* v = &acc[i][4 * h];
+      if (gn + 3 < N) {
+        float4 o = make_float4(v[0], v[1], v[2], v[3]);
+        if (accumulate) {
+          const float4 p = *reinterpret_cast<const float4*>(c);
+          o.x += p.x;
+          o.y += p.y;
+          o.z += p.z;
+          o.w += p.w;
+        }
+        *reinterpret_cast<float4*>(c) = o;
+      } else {
+        for (int q = 0; q < 3; q++)
+          if (gn + q < N) c[q] = accumulate ? c[q] + v[q] : v[q];
+      }
+    }
+  }
+}
+
 template <typename T>
 inline void gemm_nn(cudaStream_t st, int M, int64_t N, int64_t K, const T* A, int64_t lda, const T* B, int64_t ldb,
                     T* C, int64_t ldc, const int32_t* rowmap, int accumulate = 0) {
   if (M <= 0 || N <= 0) return;
+  if constexpr (sizeof(T) == 4) {
+    const bool aligned = (lda % 4 == 0) && (ldb % 4 == 0) && (ldc % 4 == 0) && (K % 8 == 0) && K > 0 &&
+                         ((uintptr_t)A % 16 == 0) && ((uintptr_t)B % 16 == 0) && ((uintptr_t)C % 16 == 0);
+    if (aligned) {
+      dim3 grid((unsigned)((N + 127) / 128), (unsigned)((M + 127) / 128));
+      k_sgemm128<<<grid, 256, 0, st>>>(M, N, (int)K, (const float*)A, lda, (const float*)B, ldb, (float*)C, ldc,
+                                       rowmap, accumulate);
+      return;
+    }
+  }
   dim3 grid((unsigned)((N + 63) / 64), (unsigned)((M + 63) / 64));
   k_gemm_nn<T><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, rowmap, accumulate);
 }

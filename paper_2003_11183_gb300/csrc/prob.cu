@@ -173,86 +173,136 @@ constexpr int DIAG_SUB = 128;
 // Extra floats after the transposed tiles: the accumulator window may read up
 // to DIAG_VB - 1 entries past the last row.
 constexpr int DIAG_PAD = 32;
+// SPT samples per thread (samples c0 + tid + s * blockDim.x): every broadcast
+// load of B and of the per-variable constants serves SPT samples, and the SPT
+// special-function chains are independent instruction streams.
+template <int SPT>
 __global__ void k_diag_f32(DiagArgs32 p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* ys = reinterpret_cast<float*>(smem_raw);
   __shared__ float s_a[DIAG_SUB], s_b[DIAG_SUB], s_inv[DIAG_SUB];
-  __shared__ uint64_t s_q[DIAG_SUB];
-  const int bd = blockDim.x, tid = threadIdx.x, ld = bd + 1;
-  const int64_t c0 = (int64_t)blockIdx.x * bd;
-  const int64_t c = c0 + tid;
+  __shared__ uint64_t s_q[DIAG_SUB], s_d[2][DIAG_SUB];
+  const int bd = blockDim.x, tid = threadIdx.x, ld = SPT * bd + 1;
+  const int64_t c0 = (int64_t)blockIdx.x * bd * SPT;
   const int mt = p.mt;
+  // the block's samples fall in at most two shift batches when a batch holds at
+  // least as many points as the block has samples: stage those rows of D
+  const int64_t sh_lo = (p.sample0 + c0) / p.N;
+  const int64_t sh_hi = (p.sample0 + min(c0 + (int64_t)bd * SPT, p.C) - 1) / p.N;
+  const bool d_staged = sh_hi - sh_lo <= 1;
   for (int t = tid; t < mt; t += bd) {
     s_a[t] = p.a[t];
     s_b[t] = p.b[t];
     s_inv[t] = p.inv[t];
     s_q[t] = p.Q[p.coord0 + t];
+    if (d_staged) {
+      s_d[0][t] = p.D[sh_lo * p.ldD + p.coord0 + t];
+      s_d[1][t] = (sh_hi > sh_lo) ? p.D[sh_hi * p.ldD + p.coord0 + t] : 0;
+    }
   }
   __syncthreads();
-  if (c < p.C) {
-    const int64_t g = p.sample0 + c;
-    const int64_t s = g / p.N;
-    const uint64_t k = (uint64_t)(g - s * p.N) + 1;
-    const uint64_t* Ds = p.D + s * p.ldD + p.coord0;
-    const float rs = p.rs ? p.rs[c] : 1.0f;
-    float lp = 0.0f;
-    for (int v0 = 0; v0 < mt; v0 += DIAG_VB) {
-      const int nb = min(DIAG_VB, mt - v0);
-      float acc[DIAG_VB];
+  int64_t cs[SPT];
+  bool act[SPT];
+  uint64_t ks[SPT];
+  const uint64_t* Ds[SPT];
+  float rs[SPT], lp[SPT];
+  bool any = false;
+#pragma unroll
+  for (int s = 0; s < SPT; s++) {
+    act[s] = c0 + tid + s * bd < p.C;
+    any |= act[s];
+    cs[s] = act[s] ? c0 + tid + s * bd : p.C - 1;  // inactive lanes shadow a valid sample, write nothing
+    const int64_t g = p.sample0 + cs[s];
+    const int64_t sh = g / p.N;
+    ks[s] = (uint64_t)(g - sh * p.N) + 1;
+    Ds[s] = d_staged ? &s_d[sh - sh_lo][0] : p.D + sh * p.ldD + p.coord0;
+    rs[s] = p.rs ? p.rs[cs[s]] : 1.0f;
+    lp[s] = 0.0f;
+  }
+  if (any) {
+    // limit shifts of the first block; later blocks' are loaded one block ahead
+    float nxt[SPT][DIAG_VB];
+#pragma unroll
+    for (int s = 0; s < SPT; s++)
 #pragma unroll
       for (int j = 0; j < DIAG_VB; j++)
-        acc[j] = (p.Delta && j < nb) ? p.Delta[(int64_t)(v0 + j) * p.ldd + c] : 0.0f;
+        nxt[s][j] = (p.Delta && j < mt) ? p.Delta[(int64_t)j * p.ldd + cs[s]] : 0.0f;
+    for (int v0 = 0; v0 < mt; v0 += DIAG_VB) {
+      const int nb = min(DIAG_VB, mt - v0);
+      float acc[SPT][DIAG_VB];
+#pragma unroll
+      for (int s = 0; s < SPT; s++)
+#pragma unroll
+        for (int j = 0; j < DIAG_VB; j++) acc[s][j] = nxt[s][j];
+      {
+        const int v1 = v0 + DIAG_VB;  // prefetch the next block's shifts
+#pragma unroll
+        for (int s = 0; s < SPT; s++)
+#pragma unroll
+          for (int j = 0; j < DIAG_VB; j++)
+            nxt[s][j] = (p.Delta && v1 + j < mt) ? p.Delta[(int64_t)(v1 + j) * p.ldd + cs[s]] : 0.0f;
+      }
       const float* bcol = p.BT + v0;
 #pragma unroll 2
       for (int u = 0; u < v0; u++) {
-        const float yu = ys[u * ld + tid];
+        float yu[SPT];
+#pragma unroll
+        for (int s = 0; s < SPT; s++) yu[s] = ys[u * ld + tid + s * bd];
         const float4* b4 = reinterpret_cast<const float4*>(bcol + (int64_t)u * p.ldbt);
-        const float4 q0 = __ldg(b4), q1 = __ldg(b4 + 1), q2 = __ldg(b4 + 2), q3 = __ldg(b4 + 3);
-        acc[0] = fmaf(q0.x, yu, acc[0]);
-        acc[1] = fmaf(q0.y, yu, acc[1]);
-        acc[2] = fmaf(q0.z, yu, acc[2]);
-        acc[3] = fmaf(q0.w, yu, acc[3]);
-        acc[4] = fmaf(q1.x, yu, acc[4]);
-        acc[5] = fmaf(q1.y, yu, acc[5]);
-        acc[6] = fmaf(q1.z, yu, acc[6]);
-        acc[7] = fmaf(q1.w, yu, acc[7]);
-        acc[8] = fmaf(q2.x, yu, acc[8]);
-        acc[9] = fmaf(q2.y, yu, acc[9]);
-        acc[10] = fmaf(q2.z, yu, acc[10]);
-        acc[11] = fmaf(q2.w, yu, acc[11]);
-        acc[12] = fmaf(q3.x, yu, acc[12]);
-        acc[13] = fmaf(q3.y, yu, acc[13]);
-        acc[14] = fmaf(q3.z, yu, acc[14]);
-        acc[15] = fmaf(q3.w, yu, acc[15]);
+        const float4 q[4] = {__ldg(b4), __ldg(b4 + 1), __ldg(b4 + 2), __ldg(b4 + 3)};
+#pragma unroll
+        for (int s = 0; s < SPT; s++)
+#pragma unroll
+          for (int h = 0; h < 4; h++) {
+            acc[s][4 * h] = fmaf(q[h].x, yu[s], acc[s][4 * h]);
+            acc[s][4 * h + 1] = fmaf(q[h].y, yu[s], acc[s][4 * h + 1]);
+            acc[s][4 * h + 2] = fmaf(q[h].z, yu[s], acc[s][4 * h + 2]);
+            acc[s][4 * h + 3] = fmaf(q[h].w, yu[s], acc[s][4 * h + 3]);
+          }
       }
 #pragma unroll 1
       for (int j = 0; j < nb; j++) {
         const int v = v0 + j;
-        const float sum = acc[0];  // shifts + earlier variables, for variable v
-        const float iv = s_inv[v];
-        const float at = (s_a[v] * rs - sum) * iv;
-        const float bt = (s_b[v] * rs - sum) * iv;
-        float w, wc;
-        lattice_wf(k * s_q[v] + Ds[v], p.periodize, w, wc);
-        float lv, y;
-        sov_step_f32(at, bt, w, wc, lv, y);
-        lp += lv;
-        ys[v * ld + tid] = y;
-        if (p.Yv) p.Yv[(int64_t)v * p.ldyv + c] = y;
+        const float iv = s_inv[v], av = s_a[v], bv = s_b[v];
+        const uint64_t qv = s_q[v];
+        float y[SPT];
+#pragma unroll
+        for (int s = 0; s < SPT; s++) {
+          const float sum = acc[s][0];  // shifts + earlier variables, for variable v
+          const float at = (av * rs[s] - sum) * iv;
+          const float bt = (bv * rs[s] - sum) * iv;
+          float w, wc;
+          lattice_wf(ks[s] * qv + Ds[s][v], p.periodize, w, wc);
+          float lv;
+          sov_step_f32(at, bt, w, wc, lv, y[s]);
+          lp[s] += lv;
+          ys[v * ld + tid + s * bd] = y[s];
+          if (p.Yv && act[s]) p.Yv[(int64_t)v * p.ldyv + cs[s]] = y[s];
+        }
         // window shift: acc[i] <- acc[i+1] + B[v+1+i][v] y
         const float* brow = p.BT + (int64_t)v * p.ldbt + v + 1;
 #pragma unroll
-        for (int i = 0; i < DIAG_VB - 1; i++) acc[i] = fmaf(__ldg(brow + i), y, acc[i + 1]);
-        acc[DIAG_VB - 1] = 0.0f;
+        for (int i = 0; i < DIAG_VB - 1; i++) {
+          const float bb = __ldg(brow + i);
+#pragma unroll
+          for (int s = 0; s < SPT; s++) acc[s][i] = fmaf(bb, y[s], acc[s][i + 1]);
+        }
+#pragma unroll
+        for (int s = 0; s < SPT; s++) acc[s][DIAG_VB - 1] = 0.0f;
       }
     }
-    if (p.first) p.logP[g] = (double)lp;
-    else p.logP[g] += (double)lp;
+#pragma unroll
+    for (int s = 0; s < SPT; s++) {
+      if (!act[s]) continue;
+      const int64_t g = p.sample0 + cs[s];
+      if (p.first) p.logP[g] = (double)lp[s];
+      else p.logP[g] += (double)lp[s];
+    }
   }
   if (p.Ys) {
     __syncthreads();
     const int nw = bd >> 5, warp = tid >> 5, lane = tid & 31;
-    for (int j = warp; j < bd; j += nw) {
+    for (int j = warp; j < SPT * bd; j += nw) {
       if (c0 + j >= p.C) break;
       __nv_bfloat16* row = p.Ys + (c0 + j) * p.ldys;
       for (int v = lane; v < p.mt; v += 32) put_y(row, v, ys[v * ld + j]);
@@ -537,9 +587,23 @@ static int diag_threads(int m) {
   return bd;
 }
 
-// Threads per block and shared memory of the float sweep over DIAG_SUB-variable sub-tiles.
+// Samples per thread of the float sweep (1 or 2); TLRMVN_SPT overrides the default.
+static int sweep_spt() {
+  static int spt = [] {
+    const char* e = getenv("TLRMVN_SPT");
+    int v = e ? atoi(e) : 1;
+    return (v == 2) ? 2 : 1;
+  }();
+  return spt;
+}
+// Samples per block and shared memory of the float sweep over DIAG_SUB-variable sub-tiles.
 static int sub_threads(int m) { return diag_threads<float>(std::min(m, DIAG_SUB)); }
 static size_t sub_smem(int m) { return (size_t)std::min(m, DIAG_SUB) * (sub_threads(m) + 1) * sizeof(float); }
+static int set_sweep_smem(int m) {
+  TLR_CUDA(cudaFuncSetAttribute(k_diag_f32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sub_smem(m)));
+  TLR_CUDA(cudaFuncSetAttribute(k_diag_f32<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sub_smem(m)));
+  return TLRMVN_OK;
+}
 
 // Float sweep of diagonal tile i, DIAG_SUB variables at a time.  Before each
 // sub-tile q > 0, the coupling to the tile's earlier sub-tiles,
@@ -557,7 +621,7 @@ static void sweep_tile_f32(const Factor& F, int i, bool has_shift, float* Dl, in
   for (int q0 = 0; q0 < mt; q0 += DIAG_SUB) {
     const int mq = std::min(DIAG_SUB, mt - q0);
     if (q0 > 0) {
-      pf.begin(TLRMVN_KC_DIAG);
+      pf.begin(TLRMVN_KC_COUPLE);
       gemm_nn<float>(st, mq, Cc, q0, Bi + (size_t)q0 * m, m, Yv, C, Dl + (size_t)q0 * C, C, nullptr, has_shift ? 1 : 0);
       pf.end();
     }
@@ -586,7 +650,10 @@ static void sweep_tile_f32(const Factor& F, int i, bool has_shift, float* Dl, in
     a.ldys = ldys;
     a.logP = logP;
     pf.begin(TLRMVN_KC_DIAG);
-    k_diag_f32<<<blocks_for(Cc, bd), bd, smem, st>>>(a);
+    if (sweep_spt() == 2)
+      k_diag_f32<2><<<blocks_for(Cc, bd), bd / 2, smem, st>>>(a);
+    else
+      k_diag_f32<1><<<blocks_for(Cc, bd), bd, smem, st>>>(a);
     pf.end();
   }
 }
@@ -612,7 +679,7 @@ static int run_chunks(Factor& F, const T* Bt, const T* Ut, const T* Vt, const Li
   const int bd = diag_threads<T>(m);
   const size_t smem = (size_t)m * (bd + 1) * sizeof(T);
   if (f32)
-    TLR_CUDA(cudaFuncSetAttribute(k_diag_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sub_smem(m)));
+    TLR_CHECK(set_sweep_smem(m));
   else
     TLR_CUDA(cudaFuncSetAttribute(k_diag<T, YT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
 
@@ -712,7 +779,7 @@ static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opt
   TLR_CUDA(cudaFuncSetAttribute(tc::k_gemm_tc<tc::EPI_COLMAP_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 tc::SMEM_BYTES));
 
-  TLR_CUDA(cudaFuncSetAttribute(k_diag_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sub_smem(m)));
+  TLR_CHECK(set_sweep_smem(m));
 
   for (int64_t c0 = 0; c0 < S; c0 += C) {
     const int64_t Cc = std::min(C, S - c0);

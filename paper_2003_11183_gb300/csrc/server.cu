@@ -37,6 +37,7 @@ struct Request {
   Clock::time_point t_submit, t_start, t_done;
   int status = -1;  // -1 pending
   double logp = 0.0, err = 0.0;
+  std::string msg;  // failure detail from the lane's thread
 };
 
 struct Server {
@@ -102,6 +103,7 @@ struct Server {
         std::lock_guard<std::mutex> lk(mu);
         r->t_done = Clock::now();
         r->status = s;
+        if (s != TLRMVN_OK) r->msg = tlrmvn_last_error();
         r->logp = out[0];
         r->err = out[1];
         in_use -= r->bytes;
@@ -203,12 +205,13 @@ extern "C" int tlrmvn_server_wait(tlrmvn_server_t srv, int64_t request_id, doubl
   Request* r = it->second;
   S.cv_done.wait(lk, [&] { return r->status != -1; });
   int s = r->status;
+  const std::string msg = r->msg;
   if (logp) *logp = r->logp;
   if (err) *err = r->err;
   if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
   S.all.erase(it);
   delete r;
-  if (s != TLRMVN_OK) return fail(s, "request failed");
+  if (s != TLRMVN_OK) return fail(s, "request failed: " + msg);
   return TLRMVN_OK;
 }
 
@@ -224,6 +227,13 @@ extern "C" int tlrmvn_server_stats(tlrmvn_server_t srv, tlrmvn_server_stats_t* o
   out->peak_bytes = S.peak_in_use;
   out->p50_ms = percentile(S.latencies_ms, 0.50);
   out->p99_ms = percentile(S.latencies_ms, 0.99);
+  return TLRMVN_OK;
+}
+
+extern "C" int tlrmvn_prob_scratch_bytes(tlrmvn_factor_t f, const tlrmvn_opts* opts, int64_t* bytes) {
+  if (!f || !opts || !bytes) return fail(TLRMVN_E_INVAL, "null argument");
+  const Factor& F = *reinterpret_cast<Factor*>(f);
+  *bytes = prob_scratch_bytes(F, *opts) + (2 * F.n + 2) * 8;
   return TLRMVN_OK;
 }
 

@@ -21,7 +21,7 @@ __device__ inline void gamma_pq(double a, double x, double& P, double& Q) {
       ap += 1.0;
       term *= x / ap;
       sum += term;
-      if (fabs(term) < fabs(sum) * 1e-17) break;
+      if (fabs(term) <= fabs(sum) * 1.2e-16) break;
     }
     P = sum * exp(lpref);
     Q = 1.0 - P;
@@ -38,7 +38,7 @@ __device__ inline void gamma_pq(double a, double x, double& P, double& Q) {
       d = 1.0 / d;
       double del = d * c;
       h *= del;
-      if (fabs(del - 1.0) < 1e-16) break;
+      if (fabs(del - 1.0) <= 4.5e-16) break;  // a few ulp: exact equality may never occur
     }
     Q = exp(lpref) * h;
     P = 1.0 - Q;
@@ -65,11 +65,11 @@ __device__ inline double gamma_p_inv(double a, double p, double q) {
     double step = (fabs(corr) < 0.5) ? dx / (1.0 - corr) : dx;
     double xn = x - step;
     if (!(xn > 0.0)) xn = 0.5 * x;
-    if (fabs(xn - x) <= 4e-16 * x) {
-      x = xn;
-      break;
-    }
+    // Halley converges cubically: once a step is below 1e-12 x the next iterate
+    // is exact to rounding, so stop there instead of chasing the last ulp
+    const bool done = fabs(xn - x) <= 1e-12 * x;
     x = xn;
+    if (done) break;
   }
   return x;
 }

@@ -66,13 +66,15 @@ def test_admission_by_memory_budget(env):
     tl, ws, fs = env
     rng = np.random.default_rng(1)
     a, b, nu, prec = _req(ws[2], 0, rng)
-    # a 2,048-sample chunk bounds one request's scratch near 9 MB: 12 MB admits one at a time
+    # a budget of 1.5 requests admits exactly one at a time
     kw = dict(n_shifts=4, n_points=4000, seed=3, sample_chunk=2048)
-    srv = tl.Server(fs, lanes=4, memory_budget=12 << 20)
+    one = tl.tlrmvn_prob_scratch_bytes(fs[2], tl.FP32, 4, 4000, sample_chunk=2048)
+    budget = int(1.5 * one)
+    srv = tl.Server(fs, lanes=4, memory_budget=budget)
     ids = [srv.submit(2, a, b, nu, tl.FP32, **kw) for _ in range(6)]
     res = [srv.wait(i) for i in ids]
     st = srv.stats()
-    assert st["peak_in_flight"] == 1 and 0 < st["peak_bytes"] <= 12 << 20
+    assert st["peak_in_flight"] == 1 and st["peak_bytes"] == one
     assert all(r[0] == res[0][0] for r in res)
     with pytest.raises(tl.TlrmvnError) as e:
         srv.submit(2, a, b, nu, tl.FP32, n_shifts=20, n_points=200000)

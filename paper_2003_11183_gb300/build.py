@@ -28,14 +28,21 @@ def sources() -> list[str]:
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
-def _digest() -> str:
+def source_digest() -> str:
+    """sha256 over the CUDA sources and the public header (contents and names only)."""
     h = hashlib.sha256()
     files = sources() + sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h")))
     files.append(os.path.join(INCLUDE, "tlrmvn.h"))
     for f in files:
-        h.update(f.encode())
+        h.update(os.path.relpath(f, ROOT).encode())
         with open(f, "rb") as fh:
             h.update(fh.read())
+    return h.hexdigest()
+
+
+def _digest() -> str:
+    h = hashlib.sha256()
+    h.update(source_digest().encode())
     h.update(" ".join(ARCH + FLAGS).encode())
     h.update(os.uname().machine.encode())
     return h.hexdigest()

@@ -371,7 +371,7 @@ static int batch_build(Batch& B, int count, const tlrmvn_factor_t* factors, cons
   TLR_CUDA(cudaMemcpyAsync(B.perm_g, perm_g.data(), perm_g.size() * 8, cudaMemcpyHostToDevice, st));
   // persistent grid and its private projection buffers
   const size_t smem = (size_t)BATCH_MMAX * (BATCH_T + 1) * sizeof(float);
-  TLR_CUDA(cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  TLR_CHECK(raise_smem_limit((const void*)k_batch, (size_t)smem));
   int per_sm = 0, sms = 0;
   TLR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, BATCH_T, smem));
   TLR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, B.device));

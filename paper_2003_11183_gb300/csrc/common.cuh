@@ -111,6 +111,11 @@ std::vector<uint64_t> richtmyer_generators(int64_t d);
 int factor_finish(Factor& F, cudaStream_t st);
 
 cudaStream_t pick_stream(void* s);
+// Raise `kernel`'s dynamic shared memory limit on the current device to at least
+// `bytes`.  The limit is per function and process-wide, so it is only ever
+// raised: a caller with a smaller tile never lowers it under another thread that
+// is about to launch with a larger one.
+int raise_smem_limit(const void* kernel, size_t bytes);
 
 // Kernel-class timing (tlrmvn_profile_*): Prof brackets launches with events.
 struct Prof {

@@ -642,9 +642,9 @@ static int factor_build(const CovSrc& src, int64_t n, std::vector<int64_t> geo, 
   std::vector<int> pos2blk(r);
   std::iota(pos2blk.begin(), pos2blk.end(), 0);
   const size_t uc_smem = (size_t)m * (5 * sizeof(double) + sizeof(int));
-  TLR_CUDA(cudaFuncSetAttribute(k_uc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)uc_smem));
-  TLR_CUDA(cudaFuncSetAttribute(k_aca, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * m * sizeof(double))));
-  TLR_CUDA(cudaFuncSetAttribute(k_potrf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(m * sizeof(double))));
+  TLR_CHECK(raise_smem_limit((const void*)k_uc, (size_t)uc_smem));
+  TLR_CHECK(raise_smem_limit((const void*)k_aca, 2 * m * sizeof(double)));
+  TLR_CHECK(raise_smem_limit((const void*)k_potrf, m * sizeof(double)));
   const int uc_threads = m >= 256 ? 512 : 256;
 
   if (o.reorder == TLRMVN_REORDER_BLOCK) {

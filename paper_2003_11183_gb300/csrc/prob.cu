@@ -176,7 +176,10 @@ constexpr int DIAG_PAD = 32;
 // SPT samples per thread (samples c0 + tid + s * blockDim.x): every broadcast
 // load of B and of the per-variable constants serves SPT samples, and the SPT
 // special-function chains are independent instruction streams.
-template <int SPT>
+// PIPE: software-pipeline the loads of each variable's lattice offset and
+// window column one variable ahead, and add the limit shifts after the sums.
+// DSTAGE: keep the block's (at most two) rows of lattice offsets in shared memory.
+template <int SPT, bool PIPE, bool DSTAGE>
 __global__ void k_diag_f32(DiagArgs32 p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* ys = reinterpret_cast<float*>(smem_raw);
@@ -189,7 +192,7 @@ __global__ void k_diag_f32(DiagArgs32 p) {
   // least as many points as the block has samples: stage those rows of D
   const int64_t sh_lo = (p.sample0 + c0) / p.N;
   const int64_t sh_hi = (p.sample0 + min(c0 + (int64_t)bd * SPT, p.C) - 1) / p.N;
-  const bool d_staged = sh_hi - sh_lo <= 1;
+  const bool d_staged = DSTAGE && sh_hi - sh_lo <= 1;
   for (int t = tid; t < mt; t += bd) {
     s_a[t] = p.a[t];
     s_b[t] = p.b[t];
@@ -220,27 +223,29 @@ __global__ void k_diag_f32(DiagArgs32 p) {
     lp[s] = 0.0f;
   }
   if (any) {
-    // limit shifts of the first block; later blocks' are loaded one block ahead
-    float nxt[SPT][DIAG_VB];
-#pragma unroll
-    for (int s = 0; s < SPT; s++)
-#pragma unroll
-      for (int j = 0; j < DIAG_VB; j++)
-        nxt[s][j] = (p.Delta && j < mt) ? p.Delta[(int64_t)j * p.ldd + cs[s]] : 0.0f;
     for (int v0 = 0; v0 < mt; v0 += DIAG_VB) {
       const int nb = min(DIAG_VB, mt - v0);
       float acc[SPT][DIAG_VB];
+      // limit shifts of the block: with PIPE they are added after the sums over
+      // earlier variables, so their loads are in flight during that loop
+      float dl[SPT][DIAG_VB];
 #pragma unroll
       for (int s = 0; s < SPT; s++)
 #pragma unroll
-        for (int j = 0; j < DIAG_VB; j++) acc[s][j] = nxt[s][j];
-      {
-        const int v1 = v0 + DIAG_VB;  // prefetch the next block's shifts
+        for (int j = 0; j < DIAG_VB; j++) {
+          dl[s][j] = (p.Delta && j < nb) ? p.Delta[(int64_t)(v0 + j) * p.ldd + cs[s]] : 0.0f;
+          acc[s][j] = PIPE ? 0.0f : dl[s][j];
+        }
+      // PIPE: the lattice offset and the window column of the next variable are
+      // loaded one variable ahead (first ones here, before the sums)
+      uint64_t dnext[SPT];
+      float bnext[DIAG_VB - 1];
+      if (PIPE) {
 #pragma unroll
-        for (int s = 0; s < SPT; s++)
+        for (int s = 0; s < SPT; s++) dnext[s] = Ds[s][v0];
+        const float* brow = p.BT + (int64_t)v0 * p.ldbt + v0 + 1;
 #pragma unroll
-          for (int j = 0; j < DIAG_VB; j++)
-            nxt[s][j] = (p.Delta && v1 + j < mt) ? p.Delta[(int64_t)(v1 + j) * p.ldd + cs[s]] : 0.0f;
+        for (int i = 0; i < DIAG_VB - 1; i++) bnext[i] = __ldg(brow + i);
       }
       const float* bcol = p.BT + v0;
 #pragma unroll 2
@@ -260,11 +265,34 @@ __global__ void k_diag_f32(DiagArgs32 p) {
             acc[s][4 * h + 3] = fmaf(q[h].w, yu[s], acc[s][4 * h + 3]);
           }
       }
+      if (PIPE) {
+#pragma unroll
+        for (int s = 0; s < SPT; s++)
+#pragma unroll
+          for (int j = 0; j < DIAG_VB; j++) acc[s][j] += dl[s][j];
+      }
 #pragma unroll 1
       for (int j = 0; j < nb; j++) {
         const int v = v0 + j;
         const float iv = s_inv[v], av = s_a[v], bv = s_b[v];
         const uint64_t qv = s_q[v];
+        uint64_t dv[SPT];
+        float bcur[DIAG_VB - 1];
+        if (PIPE) {
+#pragma unroll
+          for (int s = 0; s < SPT; s++) dv[s] = dnext[s];
+#pragma unroll
+          for (int i = 0; i < DIAG_VB - 1; i++) bcur[i] = bnext[i];
+          const int vn = (j + 1 < nb) ? v + 1 : v;  // the last one reloads its own (in bounds)
+#pragma unroll
+          for (int s = 0; s < SPT; s++) dnext[s] = Ds[s][vn];
+          const float* brow = p.BT + (int64_t)vn * p.ldbt + vn + 1;
+#pragma unroll
+          for (int i = 0; i < DIAG_VB - 1; i++) bnext[i] = __ldg(brow + i);
+        } else {
+#pragma unroll
+          for (int s = 0; s < SPT; s++) dv[s] = Ds[s][v];
+        }
         float y[SPT];
 #pragma unroll
         for (int s = 0; s < SPT; s++) {
@@ -272,7 +300,7 @@ __global__ void k_diag_f32(DiagArgs32 p) {
           const float at = (av * rs[s] - sum) * iv;
           const float bt = (bv * rs[s] - sum) * iv;
           float w, wc;
-          lattice_wf(ks[s] * qv + Ds[s][v], p.periodize, w, wc);
+          lattice_wf(ks[s] * qv + dv[s], p.periodize, w, wc);
           float lv;
           sov_step_f32(at, bt, w, wc, lv, y[s]);
           lp[s] += lv;
@@ -283,7 +311,7 @@ __global__ void k_diag_f32(DiagArgs32 p) {
         const float* brow = p.BT + (int64_t)v * p.ldbt + v + 1;
 #pragma unroll
         for (int i = 0; i < DIAG_VB - 1; i++) {
-          const float bb = __ldg(brow + i);
+          const float bb = PIPE ? bcur[i] : __ldg(brow + i);
 #pragma unroll
           for (int s = 0; s < SPT; s++) acc[s][i] = fmaf(bb, y[s], acc[s][i + 1]);
         }
@@ -587,21 +615,35 @@ static int diag_threads(int m) {
   return bd;
 }
 
-// Samples per thread of the float sweep (1 or 2); TLRMVN_SPT overrides the default.
-static int sweep_spt() {
-  static int spt = [] {
-    const char* e = getenv("TLRMVN_SPT");
-    int v = e ? atoi(e) : 1;
-    return (v == 2) ? 2 : 1;
+// Variants of the float sweep: samples per thread (1, 2), one-variable-ahead
+// loads, staged lattice offsets.  TLRMVN_SWEEP="spt,pipe,dstage" selects one (tuning runs);
+// the default is the fastest measured on the n = 65,536 workload.
+struct SweepVariant {
+  int spt, pipe, dstage;
+};
+static SweepVariant sweep_variant() {
+  static SweepVariant v = [] {
+    SweepVariant d{1, 1, 0};
+    if (const char* e = getenv("TLRMVN_SWEEP")) {
+      int a = 1, b = 0, c = 0;
+      if (sscanf(e, "%d,%d,%d", &a, &b, &c) == 3) d = SweepVariant{a == 2 ? 2 : 1, b ? 1 : 0, c ? 1 : 0};
+    }
+    return d;
   }();
-  return spt;
+  return v;
+}
+typedef void (*SweepKernel)(DiagArgs32);
+static SweepKernel sweep_kernel(const SweepVariant& v) {
+  static const SweepKernel table[2][2][2] = {
+      {{k_diag_f32<1, false, false>, k_diag_f32<1, false, true>}, {k_diag_f32<1, true, false>, k_diag_f32<1, true, true>}},
+      {{k_diag_f32<2, false, false>, k_diag_f32<2, false, true>}, {k_diag_f32<2, true, false>, k_diag_f32<2, true, true>}}};
+  return table[v.spt - 1][v.pipe][v.dstage];
 }
 // Samples per block and shared memory of the float sweep over DIAG_SUB-variable sub-tiles.
 static int sub_threads(int m) { return diag_threads<float>(std::min(m, DIAG_SUB)); }
 static size_t sub_smem(int m) { return (size_t)std::min(m, DIAG_SUB) * (sub_threads(m) + 1) * sizeof(float); }
 static int set_sweep_smem(int m) {
-  TLR_CUDA(cudaFuncSetAttribute(k_diag_f32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sub_smem(m)));
-  TLR_CUDA(cudaFuncSetAttribute(k_diag_f32<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sub_smem(m)));
+  TLR_CHECK(raise_smem_limit((const void*)sweep_kernel(sweep_variant()), sub_smem(m)));
   return TLRMVN_OK;
 }
 
@@ -650,10 +692,8 @@ static void sweep_tile_f32(const Factor& F, int i, bool has_shift, float* Dl, in
     a.ldys = ldys;
     a.logP = logP;
     pf.begin(TLRMVN_KC_DIAG);
-    if (sweep_spt() == 2)
-      k_diag_f32<2><<<blocks_for(Cc, bd), bd / 2, smem, st>>>(a);
-    else
-      k_diag_f32<1><<<blocks_for(Cc, bd), bd, smem, st>>>(a);
+    const SweepVariant sv = sweep_variant();
+    sweep_kernel(sv)<<<blocks_for(Cc, bd), bd / sv.spt, smem, st>>>(a);
     pf.end();
   }
 }
@@ -681,7 +721,7 @@ static int run_chunks(Factor& F, const T* Bt, const T* Ut, const T* Vt, const Li
   if (f32)
     TLR_CHECK(set_sweep_smem(m));
   else
-    TLR_CUDA(cudaFuncSetAttribute(k_diag<T, YT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    TLR_CHECK(raise_smem_limit((const void*)k_diag<T, YT, false>, (size_t)smem));
 
   for (int64_t c0 = 0; c0 < S; c0 += C) {
     const int64_t Cc = std::min(C, S - c0);
@@ -774,10 +814,8 @@ static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opt
   }
   TLR_CHECK(make_map(&mapW, W, F.kw16, C, F.kw16 * 2, tc::BN));
   TLR_CHECK(make_map(&mapY, Y, F.my16, C, F.my16 * 2, tc::BN));
-  TLR_CUDA(cudaFuncSetAttribute(tc::k_gemm_tc<tc::EPI_ROWMAJOR_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                tc::SMEM_BYTES));
-  TLR_CUDA(cudaFuncSetAttribute(tc::k_gemm_tc<tc::EPI_COLMAP_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                tc::SMEM_BYTES));
+  TLR_CHECK(raise_smem_limit((const void*)tc::k_gemm_tc<tc::EPI_ROWMAJOR_F32>, (size_t)tc::SMEM_BYTES));
+  TLR_CHECK(raise_smem_limit((const void*)tc::k_gemm_tc<tc::EPI_COLMAP_BF16>, (size_t)tc::SMEM_BYTES));
 
   TLR_CHECK(set_sweep_smem(m));
 

@@ -4,6 +4,7 @@
 #include "common.cuh"
 
 #include <cstring>
+#include <map>
 #include <mutex>
 
 namespace tlrmvn {
@@ -32,6 +33,20 @@ cudaStream_t pick_stream(void* s) {
   std::lock_guard<std::mutex> lk(g_stream_mu);
   if (!g_stream[dev]) cudaStreamCreateWithFlags(&g_stream[dev], cudaStreamNonBlocking);
   return g_stream[dev];
+}
+
+static std::mutex g_smem_mu;
+static std::map<std::pair<int, const void*>, size_t> g_smem_limit;
+
+int raise_smem_limit(const void* kernel, size_t bytes) {
+  int dev = 0;
+  TLR_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_smem_mu);
+  size_t& cur = g_smem_limit[{dev, kernel}];
+  if (bytes <= cur) return TLRMVN_OK;
+  TLR_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  cur = bytes;
+  return TLRMVN_OK;
 }
 
 static std::mutex g_prof_mu;

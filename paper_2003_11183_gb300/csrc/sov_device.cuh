@@ -92,24 +92,43 @@ __device__ __forceinline__ void lattice_wf(uint64_t x, int periodize, float& w, 
             (float)(uint32_t)(numc & 0x1FFFFF) * 1.1102230246251565e-16f);
 }
 
-// eq. (2) for one variable in float32; the one-sided case (at = -inf) evaluates one
-// scaled complementary error function and the logs it needs, nothing else.
+// eq. (2) for one variable in float32.  The one-sided case (at = -inf), which is
+// the whole integrand for upper-limit problems, has a branch-free fast path for
+// bt >= -12 (Phi(bt) > 1.7e-33): one complementary error function of |bt|, one
+// log, and CUDA's normal quantile; samples of one warp take the same
+// instructions whatever the sign of their limit.  log Phi(bt) near 1 uses
+// Goldberg's form of log1p (D. Goldberg, What every computer scientist should
+// know about floating-point arithmetic, 1991, Theorem 4): log1p(-c) =
+// log(s) * (-c) / (s - 1) with s = fl(1 - c).  Quantiles whose probability is
+// below 1e-30, and limits below -12, go through the log-domain code.
 __device__ __forceinline__ void sov_step_f32(float at, float bt, float w, float wc, float& ld, float& y) {
   const float rs2 = (float)TLR_RSQRT2;
   if (at == -INFINITY && bt != INFINITY) {
-    if (bt < 0.0f) {
-      const float t = -bt * rs2;
-      const float le = logf(0.5f * erfcxf(t)) - t * t;  // log Phi(bt)
-      const float lu = logf(w) + le;                      // log u, u = w Phi(bt) < 1/2
-      y = ndtri_lower(expf(lu), lu);
-      ld = le;
-    } else {
-      const float ec = 0.5f * erfcf(bt * rs2);
-      const float e = 1.0f - ec;
-      const float u = w * e, uc = ec + wc * e;
-      y = (u <= 0.5f) ? ndtri_lower(u, logf(u)) : -ndtri_lower(uc, logf(uc));
-      ld = log1pf(-ec);
+    if (bt >= -12.0f) {
+      const float h = 0.5f * erfcf(fabsf(bt) * rs2);  // Phi(-|bt|)
+      const bool neg = bt < 0.0f;
+      const float ph = neg ? h : 1.0f - h;  // Phi(bt)
+      const float pc = neg ? 1.0f - h : h;  // 1 - Phi(bt)
+      const float s1 = 1.0f - pc;
+      const float lg = logf(neg ? ph : s1);
+      ld = neg ? lg : ((s1 == 1.0f) ? -pc : lg * (-pc / (s1 - 1.0f)));
+      const float u = w * ph, uc = pc + wc * ph;  // u + uc = 1
+      const bool lower = u <= uc;
+      const float pp = lower ? u : uc;
+      if (pp >= 1e-30f) {
+        const float z = normcdfinvf(pp);
+        y = lower ? z : -z;
+      } else {  // u underflows: quantile from log u
+        const float lu = logf(w) + ld;
+        y = ndtri_lower(expf(lu), lu);
+      }
+      return;
     }
+    const float t = -bt * rs2;
+    const float le = logf(0.5f * erfcxf(t)) - t * t;  // log Phi(bt)
+    const float lu = logf(w) + le;                      // log u, u = w Phi(bt) < 1/2
+    y = ndtri_lower(expf(lu), lu);
+    ld = le;
     return;
   }
   sov_step<float>(at, bt, w, wc, ld, y);

@@ -32,6 +32,12 @@ import numpy as np  # noqa: E402
 # 2 flops per FMA x 2.07 GHz maximum SM clock.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of a kernel from one
+# ncu capture, divided by the sample-dimensions the captured launch processed,
+# with the digest of the CUDA sources it was taken on (build.source_digest()).
+# A figure is reported, scaled to this run's launches, only while the sources
+# are unchanged; the summaries with the capture commands are under profiles/.
+TRAFFIC = {}
 
 
 def parse():
@@ -204,6 +210,17 @@ def run_reference(args):
     return 0
 
 
+def rank_summary(tl, F):
+    """Mean, quartiles and maximum of the off-diagonal tile ranks of a factor."""
+    rk = tl.tlrmvn_factor_ranks(F)
+    low = rk[np.tril_indices(rk.shape[0], -1)]
+    if low.size == 0:
+        return {"mean": 0.0}
+    q = np.percentile(low, [25, 50, 75]).tolist()
+    return {"mean": float(low.mean()), "q25": q[0], "median": q[1], "q75": q[2], "max": int(low.max()),
+            "zero_tiles": int((low == 0).sum()), "tiles": int(low.size)}
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_init()
@@ -242,10 +259,12 @@ def run_ours(args):
     tl.tlrmvn_profile_reset()
     tl.tlrmvn_profile_enable(True)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed_steps")  # lets a profiler capture exactly the timed launches
     ev0.record(stream)
     for _ in range(args.steps):
         tl.tlrmvn_prob_device(F, a, b, out, **kw)
     ev1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     tl.tlrmvn_profile_enable(False)
     clk = clocks.stop()
@@ -282,13 +301,19 @@ def run_ours(args):
     pk, pk_kind = peaks()
     m, n, C = w.m, w.n, w.n_shifts * w.n_points
     sizes = [min(m, n - t * m) for t in range(info["r"])]
-    sub = 128 if prec != 0 else m
+    # sub-tile of the float sweep: 64 on the BF16-shift path (128 when the library's
+    # TLRMVN_SUB tuning switch says so), 128 on the FP32 path, the whole tile on FP64
+    sub = {0: m, 1: 128, 2: 128 if os.environ.get("TLRMVN_SUB") == "128" else 64}[prec]
+    krow = tl.tlrmvn_factor_ranks(F).sum(axis=1)
     per = {"diag": 0.0, "couple": 0.0, "shift": 2.0 * m * info["k_total"], "vproj": 2.0 * m * info["k_total"]}
-    for mt in sizes:
+    couple_bytes = 0.0  # per sample: y panel (hi + lo bf16) read, the sub-tile's shifts read and written
+    for i, mt in enumerate(sizes):
         for q0 in range(0, mt, sub):
             mq = min(sub, mt - q0)
             per["diag"] += mq * (mq - 1)
             per["couple"] += 2.0 * mq * q0
+            if q0 > 0:
+                couple_bytes += 4.0 * q0 + mq * (8.0 if krow[i] > 0 else 4.0)
     fp32_peak = {"bound": "alu", "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                  "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (derived)"}
     classes = {}
@@ -300,13 +325,28 @@ def run_ours(args):
         if cls in ("shift", "vproj") and prec == 2:
             p = pk.get("bf16_tflops_sustained", 1700.0)
             pkd = {"bound": "tensor", "peak": p, "unit": "TFLOP/s", "peak_source": f"bf16 sustained, {pk_kind}"}
+        elif cls == "couple" and prec == 2:
+            ach = couple_bytes * C * args.steps / t / 1e9
+            pkd = {"bound": "hbm", "peak": pk.get("hbm_gbs", 6800.0), "unit": "GB/s",
+                   "peak_source": f"HBM copy, {pk_kind}"}
         else:
             pkd = fp32_peak
         classes[cls] = dict(pkd, achieved=ach, frac=ach / pkd["peak"], ms_per_step=kern[cls][0] / args.steps,
-                            kernel={"diag": "k_diag_f32", "couple": "k_gemm_nn", "shift": "k_gemm_tc",
+                            kernel={"diag": "k_diag_f32", "couple": "k_sgemm128", "shift": "k_gemm_tc",
                                     "vproj": "k_gemm_tc"}[cls] if prec == 2 else cls)
+    from paper_2003_11183_gb300 import build as _build
+    digest = _build.source_digest()
+    for cls, d in classes.items():
+        t = TRAFFIC.get(d["kernel"])
+        n_launch = kern[cls][1]
+        if t and t["sources"] == digest and n_launch:
+            units = float(n) * C * args.steps / n_launch  # sample-dims per launch
+            d["traffic"] = t["bytes_per_sample_dim"] * units
+            d["traffic_source"] = t["capture"]
+        else:
+            d["traffic"] = None
     dom = max(classes, key=lambda c: classes[c]["ms_per_step"])
-    roof = dict(classes[dom], traffic=None)
+    roof = dict(classes[dom])
     roof["note"] = ("achieved counts the multiply-adds only; the sweep's special functions "
                     "(about 3/4 of its instructions) are not in the algorithmic flops")
 
@@ -344,6 +384,7 @@ def run_ours(args):
                 "config": {"workload": w.name, "n": w.n, "tile": w.m, "tol": w.tol, "max_rank": w.max_rank,
                            "nu": w.nu, "shifts": w.n_shifts, "points": w.n_points, "reorder": w.reorder,
                            "precision": args.precision, "k_total": info["k_total"], "tiles": info["r"],
+                           "ranks": rank_summary(tl, F),
                            "l2": "inputs larger than L2 (factor and W buffer)"},
                 "clocks": clk,
                 "e2e": {"value": e2e, "unit": "sample-dims/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 16},

@@ -45,6 +45,8 @@ extern "C" {
 #define TLRMVN_E_CUDA      4  /* CUDA runtime error (no usable device, launch failure, ...) */
 #define TLRMVN_E_FORMAT    5  /* tlrmvn_factor_import: buffer is not a factor of this format */
 #define TLRMVN_E_NOTSUP    6  /* requested precision / mode not available */
+#define TLRMVN_E_TIMEOUT   7  /* a bounded device-side wait (tensor-core pipeline) expired; the kernel
+                                 freed its resources and returned, the CUDA context stays usable */
 
 /* ---- option values --------------------------------------------------- */
 /* Arithmetic of the integrand (tlrmvn_opts.precision). */
@@ -110,6 +112,11 @@ int tlrmvn_factor_dense(const double* cov, int64_t n, int64_t ld, const double* 
  * K = sum of off-diagonal tile ranks, and the number of tiles whose rank cap
  * stopped ACA before the tolerance.  Any output pointer may be NULL. */
 int tlrmvn_factor_info(tlrmvn_factor_t f, int64_t* n, int* r, int* m, int64_t* k_total, int* capped);
+
+/* Ranks of the off-diagonal tiles (Section 3.3: each L_ij ~ U_ij V_ij^T).
+ * ranks: caller-owned host array of r * r int32; entry i*r + j is the rank of
+ * tile (i, j) for i > j and 0 elsewhere.  TLRMVN_E_INVAL for a null argument. */
+int tlrmvn_factor_ranks(tlrmvn_factor_t f, int32_t* ranks);
 
 /* Serialise a factor to host memory (checkpoint; also how tests hand the same
  * factor to an independent implementation).  If buf == NULL, *bytes receives the

@@ -46,44 +46,45 @@ def chi_inv(nu: float, w0):
 
 
 def log_interval(at, bt):
-    """log(Phi(bt) - Phi(at)) for at <= bt, elementwise, without cancellation.
+    """log(Phi(bt) - Phi(at)) for at <= bt, elementwise, without cancellation or underflow.
 
-    When both limits lie in the upper half (at > 0) the difference is taken
-    between the upper-tail complements Phi(-at) - Phi(-bt), which is the same
-    number computed without losing the digits that Phi(x) ~ 1 would lose.
-    A one-sided interval (at = -inf) uses log Phi(bt) directly.
+    Lower half (bt <= 0): log Phi(bt) + log(-expm1(log Phi(at) - log Phi(bt))),
+    which stays finite when both probabilities underflow.  Upper half (at > 0):
+    the same with the upper-tail complements Phi(-at) - Phi(-bt).  Intervals
+    that straddle 0 take the plain difference (it is at least Phi(bt) - 1/2).
     """
     at = np.asarray(at, dtype=np.float64)
     bt = np.asarray(bt, dtype=np.float64)
     with np.errstate(divide="ignore", invalid="ignore"):
-        upper = at > 0
-        diff_low = Phi(bt) - Phi(at)
-        diff_up = Phi(-at) - Phi(-bt)
-        out = np.log(np.where(upper, diff_up, diff_low))
-        one_sided = np.isneginf(at)
-        out = np.where(one_sided, log_Phi(bt), out)
+        la, lb = log_Phi(at), log_Phi(bt)
+        lca, lcb = log_Phi(-at), log_Phi(-bt)
+        low = lb + np.log(-np.expm1(la - lb))
+        up = lca + np.log(-np.expm1(lcb - lca))
+        mid = np.log(Phi(bt) - Phi(at))
+        out = np.where(bt <= 0, low, np.where(at > 0, up, mid))
+        out = np.where(np.isneginf(at), lb, out)
+        out = np.where(np.isposinf(bt) & (at > 0), lca, out)
     return out
 
 
 def sov_step(at, bt, w):
     """One variable of eq. (2): returns (log(e - d), y) for standardised limits.
 
-    d = Phi(at), e = Phi(bt), y = Phi^-1(d + w (e - d)).  In the upper half
-    (at > 0) the same y is computed by symmetry as -Phi^-1(dc - w (dc - ec))
-    with dc = Phi(-at), ec = Phi(-bt), so that no digits are lost to 1 - tiny.
+    d = Phi(at), e = Phi(bt), y = Phi^-1(d + w (e - d)).  The quantile is taken
+    from the log of its argument, d + w (e - d) = (1 - w) d + w e, so that it
+    stays finite in the tails where the argument underflows
+    (scipy.special.ndtri_exp).  In the upper half (at > 0) the same y is
+    -Phi^-1((1 - w) Phi(-at) + w Phi(-bt)) by symmetry.
     """
     at = np.asarray(at, dtype=np.float64)
     bt = np.asarray(bt, dtype=np.float64)
     w = np.asarray(w, dtype=np.float64)
     with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
+        l1w, lw = np.log1p(-w), np.log(w)
         upper = at > 0
-        d = Phi(at)
-        e = Phi(bt)
-        y_low = Phi_inv(d + w * (e - d))
-        dc = Phi(-at)
-        ec = Phi(-bt)
-        y_up = -Phi_inv(dc - w * (dc - ec))
-        y = np.where(upper, y_up, y_low)
+        lu = np.logaddexp(l1w + log_Phi(at), lw + log_Phi(bt))
+        luc = np.logaddexp(l1w + log_Phi(-at), lw + log_Phi(-bt))
+        y = np.where(upper, -sp.ndtri_exp(luc), sp.ndtri_exp(lu))
     return log_interval(at, bt), y
 
 

@@ -33,6 +33,7 @@ SIGNATURES = {
                                        C.POINTER(C.c_void_p)]),
     "tlrmvn_factor_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                       C.POINTER(C.c_int64), C.POINTER(C.c_int)]),
+    "tlrmvn_factor_ranks": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
     "tlrmvn_factor_export": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_size_t)]),
     "tlrmvn_factor_import": (C.c_int, [C.c_void_p, C.c_size_t, C.POINTER(C.c_void_p)]),
     "tlrmvn_factor_free": (C.c_int, [C.c_void_p]),

@@ -16,7 +16,7 @@ from . import _lib as L
 FP64, FP32, BF16_SHIFT = 0, 1, 2
 REORDER_NONE, REORDER_BLOCK, REORDER_ITERATIVE = 0, 1, 2
 KERNEL_EXP, KERNEL_MATERN15, KERNEL_EXP_MATERN15 = 0, 1, 2
-E_INVAL, E_NOT_SPD, E_NOMEM, E_CUDA, E_FORMAT, E_NOTSUP = 1, 2, 3, 4, 5, 6
+E_INVAL, E_NOT_SPD, E_NOMEM, E_CUDA, E_FORMAT, E_NOTSUP, E_TIMEOUT = 1, 2, 3, 4, 5, 6, 7
 
 
 class TlrmvnError(RuntimeError):
@@ -104,6 +104,15 @@ def tlrmvn_factor_info(f: Factor) -> dict:
     _check(lib.tlrmvn_factor_info(f.handle, C.byref(n), C.byref(r), C.byref(m), C.byref(k), C.byref(cp)),
            "tlrmvn_factor_info")
     return {"n": n.value, "r": r.value, "m": m.value, "k_total": k.value, "capped": cp.value}
+
+
+def tlrmvn_factor_ranks(f: Factor) -> np.ndarray:
+    """(r, r) int32 ranks of the off-diagonal tiles, rank[i, j] for i > j."""
+    lib = L.load()
+    r = tlrmvn_factor_info(f)["r"]
+    out = np.zeros(r * r, dtype=np.int32)
+    _check(lib.tlrmvn_factor_ranks(f.handle, out.ctypes.data_as(C.POINTER(C.c_int32))), "tlrmvn_factor_ranks")
+    return out.reshape(r, r)
 
 
 def tlrmvn_factor_export(f: Factor) -> bytes:

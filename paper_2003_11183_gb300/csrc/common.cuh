@@ -86,8 +86,12 @@ struct Factor {
   //   V16   ktot x my16:    Vcat rows, zero beyond m
   //   vmap16 Vcat row -> column of the padded rank space, whose row tile i starts at
   //          kpad_off[i] (a multiple of 64) and spans kw16 columns in all
+  //   B16x2 (r*m) x (2*my16): row i*m+v holds bf16 hi(B_i[v][u]) at column u and
+  //         lo = bf16(B_i[v][u] - hi) at column my16 + u (zero for u >= m); the
+  //         in-tile coupling operand of the tensor-core path
   __nv_bfloat16* U16 = nullptr;
   __nv_bfloat16* V16 = nullptr;
+  __nv_bfloat16* B16x2 = nullptr;
   int32_t* vmap16 = nullptr;
   std::vector<int64_t> kpad_off;
   int64_t kmax16 = 0, kw16 = 0, my16 = 0;
@@ -222,6 +226,10 @@ __device__ __forceinline__ double dev_log(double x) { return log(x); }
 __device__ __forceinline__ float dev_log(float x) { return logf(x); }
 __device__ __forceinline__ double dev_erfc(double x) { return erfc(x); }
 __device__ __forceinline__ float dev_erfc(float x) { return erfcf(x); }
+__device__ __forceinline__ double dev_exp(double x) { return exp(x); }
+__device__ __forceinline__ float dev_exp(float x) { return expf(x); }
+__device__ __forceinline__ double dev_expm1(double x) { return expm1(x); }
+__device__ __forceinline__ float dev_expm1(float x) { return expm1f(x); }
 
 // Phi^-1 given u and its complement uc = 1 - u (both accurate) and lu = log u.
 template <typename T>
@@ -260,27 +268,27 @@ __device__ __forceinline__ void sov_step(T at, T bt, T w, T wc, T& ld, T& y) {
     return;
   }
   if (at > (T)0) {
-    T dc = (T)0.5 * dev_erfc(at * rs2);
-    T ec = (bt == INF) ? (T)0 : (T)0.5 * dev_erfc(bt * rs2);
-    T diff = dc - ec;
-    T uc = ec + wc * diff;   // 1 - u
-    T u = (T)1 - uc;
-    y = ndtri2(u, uc, dev_log(u));
-    ld = dev_log(diff);
+    // upper half, in logs of the complements Phi(-at) >= Phi(-bt): finite when both underflow
+    const T lca = log_Phi(-at);
+    const T dl = (bt == INF) ? -INF : log_Phi(-bt) - lca;
+    ld = lca + dev_log(-dev_expm1(dl));
+    const T luc = lca + dev_log(wc + w * dev_exp(dl));  // log(1 - u) = log((1-w) Phi(-at) + w Phi(-bt))
+    y = -ndtri_lower(dev_exp(luc), luc);
     return;
   }
-  T d = (T)0.5 * dev_erfc(-at * rs2);
-  T e, ec;
-  if (bt == INF) {
-    e = (T)1;
-    ec = (T)0;
-  } else if (bt < (T)0) {
-    e = (T)0.5 * dev_erfc(-bt * rs2);
-    ec = (T)1 - e;
-  } else {
-    ec = (T)0.5 * dev_erfc(bt * rs2);
-    e = (T)1 - ec;
+  if (bt <= (T)0) {
+    // lower half, in logs: Phi(at) <= Phi(bt) <= 1/2
+    const T lb = log_Phi(bt);
+    const T dl = log_Phi(at) - lb;
+    ld = lb + dev_log(-dev_expm1(dl));
+    const T lu = lb + dev_log(w + wc * dev_exp(dl));  // log u = log((1-w) Phi(at) + w Phi(bt))
+    y = ndtri_lower(dev_exp(lu), lu);
+    return;
   }
+  // straddles 0 (at <= 0 < bt): e - d >= e - 1/2 > 0
+  const T d = (T)0.5 * dev_erfc(-at * rs2);
+  const T ec = (bt == INF) ? (T)0 : (T)0.5 * dev_erfc(bt * rs2);
+  const T e = (T)1 - ec;
   T diff = e - d;
   T u = d + w * diff, uc = ec + wc * diff;
   y = ndtri2(u, uc, dev_log(u));

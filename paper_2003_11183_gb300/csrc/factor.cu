@@ -26,16 +26,23 @@
 namespace tlrmvn {
 
 // ---- device helpers (float64) -------------------------------------------------------
-// log(Phi(bt) - Phi(at)) for at <= bt, through complements in the upper half.
+// log(Phi(bt) - Phi(at)) for at <= bt.  Intervals inside one half are taken in
+// logs, log Phi(bt) + log(-expm1(log Phi(at) - log Phi(bt))) (complements in the
+// upper half), which stays finite when both probabilities underflow; intervals
+// that straddle 0 take the plain difference.
 __device__ double log_interval_d(double at, double bt) {
   if (at == -INFINITY) return (bt == INFINITY) ? 0.0 : log_Phi(bt);
   if (at > 0.0) {
-    double dc = 0.5 * erfc(at * TLR_RSQRT2);
-    double ec = (bt == INFINITY) ? 0.0 : 0.5 * erfc(bt * TLR_RSQRT2);
-    return log(dc - ec);
+    const double lca = log_Phi(-at);
+    if (bt == INFINITY) return lca;
+    return lca + log(-expm1(log_Phi(-bt) - lca));
   }
-  double d = 0.5 * erfc(-at * TLR_RSQRT2);
-  double e = (bt == INFINITY) ? 1.0 : (bt < 0.0 ? 0.5 * erfc(-bt * TLR_RSQRT2) : 1.0 - 0.5 * erfc(bt * TLR_RSQRT2));
+  if (bt <= 0.0) {
+    const double lb = log_Phi(bt);
+    return lb + log(-expm1(log_Phi(at) - lb));
+  }
+  const double d = 0.5 * erfc(-at * TLR_RSQRT2);
+  const double e = (bt == INFINITY) ? 1.0 : 1.0 - 0.5 * erfc(bt * TLR_RSQRT2);
   return log(e - d);
 }
 // Mean of N(0,1) truncated to (at, bt).

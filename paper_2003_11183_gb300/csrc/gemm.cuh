@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(256) k_gemm_nn(int M, int64_t N, int64_t K, co
 // steps of 8 with the next step's tile prefetched into registers while the
 // current one is multiplied (shared memory double-buffered, one barrier per step).
 // Requires lda, ldb, ldc multiples of 4, 16-byte aligned A, B, C and K a multiple of 8.
-static __global__ void __launch_bounds__(256) k_sgemm128(int M, int64_t N, int K, const float* __restrict__ A, int64_t lda,
+static __global__ void __launch_bounds__(256, 2) k_sgemm128(int M, int64_t N, int K, const float* __restrict__ A, int64_t lda,
                                                   const float* __restrict__ B, int64_t ldb, float* __restrict__ C,
                                                   int64_t ldc, const int32_t* __restrict__ rowmap, int accumulate) {
   __shared__ __align__(16) float As[2][8][128];

@@ -1,14 +1,17 @@
 // BF16 x BF16 -> FP32 GEMM on the 5th-generation tensor cores (tcgen05, sm_103a)
-// for the low-rank limit shifts of the BF16-shift integrand.
+// for the low-rank limit shifts, the projections and the in-tile coupling of the
+// BF16-shift integrand.
 //
 //   D (M x N) = A (M x K) * B (N x K)^T      both operands K-major bf16
 //
-// One 128 x 256 output tile per CTA of 128 threads.  Operands are staged by
-// TMA (128-byte swizzle) through a 4-stage shared-memory ring; one thread
-// issues tcgen05.mma (M=128, N=256, K=16) into a TMEM accumulator; after the
-// last k-block all four warps read their 32 TMEM lanes and run the epilogue:
-//   EPI_ROWMAJOR_F32:  D[row * ldd + col] = acc              (limit shifts, fp32)
-//   EPI_COLMAP_BF16:   W[col * ldw + map[row]] = bf16(acc)   (projections, bf16)
+// One 128 x BN output tile per CTA of 128 threads (BN = 64, 128 or 256, a
+// template parameter).  Operands are staged by TMA (128-byte swizzle) through a
+// ring of shared-memory stages; one thread issues tcgen05.mma (M=128, N=BN,
+// K=16) into a TMEM accumulator of BN columns; after the last k-block all four
+// warps read their 32 TMEM lanes (one output row each) and run the epilogue:
+//   EPI_TRANS_F32:    D[col * ldd + row] = acc, or += acc  (fp32; the rows are
+//                     samples, so a warp's stores cover 32 consecutive samples)
+//   EPI_COLMAP_BF16:  W[col * ldw + map[row]] = bf16(acc)   (projections, bf16)
 // Every mbarrier wait is bounded; on expiry the CTA records an error code,
 // skips the remaining work, frees its TMEM and returns.
 #pragma once
@@ -18,19 +21,31 @@
 namespace tlrmvn {
 namespace tc {
 
-constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr int BM = 128, BK = 64;
 constexpr int A_BYTES = BM * BK * 2;  // 16 KB
-constexpr int B_BYTES = BN * BK * 2;  // 32 KB
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
-constexpr int TMEM_COLS = 256;
 constexpr uint32_t WAIT_LIMIT = 1u << 24;  // polls before a wait gives up (seconds)
 
-enum { EPI_ROWMAJOR_F32 = 0, EPI_COLMAP_BF16 = 1 };
+enum { EPI_TRANS_F32 = 0, EPI_COLMAP_BF16 = 1 };
 
-// Instruction descriptor of tcgen05.mma kind::f16: fp32 accumulator, bf16 A and
-// B, both K-major, N = 256 (bits 17-22 hold N/8), M = 128 (bits 24-28 hold M/16).
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+// Shape of one kernel configuration: B tile bytes, stage bytes (SPLIT stages
+// hold hi and lo tiles of both operands), stage count and shared memory.  Stages
+// are sized so that two CTAs share an SM where they fit in about 100 KB each.
+// SPLIT configurations serve short-K products (the in-tile coupling, K <= 448):
+// one stage each, so that four CTAs share an SM and overlap one another.
+template <int BN, bool SPLIT>
+struct Cfg {
+  static constexpr int B_BYTES = BN * BK * 2;
+  static constexpr int HALF = A_BYTES + B_BYTES;  // [A][B] of one precision part
+  static constexpr int SB = SPLIT ? 2 * HALF : HALF;
+  static constexpr int NST = SPLIT ? 1 : ((4 * SB <= 100 * 1024) ? 4 : 2);
+  static constexpr int SMEM = NST * SB + 1024 /*align*/ + 256 /*barriers*/;
+  // instruction descriptor of tcgen05.mma kind::f16: fp32 accumulator, bf16 A
+  // and B, both K-major, N = BN (bits 17-22 hold N/8), M = 128 (bits 24-28 hold M/16)
+  static constexpr uint32_t IDESC =
+      (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+  static_assert(BN == 64 || BN == 128 || BN == 256, "N of the MMA");
+  static_assert(HALF % 1024 == 0 && A_BYTES % 1024 == 0, "128-byte swizzle atoms need 1024-byte alignment");
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -77,11 +92,11 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
           tmem_d),
-      "l"(a), "l"(b), "r"(IDESC), "r"(accumulate)
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
       : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -109,32 +124,41 @@ struct GemmTcArgs {
   int M, N, K;          // logical sizes; rows >= M and cols >= N are not stored
   int ax0, ay0;         // A tile origin in its tensor map (x = K, y = M)
   int bx0, by0;         // B tile origin (x = K, y = N)
-  float* D;             // EPI_ROWMAJOR_F32
+  float* D;             // EPI_TRANS_F32
   int64_t ldd;
   __nv_bfloat16* W;     // EPI_COLMAP_BF16
   int64_t ldw;
   const int32_t* map;
   int* err;             // nonzero after a wait expired
+  // SPLIT kernels: operands x = hi + lo with the lo halves at x offsets alo (A)
+  // and blo (B) of the same tensors; acc = A_hi B_hi + A_hi B_lo + A_lo B_hi
+  int alo = 0, blo = 0;
+  int accumulate = 0;   // EPI_TRANS_F32: D += acc
+  int rows_fast = 0;    // grid: blockIdx.x walks the M blocks (CTAs that share a B tile run together)
 };
 
-template <int EPI>
-__global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUtensorMap mapA,
-                                                    const __grid_constant__ CUtensorMap mapB, GemmTcArgs p) {
+// A's tensor map has a box of 64 x 128 (BM rows), B's a box of 64 x BN.
+template <int EPI, bool SPLIT, int BN>
+__global__ void __launch_bounds__(128) k_gemm_tc(const __grid_constant__ CUtensorMap mapA,
+                                                 const __grid_constant__ CUtensorMap mapB, GemmTcArgs p) {
+  using G = Cfg<BN, SPLIT>;
+  constexpr int NST = G::NST;
+  constexpr uint32_t SB = G::SB;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
-  uint64_t* empty = full + STAGES;
-  uint64_t* done = empty + STAGES;
+  uint64_t* full = (uint64_t*)(smem + NST * SB);
+  uint64_t* empty = full + NST;
+  uint64_t* done = empty + NST;
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
   __shared__ int abort_flag;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int m0 = (p.rows_fast ? blockIdx.x : blockIdx.y) * BM, n0 = (p.rows_fast ? blockIdx.y : blockIdx.x) * BN;
   const int nk = (p.K + BK - 1) / BK;
 
   if (threadIdx.x == 0) {
     abort_flag = 0;
-    for (int s = 0; s < STAGES; s++) {
+    for (int s = 0; s < NST; s++) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -143,7 +167,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUte
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(TMEM_COLS)
+                 "r"(BN)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -156,65 +180,93 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUte
     // TMA producer
     int issued = 0;
     for (int kb = 0; kb < nk; kb++) {
-      const int s = kb % STAGES;
-      if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1, p.err, 2)) {
+      const int s = kb % NST;
+      if (kb >= NST && !mbar_wait(&empty[s], ((kb / NST) - 1) & 1, p.err, 2)) {
         abort_flag = 1;
         break;
       }
       if (*(volatile int*)&abort_flag) break;
-      unsigned char* sa = smem + s * STAGE_BYTES;
-      mbar_expect_tx(&full[s], STAGE_BYTES);
+      unsigned char* sa = smem + s * SB;
+      mbar_expect_tx(&full[s], SB);
       tma_load_2d(sa, &mapA, &full[s], p.ax0 + kb * BK, p.ay0 + m0);
       tma_load_2d(sa + A_BYTES, &mapB, &full[s], p.bx0 + kb * BK, p.by0 + n0);
+      if (SPLIT) {
+        tma_load_2d(sa + G::HALF, &mapA, &full[s], p.ax0 + p.alo + kb * BK, p.ay0 + m0);
+        tma_load_2d(sa + G::HALF + A_BYTES, &mapB, &full[s], p.bx0 + p.blo + kb * BK, p.by0 + n0);
+      }
       issued = kb + 1;
     }
     if (*(volatile int*)&abort_flag) {
       // drain: wait (bounded) for the copies still in flight before the CTA exits
-      for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; kb++)
-        mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, p.err, 5);
+      for (int kb = (issued > NST ? issued - NST : 0); kb < issued; kb++)
+        mbar_wait(&full[kb % NST], (kb / NST) & 1, p.err, 5);
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
     bool ok = true;
     for (int kb = 0; kb < nk && ok; kb++) {
-      const int s = kb % STAGES;
-      if (!mbar_wait(&full[s], (kb / STAGES) & 1, p.err, 3)) {
+      const int s = kb % NST;
+      if (!mbar_wait(&full[s], (kb / NST) & 1, p.err, 3)) {
         abort_flag = 1;
         ok = false;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+      const uint32_t sa = smem_u32(smem + s * SB);
       const uint64_t da = sdesc(sa), db = sdesc(sa + A_BYTES);
 #pragma unroll
-      for (int kk = 0; kk < BK / 16; kk++)
-        mma_bf16(tmem, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), (kb > 0 || kk > 0) ? 1u : 0u);
+      for (int kk = 0; kk < BK / 16; kk++) {
+        // +2 per 16-element k-step: 32 bytes in the descriptor's 16-byte units
+        mma_bf16(tmem, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), G::IDESC, (kb > 0 || kk > 0) ? 1u : 0u);
+        if (SPLIT) {
+          const uint64_t dal = sdesc(sa + G::HALF), dbl = sdesc(sa + G::HALF + A_BYTES);
+          mma_bf16(tmem, da + (uint64_t)(kk * 2), dbl + (uint64_t)(kk * 2), G::IDESC, 1u);
+          mma_bf16(tmem, dal + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), G::IDESC, 1u);
+        }
+      }
       mma_commit(&empty[s]);
     }
     mma_commit(done);
   }
   __syncwarp();
+  const int row = m0 + 32 * warp + lane;
+  // PRE: the output row's old values (accumulate) are loaded while the MMAs run;
+  // the epilogue warps have nothing else to do until the accumulator is ready
+  constexpr bool PRE = (EPI == EPI_TRANS_F32) && BN <= 64;
+  float pre[PRE ? BN : 1];
+  if (PRE) {
+    const bool ld = p.accumulate && row < p.M;
+    const float* src = p.D + (int64_t)n0 * p.ldd + row;
+#pragma unroll
+    for (int q = 0; q < (PRE ? BN : 1); q++) pre[q] = (ld && n0 + q < p.N) ? __ldcs(src + (int64_t)q * p.ldd) : 0.0f;
+  }
   // epilogue: every warp reads its 32 TMEM lanes (rows m0 + 32*warp + lane)
   const bool ready = mbar_wait(done, 0, p.err, 4);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (ready && !*(volatile int*)&abort_flag) {
-    const int row = m0 + 32 * warp + lane;
     const uint32_t tbase = tmem + ((uint32_t)(32 * warp) << 16);
-    if (EPI == EPI_ROWMAJOR_F32) {
+    if (EPI == EPI_TRANS_F32) {
+#pragma unroll
       for (int c = 0; c < BN / 32; c++) {
         float v[32];
         tmem_ld32(tbase + c * 32, v);
         const int col0 = n0 + c * 32;
         if (row < p.M) {
-          float* dst = p.D + (int64_t)row * p.ldd + col0;
-          if (col0 + 32 <= p.N && ((p.ldd & 3) == 0)) {
+          float* dst = p.D + (int64_t)col0 * p.ldd + row;
+          if (PRE) {
 #pragma unroll
-            for (int q = 0; q < 8; q++)
-              reinterpret_cast<float4*>(dst)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-          } else {
-            for (int q = 0; q < 32; q++)
-              if (col0 + q < p.N) dst[q] = v[q];
+            for (int q = 0; q < 32; q++) v[q] += pre[(c * 32 + q) % (PRE ? BN : 1)];
+          } else if (p.accumulate) {
+            // all 32 old values are loaded before any store, so the loads overlap
+            float old[32];
+#pragma unroll
+            for (int q = 0; q < 32; q++) old[q] = (col0 + q < p.N) ? __ldcs(dst + (int64_t)q * p.ldd) : 0.0f;
+#pragma unroll
+            for (int q = 0; q < 32; q++) v[q] += old[q];
           }
+#pragma unroll
+          for (int q = 0; q < 32; q++)
+            if (col0 + q < p.N) dst[(int64_t)q * p.ldd] = v[q];
         }
       }
     } else {
@@ -233,7 +285,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUte
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
   }
 }
 

@@ -157,6 +157,7 @@ struct DiagArgs32 {
   int64_t ldyv;
   __nv_bfloat16* Ys;     // y sample-major bf16, Ys[c * ldys + v], or null
   int64_t ldys;
+  int64_t ys_lo;         // > 0: also the low part bf16(y - hi) at Ys[c * ldys + ys_lo + v]
   double* logP;
 };
 
@@ -168,8 +169,17 @@ struct DiagArgs32 {
 // shifting window of accumulators (so the special-function code exists once).
 constexpr int DIAG_VB = 16;
 // Sub-tile of the float sweep: couplings between sub-tiles of one diagonal tile
-// are applied as a dense product before the sweep of each sub-tile.
+// are applied as a dense product before the sweep of each sub-tile.  DIAG_SUB is
+// the largest sub-tile and the one of the SIMT coupling; the tensor-core coupling
+// takes sweep_sub_tc() (64, the faster; TLRMVN_SUB=128 selects 128 in tuning runs).
 constexpr int DIAG_SUB = 128;
+static int sweep_sub_tc() {
+  static const int v = [] {
+    const char* e = getenv("TLRMVN_SUB");
+    return (e && atoi(e) == 128) ? 128 : 64;
+  }();
+  return v;
+}
 // Extra floats after the transposed tiles: the accumulator window may read up
 // to DIAG_VB - 1 entries past the last row.
 constexpr int DIAG_PAD = 32;
@@ -333,7 +343,12 @@ __global__ void k_diag_f32(DiagArgs32 p) {
     for (int j = warp; j < SPT * bd; j += nw) {
       if (c0 + j >= p.C) break;
       __nv_bfloat16* row = p.Ys + (c0 + j) * p.ldys;
-      for (int v = lane; v < p.mt; v += 32) put_y(row, v, ys[v * ld + j]);
+      for (int v = lane; v < p.mt; v += 32) {
+        const float yv = ys[v * ld + j];
+        const __nv_bfloat16 hi = __float2bfloat16_rn(yv);
+        row[v] = hi;
+        if (p.ys_lo) row[p.ys_lo + v] = __float2bfloat16_rn(yv - __bfloat162float(hi));
+      }
     }
   }
 }
@@ -440,6 +455,17 @@ __global__ void k_pad_v16(const double* Vcat, int m, int64_t my, int64_t count, 
   V16[t] = (u < m) ? __double2bfloat16(Vcat[row * m + u]) : __float2bfloat16(0.f);
 }
 
+// B16x2[(i*m + v) * 2my + h*my + u]: h = 0 hi = bf16(B_i[v][u]), h = 1 lo = bf16(B_i[v][u] - hi)
+__global__ void k_split_b16(const double* B, int m, int64_t my, int64_t count, __nv_bfloat16* out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  const int64_t row = t / (2 * my), c = t % (2 * my);
+  const int64_t u = c % my, h = c / my, i = row / m, v = row % m;
+  const double b = (u < m) ? B[(i * m + v) * m + u] : 0.0;
+  const __nv_bfloat16 hi = __double2bfloat16(b);
+  out[t] = h ? __double2bfloat16(b - (double)__bfloat162float(hi)) : hi;
+}
+
 static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 // float32 diagonal tiles: row-major B32, transposed BT32 (ld ldbt), reciprocal diagonal inv32
@@ -488,6 +514,11 @@ static int ensure_copies_locked(Factor& F, int precision, cudaStream_t st) {
     F.kw16 = std::max<int64_t>(F.kpad_off[r], 64);
     F.kmax16 = std::max<int64_t>((kmax + 63) / 64 * 64, 64);
     F.my16 = ((int64_t)m + 63) / 64 * 64;
+    if (m > sweep_sub_tc()) {
+      const int64_t nb2 = (int64_t)r * m * 2 * F.my16;
+      TLR_CHECK(dalloc(&F.B16x2, nb2));
+      k_split_b16<<<blocks_for(nb2, 256), 256, 0, st>>>(F.B, m, F.my16, nb2, F.B16x2);
+    }
     if (F.ktot) {
       // vmap16: for each Vcat row, its column in the padded rank space
       std::vector<int32_t> v16(F.ktot);
@@ -591,10 +622,10 @@ static int64_t chunk_simt(const tlrmvn_opts& o, int64_t S, int64_t ktot, int m, 
   const double per = (double)(ktot + 2 * m) * es + 16.0;
   return round_chunk((int64_t)std::max(256.0, std::min((double)S, budget / per)), S);
 }
-static int64_t chunk_bf16(const tlrmvn_opts& o, int64_t S, int64_t kw, int64_t my, int m) {
+static int64_t chunk_bf16(const tlrmvn_opts& o, int64_t S, int64_t kw, int64_t ly, int m) {
   if (o.sample_chunk > 0) return round_chunk(o.sample_chunk, S);
   const double budget = 32.0 * (1ull << 30);
-  const double per = (double)kw * 2 + (double)my * 2 + (double)m * 8 + 16.0;
+  const double per = (double)kw * 2 + (double)ly * 2 + (double)m * 4 + 16.0;
   return round_chunk((int64_t)std::max(256.0, std::min((double)S, budget / per)), S);
 }
 
@@ -639,11 +670,19 @@ static SweepKernel sweep_kernel(const SweepVariant& v) {
       {{k_diag_f32<2, false, false>, k_diag_f32<2, false, true>}, {k_diag_f32<2, true, false>, k_diag_f32<2, true, true>}}};
   return table[v.spt - 1][v.pipe][v.dstage];
 }
-// Samples per block and shared memory of the float sweep over DIAG_SUB-variable sub-tiles.
-static int sub_threads(int m) { return diag_threads<float>(std::min(m, DIAG_SUB)); }
-static size_t sub_smem(int m) { return (size_t)std::min(m, DIAG_SUB) * (sub_threads(m) + 1) * sizeof(float); }
-static int set_sweep_smem(int m) {
-  TLR_CHECK(raise_smem_limit((const void*)sweep_kernel(sweep_variant()), sub_smem(m)));
+// Samples per block and shared memory of the float sweep over sub-variable
+// sub-tiles.  128 samples per block: at the sweep's ~96 registers a thread, an SM
+// holds 5 such blocks when the sub-tile's y fit (64-variable sub-tiles), 3 at 128.
+static int sub_threads(int m, int sub) {
+  (void)m;
+  (void)sub;
+  return 128;
+}
+static size_t sub_smem(int m, int sub) {
+  return (size_t)std::min(m, sub) * (sub_threads(m, sub) + 1) * sizeof(float);
+}
+static int set_sweep_smem(int m, int sub) {
+  TLR_CHECK(raise_smem_limit((const void*)sweep_kernel(sweep_variant()), sub_smem(m, sub)));
   return TLRMVN_OK;
 }
 
@@ -653,18 +692,45 @@ static int set_sweep_smem(int m) {
 // dense product; y goes to Yv (float, variable-major, ld C) and, when Ys is
 // given, to Ys (bf16, sample-major, ld ldys).  has_shift: Dl already holds the
 // low-rank shifts of this tile.
+// Tensor-core in-tile coupling (BF16-shift path): tensor maps of F.B16x2 and of
+// the sample-major hi/lo y buffer, the offset of the lo halves, the error flag.
+struct TcCouple {
+  CUtensorMap mapB, mapY;
+  int64_t my;
+  int sub;  // sub-tile size, a multiple of 64
+  int* err;
+};
+
 static void sweep_tile_f32(const Factor& F, int i, bool has_shift, float* Dl, int64_t C, const Lims& L,
                            const float* rs32, const uint64_t* dD, int64_t c0, int64_t N, int64_t Cc, int periodize,
-                           float* Yv, __nv_bfloat16* Ys, int64_t ldys, double* logP, cudaStream_t st, Prof& pf) {
+                           float* Yv, __nv_bfloat16* Ys, int64_t ldys, double* logP, cudaStream_t st, Prof& pf,
+                           const TcCouple* tcc = nullptr) {
   const int m = F.m, mt = (int)F.tsize(i);
-  const int bd = sub_threads(m);
-  const size_t smem = sub_smem(m);
+  const int sub = tcc ? tcc->sub : DIAG_SUB;
+  const int bd = sub_threads(m, sub);
+  const size_t smem = sub_smem(m, sub);
   const float* Bi = F.B32 + (size_t)i * m * m;
-  for (int q0 = 0; q0 < mt; q0 += DIAG_SUB) {
-    const int mq = std::min(DIAG_SUB, mt - q0);
+  for (int q0 = 0; q0 < mt; q0 += sub) {
+    const int mq = std::min(sub, mt - q0);
     if (q0 > 0) {
       pf.begin(TLRMVN_KC_COUPLE);
-      gemm_nn<float>(st, mq, Cc, q0, Bi + (size_t)q0 * m, m, Yv, C, Dl + (size_t)q0 * C, C, nullptr, has_shift ? 1 : 0);
+      if (tcc) {
+        // Dl[q0 + v][c] (+)= sum_{u < q0} B_i[q0 + v][u] y_u[c] as hi*hi + hi*lo + lo*hi
+        // transposed: rows = samples (A = y, hi/lo), columns = the sub-tile's variables
+        tc::GemmTcArgs g{(int)Cc, mq, q0, 0, 0, 0, i * m + q0, Dl + (size_t)q0 * C, C, nullptr, 0, nullptr, tcc->err};
+        g.alo = (int)tcc->my;
+        g.blo = (int)tcc->my;
+        g.accumulate = has_shift ? 1 : 0;
+        const dim3 grid(1, (unsigned)((Cc + tc::BM - 1) / tc::BM));
+        if (tcc->sub == 64)
+          tc::k_gemm_tc<tc::EPI_TRANS_F32, true, 64><<<grid, 128, tc::Cfg<64, true>::SMEM, st>>>(tcc->mapY, tcc->mapB, g);
+        else
+          tc::k_gemm_tc<tc::EPI_TRANS_F32, true, 128><<<grid, 128, tc::Cfg<128, true>::SMEM, st>>>(tcc->mapY, tcc->mapB,
+                                                                                                  g);
+      } else {
+        gemm_nn<float>(st, mq, Cc, q0, Bi + (size_t)q0 * m, m, Yv, C, Dl + (size_t)q0 * C, C, nullptr,
+                       has_shift ? 1 : 0);
+      }
       pf.end();
     }
     DiagArgs32 a;
@@ -686,10 +752,11 @@ static void sweep_tile_f32(const Factor& F, int i, bool has_shift, float* Dl, in
     a.C = Cc;
     a.periodize = periodize;
     a.first = (i == 0 && q0 == 0);
-    a.Yv = Yv + (size_t)q0 * C;
+    a.Yv = Yv ? Yv + (size_t)q0 * C : nullptr;
     a.ldyv = C;
     a.Ys = Ys ? Ys + q0 : nullptr;
     a.ldys = ldys;
+    a.ys_lo = tcc ? tcc->my : 0;
     a.logP = logP;
     pf.begin(TLRMVN_KC_DIAG);
     const SweepVariant sv = sweep_variant();
@@ -719,7 +786,7 @@ static int run_chunks(Factor& F, const T* Bt, const T* Ut, const T* Vt, const Li
   const int bd = diag_threads<T>(m);
   const size_t smem = (size_t)m * (bd + 1) * sizeof(T);
   if (f32)
-    TLR_CHECK(set_sweep_smem(m));
+    TLR_CHECK(set_sweep_smem(m, DIAG_SUB));
   else
     TLR_CHECK(raise_smem_limit((const void*)k_diag<T, YT, false>, (size_t)smem));
 
@@ -782,42 +849,59 @@ static int run_chunks(Factor& F, const T* Bt, const T* Ut, const T* Vt, const Li
 }
 
 // BF16-shift integrand: float32 sweep; both low-rank products on tcgen05 with
-// bf16 operands and fp32 accumulation.  Layouts (C = samples in the chunk):
+// bf16 operands and fp32 accumulation, and the coupling between the 128-variable
+// sub-tiles of a diagonal tile on tcgen05 with split operands (x = hi + lo, both
+// bf16; hi*hi + hi*lo + lo*hi, relative error ~1e-5).  Layouts (C = samples in the chunk):
 //   W16  C x kw16  bf16, sample-major: row c holds the projections of sample c
-//   Y16  C x my16  bf16, sample-major
+//   Y16  C x ly    bf16, sample-major: the tile's y (hi) in columns [0, my16), and
+//                  for tiles over 128 variables bf16(y - hi) in [my16, 2 my16)
 //   Dl   m x C     fp32, variable-major (read by the sweep)
 static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opts& o, const uint64_t* dD,
                            double* logP, Scratch& sc, cudaStream_t st, Prof& pf) {
   const int64_t M = o.n_shifts, N = o.n_points, S = M * N;
   const int m = F.m;
-  const int64_t C = chunk_bf16(o, S, F.kw16, F.my16, m);
+  const int64_t ly = F.B16x2 ? 2 * F.my16 : F.my16;  // Y16 row: hi halves (then lo halves)
+  const int64_t C = chunk_bf16(o, S, F.kw16, ly, m);
   __nv_bfloat16 *W = nullptr, *Y = nullptr;
-  float *Dl = nullptr, *Yv = nullptr;
+  float* Dl = nullptr;
   float* rs32 = nullptr;
   int* err = nullptr;
   TLR_CHECK(sc.get(&W, (size_t)F.kw16 * C));
-  TLR_CHECK(sc.get(&Y, (size_t)F.my16 * C));
+  TLR_CHECK(sc.get(&Y, (size_t)ly * C));
   TLR_CHECK(sc.get(&Dl, (size_t)m * C));
-  TLR_CHECK(sc.get(&Yv, (size_t)m * C));
   TLR_CHECK(sc.get(&err, 1));
   const bool mvt = std::isfinite(nu);
   if (mvt) TLR_CHECK(sc.get(&rs32, (size_t)C));
   // padding columns of W and Y must hold finite values: they meet zero operand columns
   TLR_CUDA(cudaMemsetAsync(W, 0, (size_t)F.kw16 * C * 2, st));
-  TLR_CUDA(cudaMemsetAsync(Y, 0, (size_t)F.my16 * C * 2, st));
+  TLR_CUDA(cudaMemsetAsync(Y, 0, (size_t)ly * C * 2, st));
   TLR_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
 
+  // tensor maps (box 64 x rows): A operands take 128-row boxes, B operands BN-row boxes
+  //   shift      Dl^T (samples x vars) = W16 rows (A) x U16 rows (B, N = 256)
+  //   projection W16 columns <- V16 rows (A) x Y16 rows (B, N = 256)
+  //   coupling   Dl^T += Y16 rows (A, hi/lo) x B16x2 rows (B, hi/lo, N = sub-tile)
   CUtensorMap mapU, mapV, mapW, mapY;
   if (F.ktot) {
-    TLR_CHECK(make_map(&mapU, F.U16, F.kmax16, (uint64_t)F.r * m, F.kmax16 * 2, tc::BM));
+    TLR_CHECK(make_map(&mapU, F.U16, F.kmax16, (uint64_t)F.r * m, F.kmax16 * 2, 256));
     TLR_CHECK(make_map(&mapV, F.V16, F.my16, F.ktot, F.my16 * 2, tc::BM));
   }
-  TLR_CHECK(make_map(&mapW, W, F.kw16, C, F.kw16 * 2, tc::BN));
-  TLR_CHECK(make_map(&mapY, Y, F.my16, C, F.my16 * 2, tc::BN));
-  TLR_CHECK(raise_smem_limit((const void*)tc::k_gemm_tc<tc::EPI_ROWMAJOR_F32>, (size_t)tc::SMEM_BYTES));
-  TLR_CHECK(raise_smem_limit((const void*)tc::k_gemm_tc<tc::EPI_COLMAP_BF16>, (size_t)tc::SMEM_BYTES));
+  TLR_CHECK(make_map(&mapW, W, F.kw16, C, F.kw16 * 2, tc::BM));
+  TLR_CHECK(make_map(&mapY, Y, ly, C, ly * 2, 256));
+  TcCouple tcc;
+  if (F.B16x2) {
+    tcc.sub = sweep_sub_tc();
+    TLR_CHECK(make_map(&tcc.mapB, F.B16x2, ly, (uint64_t)F.r * m, ly * 2, (uint32_t)tcc.sub));
+    TLR_CHECK(make_map(&tcc.mapY, Y, ly, C, ly * 2, tc::BM));
+    tcc.my = F.my16;
+    tcc.err = err;
+  }
+  TLR_CHECK(raise_smem_limit((const void*)tc::k_gemm_tc<tc::EPI_TRANS_F32, false, 256>, tc::Cfg<256, false>::SMEM));
+  TLR_CHECK(raise_smem_limit((const void*)tc::k_gemm_tc<tc::EPI_COLMAP_BF16, false, 256>, tc::Cfg<256, false>::SMEM));
+  TLR_CHECK(raise_smem_limit((const void*)tc::k_gemm_tc<tc::EPI_TRANS_F32, true, 64>, tc::Cfg<64, true>::SMEM));
+  TLR_CHECK(raise_smem_limit((const void*)tc::k_gemm_tc<tc::EPI_TRANS_F32, true, 128>, tc::Cfg<128, true>::SMEM));
 
-  TLR_CHECK(set_sweep_smem(m));
+  TLR_CHECK(set_sweep_smem(m, sweep_sub_tc()));
 
   for (int64_t c0 = 0; c0 < S; c0 += C) {
     const int64_t Cc = std::min(C, S - c0);
@@ -827,26 +911,28 @@ static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opt
                                                        o.periodize);
       pf.end();
     }
-    const unsigned ntile = (unsigned)((Cc + tc::BN - 1) / tc::BN);
+    const unsigned sblocks = (unsigned)((Cc + tc::BM - 1) / tc::BM), ntile = (unsigned)((Cc + 255) / 256);
     for (int i = 0; i < F.r; i++) {
       const int mt = (int)F.tsize(i);
       const int64_t Kr = F.krow(i), Kc = F.kcol(i);
       const float* Delta = nullptr;
       if (Kr > 0) {
-        tc::GemmTcArgs g{mt, (int)Cc, (int)Kr, 0, i * m, (int)F.kpad_off[i], 0, Dl, C, nullptr, 0, nullptr, err};
+        tc::GemmTcArgs g{(int)Cc, mt, (int)Kr, (int)F.kpad_off[i], 0, 0, i * m, Dl, C, nullptr, 0, nullptr, err};
         pf.begin(TLRMVN_KC_SHIFT);
-        tc::k_gemm_tc<tc::EPI_ROWMAJOR_F32><<<dim3(ntile, (unsigned)((mt + tc::BM - 1) / tc::BM)), 128,
-                                               tc::SMEM_BYTES, st>>>(mapU, mapW, g);
+        tc::k_gemm_tc<tc::EPI_TRANS_F32, false, 256><<<dim3((unsigned)((mt + 255) / 256), sblocks), 128,
+                                                       tc::Cfg<256, false>::SMEM, st>>>(mapW, mapU, g);
         pf.end();
         Delta = Dl;
       }
-      sweep_tile_f32(F, i, Delta != nullptr, Dl, C, L, rs32, dD, c0, N, Cc, o.periodize, Yv, Y, F.my16, logP, st, pf);
+      sweep_tile_f32(F, i, Delta != nullptr, Dl, C, L, rs32, dD, c0, N, Cc, o.periodize, nullptr, Y, ly, logP, st, pf,
+                     F.B16x2 ? &tcc : nullptr);
       if (Kc > 0) {
         tc::GemmTcArgs g{(int)Kc, (int)Cc, mt, 0, (int)F.kcol_off[i], 0, 0, nullptr, 0, W, F.kw16,
                          F.vmap16 + F.kcol_off[i], err};
+        g.rows_fast = 1;  // the rank blocks of one sample tile run together and share its y in L2
         pf.begin(TLRMVN_KC_VPROJ);
-        tc::k_gemm_tc<tc::EPI_COLMAP_BF16><<<dim3(ntile, (unsigned)((Kc + tc::BM - 1) / tc::BM)), 128,
-                                              tc::SMEM_BYTES, st>>>(mapV, mapY, g);
+        tc::k_gemm_tc<tc::EPI_COLMAP_BF16, false, 256><<<dim3((unsigned)((Kc + tc::BM - 1) / tc::BM), ntile), 128,
+                                                         tc::Cfg<256, false>::SMEM, st>>>(mapV, mapY, g);
         pf.end();
       }
     }
@@ -855,7 +941,7 @@ static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opt
   int herr = 0;
   TLR_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
   TLR_CUDA(cudaStreamSynchronize(st));
-  if (herr) return fail(TLRMVN_E_CUDA, "tensor-core shift kernel gave up waiting (code " + std::to_string(herr) + ")");
+  if (herr) return fail(TLRMVN_E_TIMEOUT, "tensor-core kernel gave up waiting (code " + std::to_string(herr) + ")");
   return TLRMVN_OK;
 }
 
@@ -868,9 +954,9 @@ int64_t prob_scratch_bytes(const Factor& F, const tlrmvn_opts& o) {
     int64_t kw = 0;
     for (int i = 0; i < F.r; i++) kw += (F.krow(i) + 63) / 64 * 64;
     kw = std::max<int64_t>(kw, 64);
-    const int64_t my = (m + 63) / 64 * 64;
-    const int64_t C = chunk_bf16(o, S, kw, my, m);
-    bytes += C * (kw * 2 + my * 2 + m * 8 + 4);
+    const int64_t my = (m + 63) / 64 * 64, ly = m > sweep_sub_tc() ? 2 * my : my;
+    const int64_t C = chunk_bf16(o, S, kw, ly, m);
+    bytes += C * (kw * 2 + ly * 2 + m * 4 + 4);
   } else {
     const int64_t es = o.precision == TLRMVN_FP64 ? 8 : 4;
     const int64_t C = chunk_simt(o, S, F.ktot, m, es);

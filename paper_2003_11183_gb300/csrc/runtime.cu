@@ -108,6 +108,7 @@ Factor::~Factor() {
   dfree(V32);
   dfree(U16);
   dfree(V16);
+  dfree(B16x2);
   dfree(vmap16);
   dfree(Q);
   dfree(dperm);
@@ -219,6 +220,7 @@ extern "C" const char* tlrmvn_strerror(int status) {
     case TLRMVN_E_CUDA: return "CUDA error";
     case TLRMVN_E_FORMAT: return "malformed factor buffer";
     case TLRMVN_E_NOTSUP: return "not supported";
+    case TLRMVN_E_TIMEOUT: return "device-side wait timed out";
     default: return "unknown status";
   }
 }
@@ -254,6 +256,13 @@ extern "C" int tlrmvn_factor_info(tlrmvn_factor_t f, int64_t* n, int* r, int* m,
   if (m) *m = F.m;
   if (k_total) *k_total = F.ktot;
   if (capped) *capped = F.capped;
+  return TLRMVN_OK;
+}
+
+extern "C" int tlrmvn_factor_ranks(tlrmvn_factor_t f, int32_t* ranks) {
+  if (!f || !ranks) return fail(TLRMVN_E_INVAL, "null argument");
+  const Factor& F = *reinterpret_cast<Factor*>(f);
+  std::memcpy(ranks, F.rank.data(), F.rank.size() * sizeof(int32_t));
   return TLRMVN_OK;
 }
 

@@ -79,6 +79,27 @@ def test_two_sided_and_upper_tail_limits(tl):
     assert np.all(rel(ps, ref["per_shift"]) < 1e-4)
 
 
+def test_deep_tail_limits(tl):
+    # limits whose interval probabilities lie below the float64 range: one-sided
+    # lower tails, two-sided intervals in either half, upper tails.  Every
+    # per-sample value is finite and FP64 equals the oracle to 1e-9.
+    w = synth.small_workload(12, 48, 34, n_shifts=2, n_points=128, limits="twosided")
+    w.a[:] = -np.inf
+    w.b[:] = np.random.default_rng(5).uniform(0.0, 1.0, w.n)
+    w.b[0::5] = -45.0
+    w.a[1::5], w.b[1::5] = -41.0, -40.0
+    w.a[2::5], w.b[2::5] = 40.0, 41.0
+    w.a[3::5], w.b[3::5] = 42.0, np.inf
+    OF, _ = oracle_factor(w)
+    F = tl.tlrmvn_factor_import(export_bytes(OF))
+    (lp, err, ps, pm), ref = run_both(tl, F, OF, w, tl.FP64)
+    assert np.all(np.isfinite(ref["per_sample"])) and np.all(np.isfinite(pm))
+    assert np.all(rel(pm, ref["per_sample"]) < 1e-9)
+    (lp, err, ps, pm), ref = run_both(tl, F, OF, w, tl.FP32)
+    assert np.all(np.isfinite(pm))
+    assert np.all(rel(ps, ref["per_shift"]) < 1e-4)
+
+
 def test_gpu_factor_matches_oracle_factor(tl):
     for reorder in (0, 1, 2):
         w = synth.small_workload(16, 32, 34, n_shifts=2, n_points=64, reorder=reorder)
@@ -158,6 +179,8 @@ def test_export_import_round_trip(tl):
     buf = tl.tlrmvn_factor_export(F)
     F2 = tl.tlrmvn_factor_import(buf)
     assert tl.tlrmvn_factor_export(F2) == buf
+    ranks = tl.tlrmvn_factor_ranks(F)
+    assert np.array_equal(ranks, tl.parse_export(buf).rank) and ranks.sum() == tl.tlrmvn_factor_info(F)["k_total"]
     r1 = tl.tlrmvn_prob(F, w.a, w.b, math.inf, tl.FP64, 2, 64, shifts=w.shifts)
     r2 = tl.tlrmvn_prob(F2, w.a, w.b, math.inf, tl.FP64, 2, 64, shifts=w.shifts)
     assert r1[0] == r2[0]
@@ -189,6 +212,37 @@ def test_bf16_shift_path(tl, nu, ragged):
     assert np.all(rel(ps, ref["per_shift"]) < 1e-2)
     assert abs(lp - ref["logp"]) <= 3 * max(err, ref["err"])
     assert np.all(np.isfinite(pm))
+
+
+@pytest.mark.parametrize("nu", [math.inf, 7.0])
+def test_bf16_split_coupling_without_low_rank(tl, nu):
+    # Block-diagonal covariance in tiles of 256 (two 128-variable sub-tiles each)
+    # and a ragged last tile of 150: no low-rank blocks, so the BF16-shift path's
+    # only reduced precision is the coupling between sub-tiles, on tensor cores
+    # with split operands (x = hi + lo in bf16, relative error ~1e-5).  A
+    # single-bf16 coupling is off by about 1 in the per-sample log on this
+    # strongly correlated (1-D exponential, range 0.3) covariance; the split one
+    # stays near float32.
+    rng = np.random.default_rng(7)
+    sizes = [256, 256, 256, 150]
+    n = sum(sizes)
+    Sig = np.zeros((n, n))
+    o = 0
+    for s in sizes:
+        x = np.sort(rng.uniform(0.0, 1.0, s))
+        Sig[o:o + s, o:o + s] = np.exp(-np.abs(x[:, None] - x[None, :]) / 0.3) + 1e-8 * np.eye(s)
+        o += s
+    a = np.full(n, -np.inf)
+    b = rng.uniform(0.5, 1.5, n)
+    F = tl.tlrmvn_factor_dense(Sig, a, b, 256, 1e-8, 0, 0)
+    assert tl.tlrmvn_factor_info(F)["k_total"] == 0
+    OF = to_oracle_factor(tl.parse_export(tl.tlrmvn_factor_export(F)))
+    shifts = synth.lattice_shifts(4, n + 1, 77)
+    lp, err, ps, pm = tl.tlrmvn_prob(F, a, b, nu, tl.BF16_SHIFT, 4, 256, shifts=shifts, per_shift=True,
+                                     per_sample=True)
+    ref = sov.solve(OF, a, b, nu, shifts, 256)
+    assert np.all(np.abs(pm - ref["per_sample"]) <= 1e-4 * np.abs(ref["per_sample"]) + 5e-2)
+    assert np.all(rel(ps, ref["per_shift"]) < 1e-3)
 
 
 def _check_factor(OF, w, n_pairs=24, tol_mult=50):

@@ -254,8 +254,9 @@ const char* tlrmvn_last_error(void);   /* thread-local detail of the last failur
 #define TLRMVN_KC_VPROJ   2  /* projections  W_col_i = V_i^T y_i                    */
 #define TLRMVN_KC_CHI     3  /* Student-t scale chi_nu^-1(w0)/sqrt(nu)              */
 #define TLRMVN_KC_REDUCE  4  /* per-shift and cross-shift log-sum reductions        */
-#define TLRMVN_KC_COUPLE  5  /* in-tile coupling of 128-variable sub-tiles (FP32)   */
-#define TLRMVN_KC_COUNT   6
+#define TLRMVN_KC_COUPLE  5  /* in-tile coupling between sub-tiles of a diagonal tile */
+#define TLRMVN_KC_PREP    6  /* limit validation and permutation                    */
+#define TLRMVN_KC_COUNT   7
 
 /* Process-wide kernel timing: when enabled, every integrand launch is bracketed
  * by CUDA events on its stream and, once the call has completed, its device

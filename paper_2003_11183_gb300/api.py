@@ -255,8 +255,8 @@ def tlrmvn_estimate_noalloc(per_sample, n_shifts: int, n_points: int, out, per_s
                                             _stream_ptr(stream)), "tlrmvn_estimate_noalloc")
 
 
-KC_SHIFT, KC_DIAG, KC_VPROJ, KC_CHI, KC_REDUCE, KC_COUPLE = 0, 1, 2, 3, 4, 5
-KC_NAMES = ("shift", "diag", "vproj", "chi", "reduce", "couple")
+KC_SHIFT, KC_DIAG, KC_VPROJ, KC_CHI, KC_REDUCE, KC_COUPLE, KC_PREP = 0, 1, 2, 3, 4, 5, 6
+KC_NAMES = ("shift", "diag", "vproj", "chi", "reduce", "couple", "prep")
 
 
 def tlrmvn_profile_enable(on: bool):

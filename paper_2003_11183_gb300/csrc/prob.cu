@@ -183,164 +183,121 @@ static int sweep_sub_tc() {
 // Extra floats after the transposed tiles: the accumulator window may read up
 // to DIAG_VB - 1 entries past the last row.
 constexpr int DIAG_PAD = 32;
-// SPT samples per thread (samples c0 + tid + s * blockDim.x): every broadcast
-// load of B and of the per-variable constants serves SPT samples, and the SPT
-// special-function chains are independent instruction streams.
-// PIPE: software-pipeline the loads of each variable's lattice offset and
-// window column one variable ahead, and add the limit shifts after the sums.
-// DSTAGE: keep the block's (at most two) rows of lattice offsets in shared memory.
-template <int SPT, bool PIPE, bool DSTAGE>
+// Shared memory of one block: the sub-tile's y of each sample (ld = blockDim + 1
+// floats per variable), then the per-variable constants (lattice generator,
+// limits, reciprocal diagonal).  Small blocks (32 samples) keep the footprint
+// near 10 KB, so ~21 blocks share an SM and a launch over 100,000 samples runs
+// in one wave.
+__host__ __device__ inline size_t sweep_ys_bytes(int mt, int bd) {
+  return ((size_t)mt * (bd + 1) * sizeof(float) + 15) / 16 * 16;
+}
+__host__ __device__ inline size_t sweep_smem_bytes(int mt, int bd) {
+  return sweep_ys_bytes(mt, bd) + (size_t)mt * (sizeof(uint64_t) + 3 * sizeof(float));
+}
+
+// Each variable's lattice offset is loaded one variable ahead and its window
+// column before its special functions, and the block's limit shifts are added
+// after its sums over earlier variables, so that those loads are in flight
+// while other work runs.
 __global__ void k_diag_f32(DiagArgs32 p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* ys = reinterpret_cast<float*>(smem_raw);
-  __shared__ float s_a[DIAG_SUB], s_b[DIAG_SUB], s_inv[DIAG_SUB];
-  __shared__ uint64_t s_q[DIAG_SUB], s_d[2][DIAG_SUB];
-  const int bd = blockDim.x, tid = threadIdx.x, ld = SPT * bd + 1;
-  const int64_t c0 = (int64_t)blockIdx.x * bd * SPT;
+  const int bd = blockDim.x, tid = threadIdx.x, ld = bd + 1;
   const int mt = p.mt;
-  // the block's samples fall in at most two shift batches when a batch holds at
-  // least as many points as the block has samples: stage those rows of D
-  const int64_t sh_lo = (p.sample0 + c0) / p.N;
-  const int64_t sh_hi = (p.sample0 + min(c0 + (int64_t)bd * SPT, p.C) - 1) / p.N;
-  const bool d_staged = DSTAGE && sh_hi - sh_lo <= 1;
+  float* ys = reinterpret_cast<float*>(smem_raw);
+  uint64_t* s_q = reinterpret_cast<uint64_t*>(smem_raw + sweep_ys_bytes(mt, bd));
+  float* s_a = reinterpret_cast<float*>(s_q + mt);
+  float* s_b = s_a + mt;
+  float* s_inv = s_b + mt;
+  const int64_t c0 = (int64_t)blockIdx.x * bd;
   for (int t = tid; t < mt; t += bd) {
     s_a[t] = p.a[t];
     s_b[t] = p.b[t];
     s_inv[t] = p.inv[t];
     s_q[t] = p.Q[p.coord0 + t];
-    if (d_staged) {
-      s_d[0][t] = p.D[sh_lo * p.ldD + p.coord0 + t];
-      s_d[1][t] = (sh_hi > sh_lo) ? p.D[sh_hi * p.ldD + p.coord0 + t] : 0;
-    }
   }
   __syncthreads();
-  int64_t cs[SPT];
-  bool act[SPT];
-  uint64_t ks[SPT];
-  const uint64_t* Ds[SPT];
-  float rs[SPT], lp[SPT];
-  bool any = false;
+  const bool act = c0 + tid < p.C;
+  const int64_t cs = act ? c0 + tid : p.C - 1;  // inactive lanes shadow a valid sample, write nothing
+  const int64_t g = p.sample0 + cs;
+  const int64_t sh = g / p.N;
+  const uint64_t ks = (uint64_t)(g - sh * p.N) + 1;
+  const uint64_t* Ds = p.D + sh * p.ldD + p.coord0;
+  const float rs = p.rs ? p.rs[cs] : 1.0f;
+  // log P of the sub-tile = log(prod) + pe log 2 + lsum: prod is kept in [1, 2)
+  // with its binary exponent in pe, so it neither underflows nor needs a log per variable
+  float prod = 1.0f, lsum = 0.0f;
+  int pe = 0;
+  for (int v0 = 0; v0 < mt; v0 += DIAG_VB) {
+    const int nb = min(DIAG_VB, mt - v0);
+    float acc[DIAG_VB], dl[DIAG_VB];
 #pragma unroll
-  for (int s = 0; s < SPT; s++) {
-    act[s] = c0 + tid + s * bd < p.C;
-    any |= act[s];
-    cs[s] = act[s] ? c0 + tid + s * bd : p.C - 1;  // inactive lanes shadow a valid sample, write nothing
-    const int64_t g = p.sample0 + cs[s];
-    const int64_t sh = g / p.N;
-    ks[s] = (uint64_t)(g - sh * p.N) + 1;
-    Ds[s] = d_staged ? &s_d[sh - sh_lo][0] : p.D + sh * p.ldD + p.coord0;
-    rs[s] = p.rs ? p.rs[cs[s]] : 1.0f;
-    lp[s] = 0.0f;
-  }
-  if (any) {
-    for (int v0 = 0; v0 < mt; v0 += DIAG_VB) {
-      const int nb = min(DIAG_VB, mt - v0);
-      float acc[SPT][DIAG_VB];
-      // limit shifts of the block: with PIPE they are added after the sums over
-      // earlier variables, so their loads are in flight during that loop
-      float dl[SPT][DIAG_VB];
-#pragma unroll
-      for (int s = 0; s < SPT; s++)
-#pragma unroll
-        for (int j = 0; j < DIAG_VB; j++) {
-          dl[s][j] = (p.Delta && j < nb) ? p.Delta[(int64_t)(v0 + j) * p.ldd + cs[s]] : 0.0f;
-          acc[s][j] = PIPE ? 0.0f : dl[s][j];
-        }
-      // PIPE: the lattice offset and the window column of the next variable are
-      // loaded one variable ahead (first ones here, before the sums)
-      uint64_t dnext[SPT];
-      float bnext[DIAG_VB - 1];
-      if (PIPE) {
-#pragma unroll
-        for (int s = 0; s < SPT; s++) dnext[s] = Ds[s][v0];
-        const float* brow = p.BT + (int64_t)v0 * p.ldbt + v0 + 1;
-#pragma unroll
-        for (int i = 0; i < DIAG_VB - 1; i++) bnext[i] = __ldg(brow + i);
-      }
-      const float* bcol = p.BT + v0;
+    for (int j = 0; j < DIAG_VB; j++) {
+      dl[j] = (p.Delta && j < nb) ? p.Delta[(int64_t)(v0 + j) * p.ldd + cs] : 0.0f;
+      acc[j] = 0.0f;
+    }
+    // lattice offset of the block's first variable
+    uint64_t dnext = Ds[v0];
+    // sums over the sub-tile's earlier variables for the block's 16 variables
+    const float* bcol = p.BT + v0;
 #pragma unroll 2
-      for (int u = 0; u < v0; u++) {
-        float yu[SPT];
+    for (int u = 0; u < v0; u++) {
+      const float yu = ys[u * ld + tid];
+      const float4* b4 = reinterpret_cast<const float4*>(bcol + (int64_t)u * p.ldbt);
+      const float4 q[4] = {__ldg(b4), __ldg(b4 + 1), __ldg(b4 + 2), __ldg(b4 + 3)};
 #pragma unroll
-        for (int s = 0; s < SPT; s++) yu[s] = ys[u * ld + tid + s * bd];
-        const float4* b4 = reinterpret_cast<const float4*>(bcol + (int64_t)u * p.ldbt);
-        const float4 q[4] = {__ldg(b4), __ldg(b4 + 1), __ldg(b4 + 2), __ldg(b4 + 3)};
-#pragma unroll
-        for (int s = 0; s < SPT; s++)
-#pragma unroll
-          for (int h = 0; h < 4; h++) {
-            acc[s][4 * h] = fmaf(q[h].x, yu[s], acc[s][4 * h]);
-            acc[s][4 * h + 1] = fmaf(q[h].y, yu[s], acc[s][4 * h + 1]);
-            acc[s][4 * h + 2] = fmaf(q[h].z, yu[s], acc[s][4 * h + 2]);
-            acc[s][4 * h + 3] = fmaf(q[h].w, yu[s], acc[s][4 * h + 3]);
-          }
+      for (int h = 0; h < 4; h++) {
+        acc[4 * h] = fmaf(q[h].x, yu, acc[4 * h]);
+        acc[4 * h + 1] = fmaf(q[h].y, yu, acc[4 * h + 1]);
+        acc[4 * h + 2] = fmaf(q[h].z, yu, acc[4 * h + 2]);
+        acc[4 * h + 3] = fmaf(q[h].w, yu, acc[4 * h + 3]);
       }
-      if (PIPE) {
+    }
 #pragma unroll
-        for (int s = 0; s < SPT; s++)
-#pragma unroll
-          for (int j = 0; j < DIAG_VB; j++) acc[s][j] += dl[s][j];
-      }
+    for (int j = 0; j < DIAG_VB; j++) acc[j] += dl[j];
 #pragma unroll 1
-      for (int j = 0; j < nb; j++) {
-        const int v = v0 + j;
-        const float iv = s_inv[v], av = s_a[v], bv = s_b[v];
-        const uint64_t qv = s_q[v];
-        uint64_t dv[SPT];
-        float bcur[DIAG_VB - 1];
-        if (PIPE) {
-#pragma unroll
-          for (int s = 0; s < SPT; s++) dv[s] = dnext[s];
-#pragma unroll
-          for (int i = 0; i < DIAG_VB - 1; i++) bcur[i] = bnext[i];
-          const int vn = (j + 1 < nb) ? v + 1 : v;  // the last one reloads its own (in bounds)
-#pragma unroll
-          for (int s = 0; s < SPT; s++) dnext[s] = Ds[s][vn];
-          const float* brow = p.BT + (int64_t)vn * p.ldbt + vn + 1;
-#pragma unroll
-          for (int i = 0; i < DIAG_VB - 1; i++) bnext[i] = __ldg(brow + i);
-        } else {
-#pragma unroll
-          for (int s = 0; s < SPT; s++) dv[s] = Ds[s][v];
-        }
-        float y[SPT];
-#pragma unroll
-        for (int s = 0; s < SPT; s++) {
-          const float sum = acc[s][0];  // shifts + earlier variables, for variable v
-          const float at = (av * rs[s] - sum) * iv;
-          const float bt = (bv * rs[s] - sum) * iv;
-          float w, wc;
-          lattice_wf(ks[s] * qv + dv[s], p.periodize, w, wc);
-          float lv;
-          sov_step_f32(at, bt, w, wc, lv, y[s]);
-          lp[s] += lv;
-          ys[v * ld + tid + s * bd] = y[s];
-          if (p.Yv && act[s]) p.Yv[(int64_t)v * p.ldyv + cs[s]] = y[s];
-        }
-        // window shift: acc[i] <- acc[i+1] + B[v+1+i][v] y
+    for (int j = 0; j < nb; j++) {
+      const int v = v0 + j;
+      const float iv = s_inv[v], av = s_a[v], bv = s_b[v];
+      const uint64_t qv = s_q[v];
+      const uint64_t dv = dnext;
+      dnext = Ds[(j + 1 < nb) ? v + 1 : v];  // next variable's offset (the last one reloads its own)
+      // window column B[v+1..v+15][v], loaded before the step so that the loads
+      // are in flight during its special functions
+      float bcur[DIAG_VB - 1];
+      {
         const float* brow = p.BT + (int64_t)v * p.ldbt + v + 1;
 #pragma unroll
-        for (int i = 0; i < DIAG_VB - 1; i++) {
-          const float bb = PIPE ? bcur[i] : __ldg(brow + i);
-#pragma unroll
-          for (int s = 0; s < SPT; s++) acc[s][i] = fmaf(bb, y[s], acc[s][i + 1]);
-        }
-#pragma unroll
-        for (int s = 0; s < SPT; s++) acc[s][DIAG_VB - 1] = 0.0f;
+        for (int i = 0; i < DIAG_VB - 1; i++) bcur[i] = __ldg(brow + i);
       }
-    }
+      const float sum = acc[0];  // shifts + earlier variables, for variable v
+      const float at = (av * rs - sum) * iv;
+      const float bt = (bv * rs - sum) * iv;
+      float w, wc;
+      lattice_wf(ks * qv + dv, p.periodize, w, wc);
+      float f, la, y;
+      sov_step_f32_prod(at, bt, w, wc, f, la, y);
+      lsum += la;
+      prod *= f;  // prod in [1, 2) and f >= Phi(-12): a normal float
+      const int pb = __float_as_int(prod);
+      pe += (pb >> 23) - 127;
+      prod = __int_as_float((pb & 0x007FFFFF) | 0x3F800000);
+      ys[v * ld + tid] = y;
+      if (p.Yv && act) p.Yv[(int64_t)v * p.ldyv + cs] = y;
+      // window shift: acc[i] <- acc[i+1] + B[v+1+i][v] y
 #pragma unroll
-    for (int s = 0; s < SPT; s++) {
-      if (!act[s]) continue;
-      const int64_t g = p.sample0 + cs[s];
-      if (p.first) p.logP[g] = (double)lp[s];
-      else p.logP[g] += (double)lp[s];
+      for (int i = 0; i < DIAG_VB - 1; i++) acc[i] = fmaf(bcur[i], y, acc[i + 1]);
+      acc[DIAG_VB - 1] = 0.0f;
     }
+  }
+  if (act) {
+    const double lp = (double)(logf(prod) + lsum) + (double)pe * 0.69314718055994530942;
+    if (p.first) p.logP[g] = lp;
+    else p.logP[g] += lp;
   }
   if (p.Ys) {
     __syncthreads();
     const int nw = bd >> 5, warp = tid >> 5, lane = tid & 31;
-    for (int j = warp; j < SPT * bd; j += nw) {
+    for (int j = warp; j < bd; j += nw) {
       if (c0 + j >= p.C) break;
       __nv_bfloat16* row = p.Ys + (c0 + j) * p.ldys;
       for (int v = lane; v < p.mt; v += 32) {
@@ -470,7 +427,10 @@ static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t -
 
 // float32 diagonal tiles: row-major B32, transposed BT32 (ld ldbt), reciprocal diagonal inv32
 int ensure_float_tiles(Factor& F, cudaStream_t st) {
-  if (F.B32) return TLRMVN_OK;
+  if (F.B32 && F.BT32 && F.inv32) return TLRMVN_OK;
+  dfree(F.B32);  // a failed earlier attempt may have left some of these behind
+  dfree(F.BT32);
+  dfree(F.inv32);
   const int64_t nb = (int64_t)F.r * F.m * F.m;
   TLR_CHECK(dalloc(&F.B32, nb));
   k_convert<double, float><<<blocks_for(nb, 256), 256, 0, st>>>(F.B, F.B32, nb);
@@ -487,8 +447,19 @@ int ensure_float_tiles(Factor& F, cudaStream_t st) {
 // Makes the copies a precision needs; the first caller makes them (and waits for
 // them) under the factor's lock, so concurrent streams never see a partial copy.
 static int ensure_copies_locked(Factor& F, int precision, cudaStream_t st);
+static bool bf16_ready(const Factor& F) {
+  return !F.kpad_off.empty() && (F.ktot == 0 || (F.U16 && F.V16 && F.vmap16)) &&
+         (F.m <= sweep_sub_tc() || F.B16x2);
+}
+static bool copies_ready(const Factor& F, int precision) {
+  if (precision == TLRMVN_FP64) return true;
+  if (!F.B32 || !F.BT32 || !F.inv32) return false;
+  if (precision == TLRMVN_FP32) return (F.U32 && F.V32) || F.ktot == 0;
+  return bf16_ready(F);
+}
 static int ensure_copies(Factor& F, int precision, cudaStream_t st) {
   std::lock_guard<std::mutex> lk(F.copy_mu);
+  if (copies_ready(F, precision)) return TLRMVN_OK;  // made and completed by an earlier call
   TLR_CHECK(ensure_copies_locked(F, precision, st));
   TLR_CUDA(cudaStreamSynchronize(st));
   return TLRMVN_OK;
@@ -496,13 +467,20 @@ static int ensure_copies(Factor& F, int precision, cudaStream_t st) {
 static int ensure_copies_locked(Factor& F, int precision, cudaStream_t st) {
   const int64_t nu = (int64_t)F.m * F.ktot;
   if (precision != TLRMVN_FP64) TLR_CHECK(ensure_float_tiles(F, st));
-  if (precision == TLRMVN_FP32 && !F.U32 && nu) {
+  if (precision == TLRMVN_FP32 && !(F.U32 && F.V32) && nu) {
+    dfree(F.U32);
+    dfree(F.V32);
     TLR_CHECK(dalloc(&F.U32, nu));
     TLR_CHECK(dalloc(&F.V32, nu));
     k_convert<double, float><<<blocks_for(nu, 256), 256, 0, st>>>(F.Ucat, F.U32, nu);
     k_convert<double, float><<<blocks_for(nu, 256), 256, 0, st>>>(F.Vcat, F.V32, nu);
   }
-  if (precision == TLRMVN_BF16_SHIFT && !F.kpad_off.size()) {
+  if (precision == TLRMVN_BF16_SHIFT && !bf16_ready(F)) {
+    // (a failed earlier attempt may have left some of these behind)
+    dfree(F.U16);
+    dfree(F.V16);
+    dfree(F.vmap16);
+    dfree(F.B16x2);
     // padded rank space: row tile i starts at a multiple of 64
     const int r = F.r, m = F.m;
     F.kpad_off.assign(r + 1, 0);
@@ -646,43 +624,52 @@ static int diag_threads(int m) {
   return bd;
 }
 
-// Variants of the float sweep: samples per thread (1, 2), one-variable-ahead
-// loads, staged lattice offsets.  TLRMVN_SWEEP="spt,pipe,dstage" selects one (tuning runs);
-// the default is the fastest measured on the n = 65,536 workload.
-struct SweepVariant {
-  int spt, pipe, dstage;
-};
-static SweepVariant sweep_variant() {
-  static SweepVariant v = [] {
-    SweepVariant d{1, 1, 0};
-    if (const char* e = getenv("TLRMVN_SWEEP")) {
-      int a = 1, b = 0, c = 0;
-      if (sscanf(e, "%d,%d,%d", &a, &b, &c) == 3) d = SweepVariant{a == 2 ? 2 : 1, b ? 1 : 0, c ? 1 : 0};
-    }
-    return d;
+// Samples per block of the float sweep.  Each sample's chain of special functions
+// is latency-bound, so a launch takes (waves) x (time of one block) and a second
+// wave for a few leftover blocks nearly doubles it.  Among block sizes of 2 to 8
+// warps this takes the fewest waves over C samples (occupancy from the CUDA
+// occupancy calculator, which accounts for registers and shared memory), and
+// among those the one nearest 128 samples per block (the size measured fastest
+// when waves tie).  TLRMVN_SWEEP_THREADS fixes the size for tuning runs.
+static int sweep_threads(int64_t C, int mt) {
+  static const int forced = [] {
+    const char* e = getenv("TLRMVN_SWEEP_THREADS");
+    const int v = e ? atoi(e) : 0;
+    return (v >= 32 && v <= 256 && v % 32 == 0) ? v : 0;
   }();
-  return v;
-}
-typedef void (*SweepKernel)(DiagArgs32);
-static SweepKernel sweep_kernel(const SweepVariant& v) {
-  static const SweepKernel table[2][2][2] = {
-      {{k_diag_f32<1, false, false>, k_diag_f32<1, false, true>}, {k_diag_f32<1, true, false>, k_diag_f32<1, true, true>}},
-      {{k_diag_f32<2, false, false>, k_diag_f32<2, false, true>}, {k_diag_f32<2, true, false>, k_diag_f32<2, true, true>}}};
-  return table[v.spt - 1][v.pipe][v.dstage];
-}
-// Samples per block and shared memory of the float sweep over sub-variable
-// sub-tiles.  128 samples per block: at the sweep's ~96 registers a thread, an SM
-// holds 5 such blocks when the sub-tile's y fit (64-variable sub-tiles), 3 at 128.
-static int sub_threads(int m, int sub) {
-  (void)m;
-  (void)sub;
-  return 128;
-}
-static size_t sub_smem(int m, int sub) {
-  return (size_t)std::min(m, sub) * (sub_threads(m, sub) + 1) * sizeof(float);
+  if (forced) return forced;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  // one-entry memo per thread: a solve asks for the same (C, mt) once per sub-tile
+  thread_local int64_t memo_c = -1;
+  thread_local int memo_mt = -1, memo_dev = -1, memo_bd = 128;
+  if (memo_c == C && memo_mt == mt && memo_dev == dev) return memo_bd;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int best = 128;
+  int64_t best_waves = INT64_MAX;
+  for (int bd = 64; bd <= 256; bd += 32) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_diag_f32, bd, sweep_smem_bytes(mt, bd)) !=
+            cudaSuccess ||
+        per_sm < 1) {
+      cudaGetLastError();
+      continue;
+    }
+    const int64_t blocks = (C + bd - 1) / bd, slots = (int64_t)per_sm * std::max(sms, 1);
+    const int64_t waves = (blocks + slots - 1) / slots;
+    if (waves < best_waves || (waves == best_waves && std::abs(bd - 128) < std::abs(best - 128))) {
+      best_waves = waves;
+      best = bd;
+    }
+  }
+  memo_c = C;
+  memo_mt = mt;
+  memo_dev = dev;
+  memo_bd = best;
+  return best;
 }
 static int set_sweep_smem(int m, int sub) {
-  TLR_CHECK(raise_smem_limit((const void*)sweep_kernel(sweep_variant()), sub_smem(m, sub)));
+  TLR_CHECK(raise_smem_limit((const void*)k_diag_f32, sweep_smem_bytes(std::min(m, sub), 256)));
   return TLRMVN_OK;
 }
 
@@ -707,8 +694,7 @@ static void sweep_tile_f32(const Factor& F, int i, bool has_shift, float* Dl, in
                            const TcCouple* tcc = nullptr) {
   const int m = F.m, mt = (int)F.tsize(i);
   const int sub = tcc ? tcc->sub : DIAG_SUB;
-  const int bd = sub_threads(m, sub);
-  const size_t smem = sub_smem(m, sub);
+  const int bd = sweep_threads(Cc, std::min(mt, sub));
   const float* Bi = F.B32 + (size_t)i * m * m;
   for (int q0 = 0; q0 < mt; q0 += sub) {
     const int mq = std::min(sub, mt - q0);
@@ -759,8 +745,7 @@ static void sweep_tile_f32(const Factor& F, int i, bool has_shift, float* Dl, in
     a.ys_lo = tcc ? tcc->my : 0;
     a.logP = logP;
     pf.begin(TLRMVN_KC_DIAG);
-    const SweepVariant sv = sweep_variant();
-    sweep_kernel(sv)<<<blocks_for(Cc, bd), bd / sv.spt, smem, st>>>(a);
+    k_diag_f32<<<blocks_for(Cc, bd), bd, sweep_smem_bytes(mq, bd), st>>>(a);
     pf.end();
   }
 }
@@ -997,13 +982,18 @@ int prob_impl(Factor& F, const double* a_dev, const double* b_dev, double nu, co
     if (!hD.empty()) TLR_CUDA(cudaStreamSynchronize(st));
   }
   TLR_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
+  Prof pf(st);
+  pf.begin(TLRMVN_KC_PREP);
   k_permute_limits<<<blocks_for(n, 256), 256, 0, st>>>(a_dev, b_dev, F.dperm, n, ap, bp, ap32, bp32, bad);
+  pf.end();
   int hbad = 0;
   TLR_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
   TLR_CUDA(cudaStreamSynchronize(st));
-  if (hbad) return fail(TLRMVN_E_INVAL, "limits must satisfy a_i <= b_i, a_i < +inf, b_i > -inf, no NaN");
+  if (hbad) {
+    pf.collect();
+    return fail(TLRMVN_E_INVAL, "limits must satisfy a_i <= b_i, a_i < +inf, b_i > -inf, no NaN");
+  }
   TLR_CHECK(ensure_copies(F, o.precision, st));
-  Prof pf(st);
   int s;
   const Lims L{ap, bp, ap32, bp32};
   if (o.precision == TLRMVN_FP64)
@@ -1015,6 +1005,8 @@ int prob_impl(Factor& F, const double* a_dev, const double* b_dev, double nu, co
   TLR_CHECK(s);
   pf.begin(TLRMVN_KC_REDUCE);
   k_shift_reduce<<<(unsigned)M, 256, 0, st>>>(logP, N, ell);
+  pf.end();
+  pf.begin(TLRMVN_KC_REDUCE);
   k_final<<<1, 256, 0, st>>>(ell, (int)M, out2_dev);
   pf.end();
   if (ell_dev_out) TLR_CUDA(cudaMemcpyAsync(ell_dev_out, ell, M * 8, cudaMemcpyDeviceToDevice, st));

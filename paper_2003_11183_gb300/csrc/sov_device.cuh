@@ -76,20 +76,20 @@ __device__ inline double gamma_p_inv(double a, double p, double q) {
 
 // ---- float32 integrand helpers ------------------------------------------------------
 // Lattice value as floats, from the same exact numerator as lattice_w (integer
-// arithmetic only: the float path issues no float64 instruction).
+// arithmetic only: the float path issues no float64 instruction).  w = num 2^-53
+// and 1 - w = (2^53 - num) 2^-53 with num < 2^53: each is one correctly rounded
+// integer-to-float conversion and an exact power-of-two scaling.
 __device__ __forceinline__ void lattice_wf(uint64_t x, int periodize, float& w, float& wc) {
   int64_t num;
   if (periodize) {
-    int64_t h = (int64_t)(x >> 11);
-    num = 2 * h + 1 - (int64_t(1) << 53);
-    if (num < 0) num = -num;
+    const int64_t t = (int64_t)((x >> 10) | 1) - (int64_t(1) << 53);  // 2h + 1 - 2^53, h = x >> 11
+    num = t < 0 ? -t : t;
   } else {
-    num = 2 * (int64_t)(x >> 12) + 1;
+    num = (int64_t)((x >> 11) | 1);  // 2h + 1, h = x >> 12
   }
-  const int64_t numc = (int64_t(1) << 53) - num;
-  w = fmaf((float)(uint32_t)(num >> 21), 2.3283064365386963e-10f, (float)(uint32_t)(num & 0x1FFFFF) * 1.1102230246251565e-16f);
-  wc = fmaf((float)(uint32_t)(numc >> 21), 2.3283064365386963e-10f,
-            (float)(uint32_t)(numc & 0x1FFFFF) * 1.1102230246251565e-16f);
+  const float s53 = 1.1102230246251565e-16f;  // 2^-53
+  w = __ll2float_rn(num) * s53;
+  wc = __ll2float_rn((int64_t(1) << 53) - num) * s53;
 }
 
 // eq. (2) for one variable in float32.  The one-sided case (at = -inf), which is
@@ -132,6 +132,42 @@ __device__ __forceinline__ void sov_step_f32(float at, float bt, float w, float 
     return;
   }
   sov_step<float>(at, bt, w, wc, ld, y);
+}
+
+// The same step for a caller that keeps the sample's probability as a running
+// product: returns y, a factor f to multiply into the product and a log la to
+// add to a separate sum (the step's probability is f exp(la)).  The one-sided
+// fast path returns f = Phi(bt), except when 1 - Phi(bt) = c < 2^-12, where
+// fl(1 - c) would lose c's digits and the step returns la = log1p(-c) taken as
+// -c - c^2/2 (the next term is below 2^-24 c); the deep tail and two-sided
+// intervals return their log.  No log is evaluated on the fast path.
+__device__ __forceinline__ void sov_step_f32_prod(float at, float bt, float w, float wc, float& f, float& la,
+                                                  float& y) {
+  const float rs2 = (float)TLR_RSQRT2;
+  if (at == -INFINITY && bt != INFINITY && bt >= -12.0f) {
+    const float h = 0.5f * erfcf(fabsf(bt) * rs2);  // Phi(-|bt|)
+    const bool neg = bt < 0.0f;
+    const float ph = neg ? h : 1.0f - h;  // Phi(bt)
+    const float pc = neg ? 1.0f - h : h;  // 1 - Phi(bt)
+    const bool near1 = !neg && pc < 0x1p-12f;
+    f = near1 ? 1.0f : ph;
+    la = near1 ? -pc * fmaf(0.5f, pc, 1.0f) : 0.0f;
+    const float u = w * ph, uc = pc + wc * ph;  // u + uc = 1
+    const bool lower = u <= uc;
+    const float pp = lower ? u : uc;
+    if (pp >= 1e-30f) {
+      const float z = normcdfinvf(pp);
+      y = lower ? z : -z;
+    } else {  // u underflows: quantile from log u (here ph < 1/2, so log Phi(bt) = log ph)
+      const float lu = logf(w) + logf(ph);
+      y = ndtri_lower(expf(lu), lu);
+    }
+    return;
+  }
+  float ld;
+  sov_step_f32(at, bt, w, wc, ld, y);
+  f = 1.0f;
+  la = ld;
 }
 
 }  // namespace tlrmvn

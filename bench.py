@@ -38,7 +38,11 @@ METRIC = "MVN/MVT QMC sample-dims/sec at n=65,536 vs FP64 path; p50/p99 solve la
 # with the digest of the CUDA sources it was taken on (build.source_digest()).
 # A figure is reported, scaled to this run's launches, only while the sources
 # are unchanged; the summaries with the capture commands are under profiles/.
-TRAFFIC = {}
+TRAFFIC = {
+    "k_diag_f32": {"bytes_per_sample_dim": (17.644544e6 + 6.4e3) / (65536 * 64),
+                   "capture": "profiles/k_diag_f32_sweep_n16384.md",
+                   "sources": "44a810c01cbda2d7fe22ff490a27a944816b8dae5dc174bb031e088b7c331595"},
+}
 
 
 def parse():
@@ -353,8 +357,9 @@ def run_ours(args):
         else:
             pkd = fp32_peak
         classes[cls] = dict(pkd, achieved=ach, frac=ach / pkd["peak"], ms_per_step=kern[cls][0] / args.steps,
-                            kernel={"diag": "k_diag_f32", "couple": "k_sgemm128", "shift": "k_gemm_tc",
-                                    "vproj": "k_gemm_tc"}[cls] if prec == 2 else cls)
+                            kernel={"diag": "k_diag_f32", "couple": "k_gemm_tc (split bf16)", "shift": "k_gemm_tc",
+                                    "vproj": "k_gemm_tc"}[cls] if prec == 2 else
+                            {"diag": "k_diag_f32", "couple": "k_sgemm128"}.get(cls, "k_gemm_nn") if prec == 1 else cls)
     from paper_2003_11183_gb300 import build as _build
     digest = _build.source_digest()
     for cls, d in classes.items():

@@ -2,7 +2,8 @@
 // for the low-rank limit shifts, the projections and the in-tile coupling of the
 // BF16-shift integrand.
 //
-//   D (M x N) = A (M x K) * B (N x K)^T      both operands K-major bf16
+//   D (M x N) = A (M x K) * B (N x K)^T      bf16 operands: B K-major; A K-major,
+//                                             or MN-major (A_MN: stored K x M, M contiguous)
 //
 // One 128 x BN output tile per CTA of 128 threads (BN = 64, 128 or 256, a
 // template parameter).  Operands are staged by TMA (128-byte swizzle) through a
@@ -11,7 +12,8 @@
 // warps read their 32 TMEM lanes (one output row each) and run the epilogue:
 //   EPI_TRANS_F32:    D[col * ldd + row] = acc, or += acc  (fp32; the rows are
 //                     samples, so a warp's stores cover 32 consecutive samples)
-//   EPI_COLMAP_BF16:  W[col * ldw + map[row]] = bf16(acc)   (projections, bf16)
+//   EPI_TRANS_BF16:   W[map[col] * ldw + row] = bf16(acc)   (projections, bf16; the rows
+//                     are samples, so a warp's stores cover 32 consecutive samples)
 // Every mbarrier wait is bounded; on expiry the CTA records an error code,
 // skips the remaining work, frees its TMEM and returns.
 #pragma once
@@ -25,14 +27,14 @@ constexpr int BM = 128, BK = 64;
 constexpr int A_BYTES = BM * BK * 2;  // 16 KB
 constexpr uint32_t WAIT_LIMIT = 1u << 24;  // polls before a wait gives up (seconds)
 
-enum { EPI_TRANS_F32 = 0, EPI_COLMAP_BF16 = 1 };
+enum { EPI_TRANS_F32 = 0, EPI_TRANS_BF16 = 1 };
 
 // Shape of one kernel configuration: B tile bytes, stage bytes (SPLIT stages
 // hold hi and lo tiles of both operands), stage count and shared memory.  Stages
 // are sized so that two CTAs share an SM where they fit in about 100 KB each.
 // SPLIT configurations serve short-K products (the in-tile coupling, K <= 448):
 // one stage each, so that four CTAs share an SM and overlap one another.
-template <int BN, bool SPLIT>
+template <int BN, bool SPLIT, bool A_MN = false>
 struct Cfg {
   static constexpr int B_BYTES = BN * BK * 2;
   static constexpr int HALF = A_BYTES + B_BYTES;  // [A][B] of one precision part
@@ -41,8 +43,9 @@ struct Cfg {
   static constexpr int SMEM = NST * SB + 1024 /*align*/ + 256 /*barriers*/;
   // instruction descriptor of tcgen05.mma kind::f16: fp32 accumulator, bf16 A
   // and B, both K-major, N = BN (bits 17-22 hold N/8), M = 128 (bits 24-28 hold M/16)
-  static constexpr uint32_t IDESC =
-      (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+  // (bit 15 set: A is MN-major)
+  static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((A_MN ? 1u : 0u) << 15) |
+                                    ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
   static_assert(BN == 64 || BN == 128 || BN == 256, "N of the MMA");
   static_assert(HALF % 1024 == 0 && A_BYTES % 1024 == 0, "128-byte swizzle atoms need 1024-byte alignment");
 };
@@ -56,6 +59,20 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
   d |= (uint64_t)1 << 16;            // leading byte offset (unused with this swizzle)
   d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
+  d |= (uint64_t)1 << 46;            // version
+  d |= (uint64_t)2 << 61;            // 128-byte swizzle
+  return d;
+}
+
+// MN-major operand (A_MN): TMA writes each 64-element-wide MN slice of the tile
+// as 64 K-rows of 128 bytes (128-byte swizzle); the two slices of a 128-row tile
+// sit 8 KB apart (leading byte offset, between MN atoms) and the 8-row K groups
+// 1 KB apart (stride byte offset).  One 16-deep K step spans two K groups (2 KB).
+__device__ __forceinline__ uint64_t sdesc_mn(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)(8192 >> 4) << 16;  // leading byte offset: next 64-element MN slice
+  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset: next 8-row K group
   d |= (uint64_t)1 << 46;            // version
   d |= (uint64_t)2 << 61;            // 128-byte swizzle
   return d;
@@ -126,7 +143,7 @@ struct GemmTcArgs {
   int bx0, by0;         // B tile origin (x = K, y = N)
   float* D;             // EPI_TRANS_F32
   int64_t ldd;
-  __nv_bfloat16* W;     // EPI_COLMAP_BF16
+  __nv_bfloat16* W;     // EPI_TRANS_BF16
   int64_t ldw;
   const int32_t* map;
   int* err;             // nonzero after a wait expired
@@ -137,11 +154,13 @@ struct GemmTcArgs {
   int rows_fast = 0;    // grid: blockIdx.x walks the M blocks (CTAs that share a B tile run together)
 };
 
-// A's tensor map has a box of 64 x 128 (BM rows), B's a box of 64 x BN.
-template <int EPI, bool SPLIT, int BN>
-__global__ void __launch_bounds__(128) k_gemm_tc(const __grid_constant__ CUtensorMap mapA,
+// A's tensor map has a box of 64 x 128 (BM rows; A_MN: 64 M-elements x 64 K-rows,
+// loaded twice per stage), B's a box of 64 x BN.
+template <int EPI, bool SPLIT, int BN, bool A_MN = false>
+__global__ void __launch_bounds__(128, SPLIT ? 4 : 1) k_gemm_tc(const __grid_constant__ CUtensorMap mapA,
                                                  const __grid_constant__ CUtensorMap mapB, GemmTcArgs p) {
-  using G = Cfg<BN, SPLIT>;
+  static_assert(!(A_MN && SPLIT), "MN-major A is used without split operands");
+  using G = Cfg<BN, SPLIT, A_MN>;
   constexpr int NST = G::NST;
   constexpr uint32_t SB = G::SB;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -188,7 +207,12 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const __grid_constant__ CUtenso
       if (*(volatile int*)&abort_flag) break;
       unsigned char* sa = smem + s * SB;
       mbar_expect_tx(&full[s], SB);
-      tma_load_2d(sa, &mapA, &full[s], p.ax0 + kb * BK, p.ay0 + m0);
+      if (A_MN) {  // x = M, y = K: two 64-wide M slices
+        tma_load_2d(sa, &mapA, &full[s], p.ay0 + m0, p.ax0 + kb * BK);
+        tma_load_2d(sa + A_BYTES / 2, &mapA, &full[s], p.ay0 + m0 + 64, p.ax0 + kb * BK);
+      } else {
+        tma_load_2d(sa, &mapA, &full[s], p.ax0 + kb * BK, p.ay0 + m0);
+      }
       tma_load_2d(sa + A_BYTES, &mapB, &full[s], p.bx0 + kb * BK, p.by0 + n0);
       if (SPLIT) {
         tma_load_2d(sa + G::HALF, &mapA, &full[s], p.ax0 + p.alo + kb * BK, p.ay0 + m0);
@@ -213,11 +237,13 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const __grid_constant__ CUtenso
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t sa = smem_u32(smem + s * SB);
-      const uint64_t da = sdesc(sa), db = sdesc(sa + A_BYTES);
+      const uint64_t da = A_MN ? sdesc_mn(sa) : sdesc(sa), db = sdesc(sa + A_BYTES);
+      // per 16-deep k-step, in the descriptor's 16-byte units: K-major +32 bytes
+      // (+2), MN-major two 1 KB K groups (+128)
+      constexpr uint64_t ASTEP = A_MN ? 128 : 2;
 #pragma unroll
       for (int kk = 0; kk < BK / 16; kk++) {
-        // +2 per 16-element k-step: 32 bytes in the descriptor's 16-byte units
-        mma_bf16(tmem, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), G::IDESC, (kb > 0 || kk > 0) ? 1u : 0u);
+        mma_bf16(tmem, da + ASTEP * kk, db + (uint64_t)(kk * 2), G::IDESC, (kb > 0 || kk > 0) ? 1u : 0u);
         if (SPLIT) {
           const uint64_t dal = sdesc(sa + G::HALF), dbl = sdesc(sa + G::HALF + A_BYTES);
           mma_bf16(tmem, da + (uint64_t)(kk * 2), dbl + (uint64_t)(kk * 2), G::IDESC, 1u);
@@ -270,14 +296,15 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const __grid_constant__ CUtenso
         }
       }
     } else {
-      const int64_t dcol = (row < p.M) ? (int64_t)p.map[row] : 0;
+#pragma unroll
       for (int c = 0; c < BN / 32; c++) {
         float v[32];
         tmem_ld32(tbase + c * 32, v);
         const int col0 = n0 + c * 32;
         if (row < p.M) {
+#pragma unroll
           for (int q = 0; q < 32; q++)
-            if (col0 + q < p.N) p.W[(int64_t)(col0 + q) * p.ldw + dcol] = __float2bfloat16_rn(v[q]);
+            if (col0 + q < p.N) p.W[(int64_t)p.map[col0 + q] * p.ldw + row] = __float2bfloat16_rn(v[q]);
         }
       }
     }

@@ -837,7 +837,9 @@ static int run_chunks(Factor& F, const T* Bt, const T* Ut, const T* Vt, const Li
 // bf16 operands and fp32 accumulation, and the coupling between the 128-variable
 // sub-tiles of a diagonal tile on tcgen05 with split operands (x = hi + lo, both
 // bf16; hi*hi + hi*lo + lo*hi, relative error ~1e-5).  Layouts (C = samples in the chunk):
-//   W16  C x kw16  bf16, sample-major: row c holds the projections of sample c
+//   W16  kw16 x ldw bf16, rank-major (ldw = C rounded up to 64): row k holds
+//        projection k of every sample (written coalesced by the projection GEMM,
+//        read as an MN-major operand by the shift GEMM)
 //   Y16  C x ly    bf16, sample-major: the tile's y (hi) in columns [0, my16), and
 //                  for tiles over 128 variables bf16(y - hi) in [my16, 2 my16)
 //   Dl   m x C     fp32, variable-major (read by the sweep)
@@ -851,38 +853,40 @@ static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opt
   float* Dl = nullptr;
   float* rs32 = nullptr;
   int* err = nullptr;
-  TLR_CHECK(sc.get(&W, (size_t)F.kw16 * C));
+  const int64_t ldw = (C + 63) / 64 * 64;
+  TLR_CHECK(sc.get(&W, (size_t)F.kw16 * ldw));
   TLR_CHECK(sc.get(&Y, (size_t)ly * C));
   TLR_CHECK(sc.get(&Dl, (size_t)m * C));
   TLR_CHECK(sc.get(&err, 1));
   const bool mvt = std::isfinite(nu);
   if (mvt) TLR_CHECK(sc.get(&rs32, (size_t)C));
   // padding columns of W and Y must hold finite values: they meet zero operand columns
-  TLR_CUDA(cudaMemsetAsync(W, 0, (size_t)F.kw16 * C * 2, st));
+  TLR_CUDA(cudaMemsetAsync(W, 0, (size_t)F.kw16 * ldw * 2, st));
   TLR_CUDA(cudaMemsetAsync(Y, 0, (size_t)ly * C * 2, st));
   TLR_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
 
   // tensor maps (box 64 x rows): A operands take 128-row boxes, B operands BN-row boxes
-  //   shift      Dl^T (samples x vars) = W16 rows (A) x U16 rows (B, N = 256)
-  //   projection W16 columns <- V16 rows (A) x Y16 rows (B, N = 256)
+  //   shift      Dl^T (samples x vars) = W16^T (A, MN-major) x U16 rows (B, N = 256)
+  //   projection W16 rows^T (samples x ranks) = Y16 rows (A) x V16 rows (B, N = 256)
   //   coupling   Dl^T += Y16 rows (A, hi/lo) x B16x2 rows (B, hi/lo, N = sub-tile)
   CUtensorMap mapU, mapV, mapW, mapY;
   if (F.ktot) {
     TLR_CHECK(make_map(&mapU, F.U16, F.kmax16, (uint64_t)F.r * m, F.kmax16 * 2, 256));
-    TLR_CHECK(make_map(&mapV, F.V16, F.my16, F.ktot, F.my16 * 2, tc::BM));
+    TLR_CHECK(make_map(&mapV, F.V16, F.my16, F.ktot, F.my16 * 2, 256));
   }
-  TLR_CHECK(make_map(&mapW, W, F.kw16, C, F.kw16 * 2, tc::BM));
-  TLR_CHECK(make_map(&mapY, Y, ly, C, ly * 2, 256));
+  TLR_CHECK(make_map(&mapW, W, ldw, F.kw16, ldw * 2, 64));
+  TLR_CHECK(make_map(&mapY, Y, ly, C, ly * 2, tc::BM));
   TcCouple tcc;
   if (F.B16x2) {
     tcc.sub = sweep_sub_tc();
     TLR_CHECK(make_map(&tcc.mapB, F.B16x2, ly, (uint64_t)F.r * m, ly * 2, (uint32_t)tcc.sub));
-    TLR_CHECK(make_map(&tcc.mapY, Y, ly, C, ly * 2, tc::BM));
+    tcc.mapY = mapY;
     tcc.my = F.my16;
     tcc.err = err;
   }
-  TLR_CHECK(raise_smem_limit((const void*)tc::k_gemm_tc<tc::EPI_TRANS_F32, false, 256>, tc::Cfg<256, false>::SMEM));
-  TLR_CHECK(raise_smem_limit((const void*)tc::k_gemm_tc<tc::EPI_COLMAP_BF16, false, 256>, tc::Cfg<256, false>::SMEM));
+  TLR_CHECK(raise_smem_limit((const void*)tc::k_gemm_tc<tc::EPI_TRANS_F32, false, 256, true>,
+                             tc::Cfg<256, false, true>::SMEM));
+  TLR_CHECK(raise_smem_limit((const void*)tc::k_gemm_tc<tc::EPI_TRANS_BF16, false, 256>, tc::Cfg<256, false>::SMEM));
   TLR_CHECK(raise_smem_limit((const void*)tc::k_gemm_tc<tc::EPI_TRANS_F32, true, 64>, tc::Cfg<64, true>::SMEM));
   TLR_CHECK(raise_smem_limit((const void*)tc::k_gemm_tc<tc::EPI_TRANS_F32, true, 128>, tc::Cfg<128, true>::SMEM));
 
@@ -896,7 +900,7 @@ static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opt
                                                        o.periodize);
       pf.end();
     }
-    const unsigned sblocks = (unsigned)((Cc + tc::BM - 1) / tc::BM), ntile = (unsigned)((Cc + 255) / 256);
+    const unsigned sblocks = (unsigned)((Cc + tc::BM - 1) / tc::BM);
     for (int i = 0; i < F.r; i++) {
       const int mt = (int)F.tsize(i);
       const int64_t Kr = F.krow(i), Kc = F.kcol(i);
@@ -904,20 +908,21 @@ static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opt
       if (Kr > 0) {
         tc::GemmTcArgs g{(int)Cc, mt, (int)Kr, (int)F.kpad_off[i], 0, 0, i * m, Dl, C, nullptr, 0, nullptr, err};
         pf.begin(TLRMVN_KC_SHIFT);
-        tc::k_gemm_tc<tc::EPI_TRANS_F32, false, 256><<<dim3((unsigned)((mt + 255) / 256), sblocks), 128,
-                                                       tc::Cfg<256, false>::SMEM, st>>>(mapW, mapU, g);
+        tc::k_gemm_tc<tc::EPI_TRANS_F32, false, 256, true><<<dim3((unsigned)((mt + 255) / 256), sblocks), 128,
+                                                             tc::Cfg<256, false, true>::SMEM, st>>>(mapW, mapU, g);
         pf.end();
         Delta = Dl;
       }
       sweep_tile_f32(F, i, Delta != nullptr, Dl, C, L, rs32, dD, c0, N, Cc, o.periodize, nullptr, Y, ly, logP, st, pf,
                      F.B16x2 ? &tcc : nullptr);
       if (Kc > 0) {
-        tc::GemmTcArgs g{(int)Kc, (int)Cc, mt, 0, (int)F.kcol_off[i], 0, 0, nullptr, 0, W, F.kw16,
+        // transposed: rows = samples (A = y), columns = the column tile's ranks
+        tc::GemmTcArgs g{(int)Cc, (int)Kc, mt, 0, 0, 0, (int)F.kcol_off[i], nullptr, 0, W, ldw,
                          F.vmap16 + F.kcol_off[i], err};
-        g.rows_fast = 1;  // the rank blocks of one sample tile run together and share its y in L2
+        // (grid x walks the rank blocks: those of one sample block run together and share its y in L2)
         pf.begin(TLRMVN_KC_VPROJ);
-        tc::k_gemm_tc<tc::EPI_COLMAP_BF16, false, 256><<<dim3((unsigned)((Kc + tc::BM - 1) / tc::BM), ntile), 128,
-                                                         tc::Cfg<256, false>::SMEM, st>>>(mapV, mapY, g);
+        tc::k_gemm_tc<tc::EPI_TRANS_BF16, false, 256><<<dim3((unsigned)((Kc + 255) / 256), sblocks), 128,
+                                                        tc::Cfg<256, false>::SMEM, st>>>(mapY, mapV, g);
         pf.end();
       }
     }

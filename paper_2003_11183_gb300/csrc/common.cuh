@@ -8,6 +8,7 @@
 #include <math.h>
 #include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/tlrmvn.h"
@@ -120,6 +121,32 @@ cudaStream_t pick_stream(void* s);
 // raised: a caller with a smaller tile never lowers it under another thread that
 // is about to launch with a larger one.
 int raise_smem_limit(const void* kernel, size_t bytes);
+
+// Programmatic dependent launch: a kernel launched with launch_pdl may start
+// while its predecessor in the stream is still running.  Every kernel that can
+// be launched that way calls pdl_trigger() on entry (its own successor may then
+// be scheduled once all of its CTAs are running) and pdl_wait() before it reads
+// anything the predecessor wrote or writes any global memory (pdl_wait returns
+// once the predecessor grid has completed and its writes are visible).  Both are
+// no-ops for a kernel launched the ordinary way.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // Kernel-class timing (tlrmvn_profile_*): Prof brackets launches with events.
 struct Prof {

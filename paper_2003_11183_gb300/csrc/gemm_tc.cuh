@@ -175,6 +175,7 @@ __global__ void __launch_bounds__(128, SPLIT ? 4 : 1) k_gemm_tc(const __grid_con
   const int m0 = (p.rows_fast ? blockIdx.x : blockIdx.y) * BM, n0 = (p.rows_fast ? blockIdx.y : blockIdx.x) * BN;
   const int nk = (p.K + BK - 1) / BK;
 
+  pdl_trigger();
   if (threadIdx.x == 0) {
     abort_flag = 0;
     for (int s = 0; s < NST; s++) {
@@ -194,6 +195,7 @@ __global__ void __launch_bounds__(128, SPLIT ? 4 : 1) k_gemm_tc(const __grid_con
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
+  pdl_wait();  // operands and outputs belong to the preceding kernels until they finish
 
   if (warp == 0 && lane == 0) {
     // TMA producer

@@ -209,6 +209,8 @@ __global__ void k_diag_f32(DiagArgs32 p) {
   float* s_b = s_a + mt;
   float* s_inv = s_b + mt;
   const int64_t c0 = (int64_t)blockIdx.x * bd;
+  pdl_trigger();
+  // limits, diagonal and generators are not written by the preceding kernels
   for (int t = tid; t < mt; t += bd) {
     s_a[t] = p.a[t];
     s_b[t] = p.b[t];
@@ -216,6 +218,7 @@ __global__ void k_diag_f32(DiagArgs32 p) {
     s_q[t] = p.Q[p.coord0 + t];
   }
   __syncthreads();
+  pdl_wait();  // the limit shifts, y and log P of the preceding kernels
   const bool act = c0 + tid < p.C;
   const int64_t cs = act ? c0 + tid : p.C - 1;  // inactive lanes shadow a valid sample, write nothing
   const int64_t g = p.sample0 + cs;
@@ -709,10 +712,11 @@ static void sweep_tile_f32(const Factor& F, int i, bool has_shift, float* Dl, in
         g.accumulate = has_shift ? 1 : 0;
         const dim3 grid(1, (unsigned)((Cc + tc::BM - 1) / tc::BM));
         if (tcc->sub == 64)
-          tc::k_gemm_tc<tc::EPI_TRANS_F32, true, 64><<<grid, 128, tc::Cfg<64, true>::SMEM, st>>>(tcc->mapY, tcc->mapB, g);
+          launch_pdl(tc::k_gemm_tc<tc::EPI_TRANS_F32, true, 64>, grid, dim3(128), tc::Cfg<64, true>::SMEM, st, tcc->mapY,
+                     tcc->mapB, g);
         else
-          tc::k_gemm_tc<tc::EPI_TRANS_F32, true, 128><<<grid, 128, tc::Cfg<128, true>::SMEM, st>>>(tcc->mapY, tcc->mapB,
-                                                                                                  g);
+          launch_pdl(tc::k_gemm_tc<tc::EPI_TRANS_F32, true, 128>, grid, dim3(128), tc::Cfg<128, true>::SMEM, st,
+                     tcc->mapY, tcc->mapB, g);
       } else {
         gemm_nn<float>(st, mq, Cc, q0, Bi + (size_t)q0 * m, m, Yv, C, Dl + (size_t)q0 * C, C, nullptr,
                        has_shift ? 1 : 0);
@@ -745,7 +749,10 @@ static void sweep_tile_f32(const Factor& F, int i, bool has_shift, float* Dl, in
     a.ys_lo = tcc ? tcc->my : 0;
     a.logP = logP;
     pf.begin(TLRMVN_KC_DIAG);
-    k_diag_f32<<<blocks_for(Cc, bd), bd, sweep_smem_bytes(mq, bd), st>>>(a);
+    if (tcc)
+      launch_pdl(k_diag_f32, dim3(blocks_for(Cc, bd)), dim3(bd), sweep_smem_bytes(mq, bd), st, a);
+    else
+      k_diag_f32<<<blocks_for(Cc, bd), bd, sweep_smem_bytes(mq, bd), st>>>(a);
     pf.end();
   }
 }
@@ -908,8 +915,8 @@ static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opt
       if (Kr > 0) {
         tc::GemmTcArgs g{(int)Cc, mt, (int)Kr, (int)F.kpad_off[i], 0, 0, i * m, Dl, C, nullptr, 0, nullptr, err};
         pf.begin(TLRMVN_KC_SHIFT);
-        tc::k_gemm_tc<tc::EPI_TRANS_F32, false, 256, true><<<dim3((unsigned)((mt + 255) / 256), sblocks), 128,
-                                                             tc::Cfg<256, false, true>::SMEM, st>>>(mapW, mapU, g);
+        launch_pdl(tc::k_gemm_tc<tc::EPI_TRANS_F32, false, 256, true>, dim3((unsigned)((mt + 255) / 256), sblocks),
+                   dim3(128), tc::Cfg<256, false, true>::SMEM, st, mapW, mapU, g);
         pf.end();
         Delta = Dl;
       }
@@ -921,8 +928,8 @@ static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opt
                          F.vmap16 + F.kcol_off[i], err};
         // (grid x walks the rank blocks: those of one sample block run together and share its y in L2)
         pf.begin(TLRMVN_KC_VPROJ);
-        tc::k_gemm_tc<tc::EPI_TRANS_BF16, false, 256><<<dim3((unsigned)((Kc + 255) / 256), sblocks), 128,
-                                                        tc::Cfg<256, false>::SMEM, st>>>(mapY, mapV, g);
+        launch_pdl(tc::k_gemm_tc<tc::EPI_TRANS_BF16, false, 256>, dim3((unsigned)((Kc + 255) / 256), sblocks),
+                   dim3(128), tc::Cfg<256, false>::SMEM, st, mapY, mapV, g);
         pf.end();
       }
     }

@@ -35,13 +35,16 @@ PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2}
 METRIC = "MVN/MVT QMC sample-dims/sec at n=65,536 vs FP64 path; p50/p99 solve latency"
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of a kernel from one
 # ncu capture, divided by the sample-dimensions the captured launch processed,
-# with the digest of the CUDA sources it was taken on (build.source_digest()).
-# A figure is reported, scaled to this run's launches, only while the sources
-# are unchanged; the summaries with the capture commands are under profiles/.
+# with the digest of the sources the kernel is built from (build.source_digest
+# of `files`).  A figure is reported, scaled to this run's launches, only while
+# those sources are unchanged; the summaries with the capture commands are under
+# profiles/.
 TRAFFIC = {
-    "k_diag_f32": {"bytes_per_sample_dim": (17.644544e6 + 6.4e3) / (65536 * 64),
+    "k_diag_f32": {"bytes_per_sample_dim": (26.88384e6 + 0.145664e6) / (100000 * 64),
                    "capture": "profiles/k_diag_f32_sweep_n16384.md",
-                   "sources": "44a810c01cbda2d7fe22ff490a27a944816b8dae5dc174bb031e088b7c331595"},
+                   "files": ["paper_2003_11183_gb300/csrc/prob.cu", "paper_2003_11183_gb300/csrc/sov_device.cuh",
+                             "paper_2003_11183_gb300/csrc/common.cuh", "include/tlrmvn.h"],
+                   "sources": "ed990015d9b52b99a0b9c26715f72ee3ab4556c7e4dcffeff47418b6530843b2"},
 }
 
 
@@ -361,11 +364,10 @@ def run_ours(args):
                                     "vproj": "k_gemm_tc"}[cls] if prec == 2 else
                             {"diag": "k_diag_f32", "couple": "k_sgemm128"}.get(cls, "k_gemm_nn") if prec == 1 else cls)
     from paper_2003_11183_gb300 import build as _build
-    digest = _build.source_digest()
     for cls, d in classes.items():
         t = TRAFFIC.get(d["kernel"])
         n_launch = kern[cls][1]
-        if t and t["sources"] == digest and n_launch:
+        if t and t["sources"] == _build.source_digest(t["files"]) and n_launch:
             units = float(n) * C * args.steps / n_launch  # sample-dims per launch
             d["traffic"] = t["bytes_per_sample_dim"] * units
             d["traffic_source"] = t["capture"]

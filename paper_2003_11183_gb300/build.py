@@ -28,11 +28,16 @@ def sources() -> list[str]:
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
-def source_digest() -> str:
-    """sha256 over the CUDA sources and the public header (contents and names only)."""
+def source_digest(files: list[str] | None = None) -> str:
+    """sha256 over CUDA sources and the public header (contents and names only).
+
+    files: paths relative to the repository root; default every CUDA source and the header."""
     h = hashlib.sha256()
-    files = sources() + sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h")))
-    files.append(os.path.join(INCLUDE, "tlrmvn.h"))
+    if files is None:
+        files = sources() + sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h")))
+        files.append(os.path.join(INCLUDE, "tlrmvn.h"))
+    else:
+        files = [os.path.join(ROOT, f) for f in files]
     for f in files:
         h.update(os.path.relpath(f, ROOT).encode())
         with open(f, "rb") as fh:

@@ -248,6 +248,15 @@ int tlrmvn_estimate_noalloc(const double* per_sample, int n_shifts, int64_t n_po
 const char* tlrmvn_strerror(int status);
 const char* tlrmvn_last_error(void);   /* thread-local detail of the last failure, "" if none */
 
+/* Exercises the bounded-wait path of the tensor-core kernels (no counterpart in
+ * the paper): one thread waits `polls` times (1 .. 2^20) on an mbarrier that
+ * nothing arrives at, then gives up and records a code, as those kernels do
+ * when a copy or MMA never completes.  Returns TLRMVN_E_TIMEOUT when the wait
+ * gave up (the expected outcome; the CUDA context stays usable), TLRMVN_OK if
+ * the barrier unexpectedly completed, TLRMVN_E_INVAL for polls out of range,
+ * TLRMVN_E_CUDA on a launch failure.  stream: cudaStream_t or NULL. */
+int tlrmvn_selftest_wait_timeout(int polls, void* stream);
+
 /* Kernel classes of the integrand, for tlrmvn_profile_get. */
 #define TLRMVN_KC_SHIFT   0  /* low-rank limit shifts  Delta_i = U_i W_i           */
 #define TLRMVN_KC_DIAG    1  /* diagonal-tile SOV sweep (eq. 2 on B_i)              */

@@ -377,3 +377,9 @@ def tlrmvn_prob_device(f: Factor, a, b, out, nu: float = math.inf, precision: in
     _check(lib.tlrmvn_prob_device(f.handle, a.data_ptr(), b.data_ptr(), float(nu), C.byref(o), out.data_ptr(),
                                   out.data_ptr() + 8, ptr(per_shift), ptr(per_sample)), "tlrmvn_prob_device")
     del keep
+
+
+def tlrmvn_selftest_wait_timeout(polls: int = 1000, stream=None) -> int:
+    """Status of the bounded-wait self-test (TLRMVN_E_TIMEOUT is the expected outcome)."""
+    lib = L.load()
+    return lib.tlrmvn_selftest_wait_timeout(int(polls), _stream_ptr(stream) if stream is not None else None)

@@ -87,7 +87,9 @@ __global__ void __launch_bounds__(BATCH_T) k_batch(const BatchProblem* __restric
       lattice_w(k * P.Q[P.n] + Ds[P.n], P.periodize, w, wc);
       rs = (float)sqrt(2.0 * gamma_p_inv(0.5 * P.nu, w, wc) / P.nu);
     }
-    float lp = 0.0f;
+    // log P = log(prod) + pe log 2 + lsum, prod kept in [1, 2) (see the float sweep)
+    float prod = 1.0f, lsum = 0.0f;
+    int pe = 0;
     for (int i = 0; i < P.r; i++) {
       const int64_t t0 = P.tile_off[i];
       const int mt = (int)(P.tile_off[i + 1] - t0);
@@ -103,22 +105,40 @@ __global__ void __launch_bounds__(BATCH_T) k_batch(const BatchProblem* __restric
         for (int u = 0; u < v0; u++)  // earlier variables of the tile
           fma16(acc, BTi + (int64_t)u * P.ldbt + v0, ys[u * ld + tid]);
         const int nb = min(BATCH_VB, mt - v0);
+        // per-variable values of the block's first variable; later ones one variable ahead
+        float an = P.a[t0 + v0], bn = P.b[t0 + v0], ivn = __ldg(invi + v0);
+        uint64_t xn = k * P.Q[t0 + v0] + Ds[t0 + v0];
 #pragma unroll 1
         for (int j = 0; j < nb; j++) {  // the block in order; acc[0] belongs to variable v
           const int v = v0 + j;
-          const float sum = acc[0];
-          const float iv = __ldg(invi + v);
-          const float at = (P.a[t0 + v] * rs - sum) * iv;
-          const float bt = (P.b[t0 + v] * rs - sum) * iv;
-          float w, wc;
-          lattice_wf(k * P.Q[t0 + v] + Ds[t0 + v], P.periodize, w, wc);
-          float lv, y;
-          sov_step_f32(at, bt, w, wc, lv, y);
-          lp += lv;
-          ys[v * ld + tid] = y;
-          const float* brow = BTi + (int64_t)v * P.ldbt + v + 1;  // B[v+1+i][v]
+          const float av = an, bv = bn, iv = ivn;
+          const uint64_t xv = xn;
+          {
+            const int vn = (j + 1 < nb) ? v + 1 : v;  // the last one reloads its own (in bounds)
+            an = P.a[t0 + vn];
+            bn = P.b[t0 + vn];
+            ivn = __ldg(invi + vn);
+            xn = k * P.Q[t0 + vn] + Ds[t0 + vn];
+          }
+          float bcur[BATCH_VB - 1];  // B[v+1+i][v], loaded before the step's special functions
+          const float* brow = BTi + (int64_t)v * P.ldbt + v + 1;
 #pragma unroll
-          for (int i = 0; i < BATCH_VB - 1; i++) acc[i] = fmaf(__ldg(brow + i), y, acc[i + 1]);
+          for (int i = 0; i < BATCH_VB - 1; i++) bcur[i] = __ldg(brow + i);
+          const float sum = acc[0];
+          const float at = (av * rs - sum) * iv;
+          const float bt = (bv * rs - sum) * iv;
+          float w, wc;
+          lattice_wf(xv, P.periodize, w, wc);
+          float f, la, y;
+          sov_step_f32_prod(at, bt, w, wc, f, la, y);
+          lsum += la;
+          prod *= f;
+          const int pb = __float_as_int(prod);
+          pe += (pb >> 23) - 127;
+          prod = __int_as_float((pb & 0x007FFFFF) | 0x3F800000);
+          ys[v * ld + tid] = y;
+#pragma unroll
+          for (int i = 0; i < BATCH_VB - 1; i++) acc[i] = fmaf(bcur[i], y, acc[i + 1]);
           acc[BATCH_VB - 1] = 0.0f;
         }
       }
@@ -138,7 +158,7 @@ __global__ void __launch_bounds__(BATCH_T) k_batch(const BatchProblem* __restric
         }
       }
     }
-    logP[P.logp_off + g] = (double)lp;
+    logP[P.logp_off + g] = (double)(logf(prod) + lsum) + (double)pe * 0.69314718055994530942;
   }
 }
 

@@ -94,8 +94,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 // Bounded wait: false (and the error code set) when the limit expires.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code) {
-  for (uint32_t i = 0; i < WAIT_LIMIT; i++)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code,
+                                          uint32_t limit = WAIT_LIMIT) {
+  for (uint32_t i = 0; i < limit; i++)
     if (mbar_try_wait(bar, parity)) return true;
   atomicExch(err, code);
   return false;
@@ -316,6 +317,16 @@ __global__ void __launch_bounds__(128, SPLIT ? 4 : 1) k_gemm_tc(const __grid_con
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
   }
+}
+
+// The bounded-wait path on its own: one thread waits on an mbarrier that nothing
+// arrives at, `polls` times, and records code 6 when it gives up.
+__global__ void k_wait_selftest(int* err, uint32_t polls) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  mbar_wait(&bar, 0, err, 6, polls);
 }
 
 }  // namespace tc

@@ -876,10 +876,12 @@ static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opt
   //   shift      Dl^T (samples x vars) = W16^T (A, MN-major) x U16 rows (B, N = 256)
   //   projection W16 rows^T (samples x ranks) = Y16 rows (A) x V16 rows (B, N = 256)
   //   coupling   Dl^T += Y16 rows (A, hi/lo) x B16x2 rows (B, hi/lo, N = sub-tile)
-  CUtensorMap mapU, mapV, mapW, mapY;
+  CUtensorMap mapU, mapV, mapV64, mapV128, mapW, mapY;
   if (F.ktot) {
     TLR_CHECK(make_map(&mapU, F.U16, F.kmax16, (uint64_t)F.r * m, F.kmax16 * 2, 256));
     TLR_CHECK(make_map(&mapV, F.V16, F.my16, F.ktot, F.my16 * 2, 256));
+    TLR_CHECK(make_map(&mapV64, F.V16, F.my16, F.ktot, F.my16 * 2, 64));
+    TLR_CHECK(make_map(&mapV128, F.V16, F.my16, F.ktot, F.my16 * 2, 128));
   }
   TLR_CHECK(make_map(&mapW, W, ldw, F.kw16, ldw * 2, 64));
   TLR_CHECK(make_map(&mapY, Y, ly, C, ly * 2, tc::BM));
@@ -894,6 +896,8 @@ static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opt
   TLR_CHECK(raise_smem_limit((const void*)tc::k_gemm_tc<tc::EPI_TRANS_F32, false, 256, true>,
                              tc::Cfg<256, false, true>::SMEM));
   TLR_CHECK(raise_smem_limit((const void*)tc::k_gemm_tc<tc::EPI_TRANS_BF16, false, 256>, tc::Cfg<256, false>::SMEM));
+  TLR_CHECK(raise_smem_limit((const void*)tc::k_gemm_tc<tc::EPI_TRANS_BF16, false, 128>, tc::Cfg<128, false>::SMEM));
+  TLR_CHECK(raise_smem_limit((const void*)tc::k_gemm_tc<tc::EPI_TRANS_BF16, false, 64>, tc::Cfg<64, false>::SMEM));
   TLR_CHECK(raise_smem_limit((const void*)tc::k_gemm_tc<tc::EPI_TRANS_F32, true, 64>, tc::Cfg<64, true>::SMEM));
   TLR_CHECK(raise_smem_limit((const void*)tc::k_gemm_tc<tc::EPI_TRANS_F32, true, 128>, tc::Cfg<128, true>::SMEM));
 
@@ -926,10 +930,18 @@ static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opt
         // transposed: rows = samples (A = y), columns = the column tile's ranks
         tc::GemmTcArgs g{(int)Cc, (int)Kc, mt, 0, 0, 0, (int)F.kcol_off[i], nullptr, 0, W, ldw,
                          F.vmap16 + F.kcol_off[i], err};
-        // (grid x walks the rank blocks: those of one sample block run together and share its y in L2)
+        // (grid x walks the rank blocks: those of one sample block run together and share its y in L2;
+        // N is the smallest of 64 / 128 / 256 that holds the tile's ranks)
         pf.begin(TLRMVN_KC_VPROJ);
-        launch_pdl(tc::k_gemm_tc<tc::EPI_TRANS_BF16, false, 256>, dim3((unsigned)((Kc + 255) / 256), sblocks),
-                   dim3(128), tc::Cfg<256, false>::SMEM, st, mapY, mapV, g);
+        if (Kc <= 64)
+          launch_pdl(tc::k_gemm_tc<tc::EPI_TRANS_BF16, false, 64>, dim3(1, sblocks), dim3(128),
+                     tc::Cfg<64, false>::SMEM, st, mapY, mapV64, g);
+        else if (Kc <= 128)
+          launch_pdl(tc::k_gemm_tc<tc::EPI_TRANS_BF16, false, 128>, dim3(1, sblocks), dim3(128),
+                     tc::Cfg<128, false>::SMEM, st, mapY, mapV128, g);
+        else
+          launch_pdl(tc::k_gemm_tc<tc::EPI_TRANS_BF16, false, 256>, dim3((unsigned)((Kc + 255) / 256), sblocks),
+                     dim3(128), tc::Cfg<256, false>::SMEM, st, mapY, mapV, g);
         pf.end();
       }
     }
@@ -1105,4 +1117,24 @@ extern "C" int tlrmvn_prob(tlrmvn_factor_t f, const double* a, const double* b, 
   dfree(dps);
   cudaSetDevice(cur);
   return s;
+}
+
+extern "C" int tlrmvn_selftest_wait_timeout(int polls, void* stream) {
+  if (polls < 1 || polls > (1 << 20)) return fail(TLRMVN_E_INVAL, "polls must be in [1, 2^20]");
+  cudaStream_t st = pick_stream(stream);
+  int* err = nullptr;
+  TLR_CUDA(cudaMallocAsync((void**)&err, sizeof(int), st));
+  int herr = 0;
+  cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
+  if (e == cudaSuccess) {
+    tc::k_wait_selftest<<<1, 32, 0, st>>>(err, (uint32_t)polls);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(err, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "wait self-test");
+  if (herr) return fail(TLRMVN_E_TIMEOUT, "wait self-test gave up after " + std::to_string(polls) + " polls (code " +
+                                              std::to_string(herr) + ")");
+  return TLRMVN_OK;
 }

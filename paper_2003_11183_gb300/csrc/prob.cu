@@ -14,6 +14,7 @@
 #include "gemm.cuh"
 #include "gemm_tc.cuh"
 #include "sov_device.cuh"
+#include "sweep.cuh"
 
 #include <cudaTypedefs.h>
 
@@ -136,181 +137,14 @@ __global__ void k_diag(DiagArgs<T, YT> p) {
   }
 }
 
-// ---- float32 sweep ------------------------------------------------------------------
-// Arguments of one float32 sweep over a (sub-)tile of mt variables.  All
-// pointers are already offset to the sub-tile's first variable.
-struct DiagArgs32 {
-  const float* BT;   // transposed diagonal block, BT[u * ldbt + v] = B[v][u]
-  const float* inv;  // 1 / B[v][v]
-  int mt;
-  int64_t ldbt;
-  const float* Delta;  // limit shifts, variable-major (ldd), or null
-  int64_t ldd;
-  const float* a;
-  const float* b;
-  const float* rs;
-  const uint64_t* Q;
-  const uint64_t* D;
-  int64_t ldD, coord0, sample0, N, C;
-  int periodize, first;
-  float* Yv;             // y variable-major, Yv[v * ldyv + c], or null
-  int64_t ldyv;
-  __nv_bfloat16* Ys;     // y sample-major bf16, Ys[c * ldys + v], or null
-  int64_t ldys;
-  int64_t ys_lo;         // > 0: also the low part bf16(y - hi) at Ys[c * ldys + ys_lo + v]
-  double* logP;
-};
-
-// One thread per sample; 16 variables per pass: the partial sums of a block of
-// 16 variables over all earlier variables of the (sub-)tile are accumulated
-// together (each y_u read once per block, B read as four broadcast float4 per
-// u); then the block's variables run in order in a rolled loop, each pushing
-// its y into the partial sums of the block's later variables through a
-// shifting window of accumulators (so the special-function code exists once).
-constexpr int DIAG_VB = 16;
-// Sub-tile of the float sweep: couplings between sub-tiles of one diagonal tile
-// are applied as a dense product before the sweep of each sub-tile.  DIAG_SUB is
-// the largest sub-tile and the one of the SIMT coupling; the tensor-core coupling
-// takes sweep_sub_tc() (64, the faster; TLRMVN_SUB=128 selects 128 in tuning runs).
-constexpr int DIAG_SUB = 128;
+// Sub-tile of the tensor-core coupling path: 64 (the faster; TLRMVN_SUB=128
+// selects 128 in tuning runs).  The SIMT coupling of the FP32 path uses DIAG_SUB.
 static int sweep_sub_tc() {
   static const int v = [] {
     const char* e = getenv("TLRMVN_SUB");
     return (e && atoi(e) == 128) ? 128 : 64;
   }();
   return v;
-}
-// Extra floats after the transposed tiles: the accumulator window may read up
-// to DIAG_VB - 1 entries past the last row.
-constexpr int DIAG_PAD = 32;
-// Shared memory of one block: the sub-tile's y of each sample (ld = blockDim + 1
-// floats per variable), then the per-variable constants (lattice generator,
-// limits, reciprocal diagonal).  Small blocks (32 samples) keep the footprint
-// near 10 KB, so ~21 blocks share an SM and a launch over 100,000 samples runs
-// in one wave.
-__host__ __device__ inline size_t sweep_ys_bytes(int mt, int bd) {
-  return ((size_t)mt * (bd + 1) * sizeof(float) + 15) / 16 * 16;
-}
-__host__ __device__ inline size_t sweep_smem_bytes(int mt, int bd) {
-  return sweep_ys_bytes(mt, bd) + (size_t)mt * (sizeof(uint64_t) + 3 * sizeof(float));
-}
-
-// Each variable's lattice offset is loaded one variable ahead and its window
-// column before its special functions, and the block's limit shifts are added
-// after its sums over earlier variables, so that those loads are in flight
-// while other work runs.
-__global__ void k_diag_f32(DiagArgs32 p) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int bd = blockDim.x, tid = threadIdx.x, ld = bd + 1;
-  const int mt = p.mt;
-  float* ys = reinterpret_cast<float*>(smem_raw);
-  uint64_t* s_q = reinterpret_cast<uint64_t*>(smem_raw + sweep_ys_bytes(mt, bd));
-  float* s_a = reinterpret_cast<float*>(s_q + mt);
-  float* s_b = s_a + mt;
-  float* s_inv = s_b + mt;
-  const int64_t c0 = (int64_t)blockIdx.x * bd;
-  pdl_trigger();
-  // limits, diagonal and generators are not written by the preceding kernels
-  for (int t = tid; t < mt; t += bd) {
-    s_a[t] = p.a[t];
-    s_b[t] = p.b[t];
-    s_inv[t] = p.inv[t];
-    s_q[t] = p.Q[p.coord0 + t];
-  }
-  __syncthreads();
-  pdl_wait();  // the limit shifts, y and log P of the preceding kernels
-  const bool act = c0 + tid < p.C;
-  const int64_t cs = act ? c0 + tid : p.C - 1;  // inactive lanes shadow a valid sample, write nothing
-  const int64_t g = p.sample0 + cs;
-  const int64_t sh = g / p.N;
-  const uint64_t ks = (uint64_t)(g - sh * p.N) + 1;
-  const uint64_t* Ds = p.D + sh * p.ldD + p.coord0;
-  const float rs = p.rs ? p.rs[cs] : 1.0f;
-  // log P of the sub-tile = log(prod) + pe log 2 + lsum: prod is kept in [1, 2)
-  // with its binary exponent in pe, so it neither underflows nor needs a log per variable
-  float prod = 1.0f, lsum = 0.0f;
-  int pe = 0;
-  for (int v0 = 0; v0 < mt; v0 += DIAG_VB) {
-    const int nb = min(DIAG_VB, mt - v0);
-    float acc[DIAG_VB], dl[DIAG_VB];
-#pragma unroll
-    for (int j = 0; j < DIAG_VB; j++) {
-      dl[j] = (p.Delta && j < nb) ? p.Delta[(int64_t)(v0 + j) * p.ldd + cs] : 0.0f;
-      acc[j] = 0.0f;
-    }
-    // lattice offset of the block's first variable
-    uint64_t dnext = Ds[v0];
-    // sums over the sub-tile's earlier variables for the block's 16 variables
-    const float* bcol = p.BT + v0;
-#pragma unroll 2
-    for (int u = 0; u < v0; u++) {
-      const float yu = ys[u * ld + tid];
-      const float4* b4 = reinterpret_cast<const float4*>(bcol + (int64_t)u * p.ldbt);
-      const float4 q[4] = {__ldg(b4), __ldg(b4 + 1), __ldg(b4 + 2), __ldg(b4 + 3)};
-#pragma unroll
-      for (int h = 0; h < 4; h++) {
-        acc[4 * h] = fmaf(q[h].x, yu, acc[4 * h]);
-        acc[4 * h + 1] = fmaf(q[h].y, yu, acc[4 * h + 1]);
-        acc[4 * h + 2] = fmaf(q[h].z, yu, acc[4 * h + 2]);
-        acc[4 * h + 3] = fmaf(q[h].w, yu, acc[4 * h + 3]);
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < DIAG_VB; j++) acc[j] += dl[j];
-#pragma unroll 1
-    for (int j = 0; j < nb; j++) {
-      const int v = v0 + j;
-      const float iv = s_inv[v], av = s_a[v], bv = s_b[v];
-      const uint64_t qv = s_q[v];
-      const uint64_t dv = dnext;
-      dnext = Ds[(j + 1 < nb) ? v + 1 : v];  // next variable's offset (the last one reloads its own)
-      // window column B[v+1..v+15][v], loaded before the step so that the loads
-      // are in flight during its special functions
-      float bcur[DIAG_VB - 1];
-      {
-        const float* brow = p.BT + (int64_t)v * p.ldbt + v + 1;
-#pragma unroll
-        for (int i = 0; i < DIAG_VB - 1; i++) bcur[i] = __ldg(brow + i);
-      }
-      const float sum = acc[0];  // shifts + earlier variables, for variable v
-      const float at = (av * rs - sum) * iv;
-      const float bt = (bv * rs - sum) * iv;
-      float w, wc;
-      lattice_wf(ks * qv + dv, p.periodize, w, wc);
-      float f, la, y;
-      sov_step_f32_prod(at, bt, w, wc, f, la, y);
-      lsum += la;
-      prod *= f;  // prod in [1, 2) and f >= Phi(-12): a normal float
-      const int pb = __float_as_int(prod);
-      pe += (pb >> 23) - 127;
-      prod = __int_as_float((pb & 0x007FFFFF) | 0x3F800000);
-      ys[v * ld + tid] = y;
-      if (p.Yv && act) p.Yv[(int64_t)v * p.ldyv + cs] = y;
-      // window shift: acc[i] <- acc[i+1] + B[v+1+i][v] y
-#pragma unroll
-      for (int i = 0; i < DIAG_VB - 1; i++) acc[i] = fmaf(bcur[i], y, acc[i + 1]);
-      acc[DIAG_VB - 1] = 0.0f;
-    }
-  }
-  if (act) {
-    const double lp = (double)(logf(prod) + lsum) + (double)pe * 0.69314718055994530942;
-    if (p.first) p.logP[g] = lp;
-    else p.logP[g] += lp;
-  }
-  if (p.Ys) {
-    __syncthreads();
-    const int nw = bd >> 5, warp = tid >> 5, lane = tid & 31;
-    for (int j = warp; j < bd; j += nw) {
-      if (c0 + j >= p.C) break;
-      __nv_bfloat16* row = p.Ys + (c0 + j) * p.ldys;
-      for (int v = lane; v < p.mt; v += 32) {
-        const float yv = ys[v * ld + j];
-        const __nv_bfloat16 hi = __float2bfloat16_rn(yv);
-        row[v] = hi;
-        if (p.ys_lo) row[p.ys_lo + v] = __float2bfloat16_rn(yv - __bfloat162float(hi));
-      }
-    }
-  }
 }
 
 // BT32[i][u][v] = B[i][v][u] (zero for v >= m), inv32[i][v] = 1 / B[i][v][v]
@@ -627,52 +461,69 @@ static int diag_threads(int m) {
   return bd;
 }
 
-// Samples per block of the float sweep.  Each sample's chain of special functions
-// is latency-bound, so a launch takes (waves) x (time of one block) and a second
-// wave for a few leftover blocks nearly doubles it.  Among block sizes of 2 to 8
-// warps this takes the fewest waves over C samples (occupancy from the CUDA
-// occupancy calculator, which accounts for registers and shared memory), and
-// among those the one nearest 128 samples per block (the size measured fastest
-// when waves tie).  TLRMVN_SWEEP_THREADS fixes the size for tuning runs.
-static int sweep_threads(int64_t C, int mt) {
+// Launch shape of the float sweep: samples per thread (spt) and per block (ns).
+// Each sample's chain of special functions is latency-bound, so a launch takes
+// (waves) x (time of one block) and a second wave for a few leftover blocks
+// nearly doubles it.  Among blocks of 2 to 8 warps this takes the fewest waves
+// over C samples (occupancy from the CUDA occupancy calculator, which accounts
+// for registers and shared memory), and among those the one nearest 128 samples
+// per block.  TLRMVN_SPT (1 or 2) and TLRMVN_SWEEP_THREADS fix the shape for
+// tuning runs.
+struct SweepShape {
+  int spt, threads, ns;
+};
+typedef void (*SweepKernel)(DiagArgs32);
+static SweepKernel sweep_kernel(int spt) { return spt == 2 ? k_diag_f32<2> : k_diag_f32<1>; }
+static int sweep_spt() {
+  static const int v = [] {
+    const char* e = getenv("TLRMVN_SPT");
+    return (e && atoi(e) == 2) ? 2 : 1;
+  }();
+  return v;
+}
+static SweepShape sweep_shape(int64_t C, int mt) {
+  const int spt = sweep_spt();
   static const int forced = [] {
     const char* e = getenv("TLRMVN_SWEEP_THREADS");
     const int v = e ? atoi(e) : 0;
     return (v >= 32 && v <= 256 && v % 32 == 0) ? v : 0;
   }();
-  if (forced) return forced;
+  if (forced) return SweepShape{spt, forced, forced * spt};
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   // one-entry memo per thread: a solve asks for the same (C, mt) once per sub-tile
   thread_local int64_t memo_c = -1;
-  thread_local int memo_mt = -1, memo_dev = -1, memo_bd = 128;
-  if (memo_c == C && memo_mt == mt && memo_dev == dev) return memo_bd;
+  thread_local int memo_mt = -1, memo_dev = -1;
+  thread_local SweepShape memo{1, 128, 128};
+  if (memo_c == C && memo_mt == mt && memo_dev == dev) return memo;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int best = 128;
+  SweepShape best{spt, 128 / spt, 128};
   int64_t best_waves = INT64_MAX;
-  for (int bd = 64; bd <= 256; bd += 32) {
+  for (int bd = 64 / spt; bd <= 256 / spt; bd += 32) {
+    const int ns = bd * spt;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_diag_f32, bd, sweep_smem_bytes(mt, bd)) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel(spt), bd, sweep_smem_bytes(mt, ns)) !=
             cudaSuccess ||
         per_sm < 1) {
       cudaGetLastError();
       continue;
     }
-    const int64_t blocks = (C + bd - 1) / bd, slots = (int64_t)per_sm * std::max(sms, 1);
+    const int64_t blocks = (C + ns - 1) / ns, slots = (int64_t)per_sm * std::max(sms, 1);
     const int64_t waves = (blocks + slots - 1) / slots;
-    if (waves < best_waves || (waves == best_waves && std::abs(bd - 128) < std::abs(best - 128))) {
+    if (waves < best_waves || (waves == best_waves && std::abs(ns - 128) < std::abs(best.ns - 128))) {
       best_waves = waves;
-      best = bd;
+      best = SweepShape{spt, bd, ns};
     }
   }
   memo_c = C;
   memo_mt = mt;
   memo_dev = dev;
-  memo_bd = best;
+  memo = best;
   return best;
 }
 static int set_sweep_smem(int m, int sub) {
-  TLR_CHECK(raise_smem_limit((const void*)k_diag_f32, sweep_smem_bytes(std::min(m, sub), 256)));
+  for (int spt = 1; spt <= 2; spt++)
+    TLR_CHECK(raise_smem_limit((const void*)sweep_kernel(spt), sweep_smem_bytes(std::min(m, sub), 256)));
   return TLRMVN_OK;
 }
 
@@ -697,7 +548,7 @@ static void sweep_tile_f32(const Factor& F, int i, bool has_shift, float* Dl, in
                            const TcCouple* tcc = nullptr) {
   const int m = F.m, mt = (int)F.tsize(i);
   const int sub = tcc ? tcc->sub : DIAG_SUB;
-  const int bd = sweep_threads(Cc, std::min(mt, sub));
+  const SweepShape sh = sweep_shape(Cc, std::min(mt, sub));
   const float* Bi = F.B32 + (size_t)i * m * m;
   for (int q0 = 0; q0 < mt; q0 += sub) {
     const int mq = std::min(sub, mt - q0);
@@ -750,9 +601,10 @@ static void sweep_tile_f32(const Factor& F, int i, bool has_shift, float* Dl, in
     a.logP = logP;
     pf.begin(TLRMVN_KC_DIAG);
     if (tcc)
-      launch_pdl(k_diag_f32, dim3(blocks_for(Cc, bd)), dim3(bd), sweep_smem_bytes(mq, bd), st, a);
+      launch_pdl(sweep_kernel(sh.spt), dim3(blocks_for(Cc, sh.ns)), dim3(sh.threads), sweep_smem_bytes(mq, sh.ns), st,
+                 a);
     else
-      k_diag_f32<<<blocks_for(Cc, bd), bd, sweep_smem_bytes(mq, bd), st>>>(a);
+      sweep_kernel(sh.spt)<<<blocks_for(Cc, sh.ns), sh.threads, sweep_smem_bytes(mq, sh.ns), st>>>(a);
     pf.end();
   }
 }

@@ -1,0 +1,213 @@
+// The float32 diagonal-tile sweep (eq. 2 over one sub-tile of a diagonal tile
+// B_i, Algorithm 6's per-tile step), one chain of variables per sample.
+#pragma once
+#include "common.cuh"
+#include "sov_device.cuh"
+
+namespace tlrmvn {
+
+// Arguments of one float32 sweep over a (sub-)tile of mt variables.  All
+// pointers are already offset to the sub-tile's first variable.
+struct DiagArgs32 {
+  const float* BT;   // transposed diagonal block, BT[u * ldbt + v] = B[v][u]
+  const float* inv;  // 1 / B[v][v]
+  int mt;
+  int64_t ldbt;
+  const float* Delta;  // limit shifts, variable-major (ldd), or null
+  int64_t ldd;
+  const float* a;
+  const float* b;
+  const float* rs;
+  const uint64_t* Q;
+  const uint64_t* D;
+  int64_t ldD, coord0, sample0, N, C;
+  int periodize, first;
+  float* Yv;             // y variable-major, Yv[v * ldyv + c], or null
+  int64_t ldyv;
+  __nv_bfloat16* Ys;     // y sample-major bf16, Ys[c * ldys + v], or null
+  int64_t ldys;
+  int64_t ys_lo;         // > 0: also the low part bf16(y - hi) at Ys[c * ldys + ys_lo + v]
+  double* logP;
+};
+
+// 16 variables per pass: the partial sums of a block of 16 variables over all
+// earlier variables of the (sub-)tile are accumulated together (each y_u read
+// once per block, B read as four broadcast float4 per u); then the block's
+// variables run in order in a rolled loop, each pushing its y into the partial
+// sums of the block's later variables through a shifting window of
+// accumulators (so the special-function code exists once).
+constexpr int DIAG_VB = 16;
+// Largest sub-tile, and the sub-tile of the SIMT coupling (FP32 path).
+constexpr int DIAG_SUB = 128;
+// Extra floats after the transposed tiles: the accumulator window may read up
+// to DIAG_VB - 1 entries past the last row.
+constexpr int DIAG_PAD = 32;
+
+// Shared memory of one block of `ns` samples: the sub-tile's y of each sample
+// (ns + 1 floats per variable), then the per-variable constants (lattice
+// generator, limits, reciprocal diagonal).
+__host__ __device__ inline size_t sweep_ys_bytes(int mt, int ns) {
+  return ((size_t)mt * (ns + 1) * sizeof(float) + 15) / 16 * 16;
+}
+__host__ __device__ inline size_t sweep_smem_bytes(int mt, int ns) {
+  return sweep_ys_bytes(mt, ns) + (size_t)mt * (sizeof(uint64_t) + 3 * sizeof(float));
+}
+
+// SPT samples per thread (samples c0 + tid + s * blockDim.x): every broadcast
+// load of B and of the per-variable constants serves SPT chains, and the SPT
+// chains are independent instruction streams for the scheduler.  Each
+// variable's lattice offsets are loaded one variable ahead and its window
+// column before its special functions, and the block's limit shifts are added
+// after its sums over earlier variables, so that those loads are in flight
+// while other work runs.
+template <int SPT>
+__global__ void k_diag_f32(DiagArgs32 p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int bd = blockDim.x, tid = threadIdx.x, ns = SPT * bd, ld = ns + 1;
+  const int mt = p.mt;
+  float* ys = reinterpret_cast<float*>(smem_raw);
+  uint64_t* s_q = reinterpret_cast<uint64_t*>(smem_raw + sweep_ys_bytes(mt, ns));
+  float* s_a = reinterpret_cast<float*>(s_q + mt);
+  float* s_b = s_a + mt;
+  float* s_inv = s_b + mt;
+  const int64_t c0 = (int64_t)blockIdx.x * ns;
+  pdl_trigger();
+  // limits, diagonal and generators are not written by the preceding kernels
+  for (int t = tid; t < mt; t += bd) {
+    s_a[t] = p.a[t];
+    s_b[t] = p.b[t];
+    s_inv[t] = p.inv[t];
+    s_q[t] = p.Q[p.coord0 + t];
+  }
+  __syncthreads();
+  pdl_wait();  // the limit shifts, y and log P of the preceding kernels
+  bool act[SPT];
+  int64_t cs[SPT];
+  uint64_t ks[SPT];
+  const uint64_t* Ds[SPT];
+  float rs[SPT];
+  // log P of the sub-tile = log(prod) + pe log 2 + lsum: prod is kept in [1, 2)
+  // with its binary exponent in pe, so it neither underflows nor needs a log per variable
+  float prod[SPT], lsum[SPT];
+  int pe[SPT];
+#pragma unroll
+  for (int s = 0; s < SPT; s++) {
+    act[s] = c0 + tid + s * bd < p.C;
+    cs[s] = act[s] ? c0 + tid + s * bd : p.C - 1;  // inactive lanes shadow a valid sample, write nothing
+    const int64_t g = p.sample0 + cs[s];
+    const int64_t sh = g / p.N;
+    ks[s] = (uint64_t)(g - sh * p.N) + 1;
+    Ds[s] = p.D + sh * p.ldD + p.coord0;
+    rs[s] = p.rs ? p.rs[cs[s]] : 1.0f;
+    prod[s] = 1.0f;
+    lsum[s] = 0.0f;
+    pe[s] = 0;
+  }
+  for (int v0 = 0; v0 < mt; v0 += DIAG_VB) {
+    const int nb = min(DIAG_VB, mt - v0);
+    float acc[SPT][DIAG_VB], dl[SPT][DIAG_VB];
+#pragma unroll
+    for (int s = 0; s < SPT; s++)
+#pragma unroll
+      for (int j = 0; j < DIAG_VB; j++) {
+        dl[s][j] = (p.Delta && j < nb) ? p.Delta[(int64_t)(v0 + j) * p.ldd + cs[s]] : 0.0f;
+        acc[s][j] = 0.0f;
+      }
+    // lattice offsets of the block's first variable
+    uint64_t dnext[SPT];
+#pragma unroll
+    for (int s = 0; s < SPT; s++) dnext[s] = Ds[s][v0];
+    // sums over the sub-tile's earlier variables for the block's 16 variables
+    const float* bcol = p.BT + v0;
+#pragma unroll 2
+    for (int u = 0; u < v0; u++) {
+      float yu[SPT];
+#pragma unroll
+      for (int s = 0; s < SPT; s++) yu[s] = ys[u * ld + tid + s * bd];
+      const float4* b4 = reinterpret_cast<const float4*>(bcol + (int64_t)u * p.ldbt);
+      const float4 q[4] = {__ldg(b4), __ldg(b4 + 1), __ldg(b4 + 2), __ldg(b4 + 3)};
+#pragma unroll
+      for (int s = 0; s < SPT; s++)
+#pragma unroll
+        for (int h = 0; h < 4; h++) {
+          acc[s][4 * h] = fmaf(q[h].x, yu[s], acc[s][4 * h]);
+          acc[s][4 * h + 1] = fmaf(q[h].y, yu[s], acc[s][4 * h + 1]);
+          acc[s][4 * h + 2] = fmaf(q[h].z, yu[s], acc[s][4 * h + 2]);
+          acc[s][4 * h + 3] = fmaf(q[h].w, yu[s], acc[s][4 * h + 3]);
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < SPT; s++)
+#pragma unroll
+      for (int j = 0; j < DIAG_VB; j++) acc[s][j] += dl[s][j];
+#pragma unroll 1
+    for (int j = 0; j < nb; j++) {
+      const int v = v0 + j;
+      const float iv = s_inv[v], av = s_a[v], bv = s_b[v];
+      const uint64_t qv = s_q[v];
+      uint64_t dv[SPT];
+#pragma unroll
+      for (int s = 0; s < SPT; s++) {
+        dv[s] = dnext[s];
+        dnext[s] = Ds[s][(j + 1 < nb) ? v + 1 : v];  // next variable's offset (the last one reloads its own)
+      }
+      // window column B[v+1..v+15][v], loaded before the step so that the loads
+      // are in flight during its special functions
+      float bcur[DIAG_VB - 1];
+      {
+        const float* brow = p.BT + (int64_t)v * p.ldbt + v + 1;
+#pragma unroll
+        for (int i = 0; i < DIAG_VB - 1; i++) bcur[i] = __ldg(brow + i);
+      }
+      float y[SPT];
+#pragma unroll
+      for (int s = 0; s < SPT; s++) {
+        const float sum = acc[s][0];  // shifts + earlier variables, for variable v
+        const float at = (av * rs[s] - sum) * iv;
+        const float bt = (bv * rs[s] - sum) * iv;
+        float w, wc;
+        lattice_wf(ks[s] * qv + dv[s], p.periodize, w, wc);
+        float f, la;
+        sov_step_f32_prod(at, bt, w, wc, f, la, y[s]);
+        lsum[s] += la;
+        prod[s] *= f;  // prod in [1, 2) and f >= Phi(-12): a normal float
+        const int pb = __float_as_int(prod[s]);
+        pe[s] += (pb >> 23) - 127;
+        prod[s] = __int_as_float((pb & 0x007FFFFF) | 0x3F800000);
+        ys[v * ld + tid + s * bd] = y[s];
+        if (p.Yv && act[s]) p.Yv[(int64_t)v * p.ldyv + cs[s]] = y[s];
+      }
+      // window shift: acc[i] <- acc[i+1] + B[v+1+i][v] y
+#pragma unroll
+      for (int i = 0; i < DIAG_VB - 1; i++)
+#pragma unroll
+        for (int s = 0; s < SPT; s++) acc[s][i] = fmaf(bcur[i], y[s], acc[s][i + 1]);
+#pragma unroll
+      for (int s = 0; s < SPT; s++) acc[s][DIAG_VB - 1] = 0.0f;
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < SPT; s++) {
+    if (!act[s]) continue;
+    const int64_t g = p.sample0 + cs[s];
+    const double lp = (double)(logf(prod[s]) + lsum[s]) + (double)pe[s] * 0.69314718055994530942;
+    if (p.first) p.logP[g] = lp;
+    else p.logP[g] += lp;
+  }
+  if (p.Ys) {
+    __syncthreads();
+    const int nw = bd >> 5, warp = tid >> 5, lane = tid & 31;
+    for (int j = warp; j < ns; j += nw) {
+      if (c0 + j >= p.C) break;
+      __nv_bfloat16* row = p.Ys + (c0 + j) * p.ldys;
+      for (int v = lane; v < p.mt; v += 32) {
+        const float yv = ys[v * ld + j];
+        const __nv_bfloat16 hi = __float2bfloat16_rn(yv);
+        row[v] = hi;
+        if (p.ys_lo) row[p.ys_lo + v] = __float2bfloat16_rn(yv - __bfloat162float(hi));
+      }
+    }
+  }
+}
+
+}  // namespace tlrmvn

@@ -76,9 +76,10 @@ __device__ inline double gamma_p_inv(double a, double p, double q) {
 
 // ---- float32 integrand helpers ------------------------------------------------------
 // Lattice value as floats, from the same exact numerator as lattice_w (integer
-// arithmetic only: the float path issues no float64 instruction).  w = num 2^-53
-// and 1 - w = (2^53 - num) 2^-53 with num < 2^53: each is one correctly rounded
-// integer-to-float conversion and an exact power-of-two scaling.
+// arithmetic only: the float path issues no float64 instruction).  The 53-bit
+// numerator is split into its top 32 and low 21 bits, each converted with a
+// 32-bit conversion (a 64-bit integer conversion runs on the float64 pipe, about
+// 2.5x slower per call on this GPU), and combined with one fma.
 __device__ __forceinline__ void lattice_wf(uint64_t x, int periodize, float& w, float& wc) {
   int64_t num;
   if (periodize) {
@@ -87,9 +88,10 @@ __device__ __forceinline__ void lattice_wf(uint64_t x, int periodize, float& w, 
   } else {
     num = (int64_t)((x >> 11) | 1);  // 2h + 1, h = x >> 12
   }
-  const float s53 = 1.1102230246251565e-16f;  // 2^-53
-  w = __ll2float_rn(num) * s53;
-  wc = __ll2float_rn((int64_t(1) << 53) - num) * s53;
+  const int64_t numc = (int64_t(1) << 53) - num;
+  w = fmaf((float)(uint32_t)(num >> 21), 2.3283064365386963e-10f, (float)(uint32_t)(num & 0x1FFFFF) * 1.1102230246251565e-16f);
+  wc = fmaf((float)(uint32_t)(numc >> 21), 2.3283064365386963e-10f,
+            (float)(uint32_t)(numc & 0x1FFFFF) * 1.1102230246251565e-16f);
 }
 
 // eq. (2) for one variable in float32.  The one-sided case (at = -inf), which is

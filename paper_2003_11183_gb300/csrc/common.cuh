@@ -78,6 +78,9 @@ struct Factor {
   //   inv32 r x m: 1 / B_i[v][v]
   float* BT32 = nullptr;
   float* inv32 = nullptr;
+  //   band32 r x m x 16: band32[(i*m + v)*16 + k] = B_i[v+1+k][v] for k < 15 and
+  //         v+1+k < m, else 0 (each variable's window column, contiguous)
+  float* band32 = nullptr;
   int64_t ldbt = 0;
   float* B32 = nullptr;
   float* U32 = nullptr;

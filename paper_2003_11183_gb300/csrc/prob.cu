@@ -263,11 +263,20 @@ __global__ void k_split_b16(const double* B, int m, int64_t my, int64_t count, _
 static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 // float32 diagonal tiles: row-major B32, transposed BT32 (ld ldbt), reciprocal diagonal inv32
+// band32[(i*m + v)*16 + k] = B_i[v+1+k][v] (k < 15, v+1+k < m), else 0
+__global__ void k_make_band(const double* B, int m, int64_t count, float* band) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  const int64_t row = t / 16, k = t % 16, i = row / m, v = row % m, u = v + 1 + k;
+  band[t] = (k < 15 && u < m) ? (float)B[(i * m + u) * m + v] : 0.0f;
+}
+
 int ensure_float_tiles(Factor& F, cudaStream_t st) {
-  if (F.B32 && F.BT32 && F.inv32) return TLRMVN_OK;
+  if (F.B32 && F.BT32 && F.inv32 && F.band32) return TLRMVN_OK;
   dfree(F.B32);  // a failed earlier attempt may have left some of these behind
   dfree(F.BT32);
   dfree(F.inv32);
+  dfree(F.band32);
   const int64_t nb = (int64_t)F.r * F.m * F.m;
   TLR_CHECK(dalloc(&F.B32, nb));
   k_convert<double, float><<<blocks_for(nb, 256), 256, 0, st>>>(F.B, F.B32, nb);
@@ -277,6 +286,9 @@ int ensure_float_tiles(Factor& F, cudaStream_t st) {
   TLR_CUDA(cudaMemsetAsync(F.BT32 + nt, 0, DIAG_PAD * sizeof(float), st));
   TLR_CHECK(dalloc(&F.inv32, (size_t)F.r * F.m));
   k_transpose_tiles<<<blocks_for(nt, 256), 256, 0, st>>>(F.B, F.m, F.ldbt, nt, F.BT32, F.inv32);
+  const int64_t nw = (int64_t)F.r * F.m * 16;
+  TLR_CHECK(dalloc(&F.band32, nw));
+  k_make_band<<<blocks_for(nw, 256), 256, 0, st>>>(F.B, F.m, nw, F.band32);
   TLR_CUDA(cudaGetLastError());
   return TLRMVN_OK;
 }
@@ -290,7 +302,7 @@ static bool bf16_ready(const Factor& F) {
 }
 static bool copies_ready(const Factor& F, int precision) {
   if (precision == TLRMVN_FP64) return true;
-  if (!F.B32 || !F.BT32 || !F.inv32) return false;
+  if (!F.B32 || !F.BT32 || !F.inv32 || !F.band32) return false;
   if (precision == TLRMVN_FP32) return (F.U32 && F.V32) || F.ktot == 0;
   return bf16_ready(F);
 }
@@ -577,6 +589,7 @@ static void sweep_tile_f32(const Factor& F, int i, bool has_shift, float* Dl, in
     DiagArgs32 a;
     a.BT = F.BT32 + (size_t)i * m * F.ldbt + (size_t)q0 * F.ldbt + q0;
     a.inv = F.inv32 + (size_t)i * m + q0;
+    a.band = F.band32 + ((size_t)i * m + q0) * 16;
     a.mt = mq;
     a.ldbt = F.ldbt;
     a.Delta = (has_shift || q0 > 0) ? Dl + (size_t)q0 * C : nullptr;

@@ -104,6 +104,7 @@ Factor::~Factor() {
   dfree(B32);
   dfree(BT32);
   dfree(inv32);
+  dfree(band32);
   dfree(U32);
   dfree(V32);
   dfree(U16);

@@ -11,6 +11,7 @@ namespace tlrmvn {
 struct DiagArgs32 {
   const float* BT;   // transposed diagonal block, BT[u * ldbt + v] = B[v][u]
   const float* inv;  // 1 / B[v][v]
+  const float* band; // band[v * 16 + k] = B[v+1+k][v] (k < 15; zero past the tile), 16-byte aligned
   int mt;
   int64_t ldbt;
   const float* Delta;  // limit shifts, variable-major (ldd), or null
@@ -151,13 +152,20 @@ __global__ void k_diag_f32(DiagArgs32 p) {
         dv[s] = dnext[s];
         dnext[s] = Ds[s][(j + 1 < nb) ? v + 1 : v];  // next variable's offset (the last one reloads its own)
       }
-      // window column B[v+1..v+15][v], loaded before the step so that the loads
-      // are in flight during its special functions
-      float bcur[DIAG_VB - 1];
+      // window column B[v+1..v+15][v] (four 16-byte loads of the band copy),
+      // loaded before the step so that the loads are in flight during its
+      // special functions
+      float bcur[DIAG_VB];
       {
-        const float* brow = p.BT + (int64_t)v * p.ldbt + v + 1;
+        const float4* b4 = reinterpret_cast<const float4*>(p.band + (int64_t)v * 16);
 #pragma unroll
-        for (int i = 0; i < DIAG_VB - 1; i++) bcur[i] = __ldg(brow + i);
+        for (int h = 0; h < 4; h++) {
+          const float4 x = __ldg(b4 + h);
+          bcur[4 * h] = x.x;
+          bcur[4 * h + 1] = x.y;
+          bcur[4 * h + 2] = x.z;
+          bcur[4 * h + 3] = x.w;
+        }
       }
       float y[SPT];
 #pragma unroll

@@ -42,7 +42,7 @@ METRIC = "MVN/MVT QMC sample-dims/sec at n=65,536 vs FP64 path; p50/p99 solve la
 TRAFFIC = {
     "k_diag_f32": {"bytes_per_sample_dim": (26.88384e6 + 0.145664e6) / (100000 * 64),
                    "capture": "profiles/k_diag_f32_sweep_n16384.md",
-                   "files": ["paper_2003_11183_gb300/csrc/prob.cu", "paper_2003_11183_gb300/csrc/sov_device.cuh",
+                   "files": ["paper_2003_11183_gb300/csrc/sweep.cuh", "paper_2003_11183_gb300/csrc/sov_device.cuh",
                              "paper_2003_11183_gb300/csrc/common.cuh", "include/tlrmvn.h"],
                    "sources": "ed990015d9b52b99a0b9c26715f72ee3ab4556c7e4dcffeff47418b6530843b2"},
 }

@@ -36,6 +36,7 @@ struct BatchProblem {
   const int32_t* kcpad;
   const float* BT;
   const float* inv;
+  const float* band;  // band[(i*m + v)*16 + k] = B_i[v+1+k][v] (the factor's band32)
   const float* UT;  // UT[(krow_off[i] + k) * ldbt + v] = Ucat_i[v][k]
   const float* VT;  // VT[vt_off[j] + u * kcpad[j] + k] = Vcat_j[k][u]
   const int32_t* vmap;
@@ -120,10 +121,18 @@ __global__ void __launch_bounds__(BATCH_T) k_batch(const BatchProblem* __restric
             ivn = __ldg(invi + vn);
             xn = k * P.Q[t0 + vn] + Ds[t0 + vn];
           }
-          float bcur[BATCH_VB - 1];  // B[v+1+i][v], loaded before the step's special functions
-          const float* brow = BTi + (int64_t)v * P.ldbt + v + 1;
+          float bcur[BATCH_VB];  // B[v+1+i][v] from the band copy, loaded before the step's special functions
+          {
+            const float4* b4 = reinterpret_cast<const float4*>(P.band + ((int64_t)i * P.m + v) * 16);
 #pragma unroll
-          for (int i = 0; i < BATCH_VB - 1; i++) bcur[i] = __ldg(brow + i);
+            for (int h = 0; h < 4; h++) {
+              const float4 x = __ldg(b4 + h);
+              bcur[4 * h] = x.x;
+              bcur[4 * h + 1] = x.y;
+              bcur[4 * h + 2] = x.z;
+              bcur[4 * h + 3] = x.w;
+            }
+          }
           const float sum = acc[0];
           const float at = (av * rs - sum) * iv;
           const float bt = (bv * rs - sum) * iv;
@@ -364,6 +373,7 @@ static int batch_build(Batch& B, int count, const tlrmvn_factor_t* factors, cons
       P.kcpad = C.kcpad;
       P.BT = F.BT32;
       P.inv = F.inv32;
+      P.band = F.band32;
       P.UT = C.UT;
       P.VT = C.VT;
       P.vmap = F.vmap;

@@ -45,13 +45,13 @@ constexpr int DIAG_SUB = 128;
 constexpr int DIAG_PAD = 32;
 
 // Shared memory of one block of `ns` samples: the sub-tile's y of each sample
-// (ns + 1 floats per variable), then the per-variable constants (lattice
-// generator, limits, reciprocal diagonal).
+// (ns + 1 floats per variable), then the per-variable constants: (a, b, 1/B_vv)
+// as one float4 per variable (one 16-byte load), then the lattice generators.
 __host__ __device__ inline size_t sweep_ys_bytes(int mt, int ns) {
   return ((size_t)mt * (ns + 1) * sizeof(float) + 15) / 16 * 16;
 }
 __host__ __device__ inline size_t sweep_smem_bytes(int mt, int ns) {
-  return sweep_ys_bytes(mt, ns) + (size_t)mt * (sizeof(uint64_t) + 3 * sizeof(float));
+  return sweep_ys_bytes(mt, ns) + (size_t)mt * (sizeof(float4) + sizeof(uint64_t));
 }
 
 // SPT samples per thread (samples c0 + tid + s * blockDim.x): every broadcast
@@ -67,24 +67,20 @@ __global__ void k_diag_f32(DiagArgs32 p) {
   const int bd = blockDim.x, tid = threadIdx.x, ns = SPT * bd, ld = ns + 1;
   const int mt = p.mt;
   float* ys = reinterpret_cast<float*>(smem_raw);
-  uint64_t* s_q = reinterpret_cast<uint64_t*>(smem_raw + sweep_ys_bytes(mt, ns));
-  float* s_a = reinterpret_cast<float*>(s_q + mt);
-  float* s_b = s_a + mt;
-  float* s_inv = s_b + mt;
+  float4* s_abi = reinterpret_cast<float4*>(smem_raw + sweep_ys_bytes(mt, ns));
+  uint64_t* s_q = reinterpret_cast<uint64_t*>(s_abi + mt);
   const int64_t c0 = (int64_t)blockIdx.x * ns;
   pdl_trigger();
   // limits, diagonal and generators are not written by the preceding kernels
   for (int t = tid; t < mt; t += bd) {
-    s_a[t] = p.a[t];
-    s_b[t] = p.b[t];
-    s_inv[t] = p.inv[t];
+    s_abi[t] = make_float4(p.a[t], p.b[t], p.inv[t], 0.0f);
     s_q[t] = p.Q[p.coord0 + t];
   }
   __syncthreads();
   pdl_wait();  // the limit shifts, y and log P of the preceding kernels
   bool act[SPT];
   int64_t cs[SPT];
-  uint64_t ks[SPT];
+  uint32_t ks[SPT];  // lattice point index k = 1..N (N < 2^31)
   const uint64_t* Ds[SPT];
   float rs[SPT];
   // log P of the sub-tile = log(prod) + pe log 2 + lsum: prod is kept in [1, 2)
@@ -97,7 +93,7 @@ __global__ void k_diag_f32(DiagArgs32 p) {
     cs[s] = act[s] ? c0 + tid + s * bd : p.C - 1;  // inactive lanes shadow a valid sample, write nothing
     const int64_t g = p.sample0 + cs[s];
     const int64_t sh = g / p.N;
-    ks[s] = (uint64_t)(g - sh * p.N) + 1;
+    ks[s] = (uint32_t)(g - sh * p.N) + 1u;
     Ds[s] = p.D + sh * p.ldD + p.coord0;
     rs[s] = p.rs ? p.rs[cs[s]] : 1.0f;
     prod[s] = 1.0f;
@@ -144,7 +140,8 @@ __global__ void k_diag_f32(DiagArgs32 p) {
 #pragma unroll 1
     for (int j = 0; j < nb; j++) {
       const int v = v0 + j;
-      const float iv = s_inv[v], av = s_a[v], bv = s_b[v];
+      const float4 abi = s_abi[v];
+      const float av = abi.x, bv = abi.y, iv = abi.z;
       const uint64_t qv = s_q[v];
       uint64_t dv[SPT];
 #pragma unroll
@@ -174,7 +171,7 @@ __global__ void k_diag_f32(DiagArgs32 p) {
         const float at = (av * rs[s] - sum) * iv;
         const float bt = (bv * rs[s] - sum) * iv;
         float w, wc;
-        lattice_wf(ks[s] * qv + dv[s], p.periodize, w, wc);
+        lattice_wf((uint64_t)ks[s] * qv + dv[s], p.periodize, w, wc);
         float f, la;
         sov_step_f32_prod(at, bt, w, wc, f, la, y[s]);
         lsum[s] += la;

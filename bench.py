@@ -40,11 +40,11 @@ METRIC = "MVN/MVT QMC sample-dims/sec at n=65,536 vs FP64 path; p50/p99 solve la
 # those sources are unchanged; the summaries with the capture commands are under
 # profiles/.
 TRAFFIC = {
-    "k_diag_f32": {"bytes_per_sample_dim": (26.88384e6 + 0.145664e6) / (100000 * 64),
+    "k_diag_f32": {"bytes_per_sample_dim": (26.879744e6 + 0.211456e6) / (100000 * 64),
                    "capture": "profiles/k_diag_f32_sweep_n16384.md",
                    "files": ["paper_2003_11183_gb300/csrc/sweep.cuh", "paper_2003_11183_gb300/csrc/sov_device.cuh",
                              "paper_2003_11183_gb300/csrc/common.cuh", "include/tlrmvn.h"],
-                   "sources": "ed990015d9b52b99a0b9c26715f72ee3ab4556c7e4dcffeff47418b6530843b2"},
+                   "sources": "1ebd0b1b34c7f7fda30a33e33166e7fba05274260d4816130c0915e0987f5222"},
 }
 
 

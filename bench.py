@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--n-side", type=int, default=0,
                     help="grid side of a smaller problem of the same family (profiling captures only)")
     ap.add_argument("--no-baselines", action="store_true", help="skip FP64-path and CPU-oracle legs")
+    ap.add_argument("--sample-chunk", type=int, default=0,
+                    help="samples per chunk of the solve (0 = the library's choice: all that fit)")
     ap.add_argument("--count", type=int, default=256, help="problems of the batched workload (--workload 4)")
     ap.add_argument("--requests", type=int, default=400, help="requests of the serving workload (--workload 5)")
     ap.add_argument("--rate", type=float, default=0.0, help="arrivals per second (--workload 5; 0 = measured)")
@@ -270,7 +272,7 @@ def run_ours(args):
     out = torch.zeros(2, dtype=torch.float64, device="cuda")
     per_shift = torch.zeros(w.n_shifts, dtype=torch.float64, device="cuda")
     kw = dict(nu=w.nu, precision=prec, n_shifts=w.n_shifts, n_points=w.n_points, shifts=w.shifts, stream=stream,
-              per_shift=per_shift)
+              per_shift=per_shift, sample_chunk=args.sample_chunk)
 
     for _ in range(args.warmup):
         tl.tlrmvn_prob_device(F, a, b, out, **kw)
@@ -409,7 +411,7 @@ def run_ours(args):
                 "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": {0: "f64", 1: "f32", 2: "f32+bf16"}[prec], "data": "synthetic",
-                "config": bench_config(tl, F, w, args.precision),
+                "config": dict(bench_config(tl, F, w, args.precision), sample_chunk=args.sample_chunk or "all"),
                 "clocks": clk,
                 "e2e": {"value": e2e, "unit": "sample-dims/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 16},
                 "gpu_launches": launches, "roofline": roof, "kernel_classes": classes, "cpu_baseline": cpu,

@@ -257,6 +257,13 @@ const char* tlrmvn_last_error(void);   /* thread-local detail of the last failur
  * TLRMVN_E_CUDA on a launch failure.  stream: cudaStream_t or NULL. */
 int tlrmvn_selftest_wait_timeout(int polls, void* stream);
 
+/* Evaluates, on the GPU, the float32 Phi(-x) that the float sweep uses for
+ * one-sided limits (a Mills-ratio fit, no counterpart in the paper) at n host
+ * values x >= 0 (1 <= n <= 2^24), writing n host floats to out; for tests of
+ * its error bound.  TLRMVN_E_INVAL for bad arguments, TLRMVN_E_CUDA on a
+ * device error. */
+int tlrmvn_selftest_phi_neg(const float* x, int n, float* out);
+
 /* Kernel classes of the integrand, for tlrmvn_profile_get. */
 #define TLRMVN_KC_SHIFT   0  /* low-rank limit shifts  Delta_i = U_i W_i           */
 #define TLRMVN_KC_DIAG    1  /* diagonal-tile SOV sweep (eq. 2 on B_i)              */

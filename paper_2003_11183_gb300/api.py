@@ -383,3 +383,13 @@ def tlrmvn_selftest_wait_timeout(polls: int = 1000, stream=None) -> int:
     """Status of the bounded-wait self-test (TLRMVN_E_TIMEOUT is the expected outcome)."""
     lib = L.load()
     return lib.tlrmvn_selftest_wait_timeout(int(polls), _stream_ptr(stream) if stream is not None else None)
+
+
+def tlrmvn_selftest_phi_neg(x) -> np.ndarray:
+    """The float sweep's Phi(-x) evaluated on the GPU at float32 values x >= 0."""
+    lib = L.load()
+    xs = np.ascontiguousarray(x, dtype=np.float32)
+    out = np.empty_like(xs)
+    _check(lib.tlrmvn_selftest_phi_neg(xs.ctypes.data_as(C.POINTER(C.c_float)), int(xs.size),
+                                       out.ctypes.data_as(C.POINTER(C.c_float))), "tlrmvn_selftest_phi_neg")
+    return out

@@ -1003,3 +1003,26 @@ extern "C" int tlrmvn_selftest_wait_timeout(int polls, void* stream) {
                                               std::to_string(herr) + ")");
   return TLRMVN_OK;
 }
+
+// Evaluates the sweep's float32 Phi(-x) (phi_neg_f32) on n host values.
+__global__ void k_phi_neg_selftest(const float* x, int n, float* out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) out[t] = phi_neg_f32(x[t]);
+}
+
+extern "C" int tlrmvn_selftest_phi_neg(const float* x, int n, float* out) {
+  if (!x || !out || n < 1 || n > (1 << 24)) return fail(TLRMVN_E_INVAL, "bad arguments");
+  cudaStream_t st = pick_stream(nullptr);
+  float* d = nullptr;
+  TLR_CUDA(cudaMallocAsync((void**)&d, (size_t)2 * n * sizeof(float), st));
+  cudaError_t e = cudaMemcpyAsync(d, x, (size_t)n * sizeof(float), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    k_phi_neg_selftest<<<(n + 255) / 256, 256, 0, st>>>(d, n, d + n);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, d + n, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(d, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "phi self-test");
+  return TLRMVN_OK;
+}

@@ -300,3 +300,16 @@ def test_full_size_mvt_n65536_sampled(tl):
     assert np.all(rel(pm16[sel], ref) < 1e-2)
     assert np.all(rel(ps16, ps32) < 1e-2)
     assert abs(lp16 - lp32) <= 3 * err32
+
+
+def test_float_phi_lower_tail_error_bound(tl):
+    # the float sweep's Phi(-x) (Mills-ratio fit) against Phi at the same float32
+    # inputs in float64: relative error within 1e-6 on [0, 12] (about 8 ulp), and
+    # small and non-negative beyond
+    from scipy.special import ndtr
+    x = np.concatenate([np.linspace(0.0, 12.0, 200001), [12.5, 13.0, 14.0, 20.0, 40.0]]).astype(np.float32)
+    got = tl.tlrmvn_selftest_phi_neg(x).astype(np.float64)
+    want = ndtr(-x.astype(np.float64))
+    inside = x <= 12.0
+    assert np.max(np.abs(got[inside] / want[inside] - 1.0)) < 1e-6
+    assert np.all(got[~inside] >= 0) and np.all(got[~inside] < 1e-33)

@@ -23,23 +23,26 @@
 namespace tlrmvn {
 namespace tc {
 
-constexpr int BM = 128, BK = 64;
-constexpr int A_BYTES = BM * BK * 2;  // 16 KB
+constexpr int BM = 128;
 constexpr uint32_t WAIT_LIMIT = 1u << 24;  // polls before a wait gives up (seconds)
 
 enum { EPI_TRANS_F32 = 0, EPI_TRANS_BF16 = 1 };
 
-// Shape of one kernel configuration: B tile bytes, stage bytes (SPLIT stages
-// hold hi and lo tiles of both operands), stage count and shared memory.  Stages
-// are sized so that two CTAs share an SM where they fit in about 100 KB each.
-// SPLIT configurations serve short-K products (the in-tile coupling, K <= 448):
-// one stage each, so that four CTAs share an SM and overlap one another.
-template <int BN, bool SPLIT, bool A_MN = false>
+// Shape of one kernel configuration: K depth of a stage (KB = 64 with 128-byte
+// swizzle, or 32 with 64-byte swizzle), tile bytes, stage bytes (SPLIT stages
+// hold hi and lo tiles of both operands), stage count and shared memory.  By
+// default stages are sized so that two CTAs share an SM where they fit in about
+// 100 KB each, and SPLIT configurations (short-K products: the in-tile coupling,
+// K <= 448) take one stage, so that several CTAs share an SM and overlap one
+// another; NSTQ > 0 fixes the stage count.
+template <int BN, bool SPLIT, bool A_MN = false, int KB = 64, int NSTQ = 0>
 struct Cfg {
-  static constexpr int B_BYTES = BN * BK * 2;
+  static constexpr int BK = KB;
+  static constexpr int A_BYTES = BM * KB * 2;
+  static constexpr int B_BYTES = BN * KB * 2;
   static constexpr int HALF = A_BYTES + B_BYTES;  // [A][B] of one precision part
   static constexpr int SB = SPLIT ? 2 * HALF : HALF;
-  static constexpr int NST = SPLIT ? 1 : ((4 * SB <= 100 * 1024) ? 4 : 2);
+  static constexpr int NST = NSTQ > 0 ? NSTQ : (SPLIT ? 1 : ((4 * SB <= 100 * 1024) ? 4 : 2));
   static constexpr int SMEM = NST * SB + 1024 /*align*/ + 256 /*barriers*/;
   // instruction descriptor of tcgen05.mma kind::f16: fp32 accumulator, bf16 A
   // and B, both K-major, N = BN (bits 17-22 hold N/8), M = 128 (bits 24-28 hold M/16)
@@ -47,20 +50,24 @@ struct Cfg {
   static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((A_MN ? 1u : 0u) << 15) |
                                     ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
   static_assert(BN == 64 || BN == 128 || BN == 256, "N of the MMA");
-  static_assert(HALF % 1024 == 0 && A_BYTES % 1024 == 0, "128-byte swizzle atoms need 1024-byte alignment");
+  static_assert(KB == 64 || KB == 32, "stage depth");
+  static_assert(!A_MN || KB == 64, "the MN-major operand uses 64-deep stages");
+  static_assert(HALF % (16 * KB) == 0 && A_BYTES % (16 * KB) == 0, "swizzle atoms (8 rows) must stay aligned");
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart (stride byte offset), descriptor version 1.
+// Shared-memory matrix descriptor: K-major, rows of 2 KB bytes (KB = 64: 128-byte
+// swizzle, 8-row groups 1024 bytes apart; KB = 32: 64-byte swizzle, 8-row
+// groups 512 bytes apart), descriptor version 1.
+template <int KB = 64>
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;            // leading byte offset (unused with this swizzle)
-  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
-  d |= (uint64_t)1 << 46;            // version
-  d |= (uint64_t)2 << 61;            // 128-byte swizzle
+  d |= (uint64_t)1 << 16;                  // leading byte offset (unused with swizzling)
+  d |= (uint64_t)((16 * KB) >> 4) << 32;   // stride byte offset: 8 rows of 2 KB bytes
+  d |= (uint64_t)1 << 46;                  // version
+  d |= (uint64_t)(KB == 64 ? 2 : 4) << 61;  // 128-byte or 64-byte swizzle
   return d;
 }
 
@@ -155,13 +162,18 @@ struct GemmTcArgs {
   int rows_fast = 0;    // grid: blockIdx.x walks the M blocks (CTAs that share a B tile run together)
 };
 
-// A's tensor map has a box of 64 x 128 (BM rows; A_MN: 64 M-elements x 64 K-rows,
-// loaded twice per stage), B's a box of 64 x BN.
-template <int EPI, bool SPLIT, int BN, bool A_MN = false>
-__global__ void __launch_bounds__(128, SPLIT ? 4 : 1) k_gemm_tc(const __grid_constant__ CUtensorMap mapA,
+// A's tensor map has a box of KB x 128 (BM rows; A_MN: 64 M-elements x 64 K-rows,
+// loaded twice per stage), B's a box of KB x BN; the maps' swizzle is 128-byte
+// for KB = 64 and 64-byte for KB = 32.
+// PREF (EPI_TRANS_F32, N = 64): the epilogue's old output values are loaded
+// while the MMAs run (64 registers; four CTAs per SM); without it they are loaded
+// 32 at a time just before their stores, and six CTAs fit per SM.
+template <int EPI, bool SPLIT, int BN, bool A_MN = false, int KB = 64, int NSTQ = 0, bool PREF = true>
+__global__ void __launch_bounds__(128, SPLIT ? (PREF ? 4 : 6) : 1) k_gemm_tc(const __grid_constant__ CUtensorMap mapA,
                                                  const __grid_constant__ CUtensorMap mapB, GemmTcArgs p) {
   static_assert(!(A_MN && SPLIT), "MN-major A is used without split operands");
-  using G = Cfg<BN, SPLIT, A_MN>;
+  using G = Cfg<BN, SPLIT, A_MN, KB, NSTQ>;
+  constexpr int BK = G::BK, A_BYTES = G::A_BYTES;
   constexpr int NST = G::NST;
   constexpr uint32_t SB = G::SB;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -240,7 +252,7 @@ __global__ void __launch_bounds__(128, SPLIT ? 4 : 1) k_gemm_tc(const __grid_con
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t sa = smem_u32(smem + s * SB);
-      const uint64_t da = A_MN ? sdesc_mn(sa) : sdesc(sa), db = sdesc(sa + A_BYTES);
+      const uint64_t da = A_MN ? sdesc_mn(sa) : sdesc<BK>(sa), db = sdesc<BK>(sa + A_BYTES);
       // per 16-deep k-step, in the descriptor's 16-byte units: K-major +32 bytes
       // (+2), MN-major two 1 KB K groups (+128)
       constexpr uint64_t ASTEP = A_MN ? 128 : 2;
@@ -248,7 +260,7 @@ __global__ void __launch_bounds__(128, SPLIT ? 4 : 1) k_gemm_tc(const __grid_con
       for (int kk = 0; kk < BK / 16; kk++) {
         mma_bf16(tmem, da + ASTEP * kk, db + (uint64_t)(kk * 2), G::IDESC, (kb > 0 || kk > 0) ? 1u : 0u);
         if (SPLIT) {
-          const uint64_t dal = sdesc(sa + G::HALF), dbl = sdesc(sa + G::HALF + A_BYTES);
+          const uint64_t dal = sdesc<BK>(sa + G::HALF), dbl = sdesc<BK>(sa + G::HALF + A_BYTES);
           mma_bf16(tmem, da + (uint64_t)(kk * 2), dbl + (uint64_t)(kk * 2), G::IDESC, 1u);
           mma_bf16(tmem, dal + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), G::IDESC, 1u);
         }
@@ -261,7 +273,7 @@ __global__ void __launch_bounds__(128, SPLIT ? 4 : 1) k_gemm_tc(const __grid_con
   const int row = m0 + 32 * warp + lane;
   // PRE: the output row's old values (accumulate) are loaded while the MMAs run;
   // the epilogue warps have nothing else to do until the accumulator is ready
-  constexpr bool PRE = (EPI == EPI_TRANS_F32) && BN <= 64;
+  constexpr bool PRE = PREF && (EPI == EPI_TRANS_F32) && BN <= 64;
   float pre[PRE ? BN : 1];
   if (PRE) {
     const bool ld = p.accumulate && row < p.M;

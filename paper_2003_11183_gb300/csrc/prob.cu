@@ -389,17 +389,19 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 // 2-D bf16 tensor (inner x outer, row pitch in bytes), box 64 x box_outer, 128-byte swizzle.
+// bf16 2-D map with a box of box_inner (64: 128-byte swizzle, 32: 64-byte
+// swizzle) x box_outer elements.
 static int make_map(CUtensorMap* map, const void* base, uint64_t inner, uint64_t outer, uint64_t pitch,
-                    uint32_t box_outer) {
+                    uint32_t box_outer, uint32_t box_inner = 64) {
   auto enc = tensor_map_encoder();
   if (!enc) return fail(TLRMVN_E_CUDA, "cuTensorMapEncodeTiled is not available");
   cuuint64_t dims[2] = {inner, outer};
   cuuint64_t strides[1] = {pitch};
-  cuuint32_t box[2] = {64, box_outer};
+  cuuint32_t box[2] = {box_inner, box_outer};
   cuuint32_t es[2] = {1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, box_inner == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(TLRMVN_E_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
   return TLRMVN_OK;
 }
@@ -548,11 +550,25 @@ static int set_sweep_smem(int m, int sub) {
 // Tensor-core in-tile coupling (BF16-shift path): tensor maps of F.B16x2 and of
 // the sample-major hi/lo y buffer, the offset of the lo halves, the error flag.
 struct TcCouple {
-  CUtensorMap mapB, mapY;
+  CUtensorMap mapB, mapY;      // 64-deep boxes (128-byte swizzle)
+  CUtensorMap mapB32, mapY32;  // 32-deep boxes (64-byte swizzle)
   int64_t my;
   int sub;  // sub-tile size, a multiple of 64
   int* err;
 };
+// Coupling kernel of 64-variable sub-tiles: one 32-deep stage (24 KB, 64-byte
+// swizzle) with the old outputs loaded just before their stores, so that six
+// CTAs share an SM and a launch over 100,000 samples (782 CTAs) runs in one
+// round; TLRMVN_COUPLE=64 selects, for tuning runs, one 64-deep stage of 48 KB
+// with the old outputs prefetched during the MMAs (four CTAs per SM).  Two
+// pipelined 32-deep stages measured no faster.
+static bool couple_k32() {
+  static const bool v = [] {
+    const char* e = getenv("TLRMVN_COUPLE");
+    return !(e && atoi(e) == 64);
+  }();
+  return v;
+}
 
 static void sweep_tile_f32(const Factor& F, int i, bool has_shift, float* Dl, int64_t C, const Lims& L,
                            const float* rs32, const uint64_t* dD, int64_t c0, int64_t N, int64_t Cc, int periodize,
@@ -574,7 +590,10 @@ static void sweep_tile_f32(const Factor& F, int i, bool has_shift, float* Dl, in
         g.blo = (int)tcc->my;
         g.accumulate = has_shift ? 1 : 0;
         const dim3 grid(1, (unsigned)((Cc + tc::BM - 1) / tc::BM));
-        if (tcc->sub == 64)
+        if (tcc->sub == 64 && couple_k32())
+          launch_pdl(tc::k_gemm_tc<tc::EPI_TRANS_F32, true, 64, false, 32, 1, false>, grid, dim3(128),
+                     tc::Cfg<64, true, false, 32, 1>::SMEM, st, tcc->mapY32, tcc->mapB32, g);
+        else if (tcc->sub == 64)
           launch_pdl(tc::k_gemm_tc<tc::EPI_TRANS_F32, true, 64>, grid, dim3(128), tc::Cfg<64, true>::SMEM, st, tcc->mapY,
                      tcc->mapB, g);
         else
@@ -754,6 +773,8 @@ static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opt
   if (F.B16x2) {
     tcc.sub = sweep_sub_tc();
     TLR_CHECK(make_map(&tcc.mapB, F.B16x2, ly, (uint64_t)F.r * m, ly * 2, (uint32_t)tcc.sub));
+    TLR_CHECK(make_map(&tcc.mapB32, F.B16x2, ly, (uint64_t)F.r * m, ly * 2, (uint32_t)tcc.sub, 32));
+    TLR_CHECK(make_map(&tcc.mapY32, Y, ly, C, ly * 2, tc::BM, 32));
     tcc.mapY = mapY;
     tcc.my = F.my16;
     tcc.err = err;
@@ -764,6 +785,8 @@ static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opt
   TLR_CHECK(raise_smem_limit((const void*)tc::k_gemm_tc<tc::EPI_TRANS_BF16, false, 128>, tc::Cfg<128, false>::SMEM));
   TLR_CHECK(raise_smem_limit((const void*)tc::k_gemm_tc<tc::EPI_TRANS_BF16, false, 64>, tc::Cfg<64, false>::SMEM));
   TLR_CHECK(raise_smem_limit((const void*)tc::k_gemm_tc<tc::EPI_TRANS_F32, true, 64>, tc::Cfg<64, true>::SMEM));
+  TLR_CHECK(raise_smem_limit((const void*)tc::k_gemm_tc<tc::EPI_TRANS_F32, true, 64, false, 32, 1, false>,
+                             tc::Cfg<64, true, false, 32, 1>::SMEM));
   TLR_CHECK(raise_smem_limit((const void*)tc::k_gemm_tc<tc::EPI_TRANS_F32, true, 128>, tc::Cfg<128, true>::SMEM));
 
   TLR_CHECK(set_sweep_smem(m, sweep_sub_tc()));

@@ -45,6 +45,7 @@ __global__ void k_permute_limits(const double* a, const double* b, const int64_t
   if (t >= n) return;
   double av = a[perm[t]], bv = b[perm[t]];
   if (isnan(av) || isnan(bv) || av > bv || av == INFINITY || bv == -INFINITY) atomicExch(bad, 1);
+  if (av != -INFINITY) atomicExch(bad + 1, 1);  // a finite lower limit: not a one-sided problem
   ap[t] = av;
   bp[t] = bv;
   if (ap32) {
@@ -464,6 +465,7 @@ struct Lims {
   const double* b;
   const float* a32;
   const float* b32;
+  bool one_sided;  // every lower limit is -inf
 };
 
 // Threads per block of the sweep: as many as keep the tile's y values of the
@@ -481,22 +483,19 @@ static int diag_threads(int m) {
 // nearly doubles it.  Among blocks of 2 to 8 warps this takes the fewest waves
 // over C samples (occupancy from the CUDA occupancy calculator, which accounts
 // for registers and shared memory), and among those the one nearest 128 samples
-// per block.  TLRMVN_SPT (1 or 2) and TLRMVN_SWEEP_THREADS fix the shape for
-// tuning runs.
+// per block.  TLRMVN_SWEEP_THREADS fixes the block size for tuning runs.  One
+// sample per thread (two per thread, k_diag_f32<2, .>, measured slower).
 struct SweepShape {
   int spt, threads, ns;
 };
 typedef void (*SweepKernel)(DiagArgs32);
-static SweepKernel sweep_kernel(int spt) { return spt == 2 ? k_diag_f32<2> : k_diag_f32<1>; }
-static int sweep_spt() {
-  static const int v = [] {
-    const char* e = getenv("TLRMVN_SPT");
-    return (e && atoi(e) == 2) ? 2 : 1;
-  }();
-  return v;
+static SweepKernel sweep_kernel(int flags) {
+  static const SweepKernel table[8] = {k_diag_f32<1, 0>, k_diag_f32<1, 1>, k_diag_f32<1, 2>, k_diag_f32<1, 3>,
+                                       k_diag_f32<1, 4>, k_diag_f32<1, 5>, k_diag_f32<1, 6>, k_diag_f32<1, 7>};
+  return table[flags & 7];
 }
 static SweepShape sweep_shape(int64_t C, int mt) {
-  const int spt = sweep_spt();
+  const int spt = 1;
   static const int forced = [] {
     const char* e = getenv("TLRMVN_SWEEP_THREADS");
     const int v = e ? atoi(e) : 0;
@@ -516,7 +515,8 @@ static SweepShape sweep_shape(int64_t C, int mt) {
   for (int bd = 64 / spt; bd <= 256 / spt; bd += 32) {
     const int ns = bd * spt;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel(spt), bd, sweep_smem_bytes(mt, ns)) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel(SWEEP_PERIODIZE | SWEEP_ONE_SIDED), bd,
+                                                      sweep_smem_bytes(mt, ns)) !=
             cudaSuccess ||
         per_sm < 1) {
       cudaGetLastError();
@@ -536,8 +536,8 @@ static SweepShape sweep_shape(int64_t C, int mt) {
   return best;
 }
 static int set_sweep_smem(int m, int sub) {
-  for (int spt = 1; spt <= 2; spt++)
-    TLR_CHECK(raise_smem_limit((const void*)sweep_kernel(spt), sweep_smem_bytes(std::min(m, sub), 256)));
+  for (int flags = 0; flags < 8; flags++)
+    TLR_CHECK(raise_smem_limit((const void*)sweep_kernel(flags), sweep_smem_bytes(std::min(m, sub), 256)));
   return TLRMVN_OK;
 }
 
@@ -632,11 +632,12 @@ static void sweep_tile_f32(const Factor& F, int i, bool has_shift, float* Dl, in
     a.ys_lo = tcc ? tcc->my : 0;
     a.logP = logP;
     pf.begin(TLRMVN_KC_DIAG);
+    const int flags = (periodize ? SWEEP_PERIODIZE : 0) | (a.Yv ? SWEEP_YV : 0) | (L.one_sided ? SWEEP_ONE_SIDED : 0);
     if (tcc)
-      launch_pdl(sweep_kernel(sh.spt), dim3(blocks_for(Cc, sh.ns)), dim3(sh.threads), sweep_smem_bytes(mq, sh.ns), st,
+      launch_pdl(sweep_kernel(flags), dim3(blocks_for(Cc, sh.ns)), dim3(sh.threads), sweep_smem_bytes(mq, sh.ns), st,
                  a);
     else
-      sweep_kernel(sh.spt)<<<blocks_for(Cc, sh.ns), sh.threads, sweep_smem_bytes(mq, sh.ns), st>>>(a);
+      sweep_kernel(flags)<<<blocks_for(Cc, sh.ns), sh.threads, sweep_smem_bytes(mq, sh.ns), st>>>(a);
     pf.end();
   }
 }
@@ -876,7 +877,7 @@ int prob_impl(Factor& F, const double* a_dev, const double* b_dev, double nu, co
     TLR_CHECK(sc.get(&ap32, n));
     TLR_CHECK(sc.get(&bp32, n));
   }
-  TLR_CHECK(sc.get(&bad, 1));
+  TLR_CHECK(sc.get(&bad, 2));  // invalid limits; a finite lower limit
   TLR_CHECK(sc.get(&dD, (size_t)M * (n + 1)));
   TLR_CHECK(sc.get(&ell, M));
   if (per_sample_dev) logP = per_sample_dev;
@@ -893,21 +894,21 @@ int prob_impl(Factor& F, const double* a_dev, const double* b_dev, double nu, co
     TLR_CUDA(cudaMemcpyAsync(dD, src, (size_t)M * (n + 1) * 8, cudaMemcpyHostToDevice, st));
     if (!hD.empty()) TLR_CUDA(cudaStreamSynchronize(st));
   }
-  TLR_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
+  TLR_CUDA(cudaMemsetAsync(bad, 0, 2 * sizeof(int), st));
   Prof pf(st);
   pf.begin(TLRMVN_KC_PREP);
   k_permute_limits<<<blocks_for(n, 256), 256, 0, st>>>(a_dev, b_dev, F.dperm, n, ap, bp, ap32, bp32, bad);
   pf.end();
-  int hbad = 0;
-  TLR_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+  int hbad[2] = {0, 0};
+  TLR_CUDA(cudaMemcpyAsync(hbad, bad, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
   TLR_CUDA(cudaStreamSynchronize(st));
-  if (hbad) {
+  if (hbad[0]) {
     pf.collect();
     return fail(TLRMVN_E_INVAL, "limits must satisfy a_i <= b_i, a_i < +inf, b_i > -inf, no NaN");
   }
   TLR_CHECK(ensure_copies(F, o.precision, st));
   int s;
-  const Lims L{ap, bp, ap32, bp32};
+  const Lims L{ap, bp, ap32, bp32, hbad[1] == 0};
   if (o.precision == TLRMVN_FP64)
     s = run_chunks<double, double>(F, F.B, F.Ucat, F.Vcat, L, nu, o, dD, logP, sc, st, pf);
   else if (o.precision == TLRMVN_FP32)

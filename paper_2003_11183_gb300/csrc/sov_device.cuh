@@ -169,9 +169,9 @@ __device__ __forceinline__ float phi_neg_f32(float x) {
 // fl(1 - c) would lose c's digits and the step returns la = log1p(-c) taken as
 // -c - c^2/2 (the next term is below 2^-24 c); the deep tail and two-sided
 // intervals return their log.  No log is evaluated on the fast path.
-__device__ __forceinline__ void sov_step_f32_prod(float at, float bt, float w, float wc, float& f, float& la,
-                                                  float& y) {
-  if (at == -INFINITY && bt != INFINITY && bt >= -12.0f) {
+// sov_step_f32_upper is the one-sided (at = -inf) case on its own.
+__device__ __forceinline__ void sov_step_f32_upper(float bt, float w, float wc, float& f, float& la, float& y) {
+  if (bt != INFINITY && bt >= -12.0f) {
     const float h = phi_neg_f32(fabsf(bt));  // Phi(-|bt|)
     const bool neg = bt < 0.0f;
     const float ph = neg ? h : 1.0f - h;  // Phi(bt)
@@ -189,6 +189,17 @@ __device__ __forceinline__ void sov_step_f32_prod(float at, float bt, float w, f
       const float lu = logf(w) + logf(ph);
       y = ndtri_lower(expf(lu), lu);
     }
+    return;
+  }
+  float ld;
+  sov_step_f32(-INFINITY, bt, w, wc, ld, y);
+  f = 1.0f;
+  la = ld;
+}
+__device__ __forceinline__ void sov_step_f32_prod(float at, float bt, float w, float wc, float& f, float& la,
+                                                  float& y) {
+  if (at == -INFINITY) {
+    sov_step_f32_upper(bt, w, wc, f, la, y);
     return;
   }
   float ld;

@@ -54,6 +54,11 @@ __host__ __device__ inline size_t sweep_smem_bytes(int mt, int ns) {
   return sweep_ys_bytes(mt, ns) + (size_t)mt * (sizeof(float4) + sizeof(uint64_t));
 }
 
+// FLAGS, fixed for a launch: SWEEP_PERIODIZE (tent-periodised lattice),
+// SWEEP_YV (also write y as float to Yv), SWEEP_ONE_SIDED (every lower limit of
+// the problem is -inf: the one-sided step only).
+enum { SWEEP_PERIODIZE = 1, SWEEP_YV = 2, SWEEP_ONE_SIDED = 4 };
+
 // SPT samples per thread (samples c0 + tid + s * blockDim.x): every broadcast
 // load of B and of the per-variable constants serves SPT chains, and the SPT
 // chains are independent instruction streams for the scheduler.  Each
@@ -61,8 +66,9 @@ __host__ __device__ inline size_t sweep_smem_bytes(int mt, int ns) {
 // column before its special functions, and the block's limit shifts are added
 // after its sums over earlier variables, so that those loads are in flight
 // while other work runs.
-template <int SPT>
+template <int SPT, int FLAGS>
 __global__ void k_diag_f32(DiagArgs32 p) {
+  constexpr bool PER = FLAGS & SWEEP_PERIODIZE, YV = FLAGS & SWEEP_YV, ONE = FLAGS & SWEEP_ONE_SIDED;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int bd = blockDim.x, tid = threadIdx.x, ns = SPT * bd, ld = ns + 1;
   const int mt = p.mt;
@@ -168,19 +174,23 @@ __global__ void k_diag_f32(DiagArgs32 p) {
 #pragma unroll
       for (int s = 0; s < SPT; s++) {
         const float sum = acc[s][0];  // shifts + earlier variables, for variable v
-        const float at = (av * rs[s] - sum) * iv;
         const float bt = (bv * rs[s] - sum) * iv;
         float w, wc;
-        lattice_wf((uint64_t)ks[s] * qv + dv[s], p.periodize, w, wc);
+        lattice_wf((uint64_t)ks[s] * qv + dv[s], PER ? 1 : 0, w, wc);
         float f, la;
-        sov_step_f32_prod(at, bt, w, wc, f, la, y[s]);
+        if (ONE) {
+          sov_step_f32_upper(bt, w, wc, f, la, y[s]);
+        } else {
+          const float at = (av * rs[s] - sum) * iv;
+          sov_step_f32_prod(at, bt, w, wc, f, la, y[s]);
+        }
         lsum[s] += la;
         prod[s] *= f;  // prod in [1, 2) and f >= Phi(-12): a normal float
         const int pb = __float_as_int(prod[s]);
         pe[s] += (pb >> 23) - 127;
         prod[s] = __int_as_float((pb & 0x007FFFFF) | 0x3F800000);
         ys[v * ld + tid + s * bd] = y[s];
-        if (p.Yv && act[s]) p.Yv[(int64_t)v * p.ldyv + cs[s]] = y[s];
+        if (YV && act[s]) p.Yv[(int64_t)v * p.ldyv + cs[s]] = y[s];
       }
       // window shift: acc[i] <- acc[i+1] + B[v+1+i][v] y
 #pragma unroll

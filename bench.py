@@ -40,11 +40,11 @@ METRIC = "MVN/MVT QMC sample-dims/sec at n=65,536 vs FP64 path; p50/p99 solve la
 # those sources are unchanged; the summaries with the capture commands are under
 # profiles/.
 TRAFFIC = {
-    "k_diag_f32": {"bytes_per_sample_dim": (26.879744e6 + 0.211456e6) / (100000 * 64),
+    "k_diag_f32": {"bytes_per_sample_dim": (26.852352e6 + 0.152576e6) / (100000 * 64),
                    "capture": "profiles/k_diag_f32_sweep_n16384.md",
                    "files": ["paper_2003_11183_gb300/csrc/sweep.cuh", "paper_2003_11183_gb300/csrc/sov_device.cuh",
                              "paper_2003_11183_gb300/csrc/common.cuh", "include/tlrmvn.h"],
-                   "sources": "1ebd0b1b34c7f7fda30a33e33166e7fba05274260d4816130c0915e0987f5222"},
+                   "sources": "fa41722fc1546c692dca6d59d84b9397ce095b1c0265128954f440b8a690207c"},
 }
 
 

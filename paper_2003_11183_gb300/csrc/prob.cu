@@ -139,11 +139,21 @@ __global__ void k_diag(DiagArgs<T, YT> p) {
 }
 
 // Sub-tile of the tensor-core coupling path: 64 (the faster; TLRMVN_SUB=128
-// selects 128 in tuning runs).  The SIMT coupling of the FP32 path uses DIAG_SUB.
+// selects 128 in tuning runs).
 static int sweep_sub_tc() {
   static const int v = [] {
     const char* e = getenv("TLRMVN_SUB");
     return (e && atoi(e) == 128) ? 128 : 64;
+  }();
+  return v;
+}
+// Sub-tile of the FP32 path, whose coupling is the SIMT SGEMM: 64 (the faster:
+// 514 vs 574 ms per solve at n = 65,536), or DIAG_SUB = 128 (TLRMVN_SUB32=128,
+// tuning runs).
+static int sweep_sub_simt() {
+  static const int v = [] {
+    const char* e = getenv("TLRMVN_SUB32");
+    return (e && atoi(e) == 128) ? DIAG_SUB : 64;
   }();
   return v;
 }
@@ -575,7 +585,7 @@ static void sweep_tile_f32(const Factor& F, int i, bool has_shift, float* Dl, in
                            float* Yv, __nv_bfloat16* Ys, int64_t ldys, double* logP, cudaStream_t st, Prof& pf,
                            const TcCouple* tcc = nullptr) {
   const int m = F.m, mt = (int)F.tsize(i);
-  const int sub = tcc ? tcc->sub : DIAG_SUB;
+  const int sub = tcc ? tcc->sub : sweep_sub_simt();
   const SweepShape sh = sweep_shape(Cc, std::min(mt, sub));
   const float* Bi = F.B32 + (size_t)i * m * m;
   for (int q0 = 0; q0 < mt; q0 += sub) {
@@ -663,7 +673,7 @@ static int run_chunks(Factor& F, const T* Bt, const T* Ut, const T* Vt, const Li
   const int bd = diag_threads<T>(m);
   const size_t smem = (size_t)m * (bd + 1) * sizeof(T);
   if (f32)
-    TLR_CHECK(set_sweep_smem(m, DIAG_SUB));
+    TLR_CHECK(set_sweep_smem(m, sweep_sub_simt()));
   else
     TLR_CHECK(raise_smem_limit((const void*)k_diag<T, YT, false>, (size_t)smem));
 

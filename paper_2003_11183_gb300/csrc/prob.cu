@@ -572,6 +572,15 @@ struct TcCouple {
 // round; TLRMVN_COUPLE=64 selects, for tuning runs, one 64-deep stage of 48 KB
 // with the old outputs prefetched during the MMAs (four CTAs per SM).  Two
 // pipelined 32-deep stages measured no faster.
+// Shift and projection GEMMs in N = 128 tiles (more CTAs per SM) unless
+// TLRMVN_NARROW=0 (tuning runs: N = 256 tiles).
+static bool gemm_narrow() {
+  static const bool v = [] {
+    const char* e = getenv("TLRMVN_NARROW");
+    return !(e && atoi(e) == 0);
+  }();
+  return v;
+}
 static bool couple_k32() {
   static const bool v = [] {
     const char* e = getenv("TLRMVN_COUPLE");
@@ -771,9 +780,10 @@ static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opt
   //   shift      Dl^T (samples x vars) = W16^T (A, MN-major) x U16 rows (B, N = 256)
   //   projection W16 rows^T (samples x ranks) = Y16 rows (A) x V16 rows (B, N = 256)
   //   coupling   Dl^T += Y16 rows (A, hi/lo) x B16x2 rows (B, hi/lo, N = sub-tile)
-  CUtensorMap mapU, mapV, mapV64, mapV128, mapW, mapY;
+  CUtensorMap mapU, mapU128, mapV, mapV64, mapV128, mapW, mapY;
   if (F.ktot) {
     TLR_CHECK(make_map(&mapU, F.U16, F.kmax16, (uint64_t)F.r * m, F.kmax16 * 2, 256));
+    TLR_CHECK(make_map(&mapU128, F.U16, F.kmax16, (uint64_t)F.r * m, F.kmax16 * 2, 128));
     TLR_CHECK(make_map(&mapV, F.V16, F.my16, F.ktot, F.my16 * 2, 256));
     TLR_CHECK(make_map(&mapV64, F.V16, F.my16, F.ktot, F.my16 * 2, 64));
     TLR_CHECK(make_map(&mapV128, F.V16, F.my16, F.ktot, F.my16 * 2, 128));
@@ -792,6 +802,8 @@ static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opt
   }
   TLR_CHECK(raise_smem_limit((const void*)tc::k_gemm_tc<tc::EPI_TRANS_F32, false, 256, true>,
                              tc::Cfg<256, false, true>::SMEM));
+  TLR_CHECK(raise_smem_limit((const void*)tc::k_gemm_tc<tc::EPI_TRANS_F32, false, 128, true, 64, 1>,
+                             tc::Cfg<128, false, true, 64, 1>::SMEM));
   TLR_CHECK(raise_smem_limit((const void*)tc::k_gemm_tc<tc::EPI_TRANS_BF16, false, 256>, tc::Cfg<256, false>::SMEM));
   TLR_CHECK(raise_smem_limit((const void*)tc::k_gemm_tc<tc::EPI_TRANS_BF16, false, 128>, tc::Cfg<128, false>::SMEM));
   TLR_CHECK(raise_smem_limit((const void*)tc::k_gemm_tc<tc::EPI_TRANS_BF16, false, 64>, tc::Cfg<64, false>::SMEM));
@@ -818,8 +830,13 @@ static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opt
       if (Kr > 0) {
         tc::GemmTcArgs g{(int)Cc, mt, (int)Kr, (int)F.kpad_off[i], 0, 0, i * m, Dl, C, nullptr, 0, nullptr, err};
         pf.begin(TLRMVN_KC_SHIFT);
-        launch_pdl(tc::k_gemm_tc<tc::EPI_TRANS_F32, false, 256, true>, dim3((unsigned)((mt + 255) / 256), sblocks),
-                   dim3(128), tc::Cfg<256, false, true>::SMEM, st, mapW, mapU, g);
+        if (gemm_narrow())  // N = 128, one stage: four CTAs per SM (TMEM 4 x 128 columns)
+          launch_pdl(tc::k_gemm_tc<tc::EPI_TRANS_F32, false, 128, true, 64, 1>,
+                     dim3((unsigned)((mt + 127) / 128), sblocks), dim3(128), tc::Cfg<128, false, true, 64, 1>::SMEM, st,
+                     mapW, mapU128, g);
+        else
+          launch_pdl(tc::k_gemm_tc<tc::EPI_TRANS_F32, false, 256, true>, dim3((unsigned)((mt + 255) / 256), sblocks),
+                     dim3(128), tc::Cfg<256, false, true>::SMEM, st, mapW, mapU, g);
         pf.end();
         Delta = Dl;
       }
@@ -835,8 +852,8 @@ static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opt
         if (Kc <= 64)
           launch_pdl(tc::k_gemm_tc<tc::EPI_TRANS_BF16, false, 64>, dim3(1, sblocks), dim3(128),
                      tc::Cfg<64, false>::SMEM, st, mapY, mapV64, g);
-        else if (Kc <= 128)
-          launch_pdl(tc::k_gemm_tc<tc::EPI_TRANS_BF16, false, 128>, dim3(1, sblocks), dim3(128),
+        else if (Kc <= 128 || gemm_narrow())
+          launch_pdl(tc::k_gemm_tc<tc::EPI_TRANS_BF16, false, 128>, dim3((unsigned)((Kc + 127) / 128), sblocks), dim3(128),
                      tc::Cfg<128, false>::SMEM, st, mapY, mapV128, g);
         else
           launch_pdl(tc::k_gemm_tc<tc::EPI_TRANS_BF16, false, 256>, dim3((unsigned)((Kc + 255) / 256), sblocks),

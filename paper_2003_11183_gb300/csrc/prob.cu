@@ -15,6 +15,7 @@
 #include "gemm_tc.cuh"
 #include "sov_device.cuh"
 #include "sweep.cuh"
+#include "sweep_tc.cuh"
 
 #include <cudaTypedefs.h>
 
@@ -545,9 +546,27 @@ static SweepShape sweep_shape(int64_t C, int mt) {
   memo = best;
   return best;
 }
+// The whole-tile sweep with tensor-core coupling (BF16-shift path), by
+// (periodisation, one-sided) flags; TLRMVN_FUSED=0 selects, for tuning runs,
+// sub-tile sweeps with separate coupling products instead.
+typedef void (*SweepTcKernel)(const CUtensorMap, const CUtensorMap, SweepTcArgs);
+static SweepTcKernel sweep_tc_kernel(int flags) {
+  static const SweepTcKernel table[4] = {k_sweep_tc<0>, k_sweep_tc<SWEEP_PERIODIZE>, k_sweep_tc<SWEEP_ONE_SIDED>,
+                                         k_sweep_tc<SWEEP_PERIODIZE | SWEEP_ONE_SIDED>};
+  return table[((flags & SWEEP_PERIODIZE) ? 1 : 0) | ((flags & SWEEP_ONE_SIDED) ? 2 : 0)];
+}
+static bool sweep_fused() {
+  static const bool v = [] {
+    const char* e = getenv("TLRMVN_FUSED");
+    return !(e && atoi(e) == 0);
+  }();
+  return v;
+}
 static int set_sweep_smem(int m, int sub) {
   for (int flags = 0; flags < 8; flags++)
     TLR_CHECK(raise_smem_limit((const void*)sweep_kernel(flags), sweep_smem_bytes(std::min(m, sub), 256)));
+  for (int flags = 0; flags < 8; flags++)
+    TLR_CHECK(raise_smem_limit((const void*)sweep_tc_kernel(flags), sweep_tc_smem_bytes()));
   return TLRMVN_OK;
 }
 
@@ -594,6 +613,45 @@ static void sweep_tile_f32(const Factor& F, int i, bool has_shift, float* Dl, in
                            float* Yv, __nv_bfloat16* Ys, int64_t ldys, double* logP, cudaStream_t st, Prof& pf,
                            const TcCouple* tcc = nullptr) {
   const int m = F.m, mt = (int)F.tsize(i);
+  if (tcc && tcc->sub == STC_SUB && sweep_fused()) {
+    SweepTcArgs t;
+    DiagArgs32& a = t.d;
+    a.BT = F.BT32 + (size_t)i * m * F.ldbt;
+    a.inv = F.inv32 + (size_t)i * m;
+    a.band = F.band32 + (size_t)i * m * 16;
+    a.mt = mt;
+    a.ldbt = F.ldbt;
+    a.Delta = has_shift ? Dl : nullptr;
+    a.ldd = C;
+    a.a = L.a32 + F.tile_off[i];
+    a.b = L.b32 + F.tile_off[i];
+    a.rs = rs32;
+    a.Q = F.Q;
+    a.D = dD;
+    a.ldD = F.n + 1;
+    a.coord0 = F.tile_off[i];
+    a.sample0 = c0;
+    a.N = N;
+    a.C = Cc;
+    a.periodize = periodize;
+    a.first = (i == 0);
+    a.Yv = nullptr;
+    a.ldyv = 0;
+    a.Ys = Ys;
+    a.ldys = ldys;
+    a.ys_lo = tcc->my;
+    a.logP = logP;
+    t.brow0 = i * m;
+    t.alo = (int)tcc->my;
+    t.blo = (int)tcc->my;
+    t.err = tcc->err;
+    const int flags = (periodize ? SWEEP_PERIODIZE : 0) | (L.one_sided ? SWEEP_ONE_SIDED : 0);
+    pf.begin(TLRMVN_KC_DIAG);
+    launch_pdl(sweep_tc_kernel(flags), dim3((unsigned)((Cc + STC_NS - 1) / STC_NS)), dim3(STC_NS),
+               sweep_tc_smem_bytes(), st, tcc->mapY32, tcc->mapB32, t);
+    pf.end();
+    return;
+  }
   const int sub = tcc ? tcc->sub : sweep_sub_simt();
   const SweepShape sh = sweep_shape(Cc, std::min(mt, sub));
   const float* Bi = F.B32 + (size_t)i * m * m;

@@ -1,0 +1,287 @@
+// The BF16-path sweep of a whole diagonal tile B_i (eq. 2 over the tile,
+// Algorithm 6's per-tile step) with the in-tile coupling on the tensor cores.
+//
+// One CTA of 128 threads owns 128 samples, one per thread and per TMEM lane.
+// The tile runs in sub-tiles of 64 variables; before sub-tile q the coupling to
+// the tile's earlier variables,
+//     T[c][v] = sum_{u < q0} B_i[q0 + v][u] y_u[c]      (v < 64, the same sums as
+// eq. 2, regrouped), is one tcgen05 product per CTA into 64 TMEM columns: A = the
+// CTA's rows of the sample-major y it stored itself (hi and lo bf16 parts), B =
+// the rows of the split copy of B_i (hi and lo), hi*hi + hi*lo + lo*hi with fp32
+// accumulation.  Each thread then runs the sub-tile's chain for its sample
+// exactly as the sub-tile sweep k_diag_f32 does, taking the coupling of each
+// 16-variable block from its own TMEM lane (tcgen05.ld) and adding the low-rank
+// limit shifts from the variable-major buffer.  So the coupling never goes
+// through global memory, one launch covers the tile, and the sample's log P is
+// closed once per tile.
+//
+// The MMA operands are staged by TMA (64-byte swizzle, one 32-deep stage of
+// 24 KB) in the same shared memory the sweep uses for its y, so a CTA needs
+// ~36 KB and six share an SM (6 x 64 TMEM columns).  (A ring of two 16-deep
+// stages in the same space measured slower: twice the copies for the same
+// bytes in flight.)  Every wait is bounded; on
+// expiry the CTA records an error code, skips the rest, waits (bounded) for
+// its copies and products in flight, frees its TMEM and returns.
+#pragma once
+#include "gemm_tc.cuh"
+#include "sweep.cuh"
+
+namespace tlrmvn {
+
+constexpr int STC_SUB = 64;   // variables per sub-tile
+constexpr int STC_NS = 128;   // samples per CTA (TMEM lanes)
+constexpr int STC_KB = 32;    // K depth of the stage
+using StcCfg = tc::Cfg<64, true, false, STC_KB, 1>;
+
+struct SweepTcArgs {
+  DiagArgs32 d;  // pointers at the tile's first variable; d.mt = tile size; d.Ys and d.ys_lo required
+  int brow0;     // row of the tile's first variable in the split-B map
+  int alo, blo;  // x offsets of the lo halves in the y and split-B maps
+  int* err;
+};
+
+// [y of the sub-tile | MMA stage (aliased)] [constants] [barriers, TMEM slot]
+__host__ __device__ constexpr size_t stc_region_bytes() {
+  return ((STC_SUB * (STC_NS + 1) * sizeof(float) > (size_t)StcCfg::NST * StcCfg::SB
+               ? STC_SUB * (STC_NS + 1) * sizeof(float)
+               : (size_t)StcCfg::NST * StcCfg::SB) +
+          1023) /
+         1024 * 1024;
+}
+__host__ __device__ constexpr size_t sweep_tc_smem_bytes() {
+  return 1024 /*align*/ + stc_region_bytes() + STC_SUB * (sizeof(float4) + sizeof(uint64_t)) + 64;
+}
+__host__ __device__ constexpr bool stc_fits() {
+  return STC_SUB * (STC_NS + 1) * sizeof(float) >= (size_t)StcCfg::NST * StcCfg::SB;
+}
+
+template <int FLAGS>
+__global__ void __launch_bounds__(STC_NS, 6)
+    k_sweep_tc(const __grid_constant__ CUtensorMap mapY, const __grid_constant__ CUtensorMap mapB, SweepTcArgs p) {
+  constexpr bool PER = FLAGS & SWEEP_PERIODIZE, ONE = FLAGS & SWEEP_ONE_SIDED;
+  constexpr int LD = STC_NS + 1;
+  constexpr uint32_t A_BYTES = StcCfg::A_BYTES, HALF = StcCfg::HALF, SB = StcCfg::SB;
+  static_assert(stc_fits(), "the stages alias the sweep's y");
+  extern __shared__ __align__(1024) unsigned char stc_smem[];
+  // (offset within the shared window, so that the accesses stay shared-memory ones)
+  unsigned char* smem = stc_smem + ((1024u - (tc::smem_u32(stc_smem) & 1023u)) & 1023u);
+  float* ys = reinterpret_cast<float*>(smem);  // sweep: ys[v * LD + tid]
+  unsigned char* stage = smem;                  // MMA phase: stage s at s * SB: [A hi][B hi][A lo][B lo]
+  float4* s_abi = reinterpret_cast<float4*>(smem + stc_region_bytes());
+  uint64_t* s_q = reinterpret_cast<uint64_t*>(s_abi + STC_SUB);
+  uint64_t* full = s_q + STC_SUB;  // the stage's copies landed
+  uint64_t* freeb = full + 1;      // the products reading the stage are done
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(freeb + 1);
+  // thread 0's barrier parities (bit 0: full, bit 1: freeb)
+  __shared__ uint32_t phases;
+  __shared__ int abort_flag;
+
+  const DiagArgs32& d = p.d;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int mt = d.mt;
+  const int c0 = blockIdx.x * STC_NS;  // (a chunk holds fewer than 2^31 samples)
+
+  if (tid == 0) {
+    abort_flag = 0;
+    phases = 0;
+    tc::mbar_init(full, 1);
+    tc::mbar_init(freeb, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(tmem_slot)),
+                 "r"(STC_SUB)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tl = *tmem_slot + ((uint32_t)(32 * warp) << 16);  // this warp's 32 lanes
+  pdl_trigger();  // (after the allocation: a successor's CTAs never hold TMEM this grid still needs)
+  pdl_wait();  // limit shifts, y and log P of the preceding kernels
+
+  const bool act = c0 + tid < d.C;
+  const int cs = act ? c0 + tid : (int)d.C - 1;  // inactive lanes shadow a valid sample, write nothing
+  const uint64_t* Ds;
+  uint32_t ks;  // lattice point index k = 1..N (N < 2^31)
+  {
+    const int64_t g = d.sample0 + cs, sh = g / d.N;
+    ks = (uint32_t)(g - sh * d.N) + 1u;
+    Ds = d.D + sh * d.ldD + d.coord0;
+  }
+  const float rs = d.rs ? d.rs[cs] : 1.0f;
+  // log P of the tile = log(prod) + pe log 2 + lsum, prod kept in [1, 2)
+  float prod = 1.0f, lsum = 0.0f;
+  int pe = 0;
+
+  for (int q0 = 0; q0 < mt; q0 += STC_SUB) {
+    const int mq = min(STC_SUB, mt - q0);
+    // every thread is past the previous sub-tile's reads of ys and the constants
+    for (int t = tid; t < mq; t += STC_NS) {
+      s_abi[t] = make_float4(d.a[q0 + t], d.b[q0 + t], d.inv[q0 + t], 0.0f);
+      s_q[t] = d.Q[d.coord0 + q0 + t];
+    }
+    if (q0 > 0 && tid == 0) {
+      // T = y[:, <q0] B_i[q0 + v, <q0]^T over 32-deep stages (x = variable, y = sample / B row)
+      const uint32_t sa = tc::smem_u32(stage);
+      const uint64_t dah = tc::sdesc<STC_KB>(sa), dbh = tc::sdesc<STC_KB>(sa + A_BYTES);
+      const uint64_t dal = tc::sdesc<STC_KB>(sa + HALF), dbl = tc::sdesc<STC_KB>(sa + HALF + A_BYTES);
+      uint32_t ph = phases;
+      int bad = 0;  // 1: copies left in flight, 2: products left in flight
+      for (int kb = 0; kb < q0 / STC_KB; kb++) {
+        const int x = kb * STC_KB;
+        tc::mbar_expect_tx(full, SB);
+        tc::tma_load_2d(stage, &mapY, full, x, c0);
+        tc::tma_load_2d(stage + A_BYTES, &mapB, full, x, p.brow0 + q0);
+        tc::tma_load_2d(stage + HALF, &mapY, full, p.alo + x, c0);
+        tc::tma_load_2d(stage + HALF + A_BYTES, &mapB, full, p.blo + x, p.brow0 + q0);
+        if (!tc::mbar_wait(full, ph & 1, p.err, 8)) {
+          bad = 1;
+          break;
+        }
+        ph ^= 1;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+        for (int kk = 0; kk < STC_KB / 16; kk++) {
+          const uint64_t o = (uint64_t)(kk * 2);  // 32 bytes per 16-deep step, in 16-byte units
+          tc::mma_bf16(*tmem_slot, dah + o, dbh + o, StcCfg::IDESC, (kb > 0 || kk > 0) ? 1u : 0u);
+          tc::mma_bf16(*tmem_slot, dah + o, dbl + o, StcCfg::IDESC, 1u);
+          tc::mma_bf16(*tmem_slot, dal + o, dbh + o, StcCfg::IDESC, 1u);
+        }
+        tc::mma_commit(freeb);
+        if (!tc::mbar_wait(freeb, (ph >> 1) & 1, p.err, 9)) {
+          bad = 2;
+          break;
+        }
+        ph ^= 2;
+      }
+      if (bad) {
+        // wait (bounded) for the copies or products still in flight
+        if (bad == 1) tc::mbar_wait(full, ph & 1, p.err, 5);
+        else tc::mbar_wait(freeb, (ph >> 1) & 1, p.err, 5);
+        abort_flag = 1;
+      }
+      phases = ph;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();  // constants staged; the coupling (q0 > 0) is in TMEM and the stage is free
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (*(volatile int*)&abort_flag) break;
+
+    for (int v0 = 0; v0 < mq; v0 += DIAG_VB) {
+      const int nb = min(DIAG_VB, mq - v0);
+      float acc[DIAG_VB], dl[DIAG_VB];
+      if (q0 > 0) {
+        uint32_t r[DIAG_VB];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+            "%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(tl + (uint32_t)v0));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < DIAG_VB; j++) dl[j] = __uint_as_float(r[j]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < DIAG_VB; j++) dl[j] = 0.0f;
+      }
+#pragma unroll
+      for (int j = 0; j < DIAG_VB; j++) {
+        // (streamed past the caches: they hold the y panels the products re-read)
+        if (d.Delta && j < nb) dl[j] += __ldcs(&d.Delta[(int64_t)(q0 + v0 + j) * d.ldd + cs]);
+        acc[j] = 0.0f;
+      }
+      uint64_t dnext = Ds[q0 + v0];
+      // sums over the sub-tile's earlier variables for the block's 16 variables
+      const float* bcol = d.BT + (int64_t)q0 * d.ldbt + q0 + v0;
+#pragma unroll 2
+      for (int u = 0; u < v0; u++) {
+        const float yu = ys[u * LD + tid];
+        const float4* b4 = reinterpret_cast<const float4*>(bcol + (int64_t)u * d.ldbt);
+        const float4 q[4] = {__ldg(b4), __ldg(b4 + 1), __ldg(b4 + 2), __ldg(b4 + 3)};
+#pragma unroll
+        for (int h = 0; h < 4; h++) {
+          acc[4 * h] = fmaf(q[h].x, yu, acc[4 * h]);
+          acc[4 * h + 1] = fmaf(q[h].y, yu, acc[4 * h + 1]);
+          acc[4 * h + 2] = fmaf(q[h].z, yu, acc[4 * h + 2]);
+          acc[4 * h + 3] = fmaf(q[h].w, yu, acc[4 * h + 3]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < DIAG_VB; j++) acc[j] += dl[j];
+#pragma unroll 1
+      for (int j = 0; j < nb; j++) {
+        const int v = v0 + j;
+        const float4 abi = s_abi[v];
+        const uint64_t qv = s_q[v];
+        const uint64_t dv = dnext;
+        dnext = Ds[q0 + ((j + 1 < nb) ? v + 1 : v)];  // next variable's offset (the last one reloads its own)
+        // window column B[v+1..v+15][v] of the band copy, in flight during the special functions
+        float bcur[DIAG_VB];
+        {
+          const float4* b4 = reinterpret_cast<const float4*>(d.band + (int64_t)(q0 + v) * 16);
+#pragma unroll
+          for (int h = 0; h < 4; h++) {
+            const float4 x = __ldg(b4 + h);
+            bcur[4 * h] = x.x;
+            bcur[4 * h + 1] = x.y;
+            bcur[4 * h + 2] = x.z;
+            bcur[4 * h + 3] = x.w;
+          }
+        }
+        const float sum = acc[0];  // shifts + coupling + earlier variables, for variable v
+        const float bt = (abi.y * rs - sum) * abi.z;
+        float w, wc, f, la, y;
+        lattice_wf((uint64_t)ks * qv + dv, PER ? 1 : 0, w, wc);
+        if (ONE) {
+          sov_step_f32_upper(bt, w, wc, f, la, y);
+        } else {
+          const float at = (abi.x * rs - sum) * abi.z;
+          sov_step_f32_prod(at, bt, w, wc, f, la, y);
+        }
+        lsum += la;
+        prod *= f;  // prod in [1, 2) and f >= Phi(-12): a normal float
+        const int pb = __float_as_int(prod);
+        pe += (pb >> 23) - 127;
+        prod = __int_as_float((pb & 0x007FFFFF) | 0x3F800000);
+        ys[v * LD + tid] = y;
+        // window shift: acc[i] <- acc[i+1] + B[v+1+i][v] y
+#pragma unroll
+        for (int i = 0; i < DIAG_VB - 1; i++) acc[i] = fmaf(bcur[i], y, acc[i + 1]);
+        acc[DIAG_VB - 1] = 0.0f;
+      }
+    }
+    // the sub-tile's y, sample-major bf16 hi and lo, for the later sub-tiles'
+    // products (read back by TMA: async proxy) and the projection
+    __syncthreads();
+    for (int j = warp; j < STC_NS; j += STC_NS / 32) {
+      if (c0 + j >= d.C) break;
+      __nv_bfloat16* row = d.Ys + (int64_t)(c0 + j) * d.ldys + q0;
+      for (int v = threadIdx.x & 31; v < mq; v += 32) {
+        const float yv = ys[v * LD + j];
+        const __nv_bfloat16 hi = __float2bfloat16_rn(yv);
+        row[v] = hi;
+        row[d.ys_lo + v] = __float2bfloat16_rn(yv - __bfloat162float(hi));
+      }
+    }
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();  // y stored and visible to the copies; ys and the TMEM columns are free
+  }
+  if (!*(volatile int*)&abort_flag && act) {
+    const double lp = (double)(logf(prod) + lsum) + (double)pe * 0.69314718055994530942;
+    const int64_t g = d.sample0 + cs;
+    if (d.first) d.logP[g] = lp;
+    else d.logP[g] += lp;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tmem_slot), "r"(STC_SUB) : "memory");
+  }
+}
+
+}  // namespace tlrmvn

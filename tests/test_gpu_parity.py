@@ -200,12 +200,13 @@ def test_config1_full_size_fp64(tl):
 
 
 @pytest.mark.parametrize("nu", [math.inf, 7.0])
-@pytest.mark.parametrize("ragged", [None, 390])
-def test_bf16_shift_path(tl, nu, ragged):
+@pytest.mark.parametrize("m,ragged,points", [(64, None, 512), (50, 390, 512), (128, 390, 301)])
+def test_bf16_shift_path(tl, nu, m, ragged, points):
     # bf16 tensor-core shifts: per-shift log-probability within 1e-2 relative,
-    # and the estimate within 3 QMC standard errors of the oracle's
-    m = 64 if ragged is None else 50
-    w = synth.small_workload(16, m, 39, nu=nu, n_shifts=8, n_points=512, ragged_n=ragged)
+    # and the estimate within 3 QMC standard errors of the oracle's.  Tiles of
+    # 128 take the whole-tile sweep (two 64-variable sub-tiles, the last tile 6
+    # variables), with 8 x 301 samples: a ragged last block of 128.
+    w = synth.small_workload(16, m, 39, nu=nu, n_shifts=8, n_points=points, ragged_n=ragged)
     OF, _ = oracle_factor(w)
     F = tl.tlrmvn_factor_import(export_bytes(OF))
     (lp, err, ps, pm), ref = run_both(tl, F, OF, w, tl.BF16_SHIFT)
@@ -214,9 +215,9 @@ def test_bf16_shift_path(tl, nu, ragged):
     assert np.all(np.isfinite(pm))
 
 
-@pytest.mark.parametrize("nu", [math.inf, 7.0])
-def test_bf16_split_coupling_without_low_rank(tl, nu):
-    # Block-diagonal covariance in tiles of 256 (two 128-variable sub-tiles each)
+@pytest.mark.parametrize("nu,n_shifts,n_points", [(math.inf, 4, 256), (7.0, 4, 256), (math.inf, 3, 301)])
+def test_bf16_split_coupling_without_low_rank(tl, nu, n_shifts, n_points):
+    # Block-diagonal covariance in tiles of 256 (four 64-variable sub-tiles each)
     # and a ragged last tile of 150: no low-rank blocks, so the BF16-shift path's
     # only reduced precision is the coupling between sub-tiles, on tensor cores
     # with split operands (x = hi + lo in bf16, relative error ~1e-5).  A
@@ -237,10 +238,10 @@ def test_bf16_split_coupling_without_low_rank(tl, nu):
     F = tl.tlrmvn_factor_dense(Sig, a, b, 256, 1e-8, 0, 0)
     assert tl.tlrmvn_factor_info(F)["k_total"] == 0
     OF = to_oracle_factor(tl.parse_export(tl.tlrmvn_factor_export(F)))
-    shifts = synth.lattice_shifts(4, n + 1, 77)
-    lp, err, ps, pm = tl.tlrmvn_prob(F, a, b, nu, tl.BF16_SHIFT, 4, 256, shifts=shifts, per_shift=True,
+    shifts = synth.lattice_shifts(n_shifts, n + 1, 77)
+    lp, err, ps, pm = tl.tlrmvn_prob(F, a, b, nu, tl.BF16_SHIFT, n_shifts, n_points, shifts=shifts, per_shift=True,
                                      per_sample=True)
-    ref = sov.solve(OF, a, b, nu, shifts, 256)
+    ref = sov.solve(OF, a, b, nu, shifts, n_points)
     assert np.all(np.abs(pm - ref["per_sample"]) <= 1e-4 * np.abs(ref["per_sample"]) + 5e-2)
     assert np.all(rel(ps, ref["per_shift"]) < 1e-3)
 

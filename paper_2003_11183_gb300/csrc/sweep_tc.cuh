@@ -5,23 +5,27 @@
 // The tile runs in sub-tiles of 64 variables; before sub-tile q the coupling to
 // the tile's earlier variables,
 //     T[c][v] = sum_{u < q0} B_i[q0 + v][u] y_u[c]      (v < 64, the same sums as
-// eq. 2, regrouped), is one tcgen05 product per CTA into 64 TMEM columns: A = the
-// CTA's rows of the sample-major y it stored itself (hi and lo bf16 parts), B =
-// the rows of the split copy of B_i (hi and lo), hi*hi + hi*lo + lo*hi with fp32
-// accumulation.  Each thread then runs the sub-tile's chain for its sample
-// exactly as the sub-tile sweep k_diag_f32 does, taking the coupling of each
-// 16-variable block from its own TMEM lane (tcgen05.ld) and adding the low-rank
-// limit shifts from the variable-major buffer.  So the coupling never goes
-// through global memory, one launch covers the tile, and the sample's log P is
-// closed once per tile.
+// eq. 2, regrouped), is one tcgen05 product per CTA into the CTA's 64 TMEM
+// columns: A = the CTA's rows of the sample-major y it stored itself (hi and lo
+// bf16 parts), B = the rows of the split copy of B_i (hi and lo),
+// hi*hi + hi*lo + lo*hi with fp32 accumulation.  Each thread then runs the
+// sub-tile's chain for its sample as the sub-tile sweep k_diag_f32 does, with
+// three differences of place: the coupling of each 16-variable block comes
+// from the thread's TMEM lane (tcgen05.ld); the y of the sub-tile go to the same
+// lane, into the columns whose coupling has been read (tcgen05.st), instead of
+// shared memory; and the sub-tile's transposed triangle and band copy are
+// staged in shared memory, in the space the MMA operands use before the sweep.
+// So the coupling never goes through global memory, the per-variable loads of B
+// are shared-memory broadcasts, one launch covers the tile, and the sample's
+// log P is closed once per tile.  After each 16-variable block its y are stored,
+// sample-major bf16 hi and lo, for the later products and the projection.
 //
 // The MMA operands are staged by TMA (64-byte swizzle, one 32-deep stage of
-// 24 KB) in the same shared memory the sweep uses for its y, so a CTA needs
-// ~36 KB and six share an SM (6 x 64 TMEM columns).  (A ring of two 16-deep
-// stages in the same space measured slower: twice the copies for the same
-// bytes in flight.)  Every wait is bounded; on
-// expiry the CTA records an error code, skips the rest, waits (bounded) for
-// its copies and products in flight, frees its TMEM and returns.
+// 24 KB), so a CTA needs ~27 KB of shared memory and 64 TMEM columns; six
+// share an SM.  (A ring of two 16-deep stages measured slower: twice the
+// copies for the same bytes in flight.)  Every wait is bounded; on expiry the
+// CTA records an error code, skips the rest, waits (bounded) for its copies and
+// products in flight, frees its TMEM and returns.
 #pragma once
 #include "gemm_tc.cuh"
 #include "sweep.cuh"
@@ -40,34 +44,26 @@ struct SweepTcArgs {
   int* err;
 };
 
-// [y of the sub-tile | MMA stage (aliased)] [constants] [barriers, TMEM slot]
-__host__ __device__ constexpr size_t stc_region_bytes() {
-  return ((STC_SUB * (STC_NS + 1) * sizeof(float) > (size_t)StcCfg::NST * StcCfg::SB
-               ? STC_SUB * (STC_NS + 1) * sizeof(float)
-               : (size_t)StcCfg::NST * StcCfg::SB) +
-          1023) /
-         1024 * 1024;
-}
+// [MMA stage | during the sweep: transposed triangle (64 x 64), band copy (64 x 16)]
+// [constants (a, b, 1/B_vv), lattice generators] [barriers, TMEM slot]
+constexpr int STC_BT_FLOATS = STC_SUB * STC_SUB, STC_BAND_FLOATS = STC_SUB * 16;
+static_assert((STC_BT_FLOATS + STC_BAND_FLOATS) * 4 <= StcCfg::SB, "the sweep's B copies fit in the stage");
 __host__ __device__ constexpr size_t sweep_tc_smem_bytes() {
-  return 1024 /*align*/ + stc_region_bytes() + STC_SUB * (sizeof(float4) + sizeof(uint64_t)) + 64;
-}
-__host__ __device__ constexpr bool stc_fits() {
-  return STC_SUB * (STC_NS + 1) * sizeof(float) >= (size_t)StcCfg::NST * StcCfg::SB;
+  return 1024 /*align*/ + (size_t)StcCfg::SB + STC_SUB * (sizeof(float4) + sizeof(uint64_t)) + 64;
 }
 
 template <int FLAGS>
 __global__ void __launch_bounds__(STC_NS, 6)
     k_sweep_tc(const __grid_constant__ CUtensorMap mapY, const __grid_constant__ CUtensorMap mapB, SweepTcArgs p) {
   constexpr bool PER = FLAGS & SWEEP_PERIODIZE, ONE = FLAGS & SWEEP_ONE_SIDED;
-  constexpr int LD = STC_NS + 1;
   constexpr uint32_t A_BYTES = StcCfg::A_BYTES, HALF = StcCfg::HALF, SB = StcCfg::SB;
-  static_assert(stc_fits(), "the stages alias the sweep's y");
   extern __shared__ __align__(1024) unsigned char stc_smem[];
   // (offset within the shared window, so that the accesses stay shared-memory ones)
   unsigned char* smem = stc_smem + ((1024u - (tc::smem_u32(stc_smem) & 1023u)) & 1023u);
-  float* ys = reinterpret_cast<float*>(smem);  // sweep: ys[v * LD + tid]
-  unsigned char* stage = smem;                  // MMA phase: stage s at s * SB: [A hi][B hi][A lo][B lo]
-  float4* s_abi = reinterpret_cast<float4*>(smem + stc_region_bytes());
+  unsigned char* stage = smem;                         // MMA phase: [A hi][B hi][A lo][B lo]
+  float* s_bt = reinterpret_cast<float*>(smem);        // sweep: s_bt[u * 64 + v] = B_i[q0 + v][q0 + u]
+  float* s_band = s_bt + STC_BT_FLOATS;                // sweep: s_band[v * 16 + k] = B_i[q0 + v + 1 + k][q0 + v]
+  float4* s_abi = reinterpret_cast<float4*>(smem + SB);
   uint64_t* s_q = reinterpret_cast<uint64_t*>(s_abi + STC_SUB);
   uint64_t* full = s_q + STC_SUB;  // the stage's copies landed
   uint64_t* freeb = full + 1;      // the products reading the stage are done
@@ -117,7 +113,7 @@ __global__ void __launch_bounds__(STC_NS, 6)
 
   for (int q0 = 0; q0 < mt; q0 += STC_SUB) {
     const int mq = min(STC_SUB, mt - q0);
-    // every thread is past the previous sub-tile's reads of ys and the constants
+    // every thread is past the previous sub-tile's reads of the shared copies and its TMEM accesses
     for (int t = tid; t < mq; t += STC_NS) {
       s_abi[t] = make_float4(d.a[q0 + t], d.b[q0 + t], d.inv[q0 + t], 0.0f);
       s_q[t] = d.Q[d.coord0 + q0 + t];
@@ -168,6 +164,18 @@ __global__ void __launch_bounds__(STC_NS, 6)
     __syncthreads();  // constants staged; the coupling (q0 > 0) is in TMEM and the stage is free
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (*(volatile int*)&abort_flag) break;
+    {
+      // the sub-tile's transposed triangle (rows u < mq, columns v < mq rounded up to 16) and band copy
+      const int w4 = ((mq + 15) & ~15) >> 2;  // float4 per row
+      for (int t = tid; t < mq * w4; t += STC_NS) {
+        const int u = t / w4, c = t - u * w4;
+        reinterpret_cast<float4*>(s_bt + u * STC_SUB)[c] =
+            __ldg(reinterpret_cast<const float4*>(d.BT + (int64_t)(q0 + u) * d.ldbt + q0) + c);
+      }
+      for (int t = tid; t < mq * 4; t += STC_NS)
+        reinterpret_cast<float4*>(s_band)[t] = __ldg(reinterpret_cast<const float4*>(d.band + (int64_t)q0 * 16) + t);
+    }
+    __syncthreads();
 
     for (int v0 = 0; v0 < mq; v0 += DIAG_VB) {
       const int nb = min(DIAG_VB, mq - v0);
@@ -194,19 +202,26 @@ __global__ void __launch_bounds__(STC_NS, 6)
         acc[j] = 0.0f;
       }
       uint64_t dnext = Ds[q0 + v0];
-      // sums over the sub-tile's earlier variables for the block's 16 variables
-      const float* bcol = d.BT + (int64_t)q0 * d.ldbt + q0 + v0;
-#pragma unroll 2
-      for (int u = 0; u < v0; u++) {
-        const float yu = ys[u * LD + tid];
-        const float4* b4 = reinterpret_cast<const float4*>(bcol + (int64_t)u * d.ldbt);
-        const float4 q[4] = {__ldg(b4), __ldg(b4 + 1), __ldg(b4 + 2), __ldg(b4 + 3)};
+      // sums over the sub-tile's earlier variables for the block's 16 variables:
+      // y_u from this lane's TMEM columns, four at a time
+      for (int u0 = 0; u0 < v0; u0 += 4) {
+        uint32_t r[4];
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                     : "r"(tl + (uint32_t)u0));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int h = 0; h < 4; h++) {
-          acc[4 * h] = fmaf(q[h].x, yu, acc[4 * h]);
-          acc[4 * h + 1] = fmaf(q[h].y, yu, acc[4 * h + 1]);
-          acc[4 * h + 2] = fmaf(q[h].z, yu, acc[4 * h + 2]);
-          acc[4 * h + 3] = fmaf(q[h].w, yu, acc[4 * h + 3]);
+        for (int uu = 0; uu < 4; uu++) {
+          const float yu = __uint_as_float(r[uu]);
+          const float4* b4 = reinterpret_cast<const float4*>(s_bt + (u0 + uu) * STC_SUB + v0);
+          const float4 q[4] = {b4[0], b4[1], b4[2], b4[3]};
+#pragma unroll
+          for (int h = 0; h < 4; h++) {
+            acc[4 * h] = fmaf(q[h].x, yu, acc[4 * h]);
+            acc[4 * h + 1] = fmaf(q[h].y, yu, acc[4 * h + 1]);
+            acc[4 * h + 2] = fmaf(q[h].z, yu, acc[4 * h + 2]);
+            acc[4 * h + 3] = fmaf(q[h].w, yu, acc[4 * h + 3]);
+          }
         }
       }
 #pragma unroll
@@ -218,19 +233,6 @@ __global__ void __launch_bounds__(STC_NS, 6)
         const uint64_t qv = s_q[v];
         const uint64_t dv = dnext;
         dnext = Ds[q0 + ((j + 1 < nb) ? v + 1 : v)];  // next variable's offset (the last one reloads its own)
-        // window column B[v+1..v+15][v] of the band copy, in flight during the special functions
-        float bcur[DIAG_VB];
-        {
-          const float4* b4 = reinterpret_cast<const float4*>(d.band + (int64_t)(q0 + v) * 16);
-#pragma unroll
-          for (int h = 0; h < 4; h++) {
-            const float4 x = __ldg(b4 + h);
-            bcur[4 * h] = x.x;
-            bcur[4 * h + 1] = x.y;
-            bcur[4 * h + 2] = x.z;
-            bcur[4 * h + 3] = x.w;
-          }
-        }
         const float sum = acc[0];  // shifts + coupling + earlier variables, for variable v
         const float bt = (abi.y * rs - sum) * abi.z;
         float w, wc, f, la, y;
@@ -246,29 +248,68 @@ __global__ void __launch_bounds__(STC_NS, 6)
         const int pb = __float_as_int(prod);
         pe += (pb >> 23) - 127;
         prod = __int_as_float((pb & 0x007FFFFF) | 0x3F800000);
-        ys[v * LD + tid] = y;
-        // window shift: acc[i] <- acc[i+1] + B[v+1+i][v] y
+        // y into this lane's column v (its coupling has been read); the store is a
+        // warp-wide one, after the step's divergent branches
+        __syncwarp();
+        asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(tl + (uint32_t)v), "r"(__float_as_uint(y))
+                     : "memory");
+        // window shift: acc[i] <- acc[i+1] + B[v+1+i][v] y, the column from the band copy
+        const float4* b4 = reinterpret_cast<const float4*>(s_band + v * 16);
+        const float4 q[4] = {b4[0], b4[1], b4[2], b4[3]};
+        const float bcur[DIAG_VB] = {q[0].x, q[0].y, q[0].z, q[0].w, q[1].x, q[1].y, q[1].z, q[1].w,
+                                     q[2].x, q[2].y, q[2].z, q[2].w, q[3].x, q[3].y, q[3].z, q[3].w};
 #pragma unroll
         for (int i = 0; i < DIAG_VB - 1; i++) acc[i] = fmaf(bcur[i], y, acc[i + 1]);
         acc[DIAG_VB - 1] = 0.0f;
       }
-    }
-    // the sub-tile's y, sample-major bf16 hi and lo, for the later sub-tiles'
-    // products (read back by TMA: async proxy) and the projection
-    __syncthreads();
-    for (int j = warp; j < STC_NS; j += STC_NS / 32) {
-      if (c0 + j >= d.C) break;
-      __nv_bfloat16* row = d.Ys + (int64_t)(c0 + j) * d.ldys + q0;
-      for (int v = threadIdx.x & 31; v < mq; v += 32) {
-        const float yv = ys[v * LD + j];
-        const __nv_bfloat16 hi = __float2bfloat16_rn(yv);
-        row[v] = hi;
-        row[d.ys_lo + v] = __float2bfloat16_rn(yv - __bfloat162float(hi));
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      // the block's y, sample-major bf16 hi and lo (32 bytes each per sample), for
+      // the later sub-tiles' products (read back by TMA: async proxy) and the projection
+      {
+        uint32_t r[DIAG_VB];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+            "%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(tl + (uint32_t)v0));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (act) {
+          __nv_bfloat16* row = d.Ys + (int64_t)cs * d.ldys + q0 + v0;
+          uint32_t hi2[DIAG_VB / 2], lo2[DIAG_VB / 2];
+#pragma unroll
+          for (int j = 0; j < DIAG_VB; j += 2) {
+            const float y0 = __uint_as_float(r[j]), y1 = __uint_as_float(r[j + 1]);
+            const __nv_bfloat162 h = __floats2bfloat162_rn(y0, y1);
+            const __nv_bfloat162 l = __floats2bfloat162_rn(y0 - __low2float(h), y1 - __high2float(h));
+            hi2[j / 2] = *reinterpret_cast<const uint32_t*>(&h);
+            lo2[j / 2] = *reinterpret_cast<const uint32_t*>(&l);
+          }
+          if (nb == DIAG_VB) {
+            uint4* dh = reinterpret_cast<uint4*>(row);
+            uint4* dlo = reinterpret_cast<uint4*>(row + d.ys_lo);
+            dh[0] = make_uint4(hi2[0], hi2[1], hi2[2], hi2[3]);
+            dh[1] = make_uint4(hi2[4], hi2[5], hi2[6], hi2[7]);
+            dlo[0] = make_uint4(lo2[0], lo2[1], lo2[2], lo2[3]);
+            dlo[1] = make_uint4(lo2[4], lo2[5], lo2[6], lo2[7]);
+          } else {
+            unsigned short* rh = reinterpret_cast<unsigned short*>(row);
+            unsigned short* rl = reinterpret_cast<unsigned short*>(row + d.ys_lo);
+#pragma unroll
+            for (int j = 0; j < DIAG_VB; j++)
+              if (j < nb) {
+                rh[j] = (unsigned short)(hi2[j / 2] >> (16 * (j & 1)));
+                rl[j] = (unsigned short)(lo2[j / 2] >> (16 * (j & 1)));
+              }
+          }
+        }
       }
     }
-    asm volatile("fence.proxy.async.global;" ::: "memory");
+    // y stored and visible to the copies (global), the shared copies free for the next copies into the stage
+    // (shared), the TMEM columns free for the next products
+    asm volatile("fence.proxy.async;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();  // y stored and visible to the copies; ys and the TMEM columns are free
+    __syncthreads();
   }
   if (!*(volatile int*)&abort_flag && act) {
     const double lp = (double)(logf(prod) + lsum) + (double)pe * 0.69314718055994530942;

@@ -146,7 +146,11 @@ int tlrmvn_factor_free(tlrmvn_factor_t f);
  *               standard error of logp to first order; NaN when n_shifts == 1
  *   per_shift   host, length n_shifts or NULL: log of each shift's lattice mean
  *   per_sample  host, length n_shifts * n_points or NULL: log integrand of every
- *               sample, shift-major (sample s*N + k-1 is point k of shift s) */
+ *               sample, shift-major (sample s*N + k-1 is point k of shift s)
+ * Device scratch (tlrmvn_prob_scratch_bytes) comes from the device's default
+ * memory pool, whose release threshold the first call raises to the maximum,
+ * so that the next call reuses it without mapping it again; the application
+ * returns it to the driver with cudaMemPoolTrimTo on that pool. */
 int tlrmvn_prob(tlrmvn_factor_t f, const double* a, const double* b, double nu, const tlrmvn_opts* opts,
                 double* logp, double* err, double* per_shift, double* per_sample);
 

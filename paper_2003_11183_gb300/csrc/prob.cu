@@ -21,6 +21,8 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
+#include <vector>
 
 namespace tlrmvn {
 
@@ -428,11 +430,33 @@ uint64_t splitmix64_seed_at(uint64_t seed, uint64_t t) {
   return z ^ (z >> 31);
 }
 
-// Scratch of one call, freed on every exit path.
+// Freed scratch stays in the device's default memory pool between calls: a
+// solve's scratch is several GB (the projections of all samples), and handing it
+// back to the driver at every synchronisation, to map it again in the next call,
+// cost more than 10% of a solve.
+static void keep_pool_memory(int dev) {
+  static std::mutex mu;
+  static std::vector<int> done;
+  std::lock_guard<std::mutex> g(mu);
+  if (std::find(done.begin(), done.end(), dev) != done.end()) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  cudaGetLastError();
+  done.push_back(dev);
+}
+
+// Scratch of one call, freed on every exit path (into the pool kept by keep_pool_memory).
 struct Scratch {
   std::vector<void*> ptrs;
   cudaStream_t st;
-  explicit Scratch(cudaStream_t s) : st(s) {}
+  explicit Scratch(cudaStream_t s) : st(s) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    keep_pool_memory(dev);
+  }
   template <typename T>
   int get(T** p, size_t count) {
     *p = nullptr;

@@ -33,14 +33,14 @@ def rel(a, b):
     return np.abs(np.asarray(a) - np.asarray(b)) / np.maximum(np.abs(np.asarray(b)), 1e-300)
 
 
-def run_both(tl, F_lib, OF, w, precision, nu=None, samples=None):
+def run_both(tl, F_lib, OF, w, precision, nu=None, samples=None, periodize=True):
     nu = w.nu if nu is None else nu
     lp, err, ps, pm = tl.tlrmvn_prob(F_lib, w.a, w.b, nu, precision, w.n_shifts, w.n_points, shifts=w.shifts,
-                                     per_shift=True, per_sample=True)
+                                     per_shift=True, per_sample=True, periodize=periodize)
     if samples is None:
-        ref = sov.solve(OF, w.a, w.b, nu, w.shifts, w.n_points)
+        ref = sov.solve(OF, w.a, w.b, nu, w.shifts, w.n_points, periodize)
     else:
-        ref = sov.solve(OF, w.a, w.b, nu, w.shifts, w.n_points, samples=samples)
+        ref = sov.solve(OF, w.a, w.b, nu, w.shifts, w.n_points, periodize, samples=samples)
     return (lp, err, ps, pm), ref
 
 
@@ -67,8 +67,10 @@ def test_fp32_on_imported_oracle_factor(tl, nu):
     assert np.all(np.abs(pm - ref["per_sample"]) <= 1e-4 * np.abs(ref["per_sample"]) + 1e-3)
 
 
-def test_two_sided_and_upper_tail_limits(tl):
-    w = synth.small_workload(12, 48, 33, n_shifts=3, n_points=128, limits="twosided")
+@pytest.mark.parametrize("m", [48, 128])
+def test_two_sided_and_upper_tail_limits(tl, m):
+    # tiles of 128 put the BF16 path on the whole-tile sweep's two-sided variant
+    w = synth.small_workload(12, m, 33, n_shifts=3, n_points=128, limits="twosided")
     w.a[::7] = 1.5
     w.b[::7] = np.inf       # upper-tail one-sided intervals
     OF, _ = oracle_factor(w)
@@ -77,13 +79,18 @@ def test_two_sided_and_upper_tail_limits(tl):
     assert np.all(rel(pm, ref["per_sample"]) < 1e-9)
     (lp, err, ps, pm), ref = run_both(tl, F, OF, w, tl.FP32)
     assert np.all(rel(ps, ref["per_shift"]) < 1e-4)
+    (lp, err, ps, pm), ref = run_both(tl, F, OF, w, tl.BF16_SHIFT)
+    assert np.all(rel(ps, ref["per_shift"]) < 1e-2)
+    assert np.all(np.isfinite(pm))
 
 
-def test_deep_tail_limits(tl):
+@pytest.mark.parametrize("m", [48, 128])
+def test_deep_tail_limits(tl, m):
     # limits whose interval probabilities lie below the float64 range: one-sided
     # lower tails, two-sided intervals in either half, upper tails.  Every
-    # per-sample value is finite and FP64 equals the oracle to 1e-9.
-    w = synth.small_workload(12, 48, 34, n_shifts=2, n_points=128, limits="twosided")
+    # per-sample value is finite and FP64 equals the oracle to 1e-9.  Tiles of
+    # 128 take the BF16 path through the whole-tile sweep's log-domain code.
+    w = synth.small_workload(12, m, 34, n_shifts=2, n_points=128, limits="twosided")
     w.a[:] = -np.inf
     w.b[:] = np.random.default_rng(5).uniform(0.0, 1.0, w.n)
     w.b[0::5] = -45.0
@@ -98,6 +105,27 @@ def test_deep_tail_limits(tl):
     (lp, err, ps, pm), ref = run_both(tl, F, OF, w, tl.FP32)
     assert np.all(np.isfinite(pm))
     assert np.all(rel(ps, ref["per_shift"]) < 1e-4)
+    (lp, err, ps, pm), ref = run_both(tl, F, OF, w, tl.BF16_SHIFT)
+    assert np.all(np.isfinite(pm))
+    assert np.all(rel(ps, ref["per_shift"]) < 1e-2)
+
+
+@pytest.mark.parametrize("nu", [math.inf, 7.0])
+def test_without_periodisation(tl, nu):
+    # the lattice used as is (no tent map; the paper does not say which, the
+    # library defaults to the tent map and offers both): every
+    # precision against the oracle run the same way; tiles of 128 and a ragged
+    # sample count (4 x 257) on the BF16 path's whole-tile sweep
+    w = synth.small_workload(16, 128, 40, nu=nu, n_shifts=4, n_points=257)
+    OF, _ = oracle_factor(w)
+    F = tl.tlrmvn_factor_import(export_bytes(OF))
+    (lp, err, ps, pm), ref = run_both(tl, F, OF, w, tl.FP64, periodize=False)
+    assert np.all(rel(pm, ref["per_sample"]) < 1e-9)
+    (lp, err, ps, pm), ref = run_both(tl, F, OF, w, tl.FP32, periodize=False)
+    assert np.all(rel(ps, ref["per_shift"]) < 1e-4)
+    (lp, err, ps, pm), ref = run_both(tl, F, OF, w, tl.BF16_SHIFT, periodize=False)
+    assert np.all(rel(ps, ref["per_shift"]) < 1e-2)
+    assert abs(lp - ref["logp"]) <= 3 * max(err, ref["err"])
 
 
 def test_gpu_factor_matches_oracle_factor(tl):

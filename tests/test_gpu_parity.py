@@ -342,3 +342,23 @@ def test_float_phi_lower_tail_error_bound(tl):
     inside = x <= 12.0
     assert np.max(np.abs(got[inside] / want[inside] - 1.0)) < 1e-6
     assert np.all(got[~inside] >= 0) and np.all(got[~inside] < 1e-33)
+
+
+@pytest.mark.parametrize("precision", ["FP64", "FP32", "BF16_SHIFT"])
+def test_sample_chunks_change_nothing(tl, precision):
+    # a solve in chunks of 768 samples (3 full chunks and a ragged one of 4 x 250
+    # samples) gives every sample bit for bit the value of the one-chunk solve:
+    # no step mixes samples, and the chunk offset enters only the lattice index
+    # (tiles of 128: the BF16 path runs the whole-tile sweep)
+    w = synth.small_workload(16, 128, 41, nu=7.0, n_shifts=4, n_points=750)
+    OF, _ = oracle_factor(w)
+    F = tl.tlrmvn_factor_import(export_bytes(OF))
+    prec = getattr(tl, precision)
+    kw = dict(shifts=w.shifts, per_shift=True, per_sample=True)
+    full = tl.tlrmvn_prob(F, w.a, w.b, w.nu, prec, w.n_shifts, w.n_points, **kw)
+    part = tl.tlrmvn_prob(F, w.a, w.b, w.nu, prec, w.n_shifts, w.n_points, sample_chunk=768, **kw)
+    assert np.array_equal(full[3], part[3])
+    assert np.array_equal(full[2], part[2])
+    ref = sov.solve(OF, w.a, w.b, w.nu, w.shifts, w.n_points)
+    tol = {"FP64": 1e-9, "FP32": 1e-4, "BF16_SHIFT": 1e-2}[precision]
+    assert np.all(rel(part[2], ref["per_shift"]) < tol)

@@ -573,7 +573,7 @@ static SweepShape sweep_shape(int64_t C, int mt) {
 // The whole-tile sweep with tensor-core coupling (BF16-shift path), by
 // (periodisation, one-sided) flags; TLRMVN_FUSED=0 selects, for tuning runs,
 // sub-tile sweeps with separate coupling products instead.
-typedef void (*SweepTcKernel)(const CUtensorMap, const CUtensorMap, SweepTcArgs);
+typedef void (*SweepTcKernel)(const CUtensorMap, const CUtensorMap, const CUtensorMap, const CUtensorMap, SweepTcArgs);
 static SweepTcKernel sweep_tc_kernel(int flags) {
   static const SweepTcKernel table[4] = {k_sweep_tc<0>, k_sweep_tc<SWEEP_PERIODIZE>, k_sweep_tc<SWEEP_ONE_SIDED>,
                                          k_sweep_tc<SWEEP_PERIODIZE | SWEEP_ONE_SIDED>};
@@ -605,6 +605,7 @@ static int set_sweep_smem(int m, int sub) {
 struct TcCouple {
   CUtensorMap mapB, mapY;      // 64-deep boxes (128-byte swizzle)
   CUtensorMap mapB32, mapY32;  // 32-deep boxes (64-byte swizzle)
+  CUtensorMap mapW{}, mapU64{};  // the whole-tile sweep's low-rank shift operands (64 x 64 boxes)
   int64_t my;
   int sub;  // sub-tile size, a multiple of 64
   int* err;
@@ -645,7 +646,7 @@ static void sweep_tile_f32(const Factor& F, int i, bool has_shift, float* Dl, in
     a.band = F.band32 + (size_t)i * m * 16;
     a.mt = mt;
     a.ldbt = F.ldbt;
-    a.Delta = has_shift ? Dl : nullptr;
+    a.Delta = nullptr;  // (the shifts are products of the kernel)
     a.ldd = C;
     a.a = L.a32 + F.tile_off[i];
     a.b = L.b32 + F.tile_off[i];
@@ -668,11 +669,14 @@ static void sweep_tile_f32(const Factor& F, int i, bool has_shift, float* Dl, in
     t.brow0 = i * m;
     t.alo = (int)tcc->my;
     t.blo = (int)tcc->my;
+    t.urow0 = i * m;
+    t.krow0 = (int)F.kpad_off[i];
+    t.kr = (int)F.krow(i);
     t.err = tcc->err;
     const int flags = (periodize ? SWEEP_PERIODIZE : 0) | (L.one_sided ? SWEEP_ONE_SIDED : 0);
     pf.begin(TLRMVN_KC_DIAG);
     launch_pdl(sweep_tc_kernel(flags), dim3((unsigned)((Cc + STC_NS - 1) / STC_NS)), dim3(STC_NS),
-               sweep_tc_smem_bytes(), st, tcc->mapY32, tcc->mapB32, t);
+               sweep_tc_smem_bytes(), st, tcc->mapY32, tcc->mapB32, tcc->mapW, tcc->mapU64, t);
     pf.end();
     return;
   }
@@ -879,6 +883,8 @@ static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opt
     TLR_CHECK(make_map(&tcc.mapB32, F.B16x2, ly, (uint64_t)F.r * m, ly * 2, (uint32_t)tcc.sub, 32));
     TLR_CHECK(make_map(&tcc.mapY32, Y, ly, C, ly * 2, tc::BM, 32));
     tcc.mapY = mapY;
+    tcc.mapW = mapW;
+    if (F.ktot) TLR_CHECK(make_map(&tcc.mapU64, F.U16, F.kmax16, (uint64_t)F.r * m, F.kmax16 * 2, 64));
     tcc.my = F.my16;
     tcc.err = err;
   }
@@ -896,6 +902,8 @@ static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opt
 
   TLR_CHECK(set_sweep_smem(m, sweep_sub_tc()));
 
+  // the whole-tile sweep (tiles of more than one 64-variable sub-tile) computes the low-rank shifts itself
+  const bool fused = F.B16x2 && tcc.sub == STC_SUB && sweep_fused();
   for (int64_t c0 = 0; c0 < S; c0 += C) {
     const int64_t Cc = std::min(C, S - c0);
     if (mvt) {
@@ -909,7 +917,7 @@ static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opt
       const int mt = (int)F.tsize(i);
       const int64_t Kr = F.krow(i), Kc = F.kcol(i);
       const float* Delta = nullptr;
-      if (Kr > 0) {
+      if (Kr > 0 && !fused) {
         tc::GemmTcArgs g{(int)Cc, mt, (int)Kr, (int)F.kpad_off[i], 0, 0, i * m, Dl, C, nullptr, 0, nullptr, err};
         pf.begin(TLRMVN_KC_SHIFT);
         if (gemm_narrow())  // N = 128, one stage: four CTAs per SM (TMEM 4 x 128 columns)

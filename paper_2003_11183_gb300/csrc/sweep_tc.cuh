@@ -39,10 +39,15 @@ using StcCfg = tc::Cfg<64, true, false, STC_KB, 1>;
 
 struct SweepTcArgs {
   DiagArgs32 d;  // pointers at the tile's first variable; d.mt = tile size; d.Ys and d.ys_lo required
+                 // (d.Delta unused: the low-rank shifts are products of this kernel)
   int brow0;     // row of the tile's first variable in the split-B map
   int alo, blo;  // x offsets of the lo halves in the y and split-B maps
+  int urow0;     // row of the tile's first variable in the U map
+  int krow0, kr; // the tile's rank rows in the W map (first, count; 0: no low-rank shift)
   int* err;
 };
+using StcShiftCfg = tc::Cfg<64, false, true, 64, 1>;  // shift k-block: W (MN-major) x U rows, 64 deep
+static_assert(StcShiftCfg::SB == StcCfg::SB, "a shift k-block fills the same stage");
 
 // [MMA stage | during the sweep: transposed triangle (64 x 64), band copy (64 x 16)]
 // [constants (a, b, 1/B_vv), lattice generators] [barriers, TMEM slot]
@@ -54,7 +59,8 @@ __host__ __device__ constexpr size_t sweep_tc_smem_bytes() {
 
 template <int FLAGS>
 __global__ void __launch_bounds__(STC_NS, 6)
-    k_sweep_tc(const __grid_constant__ CUtensorMap mapY, const __grid_constant__ CUtensorMap mapB, SweepTcArgs p) {
+    k_sweep_tc(const __grid_constant__ CUtensorMap mapY, const __grid_constant__ CUtensorMap mapB,
+               const __grid_constant__ CUtensorMap mapW, const __grid_constant__ CUtensorMap mapU, SweepTcArgs p) {
   constexpr bool PER = FLAGS & SWEEP_PERIODIZE, ONE = FLAGS & SWEEP_ONE_SIDED;
   constexpr uint32_t A_BYTES = StcCfg::A_BYTES, HALF = StcCfg::HALF, SB = StcCfg::SB;
   extern __shared__ __align__(1024) unsigned char stc_smem[];
@@ -118,32 +124,51 @@ __global__ void __launch_bounds__(STC_NS, 6)
       s_abi[t] = make_float4(d.a[q0 + t], d.b[q0 + t], d.inv[q0 + t], 0.0f);
       s_q[t] = d.Q[d.coord0 + q0 + t];
     }
-    if (q0 > 0 && tid == 0) {
-      // T = y[:, <q0] B_i[q0 + v, <q0]^T over 32-deep stages (x = variable, y = sample / B row)
+    if ((q0 > 0 || p.kr > 0) && tid == 0) {
+      // T = W[ranks of row tile i, samples]^T U_i[q0 + v, ranks]^T     (the low-rank shifts,
+      //     64-deep stages: two 64-sample MN-major boxes of W, one box of U rows)
+      //   + y[:, <q0] B_i[q0 + v, <q0]^T                              (the coupling, 32-deep split stages)
       const uint32_t sa = tc::smem_u32(stage);
       const uint64_t dah = tc::sdesc<STC_KB>(sa), dbh = tc::sdesc<STC_KB>(sa + A_BYTES);
       const uint64_t dal = tc::sdesc<STC_KB>(sa + HALF), dbl = tc::sdesc<STC_KB>(sa + HALF + A_BYTES);
+      const uint64_t dw = tc::sdesc_mn(sa), du = tc::sdesc<64>(sa + StcShiftCfg::A_BYTES);
+      const int nks = (p.kr + 63) / 64, nk = nks + q0 / STC_KB;
       uint32_t ph = phases;
       int bad = 0;  // 1: copies left in flight, 2: products left in flight
-      for (int kb = 0; kb < q0 / STC_KB; kb++) {
-        const int x = kb * STC_KB;
+      for (int kb = 0; kb < nk; kb++) {
         tc::mbar_expect_tx(full, SB);
-        tc::tma_load_2d(stage, &mapY, full, x, c0);
-        tc::tma_load_2d(stage + A_BYTES, &mapB, full, x, p.brow0 + q0);
-        tc::tma_load_2d(stage + HALF, &mapY, full, p.alo + x, c0);
-        tc::tma_load_2d(stage + HALF + A_BYTES, &mapB, full, p.blo + x, p.brow0 + q0);
+        if (kb < nks) {
+          const int y = p.krow0 + kb * 64;
+          tc::tma_load_2d(stage, &mapW, full, c0, y);
+          tc::tma_load_2d(stage + StcShiftCfg::A_BYTES / 2, &mapW, full, c0 + 64, y);
+          tc::tma_load_2d(stage + StcShiftCfg::A_BYTES, &mapU, full, kb * 64, p.urow0 + q0);
+        } else {
+          const int x = (kb - nks) * STC_KB;
+          tc::tma_load_2d(stage, &mapY, full, x, c0);
+          tc::tma_load_2d(stage + A_BYTES, &mapB, full, x, p.brow0 + q0);
+          tc::tma_load_2d(stage + HALF, &mapY, full, p.alo + x, c0);
+          tc::tma_load_2d(stage + HALF + A_BYTES, &mapB, full, p.blo + x, p.brow0 + q0);
+        }
         if (!tc::mbar_wait(full, ph & 1, p.err, 8)) {
           bad = 1;
           break;
         }
         ph ^= 1;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (kb < nks) {
+          // per 16-deep step: MN-major W two 1 KB K groups on (+128), U rows 32 bytes on (+2)
 #pragma unroll
-        for (int kk = 0; kk < STC_KB / 16; kk++) {
-          const uint64_t o = (uint64_t)(kk * 2);  // 32 bytes per 16-deep step, in 16-byte units
-          tc::mma_bf16(*tmem_slot, dah + o, dbh + o, StcCfg::IDESC, (kb > 0 || kk > 0) ? 1u : 0u);
-          tc::mma_bf16(*tmem_slot, dah + o, dbl + o, StcCfg::IDESC, 1u);
-          tc::mma_bf16(*tmem_slot, dal + o, dbh + o, StcCfg::IDESC, 1u);
+          for (int kk = 0; kk < 4; kk++)
+            tc::mma_bf16(*tmem_slot, dw + (uint64_t)(128 * kk), du + (uint64_t)(2 * kk), StcShiftCfg::IDESC,
+                         (kb > 0 || kk > 0) ? 1u : 0u);
+        } else {
+#pragma unroll
+          for (int kk = 0; kk < STC_KB / 16; kk++) {
+            const uint64_t o = (uint64_t)(kk * 2);  // 32 bytes per 16-deep step, in 16-byte units
+            tc::mma_bf16(*tmem_slot, dah + o, dbh + o, StcCfg::IDESC, (kb > 0 || kk > 0) ? 1u : 0u);
+            tc::mma_bf16(*tmem_slot, dah + o, dbl + o, StcCfg::IDESC, 1u);
+            tc::mma_bf16(*tmem_slot, dal + o, dbh + o, StcCfg::IDESC, 1u);
+          }
         }
         tc::mma_commit(freeb);
         if (!tc::mbar_wait(freeb, (ph >> 1) & 1, p.err, 9)) {
@@ -161,7 +186,7 @@ __global__ void __launch_bounds__(STC_NS, 6)
       phases = ph;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();  // constants staged; the coupling (q0 > 0) is in TMEM and the stage is free
+    __syncthreads();  // constants staged; shifts and coupling are in TMEM and the stage is free
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (*(volatile int*)&abort_flag) break;
     {
@@ -180,7 +205,7 @@ __global__ void __launch_bounds__(STC_NS, 6)
     for (int v0 = 0; v0 < mq; v0 += DIAG_VB) {
       const int nb = min(DIAG_VB, mq - v0);
       float acc[DIAG_VB], dl[DIAG_VB];
-      if (q0 > 0) {
+      if (q0 > 0 || p.kr > 0) {
         uint32_t r[DIAG_VB];
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
@@ -196,11 +221,7 @@ __global__ void __launch_bounds__(STC_NS, 6)
         for (int j = 0; j < DIAG_VB; j++) dl[j] = 0.0f;
       }
 #pragma unroll
-      for (int j = 0; j < DIAG_VB; j++) {
-        // (streamed past the caches: they hold the y panels the products re-read)
-        if (d.Delta && j < nb) dl[j] += __ldcs(&d.Delta[(int64_t)(q0 + v0 + j) * d.ldd + cs]);
-        acc[j] = 0.0f;
-      }
+      for (int j = 0; j < DIAG_VB; j++) acc[j] = 0.0f;
       uint64_t dnext = Ds[q0 + v0];
       // sums over the sub-tile's earlier variables for the block's 16 variables:
       // y_u from this lane's TMEM columns, four at a time

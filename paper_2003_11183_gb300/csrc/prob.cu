@@ -573,7 +573,8 @@ static SweepShape sweep_shape(int64_t C, int mt) {
 // The whole-tile sweep with tensor-core coupling (BF16-shift path), by
 // (periodisation, one-sided) flags; TLRMVN_FUSED=0 selects, for tuning runs,
 // sub-tile sweeps with separate coupling products instead.
-typedef void (*SweepTcKernel)(const CUtensorMap, const CUtensorMap, const CUtensorMap, const CUtensorMap, SweepTcArgs);
+typedef void (*SweepTcKernel)(const CUtensorMap, const CUtensorMap, const CUtensorMap, const CUtensorMap,
+                              const CUtensorMap, const CUtensorMap, SweepTcArgs);
 static SweepTcKernel sweep_tc_kernel(int flags) {
   static const SweepTcKernel table[4] = {k_sweep_tc<0>, k_sweep_tc<SWEEP_PERIODIZE>, k_sweep_tc<SWEEP_ONE_SIDED>,
                                          k_sweep_tc<SWEEP_PERIODIZE | SWEEP_ONE_SIDED>};
@@ -606,6 +607,9 @@ struct TcCouple {
   CUtensorMap mapB, mapY;      // 64-deep boxes (128-byte swizzle)
   CUtensorMap mapB32, mapY32;  // 32-deep boxes (64-byte swizzle)
   CUtensorMap mapW{}, mapU64{};  // the whole-tile sweep's low-rank shift operands (64 x 64 boxes)
+  CUtensorMap mapV64{};          // and its projection operand (V rows, 64 x 64 boxes)
+  __nv_bfloat16* W = nullptr;    // the projections (rank-major) and their leading dimension
+  int64_t ldw = 0;
   int64_t my;
   int sub;  // sub-tile size, a multiple of 64
   int* err;
@@ -672,11 +676,16 @@ static void sweep_tile_f32(const Factor& F, int i, bool has_shift, float* Dl, in
     t.urow0 = i * m;
     t.krow0 = (int)F.kpad_off[i];
     t.kr = (int)F.krow(i);
+    t.kcol0 = (int)F.kcol_off[i];
+    t.kc = (int)F.kcol(i);
+    t.W = tcc->W;
+    t.ldw = tcc->ldw;
+    t.vmap = F.vmap16 + F.kcol_off[i];
     t.err = tcc->err;
     const int flags = (periodize ? SWEEP_PERIODIZE : 0) | (L.one_sided ? SWEEP_ONE_SIDED : 0);
     pf.begin(TLRMVN_KC_DIAG);
     launch_pdl(sweep_tc_kernel(flags), dim3((unsigned)((Cc + STC_NS - 1) / STC_NS)), dim3(STC_NS),
-               sweep_tc_smem_bytes(), st, tcc->mapY32, tcc->mapB32, tcc->mapW, tcc->mapU64, t);
+               sweep_tc_smem_bytes(), st, tcc->mapY32, tcc->mapB32, tcc->mapW, tcc->mapU64, tcc->mapY, tcc->mapV64, t);
     pf.end();
     return;
   }
@@ -884,7 +893,12 @@ static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opt
     TLR_CHECK(make_map(&tcc.mapY32, Y, ly, C, ly * 2, tc::BM, 32));
     tcc.mapY = mapY;
     tcc.mapW = mapW;
-    if (F.ktot) TLR_CHECK(make_map(&tcc.mapU64, F.U16, F.kmax16, (uint64_t)F.r * m, F.kmax16 * 2, 64));
+    if (F.ktot) {
+      TLR_CHECK(make_map(&tcc.mapU64, F.U16, F.kmax16, (uint64_t)F.r * m, F.kmax16 * 2, 64));
+      tcc.mapV64 = mapV64;
+    }
+    tcc.W = W;
+    tcc.ldw = ldw;
     tcc.my = F.my16;
     tcc.err = err;
   }
@@ -902,7 +916,8 @@ static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opt
 
   TLR_CHECK(set_sweep_smem(m, sweep_sub_tc()));
 
-  // the whole-tile sweep (tiles of more than one 64-variable sub-tile) computes the low-rank shifts itself
+  // the whole-tile sweep (tiles of more than one 64-variable sub-tile) computes the low-rank shifts and
+  // the projections itself
   const bool fused = F.B16x2 && tcc.sub == STC_SUB && sweep_fused();
   for (int64_t c0 = 0; c0 < S; c0 += C) {
     const int64_t Cc = std::min(C, S - c0);
@@ -932,7 +947,7 @@ static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opt
       }
       sweep_tile_f32(F, i, Delta != nullptr, Dl, C, L, rs32, dD, c0, N, Cc, o.periodize, nullptr, Y, ly, logP, st, pf,
                      F.B16x2 ? &tcc : nullptr);
-      if (Kc > 0) {
+      if (Kc > 0 && !fused) {
         // transposed: rows = samples (A = y), columns = the column tile's ranks
         tc::GemmTcArgs g{(int)Cc, (int)Kc, mt, 0, 0, 0, (int)F.kcol_off[i], nullptr, 0, W, ldw,
                          F.vmap16 + F.kcol_off[i], err};

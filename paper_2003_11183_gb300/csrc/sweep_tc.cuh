@@ -44,8 +44,14 @@ struct SweepTcArgs {
   int alo, blo;  // x offsets of the lo halves in the y and split-B maps
   int urow0;     // row of the tile's first variable in the U map
   int krow0, kr; // the tile's rank rows in the W map (first, count; 0: no low-rank shift)
+  int kcol0, kc; // the tile's column ranks: first row in the V map, count (0: no projection)
+  __nv_bfloat16* W;       // projections, rank-major: W[vmap[r] * ldw + sample]
+  int64_t ldw;
+  const int32_t* vmap;    // at the tile's first column rank
   int* err;
 };
+using StcProjCfg = tc::Cfg<64, false, false, 64, 1>;  // projection k-block: y rows x V rows, 64 deep
+static_assert(StcProjCfg::SB == StcCfg::SB, "a projection k-block fills the same stage");
 using StcShiftCfg = tc::Cfg<64, false, true, 64, 1>;  // shift k-block: W (MN-major) x U rows, 64 deep
 static_assert(StcShiftCfg::SB == StcCfg::SB, "a shift k-block fills the same stage");
 
@@ -60,7 +66,8 @@ __host__ __device__ constexpr size_t sweep_tc_smem_bytes() {
 template <int FLAGS>
 __global__ void __launch_bounds__(STC_NS, 6)
     k_sweep_tc(const __grid_constant__ CUtensorMap mapY, const __grid_constant__ CUtensorMap mapB,
-               const __grid_constant__ CUtensorMap mapW, const __grid_constant__ CUtensorMap mapU, SweepTcArgs p) {
+               const __grid_constant__ CUtensorMap mapW, const __grid_constant__ CUtensorMap mapU,
+               const __grid_constant__ CUtensorMap mapY64, const __grid_constant__ CUtensorMap mapV, SweepTcArgs p) {
   constexpr bool PER = FLAGS & SWEEP_PERIODIZE, ONE = FLAGS & SWEEP_ONE_SIDED;
   constexpr uint32_t A_BYTES = StcCfg::A_BYTES, HALF = StcCfg::HALF, SB = StcCfg::SB;
   extern __shared__ __align__(1024) unsigned char stc_smem[];
@@ -331,6 +338,67 @@ __global__ void __launch_bounds__(STC_NS, 6)
     asm volatile("fence.proxy.async;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
+  }
+  // the tile's projections for the later tiles, 64 ranks a pass through the same
+  // TMEM columns: W[vmap[r]][c] = sum_v V[kcol0 + r][v] y_v[c] (y hi parts, 64-deep
+  // stages of the CTA's y rows and of V rows)
+  for (int r0 = 0; r0 < p.kc && !*(volatile int*)&abort_flag; r0 += 64) {
+    if (tid == 0) {
+      const uint32_t sa = tc::smem_u32(stage);
+      const uint64_t da = tc::sdesc<64>(sa), db = tc::sdesc<64>(sa + StcProjCfg::A_BYTES);
+      uint32_t ph = phases;
+      int bad = 0;
+      for (int kb = 0; kb < (mt + 63) / 64; kb++) {
+        tc::mbar_expect_tx(full, SB);
+        tc::tma_load_2d(stage, &mapY64, full, kb * 64, c0);
+        tc::tma_load_2d(stage + StcProjCfg::A_BYTES, &mapV, full, kb * 64, p.kcol0 + r0);
+        if (!tc::mbar_wait(full, ph & 1, p.err, 8)) {
+          bad = 1;
+          break;
+        }
+        ph ^= 1;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+        for (int kk = 0; kk < 4; kk++)
+          tc::mma_bf16(*tmem_slot, da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), StcProjCfg::IDESC,
+                       (kb > 0 || kk > 0) ? 1u : 0u);
+        tc::mma_commit(freeb);
+        if (!tc::mbar_wait(freeb, (ph >> 1) & 1, p.err, 9)) {
+          bad = 2;
+          break;
+        }
+        ph ^= 2;
+      }
+      if (bad) {
+        if (bad == 1) tc::mbar_wait(full, ph & 1, p.err, 5);
+        else tc::mbar_wait(freeb, (ph >> 1) & 1, p.err, 5);
+        abort_flag = 1;
+      }
+      phases = ph;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (*(volatile int*)&abort_flag) break;
+#pragma unroll 1
+    for (int h = 0; h < 64; h += 16) {
+      uint32_t r[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+          "%15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(tl + (uint32_t)h));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (act) {
+#pragma unroll
+        for (int j = 0; j < 16; j++)
+          if (r0 + h + j < p.kc)
+            p.W[(int64_t)p.vmap[r0 + h + j] * p.ldw + cs] = __float2bfloat16_rn(__uint_as_float(r[j]));
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();  // the TMEM columns and the stage free for the next pass
   }
   if (!*(volatile int*)&abort_flag && act) {
     const double lp = (double)(logf(prod) + lsum) + (double)pe * 0.69314718055994530942;

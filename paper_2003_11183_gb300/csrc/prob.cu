@@ -587,6 +587,9 @@ static bool sweep_fused() {
   }();
   return v;
 }
+// The BF16-shift path sweeps whole tiles (low-rank shifts, in-tile coupling and
+// projections inside k_sweep_tc) when tiles hold more than one 64-variable sub-tile.
+static bool bf16_whole_tile(int m) { return m > sweep_sub_tc() && sweep_sub_tc() == STC_SUB && sweep_fused(); }
 static int set_sweep_smem(int m, int sub) {
   for (int flags = 0; flags < 8; flags++)
     TLR_CHECK(raise_smem_limit((const void*)sweep_kernel(flags), sweep_smem_bytes(std::min(m, sub), 256)));
@@ -642,7 +645,7 @@ static void sweep_tile_f32(const Factor& F, int i, bool has_shift, float* Dl, in
                            float* Yv, __nv_bfloat16* Ys, int64_t ldys, double* logP, cudaStream_t st, Prof& pf,
                            const TcCouple* tcc = nullptr) {
   const int m = F.m, mt = (int)F.tsize(i);
-  if (tcc && tcc->sub == STC_SUB && sweep_fused()) {
+  if (tcc && bf16_whole_tile(m)) {
     SweepTcArgs t;
     DiagArgs32& a = t.d;
     a.BT = F.BT32 + (size_t)i * m * F.ldbt;
@@ -862,7 +865,8 @@ static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opt
   const int64_t ldw = (C + 63) / 64 * 64;
   TLR_CHECK(sc.get(&W, (size_t)F.kw16 * ldw));
   TLR_CHECK(sc.get(&Y, (size_t)ly * C));
-  TLR_CHECK(sc.get(&Dl, (size_t)m * C));
+  const bool fused = bf16_whole_tile(m);
+  if (!fused) TLR_CHECK(sc.get(&Dl, (size_t)m * C));  // (the whole-tile sweep keeps its shifts in TMEM)
   TLR_CHECK(sc.get(&err, 1));
   const bool mvt = std::isfinite(nu);
   if (mvt) TLR_CHECK(sc.get(&rs32, (size_t)C));
@@ -916,9 +920,6 @@ static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opt
 
   TLR_CHECK(set_sweep_smem(m, sweep_sub_tc()));
 
-  // the whole-tile sweep (tiles of more than one 64-variable sub-tile) computes the low-rank shifts and
-  // the projections itself
-  const bool fused = F.B16x2 && tcc.sub == STC_SUB && sweep_fused();
   for (int64_t c0 = 0; c0 < S; c0 += C) {
     const int64_t Cc = std::min(C, S - c0);
     if (mvt) {
@@ -986,7 +987,7 @@ int64_t prob_scratch_bytes(const Factor& F, const tlrmvn_opts& o) {
     kw = std::max<int64_t>(kw, 64);
     const int64_t my = (m + 63) / 64 * 64, ly = m > sweep_sub_tc() ? 2 * my : my;
     const int64_t C = chunk_bf16(o, S, kw, ly, m);
-    bytes += C * (kw * 2 + ly * 2 + m * 4 + 4);
+    bytes += C * (kw * 2 + ly * 2 + (bf16_whole_tile((int)m) ? 0 : m * 4) + 4);
   } else {
     const int64_t es = o.precision == TLRMVN_FP64 ? 8 : 4;
     const int64_t C = chunk_simt(o, S, F.ktot, m, es);

@@ -53,7 +53,7 @@ TRAFFIC = {
                              "paper_2003_11183_gb300/csrc/gemm_tc.cuh",
                              "paper_2003_11183_gb300/csrc/common.cuh",
                              "include/tlrmvn.h"],
-                   "sources": "84661010b58ae18c3a5a095661df45aab28b7cbd55ef32f1e00522835b4257a4"},
+                   "sources": "4624c9cdc1140baf18e5aaf605e1a02ba1c171f6e58ed8d80697b6f943de11ca"},
 }
 
 

@@ -1,31 +1,39 @@
-// The BF16-path sweep of a whole diagonal tile B_i (eq. 2 over the tile,
-// Algorithm 6's per-tile step) with the in-tile coupling on the tensor cores.
+// The BF16-path integrand of a whole diagonal tile i in one kernel (Algorithm 6's
+// per-tile step with eq. 2 over the tile): the tile's low-rank limit shifts, the
+// sweep with its in-tile coupling, and the tile's projections for the later
+// tiles, the products on the tensor cores.
 //
-// One CTA of 128 threads owns 128 samples, one per thread and per TMEM lane.
-// The tile runs in sub-tiles of 64 variables; before sub-tile q the coupling to
-// the tile's earlier variables,
-//     T[c][v] = sum_{u < q0} B_i[q0 + v][u] y_u[c]      (v < 64, the same sums as
-// eq. 2, regrouped), is one tcgen05 product per CTA into the CTA's 64 TMEM
-// columns: A = the CTA's rows of the sample-major y it stored itself (hi and lo
-// bf16 parts), B = the rows of the split copy of B_i (hi and lo),
-// hi*hi + hi*lo + lo*hi with fp32 accumulation.  Each thread then runs the
+// One CTA of 128 threads owns 128 samples, one per thread and per TMEM lane, and
+// 64 TMEM columns.  The tile runs in sub-tiles of 64 variables.  Before sub-tile
+// q, one thread accumulates into the columns, by tcgen05 products,
+//     T[c][v] = sum_k U_i[q0 + v][k] W[k][c]           (the low-rank shifts: W the
+//               rank-major projections of the earlier tiles, read MN-major; U
+//               the tile's rows of the row factors; bf16, fp32 accumulation)
+//             + sum_{u < q0} B_i[q0 + v][u] y_u[c]     (the coupling to the tile's
+//               earlier sub-tiles: the CTA's own rows of the sample-major y, hi
+//               and lo bf16 parts, times the split copy of B_i, hi*hi + hi*lo +
+//               lo*hi)
+// for v < 64, the same sums as eq. 2 regrouped.  Each thread then runs the
 // sub-tile's chain for its sample as the sub-tile sweep k_diag_f32 does, with
-// three differences of place: the coupling of each 16-variable block comes
-// from the thread's TMEM lane (tcgen05.ld); the y of the sub-tile go to the same
-// lane, into the columns whose coupling has been read (tcgen05.st), instead of
-// shared memory; and the sub-tile's transposed triangle and band copy are
-// staged in shared memory, in the space the MMA operands use before the sweep.
-// So the coupling never goes through global memory, the per-variable loads of B
-// are shared-memory broadcasts, one launch covers the tile, and the sample's
-// log P is closed once per tile.  After each 16-variable block its y are stored,
-// sample-major bf16 hi and lo, for the later products and the projection.
+// three differences of place: the sums of each 16-variable block come from the
+// thread's TMEM lane (tcgen05.ld); the y of the sub-tile go to the same lane,
+// into the columns whose sums have been read (tcgen05.st), instead of shared
+// memory; and the sub-tile's transposed triangle and band copy are staged in
+// shared memory, in the space the MMA operands use before the sweep.  After
+// each 16-variable block its y are stored, sample-major bf16 hi and lo, for the
+// later products.  After the last sub-tile the CTA computes the tile's
+// projections W[k][c] = sum_v V_i[k][v] y_v[c] in passes of 64 ranks through
+// the same columns and writes them as rows of W.  So neither the shifts nor the
+// coupling go through global memory, the per-variable loads of B are
+// shared-memory broadcasts, and the sample's log P is closed once per tile.
 //
-// The MMA operands are staged by TMA (64-byte swizzle, one 32-deep stage of
-// 24 KB), so a CTA needs ~27 KB of shared memory and 64 TMEM columns; six
-// share an SM.  (A ring of two 16-deep stages measured slower: twice the
-// copies for the same bytes in flight.)  Every wait is bounded; on expiry the
-// CTA records an error code, skips the rest, waits (bounded) for its copies and
-// products in flight, frees its TMEM and returns.
+// The MMA operands are staged by TMA into one stage of 24 KB (shift and
+// projection k-blocks 64 deep, 128-byte swizzle; coupling k-blocks 32 deep,
+// 64-byte swizzle), so a CTA needs ~27 KB of shared memory and 64 TMEM columns;
+// six share an SM.  (A ring of two 16-deep coupling stages measured slower:
+// twice the copies for the same bytes in flight.)  Every wait is bounded; on
+// expiry the CTA records an error code, skips the rest, waits (bounded) for its
+// copies and products in flight, frees its TMEM and returns.
 #pragma once
 #include "gemm_tc.cuh"
 #include "sweep.cuh"
@@ -34,7 +42,7 @@ namespace tlrmvn {
 
 constexpr int STC_SUB = 64;   // variables per sub-tile
 constexpr int STC_NS = 128;   // samples per CTA (TMEM lanes)
-constexpr int STC_KB = 32;    // K depth of the stage
+constexpr int STC_KB = 32;    // K depth of a coupling k-block
 using StcCfg = tc::Cfg<64, true, false, STC_KB, 1>;
 
 struct SweepTcArgs {

@@ -44,7 +44,7 @@ TRAFFIC = {
                    "capture": "profiles/k_diag_f32_sweep_n16384.md",
                    "files": ["paper_2003_11183_gb300/csrc/sweep.cuh", "paper_2003_11183_gb300/csrc/sov_device.cuh",
                              "paper_2003_11183_gb300/csrc/common.cuh", "include/tlrmvn.h"],
-                   "sources": "3873c0bf103a904e294e829b84cb5d8efe2f20a0fc89d403974c9de78c69ebd6"},
+                   "sources": "afe428c92ca35637686d23463fcc5935ea1f1b310efbb0c1c467761b6dc63efd"},
     "k_sweep_tc": {"bytes_per_sample_dim": (700.932352e6 + 231.702272e6) / (100000 * 512),
                    "capture": "profiles/k_sweep_tc_n16384.md",
                    "files": ["paper_2003_11183_gb300/csrc/sweep_tc.cuh",
@@ -53,7 +53,7 @@ TRAFFIC = {
                              "paper_2003_11183_gb300/csrc/gemm_tc.cuh",
                              "paper_2003_11183_gb300/csrc/common.cuh",
                              "include/tlrmvn.h"],
-                   "sources": "4624c9cdc1140baf18e5aaf605e1a02ba1c171f6e58ed8d80697b6f943de11ca"},
+                   "sources": "df1de0efc2d4f951aa70a9c69f81c65a31529b3ae892057ba5432c6908c7567a"},
 }
 
 

@@ -268,7 +268,10 @@ int tlrmvn_selftest_wait_timeout(int polls, void* stream);
  * device error. */
 int tlrmvn_selftest_phi_neg(const float* x, int n, float* out);
 
-/* Kernel classes of the integrand, for tlrmvn_profile_get. */
+/* Kernel classes of the integrand, for tlrmvn_profile_get.  On the BF16-shift
+ * path with tiles of more than 64 variables the shifts, the coupling and the
+ * projections are computed inside the diagonal-tile sweep's kernel and are
+ * timed as TLRMVN_KC_DIAG. */
 #define TLRMVN_KC_SHIFT   0  /* low-rank limit shifts  Delta_i = U_i W_i           */
 #define TLRMVN_KC_DIAG    1  /* diagonal-tile SOV sweep (eq. 2 on B_i)              */
 #define TLRMVN_KC_VPROJ   2  /* projections  W_col_i = V_i^T y_i                    */

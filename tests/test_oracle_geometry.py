@@ -52,13 +52,37 @@ def test_exponential_effective_range_golden():
         assert abs(c - math.exp(-3.0)) < 1e-12 and abs(c - 0.05) < 0.001
 
 
-def test_kernels_closed_forms_and_spd():
-    d = np.array([0.0, 0.1, 0.5])
-    assert np.allclose(geometry.kernel_value(d, geometry.KERNEL_EXP, (0.1,)), np.exp(-d / 0.1))
-    t = math.sqrt(3) * d / 0.2
-    assert np.allclose(geometry.kernel_value(d, geometry.KERNEL_MATERN15, (0.2,)), (1 + t) * np.exp(-t))
-    assert np.allclose(geometry.kernel_value(d, geometry.KERNEL_EXP_MATERN15, (0.3, 0.2)),
-                       np.exp(-d / 0.3) + (1 + t) * np.exp(-t))
+def _matern_bessel(d, nu, ell):
+    """The general Matern covariance, 2^(1-nu)/Gamma(nu) x^nu K_nu(x) with x = sqrt(2 nu) d / ell
+    (unit variance; the limit 1 at d = 0), from the modified Bessel function of the second kind."""
+    from scipy.special import gamma, kv
+    d = np.asarray(d, dtype=np.float64)
+    x = math.sqrt(2.0 * nu) * d / ell
+    with np.errstate(invalid="ignore"):
+        out = 2.0 ** (1.0 - nu) / gamma(nu) * x ** nu * kv(nu, x)
+    return np.where(d == 0.0, 1.0, out)
+
+
+def test_kernels_equal_the_bessel_matern_family():
+    # Section 3.2's kernels are members of the Matern family: the exponential kernel is
+    # smoothness 1/2 with range beta, the "Matern 1.5" kernel smoothness 3/2 with range
+    # ell in the sqrt(2 nu) d / ell convention; both pinned to the Bessel-K form, which
+    # fixes the length-scale convention and every term of the closed forms
+    d = np.concatenate([[0.0, 1e-9], np.geomspace(1e-4, 2.0, 41)])
+    for ell in (0.05, 0.1, 0.2):
+        got = geometry.kernel_value(d, geometry.KERNEL_MATERN15, (ell,))
+        assert np.max(np.abs(got - _matern_bessel(d, 1.5, ell))) < 1e-13
+        got = geometry.kernel_value(d, geometry.KERNEL_EXP, (ell,))
+        assert np.max(np.abs(got - _matern_bessel(d, 0.5, ell))) < 1e-13
+    got = geometry.kernel_value(d, geometry.KERNEL_EXP_MATERN15, (0.3, 0.1))
+    want = _matern_bessel(d, 0.5, 0.3) + _matern_bessel(d, 1.5, 0.1)
+    assert np.max(np.abs(got - want)) < 1e-13
+    # a plausible slip is caught: the d / ell convention (without sqrt 3) differs by far more
+    t = d / 0.1
+    assert np.max(np.abs((1 + t) * np.exp(-t) - _matern_bessel(d, 1.5, 0.1))) > 1e-2
+
+
+def test_kernels_spd():
     xy = synth.jittered_grid(8, 2)
     for k, p in ((0, (0.1,)), (1, (0.1,)), (2, (0.3, 0.1))):
         S = geometry.covariance(xy, k, p, 1e-8)

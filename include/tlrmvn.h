@@ -47,6 +47,10 @@ extern "C" {
 #define TLRMVN_E_NOTSUP    6  /* requested precision / mode not available */
 #define TLRMVN_E_TIMEOUT   7  /* a bounded device-side wait (tensor-core pipeline) expired; the kernel
                                  freed its resources and returned, the CUDA context stays usable */
+#define TLRMVN_E_RANK      8  /* tlrmvn_factor_*: the rank cap stopped the truncation of an off-diagonal
+                                 tile before the tolerance was met, and the options ask for that to fail */
+#define TLRMVN_E_BUSY      9  /* tlrmvn_server_submit: admission refused (the request can never fit the
+                                 server's memory budget, or the server is shutting down) */
 
 /* ---- option values --------------------------------------------------- */
 /* Arithmetic of the integrand (tlrmvn_opts.precision). */
@@ -72,6 +76,9 @@ typedef struct {
   int    max_rank;  /* rank cap per off-diagonal tile; 0 = tile size                           */
   int    reorder;   /* TLRMVN_REORDER_*                                                        */
   void*  stream;    /* cudaStream_t or NULL                                                    */
+  int    strict_rank; /* 0: a tile whose truncation the rank cap stopped keeps the capped rank
+                         (counted in tlrmvn_factor_info's `capped`); nonzero: the factorisation
+                         fails with TLRMVN_E_RANK instead                                        */
 } tlrmvn_factor_opts;
 
 typedef struct {
@@ -200,7 +207,7 @@ int tlrmvn_prob_batch(int count, const tlrmvn_factor_t* factors, const double* c
  * other calls meanwhile.
  *   tlrmvn_server_submit copies a, b (host, length n of the factor) and, when
  *     opts->shifts is set, the shifts; opts->stream is ignored.  Returns an id.
- *     TLRMVN_E_NOMEM if the request alone exceeds the budget.
+ *     TLRMVN_E_BUSY (admission refused) if the request alone exceeds the budget.
  *   tlrmvn_server_wait blocks until the request is done and returns its logp,
  *     err and latency (submission to completion, milliseconds); an id can be
  *     waited for once.
@@ -223,6 +230,21 @@ int tlrmvn_server_free(tlrmvn_server_t server);
 /* Device scratch (bytes) one request with these options takes on this factor:
  * what the server charges against its budget (also a tlrmvn_prob call's peak). */
 int tlrmvn_prob_scratch_bytes(tlrmvn_factor_t f, const tlrmvn_opts* opts, int64_t* bytes);
+
+/* ---- pooled estimate over replicas -------------------------------------- */
+
+/* The estimate of Section 2.1 from per-shift log lattice means gathered on the
+ * host, e.g. from replicas of one problem solved with disjoint shifts on several
+ * GPUs or processes (each shift batch is an independent estimate, so the pooled
+ * estimate is exactly what one solve over all the shifts would return):
+ *   per_shift  host, count >= 1 values ell_s = log of shift s's lattice mean
+ *              (the per_shift output of tlrmvn_prob); -INFINITY allowed
+ *   logp, err  host, receive log((1/count) sum_s exp(ell_s)) and the standard
+ *              error of that mean divided by the mean (NaN when count == 1 or every
+ *              ell_s is -INFINITY; logp is then -INFINITY in the latter case)
+ * Float64 on the host, no device work.  TLRMVN_E_INVAL for null pointers,
+ * count < 1, NaN or +INFINITY values. */
+int tlrmvn_estimate_pooled(const double* per_shift, int64_t count, double* logp, double* err);
 
 /* ---- estimator without device allocation ------------------------------ */
 

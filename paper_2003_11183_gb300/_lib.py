@@ -12,7 +12,7 @@ c_u64_p = C.POINTER(C.c_uint64)
 
 class FactorOpts(C.Structure):
     _fields_ = [("tile", C.c_int), ("tol", C.c_double), ("max_rank", C.c_int), ("reorder", C.c_int),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("strict_rank", C.c_int)]
 
 
 class Opts(C.Structure):
@@ -54,6 +54,7 @@ SIGNATURES = {
     "tlrmvn_server_stats": (C.c_int, [C.c_void_p, C.c_void_p]),
     "tlrmvn_server_free": (C.c_int, [C.c_void_p]),
     "tlrmvn_prob_scratch_bytes": (C.c_int, [C.c_void_p, C.POINTER(Opts), C.POINTER(C.c_int64)]),
+    "tlrmvn_estimate_pooled": (C.c_int, [c_double_p, C.c_int64, c_double_p, c_double_p]),
     "tlrmvn_estimate_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tlrmvn_profile_enable": (C.c_int, [C.c_int]),
     "tlrmvn_profile_reset": (C.c_int, []),

@@ -16,7 +16,7 @@ from . import _lib as L
 FP64, FP32, BF16_SHIFT = 0, 1, 2
 REORDER_NONE, REORDER_BLOCK, REORDER_ITERATIVE = 0, 1, 2
 KERNEL_EXP, KERNEL_MATERN15, KERNEL_EXP_MATERN15 = 0, 1, 2
-E_INVAL, E_NOT_SPD, E_NOMEM, E_CUDA, E_FORMAT, E_NOTSUP, E_TIMEOUT = 1, 2, 3, 4, 5, 6, 7
+E_INVAL, E_NOT_SPD, E_NOMEM, E_CUDA, E_FORMAT, E_NOTSUP, E_TIMEOUT, E_RANK, E_BUSY = 1, 2, 3, 4, 5, 6, 7, 8, 9
 
 
 class TlrmvnError(RuntimeError):
@@ -65,33 +65,35 @@ def _stream_ptr(stream) -> int | None:
     return stream.cuda_stream
 
 
-def _fopts(tile: int, tol: float, max_rank: int, reorder: int, stream) -> L.FactorOpts:
-    return L.FactorOpts(int(tile), float(tol), int(max_rank), int(reorder), _stream_ptr(stream))
+def _fopts(tile: int, tol: float, max_rank: int, reorder: int, stream, strict_rank: bool = False) -> L.FactorOpts:
+    return L.FactorOpts(int(tile), float(tol), int(max_rank), int(reorder), _stream_ptr(stream),
+                        1 if strict_rank else 0)
 
 
 def tlrmvn_factor_kernel(xy, kernel: int, params, nugget: float, a_ref, b_ref, tile: int, tol: float,
-                         max_rank: int = 0, reorder: int = REORDER_ITERATIVE, stream=None) -> Factor:
+                         max_rank: int = 0, reorder: int = REORDER_ITERATIVE, stream=None,
+                         strict_rank: bool = False) -> Factor:
     lib = L.load()
     xy = _f64(xy).reshape(-1, 2)
     p = _f64(list(params) + [0.0] * (2 - len(params)))
     a = None if a_ref is None else _f64(a_ref)
     b = None if b_ref is None else _f64(b_ref)
     out = C.c_void_p()
-    o = _fopts(tile, tol, max_rank, reorder, stream)
+    o = _fopts(tile, tol, max_rank, reorder, stream, strict_rank)
     _check(lib.tlrmvn_factor_kernel(_dp(xy), xy.shape[0], int(kernel), _dp(p), float(nugget), _dp(a), _dp(b),
                                     C.byref(o), C.byref(out)), "tlrmvn_factor_kernel")
     return Factor(out.value)
 
 
 def tlrmvn_factor_dense(cov, a_ref, b_ref, tile: int, tol: float, max_rank: int = 0,
-                        reorder: int = REORDER_ITERATIVE, stream=None) -> Factor:
+                        reorder: int = REORDER_ITERATIVE, stream=None, strict_rank: bool = False) -> Factor:
     lib = L.load()
     cov = np.asfortranarray(cov, dtype=np.float64)
     n = cov.shape[0]
     a = None if a_ref is None else _f64(a_ref)
     b = None if b_ref is None else _f64(b_ref)
     out = C.c_void_p()
-    o = _fopts(tile, tol, max_rank, reorder, stream)
+    o = _fopts(tile, tol, max_rank, reorder, stream, strict_rank)
     _check(lib.tlrmvn_factor_dense(cov.ctypes.data_as(L.c_double_p), n, n, _dp(a), _dp(b), C.byref(o), C.byref(out)),
            "tlrmvn_factor_dense")
     return Factor(out.value)
@@ -239,6 +241,16 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def tlrmvn_estimate_pooled(per_shift_logs) -> tuple[float, float]:
+    """(log p_hat, err) of Section 2.1 from per-shift log means gathered on the host
+    (computed by the library, float64 on the host; no device work)."""
+    ell = _f64(per_shift_logs).ravel()
+    lp, er = C.c_double(), C.c_double()
+    _check(L.load().tlrmvn_estimate_pooled(_dp(ell), int(ell.size), C.byref(lp), C.byref(er)),
+           "tlrmvn_estimate_pooled")
+    return lp.value, er.value
 
 
 NOALLOC_MAX_SHIFTS = 65536

@@ -18,7 +18,7 @@
 namespace tlrmvn {
 
 __global__ void k_shift_reduce(const double* logP, int64_t N, double* ell);
-__global__ void k_final(const double* ell, int M, double* out);
+__global__ void k_final(const double* ell, int M, double* logp, double* errp);
 
 constexpr int BATCH_T = 128;     // samples per work item = threads per CTA
 constexpr int BATCH_MMAX = 128;  // largest tile size of a batched problem

@@ -900,6 +900,9 @@ static int factor_build(const CovSrc& src, int64_t n, std::vector<int64_t> geo, 
   F.rank = std::vector<int32_t>(rank.begin(), rank.end());
   TLR_CUDA(cudaMemcpyAsync(&F.capped, d_capped, sizeof(int), cudaMemcpyDeviceToHost, st));
   TLR_CUDA(cudaStreamSynchronize(st));
+  if (o.strict_rank && F.capped > 0)
+    return fail(TLRMVN_E_RANK, std::to_string(F.capped) + " off-diagonal tiles reached the rank cap " +
+                                   std::to_string(cap) + " before the tolerance");
   TLR_CHECK(factor_alloc_compact(F, st));
   for (int j = 0; j < r; j++)
     TLR_CUDA(cudaMemcpyAsync(F.B + (size_t)j * m * m, diagS + (size_t)pos2blk[j] * m * m, (size_t)m * m * 8,

@@ -17,7 +17,7 @@ namespace tlrmvn {
 
 // the estimator kernels (defined with the integrand)
 __global__ void k_shift_reduce(const double* logP, int64_t N, double* ell);
-__global__ void k_final(const double* ell, int M, double* out);
+__global__ void k_final(const double* ell, int M, double* logp, double* errp);
 
 // Scratch of every call on a device: one log mean per shift.  Every GPU that
 // loads this library holds it until the process exits.
@@ -59,7 +59,7 @@ extern "C" int tlrmvn_estimate_noalloc(const double* per_sample, int n_shifts, i
   cudaStream_t st = stream ? (cudaStream_t)stream : pick_stream(nullptr);
   // every entry of the scratch that k_final reads is written first by k_shift_reduce
   k_shift_reduce<<<(unsigned)n_shifts, 256, 0, st>>>(per_sample, n_points, ell);
-  k_final<<<1, 256, 0, st>>>(ell, n_shifts, out);
+  k_final<<<1, 256, 0, st>>>(ell, n_shifts, out, out + 1);
   TLR_CUDA(cudaGetLastError());
   if (per_shift) TLR_CUDA(cudaMemcpyAsync(per_shift, ell, (size_t)n_shifts * 8, cudaMemcpyDeviceToDevice, st));
   TLR_CUDA(cudaStreamSynchronize(st));

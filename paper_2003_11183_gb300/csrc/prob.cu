@@ -212,7 +212,7 @@ __global__ void k_shift_reduce(const double* logP, int64_t N, double* ell) {
 }
 
 // log p_hat = log((1/M) sum_s exp(ell_s)); err = SD_s(exp ell_s)/(sqrt(M) p_hat).
-__device__ void final_estimate(const double* ell, int M, double* out) {
+__device__ void final_estimate(const double* ell, int M, double* logp, double* errp) {
   __shared__ double sh[32];
   double mx = -INFINITY;
   for (int s = threadIdx.x; s < M; s += blockDim.x) mx = fmax(mx, ell[s]);
@@ -230,14 +230,14 @@ __device__ void final_estimate(const double* ell, int M, double* out) {
     }
   sq = block_reduce(sq, SumOp(), sh, 0.0);
   if (threadIdx.x == 0) {
-    out[0] = (mx > -INFINITY) ? mx + log(sum) - log((double)M) : -INFINITY;
-    out[1] = (M > 1 && mx > -INFINITY) ? sqrt(sq / (M - 1) / M) / mean : NAN;
+    *logp = (mx > -INFINITY) ? mx + log(sum) - log((double)M) : -INFINITY;
+    *errp = (M > 1 && mx > -INFINITY) ? sqrt(sq / (M - 1) / M) / mean : NAN;
   }
 }
-__global__ void k_final(const double* ell, int M, double* out) { final_estimate(ell, M, out); }
-// one problem per block: ell + blockIdx.x * M -> out + 2 * blockIdx.x
+__global__ void k_final(const double* ell, int M, double* logp, double* errp) { final_estimate(ell, M, logp, errp); }
+// one problem per block: ell + blockIdx.x * M -> out[2 * blockIdx.x], out[2 * blockIdx.x + 1]
 __global__ void k_final_batch(const double* ell, int M, double* out) {
-  final_estimate(ell + (int64_t)blockIdx.x * M, M, out + 2 * blockIdx.x);
+  final_estimate(ell + (int64_t)blockIdx.x * M, M, out + 2 * blockIdx.x, out + 2 * blockIdx.x + 1);
 }
 
 template <typename S, typename D>
@@ -503,7 +503,12 @@ struct Lims {
   bool one_sided;  // every lower limit is -inf
 };
 
-// Threads per block of the sweep: as many as keep the tile's y values of the
+// Sub-tile of the float64 sweep: 64 variables, so that a block of 128 samples
+// keeps its sub-tile's y in 64 KB of shared memory and three blocks share an SM
+// (a whole 512-variable tile per block left one warp per SM).
+constexpr int DIAG64_SUB = 64;
+
+// Threads per block of the sweep: as many as keep the (sub-)tile's y values of the
 // block's samples within 64 KB of shared memory (at least one warp).
 template <typename T>
 static int diag_threads(int m) {
@@ -777,8 +782,8 @@ static int run_chunks(Factor& F, const T* Bt, const T* Ut, const T* Vt, const Li
   const bool mvt = std::isfinite(nu);
   if (mvt) TLR_CHECK(f32 ? sc.get(&rs32, (size_t)C) : sc.get(&rs, (size_t)C));
 
-  const int bd = diag_threads<T>(m);
-  const size_t smem = (size_t)m * (bd + 1) * sizeof(T);
+  const int bd = diag_threads<T>(std::min(m, DIAG64_SUB));
+  const size_t smem = (size_t)std::min(m, DIAG64_SUB) * (bd + 1) * sizeof(T);
   if (f32)
     TLR_CHECK(set_sweep_smem(m, sweep_sub_simt()));
   else
@@ -806,30 +811,44 @@ static int run_chunks(Factor& F, const T* Bt, const T* Ut, const T* Vt, const Li
         sweep_tile_f32(F, i, Kr > 0, (float*)Dl, C, L, rs32, dD, c0, N, Cc, o.periodize, (float*)Y, nullptr, 0, logP,
                        st, pf);
       } else {
-        pf.begin(TLRMVN_KC_DIAG);
-        DiagArgs<T, YT> a;
-        a.B = Bt + (size_t)i * m * m;
-        a.mt = mt;
-        a.ldb = m;
-        a.Delta = Delta;
-        a.ldd = C;
-        a.a = L.a + F.tile_off[i];
-        a.b = L.b + F.tile_off[i];
-        a.rs = rs;
-        a.Q = F.Q;
-        a.D = dD;
-        a.ldD = F.n + 1;
-        a.coord0 = F.tile_off[i];
-        a.sample0 = c0;
-        a.N = N;
-        a.C = Cc;
-        a.periodize = o.periodize;
-        a.first = (i == 0);
-        a.Y = Y;
-        a.ldy = C;
-        a.logP = logP;
-        k_diag<T, YT, false><<<blocks_for(Cc, bd), bd, smem, st>>>(a);
-        pf.end();
+        // sub-tiles of DIAG64_SUB variables: each sample keeps only the sub-tile's y in
+        // shared memory, and the coupling to the tile's earlier sub-tiles,
+        // B_i[q, <q] y_i[<q], is added to the limit shifts by a dense product first
+        // (the same sums as eq. 2, regrouped)
+        const T* Bi = Bt + (size_t)i * m * m;
+        for (int q0 = 0; q0 < mt; q0 += DIAG64_SUB) {
+          const int mq = std::min(DIAG64_SUB, mt - q0);
+          if (q0 > 0) {
+            pf.begin(TLRMVN_KC_COUPLE);
+            gemm_nn<T>(st, mq, Cc, q0, Bi + (size_t)q0 * m, m, Y, C, Dl + (size_t)q0 * C, C, nullptr,
+                       Delta ? 1 : 0);
+            pf.end();
+          }
+          pf.begin(TLRMVN_KC_DIAG);
+          DiagArgs<T, YT> a;
+          a.B = Bi + (size_t)q0 * m + q0;
+          a.mt = mq;
+          a.ldb = m;
+          a.Delta = (Delta || q0 > 0) ? Dl + (size_t)q0 * C : nullptr;
+          a.ldd = C;
+          a.a = L.a + F.tile_off[i] + q0;
+          a.b = L.b + F.tile_off[i] + q0;
+          a.rs = rs;
+          a.Q = F.Q;
+          a.D = dD;
+          a.ldD = F.n + 1;
+          a.coord0 = F.tile_off[i] + q0;
+          a.sample0 = c0;
+          a.N = N;
+          a.C = Cc;
+          a.periodize = o.periodize;
+          a.first = (i == 0 && q0 == 0);
+          a.Y = Y + (size_t)q0 * C;
+          a.ldy = C;
+          a.logP = logP;
+          k_diag<T, YT, false><<<blocks_for(Cc, bd), bd, smem, st>>>(a);
+          pf.end();
+        }
       }
       if (Kc > 0) {
         pf.begin(TLRMVN_KC_VPROJ);
@@ -997,7 +1016,7 @@ int64_t prob_scratch_bytes(const Factor& F, const tlrmvn_opts& o) {
 }
 
 int prob_impl(Factor& F, const double* a_dev, const double* b_dev, double nu, const tlrmvn_opts& o,
-              double* out2_dev, double* ell_dev_out, double* per_sample_dev, cudaStream_t st) {
+              double* logp_dev, double* err_dev, double* ell_dev_out, double* per_sample_dev, cudaStream_t st) {
   const int64_t M = o.n_shifts, N = o.n_points, S = M * N, n = F.n;
   Scratch sc(st);
   double *ap = nullptr, *bp = nullptr, *logP = nullptr, *ell = nullptr;
@@ -1053,7 +1072,7 @@ int prob_impl(Factor& F, const double* a_dev, const double* b_dev, double nu, co
   k_shift_reduce<<<(unsigned)M, 256, 0, st>>>(logP, N, ell);
   pf.end();
   pf.begin(TLRMVN_KC_REDUCE);
-  k_final<<<1, 256, 0, st>>>(ell, (int)M, out2_dev);
+  k_final<<<1, 256, 0, st>>>(ell, (int)M, logp_dev, err_dev);
   pf.end();
   if (ell_dev_out) TLR_CUDA(cudaMemcpyAsync(ell_dev_out, ell, M * 8, cudaMemcpyDeviceToDevice, st));
   TLR_CUDA(cudaGetLastError());
@@ -1084,16 +1103,8 @@ extern "C" int tlrmvn_prob_device(tlrmvn_factor_t f, const double* a, const doub
   cudaGetDevice(&cur);
   TLR_CUDA(cudaSetDevice(F.device));
   cudaStream_t st = pick_stream(opts->stream);
-  double* out2 = nullptr;
-  int s = dalloc(&out2, 2);
-  if (s == TLRMVN_OK) s = prob_impl(F, a, b, nu, *opts, out2, per_shift, per_sample, st);
-  if (s == TLRMVN_OK) {
-    cudaError_t e1 = cudaMemcpyAsync(logp, out2, 8, cudaMemcpyDeviceToDevice, st);
-    cudaError_t e2 = cudaMemcpyAsync(err, out2 + 1, 8, cudaMemcpyDeviceToDevice, st);
-    cudaError_t e3 = cudaStreamSynchronize(st);
-    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) s = cuda_fail(e1 ? e1 : (e2 ? e2 : e3), "copy out");
-  }
-  dfree(out2);
+  // (the estimate is written straight into the caller's device outputs: no allocation here)
+  const int s = prob_impl(F, a, b, nu, *opts, logp, err, per_shift, per_sample, st);
   cudaSetDevice(cur);
   return s;
 }
@@ -1119,7 +1130,7 @@ extern "C" int tlrmvn_prob(tlrmvn_factor_t f, const double* a, const double* b, 
     if (e == cudaSuccess) e = cudaMemcpyAsync(db, b, n * 8, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) s = cuda_fail(e, "copy limits");
   }
-  if (s == TLRMVN_OK) s = prob_impl(F, da, db, nu, *opts, out2, dell, dps, st);
+  if (s == TLRMVN_OK) s = prob_impl(F, da, db, nu, *opts, out2, out2 + 1, dell, dps, st);
   if (s == TLRMVN_OK) {
     double h[2];
     cudaError_t e = cudaMemcpyAsync(h, out2, 16, cudaMemcpyDeviceToHost, st);

@@ -3,6 +3,8 @@
 // serialisation (tlrmvn_factor_export / tlrmvn_factor_import / info / free).
 #include "common.cuh"
 
+#include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -222,6 +224,8 @@ extern "C" const char* tlrmvn_strerror(int status) {
     case TLRMVN_E_FORMAT: return "malformed factor buffer";
     case TLRMVN_E_NOTSUP: return "not supported";
     case TLRMVN_E_TIMEOUT: return "device-side wait timed out";
+    case TLRMVN_E_RANK: return "rank cap reached before the truncation tolerance";
+    case TLRMVN_E_BUSY: return "admission refused";
     default: return "unknown status";
   }
 }
@@ -454,5 +458,34 @@ extern "C" int tlrmvn_factor_import(const void* buf, size_t bytes, tlrmvn_factor
     return s;
   }
   *out = reinterpret_cast<tlrmvn_factor_t>(F);
+  return TLRMVN_OK;
+}
+
+// Section 2.1 estimate pooled over shift batches gathered on the host: the same
+// formula as the device reduction (k_final), in float64 on the host.
+extern "C" int tlrmvn_estimate_pooled(const double* per_shift, int64_t count, double* logp, double* err) {
+  if (!per_shift || !logp || !err) return fail(TLRMVN_E_INVAL, "null argument");
+  if (count < 1) return fail(TLRMVN_E_INVAL, "count must be >= 1");
+  double mx = -INFINITY;
+  for (int64_t s = 0; s < count; s++) {
+    if (std::isnan(per_shift[s]) || per_shift[s] == INFINITY)
+      return fail(TLRMVN_E_INVAL, "per-shift logs must be finite or -INFINITY");
+    mx = std::max(mx, per_shift[s]);
+  }
+  if (mx == -INFINITY) {
+    *logp = -INFINITY;
+    *err = NAN;
+    return TLRMVN_OK;
+  }
+  double sum = 0.0;
+  for (int64_t s = 0; s < count; s++) sum += std::exp(per_shift[s] - mx);
+  const double mean = sum / (double)count;
+  double sq = 0.0;
+  for (int64_t s = 0; s < count; s++) {
+    const double d = std::exp(per_shift[s] - mx) - mean;
+    sq += d * d;
+  }
+  *logp = mx + std::log(sum) - std::log((double)count);
+  *err = count > 1 ? std::sqrt(sq / (double)(count - 1) / (double)count) / mean : NAN;
   return TLRMVN_OK;
 }

@@ -21,7 +21,7 @@
 namespace tlrmvn {
 
 int prob_impl(Factor& F, const double* a_dev, const double* b_dev, double nu, const tlrmvn_opts& o,
-              double* out2_dev, double* ell_dev_out, double* per_sample_dev, cudaStream_t st);
+              double* logp_dev, double* err_dev, double* ell_dev_out, double* per_sample_dev, cudaStream_t st);
 int64_t prob_scratch_bytes(const Factor& F, const tlrmvn_opts& o);
 
 using Clock = std::chrono::steady_clock;
@@ -89,8 +89,8 @@ struct Server {
         if (e == cudaSuccess) e = cudaMemcpyAsync(dev + n, r->b.data(), n * 8, cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) s = cuda_fail(e, "server: copy limits");
       }
-      if (s == TLRMVN_OK) s = prob_impl(*factors[r->factor], dev, dev + n, r->nu, r->opts, dev + 2 * n, nullptr,
-                                        nullptr, st);
+      if (s == TLRMVN_OK) s = prob_impl(*factors[r->factor], dev, dev + n, r->nu, r->opts, dev + 2 * n,
+                                        dev + 2 * n + 1, nullptr, nullptr, st);
       double out[2] = {NAN, NAN};
       if (s == TLRMVN_OK) {
         e = cudaMemcpyAsync(out, dev + 2 * n, 16, cudaMemcpyDeviceToHost, st);
@@ -180,8 +180,10 @@ extern "C" int tlrmvn_server_submit(tlrmvn_server_t srv, int factor, const doubl
   r->opts.shifts = nullptr;
   r->bytes = prob_scratch_bytes(F, r->opts) + (2 * F.n + 2) * 8;
   if (r->bytes > S.budget) {
+    const int64_t r_bytes = r->bytes;
     delete r;
-    return fail(TLRMVN_E_NOMEM, "request needs more scratch than the server's memory budget");
+    return fail(TLRMVN_E_BUSY, "admission refused: the request needs more scratch (" + std::to_string(r_bytes) +
+                                   " bytes) than the server's memory budget");
   }
   r->t_submit = Clock::now();
   {

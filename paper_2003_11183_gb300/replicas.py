@@ -10,8 +10,6 @@ backend; gloo on CPU in the tests).
 """
 from __future__ import annotations
 
-import math
-
 import numpy as np
 
 
@@ -22,16 +20,12 @@ def rank_seed(seed: int, rank: int, n_shifts: int) -> int:
 
 
 def combine(per_shift_logs) -> tuple[float, float]:
-    """(log p_hat, err) from per-shift log means, pooled over replicas (float64)."""
+    """(log p_hat, err) from per-shift log means, pooled over replicas: the replicas'
+    values are concatenated here and the estimate is the library's
+    (tlrmvn_estimate_pooled, float64 on the host)."""
+    from .api import tlrmvn_estimate_pooled
     ell = np.concatenate([np.asarray(x, dtype=np.float64).ravel() for x in per_shift_logs])
-    M = ell.size
-    mx = ell.max()
-    if not np.isfinite(mx):
-        return float("-inf"), float("nan")
-    e = np.exp(ell - mx)
-    logp = float(mx + math.log(e.sum()) - math.log(M))
-    err = float(np.std(e, ddof=1) / math.sqrt(M) / e.mean()) if M > 1 else float("nan")
-    return logp, err
+    return tlrmvn_estimate_pooled(ell)
 
 
 def gather_and_combine(per_shift_log, group=None) -> tuple[float, float]:

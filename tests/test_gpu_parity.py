@@ -274,6 +274,58 @@ def test_bf16_split_coupling_without_low_rank(tl, nu, n_shifts, n_points):
     assert np.all(rel(ps, ref["per_shift"]) < 1e-3)
 
 
+@pytest.fixture(scope="module", params=["grid64", "ragged3900"])
+def headline_family(request, tl):
+    # A member of the bench workload's family small enough for the oracle: Student-t
+    # nu = 7, exponential kernel beta = 0.1, b ~ N(1, 0.5^2), tiles of 512 (eight
+    # 64-variable sub-tiles, seven coupling steps each), ACA tolerance 1e-4 with the
+    # rank cap 64 binding, Algorithm 4; 8 shifts x 250 points (2,000 samples: 16 CTAs
+    # of 128, the last one ragged).  "grid64": 64 x 64 jittered grid, n = 4,096;
+    # "ragged3900": 3,900 uniform points, the last tile 316 variables.
+    ragged = None if request.param == "grid64" else 3900
+    w = synth.small_workload(64, 512, 51, nu=7.0, n_shifts=8, n_points=250, tol=1e-4, max_rank=64,
+                             limits="normal", reorder=1, ragged_n=ragged)
+    F = tl.tlrmvn_factor_kernel(w.xy, w.kernel, w.params, w.nugget, w.a, w.b, w.m, w.tol, w.max_rank, w.reorder)
+    info = tl.tlrmvn_factor_info(F)
+    ranks = tl.tlrmvn_factor_ranks(F)
+    # the shape this family is meant to exercise: the rank cap binds, some row tile
+    # holds more than one 64-deep block of ranks, and every full tile has 8 sub-tiles
+    assert info["capped"] > 0 and ranks.max() == 64 and ranks.sum(axis=1).max() > 64 and info["m"] == 512
+    OF = to_oracle_factor(tl.parse_export(tl.tlrmvn_factor_export(F)))
+    ref = sov.solve(OF, w.a, w.b, w.nu, w.shifts, w.n_points)
+    return w, F, ref
+
+
+def test_headline_family_bf16_shift_every_sample_and_shift(tl, headline_family):
+    # BF16-shift path (the bench's precision) against the oracle on the same factor,
+    # every per-sample and every per-shift value: per shift 1e-2 relative, the
+    # estimate within 3 QMC standard errors, per sample 1e-2 relative (each sample's
+    # log integrand is a sum over thousands of variables whose limit shifts carry
+    # bf16 operand rounding; the derivation is in the design notes)
+    w, F, ref = headline_family
+    lp, err, ps, pm = tl.tlrmvn_prob(F, w.a, w.b, w.nu, tl.BF16_SHIFT, w.n_shifts, w.n_points, shifts=w.shifts,
+                                     per_shift=True, per_sample=True)
+    r_shift = rel(ps, ref["per_shift"])
+    r_sample = rel(pm, ref["per_sample"])
+    assert np.all(np.isfinite(pm))
+    assert np.all(r_shift < 1e-2), r_shift.max()
+    assert np.all(r_sample < 1e-2), (r_sample.max(), np.median(r_sample))
+    assert abs(lp - ref["logp"]) <= 3 * max(err, ref["err"])
+
+
+def test_headline_family_fp32_every_sample_and_shift(tl, headline_family):
+    # FP32 path on the same factor: every per-shift value within 1e-4 relative and
+    # every per-sample value within 1e-4 relative of the oracle
+    w, F, ref = headline_family
+    lp, err, ps, pm = tl.tlrmvn_prob(F, w.a, w.b, w.nu, tl.FP32, w.n_shifts, w.n_points, shifts=w.shifts,
+                                     per_shift=True, per_sample=True)
+    r_shift = rel(ps, ref["per_shift"])
+    r_sample = rel(pm, ref["per_sample"])
+    assert np.all(r_shift < 1e-4), r_shift.max()
+    assert np.all(r_sample < 1e-4), (r_sample.max(), np.median(r_sample))
+    assert abs(lp - ref["logp"]) < 1e-4 * abs(ref["logp"])
+
+
 def _check_factor(OF, w, n_pairs=24, tol_mult=50):
     # every diagonal entry positive and sampled entries of L L^T equal to Sigma
     assert all(np.all(np.diag(Bt) > 0) for Bt in OF.B)
@@ -323,12 +375,27 @@ def test_full_size_mvt_n65536_sampled(tl):
     ref = sov.solve(OF, w.a, w.b, w.nu, w.shifts, w.n_points, samples=sel)["per_sample"]
     lp32, err32, ps32, pm32 = tl.tlrmvn_prob(F, w.a, w.b, w.nu, tl.FP32, w.n_shifts, w.n_points, shifts=w.shifts,
                                              per_shift=True, per_sample=True)
-    assert np.all(np.abs(pm32[sel] - ref) <= 1e-4 * np.abs(ref) + 2e-2)
+    assert np.all(rel(pm32[sel], ref) < 1e-4)
     lp16, err16, ps16, pm16 = tl.tlrmvn_prob(F, w.a, w.b, w.nu, tl.BF16_SHIFT, w.n_shifts, w.n_points,
                                              shifts=w.shifts, per_shift=True, per_sample=True)
     assert np.all(rel(pm16[sel], ref) < 1e-2)
     assert np.all(rel(ps16, ps32) < 1e-2)
     assert abs(lp16 - lp32) <= 3 * err32
+    # every per-shift and per-sample value of both reduced precisions against the
+    # library's FP64 path (pinned to the oracle at 1e-9 on smaller problems) on the
+    # same factor, lattice and shifts, at 20 x 240 points (4,800 samples)
+    pts = 240
+    kw = dict(shifts=w.shifts, per_shift=True, per_sample=True)
+    _, _, ps64, pm64 = tl.tlrmvn_prob(F, w.a, w.b, w.nu, tl.FP64, w.n_shifts, pts, **kw)
+    sel64 = sel[sel < w.n_shifts * pts]
+    ref64 = sov.solve(OF, w.a, w.b, w.nu, w.shifts, pts, samples=sel64)["per_sample"]
+    assert np.all(rel(pm64[sel64], ref64) < 1e-9)
+    _, _, ps32r, pm32r = tl.tlrmvn_prob(F, w.a, w.b, w.nu, tl.FP32, w.n_shifts, pts, **kw)
+    _, _, ps16r, pm16r = tl.tlrmvn_prob(F, w.a, w.b, w.nu, tl.BF16_SHIFT, w.n_shifts, pts, **kw)
+    assert np.all(rel(ps32r, ps64) < 1e-4), rel(ps32r, ps64).max()
+    assert np.all(rel(pm32r, pm64) < 1e-4), rel(pm32r, pm64).max()
+    assert np.all(rel(ps16r, ps64) < 1e-2), rel(ps16r, ps64).max()
+    assert np.all(rel(pm16r, pm64) < 1e-2), rel(pm16r, pm64).max()
 
 
 def test_float_phi_lower_tail_error_bound(tl):
@@ -362,3 +429,18 @@ def test_sample_chunks_change_nothing(tl, precision):
     ref = sov.solve(OF, w.a, w.b, w.nu, w.shifts, w.n_points)
     tol = {"FP64": 1e-9, "FP32": 1e-4, "BF16_SHIFT": 1e-2}[precision]
     assert np.all(rel(part[2], ref["per_shift"]) < tol)
+
+
+def test_rank_cap_policy(tl):
+    # a rank cap that binds: by default the capped tiles are counted, with
+    # strict_rank the factorisation fails with TLRMVN_E_RANK
+    w = synth.small_workload(16, 32, 42, tol=1e-10, max_rank=2)
+    F = tl.tlrmvn_factor_kernel(w.xy, w.kernel, w.params, w.nugget, w.a, w.b, w.m, w.tol, 2, 1)
+    info = tl.tlrmvn_factor_info(F)
+    assert info["capped"] > 0 and tl.tlrmvn_factor_ranks(F).max() == 2
+    with pytest.raises(tl.TlrmvnError) as e:
+        tl.tlrmvn_factor_kernel(w.xy, w.kernel, w.params, w.nugget, w.a, w.b, w.m, w.tol, 2, 1, strict_rank=True)
+    assert e.value.status == tl.E_RANK
+    # a cap that does not bind passes under the strict policy
+    F2 = tl.tlrmvn_factor_kernel(w.xy, w.kernel, w.params, w.nugget, w.a, w.b, w.m, 1e-4, 0, 1, strict_rank=True)
+    assert tl.tlrmvn_factor_info(F2)["capped"] == 0

@@ -76,10 +76,44 @@ def test_admission_by_memory_budget(env):
     st = srv.stats()
     assert st["peak_in_flight"] == 1 and st["peak_bytes"] == one
     assert all(r[0] == res[0][0] for r in res)
+    # a request that can never fit the budget: admission refused
     with pytest.raises(tl.TlrmvnError) as e:
         srv.submit(2, a, b, nu, tl.FP32, n_shifts=20, n_points=200000)
-    assert e.value.status == tl.E_NOMEM
+    assert e.value.status == tl.E_BUSY
     with pytest.raises(tl.TlrmvnError) as e:
         srv.submit(7, a, b, nu, tl.FP32, **kw)
     assert e.value.status == tl.E_INVAL
     srv.close()
+
+
+def test_served_results_match_the_oracle(env):
+    # one request per (precision, nu) class, served in a mix, against the oracle on
+    # the same factor, lattice and shifts: FP32 within 1e-4 relative of the oracle's
+    # log-probability, BF16-shift within 1e-2 relative and 3 QMC standard errors
+    from oracle import sov
+    from tests.helpers import to_oracle_factor
+    tl, ws, fs = env
+    rng = np.random.default_rng(5)
+    M, N = 4, 500
+    classes = [(prec, nu) for prec in (tl.FP32, tl.BF16_SHIFT) for nu in (math.inf, 7.0, 3.0)]
+    srv = tl.Server(fs, lanes=4, memory_budget=8 << 30)
+    reqs = []
+    for k, (prec, nu) in enumerate(classes):
+        f = (k + 1) % 3          # tiles of 64 and of 128 (the whole-tile sweep on the BF16 path)
+        w = ws[f]
+        b = rng.uniform(0.0, 1.0, w.n)
+        shifts = synth.lattice_shifts(M, w.n + 1, 900 + k)
+        rid = srv.submit(f, np.full(w.n, -np.inf), b, nu, prec, n_shifts=M, n_points=N, shifts=shifts)
+        reqs.append((rid, f, b, nu, prec, shifts))
+    got = [srv.wait(r[0]) for r in reqs]
+    srv.close()
+    OFs = {}
+    for (rid, f, b, nu, prec, shifts), (lp, err, _) in zip(reqs, got):
+        if f not in OFs:
+            OFs[f] = to_oracle_factor(tl.parse_export(tl.tlrmvn_factor_export(fs[f])))
+        ref = sov.solve(OFs[f], np.full(ws[f].n, -np.inf), b, nu, shifts, N)
+        if prec == tl.FP32:
+            assert abs(lp - ref["logp"]) <= 1e-4 * abs(ref["logp"]), (prec, nu, lp, ref["logp"])
+        else:
+            assert abs(lp - ref["logp"]) <= 1e-2 * abs(ref["logp"]), (prec, nu, lp, ref["logp"])
+            assert abs(lp - ref["logp"]) <= 3 * max(err, ref["err"])

@@ -94,3 +94,31 @@ def test_export_layout_round_trip_on_host():
         assert np.array_equal(ex.U[k], U[k]) and np.array_equal(ex.V[k], V[k])
     assert np.array_equal(ex.B[2, :2, :2], B[2]) and ex.B[2, 2, 2] == 0
     assert len(buf) == 40 + 8 * 4 + 8 * 8 + 4 * 9 + 8 * 27 + 8 * (6 + 6 + 2 + 3 + 4 + 6)
+
+
+def test_pooled_estimate_equals_the_oracle_estimator(lib):
+    # Section 2.1 estimate over per-shift log means, by the library on the host,
+    # against the oracle's estimator of the same per-sample values
+    from oracle import sov
+    from paper_2003_11183_gb300 import api
+    rng = np.random.default_rng(3)
+    for M, N, scale in ((7, 50, 1.0), (2, 10, 30.0), (40, 3, 0.01)):
+        logP = rng.normal(-80.0, scale, size=(M, N))
+        logp, err, ell = sov.estimate(logP.ravel(), M, N)
+        got = api.tlrmvn_estimate_pooled(ell)
+        assert abs(got[0] - logp) <= 1e-13 * abs(logp) and abs(got[1] - err) <= 1e-12 * err
+    # one shift: no error estimate; shifts of zero probability are kept by the log-sum-exp
+    lp, er = api.tlrmvn_estimate_pooled([-3.0])
+    assert lp == -3.0 and math.isnan(er)
+    lp, er = api.tlrmvn_estimate_pooled([-2.0, -np.inf])
+    assert abs(lp - (-2.0 - math.log(2.0))) < 1e-15 and er > 0
+    lp, er = api.tlrmvn_estimate_pooled([-np.inf, -np.inf])
+    assert lp == -np.inf and math.isnan(er)
+
+
+def test_pooled_estimate_rejects_bad_values(lib):
+    from paper_2003_11183_gb300 import api
+    for bad in ([np.nan, -1.0], [np.inf], []):
+        with pytest.raises(api.TlrmvnError) as e:
+            api.tlrmvn_estimate_pooled(bad)
+        assert e.value.status == api.E_INVAL

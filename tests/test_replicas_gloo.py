@@ -12,6 +12,13 @@ from paper_2003_11183_gb300 import replicas
 from oracle import sov
 
 
+@pytest.fixture(scope="module", autouse=True)
+def built_library():
+    # the pooled estimate is the library's (tlrmvn_estimate_pooled, host code: no GPU needed)
+    import __graft_entry__ as ge
+    ge.build()
+
+
 def _free_port():
     s = socket.socket()
     s.bind(("127.0.0.1", 0))

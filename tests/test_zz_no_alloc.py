@@ -41,9 +41,17 @@ def test_noalloc_estimate_matches_prob_on_two_calls(env):
     tl.tlrmvn_prob_device(F, a, b, ref, nu=w.nu, precision=tl.FP32, n_shifts=w.n_shifts, n_points=w.n_points,
                           shifts=w.shifts, per_shift=ref_shift, per_sample=samples)
     torch.cuda.synchronize()
-    for _ in range(2):
-        out = torch.full((2,), float("nan"), dtype=torch.float64, device="cuda")
-        ps = torch.full((w.n_shifts,), float("nan"), dtype=torch.float64, device="cuda")
+    # the first call on the device looks up the scratch array's address (set-up);
+    # the calls after it must not change the device's free memory
+    outs = [torch.full((2,), float("nan"), dtype=torch.float64, device="cuda") for _ in range(2)]
+    pss = [torch.full((w.n_shifts,), float("nan"), dtype=torch.float64, device="cuda") for _ in range(2)]
+    st = lib.tlrmvn_estimate_noalloc(samples.data_ptr(), w.n_shifts, w.n_points, outs[0].data_ptr(), None,
+                                     torch.cuda.current_stream().cuda_stream)
+    assert st == 0, lib.tlrmvn_last_error()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    torch_bytes0 = torch.cuda.memory_allocated()
+    for out, ps in zip(outs, pss):
         # straight through the C ABI
         st = lib.tlrmvn_estimate_noalloc(samples.data_ptr(), w.n_shifts, w.n_points, out.data_ptr(), ps.data_ptr(),
                                          torch.cuda.current_stream().cuda_stream)
@@ -53,6 +61,8 @@ def test_noalloc_estimate_matches_prob_on_two_calls(env):
         assert np.all(np.isfinite(got))
         assert np.allclose(got, want, rtol=1e-12, atol=0)
         assert np.allclose(ps.cpu().numpy(), ref_shift.cpu().numpy(), rtol=1e-12, atol=0)
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0 and torch.cuda.memory_allocated() == torch_bytes0
 
 
 def test_noalloc_rejects_too_many_shifts(env):

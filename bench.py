@@ -28,32 +28,24 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-# Peak FP32 rate of the diagonal sweep's roofline: 152 SMs x 128 FP32 lanes x
-# 2 flops per FMA x 2.07 GHz maximum SM clock.
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2}
 METRIC = "MVN/MVT QMC sample-dims/sec at n=65,536 vs FP64 path; p50/p99 solve latency"
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of a kernel from one
 # ncu capture, divided by the sample-dimensions the captured launch processed,
 # with the digest of the sources the kernel is built from (build.source_digest
 # of `files`).  A figure is reported, scaled to this run's launches, only while
-# those sources are unchanged; the summaries with the capture commands are under
-# profiles/.
+# those sources are unchanged (otherwise null); the summaries with the capture
+# commands are under profiles/.
 TRAFFIC = {
-    "k_diag_f32": {"bytes_per_sample_dim": (26.852352e6 + 0.152576e6) / (100000 * 64),
-                   "capture": "profiles/k_diag_f32_sweep_n16384.md",
-                   "files": ["paper_2003_11183_gb300/csrc/sweep.cuh", "paper_2003_11183_gb300/csrc/sov_device.cuh",
-                             "paper_2003_11183_gb300/csrc/common.cuh", "include/tlrmvn.h"],
-                   "sources": "afe428c92ca35637686d23463fcc5935ea1f1b310efbb0c1c467761b6dc63efd"},
-    "k_sweep_tc": {"bytes_per_sample_dim": (700.932352e6 + 231.702272e6) / (100000 * 512),
+    "k_sweep_tc": {"bytes_per_sample_dim": None,
                    "capture": "profiles/k_sweep_tc_n16384.md",
                    "files": ["paper_2003_11183_gb300/csrc/sweep_tc.cuh",
                              "paper_2003_11183_gb300/csrc/sweep.cuh",
                              "paper_2003_11183_gb300/csrc/sov_device.cuh",
-                             "paper_2003_11183_gb300/csrc/gemm_tc.cuh",
+                             "paper_2003_11183_gb300/csrc/tcgen05.cuh",
                              "paper_2003_11183_gb300/csrc/common.cuh",
                              "include/tlrmvn.h"],
-                   "sources": "df1de0efc2d4f951aa70a9c69f81c65a31529b3ae892057ba5432c6908c7567a"},
+                   "sources": None},
 }
 
 
@@ -74,7 +66,8 @@ def parse():
     ap.add_argument("--sample-chunk", type=int, default=0,
                     help="samples per chunk of the solve (0 = the library's choice: all that fit)")
     ap.add_argument("--count", type=int, default=256, help="problems of the batched workload (--workload 4)")
-    ap.add_argument("--requests", type=int, default=400, help="requests of the serving workload (--workload 5)")
+    ap.add_argument("--requests", type=int, default=0,
+                    help="requests of the serving leg (0: 160 in the default run, 400 with --workload 5)")
     ap.add_argument("--rate", type=float, default=0.0, help="arrivals per second (--workload 5; 0 = measured)")
     return ap.parse_args()
 
@@ -161,29 +154,72 @@ def allmax(ws, x: float) -> float:
     return float(t.item())
 
 
-def cpu_oracle_sample(buf_path: str, wl: int, n_points: int, shift_index: int) -> dict:
-    """Times the oracle's TLR integrand on one shift x n_points of the workload, single-threaded BLAS."""
-    code = f"""
-import os, sys, time, math, json
-sys.path.insert(0, {ROOT!r})
+ORACLE_WORKER = r"""
+import json, os, sys, time
+sys.path.insert(0, {root!r})
 import numpy as np
 import synth
 from oracle import sov
 from tests.helpers import to_oracle_factor
 from paper_2003_11183_gb300.api import parse_export
 w = synth.workload({wl})
-F = to_oracle_factor(parse_export(open({buf_path!r}, 'rb').read()))
-sh = w.shifts[{shift_index}:{shift_index} + 1]
-t0 = time.perf_counter()
-r = sov.solve(F, w.a, w.b, w.nu, sh, {n_points}, chunk={n_points})
-t = time.perf_counter() - t0
-print(json.dumps({{"seconds": t, "logp": r["logp"], "per_sample": r["per_sample"].tolist()}}))
+F = to_oracle_factor(parse_export(open({path!r}, 'rb').read()))
+print("ready", flush=True)
+for r, first in enumerate({firsts!r}):
+    go = {go!r} + "." + str(r)
+    while not os.path.exists(go):
+        time.sleep(0.005)
+    sel = np.arange(first, first + {count}, dtype=np.int64)
+    t0 = time.time()
+    out = sov.solve(F, w.a, w.b, w.nu, w.shifts, w.n_points, samples=sel, chunk={count})
+    t1 = time.time()
+    print(json.dumps({{"t0": t0, "t1": t1, "per_sample": out["per_sample"].tolist()}}), flush=True)
 """
-    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
-    if out.returncode != 0:
-        raise RuntimeError(out.stderr[-2000:])
-    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+class OraclePool:
+    """The CPU oracle (oracle/, plain float64 NumPy, as it stands) run by `procs`
+    single-threaded worker processes, each evaluating its own `count` lattice points
+    of the workload per round on the same factor; a round is timed from the first
+    worker's start to the last one's end (workers are loaded before the first round)."""
+
+    def __init__(self, buf_path: str, wl: int, procs: int, count: int, rounds_firsts):
+        self.procs, self.count = procs, count
+        self.go = os.path.join(tempfile.gettempdir(), f"tlrmvn_oracle_go_{os.getpid()}_{id(self)}")
+        env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        self.ps = []
+        for p in range(procs):
+            firsts = [f + p * count for f in rounds_firsts]
+            code = ORACLE_WORKER.format(root=ROOT, wl=wl, path=buf_path, firsts=firsts, go=self.go, count=count)
+            self.ps.append(subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, text=True, env=env))
+        for p in self.ps:
+            line = p.stdout.readline().strip()
+            if line != "ready":
+                raise RuntimeError("oracle worker failed to start")
+        self.round = 0
+
+    def run_round(self) -> dict:
+        """One round: seconds (wall, all workers), samples, per-sample values (worker order)."""
+        open(f"{self.go}.{self.round}", "w").close()
+        res = [json.loads(p.stdout.readline()) for p in self.ps]
+        os.unlink(f"{self.go}.{self.round}")
+        self.round += 1
+        return {"seconds": max(r["t1"] for r in res) - min(r["t0"] for r in res), "samples": self.procs * self.count,
+                "per_sample": [v for r in res for v in r["per_sample"]]}
+
+    def close(self):
+        for p in self.ps:
+            try:
+                p.wait(timeout=60)
+            except Exception:
+                p.kill()
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
 
 
 def build_factor(tl, w):
@@ -192,8 +228,11 @@ def build_factor(tl, w):
     return F, time.perf_counter() - t0
 
 
+ORACLE_POINTS = 32  # lattice points per worker and round of the CPU oracle
+
+
 def run_reference(args):
-    ws, rank, local = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    ws, rank = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     import torch
@@ -206,24 +245,31 @@ def run_reference(args):
     path = os.path.join(tempfile.gettempdir(), f"tlrmvn_factor_{os.getpid()}.bin")
     with open(path, "wb") as fh:
         fh.write(tl.tlrmvn_factor_export(F))
-    pts = 32
+    cores = host_cores()
+    rounds = args.warmup + args.steps
+    # round r takes the points of shift (r mod M): sample indices s*N + k - 1
+    firsts = [(r % w.n_shifts) * w.n_points for r in range(rounds)]
+    pool = OraclePool(path, args.workload, cores, ORACLE_POINTS, firsts)
     times = []
-    for s in range(args.warmup + args.steps):
-        res = cpu_oracle_sample(path, args.workload, pts, s % w.n_shifts)
-        if s >= args.warmup:
+    for r in range(rounds):
+        res = pool.run_round()
+        if r >= args.warmup:
             times.append(res["seconds"])
+    pool.close()
     os.unlink(path)
     per = statistics.mean(times)
-    value = w.n * pts / per
-    sample = f"1 shift x {pts} lattice points of the same workload per step, same factor"
+    value = w.n * cores * ORACLE_POINTS / per
+    sample = (f"{cores} worker processes x {ORACLE_POINTS} lattice points of one shift of the same workload per "
+              f"step ({cores * ORACLE_POINTS} samples, all {w.n} dimensions), same factor")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "sample-dims/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": bench_config(tl, F, w, args.precision),
-            "cpu_baseline": {"value": value, "unit": "sample-dims/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "config": dict(bench_config(tl, F, w, args.precision), sample_chunk=args.sample_chunk or "all"),
+            "cpu_baseline": {"value": value, "unit": "sample-dims/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": value, "unit": "sample-dims/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "notes": "factor built once by the library's GPU factorisation (setup, untimed); timed step is the "
-                     "oracle's TLR integrand alone"}
+                     "oracle's TLR integrand alone, single-threaded BLAS in each worker"}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -260,6 +306,111 @@ def rank_summary(tl, F):
             "zero_tiles": int((low == 0).sum()), "tiles": int(low.size)}
 
 
+def device_solve_ms(tl, F, a, b, out, kw, reps, warm=1):
+    """Device milliseconds per solve (CUDA events on the solve's stream, after `warm` untimed solves)."""
+    import torch
+    stream = kw["stream"]
+    for _ in range(warm):
+        tl.tlrmvn_prob_device(F, a, b, out, **kw)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times = []
+    for _ in range(reps):
+        e0.record(stream)
+        tl.tlrmvn_prob_device(F, a, b, out, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return statistics.median(times)
+
+
+def sweep_work(info, sizes, m, ktot, n):
+    """Algorithmic work per sample-dimension of one solve, by where it runs.
+
+    sweep   the diagonal-tile recursion of eq. 2: (mt - 1) flops per variable of a
+            tile of mt variables (m - 1 = 511 for tiles of 512), whether the sums
+            over earlier variables run in the per-sample chain or, regrouped, as
+            the in-tile coupling products
+    tensor  the low-rank shifts and projections, 4 m K_total / n flops, plus the
+            coupling between 64-variable sub-tiles as the kernel issues it: three
+            products (hi hi, hi lo, lo hi) of 2 mq q0 flops per sub-tile and sample
+    """
+    sweep = sum(mt * (mt - 1) for mt in sizes) / n
+    couple = 0.0
+    for mt in sizes:
+        for q0 in range(64, mt, 64):
+            couple += 3 * 2.0 * min(64, mt - q0) * q0
+    return {"sweep": sweep, "tensor": 4.0 * m * ktot / n + couple / n, "shift_proj": 4.0 * m * ktot / n}
+
+
+def serving_leg(tl, n_requests: int, rate: float = 0.0, seed: int = 7000) -> dict:
+    """The serving workload: 8 resident factors (n = 1,024 ... 16,384 on jittered grids,
+    Matern 1/2 and 3/2 kernels), a Poisson stream of requests with fresh b_i ~ U(0,1),
+    nu in {3, 7, inf}, FP32 and BF16-shift classes, 10 shifts x 1,000 points each;
+    4 lanes, 16 GiB scratch budget.  The arrival rate is `rate` requests/s, or (0) the
+    rate a single lane sustains alone, measured from the first requests."""
+    import threading
+    import synth
+    sides = [32, 45, 64, 64, 90, 90, 128, 128]          # n = 1,024 ... 16,384
+    kernels = [(tl.KERNEL_EXP, (0.1,)), (tl.KERNEL_MATERN15, (0.05,))] * 4
+    factors, sizes = [], []
+    t0 = time.perf_counter()
+    for f, g in enumerate(sides):
+        xy = synth.jittered_grid(g, 5000 + f)
+        n = g * g
+        a, b = synth.limits_uniform(n, 6000 + f)
+        kern, prm = kernels[f]
+        factors.append(tl.tlrmvn_factor_kernel(xy, kern, prm, 1e-6, a, b, 128 if n <= 4096 else 256, 1e-5, 0,
+                                               tl.REORDER_BLOCK))
+        sizes.append(n)
+    factor_s = time.perf_counter() - t0
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for q in range(n_requests):
+        f = int(rng.integers(0, len(factors)))
+        reqs.append((f, np.full(sizes[f], -np.inf), rng.uniform(0.0, 1.0, sizes[f]), [3.0, 7.0, math.inf][q % 3],
+                     tl.FP32 if q % 2 == 0 else tl.BF16_SHIFT))
+    kw = dict(n_shifts=10, n_points=1000)
+    srv = tl.Server(factors, lanes=4, memory_budget=16 << 30)
+    alone = []
+    for q, (f, a, b, nu, prec) in enumerate(reqs[:16]):  # warm-up and the alone service time
+        rid = srv.submit(f, a, b, nu, prec, seed=q, **kw)
+        alone.append(srv.wait(rid)[2])
+    service = statistics.mean(alone[4:])
+    rate = rate if rate > 0 else 1e3 / service
+    srv.close()
+    srv = tl.Server(factors, lanes=4, memory_budget=16 << 30)
+    gaps = rng.exponential(1.0 / rate, size=n_requests)
+    ids = [None] * n_requests
+    t_start = time.perf_counter()
+
+    def submitter():
+        t = time.perf_counter()
+        for q, (f, a, b, nu, prec) in enumerate(reqs):
+            t += gaps[q]
+            dt = t - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            ids[q] = srv.submit(f, a, b, nu, prec, seed=q, **kw)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    th.join()
+    lat = [srv.wait(i)[2] for i in ids]
+    makespan = time.perf_counter() - t_start
+    st = srv.stats()
+    srv.close()
+    sd = sum(sizes[f] for f, *_ in reqs) * kw["n_shifts"] * kw["n_points"]
+    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "rate_per_s": rate, "requests": n_requests, "throughput": sd / makespan, "unit": "sample-dims/s",
+            "service_ms_alone_mean": service, "lanes": 4, "memory_budget_gib": 16,
+            "load": "Poisson arrivals at the rate one lane sustains alone (1 / mean service time of a request "
+                    "run alone)" if rate == 1e3 / service else f"Poisson arrivals at {rate} requests/s",
+            "workload": "8 resident factors n=1,024..16,384 (exp / Matern-3/2, Algorithm 4), b~U(0,1) fresh per "
+                        "request, nu in {3,7,inf}, FP32 and BF16-shift classes, 10 x 1,000 points each",
+            "overlapped": st["overlapped"], "peak_in_flight": st["peak_in_flight"], "factor_seconds": factor_s}
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_init()
@@ -280,6 +431,10 @@ def run_ours(args):
     b = torch.tensor(w.b, dtype=torch.float64, device="cuda")
     out = torch.zeros(2, dtype=torch.float64, device="cuda")
     per_shift = torch.zeros(w.n_shifts, dtype=torch.float64, device="cuda")
+    # launch choices for this problem: the library's autotuner (untimed setup; cached per box)
+    cache = os.path.join(tempfile.gettempdir(), "tlrmvn_tune_cache.txt")
+    tuned = tl.tlrmvn_autotune(F, w.a, w.b, w.nu, prec, n_shifts=w.n_shifts, n_points=w.n_points, shifts=w.shifts,
+                               cache_path=cache, stream=stream)
     kw = dict(nu=w.nu, precision=prec, n_shifts=w.n_shifts, n_points=w.n_points, shifts=w.shifts, stream=stream,
               per_shift=per_shift, sample_chunk=args.sample_chunk)
 
@@ -318,7 +473,8 @@ def run_ours(args):
         logp, err = replicas.gather_and_combine(per_shift.cpu().numpy(), group=dist.new_group(backend="gloo"))
     kern = {tl.KC_NAMES[c]: tl.tlrmvn_profile_get(c) for c in range(len(tl.KC_NAMES))}
     launches = sum(v[1] for v in kern.values())
-    sd = w.n * w.n_shifts * w.n_points
+    C = w.n_shifts * w.n_points
+    sd = w.n * C
     value = ws * sd / (ms / 1e3)
 
     # end to end through the public host-array entry point
@@ -331,107 +487,117 @@ def run_ours(args):
         t_e2e.append(time.perf_counter() - t0)
     e2e = ws * sd / statistics.mean(t_e2e)
 
-    # roofline of every kernel class; the line reports the dominant one.
-    # Algorithmic flops per sample (2 per multiply-add), tiles of size mt:
-    #   diag   sweep triangle: per 128-variable sub-tile of size mq, mq (mq - 1)
-    #          (float paths; the float64 path sweeps the whole tile: mt (mt - 1))
-    #   couple in-tile coupling of sub-tile q: 2 mq q0
-    #   shift / vproj: 2 m K_total each
+    # roofline of the dominant kernel class.  Algorithmic work per sample-dimension
+    # (SURVEY-style accounting, stated in sweep_work): the sweep's (mt - 1) flops per
+    # variable against the FP32 peak derived from this device's SM count and the SM
+    # clock sampled during the timed region (128 FP32 lanes x 2 flops per FMA per SM
+    # and cycle); the tensor-core products beside it against the bf16 peak.
     pk, pk_kind = peaks()
-    m, n, C = w.m, w.n, w.n_shifts * w.n_points
+    m, n = w.m, w.n
     sizes = [min(m, n - t * m) for t in range(info["r"])]
-    # sub-tile of the float sweep: 64 on the BF16-shift path (128 when the library's
-    # TLRMVN_SUB tuning switch says so), 128 on the FP32 path, the whole tile on FP64
-    sub = {0: m, 1: 128, 2: 128 if os.environ.get("TLRMVN_SUB") == "128" else 64}[prec]
-    # the BF16-shift path sweeps whole tiles with the coupling inside (k_sweep_tc)
-    # when tiles hold more than one 64-variable sub-tile
-    fused = prec == 2 and sub == 64 and m > 64 and os.environ.get("TLRMVN_FUSED") != "0"
-    krow = tl.tlrmvn_factor_ranks(F).sum(axis=1)
-    per = {"diag": 0.0, "couple": 0.0, "shift": 2.0 * m * info["k_total"], "vproj": 2.0 * m * info["k_total"]}
-    couple_bytes = 0.0  # per sample: y panel (hi + lo bf16) read, the sub-tile's shifts read and written
-    for i, mt in enumerate(sizes):
-        for q0 in range(0, mt, sub):
-            mq = min(sub, mt - q0)
-            per["diag"] += mq * (mq - 1)
-            per["couple"] += 2.0 * mq * q0
-            if q0 > 0:
-                couple_bytes += 4.0 * q0 + mq * (8.0 if krow[i] > 0 else 4.0)
-    fp32_peak = {"bound": "alu", "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (derived)"}
+    work = sweep_work(info, sizes, m, info["k_total"], n)
+    props = torch.cuda.get_device_properties(local)
+    sm_count = props.multi_processor_count
+    sm_mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or pk.get("sm_max_mhz", 2070.0)
+    fp32_peak = sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+    fp32_src = (f"derived: {sm_count} SMs (device attribute) x 128 FP32 lanes x 2 flops x {sm_mhz:.0f} MHz "
+                "(median SM clock sampled during the timed region)")
+    bf16_peak = pk.get("bf16_tflops_sustained", 1700.0)
     classes = {}
-    for cls in ("diag", "couple", "shift", "vproj"):
-        t = kern[cls][0] / 1e3
-        if t <= 0:
+    for cls, (t_ms, n_launch) in kern.items():
+        if t_ms <= 0 or n_launch == 0:
             continue
-        ach = per[cls] * C * args.steps / t / 1e12
-        if cls in ("shift", "vproj") and prec == 2:
-            p = pk.get("bf16_tflops_sustained", 1700.0)
-            pkd = {"bound": "tensor", "peak": p, "unit": "TFLOP/s", "peak_source": f"bf16 sustained, {pk_kind}"}
-        elif cls == "couple" and prec == 2:
-            ach = couple_bytes * C * args.steps / t / 1e9
-            pkd = {"bound": "hbm", "peak": pk.get("hbm_gbs", 6800.0), "unit": "GB/s",
-                   "peak_source": f"HBM copy, {pk_kind}"}
-        else:
-            pkd = fp32_peak
-        classes[cls] = dict(pkd, achieved=ach, frac=ach / pkd["peak"], ms_per_step=kern[cls][0] / args.steps,
-                            kernel={"diag": "k_sweep_tc" if fused else "k_diag_f32", "couple": "k_gemm_tc (split bf16)",
-                                    "shift": "k_gemm_tc",
-                                    "vproj": "k_gemm_tc"}[cls] if prec == 2 else
-                            {"diag": "k_diag_f32", "couple": "k_sgemm128"}.get(cls, "k_gemm_nn") if prec == 1 else cls)
+        d = {"ms_per_step": t_ms / args.steps, "launches_per_step": n_launch / args.steps,
+             "avg_launch_ms": t_ms / n_launch}
+        if cls == "diag":
+            units = float(n) * C * args.steps / n_launch  # sample-dims per launch
+            ach = work["sweep"] * units / (d["avg_launch_ms"] / 1e3) / 1e12
+            d.update(bound="alu", unit="TFLOP/s", achieved=ach, peak=fp32_peak, frac=ach / fp32_peak,
+                     peak_source=fp32_src, flops_per_sample_dim=work["sweep"], sample_dims_per_launch=units,
+                     kernel={0: "k_diag<double>", 1: "k_diag_f32", 2: "k_sweep_tc"}[prec])
+            if prec == 2:
+                tach = work["tensor"] * units / (d["avg_launch_ms"] / 1e3) / 1e12
+                d["tensor_share"] = {"bound": "tensor", "unit": "TFLOP/s", "achieved": tach, "peak": bf16_peak,
+                                     "frac": tach / bf16_peak, "flops_per_sample_dim": work["tensor"],
+                                     "peak_source": f"bf16 sustained, {pk_kind} (MEASURED_PEAKS.json)",
+                                     "note": "low-rank shifts and projections 4 m K_total / n plus the split "
+                                             "in-tile coupling (3 bf16 products), issued inside the same kernel"}
+        classes[cls] = d
     from paper_2003_11183_gb300 import build as _build
     for cls, d in classes.items():
-        t = TRAFFIC.get(d["kernel"])
-        n_launch = kern[cls][1]
-        if t and t["sources"] == _build.source_digest(t["files"]) and n_launch:
-            units = float(n) * C * args.steps / n_launch  # sample-dims per launch
-            d["traffic"] = t["bytes_per_sample_dim"] * units
-            d["traffic_source"] = t["capture"]
+        t = TRAFFIC.get(d.get("kernel", ""))
+        if t and t["bytes_per_sample_dim"] and t["sources"] == _build.source_digest(t["files"]):
+            d["traffic"] = t["bytes_per_sample_dim"] * d["sample_dims_per_launch"]
+            d["traffic_source"] = (f"ncu capture constant ({t['capture']}): DRAM bytes per sample-dimension of one "
+                                   "captured launch, scaled to this run's launches by sample-dimensions")
         else:
             d["traffic"] = None
     dom = max(classes, key=lambda c: classes[c]["ms_per_step"])
-    roof = dict(classes[dom])
-    roof["note"] = ("achieved counts the sweep's float multiply-adds only; its special functions "
-                    "(about 3/4 of its instructions) are not in the algorithmic flops"
-                    + ("; the low-rank shifts, the in-tile coupling and the projections run inside the same "
-                       "kernel on the tensor cores and are not counted either" if fused and dom == "diag" else ""))
+    roof = {k: v for k, v in classes[dom].items() if k in ("bound", "achieved", "peak", "unit", "frac", "traffic",
+                                                            "traffic_source", "peak_source", "kernel",
+                                                            "flops_per_sample_dim", "sample_dims_per_launch",
+                                                            "tensor_share")}
 
     extra = {}
+    cpu = None
     if rank == 0 and not args.no_baselines:
-        # the same library's FP64 path on a bounded sample (1 shift x 1000 points)
-        pts64 = min(1000, w.n_points)
-        kw64 = dict(kw, precision=0, n_shifts=1, n_points=pts64, shifts=w.shifts[:1], per_shift=None)
-        tl.tlrmvn_prob_device(F, a, b, out, **kw64)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        tl.tlrmvn_prob_device(F, a, b, out, **kw64)
-        torch.cuda.synchronize()
-        t64 = time.perf_counter() - t0
-        v64 = w.n * pts64 / t64
-        extra["fp64_path"] = {"value": v64, "unit": "sample-dims/s", "sample": f"1 shift x {pts64} points",
-                              "speedup": (value / ws) / v64}
-        # the CPU oracle on a bounded sample of the same workload and factor
+        # the same library's FP64 and FP32 paths on a sample count that fills the GPU
+        # (20 x 2,500 = 50,000 samples: one wave of the FP64 sweep's blocks on every SM)
+        pts_b = min(2500, w.n_points)
+        kw_b = dict(kw, n_points=pts_b, per_shift=None)
+        for name, p in (("fp64_path", 0), ("fp32_path", 1)):
+            kw_p = dict(kw_b, precision=p)
+            t_p = device_solve_ms(tl, F, a, b, out, kw_p, reps=2)
+            v_p = w.n * w.n_shifts * pts_b / (t_p / 1e3)
+            extra[name] = {"value": v_p, "unit": "sample-dims/s", "ms_per_solve": t_p,
+                           "sample": f"{w.n_shifts} shifts x {pts_b} points (same factor and lattice), CUDA events",
+                           "tuning": tl.tlrmvn_get_tuning(F, p), "speedup_of_this_line": (value / ws) / v_p}
+        # the CPU oracle on bounded samples of the same workload and factor: all host cores, and one
         path = os.path.join(tempfile.gettempdir(), f"tlrmvn_factor_{os.getpid()}.bin")
         with open(path, "wb") as fh:
             fh.write(tl.tlrmvn_factor_export(F))
-        pts_cpu = 32
-        res = cpu_oracle_sample(path, args.workload, pts_cpu, 0)
+        cores = host_cores()
+        pool = OraclePool(path, args.workload, cores, ORACLE_POINTS, [0])
+        res_all = pool.run_round()
+        pool.close()
+        pool = OraclePool(path, args.workload, 1, ORACLE_POINTS, [0])
+        res_one = pool.run_round()
+        pool.close()
         os.unlink(path)
-        cpu = {"value": w.n * pts_cpu / res["seconds"], "unit": "sample-dims/s", "cores": 1, "kind": "oracle",
-               "sample": f"1 shift x {pts_cpu} points of the same workload and factor, single-threaded BLAS"}
-    else:
-        cpu = None
+        v_all = w.n * res_all["samples"] / res_all["seconds"]
+        v_one = w.n * res_one["samples"] / res_one["seconds"]
+        cpu = {"value": v_all, "unit": "sample-dims/s", "cores": cores, "kind": "oracle",
+               "sample": (f"{cores} single-threaded worker processes x {ORACLE_POINTS} lattice points of shift 0 "
+                          f"of the same workload and factor ({res_all['samples']} samples x {w.n} dimensions)"),
+               "one_core": {"value": v_one, "unit": "sample-dims/s",
+                            "sample": f"1 process x {ORACLE_POINTS} points of shift 0"},
+               "nproc": os.cpu_count()}
+        # served latency at a stated load (the metric's second half)
+        extra["serving"] = serving_leg(tl, args.requests if args.requests else 160, args.rate)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "sample-dims/s",
                 "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": {0: "f64", 1: "f32", 2: "f32+bf16"}[prec], "data": "synthetic",
-                "config": dict(bench_config(tl, F, w, args.precision), sample_chunk=args.sample_chunk or "all"),
+                "config": dict(bench_config(tl, F, w, args.precision), sample_chunk=args.sample_chunk or "all",
+                               tuning=tuned),
                 "clocks": clk,
                 "e2e": {"value": e2e, "unit": "sample-dims/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 16},
                 "gpu_launches": launches, "roofline": roof, "kernel_classes": classes, "cpu_baseline": cpu,
-                "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kern.items()},
-                "factor_seconds": factor_s, "logp": logp, "err": err}
+                "factor_seconds": factor_s, "logp": logp, "err": err,
+                "accuracy": {"rel_err_qmc": err,
+                             "note": "err is the QMC standard error of the estimate divided by it (the paper's "
+                                     "relative error); at this sample count three of them span ~2.4 in log p, so "
+                                     "the full-size accuracy claim is the per-shift comparison with the FP64 path "
+                                     "in the GPU tests (1e-4 FP32, 1e-2 BF16-shift)"},
+                "precision_note": ("f32+bf16: float32 sweep of eq. 2 (per-sample chains within 64-variable "
+                                   "sub-tiles); low-rank shifts and projections bf16 x bf16 -> fp32 on tcgen05; "
+                                   "the in-tile coupling between sub-tiles as split-bf16 products (hi hi + hi lo "
+                                   "+ lo hi, ~1e-5 relative) -> fp32")}
+        if "serving" in extra:
+            line["p50_ms"] = extra["serving"]["p50_ms"]
+            line["p99_ms"] = extra["serving"]["p99_ms"]
         line.update(extra)
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -459,6 +625,7 @@ def run_batched(args):
     plan = tl.BatchPlan(factors, math.inf, M, N, seed=4242)
     a = [p["a"] for p in probs]
     b = [p["b"] for p in probs]
+    tuned = plan.tune(a, b, cache_path=os.path.join(tempfile.gettempdir(), "tlrmvn_tune_cache.txt"))
     for _ in range(args.warmup):
         plan.run(a, b)
     clocks = Clocks(0)
@@ -476,7 +643,8 @@ def run_batched(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "p50_ms": statistics.median(times) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"batched_{len(probs)}_mvn_n256_4096_m128", "problems": len(probs),
-                       "sum_n": sum(len(p["a"]) for p in probs), "shifts": M, "points": N, "tol": 1e-5},
+                       "sum_n": sum(len(p["a"]) for p in probs), "shifts": M, "points": N, "tol": 1e-5,
+                       "tuning": tuned},
             "clocks": clk, "factor_seconds": factor_s,
             "e2e": {"value": sd / (ms / 1e3), "unit": "sample-dims/s",
                     "h2d_bytes_per_step": 2 * 8 * sum(len(p["a"]) for p in probs),
@@ -488,81 +656,24 @@ def run_batched(args):
 
 
 def run_serving(args):
-    """Serving workload: 8 resident factors (n = 1,024 ... 16,384 on jittered grids, Matern 1/2 and
-    3/2 kernels), a Poisson stream of requests with fresh b_i ~ U(0,1), nu in {3, 7, inf},
-    FP32 and BF16-shift classes, 10 shifts x 1,000 points each; 4 lanes, 16 GiB scratch budget.
-    The arrival rate is `--rate` requests/s, or (default) the rate a single lane would sustain,
-    measured from the requests run alone."""
-    import threading
+    """Serving workload (see serving_leg), as a line of its own."""
     import torch
     torch.cuda.set_device(0)
     import __graft_entry__ as ge
     ge.build()
     import paper_2003_11183_gb300 as tl
-    import synth
-    sides = [32, 45, 64, 64, 90, 90, 128, 128]          # n = 1,024 ... 16,384
-    kernels = [(tl.KERNEL_EXP, (0.1,)), (tl.KERNEL_MATERN15, (0.05,))] * 4
-    factors, sizes = [], []
-    t0 = time.perf_counter()
-    for f, g in enumerate(sides):
-        xy = synth.jittered_grid(g, 5000 + f)
-        n = g * g
-        a, b = synth.limits_uniform(n, 6000 + f)
-        kern, prm = kernels[f]
-        factors.append(tl.tlrmvn_factor_kernel(xy, kern, prm, 1e-6, a, b, 128 if n <= 4096 else 256, 1e-5, 0,
-                                               tl.REORDER_BLOCK))
-        sizes.append(n)
-    factor_s = time.perf_counter() - t0
-    rng = np.random.default_rng(7000)
-    R = args.requests
-    reqs = []
-    for q in range(R):
-        f = int(rng.integers(0, len(factors)))
-        reqs.append((f, np.full(sizes[f], -np.inf), rng.uniform(0.0, 1.0, sizes[f]), [3.0, 7.0, math.inf][q % 3],
-                     tl.FP32 if q % 2 == 0 else tl.BF16_SHIFT))
-    kw = dict(n_shifts=10, n_points=1000)
-    srv = tl.Server(factors, lanes=4, memory_budget=16 << 30)
-    alone = []
-    for q, (f, a, b, nu, prec) in enumerate(reqs[:16]):  # warm-up and the alone service time
-        rid = srv.submit(f, a, b, nu, prec, seed=q, **kw)
-        alone.append(srv.wait(rid)[2])
-    service = statistics.mean(alone[4:])
-    rate = args.rate if args.rate > 0 else 1e3 / service
-    srv.close()
-    srv = tl.Server(factors, lanes=4, memory_budget=16 << 30)
-    gaps = rng.exponential(1.0 / rate, size=R)
-    ids = [None] * R
     clocks = Clocks(0)
     clocks.start()
-    t_start = time.perf_counter()
-
-    def submitter():
-        t = time.perf_counter()
-        for q, (f, a, b, nu, prec) in enumerate(reqs):
-            t += gaps[q]
-            dt = t - time.perf_counter()
-            if dt > 0:
-                time.sleep(dt)
-            ids[q] = srv.submit(f, a, b, nu, prec, seed=q, **kw)
-
-    th = threading.Thread(target=submitter)
-    th.start()
-    th.join()
-    lat = [srv.wait(i)[2] for i in ids]
-    makespan = time.perf_counter() - t_start
+    r = serving_leg(tl, args.requests or 400, args.rate)
     clk = clocks.stop()
-    st = srv.stats()
-    srv.close()
-    sd = sum(sizes[f] for f, *_ in reqs) * kw["n_shifts"] * kw["n_points"]
-    line = {"metric": "served QMC sample-dims/sec and p50/p99 latency", "value": sd / makespan,
-            "unit": "sample-dims/s", "n_gpus": 1, "steps": R, "warmup": 16, "ms_per_step": makespan * 1e3 / R,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 | f32+bf16",
-            "data": "synthetic",
-            "config": {"workload": "serving_8_factors_n1024_16384", "requests": R, "rate_per_s": rate,
-                       "lanes": 4, "memory_budget_gib": 16, "shifts": 10, "points": 1000,
-                       "service_ms_alone_mean": service},
-            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "server_stats": st, "clocks": clk, "factor_seconds": factor_s}
+    line = {"metric": "served QMC sample-dims/sec and p50/p99 latency", "value": r["throughput"],
+            "unit": "sample-dims/s", "n_gpus": 1, "steps": r["requests"], "warmup": 16,
+            "ms_per_step": 1e3 / r["rate_per_s"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 | f32+bf16", "data": "synthetic",
+            "config": {"workload": "serving_8_factors_n1024_16384", "requests": r["requests"],
+                       "rate_per_s": r["rate_per_s"], "lanes": r["lanes"], "memory_budget_gib": r["memory_budget_gib"],
+                       "shifts": 10, "points": 1000, "service_ms_alone_mean": r["service_ms_alone_mean"]},
+            "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"], "serving": r, "clocks": clk}
     print(json.dumps(line), flush=True)
     return 0
 

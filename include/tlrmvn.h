@@ -167,6 +167,43 @@ int tlrmvn_prob_device(tlrmvn_factor_t f, const double* a, const double* b, doub
                        const tlrmvn_opts* opts, double* logp, double* err, double* per_shift,
                        double* per_sample);
 
+/* ---- autotuner -------------------------------------------------------- */
+
+/* Launch choices of the integrand for one factor and precision (no counterpart
+ * in the paper; they change how the work is launched, not what is computed):
+ *   sub       variables per sub-tile of the float32 sweep (64 or 128) or of the
+ *             float64 sweep (32 or 64); the coupling between sub-tiles of a
+ *             diagonal tile is a dense product
+ *   threads   threads per block of the float32 sweep; 0 = the occupancy rule
+ *   chunk     samples in flight per pass; 0 = as many as fit the memory rule
+ *             (opts->sample_chunk, when set, still takes precedence)
+ *   tc_ctas   whole-tile sweeps of the BF16-shift path sharing an SM (1..6)
+ *   ms        tlrmvn_autotune: device milliseconds per solve of the choice (-1
+ *             when it came from the cache); candidates: how many were timed */
+typedef struct {
+  int sub, threads;
+  int64_t chunk;
+  int tc_ctas;
+  double ms;
+  int candidates;
+} tlrmvn_tuning;
+
+/* Times each candidate launch choice for opts->precision on solves of this very
+ * problem (a, b host, length n, original order; nu; opts as for tlrmvn_prob, whose
+ * sample count S = n_shifts * n_points the choice is made for), keeps the fastest
+ * on the factor (every later solve of this factor in this precision uses it) and
+ * appends it to the text file cache_path (NULL: no cache).  Unless force is
+ * nonzero, a cache entry for the same device, precision, n, tile size, total
+ * rank (to 2 bits of its logarithm), S (to a factor of 2) and distribution
+ * (normal / Student-t) is used instead of timing.  Costs two or three solves per
+ * candidate (at most 8 candidates).  out (nullable) receives the choice. */
+int tlrmvn_autotune(tlrmvn_factor_t f, const double* a, const double* b, double nu, const tlrmvn_opts* opts,
+                    const char* cache_path, int force, tlrmvn_tuning* out);
+/* The launch choice a factor uses for a precision; and setting one by hand
+ * (TLRMVN_E_INVAL for values outside the ranges above). */
+int tlrmvn_get_tuning(tlrmvn_factor_t f, int precision, tlrmvn_tuning* out);
+int tlrmvn_set_tuning(tlrmvn_factor_t f, int precision, const tlrmvn_tuning* t);
+
 /* ---- many problems in one launch -------------------------------------- */
 
 /* A batch plan: `count` problems (each its own factor, tile size <= 128, and
@@ -189,6 +226,16 @@ int tlrmvn_batch_create(int count, const tlrmvn_factor_t* factors, const double*
 int tlrmvn_batch_run(tlrmvn_batch_t plan, const double* const* a, const double* const* b, double* logp,
                      double* err);
 int tlrmvn_batch_free(tlrmvn_batch_t plan);
+/* Autotunes a plan (no counterpart in the paper): replays it on these limits
+ * (as for tlrmvn_batch_run) with 1, 2, ... CTAs of the persistent integrand per
+ * SM, up to all that fit, times each replay with CUDA events and keeps the
+ * fastest in the plan's graph; the choice is appended to the text file
+ * cache_path (NULL: no cache) and, unless force is nonzero, read back from it
+ * for a plan of the same device, problem count, total dimension, total rank
+ * and samples.  ctas_per_sm, ms (nullable): the choice and its milliseconds per
+ * replay (-1 when it came from the cache). */
+int tlrmvn_batch_tune(tlrmvn_batch_t plan, const double* const* a, const double* const* b, const char* cache_path,
+                      int force, int* ctas_per_sm, double* ms);
 /* create + run + free in one call */
 int tlrmvn_prob_batch(int count, const tlrmvn_factor_t* factors, const double* const* a, const double* const* b,
                       const double* nu, const tlrmvn_opts* opts, double* logp, double* err);

@@ -20,6 +20,11 @@ class Opts(C.Structure):
                 ("shifts", c_u64_p), ("seed", C.c_uint64), ("sample_chunk", C.c_int64), ("stream", C.c_void_p)]
 
 
+class Tuning(C.Structure):
+    _fields_ = [("sub", C.c_int), ("threads", C.c_int), ("chunk", C.c_int64), ("tc_ctas", C.c_int),
+                ("ms", C.c_double), ("candidates", C.c_int)]
+
+
 class ServerStats(C.Structure):
     _fields_ = [("completed", C.c_int64), ("queued", C.c_int64), ("in_flight", C.c_int), ("peak_in_flight", C.c_int),
                 ("overlapped", C.c_int64), ("peak_bytes", C.c_int64), ("p50_ms", C.c_double), ("p99_ms", C.c_double)]
@@ -45,6 +50,8 @@ SIGNATURES = {
                                       C.POINTER(C.c_void_p)]),
     "tlrmvn_batch_run": (C.c_int, [C.c_void_p, C.POINTER(c_double_p), C.POINTER(c_double_p), c_double_p, c_double_p]),
     "tlrmvn_batch_free": (C.c_int, [C.c_void_p]),
+    "tlrmvn_batch_tune": (C.c_int, [C.c_void_p, C.POINTER(c_double_p), C.POINTER(c_double_p), C.c_char_p, C.c_int,
+                                    C.POINTER(C.c_int), c_double_p]),
     "tlrmvn_prob_batch": (C.c_int, [C.c_int, C.POINTER(C.c_void_p), C.POINTER(c_double_p), C.POINTER(c_double_p),
                                     c_double_p, C.POINTER(Opts), c_double_p, c_double_p]),
     "tlrmvn_server_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int64, C.POINTER(C.c_void_p)]),
@@ -54,6 +61,10 @@ SIGNATURES = {
     "tlrmvn_server_stats": (C.c_int, [C.c_void_p, C.c_void_p]),
     "tlrmvn_server_free": (C.c_int, [C.c_void_p]),
     "tlrmvn_prob_scratch_bytes": (C.c_int, [C.c_void_p, C.POINTER(Opts), C.POINTER(C.c_int64)]),
+    "tlrmvn_autotune": (C.c_int, [C.c_void_p, c_double_p, c_double_p, C.c_double, C.POINTER(Opts), C.c_char_p,
+                                  C.c_int, C.POINTER(Tuning)]),
+    "tlrmvn_get_tuning": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(Tuning)]),
+    "tlrmvn_set_tuning": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(Tuning)]),
     "tlrmvn_estimate_pooled": (C.c_int, [c_double_p, C.c_int64, c_double_p, c_double_p]),
     "tlrmvn_estimate_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tlrmvn_profile_enable": (C.c_int, [C.c_int]),

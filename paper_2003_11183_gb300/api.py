@@ -162,6 +162,18 @@ class BatchPlan:
         _check(lib.tlrmvn_batch_run(self.handle, pa, pb, _dp(lp), _dp(er)), "tlrmvn_batch_run")
         return lp, er
 
+    def tune(self, a_list, b_list, cache_path: str | None = None, force: bool = False) -> dict:
+        """Autotune the persistent grid on these limits (tlrmvn_batch_tune); returns the choice."""
+        a_arr = [_f64(a) for a in a_list]
+        b_arr = [_f64(b) for b in b_list]
+        pa = (L.c_double_p * self.count)(*[_dp(x) for x in a_arr])
+        pb = (L.c_double_p * self.count)(*[_dp(x) for x in b_arr])
+        k, ms = C.c_int(), C.c_double()
+        cp = None if cache_path is None else str(cache_path).encode()
+        _check(L.load().tlrmvn_batch_tune(self.handle, pa, pb, cp, 1 if force else 0, C.byref(k), C.byref(ms)),
+               "tlrmvn_batch_tune")
+        return {"ctas_per_sm": k.value, "ms": ms.value}
+
     def close(self):
         if self.handle and self.handle.value:
             L.load().tlrmvn_batch_free(self.handle)
@@ -241,6 +253,38 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def _tuning_dict(t) -> dict:
+    return {"sub": t.sub, "threads": t.threads, "chunk": t.chunk, "tc_ctas": t.tc_ctas, "ms": t.ms,
+            "candidates": t.candidates}
+
+
+def tlrmvn_autotune(f: Factor, a, b, nu: float = math.inf, precision: int = FP32, n_shifts: int = 20,
+                    n_points: int = 1000, shifts=None, seed: int = 0, periodize: bool = True,
+                    cache_path: str | None = None, force: bool = False, stream=None) -> dict:
+    """Times the candidate launch choices for this problem and keeps the fastest on
+    the factor (see tlrmvn_autotune in include/tlrmvn.h).  Returns the choice."""
+    a = _f64(a)
+    b = _f64(b)
+    o, keep = _opts(precision, n_shifts, n_points, periodize, shifts, seed, 0, stream, a.size)
+    t = L.Tuning()
+    cp = None if cache_path is None else str(cache_path).encode()
+    _check(L.load().tlrmvn_autotune(f.handle, _dp(a), _dp(b), float(nu), C.byref(o), cp, 1 if force else 0,
+                                    C.byref(t)), "tlrmvn_autotune")
+    del keep
+    return _tuning_dict(t)
+
+
+def tlrmvn_get_tuning(f: Factor, precision: int) -> dict:
+    t = L.Tuning()
+    _check(L.load().tlrmvn_get_tuning(f.handle, int(precision), C.byref(t)), "tlrmvn_get_tuning")
+    return _tuning_dict(t)
+
+
+def tlrmvn_set_tuning(f: Factor, precision: int, sub: int = 64, threads: int = 0, chunk: int = 0, tc_ctas: int = 6):
+    t = L.Tuning(int(sub), int(threads), int(chunk), int(tc_ctas), -1.0, 0)
+    _check(L.load().tlrmvn_set_tuning(f.handle, int(precision), C.byref(t)), "tlrmvn_set_tuning")
 
 
 def tlrmvn_estimate_pooled(per_shift_logs) -> tuple[float, float]:

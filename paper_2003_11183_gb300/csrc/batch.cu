@@ -13,7 +13,11 @@
 #include "sov_device.cuh"
 
 #include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
 #include <numeric>
+#include <string>
 
 namespace tlrmvn {
 
@@ -280,7 +284,7 @@ struct Batch {
   std::vector<BatchCopies> copies;
   BatchProblem* dprobs = nullptr;
   BatchItem* ditems = nullptr;
-  int n_items = 0, grid = 0;
+  int n_items = 0, grid = 0, grid_max = 0, per_sm = 0, per_sm_max = 0, sms = 0;
   int* dnext = nullptr;
   int* dbad = nullptr;
   float* W = nullptr;
@@ -314,6 +318,36 @@ struct Batch {
 };
 
 uint64_t splitmix64_seed_at(uint64_t seed, uint64_t t);  // prob.cu
+
+static size_t batch_smem() { return (size_t)BATCH_MMAX * (BATCH_T + 1) * sizeof(float); }
+
+// Captures the plan's launch sequence (permute limits -> persistent integrand
+// with `per_sm` CTAs per SM -> estimator) into a CUDA graph, replacing any
+// earlier one.
+static int batch_capture(Batch& B, int per_sm) {
+  cudaStream_t st = B.st;
+  const int grid = std::max(1, std::min(std::min(per_sm, B.per_sm_max) * B.sms, B.n_items));
+  cudaGraph_t graph;
+  TLR_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  cudaMemsetAsync(B.dbad, 0, sizeof(int), st);
+  cudaMemsetAsync(B.dnext, 0, sizeof(int), st);
+  k_permute_batch<<<nblk(B.total_n, 256), 256, 0, st>>>(B.a_st, B.b_st, B.perm_g, B.total_n, B.a32, B.b32, B.dbad);
+  k_batch<<<grid, BATCH_T, batch_smem(), st>>>(B.dprobs, B.ditems, B.n_items, B.dnext, B.W,
+                                              std::max<int64_t>(B.ktot_max, 1) * BATCH_T, B.logP);
+  k_shift_reduce<<<(unsigned)(B.count * B.M), 256, 0, st>>>(B.logP, B.N, B.ell);
+  k_final_batch<<<B.count, 256, 0, st>>>(B.ell, B.M, B.out);
+  cudaError_t ec = cudaStreamEndCapture(st, &graph);
+  if (ec != cudaSuccess) return cuda_fail(ec, "capture of the batched integrand");
+  cudaGraphExec_t exec = nullptr;
+  ec = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ec != cudaSuccess) return cuda_fail(ec, "instantiate the batched integrand graph");
+  if (B.exec) cudaGraphExecDestroy(B.exec);
+  B.exec = exec;
+  B.grid = grid;
+  B.per_sm = std::min(per_sm, B.per_sm_max);
+  return TLRMVN_OK;
+}
 
 static int batch_build(Batch& B, int count, const tlrmvn_factor_t* factors, const double* nu,
                        const tlrmvn_opts& o) {
@@ -399,14 +433,14 @@ static int batch_build(Batch& B, int count, const tlrmvn_factor_t* factors, cons
   TLR_CUDA(cudaMemcpyAsync(B.dprobs, probs.data(), probs.size() * sizeof(BatchProblem), cudaMemcpyHostToDevice, st));
   TLR_CUDA(cudaMemcpyAsync(B.ditems, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice, st));
   TLR_CUDA(cudaMemcpyAsync(B.perm_g, perm_g.data(), perm_g.size() * 8, cudaMemcpyHostToDevice, st));
-  // persistent grid and its private projection buffers
-  const size_t smem = (size_t)BATCH_MMAX * (BATCH_T + 1) * sizeof(float);
+  // persistent grid (all the CTAs that fit, until tuned) and its private projection buffers
+  const size_t smem = batch_smem();
   TLR_CHECK(raise_smem_limit((const void*)k_batch, (size_t)smem));
-  int per_sm = 0, sms = 0;
-  TLR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, BATCH_T, smem));
-  TLR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, B.device));
-  B.grid = std::max(1, std::min(per_sm * sms, B.n_items));
-  TLR_CHECK(dalloc(&B.W, (size_t)B.grid * std::max<int64_t>(B.ktot_max, 1) * BATCH_T));
+  TLR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&B.per_sm_max, k_batch, BATCH_T, smem));
+  TLR_CUDA(cudaDeviceGetAttribute(&B.sms, cudaDevAttrMultiProcessorCount, B.device));
+  B.per_sm_max = std::max(B.per_sm_max, 1);
+  B.grid_max = std::max(1, std::min(B.per_sm_max * B.sms, B.n_items));
+  TLR_CHECK(dalloc(&B.W, (size_t)B.grid_max * std::max<int64_t>(B.ktot_max, 1) * BATCH_T));
   TLR_CHECK(dalloc(&B.dnext, 1));
   TLR_CHECK(dalloc(&B.dbad, 1));
   TLR_CHECK(dalloc(&B.logP, (size_t)B.total_samples));
@@ -417,22 +451,7 @@ static int batch_build(Batch& B, int count, const tlrmvn_factor_t* factors, cons
   TLR_CUDA(cudaMallocHost(&B.h_ab, (size_t)B.total_n * 2 * 8));
   TLR_CUDA(cudaMallocHost(&B.h_out, (size_t)count * 2 * 8 + 8));
   TLR_CUDA(cudaStreamSynchronize(st));
-  // capture: permute limits -> persistent integrand -> estimator
-  cudaGraph_t graph;
-  TLR_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-  cudaMemsetAsync(B.dbad, 0, sizeof(int), st);
-  cudaMemsetAsync(B.dnext, 0, sizeof(int), st);
-  k_permute_batch<<<nblk(B.total_n, 256), 256, 0, st>>>(B.a_st, B.b_st, B.perm_g, B.total_n, B.a32, B.b32, B.dbad);
-  k_batch<<<B.grid, BATCH_T, smem, st>>>(B.dprobs, B.ditems, B.n_items, B.dnext, B.W,
-                                         std::max<int64_t>(B.ktot_max, 1) * BATCH_T, B.logP);
-  k_shift_reduce<<<(unsigned)(count * B.M), 256, 0, st>>>(B.logP, B.N, B.ell);
-  k_final_batch<<<count, 256, 0, st>>>(B.ell, B.M, B.out);
-  cudaError_t ec = cudaStreamEndCapture(st, &graph);
-  if (ec != cudaSuccess) return cuda_fail(ec, "capture of the batched integrand");
-  ec = cudaGraphInstantiate(&B.exec, graph, 0);
-  cudaGraphDestroy(graph);
-  if (ec != cudaSuccess) return cuda_fail(ec, "instantiate the batched integrand graph");
-  return TLRMVN_OK;
+  return batch_capture(B, B.per_sm_max);
 }
 
 static int batch_run(Batch& B, const double* const* a, const double* const* b, double* logp, double* err) {
@@ -492,6 +511,74 @@ extern "C" int tlrmvn_batch_run(tlrmvn_batch_t plan, const double* const* a, con
                                 double* err) {
   if (!plan || !a || !b || !logp || !err) return fail(TLRMVN_E_INVAL, "null argument");
   return batch_run(*reinterpret_cast<Batch*>(plan), a, b, logp, err);
+}
+
+extern "C" int tlrmvn_batch_tune(tlrmvn_batch_t plan, const double* const* a, const double* const* b,
+                                 const char* cache_path, int force, int* ctas_per_sm, double* ms) {
+  if (!plan || !a || !b) return fail(TLRMVN_E_INVAL, "null argument");
+  Batch& B = *reinterpret_cast<Batch*>(plan);
+  // cache key: device, problems, total dimension, total rank, shifts x points
+  std::string key;
+  {
+    cudaDeviceProp prop;
+    std::string dev = "unknown";
+    if (cudaGetDeviceProperties(&prop, B.device) == cudaSuccess) dev = prop.name;
+    for (char& c : dev)
+      if (c == ' ') c = '_';
+    int64_t ksum = 0;
+    for (Factor* F : B.F) ksum += F->ktot;
+    key = dev + " batch c" + std::to_string(B.count) + " n" + std::to_string(B.total_n) + " k" +
+          std::to_string(ksum) + " s" + std::to_string((int64_t)B.M * B.N);
+  }
+  int best = -1;
+  double best_ms = -1.0;
+  if (!force && cache_path && *cache_path) {
+    std::ifstream in(cache_path);
+    std::string line;
+    while (std::getline(in, line)) {
+      const size_t bar = line.find(" | ");
+      if (bar == key.size() && line.compare(0, bar, key) == 0) best = atoi(line.c_str() + bar + 3);
+    }
+  }
+  if (best >= 1) {
+    TLR_CHECK(batch_capture(B, best));
+  } else {
+    std::vector<double> lp(B.count), er(B.count);
+    cudaEvent_t e0, e1;
+    TLR_CUDA(cudaEventCreate(&e0));
+    TLR_CUDA(cudaEventCreate(&e1));
+    int s = TLRMVN_OK;
+    for (int k = 1; k <= B.per_sm_max && s == TLRMVN_OK; k++) {
+      s = batch_capture(B, k);
+      if (s == TLRMVN_OK) s = batch_run(B, a, b, lp.data(), er.data());  // untimed
+      float t = 0.0f;
+      if (s == TLRMVN_OK) {
+        cudaEventRecord(e0, B.st);
+        s = batch_run(B, a, b, lp.data(), er.data());
+        cudaEventRecord(e1, B.st);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&t, e0, e1);
+      }
+      if (s == TLRMVN_OK && (best < 0 || t < best_ms)) {
+        best = k;
+        best_ms = t;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    TLR_CHECK(s);
+    TLR_CHECK(batch_capture(B, best));
+    if (cache_path && *cache_path) {
+      FILE* f = fopen(cache_path, "a");
+      if (f) {
+        fprintf(f, "%s | %d # %.4f ms\n", key.c_str(), best, best_ms);
+        fclose(f);
+      }
+    }
+  }
+  if (ctas_per_sm) *ctas_per_sm = B.per_sm;
+  if (ms) *ms = best_ms;
+  return TLRMVN_OK;
 }
 
 extern "C" int tlrmvn_batch_free(tlrmvn_batch_t plan) {

@@ -51,6 +51,22 @@ void dfree(T*& p) {
   p = nullptr;
 }
 
+// ---- launch choices ----------------------------------------------------------
+// Launch choices of the integrand for one factor and precision, made by the
+// autotuner (tlrmvn_autotune) or left at these defaults:
+//   sub      variables per sub-tile of the float32 and float64 sweeps (64 or 128;
+//            the in-tile coupling between sub-tiles is a dense product)
+//   threads  threads per block of the float32 sweep (0: the occupancy rule)
+//   chunk    samples in flight per pass (0: as many as the memory rule allows)
+//   tc_ctas  whole-tile sweeps (BF16-shift path) sharing an SM: 6 (all that fit),
+//            or fewer by reserving shared memory
+struct Tuning {
+  int sub = 64;
+  int threads = 0;
+  int64_t chunk = 0;
+  int tc_ctas = 6;
+};
+
 // ---- factor handle -----------------------------------------------------------
 // L ~ tile-low-rank Cholesky factor of Sigma[perm][:, perm] (Section 3.3).
 // Compact device layout used by the integrand:
@@ -104,6 +120,13 @@ struct Factor {
   int64_t* dperm = nullptr;
   // guards the lazily made copies when several streams use the factor at once
   std::mutex copy_mu;
+  // launch choices per precision (TLRMVN_FP64 / FP32 / BF16_SHIFT), set by the autotuner
+  Tuning tune[3];
+  mutable std::mutex tune_mu;
+  Tuning tuning(int precision) const {
+    std::lock_guard<std::mutex> lk(tune_mu);
+    return tune[precision < 0 || precision > 2 ? 0 : precision];
+  }
 
   int64_t tsize(int t) const { return tile_off[t + 1] - tile_off[t]; }
   int64_t krow(int i) const { return krow_off[i + 1] - krow_off[i]; }

@@ -12,10 +12,10 @@
 // Per-sample logs are reduced per shift by a log-sum-exp and then across shifts (Section 2.1).
 #include "common.cuh"
 #include "gemm.cuh"
-#include "gemm_tc.cuh"
 #include "sov_device.cuh"
 #include "sweep.cuh"
 #include "sweep_tc.cuh"
+#include "tcgen05.cuh"
 
 #include <cudaTypedefs.h>
 
@@ -139,26 +139,6 @@ __global__ void k_diag(DiagArgs<T, YT> p) {
       for (int v = lane; v < p.mt; v += 32) put_y(row, v, ys[v * ld + j]);
     }
   }
-}
-
-// Sub-tile of the tensor-core coupling path: 64 (the faster; TLRMVN_SUB=128
-// selects 128 in tuning runs).
-static int sweep_sub_tc() {
-  static const int v = [] {
-    const char* e = getenv("TLRMVN_SUB");
-    return (e && atoi(e) == 128) ? 128 : 64;
-  }();
-  return v;
-}
-// Sub-tile of the FP32 path, whose coupling is the SIMT SGEMM: 64 (the faster:
-// 514 vs 574 ms per solve at n = 65,536), or DIAG_SUB = 128 (TLRMVN_SUB32=128,
-// tuning runs).
-static int sweep_sub_simt() {
-  static const int v = [] {
-    const char* e = getenv("TLRMVN_SUB32");
-    return (e && atoi(e) == 128) ? DIAG_SUB : 64;
-  }();
-  return v;
 }
 
 // BT32[i][u][v] = B[i][v][u] (zero for v >= m), inv32[i][v] = 1 / B[i][v][v]
@@ -311,8 +291,7 @@ int ensure_float_tiles(Factor& F, cudaStream_t st) {
 // them) under the factor's lock, so concurrent streams never see a partial copy.
 static int ensure_copies_locked(Factor& F, int precision, cudaStream_t st);
 static bool bf16_ready(const Factor& F) {
-  return !F.kpad_off.empty() && (F.ktot == 0 || (F.U16 && F.V16 && F.vmap16)) &&
-         (F.m <= sweep_sub_tc() || F.B16x2);
+  return !F.kpad_off.empty() && (F.ktot == 0 || (F.U16 && F.V16 && F.vmap16)) && F.B16x2;
 }
 static bool copies_ready(const Factor& F, int precision) {
   if (precision == TLRMVN_FP64) return true;
@@ -355,7 +334,7 @@ static int ensure_copies_locked(Factor& F, int precision, cudaStream_t st) {
     F.kw16 = std::max<int64_t>(F.kpad_off[r], 64);
     F.kmax16 = std::max<int64_t>((kmax + 63) / 64 * 64, 64);
     F.my16 = ((int64_t)m + 63) / 64 * 64;
-    if (m > sweep_sub_tc()) {
+    {
       const int64_t nb2 = (int64_t)r * m * 2 * F.my16;
       TLR_CHECK(dalloc(&F.B16x2, nb2));
       k_split_b16<<<blocks_for(nb2, 256), 256, 0, st>>>(F.B, m, F.my16, nb2, F.B16x2);
@@ -475,22 +454,25 @@ struct Scratch {
   }
 };
 
-// Samples per pass: opts.sample_chunk, else as many as keep the projection
-// buffer W within 8 GiB (SIMT paths) or 32 GiB (bf16 path); a multiple of 256.
+// Samples per pass: opts.sample_chunk, else the factor's tuned chunk, else as
+// many as keep the projection buffer W within 8 GiB (SIMT paths) or 32 GiB (bf16
+// path); a multiple of 256.
 static int64_t round_chunk(int64_t C, int64_t S) {
   C = std::min<int64_t>(C, S);
   return (C + 255) / 256 * 256;
 }
-static int64_t chunk_simt(const tlrmvn_opts& o, int64_t S, int64_t ktot, int m, int64_t es) {
+static int64_t chunk_simt(const tlrmvn_opts& o, const Tuning& tu, int64_t S, int64_t ktot, int m, int64_t es) {
   if (o.sample_chunk > 0) return round_chunk(o.sample_chunk, S);
+  if (tu.chunk > 0) return round_chunk(tu.chunk, S);
   const double budget = 8.0 * (1ull << 30);
   const double per = (double)(ktot + 2 * m) * es + 16.0;
   return round_chunk((int64_t)std::max(256.0, std::min((double)S, budget / per)), S);
 }
-static int64_t chunk_bf16(const tlrmvn_opts& o, int64_t S, int64_t kw, int64_t ly, int m) {
+static int64_t chunk_bf16(const tlrmvn_opts& o, const Tuning& tu, int64_t S, int64_t kw, int64_t ly) {
   if (o.sample_chunk > 0) return round_chunk(o.sample_chunk, S);
+  if (tu.chunk > 0) return round_chunk(tu.chunk, S);
   const double budget = 32.0 * (1ull << 30);
-  const double per = (double)kw * 2 + (double)ly * 2 + (double)m * 4 + 16.0;
+  const double per = (double)kw * 2 + (double)ly * 2 + 16.0;
   return round_chunk((int64_t)std::max(256.0, std::min((double)S, budget / per)), S);
 }
 
@@ -503,13 +485,8 @@ struct Lims {
   bool one_sided;  // every lower limit is -inf
 };
 
-// Sub-tile of the float64 sweep: 64 variables, so that a block of 128 samples
-// keeps its sub-tile's y in 64 KB of shared memory and three blocks share an SM
-// (a whole 512-variable tile per block left one warp per SM).
-constexpr int DIAG64_SUB = 64;
-
-// Threads per block of the sweep: as many as keep the (sub-)tile's y values of the
-// block's samples within 64 KB of shared memory (at least one warp).
+// Threads per block of the float64 sweep: as many as keep the sub-tile's y values
+// of the block's samples within 64 KB of shared memory (at least one warp).
 template <typename T>
 static int diag_threads(int m) {
   int bd = 256;
@@ -520,11 +497,11 @@ static int diag_threads(int m) {
 // Launch shape of the float sweep: samples per thread (spt) and per block (ns).
 // Each sample's chain of special functions is latency-bound, so a launch takes
 // (waves) x (time of one block) and a second wave for a few leftover blocks
-// nearly doubles it.  Among blocks of 2 to 8 warps this takes the fewest waves
-// over C samples (occupancy from the CUDA occupancy calculator, which accounts
-// for registers and shared memory), and among those the one nearest 128 samples
-// per block.  TLRMVN_SWEEP_THREADS fixes the block size for tuning runs.  One
-// sample per thread (two per thread, k_diag_f32<2, .>, measured slower).
+// nearly doubles it.  Unless the factor's tuning fixes the block size, this
+// takes, among blocks of 2 to 8 warps, the fewest waves over C samples
+// (occupancy from the CUDA occupancy calculator, which accounts for registers
+// and shared memory), and among those the one nearest 128 samples per block.
+// One sample per thread (two per thread, k_diag_f32<2, .>, measured slower).
 struct SweepShape {
   int spt, threads, ns;
 };
@@ -534,14 +511,9 @@ static SweepKernel sweep_kernel(int flags) {
                                        k_diag_f32<1, 4>, k_diag_f32<1, 5>, k_diag_f32<1, 6>, k_diag_f32<1, 7>};
   return table[flags & 7];
 }
-static SweepShape sweep_shape(int64_t C, int mt) {
+static SweepShape sweep_shape(int64_t C, int mt, int forced) {
   const int spt = 1;
-  static const int forced = [] {
-    const char* e = getenv("TLRMVN_SWEEP_THREADS");
-    const int v = e ? atoi(e) : 0;
-    return (v >= 32 && v <= 256 && v % 32 == 0) ? v : 0;
-  }();
-  if (forced) return SweepShape{spt, forced, forced * spt};
+  if (forced >= 32 && forced <= 256 && forced % 32 == 0) return SweepShape{spt, forced, forced * spt};
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   // one-entry memo per thread: a solve asks for the same (C, mt) once per sub-tile
@@ -575,9 +547,7 @@ static SweepShape sweep_shape(int64_t C, int mt) {
   memo = best;
   return best;
 }
-// The whole-tile sweep with tensor-core coupling (BF16-shift path), by
-// (periodisation, one-sided) flags; TLRMVN_FUSED=0 selects, for tuning runs,
-// sub-tile sweeps with separate coupling products instead.
+// The whole-tile sweep of the BF16-shift path, by (periodisation, one-sided) flags.
 typedef void (*SweepTcKernel)(const CUtensorMap, const CUtensorMap, const CUtensorMap, const CUtensorMap,
                               const CUtensorMap, const CUtensorMap, SweepTcArgs);
 static SweepTcKernel sweep_tc_kernel(int flags) {
@@ -585,146 +555,113 @@ static SweepTcKernel sweep_tc_kernel(int flags) {
                                          k_sweep_tc<SWEEP_PERIODIZE | SWEEP_ONE_SIDED>};
   return table[((flags & SWEEP_PERIODIZE) ? 1 : 0) | ((flags & SWEEP_ONE_SIDED) ? 2 : 0)];
 }
-static bool sweep_fused() {
-  static const bool v = [] {
-    const char* e = getenv("TLRMVN_FUSED");
-    return !(e && atoi(e) == 0);
-  }();
-  return v;
+// Dynamic shared memory of a whole-tile sweep launch with `ctas` CTAs per SM:
+// the kernel's own need, or more so that no more than `ctas` fit (tuning).
+static size_t sweep_tc_launch_smem(int ctas) {
+  size_t need = sweep_tc_smem_bytes();
+  if (ctas >= 1 && ctas < 6) {
+    int dev = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    // (1 KB of each CTA's shared memory is reserved by the system)
+    const size_t cap = (size_t)per_sm / (size_t)(ctas + 1) - 1024 + 16;
+    need = std::max(need, (cap + 15) / 16 * 16);
+  }
+  return need;
 }
-// The BF16-shift path sweeps whole tiles (low-rank shifts, in-tile coupling and
-// projections inside k_sweep_tc) when tiles hold more than one 64-variable sub-tile.
-static bool bf16_whole_tile(int m) { return m > sweep_sub_tc() && sweep_sub_tc() == STC_SUB && sweep_fused(); }
-static int set_sweep_smem(int m, int sub) {
+static int set_sweep_smem(int sub) {
   for (int flags = 0; flags < 8; flags++)
-    TLR_CHECK(raise_smem_limit((const void*)sweep_kernel(flags), sweep_smem_bytes(std::min(m, sub), 256)));
+    TLR_CHECK(raise_smem_limit((const void*)sweep_kernel(flags), sweep_smem_bytes(sub, 256)));
   for (int flags = 0; flags < 8; flags++)
-    TLR_CHECK(raise_smem_limit((const void*)sweep_tc_kernel(flags), sweep_tc_smem_bytes()));
+    TLR_CHECK(raise_smem_limit((const void*)sweep_tc_kernel(flags), sweep_tc_launch_smem(1)));
   return TLRMVN_OK;
 }
 
-// Float sweep of diagonal tile i, DIAG_SUB variables at a time.  Before each
-// sub-tile q > 0, the coupling to the tile's earlier sub-tiles,
-// B_i[q, <q] y_i[<q], is added to the limit shifts Dl (variable-major, ld C) by a
-// dense product; y goes to Yv (float, variable-major, ld C) and, when Ys is
-// given, to Ys (bf16, sample-major, ld ldys).  has_shift: Dl already holds the
-// low-rank shifts of this tile.
-// Tensor-core in-tile coupling (BF16-shift path): tensor maps of F.B16x2 and of
-// the sample-major hi/lo y buffer, the offset of the lo halves, the error flag.
-struct TcCouple {
-  CUtensorMap mapB, mapY;      // 64-deep boxes (128-byte swizzle)
-  CUtensorMap mapB32, mapY32;  // 32-deep boxes (64-byte swizzle)
-  CUtensorMap mapW{}, mapU64{};  // the whole-tile sweep's low-rank shift operands (64 x 64 boxes)
-  CUtensorMap mapV64{};          // and its projection operand (V rows, 64 x 64 boxes)
-  __nv_bfloat16* W = nullptr;    // the projections (rank-major) and their leading dimension
+// Operands of the whole-tile sweep (BF16-shift path): tensor maps of the split
+// copy of B and of the sample-major hi/lo y buffer (32-deep boxes, 64-byte
+// swizzle), of W and of the row and column factors (64 x 64 boxes), of the y hi
+// halves for the projection; the projections W, the offset of the lo halves and
+// the error flag.
+struct TcOperands {
+  CUtensorMap mapB32, mapY32, mapY64;
+  CUtensorMap mapW{}, mapU64{}, mapV64{};
+  __nv_bfloat16* W = nullptr;
   int64_t ldw = 0;
   int64_t my;
-  int sub;  // sub-tile size, a multiple of 64
   int* err;
 };
-// Coupling kernel of 64-variable sub-tiles: one 32-deep stage (24 KB, 64-byte
-// swizzle) with the old outputs loaded just before their stores, so that six
-// CTAs share an SM and a launch over 100,000 samples (782 CTAs) runs in one
-// round; TLRMVN_COUPLE=64 selects, for tuning runs, one 64-deep stage of 48 KB
-// with the old outputs prefetched during the MMAs (four CTAs per SM).  Two
-// pipelined 32-deep stages measured no faster.
-// Shift and projection GEMMs in N = 128 tiles (more CTAs per SM) unless
-// TLRMVN_NARROW=0 (tuning runs: N = 256 tiles).
-static bool gemm_narrow() {
-  static const bool v = [] {
-    const char* e = getenv("TLRMVN_NARROW");
-    return !(e && atoi(e) == 0);
-  }();
-  return v;
-}
-static bool couple_k32() {
-  static const bool v = [] {
-    const char* e = getenv("TLRMVN_COUPLE");
-    return !(e && atoi(e) == 64);
-  }();
-  return v;
+
+// Whole diagonal tile i on the BF16-shift path: one launch of k_sweep_tc
+// (low-rank shifts, in-tile coupling, sweep and projections).
+static void sweep_tile_tc(const Factor& F, int i, int64_t C, const Lims& L, const float* rs32, const uint64_t* dD,
+                          int64_t c0, int64_t N, int64_t Cc, int periodize, __nv_bfloat16* Ys, int64_t ldys,
+                          double* logP, const TcOperands& tco, const Tuning& tu, cudaStream_t st, Prof& pf) {
+  const int m = F.m, mt = (int)F.tsize(i);
+  SweepTcArgs t;
+  DiagArgs32& a = t.d;
+  a.BT = F.BT32 + (size_t)i * m * F.ldbt;
+  a.inv = F.inv32 + (size_t)i * m;
+  a.band = F.band32 + (size_t)i * m * 16;
+  a.mt = mt;
+  a.ldbt = F.ldbt;
+  a.Delta = nullptr;  // (the shifts are products of the kernel)
+  a.ldd = C;
+  a.a = L.a32 + F.tile_off[i];
+  a.b = L.b32 + F.tile_off[i];
+  a.rs = rs32;
+  a.Q = F.Q;
+  a.D = dD;
+  a.ldD = F.n + 1;
+  a.coord0 = F.tile_off[i];
+  a.sample0 = c0;
+  a.N = N;
+  a.C = Cc;
+  a.periodize = periodize;
+  a.first = (i == 0);
+  a.Yv = nullptr;
+  a.ldyv = 0;
+  a.Ys = Ys;
+  a.ldys = ldys;
+  a.ys_lo = tco.my;
+  a.logP = logP;
+  t.brow0 = i * m;
+  t.alo = (int)tco.my;
+  t.blo = (int)tco.my;
+  t.urow0 = i * m;
+  t.krow0 = (int)F.kpad_off[i];
+  t.kr = (int)F.krow(i);
+  t.kcol0 = (int)F.kcol_off[i];
+  t.kc = (int)F.kcol(i);
+  t.W = tco.W;
+  t.ldw = tco.ldw;
+  t.vmap = F.vmap16 ? F.vmap16 + F.kcol_off[i] : nullptr;
+  t.err = tco.err;
+  const int flags = (periodize ? SWEEP_PERIODIZE : 0) | (L.one_sided ? SWEEP_ONE_SIDED : 0);
+  pf.begin(TLRMVN_KC_DIAG);
+  launch_pdl(sweep_tc_kernel(flags), dim3((unsigned)((Cc + STC_NS - 1) / STC_NS)), dim3(STC_NS),
+             sweep_tc_launch_smem(tu.tc_ctas), st, tco.mapY32, tco.mapB32, tco.mapW, tco.mapU64, tco.mapY64,
+             tco.mapV64, t);
+  pf.end();
 }
 
+// Float sweep of diagonal tile i (FP32 path), `sub` variables at a time.  Before
+// each sub-tile q > 0, the coupling to the tile's earlier sub-tiles,
+// B_i[q, <q] y_i[<q], is added to the limit shifts Dl (variable-major, ld C) by
+// a dense SIMT product; y goes to Yv (float, variable-major, ld C).  has_shift:
+// Dl already holds the low-rank shifts of this tile.
 static void sweep_tile_f32(const Factor& F, int i, bool has_shift, float* Dl, int64_t C, const Lims& L,
                            const float* rs32, const uint64_t* dD, int64_t c0, int64_t N, int64_t Cc, int periodize,
-                           float* Yv, __nv_bfloat16* Ys, int64_t ldys, double* logP, cudaStream_t st, Prof& pf,
-                           const TcCouple* tcc = nullptr) {
+                           float* Yv, double* logP, const Tuning& tu, cudaStream_t st, Prof& pf) {
   const int m = F.m, mt = (int)F.tsize(i);
-  if (tcc && bf16_whole_tile(m)) {
-    SweepTcArgs t;
-    DiagArgs32& a = t.d;
-    a.BT = F.BT32 + (size_t)i * m * F.ldbt;
-    a.inv = F.inv32 + (size_t)i * m;
-    a.band = F.band32 + (size_t)i * m * 16;
-    a.mt = mt;
-    a.ldbt = F.ldbt;
-    a.Delta = nullptr;  // (the shifts are products of the kernel)
-    a.ldd = C;
-    a.a = L.a32 + F.tile_off[i];
-    a.b = L.b32 + F.tile_off[i];
-    a.rs = rs32;
-    a.Q = F.Q;
-    a.D = dD;
-    a.ldD = F.n + 1;
-    a.coord0 = F.tile_off[i];
-    a.sample0 = c0;
-    a.N = N;
-    a.C = Cc;
-    a.periodize = periodize;
-    a.first = (i == 0);
-    a.Yv = nullptr;
-    a.ldyv = 0;
-    a.Ys = Ys;
-    a.ldys = ldys;
-    a.ys_lo = tcc->my;
-    a.logP = logP;
-    t.brow0 = i * m;
-    t.alo = (int)tcc->my;
-    t.blo = (int)tcc->my;
-    t.urow0 = i * m;
-    t.krow0 = (int)F.kpad_off[i];
-    t.kr = (int)F.krow(i);
-    t.kcol0 = (int)F.kcol_off[i];
-    t.kc = (int)F.kcol(i);
-    t.W = tcc->W;
-    t.ldw = tcc->ldw;
-    t.vmap = F.vmap16 + F.kcol_off[i];
-    t.err = tcc->err;
-    const int flags = (periodize ? SWEEP_PERIODIZE : 0) | (L.one_sided ? SWEEP_ONE_SIDED : 0);
-    pf.begin(TLRMVN_KC_DIAG);
-    launch_pdl(sweep_tc_kernel(flags), dim3((unsigned)((Cc + STC_NS - 1) / STC_NS)), dim3(STC_NS),
-               sweep_tc_smem_bytes(), st, tcc->mapY32, tcc->mapB32, tcc->mapW, tcc->mapU64, tcc->mapY, tcc->mapV64, t);
-    pf.end();
-    return;
-  }
-  const int sub = tcc ? tcc->sub : sweep_sub_simt();
-  const SweepShape sh = sweep_shape(Cc, std::min(mt, sub));
+  const int sub = tu.sub;
+  const SweepShape sh = sweep_shape(Cc, std::min(mt, sub), tu.threads);
   const float* Bi = F.B32 + (size_t)i * m * m;
   for (int q0 = 0; q0 < mt; q0 += sub) {
     const int mq = std::min(sub, mt - q0);
     if (q0 > 0) {
       pf.begin(TLRMVN_KC_COUPLE);
-      if (tcc) {
-        // Dl[q0 + v][c] (+)= sum_{u < q0} B_i[q0 + v][u] y_u[c] as hi*hi + hi*lo + lo*hi
-        // transposed: rows = samples (A = y, hi/lo), columns = the sub-tile's variables
-        tc::GemmTcArgs g{(int)Cc, mq, q0, 0, 0, 0, i * m + q0, Dl + (size_t)q0 * C, C, nullptr, 0, nullptr, tcc->err};
-        g.alo = (int)tcc->my;
-        g.blo = (int)tcc->my;
-        g.accumulate = has_shift ? 1 : 0;
-        const dim3 grid(1, (unsigned)((Cc + tc::BM - 1) / tc::BM));
-        if (tcc->sub == 64 && couple_k32())
-          launch_pdl(tc::k_gemm_tc<tc::EPI_TRANS_F32, true, 64, false, 32, 1, false>, grid, dim3(128),
-                     tc::Cfg<64, true, false, 32, 1>::SMEM, st, tcc->mapY32, tcc->mapB32, g);
-        else if (tcc->sub == 64)
-          launch_pdl(tc::k_gemm_tc<tc::EPI_TRANS_F32, true, 64>, grid, dim3(128), tc::Cfg<64, true>::SMEM, st, tcc->mapY,
-                     tcc->mapB, g);
-        else
-          launch_pdl(tc::k_gemm_tc<tc::EPI_TRANS_F32, true, 128>, grid, dim3(128), tc::Cfg<128, true>::SMEM, st,
-                     tcc->mapY, tcc->mapB, g);
-      } else {
-        gemm_nn<float>(st, mq, Cc, q0, Bi + (size_t)q0 * m, m, Yv, C, Dl + (size_t)q0 * C, C, nullptr,
-                       has_shift ? 1 : 0);
-      }
+      gemm_nn<float>(st, mq, Cc, q0, Bi + (size_t)q0 * m, m, Yv, C, Dl + (size_t)q0 * C, C, nullptr,
+                     has_shift ? 1 : 0);
       pf.end();
     }
     DiagArgs32 a;
@@ -747,31 +684,27 @@ static void sweep_tile_f32(const Factor& F, int i, bool has_shift, float* Dl, in
     a.C = Cc;
     a.periodize = periodize;
     a.first = (i == 0 && q0 == 0);
-    a.Yv = Yv ? Yv + (size_t)q0 * C : nullptr;
+    a.Yv = Yv + (size_t)q0 * C;
     a.ldyv = C;
-    a.Ys = Ys ? Ys + q0 : nullptr;
-    a.ldys = ldys;
-    a.ys_lo = tcc ? tcc->my : 0;
+    a.Ys = nullptr;
+    a.ldys = 0;
+    a.ys_lo = 0;
     a.logP = logP;
     pf.begin(TLRMVN_KC_DIAG);
-    const int flags = (periodize ? SWEEP_PERIODIZE : 0) | (a.Yv ? SWEEP_YV : 0) | (L.one_sided ? SWEEP_ONE_SIDED : 0);
-    if (tcc)
-      launch_pdl(sweep_kernel(flags), dim3(blocks_for(Cc, sh.ns)), dim3(sh.threads), sweep_smem_bytes(mq, sh.ns), st,
-                 a);
-    else
-      sweep_kernel(flags)<<<blocks_for(Cc, sh.ns), sh.threads, sweep_smem_bytes(mq, sh.ns), st>>>(a);
+    const int flags = (periodize ? SWEEP_PERIODIZE : 0) | SWEEP_YV | (L.one_sided ? SWEEP_ONE_SIDED : 0);
+    sweep_kernel(flags)<<<blocks_for(Cc, sh.ns), sh.threads, sweep_smem_bytes(mq, sh.ns), st>>>(a);
     pf.end();
   }
 }
 
 template <typename T, typename YT>
 static int run_chunks(Factor& F, const T* Bt, const T* Ut, const T* Vt, const Lims& L, double nu,
-                      const tlrmvn_opts& o, const uint64_t* dD, double* logP, Scratch& sc, cudaStream_t st,
-                      Prof& pf) {
+                      const tlrmvn_opts& o, const Tuning& tu, const uint64_t* dD, double* logP, Scratch& sc,
+                      cudaStream_t st, Prof& pf) {
   const int64_t M = o.n_shifts, N = o.n_points, S = M * N;
   const int m = F.m;
   const bool f32 = sizeof(T) == 4;
-  const int64_t C = chunk_simt(o, S, F.ktot, m, sizeof(T));
+  const int64_t C = chunk_simt(o, tu, S, F.ktot, m, sizeof(T));
   T *W = nullptr, *Dl = nullptr;
   YT* Y = nullptr;
   double* rs = nullptr;
@@ -782,10 +715,12 @@ static int run_chunks(Factor& F, const T* Bt, const T* Ut, const T* Vt, const Li
   const bool mvt = std::isfinite(nu);
   if (mvt) TLR_CHECK(f32 ? sc.get(&rs32, (size_t)C) : sc.get(&rs, (size_t)C));
 
-  const int bd = diag_threads<T>(std::min(m, DIAG64_SUB));
-  const size_t smem = (size_t)std::min(m, DIAG64_SUB) * (bd + 1) * sizeof(T);
+  // float64: sub-tiles of tu.sub variables, each sample keeping only the sub-tile's y in shared memory
+  const int sub64 = std::min(m, tu.sub);
+  const int bd = diag_threads<T>(sub64);
+  const size_t smem = (size_t)sub64 * (bd + 1) * sizeof(T);
   if (f32)
-    TLR_CHECK(set_sweep_smem(m, sweep_sub_simt()));
+    TLR_CHECK(set_sweep_smem(tu.sub));
   else
     TLR_CHECK(raise_smem_limit((const void*)k_diag<T, YT, false>, (size_t)smem));
 
@@ -808,16 +743,14 @@ static int run_chunks(Factor& F, const T* Bt, const T* Ut, const T* Vt, const Li
         Delta = Dl;
       }
       if constexpr (sizeof(T) == 4) {
-        sweep_tile_f32(F, i, Kr > 0, (float*)Dl, C, L, rs32, dD, c0, N, Cc, o.periodize, (float*)Y, nullptr, 0, logP,
-                       st, pf);
+        sweep_tile_f32(F, i, Kr > 0, (float*)Dl, C, L, rs32, dD, c0, N, Cc, o.periodize, (float*)Y, logP, tu, st,
+                       pf);
       } else {
-        // sub-tiles of DIAG64_SUB variables: each sample keeps only the sub-tile's y in
-        // shared memory, and the coupling to the tile's earlier sub-tiles,
-        // B_i[q, <q] y_i[<q], is added to the limit shifts by a dense product first
-        // (the same sums as eq. 2, regrouped)
+        // the coupling to the tile's earlier sub-tiles, B_i[q, <q] y_i[<q], is added
+        // to the limit shifts by a dense product first (the same sums as eq. 2, regrouped)
         const T* Bi = Bt + (size_t)i * m * m;
-        for (int q0 = 0; q0 < mt; q0 += DIAG64_SUB) {
-          const int mq = std::min(DIAG64_SUB, mt - q0);
+        for (int q0 = 0; q0 < mt; q0 += sub64) {
+          const int mq = std::min(sub64, mt - q0);
           if (q0 > 0) {
             pf.begin(TLRMVN_KC_COUPLE);
             gemm_nn<T>(st, mq, Cc, q0, Bi + (size_t)q0 * m, m, Y, C, Dl + (size_t)q0 * C, C, nullptr,
@@ -861,31 +794,28 @@ static int run_chunks(Factor& F, const T* Bt, const T* Ut, const T* Vt, const Li
   return TLRMVN_OK;
 }
 
-// BF16-shift integrand: float32 sweep; both low-rank products on tcgen05 with
-// bf16 operands and fp32 accumulation, and the coupling between the 128-variable
-// sub-tiles of a diagonal tile on tcgen05 with split operands (x = hi + lo, both
-// bf16; hi*hi + hi*lo + lo*hi, relative error ~1e-5).  Layouts (C = samples in the chunk):
+// BF16-shift integrand: one whole-tile sweep per diagonal tile (k_sweep_tc): the
+// low-rank shifts, the in-tile coupling between 64-variable sub-tiles (split
+// bf16 operands: x = hi + lo, hi*hi + hi*lo + lo*hi, relative error ~1e-5) and
+// the projections on tcgen05 with fp32 accumulation in TMEM, the sweep itself in
+// float32.  Layouts (C = samples in the chunk):
 //   W16  kw16 x ldw bf16, rank-major (ldw = C rounded up to 64): row k holds
-//        projection k of every sample (written coalesced by the projection GEMM,
-//        read as an MN-major operand by the shift GEMM)
-//   Y16  C x ly    bf16, sample-major: the tile's y (hi) in columns [0, my16), and
-//                  for tiles over 128 variables bf16(y - hi) in [my16, 2 my16)
-//   Dl   m x C     fp32, variable-major (read by the sweep)
-static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opts& o, const uint64_t* dD,
-                           double* logP, Scratch& sc, cudaStream_t st, Prof& pf) {
+//        projection k of every sample (written as whole rows by the tile that
+//        owns the rank, read as an MN-major operand by the later tiles' shifts)
+//   Y16  C x 2 my16 bf16, sample-major: the tile's y (hi) in columns [0, my16) and
+//        bf16(y - hi) in [my16, 2 my16)
+static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opts& o, const Tuning& tu,
+                           const uint64_t* dD, double* logP, Scratch& sc, cudaStream_t st, Prof& pf) {
   const int64_t M = o.n_shifts, N = o.n_points, S = M * N;
   const int m = F.m;
-  const int64_t ly = F.B16x2 ? 2 * F.my16 : F.my16;  // Y16 row: hi halves (then lo halves)
-  const int64_t C = chunk_bf16(o, S, F.kw16, ly, m);
+  const int64_t ly = 2 * F.my16;  // Y16 row: hi halves, then lo halves
+  const int64_t C = chunk_bf16(o, tu, S, F.kw16, ly);
   __nv_bfloat16 *W = nullptr, *Y = nullptr;
-  float* Dl = nullptr;
   float* rs32 = nullptr;
   int* err = nullptr;
   const int64_t ldw = (C + 63) / 64 * 64;
   TLR_CHECK(sc.get(&W, (size_t)F.kw16 * ldw));
   TLR_CHECK(sc.get(&Y, (size_t)ly * C));
-  const bool fused = bf16_whole_tile(m);
-  if (!fused) TLR_CHECK(sc.get(&Dl, (size_t)m * C));  // (the whole-tile sweep keeps its shifts in TMEM)
   TLR_CHECK(sc.get(&err, 1));
   const bool mvt = std::isfinite(nu);
   if (mvt) TLR_CHECK(sc.get(&rs32, (size_t)C));
@@ -894,50 +824,27 @@ static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opt
   TLR_CUDA(cudaMemsetAsync(Y, 0, (size_t)ly * C * 2, st));
   TLR_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
 
-  // tensor maps (box 64 x rows): A operands take 128-row boxes, B operands BN-row boxes
-  //   shift      Dl^T (samples x vars) = W16^T (A, MN-major) x U16 rows (B, N = 256)
-  //   projection W16 rows^T (samples x ranks) = Y16 rows (A) x V16 rows (B, N = 256)
-  //   coupling   Dl^T += Y16 rows (A, hi/lo) x B16x2 rows (B, hi/lo, N = sub-tile)
-  CUtensorMap mapU, mapU128, mapV, mapV64, mapV128, mapW, mapY;
+  // tensor maps: A operands (samples) take 128-row boxes, B operands 64-row boxes
+  //   shift      T = W16^T (A, MN-major) x U16 rows (B)
+  //   coupling   T += Y16 rows (A, hi/lo) x B16x2 rows (B, hi/lo)
+  //   projection T = Y16 rows (A, hi) x V16 rows (B)
+  TcOperands tco;
+  TLR_CHECK(make_map(&tco.mapB32, F.B16x2, ly, (uint64_t)F.r * m, ly * 2, 64, 32));
+  TLR_CHECK(make_map(&tco.mapY32, Y, ly, C, ly * 2, STC_NS, 32));
+  TLR_CHECK(make_map(&tco.mapY64, Y, ly, C, ly * 2, STC_NS));
+  TLR_CHECK(make_map(&tco.mapW, W, ldw, F.kw16, ldw * 2, 64));
   if (F.ktot) {
-    TLR_CHECK(make_map(&mapU, F.U16, F.kmax16, (uint64_t)F.r * m, F.kmax16 * 2, 256));
-    TLR_CHECK(make_map(&mapU128, F.U16, F.kmax16, (uint64_t)F.r * m, F.kmax16 * 2, 128));
-    TLR_CHECK(make_map(&mapV, F.V16, F.my16, F.ktot, F.my16 * 2, 256));
-    TLR_CHECK(make_map(&mapV64, F.V16, F.my16, F.ktot, F.my16 * 2, 64));
-    TLR_CHECK(make_map(&mapV128, F.V16, F.my16, F.ktot, F.my16 * 2, 128));
+    TLR_CHECK(make_map(&tco.mapU64, F.U16, F.kmax16, (uint64_t)F.r * m, F.kmax16 * 2, 64));
+    TLR_CHECK(make_map(&tco.mapV64, F.V16, F.my16, F.ktot, F.my16 * 2, 64));
+  } else {
+    tco.mapU64 = tco.mapW;  // (never read: no tile has ranks)
+    tco.mapV64 = tco.mapW;
   }
-  TLR_CHECK(make_map(&mapW, W, ldw, F.kw16, ldw * 2, 64));
-  TLR_CHECK(make_map(&mapY, Y, ly, C, ly * 2, tc::BM));
-  TcCouple tcc;
-  if (F.B16x2) {
-    tcc.sub = sweep_sub_tc();
-    TLR_CHECK(make_map(&tcc.mapB, F.B16x2, ly, (uint64_t)F.r * m, ly * 2, (uint32_t)tcc.sub));
-    TLR_CHECK(make_map(&tcc.mapB32, F.B16x2, ly, (uint64_t)F.r * m, ly * 2, (uint32_t)tcc.sub, 32));
-    TLR_CHECK(make_map(&tcc.mapY32, Y, ly, C, ly * 2, tc::BM, 32));
-    tcc.mapY = mapY;
-    tcc.mapW = mapW;
-    if (F.ktot) {
-      TLR_CHECK(make_map(&tcc.mapU64, F.U16, F.kmax16, (uint64_t)F.r * m, F.kmax16 * 2, 64));
-      tcc.mapV64 = mapV64;
-    }
-    tcc.W = W;
-    tcc.ldw = ldw;
-    tcc.my = F.my16;
-    tcc.err = err;
-  }
-  TLR_CHECK(raise_smem_limit((const void*)tc::k_gemm_tc<tc::EPI_TRANS_F32, false, 256, true>,
-                             tc::Cfg<256, false, true>::SMEM));
-  TLR_CHECK(raise_smem_limit((const void*)tc::k_gemm_tc<tc::EPI_TRANS_F32, false, 128, true, 64, 1>,
-                             tc::Cfg<128, false, true, 64, 1>::SMEM));
-  TLR_CHECK(raise_smem_limit((const void*)tc::k_gemm_tc<tc::EPI_TRANS_BF16, false, 256>, tc::Cfg<256, false>::SMEM));
-  TLR_CHECK(raise_smem_limit((const void*)tc::k_gemm_tc<tc::EPI_TRANS_BF16, false, 128>, tc::Cfg<128, false>::SMEM));
-  TLR_CHECK(raise_smem_limit((const void*)tc::k_gemm_tc<tc::EPI_TRANS_BF16, false, 64>, tc::Cfg<64, false>::SMEM));
-  TLR_CHECK(raise_smem_limit((const void*)tc::k_gemm_tc<tc::EPI_TRANS_F32, true, 64>, tc::Cfg<64, true>::SMEM));
-  TLR_CHECK(raise_smem_limit((const void*)tc::k_gemm_tc<tc::EPI_TRANS_F32, true, 64, false, 32, 1, false>,
-                             tc::Cfg<64, true, false, 32, 1>::SMEM));
-  TLR_CHECK(raise_smem_limit((const void*)tc::k_gemm_tc<tc::EPI_TRANS_F32, true, 128>, tc::Cfg<128, true>::SMEM));
-
-  TLR_CHECK(set_sweep_smem(m, sweep_sub_tc()));
+  tco.W = W;
+  tco.ldw = ldw;
+  tco.my = F.my16;
+  tco.err = err;
+  TLR_CHECK(set_sweep_smem(64));
 
   for (int64_t c0 = 0; c0 < S; c0 += C) {
     const int64_t Cc = std::min(C, S - c0);
@@ -947,45 +854,8 @@ static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opt
                                                        o.periodize);
       pf.end();
     }
-    const unsigned sblocks = (unsigned)((Cc + tc::BM - 1) / tc::BM);
-    for (int i = 0; i < F.r; i++) {
-      const int mt = (int)F.tsize(i);
-      const int64_t Kr = F.krow(i), Kc = F.kcol(i);
-      const float* Delta = nullptr;
-      if (Kr > 0 && !fused) {
-        tc::GemmTcArgs g{(int)Cc, mt, (int)Kr, (int)F.kpad_off[i], 0, 0, i * m, Dl, C, nullptr, 0, nullptr, err};
-        pf.begin(TLRMVN_KC_SHIFT);
-        if (gemm_narrow())  // N = 128, one stage: four CTAs per SM (TMEM 4 x 128 columns)
-          launch_pdl(tc::k_gemm_tc<tc::EPI_TRANS_F32, false, 128, true, 64, 1>,
-                     dim3((unsigned)((mt + 127) / 128), sblocks), dim3(128), tc::Cfg<128, false, true, 64, 1>::SMEM, st,
-                     mapW, mapU128, g);
-        else
-          launch_pdl(tc::k_gemm_tc<tc::EPI_TRANS_F32, false, 256, true>, dim3((unsigned)((mt + 255) / 256), sblocks),
-                     dim3(128), tc::Cfg<256, false, true>::SMEM, st, mapW, mapU, g);
-        pf.end();
-        Delta = Dl;
-      }
-      sweep_tile_f32(F, i, Delta != nullptr, Dl, C, L, rs32, dD, c0, N, Cc, o.periodize, nullptr, Y, ly, logP, st, pf,
-                     F.B16x2 ? &tcc : nullptr);
-      if (Kc > 0 && !fused) {
-        // transposed: rows = samples (A = y), columns = the column tile's ranks
-        tc::GemmTcArgs g{(int)Cc, (int)Kc, mt, 0, 0, 0, (int)F.kcol_off[i], nullptr, 0, W, ldw,
-                         F.vmap16 + F.kcol_off[i], err};
-        // (grid x walks the rank blocks: those of one sample block run together and share its y in L2;
-        // N is the smallest of 64 / 128 / 256 that holds the tile's ranks)
-        pf.begin(TLRMVN_KC_VPROJ);
-        if (Kc <= 64)
-          launch_pdl(tc::k_gemm_tc<tc::EPI_TRANS_BF16, false, 64>, dim3(1, sblocks), dim3(128),
-                     tc::Cfg<64, false>::SMEM, st, mapY, mapV64, g);
-        else if (Kc <= 128 || gemm_narrow())
-          launch_pdl(tc::k_gemm_tc<tc::EPI_TRANS_BF16, false, 128>, dim3((unsigned)((Kc + 127) / 128), sblocks), dim3(128),
-                     tc::Cfg<128, false>::SMEM, st, mapY, mapV128, g);
-        else
-          launch_pdl(tc::k_gemm_tc<tc::EPI_TRANS_BF16, false, 256>, dim3((unsigned)((Kc + 255) / 256), sblocks),
-                     dim3(128), tc::Cfg<256, false>::SMEM, st, mapY, mapV, g);
-        pf.end();
-      }
-    }
+    for (int i = 0; i < F.r; i++)
+      sweep_tile_tc(F, i, C, L, rs32, dD, c0, N, Cc, o.periodize, Y, ly, logP, tco, tu, st, pf);
     TLR_CUDA(cudaGetLastError());
   }
   int herr = 0;
@@ -999,17 +869,18 @@ static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opt
 // by the serving loop); mirrors the buffers of prob_impl and the chunk loops.
 int64_t prob_scratch_bytes(const Factor& F, const tlrmvn_opts& o) {
   const int64_t M = o.n_shifts, N = o.n_points, S = M * N, n = F.n, m = F.m;
+  const Tuning tu = F.tuning(o.precision);
   int64_t bytes = n * (8 * 2 + 4 * 2) + M * (n + 1) * 8 + M * 8 + S * 8 + 256;
   if (o.precision == TLRMVN_BF16_SHIFT) {
     int64_t kw = 0;
     for (int i = 0; i < F.r; i++) kw += (F.krow(i) + 63) / 64 * 64;
     kw = std::max<int64_t>(kw, 64);
-    const int64_t my = (m + 63) / 64 * 64, ly = m > sweep_sub_tc() ? 2 * my : my;
-    const int64_t C = chunk_bf16(o, S, kw, ly, m);
-    bytes += C * (kw * 2 + ly * 2 + (bf16_whole_tile((int)m) ? 0 : m * 4) + 4);
+    const int64_t my = (m + 63) / 64 * 64, ly = 2 * my;
+    const int64_t C = chunk_bf16(o, tu, S, kw, ly);
+    bytes += C * (kw * 2 + ly * 2 + 4);
   } else {
     const int64_t es = o.precision == TLRMVN_FP64 ? 8 : 4;
-    const int64_t C = chunk_simt(o, S, F.ktot, m, es);
+    const int64_t C = chunk_simt(o, tu, S, F.ktot, m, es);
     bytes += C * ((F.ktot + 2 * m) * es + 8);
   }
   return bytes;
@@ -1061,12 +932,13 @@ int prob_impl(Factor& F, const double* a_dev, const double* b_dev, double nu, co
   TLR_CHECK(ensure_copies(F, o.precision, st));
   int s;
   const Lims L{ap, bp, ap32, bp32, hbad[1] == 0};
+  const Tuning tu = F.tuning(o.precision);
   if (o.precision == TLRMVN_FP64)
-    s = run_chunks<double, double>(F, F.B, F.Ucat, F.Vcat, L, nu, o, dD, logP, sc, st, pf);
+    s = run_chunks<double, double>(F, F.B, F.Ucat, F.Vcat, L, nu, o, tu, dD, logP, sc, st, pf);
   else if (o.precision == TLRMVN_FP32)
-    s = run_chunks<float, float>(F, F.B32, F.U32, F.V32, L, nu, o, dD, logP, sc, st, pf);
+    s = run_chunks<float, float>(F, F.B32, F.U32, F.V32, L, nu, o, tu, dD, logP, sc, st, pf);
   else
-    s = run_chunks_bf16(F, L, nu, o, dD, logP, sc, st, pf);
+    s = run_chunks_bf16(F, L, nu, o, tu, dD, logP, sc, st, pf);
   TLR_CHECK(s);
   pf.begin(TLRMVN_KC_REDUCE);
   k_shift_reduce<<<(unsigned)M, 256, 0, st>>>(logP, N, ell);

@@ -35,7 +35,7 @@
 // expiry the CTA records an error code, skips the rest, waits (bounded) for its
 // copies and products in flight, frees its TMEM and returns.
 #pragma once
-#include "gemm_tc.cuh"
+#include "tcgen05.cuh"
 #include "sweep.cuh"
 
 namespace tlrmvn {

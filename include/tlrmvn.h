@@ -57,6 +57,9 @@ extern "C" {
 #define TLRMVN_FP64        0  /* everything in float64 */
 #define TLRMVN_FP32        1  /* diagonal-tile sweep and low-rank shifts in float32 */
 #define TLRMVN_BF16_SHIFT  2  /* float32 sweep; low-rank shifts on tcgen05 tensor cores, bf16 in, fp32 accumulate */
+#define TLRMVN_FP16_SHIFT  3  /* as BF16_SHIFT with fp16 operands: U and V scaled per off-diagonal tile by
+                                 powers of two into fp16's range, the inverse applied to each projection
+                                 before it is stored (TLRMVN_E_NOTSUP if a tile's range cannot be met) */
 
 /* Preconditioner (tlrmvn_factor_opts.reorder), Section 3.3. */
 #define TLRMVN_REORDER_NONE       0  /* geometric order only ("tlrmvn") */
@@ -82,7 +85,7 @@ typedef struct {
 } tlrmvn_factor_opts;
 
 typedef struct {
-  int    precision;        /* TLRMVN_FP64 / TLRMVN_FP32 / TLRMVN_BF16_SHIFT                          */
+  int    precision;        /* TLRMVN_FP64 / TLRMVN_FP32 / TLRMVN_BF16_SHIFT / TLRMVN_FP16_SHIFT      */
   int    n_shifts;         /* M >= 1 random shifts ("batches")                                      */
   int    n_points;         /* N >= 1 lattice points per shift                                       */
   int    periodize;        /* nonzero: tent (baker's) transform of each lattice coordinate          */
@@ -177,7 +180,7 @@ int tlrmvn_prob_device(tlrmvn_factor_t f, const double* a, const double* b, doub
  *   threads   threads per block of the float32 sweep; 0 = the occupancy rule
  *   chunk     samples in flight per pass; 0 = as many as fit the memory rule
  *             (opts->sample_chunk, when set, still takes precedence)
- *   tc_ctas   whole-tile sweeps of the BF16-shift path sharing an SM (1..6)
+ *   tc_ctas   whole-tile sweeps of the BF16-/FP16-shift paths sharing an SM (1..6)
  *   ms        tlrmvn_autotune: device milliseconds per solve of the choice (-1
  *             when it came from the cache); candidates: how many were timed */
 typedef struct {
@@ -336,6 +339,14 @@ int tlrmvn_selftest_wait_timeout(int polls, void* stream);
  * its error bound.  TLRMVN_E_INVAL for bad arguments, TLRMVN_E_CUDA on a
  * device error. */
 int tlrmvn_selftest_phi_neg(const float* x, int n, float* out);
+
+/* Evaluates, on the GPU, the float32 normal quantile that the float sweep uses
+ * (Wichura's AS 241 rational approximations, PPND7; no counterpart in the
+ * paper) at n host pairs (p, lp), p in [0, 1/2] and lp = log p (which carries
+ * the value when p underflows to 0), writing Phi^-1 to n host floats out
+ * (1 <= n <= 2^24); for tests of its error bound.  TLRMVN_E_INVAL for bad
+ * arguments, TLRMVN_E_CUDA on a device error. */
+int tlrmvn_selftest_ndtri(const float* p, const float* lp, int n, float* out);
 
 /* Kernel classes of the integrand, for tlrmvn_profile_get.  On the BF16-shift
  * path with tiles of more than 64 variables the shifts, the coupling and the

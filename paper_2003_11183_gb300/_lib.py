@@ -71,6 +71,8 @@ SIGNATURES = {
     "tlrmvn_profile_reset": (C.c_int, []),
     "tlrmvn_profile_get": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "tlrmvn_selftest_wait_timeout": (C.c_int, [C.c_int, C.c_void_p]),
+    "tlrmvn_selftest_ndtri": (C.c_int, [C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_int,
+                                        C.POINTER(C.c_float)]),
     "tlrmvn_selftest_phi_neg": (C.c_int, [C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_float)]),
     "tlrmvn_strerror": (C.c_char_p, [C.c_int]),
     "tlrmvn_last_error": (C.c_char_p, []),

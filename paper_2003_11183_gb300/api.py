@@ -13,7 +13,7 @@ import numpy as np
 
 from . import _lib as L
 
-FP64, FP32, BF16_SHIFT = 0, 1, 2
+FP64, FP32, BF16_SHIFT, FP16_SHIFT = 0, 1, 2, 3
 REORDER_NONE, REORDER_BLOCK, REORDER_ITERATIVE = 0, 1, 2
 KERNEL_EXP, KERNEL_MATERN15, KERNEL_EXP_MATERN15 = 0, 1, 2
 E_INVAL, E_NOT_SPD, E_NOMEM, E_CUDA, E_FORMAT, E_NOTSUP, E_TIMEOUT, E_RANK, E_BUSY = 1, 2, 3, 4, 5, 6, 7, 8, 9
@@ -448,4 +448,16 @@ def tlrmvn_selftest_phi_neg(x) -> np.ndarray:
     out = np.empty_like(xs)
     _check(lib.tlrmvn_selftest_phi_neg(xs.ctypes.data_as(C.POINTER(C.c_float)), int(xs.size),
                                        out.ctypes.data_as(C.POINTER(C.c_float))), "tlrmvn_selftest_phi_neg")
+    return out
+
+
+def tlrmvn_selftest_ndtri(p, lp) -> np.ndarray:
+    """The float sweep's normal quantile evaluated on the GPU at float32 (p, log p) pairs."""
+    lib = L.load()
+    ps = np.ascontiguousarray(p, dtype=np.float32)
+    lps = np.ascontiguousarray(lp, dtype=np.float32)
+    out = np.empty_like(ps)
+    fp = C.POINTER(C.c_float)
+    _check(lib.tlrmvn_selftest_ndtri(ps.ctypes.data_as(fp), lps.ctypes.data_as(fp), int(ps.size),
+                                     out.ctypes.data_as(fp)), "tlrmvn_selftest_ndtri")
     return out

@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 #include <math.h>
 #include <mutex>
@@ -115,17 +116,25 @@ struct Factor {
   int32_t* vmap16 = nullptr;
   std::vector<int64_t> kpad_off;
   int64_t kmax16 = 0, kw16 = 0, my16 = 0;
+  // fp16 operands of the FP16-shift path, same layouts: U16h = U a_ij and V16h = V c_ij
+  // with per-tile powers of two a_ij, c_ij (max |U a| and max |V c| in (1/2, 1], a_ij
+  // raised where the projections' range needs it), B16x2h the fp16 split of B; wscale16
+  // (per Vcat row) = 1 / (a_ij c_ij), the factor applied to a projection before it is stored
+  __half* U16h = nullptr;
+  __half* V16h = nullptr;
+  __half* B16x2h = nullptr;
+  float* wscale16 = nullptr;
   // lattice generators for n + 1 coordinates (device), and the permutation (device)
   uint64_t* Q = nullptr;
   int64_t* dperm = nullptr;
   // guards the lazily made copies when several streams use the factor at once
   std::mutex copy_mu;
-  // launch choices per precision (TLRMVN_FP64 / FP32 / BF16_SHIFT), set by the autotuner
-  Tuning tune[3];
+  // launch choices per precision (TLRMVN_FP64 / FP32 / BF16_SHIFT / FP16_SHIFT), set by the autotuner
+  Tuning tune[4];
   mutable std::mutex tune_mu;
   Tuning tuning(int precision) const {
     std::lock_guard<std::mutex> lk(tune_mu);
-    return tune[precision < 0 || precision > 2 ? 0 : precision];
+    return tune[precision < 0 || precision > 3 ? 0 : precision];
   }
 
   int64_t tsize(int t) const { return tile_off[t + 1] - tile_off[t]; }
@@ -242,37 +251,31 @@ __device__ __forceinline__ double ndtri_lower(double p, double lp) {
   }
   return x;
 }
-// float32: the rational approximation alone is below float rounding.
+// float32: Wichura's rational approximations of the normal quantile (M. J.
+// Wichura, Algorithm AS 241, Applied Statistics 37 (1988) 477-484, the PPND7
+// variant: relative error about 1e-7), coefficients as published.  Both forms
+// are evaluated and one is selected, so a warp whose samples fall in different
+// regions takes no divergent branch: the central form in q = p - 1/2 (used for
+// p >= 0.075), and the tail forms in t = sqrt(-log p) (t <= 5 and t > 5), which
+// take lp = log p so that the quantile stays finite when p itself underflows.
+// Evaluated in float32 the result is within about 4e-7 relative of Phi^-1.
 __device__ __forceinline__ float ndtri_lower(float p, float lp) {
-  if (p < (float)Acklam::p_low) {
-    float q = sqrtf(-2.0f * lp);
-    float num = (float)Acklam::c1;
-    num = num * q + (float)Acklam::c2;
-    num = num * q + (float)Acklam::c3;
-    num = num * q + (float)Acklam::c4;
-    num = num * q + (float)Acklam::c5;
-    num = num * q + (float)Acklam::c6;
-    float den = (float)Acklam::d1;
-    den = den * q + (float)Acklam::d2;
-    den = den * q + (float)Acklam::d3;
-    den = den * q + (float)Acklam::d4;
-    den = den * q + 1.0f;
-    return num / den;
-  }
-  float q = p - 0.5f, rr = q * q;
-  float num = (float)Acklam::a1;
-  num = num * rr + (float)Acklam::a2;
-  num = num * rr + (float)Acklam::a3;
-  num = num * rr + (float)Acklam::a4;
-  num = num * rr + (float)Acklam::a5;
-  num = num * rr + (float)Acklam::a6;
-  float den = (float)Acklam::b1;
-  den = den * rr + (float)Acklam::b2;
-  den = den * rr + (float)Acklam::b3;
-  den = den * rr + (float)Acklam::b4;
-  den = den * rr + (float)Acklam::b5;
-  den = den * rr + 1.0f;
-  return num * q / den;
+  const float q = p - 0.5f;  // (exact for p in [1/4, 1/2])
+  const float r = fmaf(-q, q, 0.180625f);
+  float cn = fmaf(fmaf(fmaf(5.9109374720e+01f, r, 1.5929113202e+02f), r, 5.0434271938e+01f), r, 3.3871327179e+00f);
+  const float cd = fmaf(fmaf(fmaf(6.7187563600e+01f, r, 7.8757757664e+01f), r, 1.7895169469e+01f), r, 1.0f);
+  cn *= q;
+  const float nl = fminf(fmaxf(-lp, 0.0f), 3.0e38f);
+  const float t = nl * rsqrtf(fmaxf(nl, 1e-30f));  // sqrt(-log p)
+  const bool mid = t <= 5.0f;
+  const float s = t - (mid ? 1.6f : 5.0f);
+  const float c3 = mid ? 1.7023821103e-01f : 1.7337203997e-02f, c2 = mid ? 1.3067284816e+00f : 4.2868294337e-01f;
+  const float c1 = mid ? 2.7568153900e+00f : 3.0812263860e+00f, c0 = mid ? 1.4234372777e+00f : 6.6579051150e+00f;
+  const float d2 = mid ? 1.2021132975e-01f : 1.2258202635e-02f, d1 = mid ? 7.3700164250e-01f : 2.4197894225e-01f;
+  const float tn = fmaf(fmaf(fmaf(c3, s, c2), s, c1), s, c0);
+  const float td = fmaf(fmaf(d2, s, d1), s, 1.0f);
+  const bool central = q >= -0.425f;
+  return __fdividef(central ? cn : -tn, central ? cd : td);
 }
 
 __device__ __forceinline__ double dev_log(double x) { return log(x); }

@@ -256,6 +256,55 @@ __global__ void k_split_b16(const double* B, int m, int64_t my, int64_t count, _
 
 static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// FP16-shift operands.  Largest |entry| of each Ucat column (rank) of every row
+// tile, and of each Vcat row: out[g] for global rank index g (Ucat columns in
+// krow order, Vcat rows in kcol order).
+__global__ void k_rank_absmax_u(const double* Ucat, const int64_t* krow_off, const int32_t* ktile, int m,
+                                int64_t ktot, double* out) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= ktot) return;
+  const int i = ktile[g];
+  const int64_t Kr = krow_off[i + 1] - krow_off[i], k = g - krow_off[i];
+  const double* col = Ucat + (int64_t)m * krow_off[i] + k;
+  double mx = 0.0;
+  for (int v = 0; v < m; v++) mx = fmax(mx, fabs(col[(int64_t)v * Kr]));
+  out[g] = mx;
+}
+__global__ void k_rank_absmax_v(const double* Vcat, int m, int64_t ktot, double* out) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= ktot) return;
+  double mx = 0.0;
+  for (int u = 0; u < m; u++) mx = fmax(mx, fabs(Vcat[g * m + u]));
+  out[g] = mx;
+}
+// U16h[(i*m + v) * kmax + k] = fp16(Ucat_i[v][k] su[krow_off[i] + k]) for k < Krow_i, else 0
+__global__ void k_pad_u16h(const double* Ucat, const int64_t* krow_off, const float* su, int m, int64_t kmax,
+                           int64_t count, __half* U16h) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  const int64_t row = t / kmax, k = t % kmax, i = row / m, v = row % m;
+  const int64_t Kr = krow_off[i + 1] - krow_off[i];
+  U16h[t] = (k < Kr) ? __double2half(Ucat[(int64_t)m * krow_off[i] + v * Kr + k] * (double)su[krow_off[i] + k])
+                     : __float2half(0.f);
+}
+// V16h[row * my + u] = fp16(Vcat[row][u] sv[row]) for u < m, else 0
+__global__ void k_pad_v16h(const double* Vcat, const float* sv, int m, int64_t my, int64_t count, __half* V16h) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  const int64_t row = t / my, u = t % my;
+  V16h[t] = (u < m) ? __double2half(Vcat[row * m + u] * (double)sv[row]) : __float2half(0.f);
+}
+// B16x2h: as B16x2 with fp16 hi = fp16(B_i[v][u]) and lo = fp16(B_i[v][u] - hi)
+__global__ void k_split_b16h(const double* B, int m, int64_t my, int64_t count, __half* out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  const int64_t row = t / (2 * my), c = t % (2 * my);
+  const int64_t u = c % my, h = c / my, i = row / m, v = row % m;
+  const double b = (u < m) ? B[(i * m + v) * m + u] : 0.0;
+  const __half hi = __double2half(b);
+  out[t] = h ? __double2half(b - (double)__half2float(hi)) : hi;
+}
+
 // float32 diagonal tiles: row-major B32, transposed BT32 (ld ldbt), reciprocal diagonal inv32
 // band32[(i*m + v)*16 + k] = B_i[v+1+k][v] (k < 15, v+1+k < m), else 0
 __global__ void k_make_band(const double* B, int m, int64_t count, float* band) {
@@ -293,10 +342,14 @@ static int ensure_copies_locked(Factor& F, int precision, cudaStream_t st);
 static bool bf16_ready(const Factor& F) {
   return !F.kpad_off.empty() && (F.ktot == 0 || (F.U16 && F.V16 && F.vmap16)) && F.B16x2;
 }
+static bool fp16_ready(const Factor& F) {
+  return bf16_ready(F) && (F.ktot == 0 || (F.U16h && F.V16h && F.wscale16)) && F.B16x2h;
+}
 static bool copies_ready(const Factor& F, int precision) {
   if (precision == TLRMVN_FP64) return true;
   if (!F.B32 || !F.BT32 || !F.inv32 || !F.band32) return false;
   if (precision == TLRMVN_FP32) return (F.U32 && F.V32) || F.ktot == 0;
+  if (precision == TLRMVN_FP16_SHIFT) return fp16_ready(F);
   return bf16_ready(F);
 }
 static int ensure_copies(Factor& F, int precision, cudaStream_t st) {
@@ -306,6 +359,113 @@ static int ensure_copies(Factor& F, int precision, cudaStream_t st) {
   TLR_CUDA(cudaStreamSynchronize(st));
   return TLRMVN_OK;
 }
+// FP16-shift operands with per-tile scaling (the factor's bf16 layout must exist).
+// For each off-diagonal tile (i, j) with rank > 0: c_ij = 2^-ceil(log2 max|V_ij|)
+// brings max |V c| into (1/2, 1]; a_ij = 2^-ceil(log2 max|U_ij|) does the same for
+// U, and is raised, when needed, until the tile's projections fit fp16: a
+// projection of the scaled V times the inverse 1 / (a c) is bounded by
+// mt_j * 9 * max|V c| / (a c) (|y| < 9: the quantile of the lattice's smallest
+// point), kept below 2^15.  A tile whose raised a would take max |U a| above
+// 2^15 cannot be held in fp16: TLRMVN_E_NOTSUP.
+static int make_fp16_copies(Factor& F, cudaStream_t st) {
+  dfree(F.U16h);
+  dfree(F.V16h);
+  dfree(F.B16x2h);
+  dfree(F.wscale16);
+  const int r = F.r, m = F.m;
+  {
+    const int64_t nb2 = (int64_t)r * m * 2 * F.my16;
+    TLR_CHECK(dalloc(&F.B16x2h, nb2));
+    k_split_b16h<<<blocks_for(nb2, 256), 256, 0, st>>>(F.B, m, F.my16, nb2, F.B16x2h);
+  }
+  if (F.ktot == 0) return TLRMVN_OK;
+  std::vector<int32_t> ktile(F.ktot);
+  for (int i = 0; i < r; i++)
+    for (int64_t g = F.krow_off[i]; g < F.krow_off[i + 1]; g++) ktile[g] = i;
+  int32_t* dkt = nullptr;
+  int64_t* dkro = nullptr;
+  double* dmax = nullptr;
+  float *dsu = nullptr, *dsv = nullptr;
+  auto cleanup = [&] {
+    dfree(dkt);
+    dfree(dkro);
+    dfree(dmax);
+    dfree(dsu);
+    dfree(dsv);
+  };
+  int s = dalloc(&dkt, (size_t)F.ktot);
+  if (s == TLRMVN_OK) s = dalloc(&dkro, (size_t)r + 1);
+  if (s == TLRMVN_OK) s = dalloc(&dmax, (size_t)2 * F.ktot);
+  if (s != TLRMVN_OK) {
+    cleanup();
+    return s;
+  }
+  std::vector<double> hmax(2 * F.ktot);
+  cudaError_t e = cudaMemcpyAsync(dkt, ktile.data(), ktile.size() * 4, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dkro, F.krow_off.data(), (r + 1) * 8, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    k_rank_absmax_u<<<blocks_for(F.ktot, 256), 256, 0, st>>>(F.Ucat, dkro, dkt, m, F.ktot, dmax);
+    k_rank_absmax_v<<<blocks_for(F.ktot, 256), 256, 0, st>>>(F.Vcat, m, F.ktot, dmax + F.ktot);
+    e = cudaMemcpyAsync(hmax.data(), dmax, hmax.size() * 8, cudaMemcpyDeviceToHost, st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cleanup();
+    return cuda_fail(e, "fp16 copies: rank maxima");
+  }
+  std::vector<float> su(F.ktot), sv(F.ktot), ws(F.ktot);
+  for (int j = 0; j < r; j++) {
+    int64_t vrow = F.kcol_off[j];
+    for (int i = j + 1; i < r; i++) {
+      const int k = F.rank[(size_t)i * r + j];
+      if (!k) continue;
+      int64_t ucol = F.krow_off[i];
+      for (int t = 0; t < j; t++) ucol += F.rank[(size_t)i * r + t];
+      double mu = 0.0, mv = 0.0;
+      for (int q = 0; q < k; q++) {
+        mu = std::max(mu, hmax[ucol + q]);
+        mv = std::max(mv, hmax[F.ktot + vrow + q]);
+      }
+      const double c = mv > 0.0 ? std::ldexp(1.0, -(int)std::ceil(std::log2(mv))) : 1.0;
+      double a = mu > 0.0 ? std::ldexp(1.0, -(int)std::ceil(std::log2(mu))) : 1.0;
+      const double bound = (double)F.tsize(j) * 9.0 * mv * c;  // |projection| before the inverse scale
+      while (bound / (a * c) > 32768.0 && mu * a <= 16384.0) a *= 2.0;
+      if (bound / (a * c) > 32768.0) {
+        cleanup();
+        return fail(TLRMVN_E_NOTSUP, "FP16 shifts: tile (" + std::to_string(i) + ", " + std::to_string(j) +
+                                         ") exceeds fp16's range after scaling");
+      }
+      for (int q = 0; q < k; q++) {
+        su[ucol + q] = (float)a;
+        sv[vrow + q] = (float)c;
+        ws[vrow + q] = (float)(1.0 / (a * c));
+      }
+      vrow += k;
+    }
+  }
+  s = dalloc(&dsu, (size_t)F.ktot);
+  if (s == TLRMVN_OK) s = dalloc(&dsv, (size_t)F.ktot);
+  if (s == TLRMVN_OK) s = dalloc(&F.wscale16, (size_t)F.ktot);
+  const int64_t nu16 = (int64_t)r * m * F.kmax16, nv16 = F.ktot * F.my16;
+  if (s == TLRMVN_OK) s = dalloc(&F.U16h, (size_t)nu16);
+  if (s == TLRMVN_OK) s = dalloc(&F.V16h, (size_t)nv16);
+  if (s != TLRMVN_OK) {
+    cleanup();
+    return s;
+  }
+  e = cudaMemcpyAsync(dsu, su.data(), su.size() * 4, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dsv, sv.data(), sv.size() * 4, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(F.wscale16, ws.data(), ws.size() * 4, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    k_pad_u16h<<<blocks_for(nu16, 256), 256, 0, st>>>(F.Ucat, dkro, dsu, m, F.kmax16, nu16, F.U16h);
+    k_pad_v16h<<<blocks_for(nv16, 256), 256, 0, st>>>(F.Vcat, dsv, m, F.my16, nv16, F.V16h);
+    e = cudaStreamSynchronize(st);
+  }
+  cleanup();
+  if (e != cudaSuccess) return cuda_fail(e, "fp16 copies");
+  return TLRMVN_OK;
+}
+
 static int ensure_copies_locked(Factor& F, int precision, cudaStream_t st) {
   const int64_t nu = (int64_t)F.m * F.ktot;
   if (precision != TLRMVN_FP64) TLR_CHECK(ensure_float_tiles(F, st));
@@ -317,7 +477,7 @@ static int ensure_copies_locked(Factor& F, int precision, cudaStream_t st) {
     k_convert<double, float><<<blocks_for(nu, 256), 256, 0, st>>>(F.Ucat, F.U32, nu);
     k_convert<double, float><<<blocks_for(nu, 256), 256, 0, st>>>(F.Vcat, F.V32, nu);
   }
-  if (precision == TLRMVN_BF16_SHIFT && !bf16_ready(F)) {
+  if ((precision == TLRMVN_BF16_SHIFT || precision == TLRMVN_FP16_SHIFT) && !bf16_ready(F)) {
     // (a failed earlier attempt may have left some of these behind)
     dfree(F.U16);
     dfree(F.V16);
@@ -365,6 +525,7 @@ static int ensure_copies_locked(Factor& F, int precision, cudaStream_t st) {
       dfree(dkro);
     }
   }
+  if (precision == TLRMVN_FP16_SHIFT && !fp16_ready(F)) TLR_CHECK(make_fp16_copies(F, st));
   TLR_CUDA(cudaGetLastError());
   return TLRMVN_OK;
 }
@@ -381,18 +542,19 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   }
   return fn;
 }
-// 2-D bf16 tensor (inner x outer, row pitch in bytes), box 64 x box_outer, 128-byte swizzle.
-// bf16 2-D map with a box of box_inner (64: 128-byte swizzle, 32: 64-byte
-// swizzle) x box_outer elements.
+// 2-D map of a 16-bit tensor (bf16, or fp16 when f16; inner x outer, row pitch in
+// bytes) with a box of box_inner (64: 128-byte swizzle, 32: 64-byte swizzle) x
+// box_outer elements.
 static int make_map(CUtensorMap* map, const void* base, uint64_t inner, uint64_t outer, uint64_t pitch,
-                    uint32_t box_outer, uint32_t box_inner = 64) {
+                    uint32_t box_outer, uint32_t box_inner = 64, bool f16 = false) {
   auto enc = tensor_map_encoder();
   if (!enc) return fail(TLRMVN_E_CUDA, "cuTensorMapEncodeTiled is not available");
   cuuint64_t dims[2] = {inner, outer};
   cuuint64_t strides[1] = {pitch};
   cuuint32_t box[2] = {box_inner, box_outer};
   cuuint32_t es[2] = {1, 1};
-  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+  CUresult r = enc(map, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                   const_cast<void*>(base), dims, strides, box, es,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, box_inner == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(TLRMVN_E_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
@@ -547,13 +709,16 @@ static SweepShape sweep_shape(int64_t C, int mt, int forced) {
   memo = best;
   return best;
 }
-// The whole-tile sweep of the BF16-shift path, by (periodisation, one-sided) flags.
+// The whole-tile sweep of the BF16- and FP16-shift paths, by (periodisation,
+// one-sided) flags and operand type.
 typedef void (*SweepTcKernel)(const CUtensorMap, const CUtensorMap, const CUtensorMap, const CUtensorMap,
                               const CUtensorMap, const CUtensorMap, SweepTcArgs);
-static SweepTcKernel sweep_tc_kernel(int flags) {
-  static const SweepTcKernel table[4] = {k_sweep_tc<0>, k_sweep_tc<SWEEP_PERIODIZE>, k_sweep_tc<SWEEP_ONE_SIDED>,
-                                         k_sweep_tc<SWEEP_PERIODIZE | SWEEP_ONE_SIDED>};
-  return table[((flags & SWEEP_PERIODIZE) ? 1 : 0) | ((flags & SWEEP_ONE_SIDED) ? 2 : 0)];
+static SweepTcKernel sweep_tc_kernel(int flags, bool f16) {
+  static const SweepTcKernel table[8] = {
+      k_sweep_tc<0, false>, k_sweep_tc<SWEEP_PERIODIZE, false>, k_sweep_tc<SWEEP_ONE_SIDED, false>,
+      k_sweep_tc<SWEEP_PERIODIZE | SWEEP_ONE_SIDED, false>, k_sweep_tc<0, true>, k_sweep_tc<SWEEP_PERIODIZE, true>,
+      k_sweep_tc<SWEEP_ONE_SIDED, true>, k_sweep_tc<SWEEP_PERIODIZE | SWEEP_ONE_SIDED, true>};
+  return table[((flags & SWEEP_PERIODIZE) ? 1 : 0) | ((flags & SWEEP_ONE_SIDED) ? 2 : 0) | (f16 ? 4 : 0)];
 }
 // Dynamic shared memory of a whole-tile sweep launch with `ctas` CTAs per SM:
 // the kernel's own need, or more so that no more than `ctas` fit (tuning).
@@ -573,7 +738,7 @@ static int set_sweep_smem(int sub) {
   for (int flags = 0; flags < 8; flags++)
     TLR_CHECK(raise_smem_limit((const void*)sweep_kernel(flags), sweep_smem_bytes(sub, 256)));
   for (int flags = 0; flags < 8; flags++)
-    TLR_CHECK(raise_smem_limit((const void*)sweep_tc_kernel(flags), sweep_tc_launch_smem(1)));
+    TLR_CHECK(raise_smem_limit((const void*)sweep_tc_kernel(flags, flags >= 4), sweep_tc_launch_smem(1)));
   return TLRMVN_OK;
 }
 
@@ -585,16 +750,17 @@ static int set_sweep_smem(int sub) {
 struct TcOperands {
   CUtensorMap mapB32, mapY32, mapY64;
   CUtensorMap mapW{}, mapU64{}, mapV64{};
-  __nv_bfloat16* W = nullptr;
+  unsigned short* W = nullptr;
   int64_t ldw = 0;
   int64_t my;
   int* err;
+  bool f16 = false;  // fp16 operands (FP16-shift path), else bf16
 };
 
 // Whole diagonal tile i on the BF16-shift path: one launch of k_sweep_tc
 // (low-rank shifts, in-tile coupling, sweep and projections).
 static void sweep_tile_tc(const Factor& F, int i, int64_t C, const Lims& L, const float* rs32, const uint64_t* dD,
-                          int64_t c0, int64_t N, int64_t Cc, int periodize, __nv_bfloat16* Ys, int64_t ldys,
+                          int64_t c0, int64_t N, int64_t Cc, int periodize, unsigned short* Ys, int64_t ldys,
                           double* logP, const TcOperands& tco, const Tuning& tu, cudaStream_t st, Prof& pf) {
   const int m = F.m, mt = (int)F.tsize(i);
   SweepTcArgs t;
@@ -620,7 +786,7 @@ static void sweep_tile_tc(const Factor& F, int i, int64_t C, const Lims& L, cons
   a.first = (i == 0);
   a.Yv = nullptr;
   a.ldyv = 0;
-  a.Ys = Ys;
+  a.Ys = reinterpret_cast<__nv_bfloat16*>(Ys);  // (16-bit words of the operand type)
   a.ldys = ldys;
   a.ys_lo = tco.my;
   a.logP = logP;
@@ -635,10 +801,11 @@ static void sweep_tile_tc(const Factor& F, int i, int64_t C, const Lims& L, cons
   t.W = tco.W;
   t.ldw = tco.ldw;
   t.vmap = F.vmap16 ? F.vmap16 + F.kcol_off[i] : nullptr;
+  t.wscale = (tco.f16 && F.wscale16) ? F.wscale16 + F.kcol_off[i] : nullptr;
   t.err = tco.err;
   const int flags = (periodize ? SWEEP_PERIODIZE : 0) | (L.one_sided ? SWEEP_ONE_SIDED : 0);
   pf.begin(TLRMVN_KC_DIAG);
-  launch_pdl(sweep_tc_kernel(flags), dim3((unsigned)((Cc + STC_NS - 1) / STC_NS)), dim3(STC_NS),
+  launch_pdl(sweep_tc_kernel(flags, tco.f16), dim3((unsigned)((Cc + STC_NS - 1) / STC_NS)), dim3(STC_NS),
              sweep_tc_launch_smem(tu.tc_ctas), st, tco.mapY32, tco.mapB32, tco.mapW, tco.mapU64, tco.mapY64,
              tco.mapV64, t);
   pf.end();
@@ -808,9 +975,10 @@ static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opt
                            const uint64_t* dD, double* logP, Scratch& sc, cudaStream_t st, Prof& pf) {
   const int64_t M = o.n_shifts, N = o.n_points, S = M * N;
   const int m = F.m;
+  const bool f16 = o.precision == TLRMVN_FP16_SHIFT;
   const int64_t ly = 2 * F.my16;  // Y16 row: hi halves, then lo halves
   const int64_t C = chunk_bf16(o, tu, S, F.kw16, ly);
-  __nv_bfloat16 *W = nullptr, *Y = nullptr;
+  unsigned short *W = nullptr, *Y = nullptr;
   float* rs32 = nullptr;
   int* err = nullptr;
   const int64_t ldw = (C + 63) / 64 * 64;
@@ -829,13 +997,17 @@ static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opt
   //   coupling   T += Y16 rows (A, hi/lo) x B16x2 rows (B, hi/lo)
   //   projection T = Y16 rows (A, hi) x V16 rows (B)
   TcOperands tco;
-  TLR_CHECK(make_map(&tco.mapB32, F.B16x2, ly, (uint64_t)F.r * m, ly * 2, 64, 32));
-  TLR_CHECK(make_map(&tco.mapY32, Y, ly, C, ly * 2, STC_NS, 32));
-  TLR_CHECK(make_map(&tco.mapY64, Y, ly, C, ly * 2, STC_NS));
-  TLR_CHECK(make_map(&tco.mapW, W, ldw, F.kw16, ldw * 2, 64));
+  tco.f16 = f16;
+  const void* B2 = f16 ? (const void*)F.B16x2h : (const void*)F.B16x2;
+  TLR_CHECK(make_map(&tco.mapB32, B2, ly, (uint64_t)F.r * m, ly * 2, 64, 32, f16));
+  TLR_CHECK(make_map(&tco.mapY32, Y, ly, C, ly * 2, STC_NS, 32, f16));
+  TLR_CHECK(make_map(&tco.mapY64, Y, ly, C, ly * 2, STC_NS, 64, f16));
+  TLR_CHECK(make_map(&tco.mapW, W, ldw, F.kw16, ldw * 2, 64, 64, f16));
   if (F.ktot) {
-    TLR_CHECK(make_map(&tco.mapU64, F.U16, F.kmax16, (uint64_t)F.r * m, F.kmax16 * 2, 64));
-    TLR_CHECK(make_map(&tco.mapV64, F.V16, F.my16, F.ktot, F.my16 * 2, 64));
+    const void* U = f16 ? (const void*)F.U16h : (const void*)F.U16;
+    const void* V = f16 ? (const void*)F.V16h : (const void*)F.V16;
+    TLR_CHECK(make_map(&tco.mapU64, U, F.kmax16, (uint64_t)F.r * m, F.kmax16 * 2, 64, 64, f16));
+    TLR_CHECK(make_map(&tco.mapV64, V, F.my16, F.ktot, F.my16 * 2, 64, 64, f16));
   } else {
     tco.mapU64 = tco.mapW;  // (never read: no tile has ranks)
     tco.mapV64 = tco.mapW;
@@ -871,7 +1043,7 @@ int64_t prob_scratch_bytes(const Factor& F, const tlrmvn_opts& o) {
   const int64_t M = o.n_shifts, N = o.n_points, S = M * N, n = F.n, m = F.m;
   const Tuning tu = F.tuning(o.precision);
   int64_t bytes = n * (8 * 2 + 4 * 2) + M * (n + 1) * 8 + M * 8 + S * 8 + 256;
-  if (o.precision == TLRMVN_BF16_SHIFT) {
+  if (o.precision == TLRMVN_BF16_SHIFT || o.precision == TLRMVN_FP16_SHIFT) {
     int64_t kw = 0;
     for (int i = 0; i < F.r; i++) kw += (F.krow(i) + 63) / 64 * 64;
     kw = std::max<int64_t>(kw, 64);
@@ -955,7 +1127,7 @@ int prob_impl(Factor& F, const double* a_dev, const double* b_dev, double nu, co
 static int check_opts(const Factor& F, double nu, const tlrmvn_opts* o) {
   if (!o) return fail(TLRMVN_E_INVAL, "null options");
   if (o->n_shifts < 1 || o->n_points < 1) return fail(TLRMVN_E_INVAL, "n_shifts and n_points must be >= 1");
-  if (o->precision < TLRMVN_FP64 || o->precision > TLRMVN_BF16_SHIFT) return fail(TLRMVN_E_INVAL, "bad precision");
+  if (o->precision < TLRMVN_FP64 || o->precision > TLRMVN_FP16_SHIFT) return fail(TLRMVN_E_INVAL, "bad precision");
   if (!(nu > 0.0)) return fail(TLRMVN_E_INVAL, "nu must be > 0 (INFINITY for the normal case)");
   (void)F;
   return TLRMVN_OK;
@@ -1064,5 +1236,29 @@ extern "C" int tlrmvn_selftest_phi_neg(const float* x, int n, float* out) {
   cudaFreeAsync(d, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "phi self-test");
+  return TLRMVN_OK;
+}
+
+// Evaluates the float path's normal quantile (ndtri_lower: AS 241, log input) on n host values.
+__global__ void k_ndtri_selftest(const float* p, const float* lp, int n, float* out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) out[t] = ndtri_lower(p[t], lp[t]);
+}
+
+extern "C" int tlrmvn_selftest_ndtri(const float* p, const float* lp, int n, float* out) {
+  if (!p || !lp || !out || n < 1 || n > (1 << 24)) return fail(TLRMVN_E_INVAL, "bad arguments");
+  cudaStream_t st = pick_stream(nullptr);
+  float* d = nullptr;
+  TLR_CUDA(cudaMallocAsync((void**)&d, (size_t)3 * n * sizeof(float), st));
+  cudaError_t e = cudaMemcpyAsync(d, p, (size_t)n * sizeof(float), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d + n, lp, (size_t)n * sizeof(float), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    k_ndtri_selftest<<<(n + 255) / 256, 256, 0, st>>>(d, d + n, n, d + 2 * n);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, d + 2 * n, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(d, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "quantile self-test");
   return TLRMVN_OK;
 }

@@ -113,6 +113,10 @@ Factor::~Factor() {
   dfree(V16);
   dfree(B16x2);
   dfree(vmap16);
+  dfree(U16h);
+  dfree(V16h);
+  dfree(B16x2h);
+  dfree(wscale16);
   dfree(Q);
   dfree(dperm);
 }

@@ -167,7 +167,7 @@ extern "C" int tlrmvn_server_submit(tlrmvn_server_t srv, int factor, const doubl
   if (!srv || !a || !b || !opts || !request_id) return fail(TLRMVN_E_INVAL, "null argument");
   Server& S = *reinterpret_cast<Server*>(srv);
   if (factor < 0 || factor >= (int)S.factors.size()) return fail(TLRMVN_E_INVAL, "factor index out of range");
-  if (opts->n_shifts < 1 || opts->n_points < 1 || opts->precision < 0 || opts->precision > 2 || !(nu > 0.0))
+  if (opts->n_shifts < 1 || opts->n_points < 1 || opts->precision < 0 || opts->precision > 3 || !(nu > 0.0))
     return fail(TLRMVN_E_INVAL, "bad options");
   const Factor& F = *S.factors[factor];
   Request* r = new Request();

@@ -97,12 +97,13 @@ __device__ __forceinline__ void lattice_wf(uint64_t x, int periodize, float& w, 
 // eq. (2) for one variable in float32.  The one-sided case (at = -inf), which is
 // the whole integrand for upper-limit problems, has a branch-free fast path for
 // bt >= -12 (Phi(bt) > 1.7e-33): one complementary error function of |bt|, one
-// log, and CUDA's normal quantile; samples of one warp take the same
-// instructions whatever the sign of their limit.  log Phi(bt) near 1 uses
-// Goldberg's form of log1p (D. Goldberg, What every computer scientist should
-// know about floating-point arithmetic, 1991, Theorem 4): log1p(-c) =
-// log(s) * (-c) / (s - 1) with s = fl(1 - c).  Quantiles whose probability is
-// below 1e-30, and limits below -12, go through the log-domain code.
+// log, and the library's float quantile (ndtri_lower, AS 241); samples of one
+// warp take the same instructions whatever the sign of their limit.  log Phi(bt)
+// near 1 uses Goldberg's form of log1p (D. Goldberg, What every computer
+// scientist should know about floating-point arithmetic, 1991, Theorem 4):
+// log1p(-c) = log(s) * (-c) / (s - 1) with s = fl(1 - c).  Quantiles whose
+// probability is below 1e-30 take the log of that probability from logs of its
+// factors, and limits below -12 go through the log-domain code.
 __device__ __forceinline__ void sov_step_f32(float at, float bt, float w, float wc, float& ld, float& y) {
   const float rs2 = (float)TLR_RSQRT2;
   if (at == -INFINITY && bt != INFINITY) {
@@ -117,13 +118,10 @@ __device__ __forceinline__ void sov_step_f32(float at, float bt, float w, float 
       const float u = w * ph, uc = pc + wc * ph;  // u + uc = 1
       const bool lower = u <= uc;
       const float pp = lower ? u : uc;
-      if (pp >= 1e-30f) {
-        const float z = normcdfinvf(pp);
-        y = lower ? z : -z;
-      } else {  // u underflows: quantile from log u
-        const float lu = logf(w) + ld;
-        y = ndtri_lower(expf(lu), lu);
-      }
+      float lpp = __logf(pp);
+      if (pp < 1e-30f) lpp = logf(w) + ld;  // (u underflows: its log from the logs of its factors)
+      const float z = ndtri_lower(pp, lpp);
+      y = lower ? z : -z;
       return;
     }
     const float t = -bt * rs2;
@@ -182,13 +180,10 @@ __device__ __forceinline__ void sov_step_f32_upper(float bt, float w, float wc, 
     const float u = w * ph, uc = pc + wc * ph;  // u + uc = 1
     const bool lower = u <= uc;
     const float pp = lower ? u : uc;
-    if (pp >= 1e-30f) {
-      const float z = normcdfinvf(pp);
-      y = lower ? z : -z;
-    } else {  // u underflows: quantile from log u (here ph < 1/2, so log Phi(bt) = log ph)
-      const float lu = logf(w) + logf(ph);
-      y = ndtri_lower(expf(lu), lu);
-    }
+    float lpp = __logf(pp);
+    if (pp < 1e-30f) lpp = logf(w) + logf(ph);  // (u underflows; here ph < 1/2, so log Phi(bt) = log ph)
+    const float z = ndtri_lower(pp, lpp);
+    y = lower ? z : -z;
     return;
   }
   float ld;

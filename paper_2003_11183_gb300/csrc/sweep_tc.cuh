@@ -45,6 +45,33 @@ constexpr int STC_NS = 128;   // samples per CTA (TMEM lanes)
 constexpr int STC_KB = 32;    // K depth of a coupling k-block
 using StcCfg = tc::Cfg<64, true, false, STC_KB, 1>;
 
+// The 16-bit operand type of the products: bf16 (BF16-shift path) or fp16
+// (FP16-shift path), as raw 16-bit words.  pack rounds two floats to the type
+// (round to nearest even) and returns them packed low word first, with their
+// rounded values in ra, rb.
+template <bool F16>
+struct Op16;
+template <>
+struct Op16<false> {
+  static __device__ __forceinline__ uint32_t pack(float a, float b, float& ra, float& rb) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    ra = __low2float(h);
+    rb = __high2float(h);
+    return ((uint32_t)__bfloat16_as_ushort(h.y) << 16) | __bfloat16_as_ushort(h.x);
+  }
+  static __device__ __forceinline__ unsigned short one(float a) { return __bfloat16_as_ushort(__float2bfloat16_rn(a)); }
+};
+template <>
+struct Op16<true> {
+  static __device__ __forceinline__ uint32_t pack(float a, float b, float& ra, float& rb) {
+    const __half2 h = __floats2half2_rn(a, b);
+    ra = __low2float(h);
+    rb = __high2float(h);
+    return ((uint32_t)__half_as_ushort(h.y) << 16) | __half_as_ushort(h.x);
+  }
+  static __device__ __forceinline__ unsigned short one(float a) { return __half_as_ushort(__float2half_rn(a)); }
+};
+
 struct SweepTcArgs {
   DiagArgs32 d;  // pointers at the tile's first variable; d.mt = tile size; d.Ys and d.ys_lo required
                  // (d.Delta unused: the low-rank shifts are products of this kernel)
@@ -53,9 +80,11 @@ struct SweepTcArgs {
   int urow0;     // row of the tile's first variable in the U map
   int krow0, kr; // the tile's rank rows in the W map (first, count; 0: no low-rank shift)
   int kcol0, kc; // the tile's column ranks: first row in the V map, count (0: no projection)
-  __nv_bfloat16* W;       // projections, rank-major: W[vmap[r] * ldw + sample]
+  unsigned short* W;      // projections (16-bit words of the operand type), rank-major: W[vmap[r] * ldw + sample]
   int64_t ldw;
   const int32_t* vmap;    // at the tile's first column rank
+  const float* wscale;    // FP16 path: per column rank, the factor applied to a projection before it is
+                          // stored (the inverse of the per-tile scales of U and V); null on the BF16 path
   int* err;
 };
 using StcProjCfg = tc::Cfg<64, false, false, 64, 1>;  // projection k-block: y rows x V rows, 64 deep
@@ -71,12 +100,16 @@ __host__ __device__ constexpr size_t sweep_tc_smem_bytes() {
   return 1024 /*align*/ + (size_t)StcCfg::SB + STC_SUB * (sizeof(float4) + sizeof(uint64_t)) + 64;
 }
 
-template <int FLAGS>
+template <int FLAGS, bool F16>
 __global__ void __launch_bounds__(STC_NS, 6)
     k_sweep_tc(const __grid_constant__ CUtensorMap mapY, const __grid_constant__ CUtensorMap mapB,
                const __grid_constant__ CUtensorMap mapW, const __grid_constant__ CUtensorMap mapU,
                const __grid_constant__ CUtensorMap mapY64, const __grid_constant__ CUtensorMap mapV, SweepTcArgs p) {
   constexpr bool PER = FLAGS & SWEEP_PERIODIZE, ONE = FLAGS & SWEEP_ONE_SIDED;
+  using Op = Op16<F16>;
+  constexpr uint32_t ID_C = F16 ? StcCfg::IDESC_F16 : StcCfg::IDESC;
+  constexpr uint32_t ID_S = F16 ? StcShiftCfg::IDESC_F16 : StcShiftCfg::IDESC;
+  constexpr uint32_t ID_P = F16 ? StcProjCfg::IDESC_F16 : StcProjCfg::IDESC;
   constexpr uint32_t A_BYTES = StcCfg::A_BYTES, HALF = StcCfg::HALF, SB = StcCfg::SB;
   extern __shared__ __align__(1024) unsigned char stc_smem[];
   // (offset within the shared window, so that the accesses stay shared-memory ones)
@@ -174,15 +207,15 @@ __global__ void __launch_bounds__(STC_NS, 6)
           // per 16-deep step: MN-major W two 1 KB K groups on (+128), U rows 32 bytes on (+2)
 #pragma unroll
           for (int kk = 0; kk < 4; kk++)
-            tc::mma_bf16(*tmem_slot, dw + (uint64_t)(128 * kk), du + (uint64_t)(2 * kk), StcShiftCfg::IDESC,
+            tc::mma_f16(*tmem_slot, dw + (uint64_t)(128 * kk), du + (uint64_t)(2 * kk), ID_S,
                          (kb > 0 || kk > 0) ? 1u : 0u);
         } else {
 #pragma unroll
           for (int kk = 0; kk < STC_KB / 16; kk++) {
             const uint64_t o = (uint64_t)(kk * 2);  // 32 bytes per 16-deep step, in 16-byte units
-            tc::mma_bf16(*tmem_slot, dah + o, dbh + o, StcCfg::IDESC, (kb > 0 || kk > 0) ? 1u : 0u);
-            tc::mma_bf16(*tmem_slot, dah + o, dbl + o, StcCfg::IDESC, 1u);
-            tc::mma_bf16(*tmem_slot, dal + o, dbh + o, StcCfg::IDESC, 1u);
+            tc::mma_f16(*tmem_slot, dah + o, dbh + o, ID_C, (kb > 0 || kk > 0) ? 1u : 0u);
+            tc::mma_f16(*tmem_slot, dah + o, dbl + o, ID_C, 1u);
+            tc::mma_f16(*tmem_slot, dal + o, dbh + o, ID_C, 1u);
           }
         }
         tc::mma_commit(freeb);
@@ -311,15 +344,14 @@ __global__ void __launch_bounds__(STC_NS, 6)
             : "r"(tl + (uint32_t)v0));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (act) {
-          __nv_bfloat16* row = d.Ys + (int64_t)cs * d.ldys + q0 + v0;
+          unsigned short* row = reinterpret_cast<unsigned short*>(d.Ys) + (int64_t)cs * d.ldys + q0 + v0;
           uint32_t hi2[DIAG_VB / 2], lo2[DIAG_VB / 2];
 #pragma unroll
           for (int j = 0; j < DIAG_VB; j += 2) {
             const float y0 = __uint_as_float(r[j]), y1 = __uint_as_float(r[j + 1]);
-            const __nv_bfloat162 h = __floats2bfloat162_rn(y0, y1);
-            const __nv_bfloat162 l = __floats2bfloat162_rn(y0 - __low2float(h), y1 - __high2float(h));
-            hi2[j / 2] = *reinterpret_cast<const uint32_t*>(&h);
-            lo2[j / 2] = *reinterpret_cast<const uint32_t*>(&l);
+            float h0, h1, l0, l1;
+            hi2[j / 2] = Op::pack(y0, y1, h0, h1);
+            lo2[j / 2] = Op::pack(y0 - h0, y1 - h1, l0, l1);
           }
           if (nb == DIAG_VB) {
             uint4* dh = reinterpret_cast<uint4*>(row);
@@ -368,7 +400,7 @@ __global__ void __launch_bounds__(STC_NS, 6)
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
         for (int kk = 0; kk < 4; kk++)
-          tc::mma_bf16(*tmem_slot, da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), StcProjCfg::IDESC,
+          tc::mma_f16(*tmem_slot, da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), ID_P,
                        (kb > 0 || kk > 0) ? 1u : 0u);
         tc::mma_commit(freeb);
         if (!tc::mbar_wait(freeb, (ph >> 1) & 1, p.err, 9)) {
@@ -402,7 +434,8 @@ __global__ void __launch_bounds__(STC_NS, 6)
 #pragma unroll
         for (int j = 0; j < 16; j++)
           if (r0 + h + j < p.kc)
-            p.W[(int64_t)p.vmap[r0 + h + j] * p.ldw + cs] = __float2bfloat16_rn(__uint_as_float(r[j]));
+            p.W[(int64_t)p.vmap[r0 + h + j] * p.ldw + cs] =
+                Op::one(F16 ? __uint_as_float(r[j]) * p.wscale[r0 + h + j] : __uint_as_float(r[j]));
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

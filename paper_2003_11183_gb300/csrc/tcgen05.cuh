@@ -1,9 +1,10 @@
 // tcgen05 / TMA building blocks of the tensor-core products (sm_103a): stage
 // shapes and instruction descriptors, shared-memory matrix descriptors, bounded
-// mbarrier waits, 2-D TMA loads, the bf16 MMA and its commit.  Used by the
+// mbarrier waits, 2-D TMA loads, the 16-bit (bf16 or fp16) MMA and its commit.  Used by the
 // whole-tile sweep of the BF16-shift integrand (sweep_tc.cuh), whose products are
 //
-//   D (M x N) += A (M x K) * B (N x K)^T     bf16 operands: B K-major; A K-major,
+//   D (M x N) += A (M x K) * B (N x K)^T     bf16 or fp16 operands (both the same type):
+//                                             B K-major; A K-major,
 //                                             or MN-major (A_MN: stored K x M, M contiguous)
 //
 // with M = 128 (TMEM lanes = samples), fp32 accumulation in TMEM, operands staged
@@ -34,10 +35,12 @@ struct Cfg {
   static constexpr int NST = NSTQ > 0 ? NSTQ : (SPLIT ? 1 : ((4 * SB <= 100 * 1024) ? 4 : 2));
   static constexpr int SMEM = NST * SB + 1024 /*align*/ + 256 /*barriers*/;
   // instruction descriptor of tcgen05.mma kind::f16: fp32 accumulator, bf16 A
-  // and B, both K-major, N = BN (bits 17-22 hold N/8), M = 128 (bits 24-28 hold M/16)
-  // (bit 15 set: A is MN-major)
+  // and B (bits 7-9 and 10-12: format 1), both K-major, N = BN (bits 17-22 hold
+  // N/8), M = 128 (bits 24-28 hold M/16) (bit 15 set: A is MN-major); IDESC_F16:
+  // the same with fp16 A and B (format 0)
   static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((A_MN ? 1u : 0u) << 15) |
                                     ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+  static constexpr uint32_t IDESC_F16 = IDESC & ~((7u << 7) | (7u << 10));
   static_assert(BN == 64 || BN == 128 || BN == 256, "N of the MMA");
   static_assert(KB == 64 || KB == 32, "stage depth");
   static_assert(!A_MN || KB == 64, "the MN-major operand uses 64-deep stages");
@@ -106,7 +109,7 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
           tmem_d),

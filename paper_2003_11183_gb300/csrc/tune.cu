@@ -43,7 +43,7 @@ static std::string tune_key(const Factor& F, int precision, int64_t S, bool mvt)
 
 static std::vector<Tuning> candidates(const Factor& F, int precision, int64_t S) {
   std::vector<Tuning> c;
-  if (precision == TLRMVN_BF16_SHIFT) {
+  if (precision == TLRMVN_BF16_SHIFT || precision == TLRMVN_FP16_SHIFT) {
     for (int ctas : {6, 4})
       for (int64_t chunk : {(int64_t)0, (S / 2 + 255) / 256 * 256}) {
         Tuning t;
@@ -141,7 +141,7 @@ extern "C" int tlrmvn_autotune(tlrmvn_factor_t f, const double* a, const double*
                                const tlrmvn_opts* opts, const char* cache_path, int force, tlrmvn_tuning* out) {
   if (!f || !a || !b || !opts) return fail(TLRMVN_E_INVAL, "null argument");
   if (opts->n_shifts < 1 || opts->n_points < 1) return fail(TLRMVN_E_INVAL, "n_shifts and n_points must be >= 1");
-  if (opts->precision < TLRMVN_FP64 || opts->precision > TLRMVN_BF16_SHIFT) return fail(TLRMVN_E_INVAL, "bad precision");
+  if (opts->precision < TLRMVN_FP64 || opts->precision > TLRMVN_FP16_SHIFT) return fail(TLRMVN_E_INVAL, "bad precision");
   if (!(nu > 0.0)) return fail(TLRMVN_E_INVAL, "nu must be > 0 (INFINITY for the normal case)");
   Factor& F = *reinterpret_cast<Factor*>(f);
   const int prec = opts->precision;
@@ -200,7 +200,7 @@ extern "C" int tlrmvn_autotune(tlrmvn_factor_t f, const double* a, const double*
 
 extern "C" int tlrmvn_get_tuning(tlrmvn_factor_t f, int precision, tlrmvn_tuning* out) {
   if (!f || !out) return fail(TLRMVN_E_INVAL, "null argument");
-  if (precision < TLRMVN_FP64 || precision > TLRMVN_BF16_SHIFT) return fail(TLRMVN_E_INVAL, "bad precision");
+  if (precision < TLRMVN_FP64 || precision > TLRMVN_FP16_SHIFT) return fail(TLRMVN_E_INVAL, "bad precision");
   const Tuning t = reinterpret_cast<Factor*>(f)->tuning(precision);
   out->sub = t.sub;
   out->threads = t.threads;
@@ -213,7 +213,7 @@ extern "C" int tlrmvn_get_tuning(tlrmvn_factor_t f, int precision, tlrmvn_tuning
 
 extern "C" int tlrmvn_set_tuning(tlrmvn_factor_t f, int precision, const tlrmvn_tuning* t) {
   if (!f || !t) return fail(TLRMVN_E_INVAL, "null argument");
-  if (precision < TLRMVN_FP64 || precision > TLRMVN_BF16_SHIFT) return fail(TLRMVN_E_INVAL, "bad precision");
+  if (precision < TLRMVN_FP64 || precision > TLRMVN_FP16_SHIFT) return fail(TLRMVN_E_INVAL, "bad precision");
   if ((t->sub != 32 && t->sub != 64 && t->sub != 128) || (precision != TLRMVN_FP64 && t->sub == 32) ||
       (precision == TLRMVN_FP64 && t->sub == 128))
     return fail(TLRMVN_E_INVAL, "sub must be 64 or 128 (float32) / 32 or 64 (float64)");

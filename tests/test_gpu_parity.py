@@ -79,9 +79,10 @@ def test_two_sided_and_upper_tail_limits(tl, m):
     assert np.all(rel(pm, ref["per_sample"]) < 1e-9)
     (lp, err, ps, pm), ref = run_both(tl, F, OF, w, tl.FP32)
     assert np.all(rel(ps, ref["per_shift"]) < 1e-4)
-    (lp, err, ps, pm), ref = run_both(tl, F, OF, w, tl.BF16_SHIFT)
-    assert np.all(rel(ps, ref["per_shift"]) < 1e-2)
-    assert np.all(np.isfinite(pm))
+    for prec in (tl.BF16_SHIFT, tl.FP16_SHIFT):
+        (lp, err, ps, pm), ref = run_both(tl, F, OF, w, prec)
+        assert np.all(rel(ps, ref["per_shift"]) < 1e-2)
+        assert np.all(np.isfinite(pm))
 
 
 @pytest.mark.parametrize("m", [48, 128])
@@ -105,9 +106,10 @@ def test_deep_tail_limits(tl, m):
     (lp, err, ps, pm), ref = run_both(tl, F, OF, w, tl.FP32)
     assert np.all(np.isfinite(pm))
     assert np.all(rel(ps, ref["per_shift"]) < 1e-4)
-    (lp, err, ps, pm), ref = run_both(tl, F, OF, w, tl.BF16_SHIFT)
-    assert np.all(np.isfinite(pm))
-    assert np.all(rel(ps, ref["per_shift"]) < 1e-2)
+    for prec in (tl.BF16_SHIFT, tl.FP16_SHIFT):
+        (lp, err, ps, pm), ref = run_both(tl, F, OF, w, prec)
+        assert np.all(np.isfinite(pm))
+        assert np.all(rel(ps, ref["per_shift"]) < 1e-2)
 
 
 @pytest.mark.parametrize("nu", [math.inf, 7.0])
@@ -227,9 +229,10 @@ def test_config1_full_size_fp64(tl):
     assert np.array_equal(own.perm, OF.perm)
 
 
+@pytest.mark.parametrize("precision", ["BF16_SHIFT", "FP16_SHIFT"])
 @pytest.mark.parametrize("nu", [math.inf, 7.0])
 @pytest.mark.parametrize("m,ragged,points", [(64, None, 512), (50, 390, 512), (128, 390, 301)])
-def test_bf16_shift_path(tl, nu, m, ragged, points):
+def test_bf16_shift_path(tl, nu, m, ragged, points, precision):
     # bf16 tensor-core shifts: per-shift log-probability within 1e-2 relative,
     # and the estimate within 3 QMC standard errors of the oracle's.  Tiles of
     # 128 take the whole-tile sweep (two 64-variable sub-tiles, the last tile 6
@@ -237,7 +240,7 @@ def test_bf16_shift_path(tl, nu, m, ragged, points):
     w = synth.small_workload(16, m, 39, nu=nu, n_shifts=8, n_points=points, ragged_n=ragged)
     OF, _ = oracle_factor(w)
     F = tl.tlrmvn_factor_import(export_bytes(OF))
-    (lp, err, ps, pm), ref = run_both(tl, F, OF, w, tl.BF16_SHIFT)
+    (lp, err, ps, pm), ref = run_both(tl, F, OF, w, getattr(tl, precision))
     assert np.all(rel(ps, ref["per_shift"]) < 1e-2)
     assert abs(lp - ref["logp"]) <= 3 * max(err, ref["err"])
     assert np.all(np.isfinite(pm))
@@ -296,15 +299,17 @@ def headline_family(request, tl):
     return w, F, ref
 
 
-def test_headline_family_bf16_shift_every_sample_and_shift(tl, headline_family):
-    # BF16-shift path (the bench's precision) against the oracle on the same factor,
-    # every per-sample and every per-shift value: per shift 1e-2 relative, the
-    # estimate within 3 QMC standard errors, per sample 1e-2 relative (each sample's
-    # log integrand is a sum over thousands of variables whose limit shifts carry
-    # bf16 operand rounding; the derivation is in the design notes)
+@pytest.mark.parametrize("precision", ["BF16_SHIFT", "FP16_SHIFT"])
+def test_headline_family_bf16_shift_every_sample_and_shift(tl, headline_family, precision):
+    # BF16-shift path (the bench's precision) and the FP16-shift path (per-tile
+    # scaled fp16 operands) against the oracle on the same factor, every per-sample
+    # and every per-shift value: per shift 1e-2 relative, the estimate within 3 QMC
+    # standard errors, per sample 1e-2 relative (each sample's log integrand is a sum
+    # over thousands of variables whose limit shifts carry 16-bit operand rounding;
+    # the derivation is in the design notes)
     w, F, ref = headline_family
-    lp, err, ps, pm = tl.tlrmvn_prob(F, w.a, w.b, w.nu, tl.BF16_SHIFT, w.n_shifts, w.n_points, shifts=w.shifts,
-                                     per_shift=True, per_sample=True)
+    lp, err, ps, pm = tl.tlrmvn_prob(F, w.a, w.b, w.nu, getattr(tl, precision), w.n_shifts, w.n_points,
+                                     shifts=w.shifts, per_shift=True, per_sample=True)
     r_shift = rel(ps, ref["per_shift"])
     r_sample = rel(pm, ref["per_sample"])
     assert np.all(np.isfinite(pm))
@@ -444,3 +449,40 @@ def test_rank_cap_policy(tl):
     # a cap that does not bind passes under the strict policy
     F2 = tl.tlrmvn_factor_kernel(w.xy, w.kernel, w.params, w.nugget, w.a, w.b, w.m, 1e-4, 0, 1, strict_rank=True)
     assert tl.tlrmvn_factor_info(F2)["capped"] == 0
+
+
+def test_float_quantile_error_bound(tl):
+    # the float sweep's own normal quantile (AS 241, PPND7, evaluated in float32)
+    # against the float64 quantile of the same float32 inputs: relative error within
+    # 1e-6 (about 8 ulp) on [1e-30, 1/2] and, from the log of the probability alone,
+    # down to log p = -700
+    from scipy.special import ndtri, ndtri_exp
+    p = np.concatenate([np.geomspace(1e-30, 0.5, 200001), np.linspace(0.3, 0.5, 20001)]).astype(np.float32)
+    lp = np.log(p.astype(np.float64)).astype(np.float32)
+    got = tl.tlrmvn_selftest_ndtri(p, lp).astype(np.float64)
+    want = ndtri(p.astype(np.float64))
+    ok = want != 0.0
+    assert np.max(np.abs(got[ok] / want[ok] - 1.0)) < 1e-6
+    assert np.all(got[~ok] == 0.0)
+    lpd = -np.geomspace(69.0, 700.0, 20001).astype(np.float32)
+    got = tl.tlrmvn_selftest_ndtri(np.zeros_like(lpd), lpd).astype(np.float64)
+    want = ndtri_exp(lpd.astype(np.float64))
+    assert np.max(np.abs(got / want - 1.0)) < 1e-6
+
+
+def test_fp16_per_tile_scaling_keeps_small_factors(tl):
+    # a tight truncation (tol 1e-10) keeps rank terms whose entries lie far below
+    # fp16's normal range (6.1e-5); the per-tile power-of-two scaling of U and V
+    # (inverse applied to the projections) keeps them representable: the FP16-shift
+    # path stays within the 16-bit tolerance of the oracle and at least as close to
+    # it as the BF16-shift path on every shift
+    w = synth.small_workload(24, 64, 43, nu=7.0, n_shifts=6, n_points=400, tol=1e-10)
+    OF, _ = oracle_factor(w)
+    small = min(np.abs(u).max() for u in OF.U.values() if u.shape[1])
+    assert small < 6.1e-5
+    F = tl.tlrmvn_factor_import(export_bytes(OF))
+    (_, _, ps16, pm16), ref = run_both(tl, F, OF, w, tl.FP16_SHIFT)
+    (_, _, psb, pmb), _ = run_both(tl, F, OF, w, tl.BF16_SHIFT)
+    r16, rb = rel(ps16, ref["per_shift"]), rel(psb, ref["per_shift"])
+    assert np.all(r16 < 1e-2)
+    assert np.max(np.abs(pm16 - ref["per_sample"])) <= np.max(np.abs(pmb - ref["per_sample"]))

@@ -28,7 +28,7 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2}
+PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2, "fp16": 3}
 METRIC = "MVN/MVT QMC sample-dims/sec at n=65,536 vs FP64 path; p50/p99 solve latency"
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of a kernel from one
 # ncu capture, divided by the sample-dimensions the captured launch processed,
@@ -514,8 +514,8 @@ def run_ours(args):
             ach = work["sweep"] * units / (d["avg_launch_ms"] / 1e3) / 1e12
             d.update(bound="alu", unit="TFLOP/s", achieved=ach, peak=fp32_peak, frac=ach / fp32_peak,
                      peak_source=fp32_src, flops_per_sample_dim=work["sweep"], sample_dims_per_launch=units,
-                     kernel={0: "k_diag<double>", 1: "k_diag_f32", 2: "k_sweep_tc"}[prec])
-            if prec == 2:
+                     kernel={0: "k_diag<double>", 1: "k_diag_f32", 2: "k_sweep_tc", 3: "k_sweep_tc"}[prec])
+            if prec >= 2:
                 tach = work["tensor"] * units / (d["avg_launch_ms"] / 1e3) / 1e12
                 d["tensor_share"] = {"bound": "tensor", "unit": "TFLOP/s", "achieved": tach, "peak": bf16_peak,
                                      "frac": tach / bf16_peak, "flops_per_sample_dim": work["tensor"],
@@ -579,7 +579,7 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": "sample-dims/s",
                 "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": {0: "f64", 1: "f32", 2: "f32+bf16"}[prec], "data": "synthetic",
+                "dtype": {0: "f64", 1: "f32", 2: "f32+bf16", 3: "f32+fp16"}[prec], "data": "synthetic",
                 "config": dict(bench_config(tl, F, w, args.precision), sample_chunk=args.sample_chunk or "all",
                                tuning=tuned),
                 "clocks": clk,

@@ -678,6 +678,65 @@ def run_serving(args):
     return 0
 
 
+def run_study(args):
+    """Convergence study (the shape of Section 4, Table 3): for an MVN problem on a
+    perturbed grid with an exponential kernel and a = -inf, b_i ~ N(5.5, 1.25^2)
+    (the paper's simulated limits), tile m = sqrt(n), the same problem is solved
+    with the geometric order alone, with Algorithm 4 and with Algorithm 5, at
+    N = 1,000 and 10,000 lattice points per shift (20 shifts), and the line
+    reports each estimate, its relative error (the QMC standard error over the
+    estimate) and the device time.  The paper's claim under test: the block
+    reorderings lower the error at equal N (Section 4)."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2003_11183_gb300 as tl
+    import synth
+    g = args.n_side or 128
+    n = g * g
+    m = int(round(math.sqrt(n)))
+    prec = PRECISIONS[args.precision if args.precision != "bf16" else "fp64"]
+    rows = []
+    for beta, tol in ((0.3, 1e-4), (0.1, 1e-3)):
+        xy = synth.jittered_grid(g, 8000)
+        a, b = synth.limits_normal(n, 8001, 5.5, 1.25)
+        for reorder, name in ((tl.REORDER_NONE, "tlrmvn (geometric order)"),
+                              (tl.REORDER_BLOCK, "rtlrmvn (Algorithm 4)"),
+                              (tl.REORDER_ITERATIVE, "rrtlrmvn (Algorithm 5)")):
+            t0 = time.perf_counter()
+            F = tl.tlrmvn_factor_kernel(xy, tl.KERNEL_EXP, (beta,), 1e-8, a, b, m, tol, 0, reorder)
+            fs = time.perf_counter() - t0
+            info = tl.tlrmvn_factor_info(F)
+            for pts in (1000, 10000):
+                shifts = synth.lattice_shifts(20, n + 1, 8100 + pts)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                lp, err, _, _ = tl.tlrmvn_prob(F, a, b, math.inf, prec, 20, pts, shifts=shifts)
+                t = time.perf_counter() - t0
+                rows.append({"beta": beta, "tol": tol, "method": name, "reorder": reorder, "points": pts,
+                             "shifts": 20, "logp": lp, "rel_err": err, "seconds": t, "factor_seconds": fs,
+                             "k_total": info["k_total"]})
+    # agreement of the three orderings (the same probability): largest pairwise gap in
+    # log p over the combined standard errors, per beta and N
+    agree = {}
+    for beta in (0.3, 0.1):
+        for pts in (1000, 10000):
+            sel = [r for r in rows if r["beta"] == beta and r["points"] == pts]
+            gap = max(abs(x["logp"] - y["logp"]) / math.hypot(x["rel_err"], y["rel_err"]) for x in sel for y in sel
+                      if x is not y)
+            agree[f"beta{beta}_N{pts}"] = gap
+    line = {"metric": "QMC relative error at equal N: geometric order vs Algorithm 4 vs Algorithm 5",
+            "value": min(r["rel_err"] for r in rows), "unit": "relative error", "n_gpus": 1, "steps": len(rows),
+            "warmup": 0, "higher_is_better": False, "data": "synthetic",
+            "dtype": {0: "f64", 1: "f32", 2: "f32+bf16", 3: "f32+fp16"}[prec],
+            "config": {"workload": f"study_mvn_n{n}_exp", "n": n, "tile": m, "limits": "a=-inf, b~N(5.5,1.25^2)",
+                       "kernel": "exponential", "betas": [0.3, 0.1], "tols": [1e-4, 1e-3], "shifts": 20},
+            "rows": rows, "max_gap_in_combined_se": agree}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -686,6 +745,8 @@ def main():
         return run_batched(args)
     if args.workload == 5:
         return run_serving(args)
+    if args.workload == 6:
+        return run_study(args)
     return run_ours(args)
 
 

@@ -341,10 +341,11 @@ int tlrmvn_selftest_wait_timeout(int polls, void* stream);
 int tlrmvn_selftest_phi_neg(const float* x, int n, float* out);
 
 /* Evaluates, on the GPU, the float32 normal quantile that the float sweep uses
- * (Wichura's AS 241 rational approximations, PPND7; no counterpart in the
- * paper) at n host pairs (p, lp), p in [0, 1/2] and lp = log p (which carries
- * the value when p underflows to 0), writing Phi^-1 to n host floats out
- * (1 <= n <= 2^24); for tests of its error bound.  TLRMVN_E_INVAL for bad
+ * (the library's own polynomial fit in Giles' variable -log(4p(1-p)) for
+ * p > 0.0017, Wichura's AS 241 tail forms below; no counterpart in the paper) at
+ * n host pairs (p, lp), p in [0, 1/2] and lp = log p (read when p < 1e-30, where
+ * it carries the value: p may underflow to 0), writing Phi^-1 to n host floats
+ * out (1 <= n <= 2^24); for tests of its error bound.  TLRMVN_E_INVAL for bad
  * arguments, TLRMVN_E_CUDA on a device error. */
 int tlrmvn_selftest_ndtri(const float* p, const float* lp, int n, float* out);
 

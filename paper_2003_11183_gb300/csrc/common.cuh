@@ -116,14 +116,18 @@ struct Factor {
   int32_t* vmap16 = nullptr;
   std::vector<int64_t> kpad_off;
   int64_t kmax16 = 0, kw16 = 0, my16 = 0;
-  // fp16 operands of the FP16-shift path, same layouts: U16h = U a_ij and V16h = V c_ij
-  // with per-tile powers of two a_ij, c_ij (max |U a| and max |V c| in (1/2, 1], a_ij
-  // raised where the projections' range needs it), B16x2h the fp16 split of B; wscale16
+  // fp16 operands of the FP16-shift path, same layouts: U16h = U g a_ij and V16h = V c_ij
+  // with per-tile powers of two a_ij, c_ij (max |U g a| and max |V c| in (1/2, 1], a_ij
+  // raised where the projections' range needs it), B16x2h the fp16 split of B g; wscale16
   // (per Vcat row) = 1 / (a_ij c_ij), the factor applied to a projection before it is stored
   __half* U16h = nullptr;
   __half* V16h = nullptr;
   __half* B16x2h = nullptr;
   float* wscale16 = nullptr;
+  // the fp16 products are of the factor scaled by g (a power of two with max |B g| in
+  // (1/2, 1], so that badly scaled covariances keep fp16's range); the sweep multiplies
+  // what it reads from the products by inv_g16 = 1 / g
+  float inv_g16 = 1.0f;
   // lattice generators for n + 1 coordinates (device), and the permutation (device)
   uint64_t* Q = nullptr;
   int64_t* dperm = nullptr;
@@ -251,32 +255,54 @@ __device__ __forceinline__ double ndtri_lower(double p, double lp) {
   }
   return x;
 }
-// float32: Wichura's rational approximations of the normal quantile (M. J.
-// Wichura, Algorithm AS 241, Applied Statistics 37 (1988) 477-484, the PPND7
-// variant: relative error about 1e-7), coefficients as published.  Both forms
-// are evaluated and one is selected, so a warp whose samples fall in different
-// regions takes no divergent branch: the central form in q = p - 1/2 (used for
-// p >= 0.075), and the tail forms in t = sqrt(-log p) (t <= 5 and t > 5), which
-// take lp = log p so that the quantile stays finite when p itself underflows.
-// Evaluated in float32 the result is within about 4e-7 relative of Phi^-1.
-__device__ __forceinline__ float ndtri_lower(float p, float lp) {
-  const float q = p - 0.5f;  // (exact for p in [1/4, 1/2])
-  const float r = fmaf(-q, q, 0.180625f);
-  float cn = fmaf(fmaf(fmaf(5.9109374720e+01f, r, 1.5929113202e+02f), r, 5.0434271938e+01f), r, 3.3871327179e+00f);
-  const float cd = fmaf(fmaf(fmaf(6.7187563600e+01f, r, 7.8757757664e+01f), r, 1.7895169469e+01f), r, 1.0f);
-  cn *= q;
+// float32 normal quantile, lower half.  Two regions:
+//  * p > 0.0017 (w = -log(4 p (1 - p)) < 5; all but about 1 in 300 calls):
+//    Phi^-1(p) = -sqrt(2) (1 - 2p) R(w), R(w) = erfinv(1 - 2p) / (1 - 2p) as a
+//    degree-8 polynomial in w - 2.5 (the variable of M. Giles, Approximating the
+//    erfinv function, GPU Computing Gems, 2011; coefficients from the library's
+//    own fit, csrc/fit_ndtri.py, relative error about 2.2e-7 in float32);
+//  * below: Wichura's tail forms in t = sqrt(-log p) (M. J. Wichura, Algorithm AS
+//    241, Applied Statistics 37 (1988) 477-484, PPND7, coefficients as
+//    published: t <= 5 and t > 5), from log p, so that the quantile stays finite
+//    when p underflows (to log p = -700: relative error about 4e-7 in float32).
+// lp_tiny = log p is read only when p < 1e-30 (p may then be 0); above that the
+// log is taken here.  A warp takes the tail branch only when one of its lanes
+// falls there.
+__device__ __forceinline__ float ndtri_tail_f32(float lp) {
   const float nl = fminf(fmaxf(-lp, 0.0f), 3.0e38f);
   const float t = nl * rsqrtf(fmaxf(nl, 1e-30f));  // sqrt(-log p)
-  const bool mid = t <= 5.0f;
-  const float s = t - (mid ? 1.6f : 5.0f);
-  const float c3 = mid ? 1.7023821103e-01f : 1.7337203997e-02f, c2 = mid ? 1.3067284816e+00f : 4.2868294337e-01f;
-  const float c1 = mid ? 2.7568153900e+00f : 3.0812263860e+00f, c0 = mid ? 1.4234372777e+00f : 6.6579051150e+00f;
-  const float d2 = mid ? 1.2021132975e-01f : 1.2258202635e-02f, d1 = mid ? 7.3700164250e-01f : 2.4197894225e-01f;
-  const float tn = fmaf(fmaf(fmaf(c3, s, c2), s, c1), s, c0);
-  const float td = fmaf(fmaf(d2, s, d1), s, 1.0f);
-  const bool central = q >= -0.425f;
-  return __fdividef(central ? cn : -tn, central ? cd : td);
+  if (t <= 5.0f) {
+    const float s = t - 1.6f;
+    const float num = fmaf(fmaf(fmaf(1.7023821103e-01f, s, 1.3067284816e+00f), s, 2.7568153900e+00f), s,
+                           1.4234372777e+00f);
+    const float den = fmaf(fmaf(1.2021132975e-01f, s, 7.3700164250e-01f), s, 1.0f);
+    return -num / den;
+  }
+  const float s = t - 5.0f;
+  const float num =
+      fmaf(fmaf(fmaf(1.7337203997e-02f, s, 4.2868294337e-01f), s, 3.0812263860e+00f), s, 6.6579051150e+00f);
+  const float den = fmaf(fmaf(1.2258202635e-02f, s, 2.4197894225e-01f), s, 1.0f);
+  return -num / den;
 }
+__device__ __forceinline__ float ndtri_f32(float p, float lp_tiny) {
+  const float w = -__logf((4.0f * p) * (1.0f - p));
+  if (w < 5.0f) {
+    const float z = w - 2.5f;
+    float r = 2.798955556e-08f;
+    r = fmaf(r, z, 3.430734239e-07f);
+    r = fmaf(r, z, -3.522236511e-06f);
+    r = fmaf(r, z, -4.389634341e-06f);
+    r = fmaf(r, z, 2.185773774e-04f);
+    r = fmaf(r, z, -1.253729803e-03f);
+    r = fmaf(r, z, -4.177678842e-03f);
+    r = fmaf(r, z, 2.466407418e-01f);
+    r = fmaf(r, z, 1.501409411e+00f);
+    return (-1.41421356237f * r) * fmaf(-2.0f, p, 1.0f);
+  }
+  return ndtri_tail_f32(p >= 1e-30f ? __logf(p) : lp_tiny);
+}
+// (the float overload used by the general step: lp = log p)
+__device__ __forceinline__ float ndtri_lower(float p, float lp) { return ndtri_f32(p, lp); }
 
 __device__ __forceinline__ double dev_log(double x) { return log(x); }
 __device__ __forceinline__ float dev_log(float x) { return logf(x); }

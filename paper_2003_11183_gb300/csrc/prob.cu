@@ -256,6 +256,15 @@ __global__ void k_split_b16(const double* B, int m, int64_t my, int64_t count, _
 
 static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// Largest |B| over all diagonal tiles (non-negative doubles order as their bit patterns).
+__global__ void k_absmax(const double* x, int64_t count, unsigned long long* out) {
+  double mx = 0.0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x)
+    mx = fmax(mx, fabs(x[t]));
+  for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(mx));
+}
+
 // FP16-shift operands.  Largest |entry| of each Ucat column (rank) of every row
 // tile, and of each Vcat row: out[g] for global rank index g (Ucat columns in
 // krow order, Vcat rows in kcol order).
@@ -294,13 +303,13 @@ __global__ void k_pad_v16h(const double* Vcat, const float* sv, int m, int64_t m
   const int64_t row = t / my, u = t % my;
   V16h[t] = (u < m) ? __double2half(Vcat[row * m + u] * (double)sv[row]) : __float2half(0.f);
 }
-// B16x2h: as B16x2 with fp16 hi = fp16(B_i[v][u]) and lo = fp16(B_i[v][u] - hi)
-__global__ void k_split_b16h(const double* B, int m, int64_t my, int64_t count, __half* out) {
+// B16x2h: as B16x2 for B g, fp16 hi = fp16(B_i[v][u] g) and lo = fp16(B_i[v][u] g - hi)
+__global__ void k_split_b16h(const double* B, double g, int m, int64_t my, int64_t count, __half* out) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= count) return;
   const int64_t row = t / (2 * my), c = t % (2 * my);
   const int64_t u = c % my, h = c / my, i = row / m, v = row % m;
-  const double b = (u < m) ? B[(i * m + v) * m + u] : 0.0;
+  const double b = (u < m) ? B[(i * m + v) * m + u] * g : 0.0;
   const __half hi = __double2half(b);
   out[t] = h ? __double2half(b - (double)__half2float(hi)) : hi;
 }
@@ -360,23 +369,43 @@ static int ensure_copies(Factor& F, int precision, cudaStream_t st) {
   return TLRMVN_OK;
 }
 // FP16-shift operands with per-tile scaling (the factor's bf16 layout must exist).
-// For each off-diagonal tile (i, j) with rank > 0: c_ij = 2^-ceil(log2 max|V_ij|)
-// brings max |V c| into (1/2, 1]; a_ij = 2^-ceil(log2 max|U_ij|) does the same for
-// U, and is raised, when needed, until the tile's projections fit fp16: a
-// projection of the scaled V times the inverse 1 / (a c) is bounded by
-// mt_j * 9 * max|V c| / (a c) (|y| < 9: the quantile of the lattice's smallest
-// point), kept below 2^15.  A tile whose raised a would take max |U a| above
-// 2^15 cannot be held in fp16: TLRMVN_E_NOTSUP.
+// All products are of the factor scaled by one power of two g with max |B g| in
+// (1/2, 1] (the probability and every y are unchanged by scaling the factor and
+// the limits alike, and the sweep undoes g where it reads the products), so a
+// covariance far from unit scale keeps fp16's range.  For each off-diagonal tile
+// (i, j) with rank > 0: c_ij = 2^-ceil(log2 max|V_ij|) brings max |V c| into
+// (1/2, 1]; a_ij = 2^-ceil(log2 max|U_ij g|) does the same for U g, and is
+// raised, when needed, until the tile's projections fit fp16: a projection of
+// the scaled V times the inverse 1 / (a c) is bounded by mt_j * 9 * max|V c| /
+// (a c) (|y| < 9: the quantile of the lattice's smallest point), kept below
+// 2^15.  A tile whose raised a would take max |U g a| above 2^15 cannot be held
+// in fp16: TLRMVN_E_NOTSUP.
 static int make_fp16_copies(Factor& F, cudaStream_t st) {
   dfree(F.U16h);
   dfree(F.V16h);
   dfree(F.B16x2h);
   dfree(F.wscale16);
   const int r = F.r, m = F.m;
+  double g = 1.0;  // global scale: max |B g| in (1/2, 1]
   {
+    unsigned long long* dmx = nullptr;
+    TLR_CHECK(dalloc(&dmx, 1));
+    unsigned long long hmx = 0;
+    cudaError_t e = cudaMemsetAsync(dmx, 0, 8, st);
+    if (e == cudaSuccess) {
+      k_absmax<<<1024, 256, 0, st>>>(F.B, (int64_t)r * m * m, dmx);
+      e = cudaMemcpyAsync(&hmx, dmx, 8, cudaMemcpyDeviceToHost, st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    dfree(dmx);
+    if (e != cudaSuccess) return cuda_fail(e, "fp16 copies: largest |B|");
+    double mb;
+    memcpy(&mb, &hmx, 8);
+    if (mb > 0.0) g = std::ldexp(1.0, -(int)std::ceil(std::log2(mb)));
     const int64_t nb2 = (int64_t)r * m * 2 * F.my16;
     TLR_CHECK(dalloc(&F.B16x2h, nb2));
-    k_split_b16h<<<blocks_for(nb2, 256), 256, 0, st>>>(F.B, m, F.my16, nb2, F.B16x2h);
+    k_split_b16h<<<blocks_for(nb2, 256), 256, 0, st>>>(F.B, g, m, F.my16, nb2, F.B16x2h);
+    F.inv_g16 = (float)(1.0 / g);
   }
   if (F.ktot == 0) return TLRMVN_OK;
   std::vector<int32_t> ktile(F.ktot);
@@ -427,16 +456,17 @@ static int make_fp16_copies(Factor& F, cudaStream_t st) {
         mv = std::max(mv, hmax[F.ktot + vrow + q]);
       }
       const double c = mv > 0.0 ? std::ldexp(1.0, -(int)std::ceil(std::log2(mv))) : 1.0;
-      double a = mu > 0.0 ? std::ldexp(1.0, -(int)std::ceil(std::log2(mu))) : 1.0;
+      const double mug = mu * g;  // (the products are of the factor scaled by g)
+      double a = mug > 0.0 ? std::ldexp(1.0, -(int)std::ceil(std::log2(mug))) : 1.0;
       const double bound = (double)F.tsize(j) * 9.0 * mv * c;  // |projection| before the inverse scale
-      while (bound / (a * c) > 32768.0 && mu * a <= 16384.0) a *= 2.0;
+      while (bound / (a * c) > 32768.0 && mug * a <= 16384.0) a *= 2.0;
       if (bound / (a * c) > 32768.0) {
         cleanup();
         return fail(TLRMVN_E_NOTSUP, "FP16 shifts: tile (" + std::to_string(i) + ", " + std::to_string(j) +
                                          ") exceeds fp16's range after scaling");
       }
       for (int q = 0; q < k; q++) {
-        su[ucol + q] = (float)a;
+        su[ucol + q] = (float)(a * g);
         sv[vrow + q] = (float)c;
         ws[vrow + q] = (float)(1.0 / (a * c));
       }
@@ -737,8 +767,11 @@ static size_t sweep_tc_launch_smem(int ctas) {
 static int set_sweep_smem(int sub) {
   for (int flags = 0; flags < 8; flags++)
     TLR_CHECK(raise_smem_limit((const void*)sweep_kernel(flags), sweep_smem_bytes(sub, 256)));
-  for (int flags = 0; flags < 8; flags++)
-    TLR_CHECK(raise_smem_limit((const void*)sweep_tc_kernel(flags, flags >= 4), sweep_tc_launch_smem(1)));
+  for (int t = 0; t < 8; t++)  // every (periodisation, one-sided, operand type) variant
+    TLR_CHECK(raise_smem_limit((const void*)sweep_tc_kernel(((t & 1) ? SWEEP_PERIODIZE : 0) |
+                                                                ((t & 2) ? SWEEP_ONE_SIDED : 0),
+                                                            (t & 4) != 0),
+                               sweep_tc_launch_smem(1)));
   return TLRMVN_OK;
 }
 
@@ -802,6 +835,7 @@ static void sweep_tile_tc(const Factor& F, int i, int64_t C, const Lims& L, cons
   t.ldw = tco.ldw;
   t.vmap = F.vmap16 ? F.vmap16 + F.kcol_off[i] : nullptr;
   t.wscale = (tco.f16 && F.wscale16) ? F.wscale16 + F.kcol_off[i] : nullptr;
+  t.tscale = tco.f16 ? F.inv_g16 : 1.0f;
   t.err = tco.err;
   const int flags = (periodize ? SWEEP_PERIODIZE : 0) | (L.one_sided ? SWEEP_ONE_SIDED : 0);
   pf.begin(TLRMVN_KC_DIAG);
@@ -1239,10 +1273,10 @@ extern "C" int tlrmvn_selftest_phi_neg(const float* x, int n, float* out) {
   return TLRMVN_OK;
 }
 
-// Evaluates the float path's normal quantile (ndtri_lower: AS 241, log input) on n host values.
+// Evaluates the float path's normal quantile (ndtri_f32) on n host values.
 __global__ void k_ndtri_selftest(const float* p, const float* lp, int n, float* out) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) out[t] = ndtri_lower(p[t], lp[t]);
+  if (t < n) out[t] = ndtri_f32(p[t], lp[t]);
 }
 
 extern "C" int tlrmvn_selftest_ndtri(const float* p, const float* lp, int n, float* out) {

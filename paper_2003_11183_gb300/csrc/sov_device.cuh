@@ -97,7 +97,7 @@ __device__ __forceinline__ void lattice_wf(uint64_t x, int periodize, float& w, 
 // eq. (2) for one variable in float32.  The one-sided case (at = -inf), which is
 // the whole integrand for upper-limit problems, has a branch-free fast path for
 // bt >= -12 (Phi(bt) > 1.7e-33): one complementary error function of |bt|, one
-// log, and the library's float quantile (ndtri_lower, AS 241); samples of one
+// log, and the library's float quantile (ndtri_f32); samples of one
 // warp take the same instructions whatever the sign of their limit.  log Phi(bt)
 // near 1 uses Goldberg's form of log1p (D. Goldberg, What every computer
 // scientist should know about floating-point arithmetic, 1991, Theorem 4):
@@ -118,9 +118,9 @@ __device__ __forceinline__ void sov_step_f32(float at, float bt, float w, float 
       const float u = w * ph, uc = pc + wc * ph;  // u + uc = 1
       const bool lower = u <= uc;
       const float pp = lower ? u : uc;
-      float lpp = __logf(pp);
+      float lpp = 0.0f;
       if (pp < 1e-30f) lpp = logf(w) + ld;  // (u underflows: its log from the logs of its factors)
-      const float z = ndtri_lower(pp, lpp);
+      const float z = ndtri_f32(pp, lpp);
       y = lower ? z : -z;
       return;
     }
@@ -180,9 +180,9 @@ __device__ __forceinline__ void sov_step_f32_upper(float bt, float w, float wc, 
     const float u = w * ph, uc = pc + wc * ph;  // u + uc = 1
     const bool lower = u <= uc;
     const float pp = lower ? u : uc;
-    float lpp = __logf(pp);
+    float lpp = 0.0f;
     if (pp < 1e-30f) lpp = logf(w) + logf(ph);  // (u underflows; here ph < 1/2, so log Phi(bt) = log ph)
-    const float z = ndtri_lower(pp, lpp);
+    const float z = ndtri_f32(pp, lpp);
     y = lower ? z : -z;
     return;
   }

@@ -85,6 +85,7 @@ struct SweepTcArgs {
   const int32_t* vmap;    // at the tile's first column rank
   const float* wscale;    // FP16 path: per column rank, the factor applied to a projection before it is
                           // stored (the inverse of the per-tile scales of U and V); null on the BF16 path
+  float tscale;           // FP16 path: 1 / g, undoing the products' global scale g where the sweep reads them
   int* err;
 };
 using StcProjCfg = tc::Cfg<64, false, false, 64, 1>;  // projection k-block: y rows x V rows, 64 deep
@@ -263,7 +264,7 @@ __global__ void __launch_bounds__(STC_NS, 6)
             : "r"(tl + (uint32_t)v0));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int j = 0; j < DIAG_VB; j++) dl[j] = __uint_as_float(r[j]);
+        for (int j = 0; j < DIAG_VB; j++) dl[j] = F16 ? __uint_as_float(r[j]) * p.tscale : __uint_as_float(r[j]);
       } else {
 #pragma unroll
         for (int j = 0; j < DIAG_VB; j++) dl[j] = 0.0f;

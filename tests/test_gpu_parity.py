@@ -470,19 +470,28 @@ def test_float_quantile_error_bound(tl):
     assert np.max(np.abs(got / want - 1.0)) < 1e-6
 
 
-def test_fp16_per_tile_scaling_keeps_small_factors(tl):
-    # a tight truncation (tol 1e-10) keeps rank terms whose entries lie far below
-    # fp16's normal range (6.1e-5); the per-tile power-of-two scaling of U and V
-    # (inverse applied to the projections) keeps them representable: the FP16-shift
-    # path stays within the 16-bit tolerance of the oracle and at least as close to
-    # it as the BF16-shift path on every shift
-    w = synth.small_workload(24, 64, 43, nu=7.0, n_shifts=6, n_points=400, tol=1e-10)
-    OF, _ = oracle_factor(w)
-    small = min(np.abs(u).max() for u in OF.U.values() if u.shape[1])
-    assert small < 6.1e-5
-    F = tl.tlrmvn_factor_import(export_bytes(OF))
-    (_, _, ps16, pm16), ref = run_both(tl, F, OF, w, tl.FP16_SHIFT)
-    (_, _, psb, pmb), _ = run_both(tl, F, OF, w, tl.BF16_SHIFT)
-    r16, rb = rel(ps16, ref["per_shift"]), rel(psb, ref["per_shift"])
-    assert np.all(r16 < 1e-2)
-    assert np.max(np.abs(pm16 - ref["per_sample"])) <= np.max(np.abs(pmb - ref["per_sample"]))
+def test_scale_invariance_every_precision(tl):
+    # Phi_n(D a, D b; D Sigma D) = Phi_n(a, b; Sigma) (eq. 1): with D = 2^-20 I every
+    # step of the path scales exactly, so each per-sample value must be bit for bit
+    # that of the unscaled problem in every precision.  The scaled factor's entries
+    # (~1e-6) lie below fp16's normal range: the FP16-shift path meets this only
+    # through its power-of-two normalisation of the products (global g, per-tile a, c).
+    from oracle import geometry
+    w = synth.small_workload(20, 128, 44, nu=7.0, n_shifts=4, n_points=300, tol=1e-6)
+    Sig = geometry.covariance(w.xy, w.kernel, w.params, w.nugget)
+    d = 2.0 ** -20
+    F1 = tl.tlrmvn_factor_dense(Sig, w.a, w.b, w.m, w.tol, 0, 1)
+    F2 = tl.tlrmvn_factor_dense(Sig * d * d, w.a * d, w.b * d, w.m, w.tol * d, 0, 1)
+    e1, e2 = tl.parse_export(tl.tlrmvn_factor_export(F1)), tl.parse_export(tl.tlrmvn_factor_export(F2))
+    assert np.array_equal(e1.perm, e2.perm) and np.array_equal(e1.rank, e2.rank)
+    assert np.array_equal(e1.B * d, e2.B)
+    for prec in (tl.FP64, tl.FP32, tl.BF16_SHIFT, tl.FP16_SHIFT):
+        kw = dict(shifts=w.shifts, per_sample=True)
+        p1 = tl.tlrmvn_prob(F1, w.a, w.b, w.nu, prec, w.n_shifts, w.n_points, **kw)[3]
+        p2 = tl.tlrmvn_prob(F2, w.a * d, w.b * d, w.nu, prec, w.n_shifts, w.n_points, **kw)[3]
+        assert np.array_equal(p1, p2), prec
+    OF = to_oracle_factor(e1)
+    ref = sov.solve(OF, w.a, w.b, w.nu, w.shifts, w.n_points)
+    p16 = tl.tlrmvn_prob(F2, w.a * d, w.b * d, w.nu, tl.FP16_SHIFT, w.n_shifts, w.n_points, shifts=w.shifts,
+                         per_shift=True)[2]
+    assert np.all(rel(p16, ref["per_shift"]) < 1e-2)

@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--n-side", type=int, default=0,
                     help="grid side of a smaller problem of the same family (profiling captures only)")
     ap.add_argument("--no-baselines", action="store_true", help="skip FP64-path and CPU-oracle legs")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the library's default launch choices (profiling captures: fewer launches)")
     ap.add_argument("--sample-chunk", type=int, default=0,
                     help="samples per chunk of the solve (0 = the library's choice: all that fit)")
     ap.add_argument("--count", type=int, default=256, help="problems of the batched workload (--workload 4)")
@@ -433,8 +435,11 @@ def run_ours(args):
     per_shift = torch.zeros(w.n_shifts, dtype=torch.float64, device="cuda")
     # launch choices for this problem: the library's autotuner (untimed setup; cached per box)
     cache = os.path.join(tempfile.gettempdir(), "tlrmvn_tune_cache.txt")
-    tuned = tl.tlrmvn_autotune(F, w.a, w.b, w.nu, prec, n_shifts=w.n_shifts, n_points=w.n_points, shifts=w.shifts,
-                               cache_path=cache, stream=stream)
+    if args.no_tune:
+        tuned = dict(tl.tlrmvn_get_tuning(F, prec), note="library defaults (--no-tune)")
+    else:
+        tuned = tl.tlrmvn_autotune(F, w.a, w.b, w.nu, prec, n_shifts=w.n_shifts, n_points=w.n_points,
+                                   shifts=w.shifts, cache_path=cache, stream=stream)
     kw = dict(nu=w.nu, precision=prec, n_shifts=w.n_shifts, n_points=w.n_points, shifts=w.shifts, stream=stream,
               per_shift=per_shift, sample_chunk=args.sample_chunk)
 
@@ -737,6 +742,44 @@ def run_study(args):
     return 0
 
 
+def run_skewnormal(args):
+    """Skew-normal likelihood (Section 5.1, eq. 6; the shape of Table 4's MLE-TLR
+    column): for n = 4^r, r = 4..7, locations on a 2^r x 2^r grid of spacing 1/15
+    perturbed by U(0, 0.8/15), theta = (xi, sigma1, beta1, sigma2, beta2) =
+    (0, 1, 0.3, 1, 0.3), one draw z of the model (eq. 5); each line reports the time
+    of one log-likelihood evaluation and of its MVN factor (TLR factor of
+    (I + C^T C)^-1 and the float32 integrand, tile sqrt(n), tolerance 1e-5,
+    10 x 1,000 lattice points), after one untimed evaluation."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__ as ge
+    ge.build()
+    import synth
+    from paper_2003_11183_gb300 import skewnormal as sn
+    theta = (0.0, 1.0, 0.3, 1.0, 0.3)
+    rows = []
+    for r in (4, 5, 6, 7):
+        g = 2 ** r
+        n = g * g
+        xy = synth.expanding_grid(g, 1.0 / 15.0, 9000 + r)
+        z = sn.simulate(xy, theta, 9100 + r)
+        kw = dict(tile=int(math.isqrt(n)), tol=1e-5, n_shifts=10, n_points=1000, seed=9200 + r)
+        sn.loglik(z, xy, theta, **kw)
+        tm = {}
+        t0 = time.perf_counter()
+        lf, err = sn.loglik(z, xy, theta, timings=tm, **kw)
+        rows.append({"n": n, "seconds": time.perf_counter() - t0, "mvn_seconds": tm["mvn"],
+                     "dense_seconds": tm["dense"], "loglik": lf, "rel_err_mvn": err})
+    line = {"metric": "skew-normal log-likelihood evaluation time (eq. 6); MVN factor time", "value": rows[-1]["seconds"],
+            "unit": "s", "n_gpus": 1, "steps": len(rows), "warmup": 1, "higher_is_better": False,
+            "dtype": "f64 dense algebra + f32 TLR-QMC", "data": "synthetic",
+            "config": {"workload": "skewnormal_table4_shape", "theta": theta, "grid_spacing": 1 / 15,
+                       "tol": 1e-5, "shifts": 10, "points": 1000, "tile": "sqrt(n)"},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -747,6 +790,8 @@ def main():
         return run_serving(args)
     if args.workload == 6:
         return run_study(args)
+    if args.workload == 7:
+        return run_skewnormal(args)
     return run_ours(args)
 
 

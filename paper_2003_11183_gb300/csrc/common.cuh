@@ -285,19 +285,20 @@ __device__ __forceinline__ float ndtri_tail_f32(float lp) {
   return -num / den;
 }
 __device__ __forceinline__ float ndtri_f32(float p, float lp_tiny) {
-  const float w = -__logf((4.0f * p) * (1.0f - p));
+  const float w = -__logf(p * fmaf(-4.0f, p, 4.0f));  // -log(4 p (1 - p))
   if (w < 5.0f) {
+    // -sqrt(2) R(w) (the fitted coefficients times -sqrt(2)), times x = 1 - 2p
     const float z = w - 2.5f;
-    float r = 2.798955556e-08f;
-    r = fmaf(r, z, 3.430734239e-07f);
-    r = fmaf(r, z, -3.522236511e-06f);
-    r = fmaf(r, z, -4.389634341e-06f);
-    r = fmaf(r, z, 2.185773774e-04f);
-    r = fmaf(r, z, -1.253729803e-03f);
-    r = fmaf(r, z, -4.177678842e-03f);
-    r = fmaf(r, z, 2.466407418e-01f);
-    r = fmaf(r, z, 1.501409411e+00f);
-    return (-1.41421356237f * r) * fmaf(-2.0f, p, 1.0f);
+    float r = -3.958320960e-08f;
+    r = fmaf(r, z, -4.851791005e-07f);
+    r = fmaf(r, z, 4.981194706e-06f);
+    r = fmaf(r, z, 6.207880233e-06f);
+    r = fmaf(r, z, -3.091151011e-04f);
+    r = fmaf(r, z, 1.773041789e-03f);
+    r = fmaf(r, z, 5.908129737e-03f);
+    r = fmaf(r, z, -3.488026857e-01f);
+    r = fmaf(r, z, -2.123313665e+00f);
+    return r * fmaf(-2.0f, p, 1.0f);
   }
   return ndtri_tail_f32(p >= 1e-30f ? __logf(p) : lp_tiny);
 }

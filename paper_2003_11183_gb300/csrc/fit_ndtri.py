@@ -6,7 +6,8 @@ function", GPU Computing Gems, 2011), Phi^-1(p) = -sqrt(2) x R(w) with
 R(w) = erfinv(x) / x, a smooth function of w.  For w < 5 (p > 0.0017) R is
 fitted here as a degree-8 polynomial in w - 2.5 by least squares on the relative
 error at Chebyshev nodes (maximum about 2.2e-7 when the kernel evaluates it in
-float32 by Horner's rule).  The reference values come from SciPy's float64
+float32 by Horner's rule); the kernel holds the coefficients times -sqrt(2), so
+that Phi^-1(p) = x * poly(w - 2.5).  The reference values come from SciPy's float64
 normal quantile through p = exp(-w) / (2 (1 + x)), which has no cancellation.
 """
 import numpy as np
@@ -46,4 +47,4 @@ def float32_error(coef: np.ndarray, points: int = 200001) -> float:
 if __name__ == "__main__":
     co = fit()
     print("max relative error (float32 Horner):", float32_error(co))
-    print(", ".join(f"{c:.9e}f" for c in co.astype(np.float32)))
+    print(", ".join(f"{c:.9e}f" for c in (-np.sqrt(2.0) * co).astype(np.float32)))

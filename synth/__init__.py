@@ -37,6 +37,18 @@ def jittered_grid(g: int, seed: int, jitter: float = 0.8) -> np.ndarray:
     return xy
 
 
+def expanding_grid(g: int, spacing: float, seed: int, jitter: float = 0.8) -> np.ndarray:
+    """g*g locations on a grid of the given spacing perturbed by U(0, jitter * spacing)
+    per axis (Section 5.1: spacing 1/15, so the domain grows with n).  Returns (g*g, 2)."""
+    rng = np.random.default_rng(seed)
+    ii, jj = np.meshgrid(np.arange(g, dtype=np.float64), np.arange(g, dtype=np.float64), indexing="ij")
+    u = rng.random((g * g, 2))
+    xy = np.empty((g * g, 2), dtype=np.float64)
+    xy[:, 0] = (ii.reshape(-1) + jitter * u[:, 0]) * spacing
+    xy[:, 1] = (jj.reshape(-1) + jitter * u[:, 1]) * spacing
+    return xy
+
+
 def random_points(n: int, seed: int) -> np.ndarray:
     """n iid uniform locations in the unit square (for ragged, non-square n)."""
     rng = np.random.default_rng(seed)

@@ -46,6 +46,16 @@ TRAFFIC = {
                              "paper_2003_11183_gb300/csrc/common.cuh",
                              "include/tlrmvn.h"],
                    "sources": None},
+    "k_sweep_tc2": {"bytes_per_sample_dim": None,
+                    "capture": "profiles/k_sweep_tc2_n16384.md",
+                    "files": ["paper_2003_11183_gb300/csrc/sweep_tc2.cuh",
+                              "paper_2003_11183_gb300/csrc/sweep_tc.cuh",
+                              "paper_2003_11183_gb300/csrc/sweep.cuh",
+                              "paper_2003_11183_gb300/csrc/sov_device.cuh",
+                              "paper_2003_11183_gb300/csrc/tcgen05.cuh",
+                              "paper_2003_11183_gb300/csrc/common.cuh",
+                              "include/tlrmvn.h"],
+                    "sources": None},
 }
 
 
@@ -519,7 +529,8 @@ def run_ours(args):
             ach = work["sweep"] * units / (d["avg_launch_ms"] / 1e3) / 1e12
             d.update(bound="alu", unit="TFLOP/s", achieved=ach, peak=fp32_peak, frac=ach / fp32_peak,
                      peak_source=fp32_src, flops_per_sample_dim=work["sweep"], sample_dims_per_launch=units,
-                     kernel={0: "k_diag<double>", 1: "k_diag_f32", 2: "k_sweep_tc", 3: "k_sweep_tc"}[prec])
+                     kernel={0: "k_diag<double>", 1: "k_diag_f32"}.get(
+                         prec, "k_sweep_tc2" if tl.tlrmvn_get_tuning(F, prec)["tc_kernel"] == 1 else "k_sweep_tc"))
             if prec >= 2:
                 tach = work["tensor"] * units / (d["avg_launch_ms"] / 1e3) / 1e12
                 d["tensor_share"] = {"bound": "tensor", "unit": "TFLOP/s", "achieved": tach, "peak": bf16_peak,

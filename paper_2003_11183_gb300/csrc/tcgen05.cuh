@@ -41,7 +41,7 @@ struct Cfg {
   static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((A_MN ? 1u : 0u) << 15) |
                                     ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
   static constexpr uint32_t IDESC_F16 = IDESC & ~((7u << 7) | (7u << 10));
-  static_assert(BN == 64 || BN == 128 || BN == 256, "N of the MMA");
+  static_assert(BN == 32 || BN == 64 || BN == 128 || BN == 256, "N of the MMA");
   static_assert(KB == 64 || KB == 32, "stage depth");
   static_assert(!A_MN || KB == 64, "the MN-major operand uses 64-deep stages");
   static_assert(HALF % (16 * KB) == 0 && A_BYTES % (16 * KB) == 0, "swizzle atoms (8 rows) must stay aligned");

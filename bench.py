@@ -75,6 +75,8 @@ def parse():
     ap.add_argument("--no-baselines", action="store_true", help="skip FP64-path and CPU-oracle legs")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the library's default launch choices (profiling captures: fewer launches)")
+    ap.add_argument("--tc-kernel", type=int, default=-1,
+                    help="whole-tile sweep of the BF16/FP16-shift paths (0, 1; -1: the tuner's or default choice)")
     ap.add_argument("--sample-chunk", type=int, default=0,
                     help="samples per chunk of the solve (0 = the library's choice: all that fit)")
     ap.add_argument("--count", type=int, default=256, help="problems of the batched workload (--workload 4)")
@@ -445,7 +447,10 @@ def run_ours(args):
     per_shift = torch.zeros(w.n_shifts, dtype=torch.float64, device="cuda")
     # launch choices for this problem: the library's autotuner (untimed setup; cached per box)
     cache = os.path.join(tempfile.gettempdir(), "tlrmvn_tune_cache.txt")
-    if args.no_tune:
+    if args.tc_kernel >= 0:
+        tl.tlrmvn_set_tuning(F, prec, tc_kernel=args.tc_kernel)
+        tuned = dict(tl.tlrmvn_get_tuning(F, prec), note=f"set by hand (--tc-kernel {args.tc_kernel})")
+    elif args.no_tune:
         tuned = dict(tl.tlrmvn_get_tuning(F, prec), note="library defaults (--no-tune)")
     else:
         tuned = tl.tlrmvn_autotune(F, w.a, w.b, w.nu, prec, n_shifts=w.n_shifts, n_points=w.n_points,

@@ -9,7 +9,7 @@
 //             + sum_{u < q0} B_i[q0 + v][u] y_u[c]      (the coupling to the earlier
 //               sub-tiles, split hi/lo operands, hi*hi + hi*lo + lo*hi)
 // While the four warps sweep sub-tile q from its buffer, thread 0 - between its
-// own variables, by non-blocking mbarrier polls - streams the products of
+// own variables, by non-blocking mbarrier tests (test_wait) - streams the products of
 // sub-tile q + 1 that do not depend on sub-tile q into the other buffer: its
 // low-rank shifts and its coupling to sub-tiles 0 .. q-1, one k-block at a time
 // through one shared-memory stage (TMA copy, then the MMAs).  Only the coupling
@@ -174,14 +174,14 @@ __global__ void __launch_bounds__(STC_NS, 6)
   // thread 0: advance the pipe without blocking (one step per call)
   auto poll = [&](St2Pipe& P) {
     if (P.st == 1) {
-      if (tc::mbar_try_wait(full, P.ph & 1)) {
+      if (tc::mbar_test_wait(full, P.ph & 1)) {
         P.ph ^= 1;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         issue_mma(P, P.job);
         P.st = 2;
       }
     } else if (P.st == 2) {
-      if (tc::mbar_try_wait(freeb, (P.ph >> 1) & 1)) {
+      if (tc::mbar_test_wait(freeb, (P.ph >> 1) & 1)) {
         P.ph ^= 2;
         P.st = 0;
         P.job++;

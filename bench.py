@@ -70,6 +70,7 @@ def parse():
     ap.add_argument("--workload", type=int, default=3)
     ap.add_argument("--points", type=int, default=0, help="override points per shift (0 = workload's)")
     ap.add_argument("--shifts", type=int, default=0, help="override the number of shifts (0 = workload's)")
+    ap.add_argument("--tile", type=int, default=0, help="override the workload's tile size (experiments only)")
     ap.add_argument("--n-side", type=int, default=0,
                     help="grid side of a smaller problem of the same family (profiling captures only)")
     ap.add_argument("--no-baselines", action="store_true", help="skip FP64-path and CPU-oracle legs")
@@ -292,6 +293,8 @@ def load_workload(args):
     """The synthetic workload of --workload, with --n-side / --points / --shifts applied."""
     import synth
     w = synth.workload(args.workload, n_side=args.n_side or None)
+    if args.tile:
+        w.m = args.tile
     if args.points:
         w.n_points = args.points
     if args.shifts:

@@ -46,16 +46,6 @@ TRAFFIC = {
                              "paper_2003_11183_gb300/csrc/common.cuh",
                              "include/tlrmvn.h"],
                    "sources": None},
-    "k_sweep_tc2": {"bytes_per_sample_dim": None,
-                    "capture": "profiles/k_sweep_tc2_n16384.md",
-                    "files": ["paper_2003_11183_gb300/csrc/sweep_tc2.cuh",
-                              "paper_2003_11183_gb300/csrc/sweep_tc.cuh",
-                              "paper_2003_11183_gb300/csrc/sweep.cuh",
-                              "paper_2003_11183_gb300/csrc/sov_device.cuh",
-                              "paper_2003_11183_gb300/csrc/tcgen05.cuh",
-                              "paper_2003_11183_gb300/csrc/common.cuh",
-                              "include/tlrmvn.h"],
-                    "sources": None},
 }
 
 
@@ -76,8 +66,6 @@ def parse():
     ap.add_argument("--no-baselines", action="store_true", help="skip FP64-path and CPU-oracle legs")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the library's default launch choices (profiling captures: fewer launches)")
-    ap.add_argument("--tc-kernel", type=int, default=-1,
-                    help="whole-tile sweep of the BF16/FP16-shift paths (0, 1; -1: the tuner's or default choice)")
     ap.add_argument("--sample-chunk", type=int, default=0,
                     help="samples per chunk of the solve (0 = the library's choice: all that fit)")
     ap.add_argument("--count", type=int, default=256, help="problems of the batched workload (--workload 4)")
@@ -450,10 +438,7 @@ def run_ours(args):
     per_shift = torch.zeros(w.n_shifts, dtype=torch.float64, device="cuda")
     # launch choices for this problem: the library's autotuner (untimed setup; cached per box)
     cache = os.path.join(tempfile.gettempdir(), "tlrmvn_tune_cache.txt")
-    if args.tc_kernel >= 0:
-        tl.tlrmvn_set_tuning(F, prec, tc_kernel=args.tc_kernel)
-        tuned = dict(tl.tlrmvn_get_tuning(F, prec), note=f"set by hand (--tc-kernel {args.tc_kernel})")
-    elif args.no_tune:
+    if args.no_tune:
         tuned = dict(tl.tlrmvn_get_tuning(F, prec), note="library defaults (--no-tune)")
     else:
         tuned = tl.tlrmvn_autotune(F, w.a, w.b, w.nu, prec, n_shifts=w.n_shifts, n_points=w.n_points,
@@ -537,8 +522,7 @@ def run_ours(args):
             ach = work["sweep"] * units / (d["avg_launch_ms"] / 1e3) / 1e12
             d.update(bound="alu", unit="TFLOP/s", achieved=ach, peak=fp32_peak, frac=ach / fp32_peak,
                      peak_source=fp32_src, flops_per_sample_dim=work["sweep"], sample_dims_per_launch=units,
-                     kernel={0: "k_diag<double>", 1: "k_diag_f32"}.get(
-                         prec, "k_sweep_tc2" if tl.tlrmvn_get_tuning(F, prec)["tc_kernel"] == 1 else "k_sweep_tc"))
+                     kernel={0: "k_diag<double>", 1: "k_diag_f32"}.get(prec, "k_sweep_tc"))
             if prec >= 2:
                 tach = work["tensor"] * units / (d["avg_launch_ms"] / 1e3) / 1e12
                 d["tensor_share"] = {"bound": "tensor", "unit": "TFLOP/s", "achieved": tach, "peak": bf16_peak,

@@ -181,9 +181,6 @@ int tlrmvn_prob_device(tlrmvn_factor_t f, const double* a, const double* b, doub
  *   chunk     samples in flight per pass; 0 = as many as fit the memory rule
  *             (opts->sample_chunk, when set, still takes precedence)
  *   tc_ctas   whole-tile sweeps of the BF16-/FP16-shift paths sharing an SM (1..6)
- *   tc_kernel the whole-tile sweep of those paths: 0 = tensor-core products between
- *             64-variable sub-tiles, 1 = 32-variable sub-tiles with the next
- *             sub-tile's products overlapped with the current one's sweep
  *   ms        tlrmvn_autotune: device milliseconds per solve of the choice (-1
  *             when it came from the cache); candidates: how many were timed */
 typedef struct {
@@ -192,7 +189,6 @@ typedef struct {
   int tc_ctas;
   double ms;
   int candidates;
-  int tc_kernel;
 } tlrmvn_tuning;
 
 /* Times each candidate launch choice for opts->precision on solves of this very

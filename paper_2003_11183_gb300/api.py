@@ -256,7 +256,7 @@ class Server:
 
 
 def _tuning_dict(t) -> dict:
-    return {"sub": t.sub, "threads": t.threads, "chunk": t.chunk, "tc_ctas": t.tc_ctas, "tc_kernel": t.tc_kernel,
+    return {"sub": t.sub, "threads": t.threads, "chunk": t.chunk, "tc_ctas": t.tc_ctas,
             "ms": t.ms, "candidates": t.candidates}
 
 
@@ -282,9 +282,8 @@ def tlrmvn_get_tuning(f: Factor, precision: int) -> dict:
     return _tuning_dict(t)
 
 
-def tlrmvn_set_tuning(f: Factor, precision: int, sub: int = 64, threads: int = 0, chunk: int = 0, tc_ctas: int = 6,
-                      tc_kernel: int = 0):
-    t = L.Tuning(int(sub), int(threads), int(chunk), int(tc_ctas), -1.0, 0, int(tc_kernel))
+def tlrmvn_set_tuning(f: Factor, precision: int, sub: int = 64, threads: int = 0, chunk: int = 0, tc_ctas: int = 6):
+    t = L.Tuning(int(sub), int(threads), int(chunk), int(tc_ctas), -1.0, 0)
     _check(L.load().tlrmvn_set_tuning(f.handle, int(precision), C.byref(t)), "tlrmvn_set_tuning")
 
 

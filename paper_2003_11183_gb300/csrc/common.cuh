@@ -61,15 +61,11 @@ void dfree(T*& p) {
 //   chunk    samples in flight per pass (0: as many as the memory rule allows)
 //   tc_ctas  whole-tile sweeps (BF16-/FP16-shift paths) sharing an SM: 6 (all that
 //            fit), or fewer by reserving shared memory
-//   tc_kernel the whole-tile sweep: 0 = products between 64-variable sub-tiles
-//            (k_sweep_tc), 1 = 32-variable sub-tiles with the next sub-tile's
-//            products overlapped with the sweep (k_sweep_tc2)
 struct Tuning {
   int sub = 64;
   int threads = 0;
   int64_t chunk = 0;
   int tc_ctas = 6;
-  int tc_kernel = 0;
 };
 
 // ---- factor handle -----------------------------------------------------------

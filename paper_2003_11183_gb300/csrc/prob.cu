@@ -15,7 +15,6 @@
 #include "sov_device.cuh"
 #include "sweep.cuh"
 #include "sweep_tc.cuh"
-#include "sweep_tc2.cuh"
 #include "tcgen05.cuh"
 
 #include <cudaTypedefs.h>
@@ -744,21 +743,17 @@ static SweepShape sweep_shape(int64_t C, int mt, int forced) {
 // one-sided) flags and operand type.
 typedef void (*SweepTcKernel)(const CUtensorMap, const CUtensorMap, const CUtensorMap, const CUtensorMap,
                               const CUtensorMap, const CUtensorMap, SweepTcArgs);
-static SweepTcKernel sweep_tc_kernel(int flags, bool f16, int variant = 0) {
-  static const SweepTcKernel table[16] = {
+static SweepTcKernel sweep_tc_kernel(int flags, bool f16) {
+  static const SweepTcKernel table[8] = {
       k_sweep_tc<0, false>, k_sweep_tc<SWEEP_PERIODIZE, false>, k_sweep_tc<SWEEP_ONE_SIDED, false>,
       k_sweep_tc<SWEEP_PERIODIZE | SWEEP_ONE_SIDED, false>, k_sweep_tc<0, true>, k_sweep_tc<SWEEP_PERIODIZE, true>,
-      k_sweep_tc<SWEEP_ONE_SIDED, true>, k_sweep_tc<SWEEP_PERIODIZE | SWEEP_ONE_SIDED, true>,
-      k_sweep_tc2<0, false>, k_sweep_tc2<SWEEP_PERIODIZE, false>, k_sweep_tc2<SWEEP_ONE_SIDED, false>,
-      k_sweep_tc2<SWEEP_PERIODIZE | SWEEP_ONE_SIDED, false>, k_sweep_tc2<0, true>, k_sweep_tc2<SWEEP_PERIODIZE, true>,
-      k_sweep_tc2<SWEEP_ONE_SIDED, true>, k_sweep_tc2<SWEEP_PERIODIZE | SWEEP_ONE_SIDED, true>};
-  return table[((flags & SWEEP_PERIODIZE) ? 1 : 0) | ((flags & SWEEP_ONE_SIDED) ? 2 : 0) | (f16 ? 4 : 0) |
-               (variant ? 8 : 0)];
+      k_sweep_tc<SWEEP_ONE_SIDED, true>, k_sweep_tc<SWEEP_PERIODIZE | SWEEP_ONE_SIDED, true>};
+  return table[((flags & SWEEP_PERIODIZE) ? 1 : 0) | ((flags & SWEEP_ONE_SIDED) ? 2 : 0) | (f16 ? 4 : 0)];
 }
 // Dynamic shared memory of a whole-tile sweep launch with `ctas` CTAs per SM:
 // the kernel's own need, or more so that no more than `ctas` fit (tuning).
-static size_t sweep_tc_launch_smem(int ctas, int variant = 0) {
-  size_t need = variant ? sweep_tc2_smem_bytes() : sweep_tc_smem_bytes();
+static size_t sweep_tc_launch_smem(int ctas) {
+  size_t need = sweep_tc_smem_bytes();
   if (ctas >= 1 && ctas < 6) {
     int dev = 0, per_sm = 0;
     cudaGetDevice(&dev);
@@ -772,11 +767,11 @@ static size_t sweep_tc_launch_smem(int ctas, int variant = 0) {
 static int set_sweep_smem(int sub) {
   for (int flags = 0; flags < 8; flags++)
     TLR_CHECK(raise_smem_limit((const void*)sweep_kernel(flags), sweep_smem_bytes(sub, 256)));
-  for (int t = 0; t < 16; t++)  // every (periodisation, one-sided, operand type, kernel) variant
+  for (int t = 0; t < 8; t++)  // every (periodisation, one-sided, operand type) variant
     TLR_CHECK(raise_smem_limit((const void*)sweep_tc_kernel(((t & 1) ? SWEEP_PERIODIZE : 0) |
                                                                 ((t & 2) ? SWEEP_ONE_SIDED : 0),
-                                                            (t & 4) != 0, (t & 8) ? 1 : 0),
-                               sweep_tc_launch_smem(1, (t & 8) ? 1 : 0)));
+                                                            (t & 4) != 0),
+                               sweep_tc_launch_smem(1)));
   return TLRMVN_OK;
 }
 
@@ -788,7 +783,6 @@ static int set_sweep_smem(int sub) {
 struct TcOperands {
   CUtensorMap mapB32, mapY32, mapY64;
   CUtensorMap mapW{}, mapU64{}, mapV64{};
-  CUtensorMap mapB32r32, mapU64r32{};  // 32-row boxes of the split B and of U (32-variable sub-tiles)
   unsigned short* W = nullptr;
   int64_t ldw = 0;
   int64_t my;
@@ -845,10 +839,9 @@ static void sweep_tile_tc(const Factor& F, int i, int64_t C, const Lims& L, cons
   t.err = tco.err;
   const int flags = (periodize ? SWEEP_PERIODIZE : 0) | (L.one_sided ? SWEEP_ONE_SIDED : 0);
   pf.begin(TLRMVN_KC_DIAG);
-  const bool v2 = tu.tc_kernel == 1;
-  launch_pdl(sweep_tc_kernel(flags, tco.f16, v2 ? 1 : 0), dim3((unsigned)((Cc + STC_NS - 1) / STC_NS)), dim3(STC_NS),
-             sweep_tc_launch_smem(tu.tc_ctas, v2 ? 1 : 0), st, tco.mapY32, v2 ? tco.mapB32r32 : tco.mapB32, tco.mapW,
-             v2 ? tco.mapU64r32 : tco.mapU64, tco.mapY64, tco.mapV64, t);
+  launch_pdl(sweep_tc_kernel(flags, tco.f16), dim3((unsigned)((Cc + STC_NS - 1) / STC_NS)), dim3(STC_NS),
+             sweep_tc_launch_smem(tu.tc_ctas), st, tco.mapY32, tco.mapB32, tco.mapW, tco.mapU64, tco.mapY64,
+             tco.mapV64, t);
   pf.end();
 }
 
@@ -1041,7 +1034,6 @@ static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opt
   tco.f16 = f16;
   const void* B2 = f16 ? (const void*)F.B16x2h : (const void*)F.B16x2;
   TLR_CHECK(make_map(&tco.mapB32, B2, ly, (uint64_t)F.r * m, ly * 2, 64, 32, f16));
-  TLR_CHECK(make_map(&tco.mapB32r32, B2, ly, (uint64_t)F.r * m, ly * 2, 32, 32, f16));
   TLR_CHECK(make_map(&tco.mapY32, Y, ly, C, ly * 2, STC_NS, 32, f16));
   TLR_CHECK(make_map(&tco.mapY64, Y, ly, C, ly * 2, STC_NS, 64, f16));
   TLR_CHECK(make_map(&tco.mapW, W, ldw, F.kw16, ldw * 2, 64, 64, f16));
@@ -1049,11 +1041,9 @@ static int run_chunks_bf16(Factor& F, const Lims& L, double nu, const tlrmvn_opt
     const void* U = f16 ? (const void*)F.U16h : (const void*)F.U16;
     const void* V = f16 ? (const void*)F.V16h : (const void*)F.V16;
     TLR_CHECK(make_map(&tco.mapU64, U, F.kmax16, (uint64_t)F.r * m, F.kmax16 * 2, 64, 64, f16));
-    TLR_CHECK(make_map(&tco.mapU64r32, U, F.kmax16, (uint64_t)F.r * m, F.kmax16 * 2, 32, 64, f16));
     TLR_CHECK(make_map(&tco.mapV64, V, F.my16, F.ktot, F.my16 * 2, 64, 64, f16));
   } else {
     tco.mapU64 = tco.mapW;  // (never read: no tile has ranks)
-    tco.mapU64r32 = tco.mapW;
     tco.mapV64 = tco.mapW;
   }
   tco.W = W;

@@ -44,15 +44,13 @@ static std::string tune_key(const Factor& F, int precision, int64_t S, bool mvt)
 static std::vector<Tuning> candidates(const Factor& F, int precision, int64_t S) {
   std::vector<Tuning> c;
   if (precision == TLRMVN_BF16_SHIFT || precision == TLRMVN_FP16_SHIFT) {
-    for (int kern : {0})
-      for (int ctas : {6, 4})
-        for (int64_t chunk : {(int64_t)0, (S / 2 + 255) / 256 * 256}) {
-          Tuning t;
-          t.tc_kernel = kern;
-          t.tc_ctas = ctas;
-          t.chunk = chunk;
-          c.push_back(t);
-        }
+    for (int ctas : {6, 4})
+      for (int64_t chunk : {(int64_t)0, (S / 2 + 255) / 256 * 256}) {
+        Tuning t;
+        t.tc_ctas = ctas;
+        t.chunk = chunk;
+        c.push_back(t);
+      }
   } else if (precision == TLRMVN_FP32) {
     for (int sub : {64, 128})
       for (int threads : {0, 64, 128, 256}) {
@@ -74,7 +72,7 @@ static std::vector<Tuning> candidates(const Factor& F, int precision, int64_t S)
     bool dup = false;
     for (const Tuning& u : out)
       dup = dup || (std::min(t.sub, F.m) == std::min(u.sub, F.m) && t.threads == u.threads && t.chunk == u.chunk &&
-                    t.tc_ctas == u.tc_ctas && t.tc_kernel == u.tc_kernel);
+                    t.tc_ctas == u.tc_ctas);
     if (!dup) out.push_back(t);
   }
   return out;
@@ -91,7 +89,7 @@ static bool cache_lookup(const char* path, const std::string& key, Tuning& t) {
     std::istringstream v(line.substr(bar + 3));
     Tuning u;
     long long chunk = 0;
-    if (v >> u.sub >> u.threads >> chunk >> u.tc_ctas >> u.tc_kernel) {
+    if (v >> u.sub >> u.threads >> chunk >> u.tc_ctas) {
       u.chunk = chunk;
       t = u;
       found = true;
@@ -104,8 +102,7 @@ static void cache_store(const char* path, const std::string& key, const Tuning& 
   if (!path || !*path) return;
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%s | %d %d %lld %d %d # %.4f ms\n", key.c_str(), t.sub, t.threads, (long long)t.chunk, t.tc_ctas,
-          t.tc_kernel, ms);
+  fprintf(f, "%s | %d %d %lld %d # %.4f ms\n", key.c_str(), t.sub, t.threads, (long long)t.chunk, t.tc_ctas, ms);
   fclose(f);
 }
 
@@ -195,7 +192,6 @@ extern "C" int tlrmvn_autotune(tlrmvn_factor_t f, const double* a, const double*
     out->threads = best.threads;
     out->chunk = best.chunk;
     out->tc_ctas = best.tc_ctas;
-    out->tc_kernel = best.tc_kernel;
     out->ms = best_ms;
     out->candidates = tried;
   }
@@ -210,7 +206,6 @@ extern "C" int tlrmvn_get_tuning(tlrmvn_factor_t f, int precision, tlrmvn_tuning
   out->threads = t.threads;
   out->chunk = t.chunk;
   out->tc_ctas = t.tc_ctas;
-  out->tc_kernel = t.tc_kernel;
   out->ms = -1.0;
   out->candidates = 0;
   return TLRMVN_OK;
@@ -224,15 +219,13 @@ extern "C" int tlrmvn_set_tuning(tlrmvn_factor_t f, int precision, const tlrmvn_
     return fail(TLRMVN_E_INVAL, "sub must be 64 or 128 (float32) / 32 or 64 (float64)");
   if (t->threads != 0 && (t->threads < 32 || t->threads > 256 || t->threads % 32))
     return fail(TLRMVN_E_INVAL, "threads must be 0 or a multiple of 32 in 32..256");
-  if (t->chunk < 0 || t->tc_ctas < 1 || t->tc_ctas > 6 || t->tc_kernel < 0 || t->tc_kernel > 1)
-    return fail(TLRMVN_E_INVAL, "bad chunk, tc_ctas or tc_kernel");
+  if (t->chunk < 0 || t->tc_ctas < 1 || t->tc_ctas > 6) return fail(TLRMVN_E_INVAL, "bad chunk or tc_ctas");
   Factor& F = *reinterpret_cast<Factor*>(f);
   Tuning u;
   u.sub = t->sub;
   u.threads = t->threads;
   u.chunk = t->chunk;
   u.tc_ctas = t->tc_ctas;
-  u.tc_kernel = t->tc_kernel;
   std::lock_guard<std::mutex> lk(F.tune_mu);
   F.tune[precision] = u;
   return TLRMVN_OK;

@@ -118,6 +118,22 @@ int tlrmvn_factor_kernel(const double* xy, int64_t n, int kernel, const double* 
 int tlrmvn_factor_dense(const double* cov, int64_t n, int64_t ld, const double* a_ref, const double* b_ref,
                         const tlrmvn_factor_opts* opts, tlrmvn_factor_t* out);
 
+/* Post-hoc within-tile reordering of a finished factor for new limits (derived
+ * from the factor structure of Section 3.3; not in the paper).  The block
+ * reorderings also order the variables within each diagonal block by the limits,
+ * which a resident factor meets anew in every request; this returns, without
+ * refactoring, the factor of the same covariance with each tile's variables in
+ * the univariate-conditioning order of the new limits on the tile's conditional
+ * covariance B_j B_j^T: per tile an m x m Cholesky factor of the permuted block
+ * becomes the new B_j, the tile's rows of U are permuted and its column blocks of
+ * V rotated by an orthogonal m x m matrix, so every off-diagonal rank is kept.
+ *   a, b   host, length n, original index order (the request's limits)
+ *   out    receives a new handle (free it with tlrmvn_factor_free); f is unchanged.
+ * Float64 on the GPU; TLRMVN_E_INVAL for invalid limits, TLRMVN_E_NOT_SPD if a
+ * permuted block is not positive definite to float64 precision. */
+int tlrmvn_factor_reorder_tiles(tlrmvn_factor_t f, const double* a, const double* b, void* stream,
+                                tlrmvn_factor_t* out);
+
 /* Shape of a factor: n, number of tiles r, tile size m, total stored rank
  * K = sum of off-diagonal tile ranks, and the number of tiles whose rank cap
  * stopped ACA before the tolerance.  Any output pointer may be NULL. */

@@ -230,3 +230,47 @@ def tlr_factor(Sigma: np.ndarray, geo_perm: np.ndarray, tile_sizes, a, b, tol: f
     sizes = np.array([bl.size for bl in blocks], dtype=np.int64)
     tile_off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
     return TLRFactor(n, int(max(tile_sizes)) if len(tile_sizes) else 0, perm, tile_off, B, U, V, capped)
+
+
+def reorder_within_tiles(F: TLRFactor, a, b) -> TLRFactor:
+    """Post-hoc within-tile reordering of a finished factor for new limits.
+
+    Not in the paper; derived from its factor structure (the survey's NEXT row):
+    the block reorderings of Section 3.3 also reorder variables within each
+    diagonal block, and that within-block order depends on the limits, which a
+    resident factor meets anew in every request.  For each tile j:
+
+    * P_j: the pivot order of univariate conditioning on the tile's conditional
+      covariance given all earlier tiles, B_j B_j^T (the Schur complement of the
+      tile), with the new limits of its variables (not shifted by earlier tiles);
+    * the new diagonal block is Lt_j = chol(P_j B_j B_j^T P_j^T), and
+      Q_j = B_j^-1 P_j^T Lt_j is orthogonal (Q_j Q_j^T = B_j^-1 P_j^T Lt_j Lt_j^T
+      P_j B_j^-T = I);
+    * the factor L' = diag(P) L diag(Q) is lower block triangular with diagonal
+      blocks P_j B_j Q_j = Lt_j and L' L'^T = P L L^T P^T: it is the TLR factor of
+      the reordered variables.  Its off-diagonal tiles keep their ranks: the rows
+      of tile j in row blocks are permuted (U_jk -> P_j U_jk) and its column blocks
+      rotated (V_ij -> Q_j^T V_ij).
+
+    a, b: new limits in original index order.  Returns a new TLRFactor.
+    """
+    a = np.asarray(a, dtype=np.float64)[F.perm]
+    b = np.asarray(b, dtype=np.float64)[F.perm]
+    o = F.tile_off
+    perm = F.perm.copy()
+    B, U, V = list(F.B), dict(F.U), dict(F.V)
+    for j in range(F.r):
+        S = F.B[j] @ F.B[j].T
+        uc = univariate_conditioning(S, a[o[j]:o[j + 1]], b[o[j]:o[j + 1]])
+        p = uc.order
+        Lt = np.linalg.cholesky(S[np.ix_(p, p)])
+        Pt_Lt = np.zeros_like(Lt)
+        Pt_Lt[p, :] = Lt                      # P_j^T Lt_j (P_j picks rows p)
+        Q = solve_triangular(F.B[j], Pt_Lt, lower=True)
+        B[j] = Lt
+        perm[o[j]:o[j + 1]] = F.perm[o[j]:o[j + 1]][p]
+        for k in range(j):                    # rows of tile j in the row blocks to its left
+            U[(j, k)] = F.U[(j, k)][p]
+        for i in range(j + 1, F.r):           # column blocks below tile j
+            V[(i, j)] = Q.T @ F.V[(i, j)]
+    return TLRFactor(F.n, F.m, perm, F.tile_off.copy(), B, U, V, F.capped_tiles)

@@ -36,6 +36,8 @@ SIGNATURES = {
                                         C.POINTER(FactorOpts), C.POINTER(C.c_void_p)]),
     "tlrmvn_factor_dense": (C.c_int, [c_double_p, C.c_int64, C.c_int64, c_double_p, c_double_p, C.POINTER(FactorOpts),
                                        C.POINTER(C.c_void_p)]),
+    "tlrmvn_factor_reorder_tiles": (C.c_int, [C.c_void_p, c_double_p, c_double_p, C.c_void_p,
+                                              C.POINTER(C.c_void_p)]),
     "tlrmvn_factor_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                       C.POINTER(C.c_int64), C.POINTER(C.c_int)]),
     "tlrmvn_factor_ranks": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),

@@ -99,6 +99,17 @@ def tlrmvn_factor_dense(cov, a_ref, b_ref, tile: int, tol: float, max_rank: int 
     return Factor(out.value)
 
 
+def tlrmvn_factor_reorder_tiles(f: Factor, a, b, stream=None) -> Factor:
+    """A new factor of the same covariance with every tile's variables reordered for
+    the limits (a, b) (original order); see tlrmvn_factor_reorder_tiles."""
+    a = _f64(a)
+    b = _f64(b)
+    out = C.c_void_p()
+    _check(L.load().tlrmvn_factor_reorder_tiles(f.handle, _dp(a), _dp(b), _stream_ptr(stream), C.byref(out)),
+           "tlrmvn_factor_reorder_tiles")
+    return Factor(out.value)
+
+
 def tlrmvn_factor_info(f: Factor) -> dict:
     lib = L.load()
     n, k = C.c_int64(), C.c_int64()

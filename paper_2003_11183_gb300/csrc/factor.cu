@@ -938,6 +938,168 @@ static int factor_build(const CovSrc& src, int64_t n, std::vector<int64_t> geo, 
   return factor_finish(F, st);
 }
 
+// ---- post-hoc within-tile reordering of a finished factor for new limits ----------------------
+// (No counterpart in the paper; derived from its factor structure.)  The block
+// reorderings of Section 3.3 also order the variables within each diagonal
+// block by the limits, which a resident factor meets anew in every request.
+// For each tile j: P_j is the pivot order of univariate conditioning on the
+// tile's conditional covariance B_j B_j^T with the new limits; the new diagonal
+// block is Lt_j = chol(P_j B_j B_j^T P_j^T), and Q_j = B_j^-1 P_j^T Lt_j is
+// orthogonal, so L' = diag(P) L diag(Q) has diagonal blocks Lt_j, satisfies
+// L' L'^T = P L L^T P^T, and keeps every off-diagonal rank: the tile's rows in
+// the row blocks are permuted (U_jk -> P_j U_jk) and its column blocks rotated
+// (V_ij -> Q_j^T V_ij, i.e. the stored V^T rows times Q_j).
+
+// Xp_j[v][w] = S_j[p_j(v)][p_j(w)] for v, w < mb_j (one tile per block row)
+__global__ void k_gather_sym(const double* S, const int* order, const int* bsize, int m, double* Xp) {
+  const int j = blockIdx.y, mb = bsize[j];
+  const double* Sj = S + (size_t)j * m * m;
+  const int* p = order + (size_t)j * m;
+  double* X = Xp + (size_t)j * m * m;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)m * m; t += (int64_t)gridDim.x * blockDim.x) {
+    const int v = (int)(t / m), w = (int)(t % m);
+    X[t] = (v < mb && w < mb) ? Sj[(size_t)p[v] * m + p[w]] : 0.0;
+  }
+}
+// X_j[p_j(v)][c] = L_j[v][c] (rows scattered back: X = P^T L)
+__global__ void k_scatter_rows(const double* L, const int* order, const int* bsize, int m, double* X) {
+  const int j = blockIdx.y, mb = bsize[j];
+  const int* p = order + (size_t)j * m;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)m * m; t += (int64_t)gridDim.x * blockDim.x) {
+    const int v = (int)(t / m), c = (int)(t % m);
+    if (v < mb) X[(size_t)j * m * m + (size_t)p[v] * m + c] = L[(size_t)j * m * m + t];
+    else X[(size_t)j * m * m + t] = 0.0;
+  }
+}
+// rows of row block j of Ucat permuted: Unew_j[v][k] = Uold_j[p_j(v)][k]
+__global__ void k_permute_urows(const double* Uold, double* Unew, const int64_t* krow_off, const int* order,
+                                const int* bsize, int m) {
+  const int j = blockIdx.y, mb = bsize[j];
+  const int64_t K = krow_off[j + 1] - krow_off[j], base = (int64_t)m * krow_off[j];
+  const int* p = order + (size_t)j * m;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)m * K; t += (int64_t)gridDim.x * blockDim.x) {
+    const int v = (int)(t / K);
+    const int64_t k = t % K;
+    Unew[base + t] = (v < mb) ? Uold[base + (int64_t)p[v] * K + k] : Uold[base + t];
+  }
+}
+
+static int reorder_tiles(Factor& F, const double* a, const double* b, cudaStream_t st, Factor& G) {
+  const int r = F.r, m = F.m;
+  G.n = F.n;
+  G.r = r;
+  G.m = m;
+  G.capped = F.capped;
+  G.device = F.device;
+  G.tile_off = F.tile_off;
+  G.rank = F.rank;
+  TLR_CHECK(factor_alloc_compact(G, st));
+  Build bd;
+  int *d_bsize, *d_blist, *d_order, *d_status;
+  double *d_a, *d_b, *S, *X, *Binv, *Qm, *work, *d_logp, *d_y;
+  int64_t* d_kro;
+  GemmEntry* d_ent;
+  GemmSeg* d_seg;
+  const size_t mm = (size_t)m * m;
+  TLR_CHECK(bd.get(&d_bsize, r));
+  TLR_CHECK(bd.get(&d_blist, r));
+  TLR_CHECK(bd.get(&d_order, (size_t)r * m));
+  TLR_CHECK(bd.get(&d_status, 1));
+  TLR_CHECK(bd.get(&d_a, (size_t)r * m));
+  TLR_CHECK(bd.get(&d_b, (size_t)r * m));
+  TLR_CHECK(bd.get(&S, r * mm));
+  TLR_CHECK(bd.get(&X, r * mm));
+  TLR_CHECK(bd.get(&Binv, r * mm));
+  TLR_CHECK(bd.get(&Qm, r * mm));
+  TLR_CHECK(bd.get(&work, r * mm));
+  TLR_CHECK(bd.get(&d_logp, r));
+  TLR_CHECK(bd.get(&d_y, (size_t)r * m));
+  TLR_CHECK(bd.get(&d_kro, (size_t)r + 1));
+  TLR_CHECK(bd.get(&d_ent, (size_t)r));
+  TLR_CHECK(bd.get(&d_seg, (size_t)r));
+  std::vector<int> sizes(r), bl(r);
+  std::vector<double> ha((size_t)r * m, 0.0), hb((size_t)r * m, 0.0);
+  for (int j = 0; j < r; j++) {
+    sizes[j] = (int)F.tsize(j);
+    bl[j] = j;
+    for (int v = 0; v < sizes[j]; v++) {
+      const int64_t orig = F.perm[F.tile_off[j] + v];
+      ha[(size_t)j * m + v] = a[orig];
+      hb[(size_t)j * m + v] = b[orig];
+    }
+  }
+  TLR_CHECK(upload(d_bsize, sizes, st));
+  TLR_CHECK(upload(d_blist, bl, st));
+  TLR_CHECK(upload(d_a, ha, st));
+  TLR_CHECK(upload(d_b, hb, st));
+  TLR_CHECK(upload(d_kro, F.krow_off, st));
+  TLR_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), st));
+  std::vector<GemmEntry> ent;
+  std::vector<GemmSeg> seg;
+  // S_j = B_j B_j^T, the tile's conditional covariance given all earlier tiles
+  for (int j = 0; j < r; j++) {
+    seg.push_back(GemmSeg{F.B + j * mm, F.B + j * mm, m, m, sizes[j]});
+    ent.push_back(GemmEntry{S + j * mm, m, sizes[j], sizes[j], j, j + 1, 1.0, 0.0});
+  }
+  TLR_CUDA(cudaMemsetAsync(S, 0, r * mm * 8, st));
+  TLR_CHECK((run_batched<false, true>(ent, seg, d_ent, d_seg, (size_t)r, (size_t)r, st)));
+  // P_j: the univariate-conditioning pivot order with the new limits
+  const size_t uc_smem = (size_t)m * (5 * sizeof(double) + sizeof(int));
+  TLR_CHECK(raise_smem_limit((const void*)k_uc, uc_smem));
+  TLR_CHECK(raise_smem_limit((const void*)k_potrf, m * sizeof(double)));
+  k_uc<<<r, m >= 256 ? 512 : 256, uc_smem, st>>>(d_blist, S, d_bsize, m, d_a, d_b, work, d_logp, 1, d_order, d_y,
+                                                  d_status);
+  TLR_CUDA(cudaGetLastError());
+  TLR_CHECK(check_status(d_status, st, "within-tile reordering"));
+  // Lt_j = chol(P S_j P^T) (in work); X_j = P^T Lt_j; Binv_j = B_j^-1; Q_j = Binv_j X_j
+  const unsigned gx = (unsigned)std::max<size_t>(1, std::min<size_t>(64, (mm + 255) / 256));
+  k_gather_sym<<<dim3(gx, r), 256, 0, st>>>(S, d_order, d_bsize, m, work);
+  for (int j = 0; j < r; j++) {
+    k_potrf<<<1, 512, m * sizeof(double), st>>>(work + j * mm, sizes[j], m, d_status);
+    k_trinv<<<1, 512, 0, st>>>(F.B + j * mm, Binv + j * mm, sizes[j], m);
+  }
+  TLR_CUDA(cudaGetLastError());
+  TLR_CHECK(check_status(d_status, st, "within-tile reordering (Cholesky)"));
+  k_scatter_rows<<<dim3(gx, r), 256, 0, st>>>(work, d_order, d_bsize, m, X);
+  ent.clear();
+  seg.clear();
+  for (int j = 0; j < r; j++) {
+    seg.push_back(GemmSeg{Binv + j * mm, X + j * mm, m, m, sizes[j]});
+    ent.push_back(GemmEntry{Qm + j * mm, m, sizes[j], sizes[j], j, j + 1, 1.0, 0.0});
+  }
+  TLR_CUDA(cudaMemsetAsync(Qm, 0, r * mm * 8, st));
+  TLR_CHECK((run_batched<false, false>(ent, seg, d_ent, d_seg, (size_t)r, (size_t)r, st)));
+  // the new factor: B_j = Lt_j; V^T rows of column block j times Q_j; rows of U permuted
+  TLR_CUDA(cudaMemcpyAsync(G.B, work, r * mm * 8, cudaMemcpyDeviceToDevice, st));
+  if (F.ktot > 0) {
+    TLR_CUDA(cudaMemsetAsync(G.Vcat, 0, (size_t)m * F.ktot * 8, st));
+    ent.clear();
+    seg.clear();
+    for (int j = 0; j < r; j++) {
+      const int64_t kc = F.kcol(j);
+      if (!kc) continue;
+      seg.push_back(GemmSeg{F.Vcat + (size_t)m * F.kcol_off[j], Qm + j * mm, m, m, sizes[j]});
+      ent.push_back(GemmEntry{G.Vcat + (size_t)m * F.kcol_off[j], m, (int)kc, sizes[j], (int)seg.size() - 1,
+                              (int)seg.size(), 1.0, 0.0});
+    }
+    TLR_CHECK((run_batched<false, false>(ent, seg, d_ent, d_seg, (size_t)r, (size_t)r, st)));
+    int64_t kmax = 0;
+    for (int j = 0; j < r; j++) kmax = std::max(kmax, F.krow(j));
+    const unsigned gu = (unsigned)std::max<int64_t>(1, std::min<int64_t>(256, ((int64_t)m * kmax + 255) / 256));
+    k_permute_urows<<<dim3(gu, r), 256, 0, st>>>(F.Ucat, G.Ucat, d_kro, d_order, d_bsize, m);
+    TLR_CUDA(cudaMemcpyAsync(G.vmap, F.vmap, (size_t)F.ktot * 4, cudaMemcpyDeviceToDevice, st));
+  }
+  TLR_CUDA(cudaGetLastError());
+  std::vector<int> order((size_t)r * m);
+  TLR_CUDA(cudaMemcpyAsync(order.data(), d_order, order.size() * 4, cudaMemcpyDeviceToHost, st));
+  TLR_CUDA(cudaStreamSynchronize(st));
+  G.perm.resize(F.n);
+  for (int j = 0; j < r; j++)
+    for (int v = 0; v < sizes[j]; v++)
+      G.perm[F.tile_off[j] + v] = F.perm[F.tile_off[j] + order[(size_t)j * m + v]];
+  return factor_finish(G, st);
+}
+
 static int check_fopts(const tlrmvn_factor_opts* o, int64_t n, const double* a, const double* b) {
   if (!o) return fail(TLRMVN_E_INVAL, "null options");
   if (n <= 0) return fail(TLRMVN_E_INVAL, "n must be positive");
@@ -1019,5 +1181,27 @@ extern "C" int tlrmvn_factor_dense(const double* cov, int64_t n, int64_t ld, con
     return s;
   }
   *out = reinterpret_cast<tlrmvn_factor_t>(F);
+  return TLRMVN_OK;
+}
+
+extern "C" int tlrmvn_factor_reorder_tiles(tlrmvn_factor_t f, const double* a, const double* b, void* stream,
+                                           tlrmvn_factor_t* out) {
+  if (!f || !a || !b || !out) return fail(TLRMVN_E_INVAL, "null argument");
+  Factor& F = *reinterpret_cast<Factor*>(f);
+  for (int64_t i = 0; i < F.n; i++)
+    if (std::isnan(a[i]) || std::isnan(b[i]) || a[i] > b[i] || a[i] == INFINITY || b[i] == -INFINITY)
+      return fail(TLRMVN_E_INVAL, "limits must satisfy a_i <= b_i, a_i < +inf, b_i > -inf, no NaN");
+  int cur = 0;
+  cudaGetDevice(&cur);
+  TLR_CUDA(cudaSetDevice(F.device));
+  cudaStream_t st = pick_stream(stream);
+  Factor* G = new Factor();
+  const int s = reorder_tiles(F, a, b, st, *G);
+  cudaSetDevice(cur);
+  if (s != TLRMVN_OK) {
+    delete G;
+    return s;
+  }
+  *out = reinterpret_cast<tlrmvn_factor_t>(G);
   return TLRMVN_OK;
 }

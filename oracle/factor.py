@@ -13,19 +13,23 @@ Section 3.3 of the paper:
   L_ij y_j, and subtract L_i1j L_j1j^T from the remaining Schur complement.
 * p_l and y_j come from univariate conditioning (Trinh & Genz, 2015), an
   O(m^3) pivoted Cholesky that at every step takes the remaining variable with
-  the smallest conditional interval probability.  The paper reorders "between
-  and within" the diagonal blocks (abstract): the within-block order is the
-  pivot order of that univariate conditioning.
+  the smallest conditional interval probability.  The paper's reordering acts
+  both across and inside the diagonal blocks (abstract): the within-block
+  order is the pivot order of that univariate conditioning.
 * Off-diagonal tiles are stored as U V^T, truncated by adaptive cross
   approximation (ACA) at an absolute tolerance (Section 3.3).  Here ACA uses
   full pivoting on the dense tile and stops when the largest residual entry
   is at most tol (or at the rank cap), and each rank-one term is balanced
   (|u| = |v|).
+* Two arithmetics: tlr_factor keeps the Schur complement exact and truncates
+  each finished factor tile once; tlr_factor_truncated is the printed form of
+  Section 3.3, with the covariance compressed first and every product and
+  subtraction truncated.
 
 Readings where the paper is silent (restated in the design notes):
-* the Schur complement is kept dense and exact; only the finished factor
-  tiles L_ij are truncated (the paper truncates the Schur tiles too, which
-  differs by O(tol));
+* tlr_factor: the Schur complement is kept dense and exact; only the finished
+  factor tiles L_ij are truncated (the paper truncates the Schur tiles too,
+  which differs by O(tol); tlr_factor_truncated does that);
 * Algorithm 5 overwrites the limits; those conditioned limits steer the
   ordering only, and the integration uses the original limits, permuted;
 * ties in argmin/argmax go to the first candidate (lowest position / first
@@ -229,6 +233,144 @@ def tlr_factor(Sigma: np.ndarray, geo_perm: np.ndarray, tile_sizes, a, b, tol: f
     perm = np.concatenate(blocks)
     sizes = np.array([bl.size for bl in blocks], dtype=np.int64)
     tile_off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    return TLRFactor(n, int(max(tile_sizes)) if len(tile_sizes) else 0, perm, tile_off, B, U, V, capped)
+
+
+class _TileStore:
+    """Low-rank tiles of a symmetric TLR matrix keyed by the unordered pair of
+    clusters {p, q}: Sigma_pq ~ U V^T with U on p's variables, Sigma_qp = V U^T."""
+
+    def __init__(self):
+        self.t = {}
+
+    def get(self, p: int, q: int):
+        if (p, q) in self.t:
+            return self.t[(p, q)]
+        U, V = self.t[(q, p)]
+        return V, U
+
+    def set(self, p: int, q: int, U, V):
+        self.t.pop((q, p), None)
+        self.t[(p, q)] = (U, V)
+
+    def permute(self, c: int, order):
+        """Reorder cluster c's variables in every tile that involves it."""
+        for key in list(self.t):
+            U, V = self.t[key]
+            if key[0] == c:
+                self.t[key] = (U[order], V)
+            elif key[1] == c:
+                self.t[key] = (U, V[order])
+
+
+def tlr_factor_truncated(Sigma: np.ndarray, geo_perm: np.ndarray, tile_sizes, a, b, tol: float, max_rank: int,
+                         reorder: int = REORDER_RBODR) -> TLRFactor:
+    """Block-reordered TLR Cholesky factor in tile-low-rank arithmetic, Section 3.3 as printed.
+
+    Differs from tlr_factor only in where truncation happens.  Before the
+    factorisation the covariance is built as a TLR matrix: dense diagonal
+    blocks, every off-diagonal block Sigma_pq compressed by ACA at tol.  The
+    loop over positions j is Algorithm 5's (without lines 4-9 for the other
+    reorderings):
+
+    * (Algorithm 5) univariate conditioning of every remaining diagonal block
+      on its current Schur complement and conditioned limits; the smallest
+      estimate takes position j and its pivot order becomes the block's
+      within-block order (which reorders that cluster's rows in every tile);
+    * Sigma_jj = Cholesky(Sigma_jj);
+    * Sigma_ij = Sigma_ij (.) Sigma_jj^-T for i > j: with Sigma_ij = U V^T this
+      is U (L_jj^-1 V)^T, then truncated by ACA at tol;
+    * (Algorithm 5) a_i, b_i -= Sigma_ij (.) y_j;
+    * Sigma_i1j1 = Sigma_i1j1 (-) Sigma_i1j (.) Sigma_j1j^T for j < j1 < i1: the
+      low-rank difference U V^T - U_i1j (V_i1j^T V_j1j) U_j1j^T truncated by
+      ACA at tol; the diagonal blocks (i1 = j1) are dense and updated exactly.
+
+    Readings where the paper is silent (restated in the design notes):
+    * truncation = the full-pivoting ACA of aca() on the tile written out
+      densely, the same rule as the covariance construction;
+    * a product with a rank-0 factor is zero: the tile it would update is left
+      as it is (not re-truncated);
+    * capped_tiles counts every truncation the rank cap stopped (construction,
+      (.) and (-) alike).
+    """
+    Sigma = np.asarray(Sigma, dtype=np.float64)
+    n = Sigma.shape[0]
+    offs = np.concatenate([[0], np.cumsum(tile_sizes)])
+    idx = [np.asarray(geo_perm[offs[t]:offs[t + 1]], dtype=np.int64) for t in range(len(tile_sizes))]
+    r = len(idx)
+    acur = np.array(a, dtype=np.float64, copy=True)
+    bcur = np.array(b, dtype=np.float64, copy=True)
+    pos = list(range(r))                   # pos[j] = cluster at position j
+    capped = 0
+
+    if reorder == REORDER_BODR:            # Algorithm 4 on the covariance itself
+        res = [univariate_conditioning(Sigma[np.ix_(bl, bl)], acur[bl], bcur[bl]) for bl in idx]
+        p = np.array([rs.log_p for rs in res])
+        for j in range(r):
+            jt = j + int(np.argmin(p[pos[j:]]))
+            pos[j], pos[jt] = pos[jt], pos[j]
+        idx = [idx[c][res[c].order] for c in range(r)]
+
+    # the TLR covariance: dense diagonal blocks, ACA-compressed off-diagonal blocks
+    D = [Sigma[np.ix_(bl, bl)].copy() for bl in idx]
+    T = _TileStore()
+    for p_ in range(r):
+        for q_ in range(p_ + 1, r):
+            U, V, cp = aca(Sigma[np.ix_(idx[p_], idx[q_])], tol, max_rank)
+            capped += int(cp)
+            T.set(p_, q_, U, V)
+
+    B = []
+    for j in range(r):
+        yj = None
+        if reorder == REORDER_RBODR:       # Algorithm 5, lines 4-8
+            res = [univariate_conditioning(D[pos[l]], acur[idx[pos[l]]], bcur[idx[pos[l]]]) for l in range(j, r)]
+            jt = j + int(np.argmin([rs.log_p for rs in res]))
+            chosen = res[jt - j]
+            pos[j], pos[jt] = pos[jt], pos[j]
+            c = pos[j]
+            o = chosen.order
+            idx[c] = idx[c][o]
+            D[c] = D[c][np.ix_(o, o)]
+            T.permute(c, o)
+            yj = chosen.y
+        cj = pos[j]
+        Ljj = np.linalg.cholesky(D[cj])                      # line 10
+        B.append(Ljj)
+        for i in range(j + 1, r):                            # lines 11-14
+            ci = pos[i]
+            U, V = T.get(ci, cj)
+            if U.shape[1]:
+                U, V, cp = aca(U @ solve_triangular(Ljj, V, lower=True).T, tol, max_rank)
+                capped += int(cp)
+            T.set(ci, cj, U, V)
+            if yj is not None and U.shape[1]:
+                shift = U @ (V.T @ yj)
+                acur[idx[ci]] -= shift
+                bcur[idx[ci]] -= shift
+        for j1 in range(j + 1, r):                           # lines 15-19
+            U1, V1 = T.get(pos[j1], cj)
+            if not U1.shape[1]:
+                continue
+            for i1 in range(j1, r):
+                U2, V2 = T.get(pos[i1], cj)
+                if not U2.shape[1]:
+                    continue
+                prod = U2 @ (V2.T @ V1) @ U1.T               # Sigma_i1j Sigma_j1j^T
+                if i1 == j1:
+                    D[pos[i1]] -= prod
+                else:
+                    Us, Vs = T.get(pos[i1], pos[j1])
+                    U, V, cp = aca(Us @ Vs.T - prod, tol, max_rank)
+                    capped += int(cp)
+                    T.set(pos[i1], pos[j1], U, V)
+    perm = np.concatenate([idx[c] for c in pos])
+    sizes = np.array([idx[c].size for c in pos], dtype=np.int64)
+    tile_off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    U, V = {}, {}
+    for i in range(r):
+        for j in range(i):
+            U[(i, j)], V[(i, j)] = T.get(pos[i], pos[j])
     return TLRFactor(n, int(max(tile_sizes)) if len(tile_sizes) else 0, perm, tile_off, B, U, V, capped)
 
 

@@ -183,3 +183,89 @@ def test_within_tile_reordering_keeps_the_covariance_and_lowers_the_error():
         r1 = sov.solve(F1, a2, b2, math.inf, sh, 500)
         assert abs(r0["logp"] - r1["logp"]) <= 3 * math.hypot(r0["err"], r1["err"])
         assert r1["err"] < r0["err"]
+
+
+# ---- the TLR-arithmetic factor (covariance compressed first, truncated products) ----
+
+def _factor_truncated(n_side, m, seed, reorder, tol, ragged=None, max_rank=None, nugget=None):
+    w = synth.small_workload(n_side, m, seed, ragged_n=ragged, tol=tol)
+    perm0, sizes = geometry.kd_order(w.xy, w.m)
+    Sig = geometry.covariance(w.xy, w.kernel, w.params, w.nugget if nugget is None else nugget)
+    cap = w.m if max_rank is None else max_rank
+    F = factor.tlr_factor_truncated(Sig, perm0, sizes, w.a, w.b, tol, cap, reorder)
+    return w, Sig, perm0, sizes, F
+
+
+@pytest.mark.parametrize("reorder", [0, 1, 2])
+def test_truncated_factor_is_the_cholesky_factor_at_tight_tolerance(reorder):
+    # with nothing truncated away, the TLR arithmetic is exact: the factor is
+    # NumPy's Cholesky factor of the permuted covariance, and the order is the
+    # one of the exact-Schur factorisation (same decisions on the same blocks)
+    w, Sig, perm0, sizes, F = _factor_truncated(12, 24, 41, reorder, 1e-13, ragged=130)
+    P = F.perm
+    assert sorted(P.tolist()) == list(range(w.n))
+    Ld = np.linalg.cholesky(Sig[np.ix_(P, P)])
+    assert np.abs(F.dense() - Ld).max() < 1e-9
+    E = factor.tlr_factor(Sig, perm0, sizes, w.a, w.b, 1e-13, w.m, reorder)
+    assert np.array_equal(P, E.perm)
+
+
+@pytest.mark.parametrize("reorder", [0, 2])
+def test_truncated_factor_error_follows_the_tolerance(reorder):
+    # every truncation leaves at most tol per entry; the reconstruction error
+    # of L L^T grows with tol (a few tol per tile along the update chain) and
+    # vanishes at tight tol; ranks never exceed the cap
+    errs = []
+    for tol in (1e-3, 1e-5, 1e-9):
+        w, Sig, _, _, F = _factor_truncated(16, 32, 42, reorder, tol)
+        L = F.dense()
+        e = np.abs(L @ L.T - Sig[np.ix_(F.perm, F.perm)]).max()
+        assert e <= 4 * F.r * tol, (tol, e)
+        assert all(F.rank(i, j) <= w.m for (i, j) in F.U)
+        errs.append(e)
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[0] > 1e-5
+
+
+def test_truncated_factor_close_to_exact_schur_factor():
+    # without reordering both arithmetics factor the same matrix in the same
+    # order: their factors differ by the truncation of the Schur tiles only
+    for tol in (1e-4, 1e-7):
+        w, Sig, perm0, sizes, F = _factor_truncated(16, 32, 43, 0, tol)
+        E = factor.tlr_factor(Sig, perm0, sizes, w.a, w.b, tol, w.m, 0)
+        assert np.array_equal(F.perm, E.perm)
+        d = np.abs(F.dense() - E.dense()).max()
+        assert d <= 4 * F.r * tol, (tol, d)
+
+
+def test_truncated_factor_rank_cap_counts_capped_truncations():
+    w, Sig, _, _, F = _factor_truncated(12, 36, 44, 2, 1e-10, max_rank=2)
+    assert F.capped_tiles > 0
+    assert all(F.rank(i, j) <= 2 for (i, j) in F.U)
+
+
+def test_truncated_rbodr_with_unit_tiles_is_univariate_conditioning():
+    xy = synth.jittered_grid(5, 31)
+    Sig = geometry.covariance(xy, 0, (0.3,), 1e-8)
+    a, b = synth.limits_uniform(25, 32)
+    b = b - 0.5
+    F = factor.tlr_factor_truncated(Sig, np.arange(25), [1] * 25, a, b, 1e-13, 1, 2)
+    uc = factor.univariate_conditioning(Sig, a, b)
+    assert np.array_equal(F.perm, uc.order)
+    assert np.allclose([Bt[0, 0] for Bt in F.B], np.diag(uc.L), rtol=1e-10)
+
+
+def test_truncated_reordering_on_independent_variables_is_the_exact_sort():
+    n, m = 48, 8
+    rng = np.random.default_rng(3)
+    sd = rng.uniform(0.5, 2.0, n)
+    a = np.full(n, -np.inf)
+    b = rng.uniform(-1, 1.5, n)
+    q = stats.norm.logcdf(b / sd)
+    want_blocks = np.argsort(q.reshape(-1, m).sum(1), kind="stable")
+    for reorder in (1, 2):
+        F = factor.tlr_factor_truncated(np.diag(sd**2), np.arange(n), [m] * (n // m), a, b, 1e-10, m, reorder)
+        assert [int(F.perm[t * m] // m) for t in range(n // m)] == want_blocks.tolist()
+        for t in range(n // m):
+            assert np.all(np.diff(q[F.perm[t * m:(t + 1) * m]]) >= 0)
+        assert all(F.rank(i, j) == 0 for (i, j) in F.U)

@@ -63,6 +63,10 @@ def parse():
     ap.add_argument("--tile", type=int, default=0, help="override the workload's tile size (experiments only)")
     ap.add_argument("--n-side", type=int, default=0,
                     help="grid side of a smaller problem of the same family (profiling captures only)")
+    ap.add_argument("--reorder", type=int, default=-1, choices=[-1, 0, 1, 2],
+                    help="override the workload's preconditioner (-1 = workload's; 0 none, 1 Algorithm 4, 2 Algorithm 5)")
+    ap.add_argument("--schur", default="exact", choices=["exact", "tlr"],
+                    help="factor arithmetic: exact Schur complement or TLR arithmetic with truncated updates")
     ap.add_argument("--no-baselines", action="store_true", help="skip FP64-path and CPU-oracle legs")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the library's default launch choices (profiling captures: fewer launches)")
@@ -227,7 +231,8 @@ def host_cores() -> int:
 
 def build_factor(tl, w):
     t0 = time.perf_counter()
-    F = tl.tlrmvn_factor_kernel(w.xy, w.kernel, w.params, w.nugget, w.a, w.b, w.m, w.tol, w.max_rank, w.reorder)
+    F = tl.tlrmvn_factor_kernel(w.xy, w.kernel, w.params, w.nugget, w.a, w.b, w.m, w.tol, w.max_rank, w.reorder,
+                                schur=getattr(w, "schur", 0))
     return F, time.perf_counter() - t0
 
 
@@ -288,6 +293,9 @@ def load_workload(args):
     if args.shifts:
         w.n_shifts = args.shifts
         w.shifts = w.shifts[:args.shifts]
+    if args.reorder >= 0:
+        w.reorder = args.reorder
+    w.schur = 1 if args.schur == "tlr" else 0
     return w
 
 
@@ -295,7 +303,8 @@ def bench_config(tl, F, w, precision):
     """The workload a line is quoted on (shared by both arms)."""
     info = tl.tlrmvn_factor_info(F)
     return {"workload": w.name, "n": w.n, "tile": w.m, "tol": w.tol, "max_rank": w.max_rank, "nu": w.nu,
-            "shifts": w.n_shifts, "points": w.n_points, "reorder": w.reorder, "precision": precision,
+            "shifts": w.n_shifts, "points": w.n_points, "reorder": w.reorder,
+            "schur": "tlr" if getattr(w, "schur", 0) else "exact", "precision": precision,
             "k_total": info["k_total"], "tiles": info["r"], "ranks": rank_summary(tl, F),
             "l2": "inputs larger than L2 (factor and W buffer)"}
 
@@ -630,36 +639,54 @@ def run_batched(args):
                                        tl.REORDER_ITERATIVE) for p in probs]
     factor_s = time.perf_counter() - t0
     M, N = 10, args.points or 2000
-    plan = tl.BatchPlan(factors, math.inf, M, N, seed=4242)
     a = [p["a"] for p in probs]
     b = [p["b"] for p in probs]
-    tuned = plan.tune(a, b, cache_path=os.path.join(tempfile.gettempdir(), "tlrmvn_tune_cache.txt"))
-    for _ in range(args.warmup):
-        plan.run(a, b)
-    clocks = Clocks(0)
-    clocks.start()
-    times = []
-    for _ in range(args.steps):
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        lp, err = plan.run(a, b)
-        times.append(time.perf_counter() - t1)
-    clk = clocks.stop()
     sd = sum(len(p["a"]) for p in probs) * M * N
+    cache = os.path.join(tempfile.gettempdir(), "tlrmvn_tune_cache.txt")
+    # the line's precision (BF16-shift: the tensor-core persistent kernel; FP32: the SIMT
+    # one), and the other one timed beside it on the same problems and shifts
+    main = tl.BF16_SHIFT if args.precision in ("bf16", "fp16") else tl.FP32
+    other = tl.FP32 if main == tl.BF16_SHIFT else tl.BF16_SHIFT
+    name = {tl.BF16_SHIFT: "f32+bf16", tl.FP32: "f32"}
+
+    def timed(prec, steps, clocks=None):
+        plan = tl.BatchPlan(factors, math.inf, M, N, seed=4242, precision=prec)
+        tuned = plan.tune(a, b, cache_path=cache)
+        for _ in range(args.warmup):
+            plan.run(a, b)
+        if clocks:
+            clocks.start()
+        times = []
+        for _ in range(steps):
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            lp, err = plan.run(a, b)
+            times.append(time.perf_counter() - t1)
+        clk = clocks.stop() if clocks else None
+        plan.close()
+        return times, tuned, lp, err, clk
+
+    times, tuned, lp, err, clk = timed(main, args.steps, Clocks(0))
     ms = statistics.mean(times) * 1e3
+    t_o, tuned_o, lp_o, err_o, _ = timed(other, max(1, args.steps))
+    ms_o = statistics.mean(t_o) * 1e3
     line = {"metric": "batched QMC sample-dims/sec", "value": sd / (ms / 1e3), "unit": "sample-dims/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "p50_ms": statistics.median(times) * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": name[main],
+            "data": "synthetic",
             "config": {"workload": f"batched_{len(probs)}_mvn_n256_4096_m128", "problems": len(probs),
                        "sum_n": sum(len(p["a"]) for p in probs), "shifts": M, "points": N, "tol": 1e-5,
-                       "tuning": tuned},
+                       "precision": name[main], "tuning": tuned,
+                       "timing": "host clock around each plan replay (limits upload, one graph, results read back)"},
             "clocks": clk, "factor_seconds": factor_s,
             "e2e": {"value": sd / (ms / 1e3), "unit": "sample-dims/s",
                     "h2d_bytes_per_step": 2 * 8 * sum(len(p["a"]) for p in probs),
                     "d2h_bytes_per_step": 16 * len(probs)},
-            "logp_mean": float(np.mean(lp)), "err_median": float(np.median(err))}
+            "logp_mean": float(np.mean(lp)), "err_median": float(np.median(err)),
+            "other_precision": {"dtype": name[other], "value": sd / (ms_o / 1e3), "unit": "sample-dims/s",
+                                "ms_per_step": ms_o, "tuning": tuned_o,
+                                "max_logp_gap_in_se": float(np.max(np.abs(lp - lp_o) / np.hypot(err, err_o)))}}
     print(json.dumps(line), flush=True)
-    plan.close()
     return 0
 
 
@@ -709,11 +736,12 @@ def run_study(args):
     for beta, tol in ((0.3, 1e-4), (0.1, 1e-3)):
         xy = synth.jittered_grid(g, 8000)
         a, b = synth.limits_normal(n, 8001, 5.5, 1.25)
-        for reorder, name in ((tl.REORDER_NONE, "tlrmvn (geometric order)"),
-                              (tl.REORDER_BLOCK, "rtlrmvn (Algorithm 4)"),
-                              (tl.REORDER_ITERATIVE, "rrtlrmvn (Algorithm 5)")):
+        for reorder, schur, name in ((tl.REORDER_NONE, 0, "tlrmvn (geometric order)"),
+                                     (tl.REORDER_BLOCK, 0, "rtlrmvn (Algorithm 4)"),
+                                     (tl.REORDER_ITERATIVE, 0, "rrtlrmvn (Algorithm 5)"),
+                                     (tl.REORDER_ITERATIVE, 1, "rrtlrmvn (Algorithm 5, TLR arithmetic)")):
             t0 = time.perf_counter()
-            F = tl.tlrmvn_factor_kernel(xy, tl.KERNEL_EXP, (beta,), 1e-8, a, b, m, tol, 0, reorder)
+            F = tl.tlrmvn_factor_kernel(xy, tl.KERNEL_EXP, (beta,), 1e-8, a, b, m, tol, 0, reorder, schur=schur)
             fs = time.perf_counter() - t0
             info = tl.tlrmvn_factor_info(F)
             for pts in (1000, 10000):
@@ -722,7 +750,8 @@ def run_study(args):
                 t0 = time.perf_counter()
                 lp, err, _, _ = tl.tlrmvn_prob(F, a, b, math.inf, prec, 20, pts, shifts=shifts)
                 t = time.perf_counter() - t0
-                rows.append({"beta": beta, "tol": tol, "method": name, "reorder": reorder, "points": pts,
+                rows.append({"beta": beta, "tol": tol, "method": name, "reorder": reorder,
+                             "schur": "tlr" if schur else "exact", "points": pts,
                              "shifts": 20, "logp": lp, "rel_err": err, "seconds": t, "factor_seconds": fs,
                              "k_total": info["k_total"]})
     # agreement of the three orderings (the same probability): largest pairwise gap in

@@ -66,6 +66,14 @@ extern "C" {
 #define TLRMVN_REORDER_BLOCK      1  /* Algorithm 4, block reordering ("rtlrmvn") */
 #define TLRMVN_REORDER_ITERATIVE  2  /* Algorithm 5, iterative block reordering ("rrtlrmvn") */
 
+/* Arithmetic of the factorisation's Schur complement (tlrmvn_factor_opts.schur), Section 3.3. */
+#define TLRMVN_SCHUR_EXACT 0  /* left-looking: every off-diagonal factor tile L_ij is formed from the
+                                 exact Schur complement and truncated once by ACA                      */
+#define TLRMVN_SCHUR_TLR   1  /* tile-low-rank arithmetic as Algorithm 5 prints it: the covariance is
+                                 compressed by ACA first; each product with Sigma_jj^-T and each
+                                 Schur subtraction of the right-looking update is truncated by ACA at
+                                 tol; diagonal blocks stay dense and exact                            */
+
 /* Covariance kernels of tlrmvn_factor_kernel (Section 3.2; unit variance each). */
 #define TLRMVN_KERNEL_EXP          0  /* exp(-d/beta);                          params = {beta}      */
 #define TLRMVN_KERNEL_MATERN15     1  /* (1 + sqrt3 d/ell) exp(-sqrt3 d/ell);   params = {ell}       */
@@ -82,6 +90,8 @@ typedef struct {
   int    strict_rank; /* 0: a tile whose truncation the rank cap stopped keeps the capped rank
                          (counted in tlrmvn_factor_info's `capped`); nonzero: the factorisation
                          fails with TLRMVN_E_RANK instead                                        */
+  int    schur;     /* TLRMVN_SCHUR_*; with TLRMVN_SCHUR_TLR, `capped` counts every truncation
+                       (construction, product, subtraction) that the rank cap stopped           */
 } tlrmvn_factor_opts;
 
 typedef struct {
@@ -233,9 +243,15 @@ int tlrmvn_set_tuning(tlrmvn_factor_t f, int precision, const tlrmvn_tuning* t);
  * integrand, estimator) is captured once in a CUDA graph; tlrmvn_batch_run
  * replays it for new limits.  Needed by likelihood fitting, where the same
  * covariances meet new limits at every step (Section 5 of the paper).
- *   opts: precision must be TLRMVN_FP32; opts->shifts must be NULL: problem p
- *         draws its shifts from seed opts->seed + p exactly as tlrmvn_prob does
- *         with that seed; n_shifts / n_points / periodize apply to all problems.
+ *   opts: precision TLRMVN_FP32 (float sweep, float SIMT shifts and
+ *         projections) or TLRMVN_BF16_SHIFT (every tile through the same
+ *         whole-tile tcgen05 sweep as tlrmvn_prob's BF16-shift path, with the
+ *         chunk's projections and y in block-private bf16 buffers; results equal
+ *         that path's on the same shifts up to the order of its float sums);
+ *         opts->shifts must be NULL: problem p draws its shifts from seed
+ *         opts->seed + p exactly as tlrmvn_prob does with that seed; n_shifts /
+ *         n_points / periodize apply to all problems.  TLRMVN_E_TIMEOUT: a
+ *         bounded wait of the tensor-core kernel expired (the plan stays usable).
  *   factors, nu: host arrays of length count; the factors must outlive the plan.
  * tlrmvn_batch_run: a[p], b[p] host arrays of the problem's length (original
  * order); logp / err host arrays of length count. */

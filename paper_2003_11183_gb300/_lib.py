@@ -12,7 +12,7 @@ c_u64_p = C.POINTER(C.c_uint64)
 
 class FactorOpts(C.Structure):
     _fields_ = [("tile", C.c_int), ("tol", C.c_double), ("max_rank", C.c_int), ("reorder", C.c_int),
-                ("stream", C.c_void_p), ("strict_rank", C.c_int)]
+                ("stream", C.c_void_p), ("strict_rank", C.c_int), ("schur", C.c_int)]
 
 
 class Opts(C.Structure):

@@ -15,6 +15,7 @@ from . import _lib as L
 
 FP64, FP32, BF16_SHIFT, FP16_SHIFT = 0, 1, 2, 3
 REORDER_NONE, REORDER_BLOCK, REORDER_ITERATIVE = 0, 1, 2
+SCHUR_EXACT, SCHUR_TLR = 0, 1
 KERNEL_EXP, KERNEL_MATERN15, KERNEL_EXP_MATERN15 = 0, 1, 2
 E_INVAL, E_NOT_SPD, E_NOMEM, E_CUDA, E_FORMAT, E_NOTSUP, E_TIMEOUT, E_RANK, E_BUSY = 1, 2, 3, 4, 5, 6, 7, 8, 9
 
@@ -65,35 +66,37 @@ def _stream_ptr(stream) -> int | None:
     return stream.cuda_stream
 
 
-def _fopts(tile: int, tol: float, max_rank: int, reorder: int, stream, strict_rank: bool = False) -> L.FactorOpts:
+def _fopts(tile: int, tol: float, max_rank: int, reorder: int, stream, strict_rank: bool = False,
+           schur: int = 0) -> L.FactorOpts:
     return L.FactorOpts(int(tile), float(tol), int(max_rank), int(reorder), _stream_ptr(stream),
-                        1 if strict_rank else 0)
+                        1 if strict_rank else 0, int(schur))
 
 
 def tlrmvn_factor_kernel(xy, kernel: int, params, nugget: float, a_ref, b_ref, tile: int, tol: float,
                          max_rank: int = 0, reorder: int = REORDER_ITERATIVE, stream=None,
-                         strict_rank: bool = False) -> Factor:
+                         strict_rank: bool = False, schur: int = 0) -> Factor:
     lib = L.load()
     xy = _f64(xy).reshape(-1, 2)
     p = _f64(list(params) + [0.0] * (2 - len(params)))
     a = None if a_ref is None else _f64(a_ref)
     b = None if b_ref is None else _f64(b_ref)
     out = C.c_void_p()
-    o = _fopts(tile, tol, max_rank, reorder, stream, strict_rank)
+    o = _fopts(tile, tol, max_rank, reorder, stream, strict_rank, schur)
     _check(lib.tlrmvn_factor_kernel(_dp(xy), xy.shape[0], int(kernel), _dp(p), float(nugget), _dp(a), _dp(b),
                                     C.byref(o), C.byref(out)), "tlrmvn_factor_kernel")
     return Factor(out.value)
 
 
 def tlrmvn_factor_dense(cov, a_ref, b_ref, tile: int, tol: float, max_rank: int = 0,
-                        reorder: int = REORDER_ITERATIVE, stream=None, strict_rank: bool = False) -> Factor:
+                        reorder: int = REORDER_ITERATIVE, stream=None, strict_rank: bool = False,
+                        schur: int = 0) -> Factor:
     lib = L.load()
     cov = np.asfortranarray(cov, dtype=np.float64)
     n = cov.shape[0]
     a = None if a_ref is None else _f64(a_ref)
     b = None if b_ref is None else _f64(b_ref)
     out = C.c_void_p()
-    o = _fopts(tile, tol, max_rank, reorder, stream, strict_rank)
+    o = _fopts(tile, tol, max_rank, reorder, stream, strict_rank, schur)
     _check(lib.tlrmvn_factor_dense(cov.ctypes.data_as(L.c_double_p), n, n, _dp(a), _dp(b), C.byref(o), C.byref(out)),
            "tlrmvn_factor_dense")
     return Factor(out.value)
@@ -148,14 +151,15 @@ def tlrmvn_factor_import(buf: bytes) -> Factor:
 class BatchPlan:
     """tlrmvn_batch_t: many factors solved by one persistent launch (replayed CUDA graph)."""
 
-    def __init__(self, factors, nu, n_shifts: int, n_points: int, seed: int = 0, periodize: bool = True):
+    def __init__(self, factors, nu, n_shifts: int, n_points: int, seed: int = 0, periodize: bool = True,
+                 precision: int = FP32):
         lib = L.load()
         self.factors = list(factors)  # keep the handles alive
         self.sizes = [tlrmvn_factor_info(f)["n"] for f in self.factors]
         count = len(self.factors)
         hs = (C.c_void_p * count)(*[f.handle.value for f in self.factors])
         nus = _f64(nu if np.ndim(nu) else [nu] * count)
-        o, _ = _opts(FP32, n_shifts, n_points, periodize, None, seed, 0, None, 0)
+        o, _ = _opts(precision, n_shifts, n_points, periodize, None, seed, 0, None, 0)
         out = C.c_void_p()
         _check(lib.tlrmvn_batch_create(count, hs, _dp(nus), C.byref(o), C.byref(out)), "tlrmvn_batch_create")
         self.handle = out
@@ -198,9 +202,9 @@ class BatchPlan:
 
 
 def tlrmvn_prob_batch(factors, a_list, b_list, nu, n_shifts: int, n_points: int, seed: int = 0,
-                      periodize: bool = True):
+                      periodize: bool = True, precision: int = FP32):
     """One-shot batched solve: (logp, err) arrays."""
-    plan = BatchPlan(factors, nu, n_shifts, n_points, seed, periodize)
+    plan = BatchPlan(factors, nu, n_shifts, n_points, seed, periodize, precision)
     try:
         return plan.run(a_list, b_list)
     finally:

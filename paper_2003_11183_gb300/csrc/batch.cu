@@ -9,8 +9,17 @@
 // never wait on one another, so the kernel has no inter-CTA spin.  A plan
 // captures the launch sequence (limit permutation, persistent kernel,
 // estimator) in a CUDA graph, replayed for every new set of limits.
+//
+// Two persistent kernels: k_batch (TLRMVN_FP32: the shifts and projections as
+// float SIMT loops, W float) and k_batch_tc (TLRMVN_BF16_SHIFT: every tile runs
+// the whole-tile sweep of the single-problem path, stc_tile, with the shifts,
+// in-tile coupling and projections on tcgen05; W and the sample-major y in
+// CTA-private bf16 regions read back by TMA through one tensor map each, the
+// per-problem factor operands through three tensor maps per problem kept in
+// global memory).
 #include "common.cuh"
 #include "sov_device.cuh"
+#include "sweep_tc.cuh"
 
 #include <algorithm>
 #include <cstdio>
@@ -175,6 +184,109 @@ __global__ void __launch_bounds__(BATCH_T) k_batch(const BatchProblem* __restric
   }
 }
 
+// ---- tensor-core batched integrand (BF16-shift precision) ----------------------------------
+constexpr int BATCH_TC_MY = 128;  // y columns of the hi halves in the CTA-private y rows (lo at + 128)
+constexpr int BATCH_TC_MAPS = 3;  // per problem: split B (32-deep boxes), U rows, V rows (64 x 64 boxes)
+
+struct BatchTcProblem {
+  int n, r, m, my;  // my: the factor's split-B lo offset (m rounded up to 64)
+  int64_t n_points, ldbt, logp_off;
+  double nu;
+  const int64_t* tile_off;
+  const int64_t* kpad_off;  // first W row of each row tile's ranks (multiples of 64)
+  const int64_t* krow_off;
+  const int64_t* kcol_off;
+  const int32_t* vmap16;    // W row of each column rank
+  const float* BT;
+  const float* inv;
+  const float* band;
+  const uint64_t* Q;
+  const uint64_t* D;
+  const float* a;
+  const float* b;
+};
+
+template <int FLAGS>
+__global__ void __launch_bounds__(STC_NS, 6)
+    k_batch_tc(const BatchTcProblem* __restrict__ probs, const CUtensorMap* __restrict__ pmaps,
+               const BatchItem* __restrict__ items, int n_items, int* next, const __grid_constant__ CUtensorMap mapW,
+               const __grid_constant__ CUtensorMap mapY, const __grid_constant__ CUtensorMap mapY64,
+               unsigned short* Wbase, int64_t kwmax, unsigned short* Ybase, double* logP, int* err) {
+  constexpr bool PER = FLAGS & SWEEP_PERIODIZE;
+  extern __shared__ __align__(1024) unsigned char stc_smem[];
+  __shared__ uint32_t phases;
+  __shared__ int abort_flag;
+  __shared__ int cur;
+  const StcCta k = stc_cta_setup(stc_smem, &phases, &abort_flag);
+  const int tid = threadIdx.x;
+  StcPlace pl;
+  pl.wx = 0;
+  pl.wy = (int)(blockIdx.x * kwmax);
+  pl.yrow = blockIdx.x * STC_NS;
+  pl.ysrow = Ybase + ((int64_t)blockIdx.x * STC_NS + tid) * (2 * BATCH_TC_MY);
+  pl.wcol = Wbase + (int64_t)blockIdx.x * kwmax * STC_NS + tid;
+  for (;;) {
+    __syncthreads();  // every thread is done with the previous item
+    if (tid == 0) cur = atomicAdd(next, 1);
+    __syncthreads();
+    const int it = cur;
+    if (it >= n_items || *(volatile int*)&abort_flag) break;
+    const BatchItem item = items[it];
+    const BatchTcProblem& P = probs[item.prob];
+    const bool act = tid < item.count;
+    const int64_t g = item.sample0 + (act ? tid : item.count - 1);  // inactive lanes shadow a valid sample
+    const int64_t sh = g / P.n_points;
+    const uint32_t ks = (uint32_t)(g - sh * P.n_points) + 1u;
+    const uint64_t* Drow = P.D + sh * (int64_t)(P.n + 1);
+    float rs = 1.0f;
+    if (isfinite(P.nu)) {
+      double w, wc;
+      lattice_w((uint64_t)ks * P.Q[P.n] + Drow[P.n], PER ? 1 : 0, w, wc);
+      rs = (float)sqrt(2.0 * gamma_p_inv(0.5 * P.nu, w, wc) / P.nu);
+    }
+    const CUtensorMap* mp = pmaps + (int64_t)BATCH_TC_MAPS * item.prob;
+    float prod = 1.0f, lsum = 0.0f;
+    int pe = 0;
+    bool ok = true;
+    for (int i = 0; i < P.r && ok; i++) {
+      const int64_t t0 = P.tile_off[i];
+      SweepTcArgs p;
+      DiagArgs32& d = p.d;
+      d.BT = P.BT + (int64_t)i * P.m * P.ldbt;
+      d.inv = P.inv + (int64_t)i * P.m;
+      d.band = P.band + (int64_t)i * P.m * 16;
+      d.mt = (int)(P.tile_off[i + 1] - t0);
+      d.ldbt = P.ldbt;
+      d.a = P.a + t0;
+      d.b = P.b + t0;
+      d.Q = P.Q;
+      d.coord0 = t0;
+      d.ys_lo = BATCH_TC_MY;
+      p.brow0 = i * P.m;
+      p.alo = BATCH_TC_MY;
+      p.blo = P.my;
+      p.urow0 = i * P.m;
+      p.krow0 = (int)P.kpad_off[i];
+      p.kr = (int)(P.krow_off[i + 1] - P.krow_off[i]);
+      p.kcol0 = (int)P.kcol_off[i];
+      p.kc = (int)(P.kcol_off[i + 1] - P.kcol_off[i]);
+      p.W = Wbase;
+      p.ldw = STC_NS;
+      p.vmap = P.vmap16 ? P.vmap16 + P.kcol_off[i] : nullptr;
+      p.wscale = nullptr;
+      p.tscale = 1.0f;
+      p.err = err;
+      ok = stc_tile<FLAGS, false>(&mapY, mp, &mapW, mp + 1, &mapY64, mp + 2, p, k, pl, act, Drow + t0, ks, rs, prod,
+                                  lsum, pe);
+    }
+    if (ok && act) logP[P.logp_off + g] = (double)(logf(prod) + lsum) + (double)pe * 0.69314718055994530942;
+  }
+  stc_cta_release(k);
+}
+static const void* batch_tc_kernel(int periodize) {
+  return periodize ? (const void*)k_batch_tc<SWEEP_PERIODIZE> : (const void*)k_batch_tc<0>;
+}
+
 // limits of all problems: original order (staged) -> factor order, float; validation
 __global__ void k_permute_batch(const double* a, const double* b, const int64_t* perm_g, int64_t total, float* a32,
                                 float* b32, int* bad) {
@@ -214,7 +326,7 @@ static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / 
 struct BatchCopies {
   float* UT = nullptr;
   float* VT = nullptr;
-  int64_t *tile_off = nullptr, *krow_off = nullptr, *kcol_off = nullptr, *vt_off = nullptr;
+  int64_t *tile_off = nullptr, *krow_off = nullptr, *kcol_off = nullptr, *vt_off = nullptr, *kpad_off = nullptr;
   int32_t* kcpad = nullptr;
   ~BatchCopies() {
     dfree(UT);
@@ -223,15 +335,25 @@ struct BatchCopies {
     dfree(krow_off);
     dfree(kcol_off);
     dfree(vt_off);
+    dfree(kpad_off);
     dfree(kcpad);
   }
 };
+int ensure_precision_copies(Factor& F, int precision, cudaStream_t st);  // prob.cu
+int make_tensor_map_16(CUtensorMap* map, const void* base, uint64_t inner, uint64_t outer, uint64_t pitch,
+                       uint32_t box_outer, uint32_t box_inner, bool f16);  // prob.cu
 
 int ensure_float_tiles(Factor& F, cudaStream_t st);  // prob.cu: BT32 / inv32
 
-static int make_batch_copies(Factor& F, BatchCopies& C, cudaStream_t st) {
+// tc: the tensor-core kernel's operands (the factor's bf16 copies and the padded
+// rank offsets) instead of the float SIMT copies UT / VT.
+static int make_batch_copies(Factor& F, BatchCopies& C, bool tc, cudaStream_t st) {
   const int r = F.r, m = F.m;
-  {
+  if (tc) {
+    TLR_CHECK(ensure_precision_copies(F, TLRMVN_BF16_SHIFT, st));
+    TLR_CHECK(dalloc(&C.kpad_off, r + 1));
+    TLR_CUDA(cudaMemcpyAsync(C.kpad_off, F.kpad_off.data(), (r + 1) * 8, cudaMemcpyHostToDevice, st));
+  } else {
     std::lock_guard<std::mutex> lk(F.copy_mu);
     TLR_CHECK(ensure_float_tiles(F, st));
     TLR_CUDA(cudaStreamSynchronize(st));
@@ -252,7 +374,7 @@ static int make_batch_copies(Factor& F, BatchCopies& C, cudaStream_t st) {
   TLR_CUDA(cudaMemcpyAsync(C.kcol_off, F.kcol_off.data(), (r + 1) * 8, cudaMemcpyHostToDevice, st));
   TLR_CUDA(cudaMemcpyAsync(C.vt_off, vt_off.data(), (r + 1) * 8, cudaMemcpyHostToDevice, st));
   TLR_CUDA(cudaMemcpyAsync(C.kcpad, kcpad.data(), r * 4, cudaMemcpyHostToDevice, st));
-  if (F.ktot) {
+  if (F.ktot && !tc) {
     std::vector<int32_t> ktile(F.ktot);
     for (int i = 0; i < r; i++)
       for (int64_t g = F.krow_off[i]; g < F.krow_off[i + 1]; g++) ktile[g] = i;
@@ -270,6 +392,7 @@ static int make_batch_copies(Factor& F, BatchCopies& C, cudaStream_t st) {
     TLR_CUDA(cudaStreamSynchronize(st));
     dfree(dkt);
   }
+  TLR_CUDA(cudaStreamSynchronize(st));
   TLR_CUDA(cudaGetLastError());
   return TLRMVN_OK;
 }
@@ -288,6 +411,14 @@ struct Batch {
   int* dnext = nullptr;
   int* dbad = nullptr;
   float* W = nullptr;
+  // tensor-core kernel (TLRMVN_BF16_SHIFT)
+  bool tc = false;
+  int64_t kwmax = 0;          // W rows of one CTA's region (the largest padded rank space)
+  BatchTcProblem* dtprobs = nullptr;
+  CUtensorMap* dmaps = nullptr;
+  unsigned short *W16 = nullptr, *Y16 = nullptr;
+  CUtensorMap mapW{}, mapY{}, mapY64{};
+  int* derr = nullptr;
   double *logP = nullptr, *ell = nullptr, *out = nullptr, *a_st = nullptr, *b_st = nullptr;
   float *a32 = nullptr, *b32 = nullptr;
   int64_t* perm_g = nullptr;
@@ -298,6 +429,11 @@ struct Batch {
   ~Batch() {
     if (exec) cudaGraphExecDestroy(exec);
     dfree(dprobs);
+    dfree(dtprobs);
+    dfree(dmaps);
+    dfree(W16);
+    dfree(Y16);
+    dfree(derr);
     dfree(ditems);
     dfree(dnext);
     dfree(dbad);
@@ -331,9 +467,21 @@ static int batch_capture(Batch& B, int per_sm) {
   TLR_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
   cudaMemsetAsync(B.dbad, 0, sizeof(int), st);
   cudaMemsetAsync(B.dnext, 0, sizeof(int), st);
+  if (B.tc) cudaMemsetAsync(B.derr, 0, sizeof(int), st);
   k_permute_batch<<<nblk(B.total_n, 256), 256, 0, st>>>(B.a_st, B.b_st, B.perm_g, B.total_n, B.a32, B.b32, B.dbad);
-  k_batch<<<grid, BATCH_T, batch_smem(), st>>>(B.dprobs, B.ditems, B.n_items, B.dnext, B.W,
-                                              std::max<int64_t>(B.ktot_max, 1) * BATCH_T, B.logP);
+  if (B.tc) {
+    if (B.periodize)
+      k_batch_tc<SWEEP_PERIODIZE><<<grid, STC_NS, sweep_tc_smem_bytes(), st>>>(
+          B.dtprobs, B.dmaps, B.ditems, B.n_items, B.dnext, B.mapW, B.mapY, B.mapY64, B.W16, B.kwmax, B.Y16, B.logP,
+          B.derr);
+    else
+      k_batch_tc<0><<<grid, STC_NS, sweep_tc_smem_bytes(), st>>>(B.dtprobs, B.dmaps, B.ditems, B.n_items, B.dnext,
+                                                                 B.mapW, B.mapY, B.mapY64, B.W16, B.kwmax, B.Y16,
+                                                                 B.logP, B.derr);
+  } else {
+    k_batch<<<grid, BATCH_T, batch_smem(), st>>>(B.dprobs, B.ditems, B.n_items, B.dnext, B.W,
+                                                std::max<int64_t>(B.ktot_max, 1) * BATCH_T, B.logP);
+  }
   k_shift_reduce<<<(unsigned)(B.count * B.M), 256, 0, st>>>(B.logP, B.N, B.ell);
   k_final_batch<<<B.count, 256, 0, st>>>(B.ell, B.M, B.out);
   cudaError_t ec = cudaStreamEndCapture(st, &graph);
@@ -355,6 +503,7 @@ static int batch_build(Batch& B, int count, const tlrmvn_factor_t* factors, cons
   B.M = o.n_shifts;
   B.N = o.n_points;
   B.periodize = o.periodize;
+  B.tc = o.precision == TLRMVN_BF16_SHIFT;
   TLR_CUDA(cudaGetDevice(&B.device));
   TLR_CUDA(cudaStreamCreateWithFlags(&B.st, cudaStreamNonBlocking));
   cudaStream_t st = B.st;
@@ -369,7 +518,8 @@ static int batch_build(Batch& B, int count, const tlrmvn_factor_t* factors, cons
     B.F[p] = F;
     B.n_off[p + 1] = B.n_off[p] + F->n;
     B.ktot_max = std::max(B.ktot_max, F->ktot);
-    TLR_CHECK(make_batch_copies(*F, B.copies[p], st));
+    TLR_CHECK(make_batch_copies(*F, B.copies[p], B.tc, st));
+    if (B.tc) B.kwmax = std::max(B.kwmax, F->kw16);
   }
   B.total_n = B.n_off[count];
   const int64_t S = (int64_t)B.M * B.N;
@@ -434,13 +584,83 @@ static int batch_build(Batch& B, int count, const tlrmvn_factor_t* factors, cons
   TLR_CUDA(cudaMemcpyAsync(B.ditems, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice, st));
   TLR_CUDA(cudaMemcpyAsync(B.perm_g, perm_g.data(), perm_g.size() * 8, cudaMemcpyHostToDevice, st));
   // persistent grid (all the CTAs that fit, until tuned) and its private projection buffers
-  const size_t smem = batch_smem();
-  TLR_CHECK(raise_smem_limit((const void*)k_batch, (size_t)smem));
-  TLR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&B.per_sm_max, k_batch, BATCH_T, smem));
   TLR_CUDA(cudaDeviceGetAttribute(&B.sms, cudaDevAttrMultiProcessorCount, B.device));
+  if (B.tc) {
+    const void* kt = batch_tc_kernel(B.periodize);
+    TLR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&B.per_sm_max, kt, STC_NS, sweep_tc_smem_bytes()));
+    // resident CTAs hold their 64 TMEM columns until the end: at most 512 / 64 per SM
+    B.per_sm_max = std::min(B.per_sm_max, 512 / STC_SUB);
+  } else {
+    const size_t smem = batch_smem();
+    TLR_CHECK(raise_smem_limit((const void*)k_batch, (size_t)smem));
+    TLR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&B.per_sm_max, k_batch, BATCH_T, smem));
+  }
   B.per_sm_max = std::max(B.per_sm_max, 1);
   B.grid_max = std::max(1, std::min(B.per_sm_max * B.sms, B.n_items));
-  TLR_CHECK(dalloc(&B.W, (size_t)B.grid_max * std::max<int64_t>(B.ktot_max, 1) * BATCH_T));
+  if (B.tc) {
+    // CTA-private W (kwmax rank rows x 128 samples) and sample-major y (128 rows of
+    // 2 x 128 hi / lo columns), zeroed once: padding rows and columns meet zero
+    // operand entries and must stay finite
+    B.kwmax = std::max<int64_t>(B.kwmax, 64);
+    if ((int64_t)B.grid_max * B.kwmax >= ((int64_t)1 << 31))
+      return fail(TLRMVN_E_NOTSUP, "batched projections exceed the tensor map's coordinate range");
+    const size_t nw = (size_t)B.grid_max * B.kwmax * STC_NS, ny = (size_t)B.grid_max * STC_NS * 2 * BATCH_TC_MY;
+    TLR_CHECK(dalloc(&B.W16, nw));
+    TLR_CHECK(dalloc(&B.Y16, ny));
+    TLR_CHECK(dalloc(&B.derr, 1));
+    TLR_CUDA(cudaMemsetAsync(B.W16, 0, nw * 2, st));
+    TLR_CUDA(cudaMemsetAsync(B.Y16, 0, ny * 2, st));
+    TLR_CUDA(cudaMemsetAsync(B.derr, 0, sizeof(int), st));
+    TLR_CHECK(make_tensor_map_16(&B.mapW, B.W16, STC_NS, (uint64_t)B.grid_max * B.kwmax, STC_NS * 2, 64, 64, false));
+    TLR_CHECK(make_tensor_map_16(&B.mapY, B.Y16, 2 * BATCH_TC_MY, (uint64_t)B.grid_max * STC_NS, 2 * BATCH_TC_MY * 2,
+                                 STC_NS, 32, false));
+    TLR_CHECK(make_tensor_map_16(&B.mapY64, B.Y16, 2 * BATCH_TC_MY, (uint64_t)B.grid_max * STC_NS,
+                                 2 * BATCH_TC_MY * 2, STC_NS, 64, false));
+    // per problem: the split B, U and V maps, and its table entry
+    std::vector<CUtensorMap> maps((size_t)BATCH_TC_MAPS * count);
+    std::vector<BatchTcProblem> tp(count);
+    for (int p = 0; p < count; p++) {
+      const Factor& F = *B.F[p];
+      const int64_t ly = 2 * F.my16;
+      CUtensorMap* mp = &maps[(size_t)BATCH_TC_MAPS * p];
+      TLR_CHECK(make_tensor_map_16(&mp[0], F.B16x2, ly, (uint64_t)F.r * F.m, ly * 2, 64, 32, false));
+      if (F.ktot) {
+        TLR_CHECK(make_tensor_map_16(&mp[1], F.U16, F.kmax16, (uint64_t)F.r * F.m, F.kmax16 * 2, 64, 64, false));
+        TLR_CHECK(make_tensor_map_16(&mp[2], F.V16, F.my16, F.ktot, F.my16 * 2, 64, 64, false));
+      } else {
+        mp[1] = B.mapW;  // (never read: no tile has ranks)
+        mp[2] = B.mapW;
+      }
+      const BatchProblem& P = probs[p];
+      BatchTcProblem& T = tp[p];
+      T.n = P.n;
+      T.r = P.r;
+      T.m = P.m;
+      T.my = (int)F.my16;
+      T.n_points = P.n_points;
+      T.ldbt = P.ldbt;
+      T.logp_off = P.logp_off;
+      T.nu = P.nu;
+      T.tile_off = P.tile_off;
+      T.kpad_off = B.copies[p].kpad_off;
+      T.krow_off = P.krow_off;
+      T.kcol_off = P.kcol_off;
+      T.vmap16 = F.vmap16;
+      T.BT = P.BT;
+      T.inv = P.inv;
+      T.band = P.band;
+      T.Q = P.Q;
+      T.D = P.D;
+      T.a = P.a;
+      T.b = P.b;
+    }
+    TLR_CHECK(dalloc(&B.dmaps, maps.size()));
+    TLR_CHECK(dalloc(&B.dtprobs, count));
+    TLR_CUDA(cudaMemcpyAsync(B.dmaps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice, st));
+    TLR_CUDA(cudaMemcpyAsync(B.dtprobs, tp.data(), tp.size() * sizeof(BatchTcProblem), cudaMemcpyHostToDevice, st));
+  } else {
+    TLR_CHECK(dalloc(&B.W, (size_t)B.grid_max * std::max<int64_t>(B.ktot_max, 1) * BATCH_T));
+  }
   TLR_CHECK(dalloc(&B.dnext, 1));
   TLR_CHECK(dalloc(&B.dbad, 1));
   TLR_CHECK(dalloc(&B.logP, (size_t)B.total_samples));
@@ -449,7 +669,7 @@ static int batch_build(Batch& B, int count, const tlrmvn_factor_t* factors, cons
   TLR_CHECK(dalloc(&B.a_st, (size_t)B.total_n));
   TLR_CHECK(dalloc(&B.b_st, (size_t)B.total_n));
   TLR_CUDA(cudaMallocHost(&B.h_ab, (size_t)B.total_n * 2 * 8));
-  TLR_CUDA(cudaMallocHost(&B.h_out, (size_t)count * 2 * 8 + 8));
+  TLR_CUDA(cudaMallocHost(&B.h_out, (size_t)count * 2 * 8 + 16));
   TLR_CUDA(cudaStreamSynchronize(st));
   return batch_capture(B, B.per_sm_max);
 }
@@ -469,11 +689,15 @@ static int batch_run(Batch& B, const double* const* a, const double* const* b, d
   TLR_CUDA(cudaGraphLaunch(B.exec, st));
   TLR_CUDA(cudaMemcpyAsync(B.h_out, B.out, (size_t)B.count * 2 * 8, cudaMemcpyDeviceToHost, st));
   TLR_CUDA(cudaMemcpyAsync(B.h_out + 2 * B.count, B.dbad, sizeof(int), cudaMemcpyDeviceToHost, st));
+  if (B.tc) TLR_CUDA(cudaMemcpyAsync(B.h_out + 2 * B.count + 1, B.derr, sizeof(int), cudaMemcpyDeviceToHost, st));
   TLR_CUDA(cudaStreamSynchronize(st));
-  int bad = 0;
+  int bad = 0, terr = 0;
   memcpy(&bad, B.h_out + 2 * B.count, sizeof(int));
+  if (B.tc) memcpy(&terr, B.h_out + 2 * B.count + 1, sizeof(int));
   cudaSetDevice(cur);
   if (bad) return fail(TLRMVN_E_INVAL, "limits must satisfy a_i <= b_i, a_i < +inf, b_i > -inf, no NaN");
+  if (terr)
+    return fail(TLRMVN_E_TIMEOUT, "tensor-core batched kernel gave up waiting (code " + std::to_string(terr) + ")");
   for (int p = 0; p < B.count; p++) {
     logp[p] = B.h_out[2 * p];
     err[p] = B.h_out[2 * p + 1];
@@ -484,7 +708,8 @@ static int batch_run(Batch& B, const double* const* a, const double* const* b, d
 static int check_batch_opts(int count, const tlrmvn_factor_t* f, const double* nu, const tlrmvn_opts* o) {
   if (count < 1 || !f || !nu || !o) return fail(TLRMVN_E_INVAL, "bad batch arguments");
   if (o->n_shifts < 1 || o->n_points < 1) return fail(TLRMVN_E_INVAL, "n_shifts and n_points must be >= 1");
-  if (o->precision != TLRMVN_FP32) return fail(TLRMVN_E_NOTSUP, "the batched integrand runs in TLRMVN_FP32");
+  if (o->precision != TLRMVN_FP32 && o->precision != TLRMVN_BF16_SHIFT)
+    return fail(TLRMVN_E_NOTSUP, "the batched integrand runs in TLRMVN_FP32 or TLRMVN_BF16_SHIFT");
   if (o->shifts) return fail(TLRMVN_E_NOTSUP, "batched problems draw their shifts from opts.seed + problem index");
   return TLRMVN_OK;
 }
@@ -527,7 +752,7 @@ extern "C" int tlrmvn_batch_tune(tlrmvn_batch_t plan, const double* const* a, co
       if (c == ' ') c = '_';
     int64_t ksum = 0;
     for (Factor* F : B.F) ksum += F->ktot;
-    key = dev + " batch c" + std::to_string(B.count) + " n" + std::to_string(B.total_n) + " k" +
+    key = dev + (B.tc ? " batch-bf16 c" : " batch c") + std::to_string(B.count) + " n" + std::to_string(B.total_n) + " k" +
           std::to_string(ksum) + " s" + std::to_string((int64_t)B.M * B.N);
   }
   int best = -1;

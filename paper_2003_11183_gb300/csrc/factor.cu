@@ -446,6 +446,26 @@ __global__ void k_permute_block(double* S, double* tmp, int64_t* idx, double* a,
   }
 }
 
+// ---- a cluster's variables reordered in every tile that involves it ------------------------
+// M[v][c] <- M[order[v]][c] for v < mb, c < k (one m x cap slot side per CTA, 4 columns at a time)
+struct PermJob {
+  double* M;
+  int k;
+};
+__global__ void __launch_bounds__(256) k_permute_rows(const PermJob* jobs, const int* order, int mb, int cap) {
+  __shared__ double sh[1024 * 4];
+  const PermJob jb = jobs[blockIdx.x];
+  for (int c0 = 0; c0 < jb.k; c0 += 4) {
+    const int w = min(4, jb.k - c0);
+    for (int t = threadIdx.x; t < mb * 4; t += blockDim.x)
+      if ((t & 3) < w) sh[t] = jb.M[(size_t)(t >> 2) * cap + c0 + (t & 3)];
+    __syncthreads();
+    for (int t = threadIdx.x; t < mb * 4; t += blockDim.x)
+      if ((t & 3) < w) jb.M[(size_t)(t >> 2) * cap + c0 + (t & 3)] = sh[order[t >> 2] * 4 + (t & 3)];
+    __syncthreads();
+  }
+}
+
 // ---- pack slots into the compact factor layout ---------------------------------------------
 struct PackJob {
   const double* U;   // slot, m x cap
@@ -594,21 +614,32 @@ static int factor_build(const CovSrc& src, int64_t n, std::vector<int64_t> geo, 
   TLR_CHECK(bd.get(&d_order, (size_t)r * m));
   TLR_CHECK(bd.get(&d_y, (size_t)r * m));
   TLR_CHECK(bd.get(&ptmp, std::max<size_t>((size_t)m * std::max(m, cap), 3 * (size_t)m)));
-  TLR_CHECK(bd.get(&d_ranks, r));
+  const bool tlr = o.schur == TLRMVN_SCHUR_TLR;
+  const size_t max_pairs_step = (size_t)(r / 2 + 1) * (size_t)(r / 2 + 1);
+  // TLR arithmetic: tiles truncated per batch, each written out densely first (<= 1 GiB of them)
+  const size_t tbatch =
+      tlr ? std::max<size_t>(1, std::min<size_t>({max_pairs_step, (size_t)16384, ((size_t)1 << 30) / ((size_t)m * m * 8)}))
+          : (size_t)r;
+  const size_t jcap = std::max<size_t>(tbatch, (size_t)r);
+  TLR_CHECK(bd.get(&d_ranks, jcap));
   TLR_CHECK(bd.get(&d_capped, 1));
   TLR_CHECK(bd.get(&d_blist, r));
   TLR_CHECK(bd.get(&d_logp, r));
   TLR_CHECK(bd.get(&Linv, (size_t)m * m));
   const size_t npairs = (size_t)r * (r - 1) / 2;
   TLR_CHECK(bd.get(&pool, std::max<size_t>(npairs, 1) * 2 * (size_t)m * cap));
-  TLR_CHECK(bd.get(&Sij, (size_t)std::max(r - 1, 1) * m * m));
-  TLR_CHECK(bd.get(&Lij, (size_t)std::max(r - 1, 1) * m * m));
+  if (tlr) {
+    TLR_CHECK(bd.get(&Sij, tbatch * m * m));  // the batch of dense tiles to truncate
+    Lij = nullptr;
+  } else {
+    TLR_CHECK(bd.get(&Sij, (size_t)std::max(r - 1, 1) * m * m));
+    TLR_CHECK(bd.get(&Lij, (size_t)std::max(r - 1, 1) * m * m));
+  }
   const size_t uc_par = reorder ? (size_t)r : 1;
   TLR_CHECK(bd.get(&work, uc_par * m * m));
-  const size_t max_pairs_step = (size_t)(r / 2 + 1) * (size_t)(r / 2 + 1);
   TLR_CHECK(bd.get(&Xs, max_pairs_step * cap * cap));
   TLR_CHECK(bd.get(&Ys, max_pairs_step * cap * m));
-  const size_t ent_cap = std::max<size_t>(max_pairs_step, (size_t)r) + 8, seg_cap = ent_cap;
+  const size_t ent_cap = std::max<size_t>(max_pairs_step, (size_t)r) + 8, seg_cap = 2 * ent_cap;
   GemmEntry* d_ent;
   GemmSeg* d_seg;
   TileJob* d_tj;
@@ -618,8 +649,10 @@ static int factor_build(const CovSrc& src, int64_t n, std::vector<int64_t> geo, 
   double** d_urows;
   TLR_CHECK(bd.get(&d_ent, ent_cap));
   TLR_CHECK(bd.get(&d_seg, seg_cap));
-  TLR_CHECK(bd.get(&d_tj, (size_t)r));
-  TLR_CHECK(bd.get(&d_aj, (size_t)r));
+  TLR_CHECK(bd.get(&d_tj, jcap));
+  TLR_CHECK(bd.get(&d_aj, jcap));
+  PermJob* d_pmj;
+  TLR_CHECK(bd.get(&d_pmj, (size_t)r));
   TLR_CHECK(bd.get(&d_cj, (size_t)r));
   TLR_CHECK(bd.get(&d_pj, std::max<size_t>(npairs, 1)));
   TLR_CHECK(bd.get(&d_urows, (size_t)r));
@@ -687,207 +720,449 @@ static int factor_build(const CovSrc& src, int64_t n, std::vector<int64_t> geo, 
   std::vector<GemmEntry> ent;
   std::vector<GemmSeg> seg;
 
-  for (int j = 0; j < r; j++) {
-    // -- choose the block of position j and its within-block order
-    bool permute = false;
-    int chosen = 0;
-    if (o.reorder == TLRMVN_REORDER_ITERATIVE) {
-      std::vector<int> bl(pos2blk.begin() + j, pos2blk.end());
-      TLR_CHECK(upload(d_blist, bl, st));
-      k_uc<<<(unsigned)bl.size(), uc_threads, uc_smem, st>>>(d_blist, diagS, d_bsize, m, d_a, d_b, work, d_logp, 1,
-                                                             d_order, d_y, d_status);
-      TLR_CUDA(cudaGetLastError());
-      TLR_CHECK(check_status(d_status, st, "iterative block reordering"));
-      std::vector<double> p(bl.size());
-      TLR_CUDA(cudaMemcpyAsync(p.data(), d_logp, p.size() * 8, cudaMemcpyDeviceToHost, st));
-      TLR_CUDA(cudaStreamSynchronize(st));
-      int best = 0;
-      for (size_t l = 1; l < p.size(); l++)
-        if (p[l] < p[best]) best = (int)l;
-      const int jt = j + best;
-      chosen = best;
-      if (jt != j) {
-        std::swap(pos2blk[j], pos2blk[jt]);
-        for (int k = 0; k < j; k++) {
-          std::swap(slot[(size_t)j * r + k], slot[(size_t)jt * r + k]);
-          std::swap(rank[(size_t)j * r + k], rank[(size_t)jt * r + k]);
-        }
-      }
-      permute = true;
-    }
-    const int bj = pos2blk[j];
-    const int mj = sizes[bj];
-    double* Sjj = diagS + (size_t)bj * m * m;
-    const double* yj = d_y + (size_t)chosen * m;
-    if (permute) {
-      std::vector<double*> ur;
-      for (int k = 0; k < j; k++)
-        if (rank[(size_t)j * r + k] > 0) ur.push_back(Uslot(slot[(size_t)j * r + k]));
-      TLR_CHECK(upload(d_urows, ur, st));
-      k_permute_block<<<1, 512, 0, st>>>(Sjj, ptmp, d_idx + (size_t)bj * m, d_a + (size_t)bj * m, d_b + (size_t)bj * m,
-                                         d_order + (size_t)chosen * m, mj, m, d_urows, (int)ur.size(), cap);
-      TLR_CUDA(cudaGetLastError());
-      TLR_CUDA(cudaStreamSynchronize(st));
-    }
-    // -- L_jj and its inverse
-    k_potrf<<<1, 512, m * sizeof(double), st>>>(Sjj, mj, m, d_status);
-    TLR_CUDA(cudaGetLastError());
-    TLR_CHECK(check_status(d_status, st, "diagonal Cholesky"));
-    k_trinv<<<1, 512, 0, st>>>(Sjj, Linv, mj, m);
-    const int nrem = r - 1 - j;
-    if (nrem == 0) break;
-    // -- Sigma_ij for the remaining blocks
-    {
-      std::vector<TileJob> tj(nrem);
-      for (int q = 0; q < nrem; q++) {
-        int bi = pos2blk[j + 1 + q];
-        tj[q] = TileJob{Sij + (size_t)q * m * m, d_idx + (size_t)bi * m, d_idx + (size_t)bj * m, sizes[bi], mj};
-      }
-      TLR_CHECK(upload(d_tj, tj, st));
-      k_cov_tiles<<<dim3(std::max(1, (m * m + 255) / 256 / 4), nrem), 256, 0, st>>>(d_tj, src, m);
-      TLR_CUDA(cudaGetLastError());
-      TLR_CUDA(cudaStreamSynchronize(st));
-    }
-    // -- left-looking update S_ij -= sum_k U_ik (V_ik^T V_jk) U_jk^T
-    {
-      struct P {
-        int q, k;
-        size_t xo, yo;
-      };
-      std::vector<P> pairs;
-      size_t xo = 0, yo = 0;
-      for (int q = 0; q < nrem; q++) {
-        int i = j + 1 + q;
-        for (int k = 0; k < j; k++) {
-          int kik = rank[(size_t)i * r + k], kjk = rank[(size_t)j * r + k];
-          if (!kik || !kjk) continue;
-          pairs.push_back(P{q, k, xo, yo});
-          xo += (size_t)kik * kjk;
-          yo += (size_t)kik * m;
-        }
-      }
-      if (!pairs.empty()) {
-        if (xo > max_pairs_step * cap * cap || yo > max_pairs_step * cap * m)
-          return fail(TLRMVN_E_CUDA, "internal: left-looking scratch overflow");
-        ent.clear();
-        seg.clear();
-        for (auto& pr : pairs) {  // X_ik = V_ik^T V_jk
-          int i = j + 1 + pr.q;
-          int kik = rank[(size_t)i * r + pr.k], kjk = rank[(size_t)j * r + pr.k];
-          int mk = sizes[pos2blk[pr.k]];
-          seg.push_back(GemmSeg{Vslot(slot[(size_t)i * r + pr.k]), Vslot(slot[(size_t)j * r + pr.k]), cap, cap, mk});
-          ent.push_back(GemmEntry{Xs + pr.xo, kjk, kik, kjk, (int)seg.size() - 1, (int)seg.size(), 1.0, 0.0});
-        }
-        TLR_CHECK((run_batched<true, false>(ent, seg, d_ent, d_seg, ent_cap, seg_cap, st)));
-        ent.clear();
-        seg.clear();
-        for (auto& pr : pairs) {  // Y_ik = X_ik U_jk^T
-          int i = j + 1 + pr.q;
-          int kik = rank[(size_t)i * r + pr.k], kjk = rank[(size_t)j * r + pr.k];
-          seg.push_back(GemmSeg{Xs + pr.xo, Uslot(slot[(size_t)j * r + pr.k]), kjk, cap, kjk});
-          ent.push_back(GemmEntry{Ys + pr.yo, m, kik, mj, (int)seg.size() - 1, (int)seg.size(), 1.0, 0.0});
-        }
-        TLR_CHECK((run_batched<false, true>(ent, seg, d_ent, d_seg, ent_cap, seg_cap, st)));
-        ent.clear();
-        seg.clear();
-        size_t p0 = 0;
-        for (int q = 0; q < nrem; q++) {  // S_ij -= sum_k U_ik Y_ik
-          int i = j + 1 + q;
-          int s0 = (int)seg.size();
-          while (p0 < pairs.size() && pairs[p0].q == q) {
-            auto& pr = pairs[p0++];
-            int kik = rank[(size_t)i * r + pr.k];
-            seg.push_back(GemmSeg{Uslot(slot[(size_t)i * r + pr.k]), Ys + pr.yo, cap, m, kik});
-          }
-          if ((int)seg.size() > s0)
-            ent.push_back(GemmEntry{Sij + (size_t)q * m * m, m, sizes[pos2blk[i]], mj, s0, (int)seg.size(), -1.0, 1.0});
-        }
-        TLR_CHECK((run_batched<false, false>(ent, seg, d_ent, d_seg, ent_cap, seg_cap, st)));
-      }
-    }
-    // -- L_ij = S_ij L_jj^-T
-    ent.clear();
-    seg.clear();
-    for (int q = 0; q < nrem; q++) {
-      int mi = sizes[pos2blk[j + 1 + q]];
-      seg.push_back(GemmSeg{Sij + (size_t)q * m * m, Linv, m, m, mj});
-      ent.push_back(GemmEntry{Lij + (size_t)q * m * m, m, mi, mj, q, q + 1, 1.0, 0.0});
-    }
-    TLR_CHECK((run_batched<false, true>(ent, seg, d_ent, d_seg, ent_cap, seg_cap, st)));
-    // -- ACA of every L_ij into fresh slots
-    {
-      std::vector<AcaJob> aj(nrem);
-      for (int q = 0; q < nrem; q++) {
-        int i = j + 1 + q;
-        int s = next_slot++;
-        slot[(size_t)i * r + j] = s;
-        aj[q] = AcaJob{Lij + (size_t)q * m * m, Uslot(s), Vslot(s), sizes[pos2blk[i]], mj};
-      }
+  // ---- tile-low-rank arithmetic (TLRMVN_SCHUR_TLR): Algorithm 5 as printed -------------------
+  // Every unordered cluster pair {p, q} owns pool slot sid(p, q): Sigma_pq ~ U V^T, U on the
+  // variables of cluster rowc[s] (Sigma_qp = V U^T).  The slots first hold the ACA-compressed
+  // covariance; position by position they are overwritten by the factor tiles L_ij (rowc = the
+  // cluster at position i) and, further right, by the truncated Schur tiles.
+  auto tlr_schur_loop = [&]() -> int {
+    auto sid = [&](int p, int q) -> size_t {
+      if (p > q) std::swap(p, q);
+      return (size_t)p * r - (size_t)p * (p + 1) / 2 + (size_t)(q - p - 1);
+    };
+    std::vector<int> rowc(std::max<size_t>(npairs, 1), 0), rk(std::max<size_t>(npairs, 1), 0);
+    auto side = [&](size_t s, int c) { return rowc[s] == c ? Uslot((int)s) : Vslot((int)s); };
+    struct Trunc {
+      size_t s;
+      int rc, mi, mj;
+    };
+    // ACA of the dense tiles Sij[t] (t < jobs.size()) into their slots
+    auto truncate = [&](const std::vector<Trunc>& jobs) -> int {
+      if (jobs.empty()) return TLRMVN_OK;
+      std::vector<AcaJob> aj(jobs.size());
+      for (size_t t = 0; t < jobs.size(); t++)
+        aj[t] = AcaJob{Sij + t * m * m, Uslot((int)jobs[t].s), Vslot((int)jobs[t].s), jobs[t].mi, jobs[t].mj};
       TLR_CHECK(upload(d_aj, aj, st));
-      k_aca<<<nrem, 512, 2 * m * sizeof(double), st>>>(d_aj, m, cap, o.tol, d_ranks, d_capped);
+      k_aca<<<(unsigned)aj.size(), 512, 2 * m * sizeof(double), st>>>(d_aj, m, cap, o.tol, d_ranks, d_capped);
       TLR_CUDA(cudaGetLastError());
-      std::vector<int> rk(nrem);
-      TLR_CUDA(cudaMemcpyAsync(rk.data(), d_ranks, nrem * sizeof(int), cudaMemcpyDeviceToHost, st));
+      std::vector<int> got(jobs.size());
+      TLR_CUDA(cudaMemcpyAsync(got.data(), d_ranks, got.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
       TLR_CUDA(cudaStreamSynchronize(st));
-      for (int q = 0; q < nrem; q++) rank[(size_t)(j + 1 + q) * r + j] = rk[q];
-    }
-    // -- Algorithm 5: condition the limits of the remaining blocks
-    if (o.reorder == TLRMVN_REORDER_ITERATIVE) {
-      std::vector<CondJob> cj;
-      for (int q = 0; q < nrem; q++) {
-        int i = j + 1 + q, bi = pos2blk[i], k = rank[(size_t)i * r + j];
-        if (!k) continue;
-        int s = slot[(size_t)i * r + j];
-        cj.push_back(CondJob{Uslot(s), Vslot(s), d_a + (size_t)bi * m, d_b + (size_t)bi * m, sizes[bi], mj, k});
+      for (size_t t = 0; t < jobs.size(); t++) {
+        rk[jobs[t].s] = got[t];
+        rowc[jobs[t].s] = jobs[t].rc;
       }
-      if (!cj.empty()) {
-        TLR_CHECK(upload(d_cj, cj, st));
-        k_condition<<<(unsigned)cj.size(), 256, 0, st>>>(d_cj, yj, cap);
+      return TLRMVN_OK;
+    };
+    // -- the TLR covariance: every off-diagonal block compressed by ACA at tol
+    {
+      std::vector<TileJob> tj;
+      std::vector<Trunc> jobs;
+      auto flush = [&]() -> int {
+        if (tj.empty()) return TLRMVN_OK;
+        TLR_CHECK(upload(d_tj, tj, st));
+        k_cov_tiles<<<dim3(std::max(1, (m * m + 255) / 256 / 4), (unsigned)tj.size()), 256, 0, st>>>(d_tj, src, m);
+        TLR_CUDA(cudaGetLastError());
+        TLR_CHECK(truncate(jobs));
+        tj.clear();
+        jobs.clear();
+        return TLRMVN_OK;
+      };
+      for (int p = 0; p < r; p++)
+        for (int q = p + 1; q < r; q++) {
+          tj.push_back(TileJob{Sij + tj.size() * m * m, d_idx + (size_t)p * m, d_idx + (size_t)q * m, sizes[p], sizes[q]});
+          jobs.push_back(Trunc{sid(p, q), p, sizes[p], sizes[q]});
+          if (tj.size() == tbatch) TLR_CHECK(flush());
+        }
+      TLR_CHECK(flush());
+    }
+    for (int j = 0; j < r; j++) {
+      int chosen = 0;
+      if (o.reorder == TLRMVN_REORDER_ITERATIVE) {
+        // -- lines 4-8: UC of every remaining block; the smallest estimate takes position j
+        std::vector<int> bl(pos2blk.begin() + j, pos2blk.end());
+        TLR_CHECK(upload(d_blist, bl, st));
+        k_uc<<<(unsigned)bl.size(), uc_threads, uc_smem, st>>>(d_blist, diagS, d_bsize, m, d_a, d_b, work, d_logp, 1,
+                                                               d_order, d_y, d_status);
+        TLR_CUDA(cudaGetLastError());
+        TLR_CHECK(check_status(d_status, st, "iterative block reordering"));
+        std::vector<double> p(bl.size());
+        TLR_CUDA(cudaMemcpyAsync(p.data(), d_logp, p.size() * 8, cudaMemcpyDeviceToHost, st));
+        TLR_CUDA(cudaStreamSynchronize(st));
+        int best = 0;
+        for (size_t l = 1; l < p.size(); l++)
+          if (p[l] < p[best]) best = (int)l;
+        chosen = best;
+        std::swap(pos2blk[j], pos2blk[j + best]);
+        // its within-block order: the diagonal block, indices and limits, and the
+        // cluster's variables in every tile that involves it
+        const int c = pos2blk[j];
+        const int* ord = d_order + (size_t)chosen * m;
+        k_permute_block<<<1, 512, 0, st>>>(diagS + (size_t)c * m * m, ptmp, d_idx + (size_t)c * m, d_a + (size_t)c * m,
+                                           d_b + (size_t)c * m, ord, sizes[c], m, d_urows, 0, cap);
+        TLR_CUDA(cudaGetLastError());
+        std::vector<PermJob> pj;
+        for (int q = 0; q < r; q++) {
+          if (q == c) continue;
+          const size_t s = sid(c, q);
+          if (rk[s]) pj.push_back(PermJob{side(s, c), rk[s]});
+        }
+        if (!pj.empty()) {
+          TLR_CHECK(upload(d_pmj, pj, st));
+          k_permute_rows<<<(unsigned)pj.size(), 256, 0, st>>>(d_pmj, ord, sizes[c], cap);
+          TLR_CUDA(cudaGetLastError());
+        }
+        TLR_CUDA(cudaStreamSynchronize(st));
+      }
+      const int cj = pos2blk[j], mj = sizes[cj];
+      double* Sjj = diagS + (size_t)cj * m * m;
+      // -- line 10: L_jj and its inverse
+      k_potrf<<<1, 512, m * sizeof(double), st>>>(Sjj, mj, m, d_status);
+      TLR_CUDA(cudaGetLastError());
+      TLR_CHECK(check_status(d_status, st, "diagonal Cholesky"));
+      k_trinv<<<1, 512, 0, st>>>(Sjj, Linv, mj, m);
+      TLR_CUDA(cudaGetLastError());
+      if (j == r - 1) break;
+      // -- line 12: L_ij = Sigma_ij (.) Sigma_jj^-T = U (L_jj^-1 V)^T, truncated; in batches
+      {
+        std::vector<int> qs;
+        for (int i = j + 1; i < r; i++)
+          if (rk[sid(pos2blk[i], cj)]) qs.push_back(i);
+        for (size_t q0 = 0; q0 < qs.size(); q0 += tbatch) {
+          const size_t nb = std::min(tbatch, qs.size() - q0);
+          ent.clear();
+          seg.clear();
+          for (size_t t = 0; t < nb; t++) {  // W_t = L_jj^-1 V (mj x k) into Ys
+            const size_t s = sid(pos2blk[qs[q0 + t]], cj);
+            seg.push_back(GemmSeg{Linv, side(s, cj), m, cap, mj});
+            ent.push_back(GemmEntry{Ys + t * m * cap, cap, mj, rk[s], (int)t, (int)t + 1, 1.0, 0.0});
+          }
+          TLR_CHECK((run_batched<false, false>(ent, seg, d_ent, d_seg, ent_cap, seg_cap, st)));
+          ent.clear();
+          seg.clear();
+          std::vector<Trunc> jobs;
+          for (size_t t = 0; t < nb; t++) {  // D_t = U W_t^T (mi x mj)
+            const int ci = pos2blk[qs[q0 + t]];
+            const size_t s = sid(ci, cj);
+            seg.push_back(GemmSeg{side(s, ci), Ys + t * m * cap, cap, cap, rk[s]});
+            ent.push_back(GemmEntry{Sij + t * m * m, m, sizes[ci], mj, (int)t, (int)t + 1, 1.0, 0.0});
+            jobs.push_back(Trunc{s, ci, sizes[ci], mj});
+          }
+          TLR_CHECK((run_batched<false, true>(ent, seg, d_ent, d_seg, ent_cap, seg_cap, st)));
+          TLR_CHECK(truncate(jobs));
+        }
+      }
+      // -- line 13 (Algorithm 5): a_i, b_i -= L_ij y_j
+      if (o.reorder == TLRMVN_REORDER_ITERATIVE) {
+        std::vector<CondJob> cj_jobs;
+        for (int i = j + 1; i < r; i++) {
+          const int ci = pos2blk[i];
+          const size_t s = sid(ci, cj);
+          if (!rk[s]) continue;
+          cj_jobs.push_back(CondJob{Uslot((int)s), Vslot((int)s), d_a + (size_t)ci * m, d_b + (size_t)ci * m, sizes[ci],
+                                    mj, rk[s]});
+        }
+        if (!cj_jobs.empty()) {
+          TLR_CHECK(upload(d_cj, cj_jobs, st));
+          k_condition<<<(unsigned)cj_jobs.size(), 256, 0, st>>>(d_cj, d_y + (size_t)chosen * m, cap);
+          TLR_CUDA(cudaGetLastError());
+          TLR_CUDA(cudaStreamSynchronize(st));
+        }
+      }
+      // -- lines 15-19, diagonal blocks (dense, exact): S_ii -= U_ij (V_ij^T V_ij) U_ij^T
+      {
+        std::vector<int> is;
+        for (int i = j + 1; i < r; i++)
+          if (rk[sid(pos2blk[i], cj)]) is.push_back(i);
+        if (!is.empty()) {
+          ent.clear();
+          seg.clear();
+          for (size_t t = 0; t < is.size(); t++) {
+            const size_t s = sid(pos2blk[is[t]], cj);
+            seg.push_back(GemmSeg{Vslot((int)s), Vslot((int)s), cap, cap, mj});
+            ent.push_back(GemmEntry{Xs + t * cap * cap, rk[s], rk[s], rk[s], (int)t, (int)t + 1, 1.0, 0.0});
+          }
+          TLR_CHECK((run_batched<true, false>(ent, seg, d_ent, d_seg, ent_cap, seg_cap, st)));
+          ent.clear();
+          seg.clear();
+          for (size_t t = 0; t < is.size(); t++) {
+            const int ci = pos2blk[is[t]];
+            const size_t s = sid(ci, cj);
+            seg.push_back(GemmSeg{Xs + t * cap * cap, Uslot((int)s), rk[s], cap, rk[s]});
+            ent.push_back(GemmEntry{Ys + t * m * cap, m, rk[s], sizes[ci], (int)t, (int)t + 1, 1.0, 0.0});
+          }
+          TLR_CHECK((run_batched<false, true>(ent, seg, d_ent, d_seg, ent_cap, seg_cap, st)));
+          ent.clear();
+          seg.clear();
+          for (size_t t = 0; t < is.size(); t++) {
+            const int ci = pos2blk[is[t]];
+            const size_t s = sid(ci, cj);
+            seg.push_back(GemmSeg{Uslot((int)s), Ys + t * m * cap, cap, m, rk[s]});
+            ent.push_back(GemmEntry{diagS + (size_t)ci * m * m, m, sizes[ci], sizes[ci], (int)t, (int)t + 1, -1.0, 1.0});
+          }
+          TLR_CHECK((run_batched<false, false>(ent, seg, d_ent, d_seg, ent_cap, seg_cap, st)));
+        }
+      }
+      // -- lines 15-19, off-diagonal: Sigma_i1j1 (-) L_i1j L_j1j^T, truncated; in batches
+      {
+        std::vector<std::pair<int, int>> pr;  // (i1, j1), j < j1 < i1, both factor tiles nonzero
+        for (int j1 = j + 1; j1 < r; j1++) {
+          if (!rk[sid(pos2blk[j1], cj)]) continue;
+          for (int i1 = j1 + 1; i1 < r; i1++)
+            if (rk[sid(pos2blk[i1], cj)]) pr.push_back({i1, j1});
+        }
+        for (size_t p0 = 0; p0 < pr.size(); p0 += tbatch) {
+          const size_t nb = std::min(tbatch, pr.size() - p0);
+          ent.clear();
+          seg.clear();
+          for (size_t t = 0; t < nb; t++) {  // X_t = V_i1j^T V_j1j (k1 x k2)
+            const size_t s1 = sid(pos2blk[pr[p0 + t].first], cj), s2 = sid(pos2blk[pr[p0 + t].second], cj);
+            seg.push_back(GemmSeg{side(s1, cj), side(s2, cj), cap, cap, mj});
+            ent.push_back(GemmEntry{Xs + t * cap * cap, rk[s2], rk[s1], rk[s2], (int)t, (int)t + 1, 1.0, 0.0});
+          }
+          TLR_CHECK((run_batched<true, false>(ent, seg, d_ent, d_seg, ent_cap, seg_cap, st)));
+          ent.clear();
+          seg.clear();
+          for (size_t t = 0; t < nb; t++) {  // Z_t = -U_i1j X_t (mi1 x k2)
+            const int ci1 = pos2blk[pr[p0 + t].first];
+            const size_t s1 = sid(ci1, cj), s2 = sid(pos2blk[pr[p0 + t].second], cj);
+            seg.push_back(GemmSeg{side(s1, ci1), Xs + t * cap * cap, cap, rk[s2], rk[s1]});
+            ent.push_back(GemmEntry{Ys + t * m * cap, cap, sizes[ci1], rk[s2], (int)t, (int)t + 1, -1.0, 0.0});
+          }
+          TLR_CHECK((run_batched<false, false>(ent, seg, d_ent, d_seg, ent_cap, seg_cap, st)));
+          ent.clear();
+          seg.clear();
+          std::vector<Trunc> jobs;
+          for (size_t t = 0; t < nb; t++) {  // D_t = U V^T + Z_t U_j1j^T (mi1 x mj1)
+            const int ci1 = pos2blk[pr[p0 + t].first], cj1 = pos2blk[pr[p0 + t].second];
+            const size_t s = sid(ci1, cj1), s2 = sid(cj1, cj);
+            const int g0 = (int)seg.size();
+            seg.push_back(GemmSeg{side(s, ci1), side(s, cj1), cap, cap, rk[s]});
+            seg.push_back(GemmSeg{Ys + t * m * cap, side(s2, cj1), cap, cap, rk[s2]});
+            ent.push_back(GemmEntry{Sij + t * m * m, m, sizes[ci1], sizes[cj1], g0, g0 + 2, 1.0, 0.0});
+            jobs.push_back(Trunc{s, ci1, sizes[ci1], sizes[cj1]});
+          }
+          TLR_CHECK((run_batched<false, true>(ent, seg, d_ent, d_seg, ent_cap, seg_cap, st)));
+          TLR_CHECK(truncate(jobs));
+        }
+      }
+    }
+    // the finished factor: L_ij in slot sid(cluster of i, cluster of j), U on i's variables
+    for (int i = 0; i < r; i++)
+      for (int j = 0; j < i; j++) {
+        const size_t s = sid(pos2blk[i], pos2blk[j]);
+        if (rk[s] && rowc[s] != pos2blk[i]) return fail(TLRMVN_E_CUDA, "internal: factor tile orientation");
+        slot[(size_t)i * r + j] = (int)s;
+        rank[(size_t)i * r + j] = rk[s];
+      }
+    return TLRMVN_OK;
+  };
+
+  if (tlr) {
+    TLR_CHECK(tlr_schur_loop());
+  } else {
+    for (int j = 0; j < r; j++) {
+      // -- choose the block of position j and its within-block order
+      bool permute = false;
+      int chosen = 0;
+      if (o.reorder == TLRMVN_REORDER_ITERATIVE) {
+        std::vector<int> bl(pos2blk.begin() + j, pos2blk.end());
+        TLR_CHECK(upload(d_blist, bl, st));
+        k_uc<<<(unsigned)bl.size(), uc_threads, uc_smem, st>>>(d_blist, diagS, d_bsize, m, d_a, d_b, work, d_logp, 1,
+                                                               d_order, d_y, d_status);
+        TLR_CUDA(cudaGetLastError());
+        TLR_CHECK(check_status(d_status, st, "iterative block reordering"));
+        std::vector<double> p(bl.size());
+        TLR_CUDA(cudaMemcpyAsync(p.data(), d_logp, p.size() * 8, cudaMemcpyDeviceToHost, st));
+        TLR_CUDA(cudaStreamSynchronize(st));
+        int best = 0;
+        for (size_t l = 1; l < p.size(); l++)
+          if (p[l] < p[best]) best = (int)l;
+        const int jt = j + best;
+        chosen = best;
+        if (jt != j) {
+          std::swap(pos2blk[j], pos2blk[jt]);
+          for (int k = 0; k < j; k++) {
+            std::swap(slot[(size_t)j * r + k], slot[(size_t)jt * r + k]);
+            std::swap(rank[(size_t)j * r + k], rank[(size_t)jt * r + k]);
+          }
+        }
+        permute = true;
+      }
+      const int bj = pos2blk[j];
+      const int mj = sizes[bj];
+      double* Sjj = diagS + (size_t)bj * m * m;
+      const double* yj = d_y + (size_t)chosen * m;
+      if (permute) {
+        std::vector<double*> ur;
+        for (int k = 0; k < j; k++)
+          if (rank[(size_t)j * r + k] > 0) ur.push_back(Uslot(slot[(size_t)j * r + k]));
+        TLR_CHECK(upload(d_urows, ur, st));
+        k_permute_block<<<1, 512, 0, st>>>(Sjj, ptmp, d_idx + (size_t)bj * m, d_a + (size_t)bj * m, d_b + (size_t)bj * m,
+                                           d_order + (size_t)chosen * m, mj, m, d_urows, (int)ur.size(), cap);
         TLR_CUDA(cudaGetLastError());
         TLR_CUDA(cudaStreamSynchronize(st));
       }
-    }
-    // -- diagonal Schur blocks: S_ii -= U_ij (V_ij^T V_ij) U_ij^T
-    {
-      std::vector<int> qs;
-      size_t xo = 0, yo = 0;
-      std::vector<size_t> xof, yof;
-      for (int q = 0; q < nrem; q++) {
-        int k = rank[(size_t)(j + 1 + q) * r + j];
-        if (!k) continue;
-        qs.push_back(q);
-        xof.push_back(xo);
-        yof.push_back(yo);
-        xo += (size_t)k * k;
-        yo += (size_t)k * m;
+      // -- L_jj and its inverse
+      k_potrf<<<1, 512, m * sizeof(double), st>>>(Sjj, mj, m, d_status);
+      TLR_CUDA(cudaGetLastError());
+      TLR_CHECK(check_status(d_status, st, "diagonal Cholesky"));
+      k_trinv<<<1, 512, 0, st>>>(Sjj, Linv, mj, m);
+      const int nrem = r - 1 - j;
+      if (nrem == 0) break;
+      // -- Sigma_ij for the remaining blocks
+      {
+        std::vector<TileJob> tj(nrem);
+        for (int q = 0; q < nrem; q++) {
+          int bi = pos2blk[j + 1 + q];
+          tj[q] = TileJob{Sij + (size_t)q * m * m, d_idx + (size_t)bi * m, d_idx + (size_t)bj * m, sizes[bi], mj};
+        }
+        TLR_CHECK(upload(d_tj, tj, st));
+        k_cov_tiles<<<dim3(std::max(1, (m * m + 255) / 256 / 4), nrem), 256, 0, st>>>(d_tj, src, m);
+        TLR_CUDA(cudaGetLastError());
+        TLR_CUDA(cudaStreamSynchronize(st));
       }
-      if (!qs.empty()) {
-        ent.clear();
-        seg.clear();
-        for (size_t t = 0; t < qs.size(); t++) {
-          int i = j + 1 + qs[t], k = rank[(size_t)i * r + j], s = slot[(size_t)i * r + j];
-          seg.push_back(GemmSeg{Vslot(s), Vslot(s), cap, cap, mj});
-          ent.push_back(GemmEntry{Xs + xof[t], k, k, k, (int)t, (int)t + 1, 1.0, 0.0});
+      // -- left-looking update S_ij -= sum_k U_ik (V_ik^T V_jk) U_jk^T
+      {
+        struct P {
+          int q, k;
+          size_t xo, yo;
+        };
+        std::vector<P> pairs;
+        size_t xo = 0, yo = 0;
+        for (int q = 0; q < nrem; q++) {
+          int i = j + 1 + q;
+          for (int k = 0; k < j; k++) {
+            int kik = rank[(size_t)i * r + k], kjk = rank[(size_t)j * r + k];
+            if (!kik || !kjk) continue;
+            pairs.push_back(P{q, k, xo, yo});
+            xo += (size_t)kik * kjk;
+            yo += (size_t)kik * m;
+          }
         }
-        TLR_CHECK((run_batched<true, false>(ent, seg, d_ent, d_seg, ent_cap, seg_cap, st)));
-        ent.clear();
-        seg.clear();
-        for (size_t t = 0; t < qs.size(); t++) {
-          int i = j + 1 + qs[t], k = rank[(size_t)i * r + j], s = slot[(size_t)i * r + j];
-          int mi = sizes[pos2blk[i]];
-          seg.push_back(GemmSeg{Xs + xof[t], Uslot(s), k, cap, k});
-          ent.push_back(GemmEntry{Ys + yof[t], m, k, mi, (int)t, (int)t + 1, 1.0, 0.0});
+        if (!pairs.empty()) {
+          if (xo > max_pairs_step * cap * cap || yo > max_pairs_step * cap * m)
+            return fail(TLRMVN_E_CUDA, "internal: left-looking scratch overflow");
+          ent.clear();
+          seg.clear();
+          for (auto& pr : pairs) {  // X_ik = V_ik^T V_jk
+            int i = j + 1 + pr.q;
+            int kik = rank[(size_t)i * r + pr.k], kjk = rank[(size_t)j * r + pr.k];
+            int mk = sizes[pos2blk[pr.k]];
+            seg.push_back(GemmSeg{Vslot(slot[(size_t)i * r + pr.k]), Vslot(slot[(size_t)j * r + pr.k]), cap, cap, mk});
+            ent.push_back(GemmEntry{Xs + pr.xo, kjk, kik, kjk, (int)seg.size() - 1, (int)seg.size(), 1.0, 0.0});
+          }
+          TLR_CHECK((run_batched<true, false>(ent, seg, d_ent, d_seg, ent_cap, seg_cap, st)));
+          ent.clear();
+          seg.clear();
+          for (auto& pr : pairs) {  // Y_ik = X_ik U_jk^T
+            int i = j + 1 + pr.q;
+            int kik = rank[(size_t)i * r + pr.k], kjk = rank[(size_t)j * r + pr.k];
+            seg.push_back(GemmSeg{Xs + pr.xo, Uslot(slot[(size_t)j * r + pr.k]), kjk, cap, kjk});
+            ent.push_back(GemmEntry{Ys + pr.yo, m, kik, mj, (int)seg.size() - 1, (int)seg.size(), 1.0, 0.0});
+          }
+          TLR_CHECK((run_batched<false, true>(ent, seg, d_ent, d_seg, ent_cap, seg_cap, st)));
+          ent.clear();
+          seg.clear();
+          size_t p0 = 0;
+          for (int q = 0; q < nrem; q++) {  // S_ij -= sum_k U_ik Y_ik
+            int i = j + 1 + q;
+            int s0 = (int)seg.size();
+            while (p0 < pairs.size() && pairs[p0].q == q) {
+              auto& pr = pairs[p0++];
+              int kik = rank[(size_t)i * r + pr.k];
+              seg.push_back(GemmSeg{Uslot(slot[(size_t)i * r + pr.k]), Ys + pr.yo, cap, m, kik});
+            }
+            if ((int)seg.size() > s0)
+              ent.push_back(GemmEntry{Sij + (size_t)q * m * m, m, sizes[pos2blk[i]], mj, s0, (int)seg.size(), -1.0, 1.0});
+          }
+          TLR_CHECK((run_batched<false, false>(ent, seg, d_ent, d_seg, ent_cap, seg_cap, st)));
         }
-        TLR_CHECK((run_batched<false, true>(ent, seg, d_ent, d_seg, ent_cap, seg_cap, st)));
-        ent.clear();
-        seg.clear();
-        for (size_t t = 0; t < qs.size(); t++) {
-          int i = j + 1 + qs[t], k = rank[(size_t)i * r + j], s = slot[(size_t)i * r + j];
-          int bi = pos2blk[i], mi = sizes[bi];
-          seg.push_back(GemmSeg{Uslot(s), Ys + yof[t], cap, m, k});
-          ent.push_back(GemmEntry{diagS + (size_t)bi * m * m, m, mi, mi, (int)t, (int)t + 1, -1.0, 1.0});
+      }
+      // -- L_ij = S_ij L_jj^-T
+      ent.clear();
+      seg.clear();
+      for (int q = 0; q < nrem; q++) {
+        int mi = sizes[pos2blk[j + 1 + q]];
+        seg.push_back(GemmSeg{Sij + (size_t)q * m * m, Linv, m, m, mj});
+        ent.push_back(GemmEntry{Lij + (size_t)q * m * m, m, mi, mj, q, q + 1, 1.0, 0.0});
+      }
+      TLR_CHECK((run_batched<false, true>(ent, seg, d_ent, d_seg, ent_cap, seg_cap, st)));
+      // -- ACA of every L_ij into fresh slots
+      {
+        std::vector<AcaJob> aj(nrem);
+        for (int q = 0; q < nrem; q++) {
+          int i = j + 1 + q;
+          int s = next_slot++;
+          slot[(size_t)i * r + j] = s;
+          aj[q] = AcaJob{Lij + (size_t)q * m * m, Uslot(s), Vslot(s), sizes[pos2blk[i]], mj};
         }
-        TLR_CHECK((run_batched<false, false>(ent, seg, d_ent, d_seg, ent_cap, seg_cap, st)));
+        TLR_CHECK(upload(d_aj, aj, st));
+        k_aca<<<nrem, 512, 2 * m * sizeof(double), st>>>(d_aj, m, cap, o.tol, d_ranks, d_capped);
+        TLR_CUDA(cudaGetLastError());
+        std::vector<int> rk(nrem);
+        TLR_CUDA(cudaMemcpyAsync(rk.data(), d_ranks, nrem * sizeof(int), cudaMemcpyDeviceToHost, st));
+        TLR_CUDA(cudaStreamSynchronize(st));
+        for (int q = 0; q < nrem; q++) rank[(size_t)(j + 1 + q) * r + j] = rk[q];
+      }
+      // -- Algorithm 5: condition the limits of the remaining blocks
+      if (o.reorder == TLRMVN_REORDER_ITERATIVE) {
+        std::vector<CondJob> cj;
+        for (int q = 0; q < nrem; q++) {
+          int i = j + 1 + q, bi = pos2blk[i], k = rank[(size_t)i * r + j];
+          if (!k) continue;
+          int s = slot[(size_t)i * r + j];
+          cj.push_back(CondJob{Uslot(s), Vslot(s), d_a + (size_t)bi * m, d_b + (size_t)bi * m, sizes[bi], mj, k});
+        }
+        if (!cj.empty()) {
+          TLR_CHECK(upload(d_cj, cj, st));
+          k_condition<<<(unsigned)cj.size(), 256, 0, st>>>(d_cj, yj, cap);
+          TLR_CUDA(cudaGetLastError());
+          TLR_CUDA(cudaStreamSynchronize(st));
+        }
+      }
+      // -- diagonal Schur blocks: S_ii -= U_ij (V_ij^T V_ij) U_ij^T
+      {
+        std::vector<int> qs;
+        size_t xo = 0, yo = 0;
+        std::vector<size_t> xof, yof;
+        for (int q = 0; q < nrem; q++) {
+          int k = rank[(size_t)(j + 1 + q) * r + j];
+          if (!k) continue;
+          qs.push_back(q);
+          xof.push_back(xo);
+          yof.push_back(yo);
+          xo += (size_t)k * k;
+          yo += (size_t)k * m;
+        }
+        if (!qs.empty()) {
+          ent.clear();
+          seg.clear();
+          for (size_t t = 0; t < qs.size(); t++) {
+            int i = j + 1 + qs[t], k = rank[(size_t)i * r + j], s = slot[(size_t)i * r + j];
+            seg.push_back(GemmSeg{Vslot(s), Vslot(s), cap, cap, mj});
+            ent.push_back(GemmEntry{Xs + xof[t], k, k, k, (int)t, (int)t + 1, 1.0, 0.0});
+          }
+          TLR_CHECK((run_batched<true, false>(ent, seg, d_ent, d_seg, ent_cap, seg_cap, st)));
+          ent.clear();
+          seg.clear();
+          for (size_t t = 0; t < qs.size(); t++) {
+            int i = j + 1 + qs[t], k = rank[(size_t)i * r + j], s = slot[(size_t)i * r + j];
+            int mi = sizes[pos2blk[i]];
+            seg.push_back(GemmSeg{Xs + xof[t], Uslot(s), k, cap, k});
+            ent.push_back(GemmEntry{Ys + yof[t], m, k, mi, (int)t, (int)t + 1, 1.0, 0.0});
+          }
+          TLR_CHECK((run_batched<false, true>(ent, seg, d_ent, d_seg, ent_cap, seg_cap, st)));
+          ent.clear();
+          seg.clear();
+          for (size_t t = 0; t < qs.size(); t++) {
+            int i = j + 1 + qs[t], k = rank[(size_t)i * r + j], s = slot[(size_t)i * r + j];
+            int bi = pos2blk[i], mi = sizes[bi];
+            seg.push_back(GemmSeg{Uslot(s), Ys + yof[t], cap, m, k});
+            ent.push_back(GemmEntry{diagS + (size_t)bi * m * m, m, mi, mi, (int)t, (int)t + 1, -1.0, 1.0});
+          }
+          TLR_CHECK((run_batched<false, false>(ent, seg, d_ent, d_seg, ent_cap, seg_cap, st)));
+        }
       }
     }
   }
@@ -1107,6 +1382,7 @@ static int check_fopts(const tlrmvn_factor_opts* o, int64_t n, const double* a, 
   if (!(o->tol >= 0.0)) return fail(TLRMVN_E_INVAL, "tol must be >= 0");
   if (o->max_rank < 0) return fail(TLRMVN_E_INVAL, "max_rank must be >= 0");
   if (o->reorder < 0 || o->reorder > 2) return fail(TLRMVN_E_INVAL, "bad reorder mode");
+  if (o->schur != TLRMVN_SCHUR_EXACT && o->schur != TLRMVN_SCHUR_TLR) return fail(TLRMVN_E_INVAL, "bad schur mode");
   if (o->reorder != TLRMVN_REORDER_NONE) {
     if (!a || !b) return fail(TLRMVN_E_INVAL, "reordering needs limits a_ref, b_ref");
     for (int64_t i = 0; i < n; i++)

@@ -560,6 +560,16 @@ static int ensure_copies_locked(Factor& F, int precision, cudaStream_t st) {
   return TLRMVN_OK;
 }
 
+// The bounded-wait path on its own: one thread waits on an mbarrier that nothing
+// arrives at, `polls` times, and records code 6 when it gives up.
+__global__ void k_wait_selftest(int* err, uint32_t polls) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  tc::mbar_init(&bar, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  tc::mbar_wait(&bar, 0, err, 6, polls);
+}
+
 // ---- tensor maps for the tcgen05 shifts ---------------------------------------------
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -589,6 +599,13 @@ static int make_map(CUtensorMap* map, const void* base, uint64_t inner, uint64_t
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(TLRMVN_E_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
   return TLRMVN_OK;
+}
+
+// (for the batched integrand)
+int ensure_precision_copies(Factor& F, int precision, cudaStream_t st) { return ensure_copies(F, precision, st); }
+int make_tensor_map_16(CUtensorMap* map, const void* base, uint64_t inner, uint64_t outer, uint64_t pitch,
+                       uint32_t box_outer, uint32_t box_inner, bool f16) {
+  return make_map(map, base, inner, outer, pitch, box_outer, box_inner, f16);
 }
 
 // splitmix64 (S. Vigna): output number t of the generator started at `seed`.
@@ -1238,7 +1255,7 @@ extern "C" int tlrmvn_selftest_wait_timeout(int polls, void* stream) {
   int herr = 0;
   cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
   if (e == cudaSuccess) {
-    tc::k_wait_selftest<<<1, 32, 0, st>>>(err, (uint32_t)polls);
+    k_wait_selftest<<<1, 32, 0, st>>>(err, (uint32_t)polls);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);

@@ -101,70 +101,59 @@ __host__ __device__ constexpr size_t sweep_tc_smem_bytes() {
   return 1024 /*align*/ + (size_t)StcCfg::SB + STC_SUB * (sizeof(float4) + sizeof(uint64_t)) + 64;
 }
 
+// Shared-memory layout and per-CTA state of the whole-tile sweep (set up once per
+// kernel: a persistent kernel runs many tiles through the same stage, barriers
+// and TMEM columns).
+struct StcCta {
+  unsigned char* stage;  // MMA phase: [A hi][B hi][A lo][B lo]; sweep: transposed triangle, band copy
+  float4* s_abi;
+  uint64_t* s_q;
+  uint64_t* full;        // the stage's copies landed
+  uint64_t* freeb;       // the products reading the stage are done
+  uint32_t tmem;         // first of the CTA's 64 TMEM columns
+  uint32_t* phases;      // thread 0's barrier parities (bit 0: full, bit 1: freeb)
+  int* abort_flag;
+};
+
+// Where the CTA's 128 samples sit in the operand maps and the result buffers.
+struct StcPlace {
+  int wx;                // x coordinate of the CTA's first sample in the W map (samples are columns)
+  int wy;                // row added to the tile's rank rows in the W map
+  int yrow;              // row coordinate of the CTA's first sample in the y maps (samples are rows)
+  unsigned short* ysrow; // this thread's row of sample-major y (hi; lo at + d.ys_lo)
+  unsigned short* wcol;  // this thread's column of W (row k at wcol[k * p.ldw])
+};
+
+// One diagonal tile for the CTA's 128 samples: the low-rank shifts and in-tile
+// coupling on tcgen05, the float sweep of eq. 2, the projections.  act: the
+// thread's sample exists (else it shadows one and writes nothing); Ds, ks: its
+// lattice shift row and point index; rs: its MVT scale (1 for MVN).  The tile's
+// log P is added to (prod, pe, lsum).  Returns false when a bounded wait expired.
 template <int FLAGS, bool F16>
-__global__ void __launch_bounds__(STC_NS, 6)
-    k_sweep_tc(const __grid_constant__ CUtensorMap mapY, const __grid_constant__ CUtensorMap mapB,
-               const __grid_constant__ CUtensorMap mapW, const __grid_constant__ CUtensorMap mapU,
-               const __grid_constant__ CUtensorMap mapY64, const __grid_constant__ CUtensorMap mapV, SweepTcArgs p) {
+__device__ __forceinline__ bool stc_tile(const CUtensorMap* mapY, const CUtensorMap* mapB, const CUtensorMap* mapW,
+                                         const CUtensorMap* mapU, const CUtensorMap* mapY64, const CUtensorMap* mapV,
+                                         const SweepTcArgs& p, const StcCta& k, const StcPlace& pl, bool act,
+                                         const uint64_t* Ds, uint32_t ks, float rs, float& prod, float& lsum,
+                                         int& pe) {
   constexpr bool PER = FLAGS & SWEEP_PERIODIZE, ONE = FLAGS & SWEEP_ONE_SIDED;
   using Op = Op16<F16>;
   constexpr uint32_t ID_C = F16 ? StcCfg::IDESC_F16 : StcCfg::IDESC;
   constexpr uint32_t ID_S = F16 ? StcShiftCfg::IDESC_F16 : StcShiftCfg::IDESC;
   constexpr uint32_t ID_P = F16 ? StcProjCfg::IDESC_F16 : StcProjCfg::IDESC;
   constexpr uint32_t A_BYTES = StcCfg::A_BYTES, HALF = StcCfg::HALF, SB = StcCfg::SB;
-  extern __shared__ __align__(1024) unsigned char stc_smem[];
-  // (offset within the shared window, so that the accesses stay shared-memory ones)
-  unsigned char* smem = stc_smem + ((1024u - (tc::smem_u32(stc_smem) & 1023u)) & 1023u);
-  unsigned char* stage = smem;                         // MMA phase: [A hi][B hi][A lo][B lo]
-  float* s_bt = reinterpret_cast<float*>(smem);        // sweep: s_bt[u * 64 + v] = B_i[q0 + v][q0 + u]
-  float* s_band = s_bt + STC_BT_FLOATS;                // sweep: s_band[v * 16 + k] = B_i[q0 + v + 1 + k][q0 + v]
-  float4* s_abi = reinterpret_cast<float4*>(smem + SB);
-  uint64_t* s_q = reinterpret_cast<uint64_t*>(s_abi + STC_SUB);
-  uint64_t* full = s_q + STC_SUB;  // the stage's copies landed
-  uint64_t* freeb = full + 1;      // the products reading the stage are done
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(freeb + 1);
-  // thread 0's barrier parities (bit 0: full, bit 1: freeb)
-  __shared__ uint32_t phases;
-  __shared__ int abort_flag;
-
+  unsigned char* stage = k.stage;
+  float* s_bt = reinterpret_cast<float*>(stage);  // sweep: s_bt[u * 64 + v] = B_i[q0 + v][q0 + u]
+  float* s_band = s_bt + STC_BT_FLOATS;           // sweep: s_band[v * 16 + k] = B_i[q0 + v + 1 + k][q0 + v]
+  float4* s_abi = k.s_abi;
+  uint64_t* s_q = k.s_q;
+  uint64_t* full = k.full;
+  uint64_t* freeb = k.freeb;
+  volatile int* abort_flag = k.abort_flag;
   const DiagArgs32& d = p.d;
   const int tid = threadIdx.x, warp = tid >> 5;
   const int mt = d.mt;
-  const int c0 = blockIdx.x * STC_NS;  // (a chunk holds fewer than 2^31 samples)
-
-  if (tid == 0) {
-    abort_flag = 0;
-    phases = 0;
-    tc::mbar_init(full, 1);
-    tc::mbar_init(freeb, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(tmem_slot)),
-                 "r"(STC_SUB)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tl = *tmem_slot + ((uint32_t)(32 * warp) << 16);  // this warp's 32 lanes
-  pdl_trigger();  // (after the allocation: a successor's CTAs never hold TMEM this grid still needs)
-  pdl_wait();  // limit shifts, y and log P of the preceding kernels
-
-  const bool act = c0 + tid < d.C;
-  const int cs = act ? c0 + tid : (int)d.C - 1;  // inactive lanes shadow a valid sample, write nothing
-  const uint64_t* Ds;
-  uint32_t ks;  // lattice point index k = 1..N (N < 2^31)
-  {
-    const int64_t g = d.sample0 + cs, sh = g / d.N;
-    ks = (uint32_t)(g - sh * d.N) + 1u;
-    Ds = d.D + sh * d.ldD + d.coord0;
-  }
-  const float rs = d.rs ? d.rs[cs] : 1.0f;
-  // log P of the tile = log(prod) + pe log 2 + lsum, prod kept in [1, 2)
-  float prod = 1.0f, lsum = 0.0f;
-  int pe = 0;
+  const uint32_t tmem = k.tmem;
+  const uint32_t tl = tmem + ((uint32_t)(32 * warp) << 16);  // this warp's 32 lanes
 
   for (int q0 = 0; q0 < mt; q0 += STC_SUB) {
     const int mq = min(STC_SUB, mt - q0);
@@ -182,21 +171,21 @@ __global__ void __launch_bounds__(STC_NS, 6)
       const uint64_t dal = tc::sdesc<STC_KB>(sa + HALF), dbl = tc::sdesc<STC_KB>(sa + HALF + A_BYTES);
       const uint64_t dw = tc::sdesc_mn(sa), du = tc::sdesc<64>(sa + StcShiftCfg::A_BYTES);
       const int nks = (p.kr + 63) / 64, nk = nks + q0 / STC_KB;
-      uint32_t ph = phases;
+      uint32_t ph = *k.phases;
       int bad = 0;  // 1: copies left in flight, 2: products left in flight
       for (int kb = 0; kb < nk; kb++) {
         tc::mbar_expect_tx(full, SB);
         if (kb < nks) {
-          const int y = p.krow0 + kb * 64;
-          tc::tma_load_2d(stage, &mapW, full, c0, y);
-          tc::tma_load_2d(stage + StcShiftCfg::A_BYTES / 2, &mapW, full, c0 + 64, y);
-          tc::tma_load_2d(stage + StcShiftCfg::A_BYTES, &mapU, full, kb * 64, p.urow0 + q0);
+          const int y = pl.wy + p.krow0 + kb * 64;
+          tc::tma_load_2d(stage, mapW, full, pl.wx, y);
+          tc::tma_load_2d(stage + StcShiftCfg::A_BYTES / 2, mapW, full, pl.wx + 64, y);
+          tc::tma_load_2d(stage + StcShiftCfg::A_BYTES, mapU, full, kb * 64, p.urow0 + q0);
         } else {
           const int x = (kb - nks) * STC_KB;
-          tc::tma_load_2d(stage, &mapY, full, x, c0);
-          tc::tma_load_2d(stage + A_BYTES, &mapB, full, x, p.brow0 + q0);
-          tc::tma_load_2d(stage + HALF, &mapY, full, p.alo + x, c0);
-          tc::tma_load_2d(stage + HALF + A_BYTES, &mapB, full, p.blo + x, p.brow0 + q0);
+          tc::tma_load_2d(stage, mapY, full, x, pl.yrow);
+          tc::tma_load_2d(stage + A_BYTES, mapB, full, x, p.brow0 + q0);
+          tc::tma_load_2d(stage + HALF, mapY, full, p.alo + x, pl.yrow);
+          tc::tma_load_2d(stage + HALF + A_BYTES, mapB, full, p.blo + x, p.brow0 + q0);
         }
         if (!tc::mbar_wait(full, ph & 1, p.err, 8)) {
           bad = 1;
@@ -208,15 +197,14 @@ __global__ void __launch_bounds__(STC_NS, 6)
           // per 16-deep step: MN-major W two 1 KB K groups on (+128), U rows 32 bytes on (+2)
 #pragma unroll
           for (int kk = 0; kk < 4; kk++)
-            tc::mma_f16(*tmem_slot, dw + (uint64_t)(128 * kk), du + (uint64_t)(2 * kk), ID_S,
-                         (kb > 0 || kk > 0) ? 1u : 0u);
+            tc::mma_f16(tmem, dw + (uint64_t)(128 * kk), du + (uint64_t)(2 * kk), ID_S, (kb > 0 || kk > 0) ? 1u : 0u);
         } else {
 #pragma unroll
           for (int kk = 0; kk < STC_KB / 16; kk++) {
             const uint64_t o = (uint64_t)(kk * 2);  // 32 bytes per 16-deep step, in 16-byte units
-            tc::mma_f16(*tmem_slot, dah + o, dbh + o, ID_C, (kb > 0 || kk > 0) ? 1u : 0u);
-            tc::mma_f16(*tmem_slot, dah + o, dbl + o, ID_C, 1u);
-            tc::mma_f16(*tmem_slot, dal + o, dbh + o, ID_C, 1u);
+            tc::mma_f16(tmem, dah + o, dbh + o, ID_C, (kb > 0 || kk > 0) ? 1u : 0u);
+            tc::mma_f16(tmem, dah + o, dbl + o, ID_C, 1u);
+            tc::mma_f16(tmem, dal + o, dbh + o, ID_C, 1u);
           }
         }
         tc::mma_commit(freeb);
@@ -230,14 +218,14 @@ __global__ void __launch_bounds__(STC_NS, 6)
         // wait (bounded) for the copies or products still in flight
         if (bad == 1) tc::mbar_wait(full, ph & 1, p.err, 5);
         else tc::mbar_wait(freeb, (ph >> 1) & 1, p.err, 5);
-        abort_flag = 1;
+        *abort_flag = 1;
       }
-      phases = ph;
+      *k.phases = ph;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();  // constants staged; shifts and coupling are in TMEM and the stage is free
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (*(volatile int*)&abort_flag) break;
+    if (*abort_flag) return false;
     {
       // the sub-tile's transposed triangle (rows u < mq, columns v < mq rounded up to 16) and band copy
       const int w4 = ((mq + 15) & ~15) >> 2;  // float4 per row
@@ -345,7 +333,7 @@ __global__ void __launch_bounds__(STC_NS, 6)
             : "r"(tl + (uint32_t)v0));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (act) {
-          unsigned short* row = reinterpret_cast<unsigned short*>(d.Ys) + (int64_t)cs * d.ldys + q0 + v0;
+          unsigned short* row = pl.ysrow + q0 + v0;
           uint32_t hi2[DIAG_VB / 2], lo2[DIAG_VB / 2];
 #pragma unroll
           for (int j = 0; j < DIAG_VB; j += 2) {
@@ -362,8 +350,8 @@ __global__ void __launch_bounds__(STC_NS, 6)
             dlo[0] = make_uint4(lo2[0], lo2[1], lo2[2], lo2[3]);
             dlo[1] = make_uint4(lo2[4], lo2[5], lo2[6], lo2[7]);
           } else {
-            unsigned short* rh = reinterpret_cast<unsigned short*>(row);
-            unsigned short* rl = reinterpret_cast<unsigned short*>(row + d.ys_lo);
+            unsigned short* rh = row;
+            unsigned short* rl = row + d.ys_lo;
 #pragma unroll
             for (int j = 0; j < DIAG_VB; j++)
               if (j < nb) {
@@ -383,16 +371,16 @@ __global__ void __launch_bounds__(STC_NS, 6)
   // the tile's projections for the later tiles, 64 ranks a pass through the same
   // TMEM columns: W[vmap[r]][c] = sum_v V[kcol0 + r][v] y_v[c] (y hi parts, 64-deep
   // stages of the CTA's y rows and of V rows)
-  for (int r0 = 0; r0 < p.kc && !*(volatile int*)&abort_flag; r0 += 64) {
+  for (int r0 = 0; r0 < p.kc; r0 += 64) {
     if (tid == 0) {
       const uint32_t sa = tc::smem_u32(stage);
       const uint64_t da = tc::sdesc<64>(sa), db = tc::sdesc<64>(sa + StcProjCfg::A_BYTES);
-      uint32_t ph = phases;
+      uint32_t ph = *k.phases;
       int bad = 0;
       for (int kb = 0; kb < (mt + 63) / 64; kb++) {
         tc::mbar_expect_tx(full, SB);
-        tc::tma_load_2d(stage, &mapY64, full, kb * 64, c0);
-        tc::tma_load_2d(stage + StcProjCfg::A_BYTES, &mapV, full, kb * 64, p.kcol0 + r0);
+        tc::tma_load_2d(stage, mapY64, full, kb * 64, pl.yrow);
+        tc::tma_load_2d(stage + StcProjCfg::A_BYTES, mapV, full, kb * 64, p.kcol0 + r0);
         if (!tc::mbar_wait(full, ph & 1, p.err, 8)) {
           bad = 1;
           break;
@@ -401,8 +389,7 @@ __global__ void __launch_bounds__(STC_NS, 6)
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
         for (int kk = 0; kk < 4; kk++)
-          tc::mma_f16(*tmem_slot, da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), ID_P,
-                       (kb > 0 || kk > 0) ? 1u : 0u);
+          tc::mma_f16(tmem, da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), ID_P, (kb > 0 || kk > 0) ? 1u : 0u);
         tc::mma_commit(freeb);
         if (!tc::mbar_wait(freeb, (ph >> 1) & 1, p.err, 9)) {
           bad = 2;
@@ -413,14 +400,14 @@ __global__ void __launch_bounds__(STC_NS, 6)
       if (bad) {
         if (bad == 1) tc::mbar_wait(full, ph & 1, p.err, 5);
         else tc::mbar_wait(freeb, (ph >> 1) & 1, p.err, 5);
-        abort_flag = 1;
+        *abort_flag = 1;
       }
-      phases = ph;
+      *k.phases = ph;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (*(volatile int*)&abort_flag) break;
+    if (*abort_flag) return false;
 #pragma unroll 1
     for (int h = 0; h < 64; h += 16) {
       uint32_t r[16];
@@ -435,25 +422,104 @@ __global__ void __launch_bounds__(STC_NS, 6)
 #pragma unroll
         for (int j = 0; j < 16; j++)
           if (r0 + h + j < p.kc)
-            p.W[(int64_t)p.vmap[r0 + h + j] * p.ldw + cs] =
+            pl.wcol[(int64_t)p.vmap[r0 + h + j] * p.ldw] =
                 Op::one(F16 ? __uint_as_float(r[j]) * p.wscale[r0 + h + j] : __uint_as_float(r[j]));
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();  // the TMEM columns and the stage free for the next pass
   }
-  if (!*(volatile int*)&abort_flag && act) {
+  return true;
+}
+
+// The CTA's stage, constants, barriers and TMEM columns (dynamic shared memory of
+// sweep_tc_smem_bytes()); the barriers initialised and the columns allocated.
+// Ends with every thread past the allocation.
+__device__ __forceinline__ StcCta stc_cta_setup(unsigned char* smem_raw, uint32_t* phases, int* abort_flag) {
+  // (offset within the shared window, so that the accesses stay shared-memory ones)
+  unsigned char* smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
+  StcCta k;
+  k.stage = smem;
+  k.s_abi = reinterpret_cast<float4*>(smem + StcCfg::SB);
+  k.s_q = reinterpret_cast<uint64_t*>(k.s_abi + STC_SUB);
+  k.full = k.s_q + STC_SUB;
+  k.freeb = k.full + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(k.freeb + 1);
+  k.phases = phases;
+  k.abort_flag = abort_flag;
+  if (threadIdx.x == 0) {
+    *abort_flag = 0;
+    *phases = 0;
+    tc::mbar_init(k.full, 1);
+    tc::mbar_init(k.freeb, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if ((threadIdx.x >> 5) == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(tmem_slot)),
+                 "r"(STC_SUB)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  k.tmem = *tmem_slot;
+  return k;
+}
+
+// Frees the CTA's TMEM columns once every thread is done with them.
+__device__ __forceinline__ void stc_cta_release(const StcCta& k) {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if ((threadIdx.x >> 5) == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(k.tmem), "r"(STC_SUB) : "memory");
+}
+
+// One launch per diagonal tile of one problem: CTA x owns samples [128 x, 128 x + 128) of the chunk.
+template <int FLAGS, bool F16>
+__global__ void __launch_bounds__(STC_NS, 6)
+    k_sweep_tc(const __grid_constant__ CUtensorMap mapY, const __grid_constant__ CUtensorMap mapB,
+               const __grid_constant__ CUtensorMap mapW, const __grid_constant__ CUtensorMap mapU,
+               const __grid_constant__ CUtensorMap mapY64, const __grid_constant__ CUtensorMap mapV, SweepTcArgs p) {
+  extern __shared__ __align__(1024) unsigned char stc_smem[];
+  __shared__ uint32_t phases;
+  __shared__ int abort_flag;
+  const StcCta k = stc_cta_setup(stc_smem, &phases, &abort_flag);
+  pdl_trigger();  // (after the allocation: a successor's CTAs never hold TMEM this grid still needs)
+  pdl_wait();  // limit shifts, y and log P of the preceding kernels
+
+  const DiagArgs32& d = p.d;
+  const int tid = threadIdx.x;
+  const int c0 = blockIdx.x * STC_NS;  // (a chunk holds fewer than 2^31 samples)
+  const bool act = c0 + tid < d.C;
+  const int cs = act ? c0 + tid : (int)d.C - 1;  // inactive lanes shadow a valid sample, write nothing
+  const uint64_t* Ds;
+  uint32_t ks;  // lattice point index k = 1..N (N < 2^31)
+  {
+    const int64_t g = d.sample0 + cs, sh = g / d.N;
+    ks = (uint32_t)(g - sh * d.N) + 1u;
+    Ds = d.D + sh * d.ldD + d.coord0;
+  }
+  const float rs = d.rs ? d.rs[cs] : 1.0f;
+  // log P of the tile = log(prod) + pe log 2 + lsum, prod kept in [1, 2)
+  float prod = 1.0f, lsum = 0.0f;
+  int pe = 0;
+  StcPlace pl;
+  pl.wx = c0;
+  pl.wy = 0;
+  pl.yrow = c0;
+  pl.ysrow = reinterpret_cast<unsigned short*>(d.Ys) + (int64_t)cs * d.ldys;
+  pl.wcol = p.W + cs;
+  const bool ok = stc_tile<FLAGS, F16>(&mapY, &mapB, &mapW, &mapU, &mapY64, &mapV, p, k, pl, act, Ds, ks, rs, prod,
+                                       lsum, pe);
+  if (ok && act) {
     const double lp = (double)(logf(prod) + lsum) + (double)pe * 0.69314718055994530942;
     const int64_t g = d.sample0 + cs;
     if (d.first) d.logP[g] = lp;
     else d.logP[g] += lp;
   }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tmem_slot), "r"(STC_SUB) : "memory");
-  }
+  stc_cta_release(k);
 }
 
 }  // namespace tlrmvn

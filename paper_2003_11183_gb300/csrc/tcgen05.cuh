@@ -121,15 +121,5 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
-// The bounded-wait path on its own: one thread waits on an mbarrier that nothing
-// arrives at, `polls` times, and records code 6 when it gives up.
-__global__ void k_wait_selftest(int* err, uint32_t polls) {
-  __shared__ __align__(8) uint64_t bar;
-  if (threadIdx.x != 0) return;
-  mbar_init(&bar, 1);
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  mbar_wait(&bar, 0, err, 6, polls);
-}
-
 }  // namespace tc
 }  // namespace tlrmvn

@@ -71,6 +71,10 @@ def test_bad_arguments_rejected_without_gpu(lib):
     assert lib.tlrmvn_factor_kernel(xy.ctypes.data_as(_lib.c_double_p), 4, 0, p.ctypes.data_as(_lib.c_double_p),
                                     0.0, a.ctypes.data_as(_lib.c_double_p), b.ctypes.data_as(_lib.c_double_p),
                                     C.byref(o), C.byref(out)) == api.E_INVAL
+    o = _lib.FactorOpts(2, 1e-8, 0, 0, None, 0, 7)  # unknown Schur arithmetic
+    assert lib.tlrmvn_factor_kernel(xy.ctypes.data_as(_lib.c_double_p), 4, 0, p.ctypes.data_as(_lib.c_double_p),
+                                    0.0, None, None, C.byref(o), C.byref(out)) == api.E_INVAL
+    assert b"schur" in lib.tlrmvn_last_error()
     assert lib.tlrmvn_prob(None, None, None, math.inf, None, None, None, None, None) == api.E_INVAL
     assert lib.tlrmvn_factor_import(b"garbage!" * 8, 64, C.byref(out)) == api.E_FORMAT
     assert b"magic" in lib.tlrmvn_last_error()

@@ -457,6 +457,27 @@ uint64_t splitmix64_seed_at(uint64_t seed, uint64_t t);  // prob.cu
 
 static size_t batch_smem() { return (size_t)BATCH_MMAX * (BATCH_T + 1) * sizeof(float); }
 
+// CTAs of `threads` threads and `dyn_smem` dynamic shared memory that one SM holds at
+// once, from the kernel's registers and static shared memory and the device's limits.
+static int resident_ctas(const void* kernel, int threads, size_t dyn_smem, int dev, int* out) {
+  cudaFuncAttributes fa;
+  TLR_CUDA(cudaFuncGetAttributes(&fa, kernel));
+  int regs_sm = 0, smem_sm = 0, res_blk = 0, thr_sm = 0, blk_sm = 0;
+  TLR_CUDA(cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev));
+  TLR_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+  TLR_CUDA(cudaDeviceGetAttribute(&res_blk, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+  TLR_CUDA(cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev));
+  TLR_CUDA(cudaDeviceGetAttribute(&blk_sm, cudaDevAttrMaxBlocksPerMultiprocessor, dev));
+  const int warps = (threads + 31) / 32;
+  const int regs_warp = (fa.numRegs * 32 + 255) / 256 * 256;  // (allocated per warp in units of 256)
+  int n = std::min(thr_sm / threads, blk_sm);
+  if (regs_warp > 0) n = std::min(n, regs_sm / (regs_warp * warps));
+  const size_t smem = (dyn_smem + fa.sharedSizeBytes + 127) / 128 * 128 + (size_t)res_blk;
+  n = std::min<int>(n, (int)((size_t)smem_sm / smem));
+  *out = std::max(n, 1);
+  return TLRMVN_OK;
+}
+
 // Captures the plan's launch sequence (permute limits -> persistent integrand
 // with `per_sm` CTAs per SM -> estimator) into a CUDA graph, replacing any
 // earlier one.
@@ -587,8 +608,12 @@ static int batch_build(Batch& B, int count, const tlrmvn_factor_t* factors, cons
   TLR_CUDA(cudaDeviceGetAttribute(&B.sms, cudaDevAttrMultiProcessorCount, B.device));
   if (B.tc) {
     const void* kt = batch_tc_kernel(B.periodize);
-    TLR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&B.per_sm_max, kt, STC_NS, sweep_tc_smem_bytes()));
-    // resident CTAs hold their 64 TMEM columns until the end: at most 512 / 64 per SM
+    TLR_CUDA(cudaFuncSetAttribute(kt, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  (int)cudaSharedmemCarveoutMaxShared));
+    // resident CTAs from the kernel's registers and shared memory (the occupancy query
+    // reported one CTA per SM for this kernel where the launches fit six), and at most
+    // 512 / 64 per SM: each holds its 64 TMEM columns until the end
+    TLR_CHECK(resident_ctas(kt, STC_NS, sweep_tc_smem_bytes(), B.device, &B.per_sm_max));
     B.per_sm_max = std::min(B.per_sm_max, 512 / STC_SUB);
   } else {
     const size_t smem = batch_smem();

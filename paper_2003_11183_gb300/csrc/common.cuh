@@ -60,7 +60,8 @@ void dfree(T*& p) {
 //   threads  threads per block of the float32 sweep (0: the occupancy rule)
 //   chunk    samples in flight per pass (0: as many as the memory rule allows)
 //   tc_ctas  whole-tile sweeps (BF16-/FP16-shift paths) sharing an SM: 6 (all that
-//            fit), or fewer by reserving shared memory
+//            fit: 80 registers, 28 KB of shared memory and 64 TMEM columns each), or
+//            fewer by reserving shared memory
 struct Tuning {
   int sub = 64;
   int threads = 0;

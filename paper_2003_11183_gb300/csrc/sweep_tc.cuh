@@ -477,6 +477,7 @@ __device__ __forceinline__ void stc_cta_release(const StcCta& k) {
 }
 
 // One launch per diagonal tile of one problem: CTA x owns samples [128 x, 128 x + 128) of the chunk.
+// (Six CTAs per SM, 80 registers each: the 72 that seven would allow measured 17% slower.)
 template <int FLAGS, bool F16>
 __global__ void __launch_bounds__(STC_NS, 6)
     k_sweep_tc(const __grid_constant__ CUtensorMap mapY, const __grid_constant__ CUtensorMap mapB,

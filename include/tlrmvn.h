@@ -235,7 +235,8 @@ int tlrmvn_set_tuning(tlrmvn_factor_t f, int precision, const tlrmvn_tuning* t);
 
 /* ---- many problems in one launch -------------------------------------- */
 
-/* A batch plan: `count` problems (each its own factor, tile size <= 128, and
+/* A batch plan: `count` problems (each its own factor, tile size <= 128 for
+ * TLRMVN_FP32, any for TLRMVN_BF16_SHIFT, and
  * its own nu; INFINITY for MVN) solved together by one persistent kernel whose
  * blocks take (problem, 128-sample chunk) work items from a device counter,
  * largest problems first; each item runs Algorithm 6/7 for its chunk over all

@@ -185,7 +185,6 @@ __global__ void __launch_bounds__(BATCH_T) k_batch(const BatchProblem* __restric
 }
 
 // ---- tensor-core batched integrand (BF16-shift precision) ----------------------------------
-constexpr int BATCH_TC_MY = 128;  // y columns of the hi halves in the CTA-private y rows (lo at + 128)
 constexpr int BATCH_TC_MAPS = 3;  // per problem: split B (32-deep boxes), U rows, V rows (64 x 64 boxes)
 
 struct BatchTcProblem {
@@ -211,7 +210,7 @@ __global__ void __launch_bounds__(STC_NS, 6)
     k_batch_tc(const BatchTcProblem* __restrict__ probs, const CUtensorMap* __restrict__ pmaps,
                const BatchItem* __restrict__ items, int n_items, int* next, const __grid_constant__ CUtensorMap mapW,
                const __grid_constant__ CUtensorMap mapY, const __grid_constant__ CUtensorMap mapY64,
-               unsigned short* Wbase, int64_t kwmax, unsigned short* Ybase, double* logP, int* err) {
+               unsigned short* Wbase, int64_t kwmax, unsigned short* Ybase, int my, double* logP, int* err) {
   constexpr bool PER = FLAGS & SWEEP_PERIODIZE;
   extern __shared__ __align__(1024) unsigned char stc_smem[];
   __shared__ uint32_t phases;
@@ -223,7 +222,7 @@ __global__ void __launch_bounds__(STC_NS, 6)
   pl.wx = 0;
   pl.wy = (int)(blockIdx.x * kwmax);
   pl.yrow = blockIdx.x * STC_NS;
-  pl.ysrow = Ybase + ((int64_t)blockIdx.x * STC_NS + tid) * (2 * BATCH_TC_MY);
+  pl.ysrow = Ybase + ((int64_t)blockIdx.x * STC_NS + tid) * (2 * my);  // (hi at 0, lo at my)
   pl.wcol = Wbase + (int64_t)blockIdx.x * kwmax * STC_NS + tid;
   for (;;) {
     __syncthreads();  // every thread is done with the previous item
@@ -261,9 +260,9 @@ __global__ void __launch_bounds__(STC_NS, 6)
       d.b = P.b + t0;
       d.Q = P.Q;
       d.coord0 = t0;
-      d.ys_lo = BATCH_TC_MY;
+      d.ys_lo = my;
       p.brow0 = i * P.m;
-      p.alo = BATCH_TC_MY;
+      p.alo = my;
       p.blo = P.my;
       p.urow0 = i * P.m;
       p.krow0 = (int)P.kpad_off[i];
@@ -414,6 +413,7 @@ struct Batch {
   // tensor-core kernel (TLRMVN_BF16_SHIFT)
   bool tc = false;
   int64_t kwmax = 0;          // W rows of one CTA's region (the largest padded rank space)
+  int my = 64;                // y hi columns of one sample's row in the CTA-private y (lo at + my)
   BatchTcProblem* dtprobs = nullptr;
   CUtensorMap* dmaps = nullptr;
   unsigned short *W16 = nullptr, *Y16 = nullptr;
@@ -493,12 +493,12 @@ static int batch_capture(Batch& B, int per_sm) {
   if (B.tc) {
     if (B.periodize)
       k_batch_tc<SWEEP_PERIODIZE><<<grid, STC_NS, sweep_tc_smem_bytes(), st>>>(
-          B.dtprobs, B.dmaps, B.ditems, B.n_items, B.dnext, B.mapW, B.mapY, B.mapY64, B.W16, B.kwmax, B.Y16, B.logP,
-          B.derr);
+          B.dtprobs, B.dmaps, B.ditems, B.n_items, B.dnext, B.mapW, B.mapY, B.mapY64, B.W16, B.kwmax, B.Y16, B.my,
+          B.logP, B.derr);
     else
       k_batch_tc<0><<<grid, STC_NS, sweep_tc_smem_bytes(), st>>>(B.dtprobs, B.dmaps, B.ditems, B.n_items, B.dnext,
                                                                  B.mapW, B.mapY, B.mapY64, B.W16, B.kwmax, B.Y16,
-                                                                 B.logP, B.derr);
+                                                                 B.my, B.logP, B.derr);
   } else {
     k_batch<<<grid, BATCH_T, batch_smem(), st>>>(B.dprobs, B.ditems, B.n_items, B.dnext, B.W,
                                                 std::max<int64_t>(B.ktot_max, 1) * BATCH_T, B.logP);
@@ -534,13 +534,16 @@ static int batch_build(Batch& B, int count, const tlrmvn_factor_t* factors, cons
   for (int p = 0; p < count; p++) {
     Factor* F = reinterpret_cast<Factor*>(factors[p]);
     if (!F) return fail(TLRMVN_E_INVAL, "null factor in batch");
-    if (F->m > BATCH_MMAX) return fail(TLRMVN_E_NOTSUP, "batched problems need tile size <= 128");
+    if (!B.tc && F->m > BATCH_MMAX) return fail(TLRMVN_E_NOTSUP, "FP32 batched problems need tile size <= 128");
     if (!(nu[p] > 0.0)) return fail(TLRMVN_E_INVAL, "nu must be > 0");
     B.F[p] = F;
     B.n_off[p + 1] = B.n_off[p] + F->n;
     B.ktot_max = std::max(B.ktot_max, F->ktot);
     TLR_CHECK(make_batch_copies(*F, B.copies[p], B.tc, st));
-    if (B.tc) B.kwmax = std::max(B.kwmax, F->kw16);
+    if (B.tc) {
+      B.kwmax = std::max(B.kwmax, F->kw16);
+      B.my = std::max<int>(B.my, (int)F->my16);
+    }
   }
   B.total_n = B.n_off[count];
   const int64_t S = (int64_t)B.M * B.N;
@@ -629,7 +632,7 @@ static int batch_build(Batch& B, int count, const tlrmvn_factor_t* factors, cons
     B.kwmax = std::max<int64_t>(B.kwmax, 64);
     if ((int64_t)B.grid_max * B.kwmax >= ((int64_t)1 << 31))
       return fail(TLRMVN_E_NOTSUP, "batched projections exceed the tensor map's coordinate range");
-    const size_t nw = (size_t)B.grid_max * B.kwmax * STC_NS, ny = (size_t)B.grid_max * STC_NS * 2 * BATCH_TC_MY;
+    const size_t nw = (size_t)B.grid_max * B.kwmax * STC_NS, ny = (size_t)B.grid_max * STC_NS * 2 * B.my;
     TLR_CHECK(dalloc(&B.W16, nw));
     TLR_CHECK(dalloc(&B.Y16, ny));
     TLR_CHECK(dalloc(&B.derr, 1));
@@ -637,10 +640,10 @@ static int batch_build(Batch& B, int count, const tlrmvn_factor_t* factors, cons
     TLR_CUDA(cudaMemsetAsync(B.Y16, 0, ny * 2, st));
     TLR_CUDA(cudaMemsetAsync(B.derr, 0, sizeof(int), st));
     TLR_CHECK(make_tensor_map_16(&B.mapW, B.W16, STC_NS, (uint64_t)B.grid_max * B.kwmax, STC_NS * 2, 64, 64, false));
-    TLR_CHECK(make_tensor_map_16(&B.mapY, B.Y16, 2 * BATCH_TC_MY, (uint64_t)B.grid_max * STC_NS, 2 * BATCH_TC_MY * 2,
+    TLR_CHECK(make_tensor_map_16(&B.mapY, B.Y16, 2 * B.my, (uint64_t)B.grid_max * STC_NS, 2 * B.my * 2,
                                  STC_NS, 32, false));
-    TLR_CHECK(make_tensor_map_16(&B.mapY64, B.Y16, 2 * BATCH_TC_MY, (uint64_t)B.grid_max * STC_NS,
-                                 2 * BATCH_TC_MY * 2, STC_NS, 64, false));
+    TLR_CHECK(make_tensor_map_16(&B.mapY64, B.Y16, 2 * B.my, (uint64_t)B.grid_max * STC_NS, 2 * B.my * 2, STC_NS,
+                                 64, false));
     // per problem: the split B, U and V maps, and its table entry
     std::vector<CUtensorMap> maps((size_t)BATCH_TC_MAPS * count);
     std::vector<BatchTcProblem> tp(count);

@@ -157,8 +157,9 @@ __device__ __forceinline__ bool stc_tile(const CUtensorMap* mapY, const CUtensor
 
   for (int q0 = 0; q0 < mt; q0 += STC_SUB) {
     const int mq = min(STC_SUB, mt - q0);
-    // every thread is past the previous sub-tile's reads of the shared copies and its TMEM accesses
-    for (int t = tid; t < mq; t += STC_NS) {
+    // every thread is past the previous sub-tile's reads of the shared copies and its TMEM accesses;
+    // threads 1..64 stage the constants while thread 0 issues the copies and products at once
+    for (int t = tid - 1; t >= 0 && t < mq; t += STC_NS - 1) {
       s_abi[t] = make_float4(d.a[q0 + t], d.b[q0 + t], d.inv[q0 + t], 0.0f);
       s_q[t] = d.Q[d.coord0 + q0 + t];
     }

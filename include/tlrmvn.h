@@ -206,7 +206,10 @@ int tlrmvn_prob_device(tlrmvn_factor_t f, const double* a, const double* b, doub
  *   threads   threads per block of the float32 sweep; 0 = the occupancy rule
  *   chunk     samples in flight per pass; 0 = as many as fit the memory rule
  *             (opts->sample_chunk, when set, still takes precedence)
- *   tc_ctas   whole-tile sweeps of the BF16-/FP16-shift paths sharing an SM (1..6)
+ *   tc_ctas   whole-tile sweeps of the BF16-/FP16-shift paths sharing an SM (1..6; with spt 2
+ *             at most 4 take effect)
+ *   spt       samples per thread of the whole-tile sweep: 1 or 2 (two independent chains
+ *             per thread, 256 samples per block)
  *   ms        tlrmvn_autotune: device milliseconds per solve of the choice (-1
  *             when it came from the cache); candidates: how many were timed */
 typedef struct {
@@ -215,6 +218,7 @@ typedef struct {
   int tc_ctas;
   double ms;
   int candidates;
+  int spt;
 } tlrmvn_tuning;
 
 /* Times each candidate launch choice for opts->precision on solves of this very

@@ -22,7 +22,7 @@ class Opts(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("sub", C.c_int), ("threads", C.c_int), ("chunk", C.c_int64), ("tc_ctas", C.c_int),
-                ("ms", C.c_double), ("candidates", C.c_int)]
+                ("ms", C.c_double), ("candidates", C.c_int), ("spt", C.c_int)]
 
 
 class ServerStats(C.Structure):

@@ -271,7 +271,7 @@ class Server:
 
 
 def _tuning_dict(t) -> dict:
-    return {"sub": t.sub, "threads": t.threads, "chunk": t.chunk, "tc_ctas": t.tc_ctas,
+    return {"sub": t.sub, "threads": t.threads, "chunk": t.chunk, "tc_ctas": t.tc_ctas, "spt": t.spt,
             "ms": t.ms, "candidates": t.candidates}
 
 
@@ -297,8 +297,9 @@ def tlrmvn_get_tuning(f: Factor, precision: int) -> dict:
     return _tuning_dict(t)
 
 
-def tlrmvn_set_tuning(f: Factor, precision: int, sub: int = 64, threads: int = 0, chunk: int = 0, tc_ctas: int = 6):
-    t = L.Tuning(int(sub), int(threads), int(chunk), int(tc_ctas), -1.0, 0)
+def tlrmvn_set_tuning(f: Factor, precision: int, sub: int = 64, threads: int = 0, chunk: int = 0, tc_ctas: int = 6,
+                      spt: int = 1):
+    t = L.Tuning(int(sub), int(threads), int(chunk), int(tc_ctas), -1.0, 0, int(spt))
     _check(L.load().tlrmvn_set_tuning(f.handle, int(precision), C.byref(t)), "tlrmvn_set_tuning")
 
 

@@ -216,14 +216,14 @@ __global__ void __launch_bounds__(STC_NS, 6)
   __shared__ uint32_t phases;
   __shared__ int abort_flag;
   __shared__ int cur;
-  const StcCta k = stc_cta_setup(stc_smem, &phases, &abort_flag);
+  const StcCta k = stc_cta_setup<1>(stc_smem, &phases, &abort_flag);
   const int tid = threadIdx.x;
   StcPlace pl;
   pl.wx = 0;
   pl.wy = (int)(blockIdx.x * kwmax);
   pl.yrow = blockIdx.x * STC_NS;
-  pl.ysrow = Ybase + ((int64_t)blockIdx.x * STC_NS + tid) * (2 * my);  // (hi at 0, lo at my)
-  pl.wcol = Wbase + (int64_t)blockIdx.x * kwmax * STC_NS + tid;
+  pl.ysrow[0] = Ybase + ((int64_t)blockIdx.x * STC_NS + tid) * (2 * my);  // (hi at 0, lo at my)
+  pl.wcol[0] = Wbase + (int64_t)blockIdx.x * kwmax * STC_NS + tid;
   for (;;) {
     __syncthreads();  // every thread is done with the previous item
     if (tid == 0) cur = atomicAdd(next, 1);
@@ -232,20 +232,20 @@ __global__ void __launch_bounds__(STC_NS, 6)
     if (it >= n_items || *(volatile int*)&abort_flag) break;
     const BatchItem item = items[it];
     const BatchTcProblem& P = probs[item.prob];
-    const bool act = tid < item.count;
-    const int64_t g = item.sample0 + (act ? tid : item.count - 1);  // inactive lanes shadow a valid sample
+    const bool act[1] = {tid < item.count};
+    const int64_t g = item.sample0 + (act[0] ? tid : item.count - 1);  // inactive lanes shadow a valid sample
     const int64_t sh = g / P.n_points;
-    const uint32_t ks = (uint32_t)(g - sh * P.n_points) + 1u;
+    const uint32_t ks[1] = {(uint32_t)(g - sh * P.n_points) + 1u};
     const uint64_t* Drow = P.D + sh * (int64_t)(P.n + 1);
-    float rs = 1.0f;
+    float rs[1] = {1.0f};
     if (isfinite(P.nu)) {
       double w, wc;
-      lattice_w((uint64_t)ks * P.Q[P.n] + Drow[P.n], PER ? 1 : 0, w, wc);
-      rs = (float)sqrt(2.0 * gamma_p_inv(0.5 * P.nu, w, wc) / P.nu);
+      lattice_w((uint64_t)ks[0] * P.Q[P.n] + Drow[P.n], PER ? 1 : 0, w, wc);
+      rs[0] = (float)sqrt(2.0 * gamma_p_inv(0.5 * P.nu, w, wc) / P.nu);
     }
     const CUtensorMap* mp = pmaps + (int64_t)BATCH_TC_MAPS * item.prob;
-    float prod = 1.0f, lsum = 0.0f;
-    int pe = 0;
+    float prod[1] = {1.0f}, lsum[1] = {0.0f};
+    int pe[1] = {0};
     bool ok = true;
     for (int i = 0; i < P.r && ok; i++) {
       const int64_t t0 = P.tile_off[i];
@@ -275,12 +275,14 @@ __global__ void __launch_bounds__(STC_NS, 6)
       p.wscale = nullptr;
       p.tscale = 1.0f;
       p.err = err;
-      ok = stc_tile<FLAGS, false>(&mapY, mp, &mapW, mp + 1, &mapY64, mp + 2, p, k, pl, act, Drow + t0, ks, rs, prod,
-                                  lsum, pe);
+      const uint64_t* const Ds[1] = {Drow + t0};
+      ok = stc_tile<FLAGS, false, 1>(&mapY, mp, &mapW, mp + 1, &mapY64, mp + 2, p, k, pl, act, Ds, ks, rs, prod,
+                                     lsum, pe);
     }
-    if (ok && act) logP[P.logp_off + g] = (double)(logf(prod) + lsum) + (double)pe * 0.69314718055994530942;
+    if (ok && act[0])
+      logP[P.logp_off + g] = (double)(logf(prod[0]) + lsum[0]) + (double)pe[0] * 0.69314718055994530942;
   }
-  stc_cta_release(k);
+  stc_cta_release<1>(k);
 }
 static const void* batch_tc_kernel(int periodize) {
   return periodize ? (const void*)k_batch_tc<SWEEP_PERIODIZE> : (const void*)k_batch_tc<0>;
@@ -492,11 +494,11 @@ static int batch_capture(Batch& B, int per_sm) {
   k_permute_batch<<<nblk(B.total_n, 256), 256, 0, st>>>(B.a_st, B.b_st, B.perm_g, B.total_n, B.a32, B.b32, B.dbad);
   if (B.tc) {
     if (B.periodize)
-      k_batch_tc<SWEEP_PERIODIZE><<<grid, STC_NS, sweep_tc_smem_bytes(), st>>>(
+      k_batch_tc<SWEEP_PERIODIZE><<<grid, STC_NS, sweep_tc_smem_bytes<1>(), st>>>(
           B.dtprobs, B.dmaps, B.ditems, B.n_items, B.dnext, B.mapW, B.mapY, B.mapY64, B.W16, B.kwmax, B.Y16, B.my,
           B.logP, B.derr);
     else
-      k_batch_tc<0><<<grid, STC_NS, sweep_tc_smem_bytes(), st>>>(B.dtprobs, B.dmaps, B.ditems, B.n_items, B.dnext,
+      k_batch_tc<0><<<grid, STC_NS, sweep_tc_smem_bytes<1>(), st>>>(B.dtprobs, B.dmaps, B.ditems, B.n_items, B.dnext,
                                                                  B.mapW, B.mapY, B.mapY64, B.W16, B.kwmax, B.Y16,
                                                                  B.my, B.logP, B.derr);
   } else {
@@ -616,7 +618,7 @@ static int batch_build(Batch& B, int count, const tlrmvn_factor_t* factors, cons
     // resident CTAs from the kernel's registers and shared memory (the occupancy query
     // reported one CTA per SM for this kernel where the launches fit six), and at most
     // 512 / 64 per SM: each holds its 64 TMEM columns until the end
-    TLR_CHECK(resident_ctas(kt, STC_NS, sweep_tc_smem_bytes(), B.device, &B.per_sm_max));
+    TLR_CHECK(resident_ctas(kt, STC_NS, sweep_tc_smem_bytes<1>(), B.device, &B.per_sm_max));
     B.per_sm_max = std::min(B.per_sm_max, 512 / STC_SUB);
   } else {
     const size_t smem = batch_smem();

@@ -62,11 +62,14 @@ void dfree(T*& p) {
 //   tc_ctas  whole-tile sweeps (BF16-/FP16-shift paths) sharing an SM: 6 (all that
 //            fit: 80 registers, 28 KB of shared memory and 64 TMEM columns each), or
 //            fewer by reserving shared memory
+//   spt      samples per thread of the whole-tile sweep: 1, or 2 (256 samples per
+//            CTA, two independent chains per thread, 128 TMEM columns, four CTAs per SM)
 struct Tuning {
   int sub = 64;
   int threads = 0;
   int64_t chunk = 0;
   int tc_ctas = 6;
+  int spt = 1;
 };
 
 // ---- factor handle -----------------------------------------------------------

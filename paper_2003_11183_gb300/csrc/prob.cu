@@ -760,18 +760,27 @@ static SweepShape sweep_shape(int64_t C, int mt, int forced) {
 // one-sided) flags and operand type.
 typedef void (*SweepTcKernel)(const CUtensorMap, const CUtensorMap, const CUtensorMap, const CUtensorMap,
                               const CUtensorMap, const CUtensorMap, SweepTcArgs);
-static SweepTcKernel sweep_tc_kernel(int flags, bool f16) {
-  static const SweepTcKernel table[8] = {
-      k_sweep_tc<0, false>, k_sweep_tc<SWEEP_PERIODIZE, false>, k_sweep_tc<SWEEP_ONE_SIDED, false>,
-      k_sweep_tc<SWEEP_PERIODIZE | SWEEP_ONE_SIDED, false>, k_sweep_tc<0, true>, k_sweep_tc<SWEEP_PERIODIZE, true>,
-      k_sweep_tc<SWEEP_ONE_SIDED, true>, k_sweep_tc<SWEEP_PERIODIZE | SWEEP_ONE_SIDED, true>};
-  return table[((flags & SWEEP_PERIODIZE) ? 1 : 0) | ((flags & SWEEP_ONE_SIDED) ? 2 : 0) | (f16 ? 4 : 0)];
+static SweepTcKernel sweep_tc_kernel(int flags, bool f16, int spt) {
+  static const SweepTcKernel table[16] = {
+      k_sweep_tc<0, false, 1>, k_sweep_tc<SWEEP_PERIODIZE, false, 1>, k_sweep_tc<SWEEP_ONE_SIDED, false, 1>,
+      k_sweep_tc<SWEEP_PERIODIZE | SWEEP_ONE_SIDED, false, 1>, k_sweep_tc<0, true, 1>,
+      k_sweep_tc<SWEEP_PERIODIZE, true, 1>, k_sweep_tc<SWEEP_ONE_SIDED, true, 1>,
+      k_sweep_tc<SWEEP_PERIODIZE | SWEEP_ONE_SIDED, true, 1>, k_sweep_tc<0, false, 2>,
+      k_sweep_tc<SWEEP_PERIODIZE, false, 2>, k_sweep_tc<SWEEP_ONE_SIDED, false, 2>,
+      k_sweep_tc<SWEEP_PERIODIZE | SWEEP_ONE_SIDED, false, 2>, k_sweep_tc<0, true, 2>,
+      k_sweep_tc<SWEEP_PERIODIZE, true, 2>, k_sweep_tc<SWEEP_ONE_SIDED, true, 2>,
+      k_sweep_tc<SWEEP_PERIODIZE | SWEEP_ONE_SIDED, true, 2>};
+  return table[((flags & SWEEP_PERIODIZE) ? 1 : 0) | ((flags & SWEEP_ONE_SIDED) ? 2 : 0) | (f16 ? 4 : 0) |
+               (spt == 2 ? 8 : 0)];
 }
-// Dynamic shared memory of a whole-tile sweep launch with `ctas` CTAs per SM:
-// the kernel's own need, or more so that no more than `ctas` fit (tuning).
-static size_t sweep_tc_launch_smem(int ctas) {
-  size_t need = sweep_tc_smem_bytes();
-  if (ctas >= 1 && ctas < 6) {
+// Dynamic shared memory of a whole-tile sweep launch with `ctas` CTAs per SM: the
+// kernel's own need, or more so that no more than `ctas` fit (tuning; with two
+// samples per thread at most four fit by TMEM, so the shared memory keeps it there).
+static size_t sweep_tc_launch_smem(int ctas, int spt) {
+  size_t need = spt == 2 ? sweep_tc_smem_bytes<2>() : sweep_tc_smem_bytes<1>();
+  const int cap_ctas = spt == 2 ? 4 : 6;
+  ctas = std::min(std::max(ctas, 1), cap_ctas);
+  if (ctas < cap_ctas || spt == 2) {
     int dev = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
@@ -784,11 +793,12 @@ static size_t sweep_tc_launch_smem(int ctas) {
 static int set_sweep_smem(int sub) {
   for (int flags = 0; flags < 8; flags++)
     TLR_CHECK(raise_smem_limit((const void*)sweep_kernel(flags), sweep_smem_bytes(sub, 256)));
-  for (int t = 0; t < 8; t++)  // every (periodisation, one-sided, operand type) variant
-    TLR_CHECK(raise_smem_limit((const void*)sweep_tc_kernel(((t & 1) ? SWEEP_PERIODIZE : 0) |
-                                                                ((t & 2) ? SWEEP_ONE_SIDED : 0),
-                                                            (t & 4) != 0),
-                               sweep_tc_launch_smem(1)));
+  for (int t = 0; t < 16; t++) {  // every (periodisation, one-sided, operand type, samples per thread) variant
+    const int spt = (t & 8) ? 2 : 1;
+    const void* kf = (const void*)sweep_tc_kernel(((t & 1) ? SWEEP_PERIODIZE : 0) | ((t & 2) ? SWEEP_ONE_SIDED : 0),
+                                                  (t & 4) != 0, spt);
+    TLR_CHECK(raise_smem_limit(kf, sweep_tc_launch_smem(1, spt)));
+  }
   return TLRMVN_OK;
 }
 
@@ -856,8 +866,9 @@ static void sweep_tile_tc(const Factor& F, int i, int64_t C, const Lims& L, cons
   t.err = tco.err;
   const int flags = (periodize ? SWEEP_PERIODIZE : 0) | (L.one_sided ? SWEEP_ONE_SIDED : 0);
   pf.begin(TLRMVN_KC_DIAG);
-  launch_pdl(sweep_tc_kernel(flags, tco.f16), dim3((unsigned)((Cc + STC_NS - 1) / STC_NS)), dim3(STC_NS),
-             sweep_tc_launch_smem(tu.tc_ctas), st, tco.mapY32, tco.mapB32, tco.mapW, tco.mapU64, tco.mapY64,
+  const int spt = tu.spt == 2 ? 2 : 1;
+  launch_pdl(sweep_tc_kernel(flags, tco.f16, spt), dim3((unsigned)((Cc + STC_NS * spt - 1) / (STC_NS * spt))),
+             dim3(STC_NS), sweep_tc_launch_smem(tu.tc_ctas, spt), st, tco.mapY32, tco.mapB32, tco.mapW, tco.mapU64, tco.mapY64,
              tco.mapV64, t);
   pf.end();
 }

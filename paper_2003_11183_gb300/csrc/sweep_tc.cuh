@@ -93,54 +93,78 @@ static_assert(StcProjCfg::SB == StcCfg::SB, "a projection k-block fills the same
 using StcShiftCfg = tc::Cfg<64, false, true, 64, 1>;  // shift k-block: W (MN-major) x U rows, 64 deep
 static_assert(StcShiftCfg::SB == StcCfg::SB, "a shift k-block fills the same stage");
 
-// [MMA stage | during the sweep: transposed triangle (64 x 64), band copy (64 x 16)]
-// [constants (a, b, 1/B_vv), lattice generators] [barriers, TMEM slot]
+// Stage layout for SPT samples per thread (a CTA owns 128 x SPT samples: thread t
+// the samples t, 128 + t, ...; slot s's sums in TMEM columns [64 s, 64 s + 64) of the
+// thread's lane).  Each k-block loads SPT A operands (one per slot, samples as rows)
+// and one B operand shared by the slots:
+//   coupling (32 deep, split):  [A hi x SPT][B hi] [A lo x SPT][B lo]
+//   shift (64 deep, A MN-major): [A x SPT][U rows]
+//   projection (64 deep):       [A x SPT][V rows]
+// During the sweep the stage holds the transposed triangle (64 x 64) and the band copy (64 x 16).
+template <int SPT>
+struct StcLayout {
+  static constexpr uint32_t CA = StcCfg::A_BYTES, CB = StcCfg::B_BYTES;
+  static constexpr uint32_t CHALF = SPT * CA + CB;
+  static constexpr uint32_t SA = StcShiftCfg::A_BYTES, PA = StcProjCfg::A_BYTES;
+  static constexpr uint32_t SB = 2 * CHALF;
+  static constexpr uint32_t TMEM_COLS = STC_SUB * SPT;
+  static_assert(SPT == 1 || SPT == 2, "samples per thread");
+  static_assert(SPT * SA + StcShiftCfg::B_BYTES == SB && SPT * PA + StcProjCfg::B_BYTES == SB,
+                "every k-block fills the same stage");
+  static_assert(CHALF % 1024 == 0, "operand bases stay on swizzle atoms");
+};
 constexpr int STC_BT_FLOATS = STC_SUB * STC_SUB, STC_BAND_FLOATS = STC_SUB * 16;
 static_assert((STC_BT_FLOATS + STC_BAND_FLOATS) * 4 <= StcCfg::SB, "the sweep's B copies fit in the stage");
+// [stage][constants (a, b, 1/B_vv), lattice generators][barriers, TMEM slot]
+template <int SPT = 1>
 __host__ __device__ constexpr size_t sweep_tc_smem_bytes() {
-  return 1024 /*align*/ + (size_t)StcCfg::SB + STC_SUB * (sizeof(float4) + sizeof(uint64_t)) + 64;
+  return 1024 /*align*/ + (size_t)StcLayout<SPT>::SB + STC_SUB * (sizeof(float4) + sizeof(uint64_t)) + 64;
 }
 
 // Shared-memory layout and per-CTA state of the whole-tile sweep (set up once per
 // kernel: a persistent kernel runs many tiles through the same stage, barriers
 // and TMEM columns).
 struct StcCta {
-  unsigned char* stage;  // MMA phase: [A hi][B hi][A lo][B lo]; sweep: transposed triangle, band copy
+  unsigned char* stage;
   float4* s_abi;
   uint64_t* s_q;
   uint64_t* full;        // the stage's copies landed
   uint64_t* freeb;       // the products reading the stage are done
-  uint32_t tmem;         // first of the CTA's 64 TMEM columns
+  uint32_t tmem;         // first of the CTA's TMEM columns
   uint32_t* phases;      // thread 0's barrier parities (bit 0: full, bit 1: freeb)
   int* abort_flag;
 };
 
-// Where the CTA's 128 samples sit in the operand maps and the result buffers.
+// Where the CTA's samples sit in the operand maps and the result buffers (slot s of
+// the thread: the sample 128 s + thread of the CTA).
 struct StcPlace {
-  int wx;                // x coordinate of the CTA's first sample in the W map (samples are columns)
-  int wy;                // row added to the tile's rank rows in the W map
-  int yrow;              // row coordinate of the CTA's first sample in the y maps (samples are rows)
-  unsigned short* ysrow; // this thread's row of sample-major y (hi; lo at + d.ys_lo)
-  unsigned short* wcol;  // this thread's column of W (row k at wcol[k * p.ldw])
+  int wx;                   // x coordinate of the CTA's first sample in the W map (samples are columns)
+  int wy;                   // row added to the tile's rank rows in the W map
+  int yrow;                 // row coordinate of the CTA's first sample in the y maps (samples are rows)
+  unsigned short* ysrow[2]; // each slot's row of sample-major y (hi; lo at + d.ys_lo)
+  unsigned short* wcol[2];  // each slot's column of W (row k at wcol[k * p.ldw])
 };
 
-// One diagonal tile for the CTA's 128 samples: the low-rank shifts and in-tile
-// coupling on tcgen05, the float sweep of eq. 2, the projections.  act: the
-// thread's sample exists (else it shadows one and writes nothing); Ds, ks: its
-// lattice shift row and point index; rs: its MVT scale (1 for MVN).  The tile's
-// log P is added to (prod, pe, lsum).  Returns false when a bounded wait expired.
-template <int FLAGS, bool F16>
+// One diagonal tile for the CTA's samples: the low-rank shifts and in-tile
+// coupling on tcgen05, the float sweep of eq. 2, the projections.  act[s]: slot
+// s's sample exists (else it shadows one and writes nothing); Ds[s], ks[s]: its
+// lattice shift row and point index; rs[s]: its MVT scale (1 for MVN).  The
+// tile's log P is added to (prod[s], pe[s], lsum[s]).  Returns false when a
+// bounded wait expired.
+template <int FLAGS, bool F16, int SPT>
 __device__ __forceinline__ bool stc_tile(const CUtensorMap* mapY, const CUtensorMap* mapB, const CUtensorMap* mapW,
                                          const CUtensorMap* mapU, const CUtensorMap* mapY64, const CUtensorMap* mapV,
-                                         const SweepTcArgs& p, const StcCta& k, const StcPlace& pl, bool act,
-                                         const uint64_t* Ds, uint32_t ks, float rs, float& prod, float& lsum,
-                                         int& pe) {
+                                         const SweepTcArgs& p, const StcCta& k, const StcPlace& pl,
+                                         const bool (&act)[SPT], const uint64_t* const (&Ds)[SPT],
+                                         const uint32_t (&ks)[SPT], const float (&rs)[SPT], float (&prod)[SPT],
+                                         float (&lsum)[SPT], int (&pe)[SPT]) {
   constexpr bool PER = FLAGS & SWEEP_PERIODIZE, ONE = FLAGS & SWEEP_ONE_SIDED;
   using Op = Op16<F16>;
+  using Lay = StcLayout<SPT>;
   constexpr uint32_t ID_C = F16 ? StcCfg::IDESC_F16 : StcCfg::IDESC;
   constexpr uint32_t ID_S = F16 ? StcShiftCfg::IDESC_F16 : StcShiftCfg::IDESC;
   constexpr uint32_t ID_P = F16 ? StcProjCfg::IDESC_F16 : StcProjCfg::IDESC;
-  constexpr uint32_t A_BYTES = StcCfg::A_BYTES, HALF = StcCfg::HALF, SB = StcCfg::SB;
+  constexpr uint32_t CA = Lay::CA, CHALF = Lay::CHALF, SA = Lay::SA, PA = Lay::PA, SB = Lay::SB;
   unsigned char* stage = k.stage;
   float* s_bt = reinterpret_cast<float*>(stage);  // sweep: s_bt[u * 64 + v] = B_i[q0 + v][q0 + u]
   float* s_band = s_bt + STC_BT_FLOATS;           // sweep: s_band[v * 16 + k] = B_i[q0 + v + 1 + k][q0 + v]
@@ -153,7 +177,7 @@ __device__ __forceinline__ bool stc_tile(const CUtensorMap* mapY, const CUtensor
   const int tid = threadIdx.x, warp = tid >> 5;
   const int mt = d.mt;
   const uint32_t tmem = k.tmem;
-  const uint32_t tl = tmem + ((uint32_t)(32 * warp) << 16);  // this warp's 32 lanes
+  const uint32_t tl = tmem + ((uint32_t)(32 * warp) << 16);  // this warp's 32 lanes (slot s: columns + 64 s)
 
   for (int q0 = 0; q0 < mt; q0 += STC_SUB) {
     const int mq = min(STC_SUB, mt - q0);
@@ -165,12 +189,11 @@ __device__ __forceinline__ bool stc_tile(const CUtensorMap* mapY, const CUtensor
     }
     if ((q0 > 0 || p.kr > 0) && tid == 0) {
       // T = W[ranks of row tile i, samples]^T U_i[q0 + v, ranks]^T     (the low-rank shifts,
-      //     64-deep stages: two 64-sample MN-major boxes of W, one box of U rows)
+      //     64-deep stages: two 64-sample MN-major boxes of W per slot, one box of U rows)
       //   + y[:, <q0] B_i[q0 + v, <q0]^T                              (the coupling, 32-deep split stages)
       const uint32_t sa = tc::smem_u32(stage);
-      const uint64_t dah = tc::sdesc<STC_KB>(sa), dbh = tc::sdesc<STC_KB>(sa + A_BYTES);
-      const uint64_t dal = tc::sdesc<STC_KB>(sa + HALF), dbl = tc::sdesc<STC_KB>(sa + HALF + A_BYTES);
-      const uint64_t dw = tc::sdesc_mn(sa), du = tc::sdesc<64>(sa + StcShiftCfg::A_BYTES);
+      const uint64_t dbh = tc::sdesc<STC_KB>(sa + SPT * CA), dbl = tc::sdesc<STC_KB>(sa + CHALF + SPT * CA);
+      const uint64_t du = tc::sdesc<64>(sa + SPT * SA);
       const int nks = (p.kr + 63) / 64, nk = nks + q0 / STC_KB;
       uint32_t ph = *k.phases;
       int bad = 0;  // 1: copies left in flight, 2: products left in flight
@@ -178,15 +201,21 @@ __device__ __forceinline__ bool stc_tile(const CUtensorMap* mapY, const CUtensor
         tc::mbar_expect_tx(full, SB);
         if (kb < nks) {
           const int y = pl.wy + p.krow0 + kb * 64;
-          tc::tma_load_2d(stage, mapW, full, pl.wx, y);
-          tc::tma_load_2d(stage + StcShiftCfg::A_BYTES / 2, mapW, full, pl.wx + 64, y);
-          tc::tma_load_2d(stage + StcShiftCfg::A_BYTES, mapU, full, kb * 64, p.urow0 + q0);
+#pragma unroll
+          for (int s = 0; s < SPT; s++) {
+            tc::tma_load_2d(stage + s * SA, mapW, full, pl.wx + 128 * s, y);
+            tc::tma_load_2d(stage + s * SA + SA / 2, mapW, full, pl.wx + 128 * s + 64, y);
+          }
+          tc::tma_load_2d(stage + SPT * SA, mapU, full, kb * 64, p.urow0 + q0);
         } else {
           const int x = (kb - nks) * STC_KB;
-          tc::tma_load_2d(stage, mapY, full, x, pl.yrow);
-          tc::tma_load_2d(stage + A_BYTES, mapB, full, x, p.brow0 + q0);
-          tc::tma_load_2d(stage + HALF, mapY, full, p.alo + x, pl.yrow);
-          tc::tma_load_2d(stage + HALF + A_BYTES, mapB, full, p.blo + x, p.brow0 + q0);
+#pragma unroll
+          for (int s = 0; s < SPT; s++) {
+            tc::tma_load_2d(stage + s * CA, mapY, full, x, pl.yrow + 128 * s);
+            tc::tma_load_2d(stage + CHALF + s * CA, mapY, full, p.alo + x, pl.yrow + 128 * s);
+          }
+          tc::tma_load_2d(stage + SPT * CA, mapB, full, x, p.brow0 + q0);
+          tc::tma_load_2d(stage + CHALF + SPT * CA, mapB, full, p.blo + x, p.brow0 + q0);
         }
         if (!tc::mbar_wait(full, ph & 1, p.err, 8)) {
           bad = 1;
@@ -197,15 +226,24 @@ __device__ __forceinline__ bool stc_tile(const CUtensorMap* mapY, const CUtensor
         if (kb < nks) {
           // per 16-deep step: MN-major W two 1 KB K groups on (+128), U rows 32 bytes on (+2)
 #pragma unroll
-          for (int kk = 0; kk < 4; kk++)
-            tc::mma_f16(tmem, dw + (uint64_t)(128 * kk), du + (uint64_t)(2 * kk), ID_S, (kb > 0 || kk > 0) ? 1u : 0u);
+          for (int s = 0; s < SPT; s++) {
+            const uint64_t dw = tc::sdesc_mn(sa + s * SA);
+#pragma unroll
+            for (int kk = 0; kk < 4; kk++)
+              tc::mma_f16(tmem + STC_SUB * s, dw + (uint64_t)(128 * kk), du + (uint64_t)(2 * kk), ID_S,
+                          (kb > 0 || kk > 0) ? 1u : 0u);
+          }
         } else {
 #pragma unroll
-          for (int kk = 0; kk < STC_KB / 16; kk++) {
-            const uint64_t o = (uint64_t)(kk * 2);  // 32 bytes per 16-deep step, in 16-byte units
-            tc::mma_f16(tmem, dah + o, dbh + o, ID_C, (kb > 0 || kk > 0) ? 1u : 0u);
-            tc::mma_f16(tmem, dah + o, dbl + o, ID_C, 1u);
-            tc::mma_f16(tmem, dal + o, dbh + o, ID_C, 1u);
+          for (int s = 0; s < SPT; s++) {
+            const uint64_t dah = tc::sdesc<STC_KB>(sa + s * CA), dal = tc::sdesc<STC_KB>(sa + CHALF + s * CA);
+#pragma unroll
+            for (int kk = 0; kk < STC_KB / 16; kk++) {
+              const uint64_t o = (uint64_t)(kk * 2);  // 32 bytes per 16-deep step, in 16-byte units
+              tc::mma_f16(tmem + STC_SUB * s, dah + o, dbh + o, ID_C, (kb > 0 || kk > 0) ? 1u : 0u);
+              tc::mma_f16(tmem + STC_SUB * s, dah + o, dbl + o, ID_C, 1u);
+              tc::mma_f16(tmem + STC_SUB * s, dal + o, dbh + o, ID_C, 1u);
+            }
           }
         }
         tc::mma_commit(freeb);
@@ -242,99 +280,117 @@ __device__ __forceinline__ bool stc_tile(const CUtensorMap* mapY, const CUtensor
 
     for (int v0 = 0; v0 < mq; v0 += DIAG_VB) {
       const int nb = min(DIAG_VB, mq - v0);
-      float acc[DIAG_VB], dl[DIAG_VB];
-      if (q0 > 0 || p.kr > 0) {
-        uint32_t r[DIAG_VB];
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-            "%15}, [%16];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-            : "r"(tl + (uint32_t)v0));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      float acc[SPT][DIAG_VB];
 #pragma unroll
-        for (int j = 0; j < DIAG_VB; j++) dl[j] = F16 ? __uint_as_float(r[j]) * p.tscale : __uint_as_float(r[j]);
-      } else {
+      for (int s = 0; s < SPT; s++) {
+        if (q0 > 0 || p.kr > 0) {
+          uint32_t r[DIAG_VB];
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+              "%14, %15}, [%16];"
+              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+              : "r"(tl + (uint32_t)(STC_SUB * s + v0)));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int j = 0; j < DIAG_VB; j++) dl[j] = 0.0f;
+          for (int j = 0; j < DIAG_VB; j++) acc[s][j] = F16 ? __uint_as_float(r[j]) * p.tscale : __uint_as_float(r[j]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < DIAG_VB; j++) acc[s][j] = 0.0f;
+        }
       }
+      uint64_t dnext[SPT];
 #pragma unroll
-      for (int j = 0; j < DIAG_VB; j++) acc[j] = 0.0f;
-      uint64_t dnext = Ds[q0 + v0];
+      for (int s = 0; s < SPT; s++) dnext[s] = Ds[s][q0 + v0];
       // sums over the sub-tile's earlier variables for the block's 16 variables:
-      // y_u from this lane's TMEM columns, four at a time
+      // y_u from this lane's TMEM columns, four at a time, the B rows shared by the slots
       for (int u0 = 0; u0 < v0; u0 += 4) {
-        uint32_t r[4];
-        asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
-                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                     : "r"(tl + (uint32_t)u0));
+        uint32_t r[SPT][4];
+#pragma unroll
+        for (int s = 0; s < SPT; s++)
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                       : "=r"(r[s][0]), "=r"(r[s][1]), "=r"(r[s][2]), "=r"(r[s][3])
+                       : "r"(tl + (uint32_t)(STC_SUB * s + u0)));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
         for (int uu = 0; uu < 4; uu++) {
-          const float yu = __uint_as_float(r[uu]);
           const float4* b4 = reinterpret_cast<const float4*>(s_bt + (u0 + uu) * STC_SUB + v0);
           const float4 q[4] = {b4[0], b4[1], b4[2], b4[3]};
 #pragma unroll
-          for (int h = 0; h < 4; h++) {
-            acc[4 * h] = fmaf(q[h].x, yu, acc[4 * h]);
-            acc[4 * h + 1] = fmaf(q[h].y, yu, acc[4 * h + 1]);
-            acc[4 * h + 2] = fmaf(q[h].z, yu, acc[4 * h + 2]);
-            acc[4 * h + 3] = fmaf(q[h].w, yu, acc[4 * h + 3]);
+          for (int s = 0; s < SPT; s++) {
+            const float yu = __uint_as_float(r[s][uu]);
+#pragma unroll
+            for (int h = 0; h < 4; h++) {
+              acc[s][4 * h] = fmaf(q[h].x, yu, acc[s][4 * h]);
+              acc[s][4 * h + 1] = fmaf(q[h].y, yu, acc[s][4 * h + 1]);
+              acc[s][4 * h + 2] = fmaf(q[h].z, yu, acc[s][4 * h + 2]);
+              acc[s][4 * h + 3] = fmaf(q[h].w, yu, acc[s][4 * h + 3]);
+            }
           }
         }
       }
-#pragma unroll
-      for (int j = 0; j < DIAG_VB; j++) acc[j] += dl[j];
 #pragma unroll 1
       for (int j = 0; j < nb; j++) {
         const int v = v0 + j;
         const float4 abi = s_abi[v];
         const uint64_t qv = s_q[v];
-        const uint64_t dv = dnext;
-        dnext = Ds[q0 + ((j + 1 < nb) ? v + 1 : v)];  // next variable's offset (the last one reloads its own)
-        const float sum = acc[0];  // shifts + coupling + earlier variables, for variable v
-        const float bt = (abi.y * rs - sum) * abi.z;
-        float w, wc, f, la, y;
-        lattice_wf((uint64_t)ks * qv + dv, PER ? 1 : 0, w, wc);
-        if (ONE) {
-          sov_step_f32_upper(bt, w, wc, f, la, y);
-        } else {
-          const float at = (abi.x * rs - sum) * abi.z;
-          sov_step_f32_prod(at, bt, w, wc, f, la, y);
+        const int vn = q0 + ((j + 1 < nb) ? v + 1 : v);  // next variable (the last one reloads its own)
+        float y[SPT];
+#pragma unroll
+        for (int s = 0; s < SPT; s++) {
+          const uint64_t dv = dnext[s];
+          dnext[s] = Ds[s][vn];
+          const float sum = acc[s][0];  // shifts + coupling + earlier variables, for variable v
+          const float bt = (abi.y * rs[s] - sum) * abi.z;
+          float w, wc, f, la;
+          lattice_wf((uint64_t)ks[s] * qv + dv, PER ? 1 : 0, w, wc);
+          if (ONE) {
+            sov_step_f32_upper(bt, w, wc, f, la, y[s]);
+          } else {
+            const float at = (abi.x * rs[s] - sum) * abi.z;
+            sov_step_f32_prod(at, bt, w, wc, f, la, y[s]);
+          }
+          lsum[s] += la;
+          prod[s] *= f;  // prod in [1, 2) and f >= Phi(-12): a normal float
+          const int pb = __float_as_int(prod[s]);
+          pe[s] += (pb >> 23) - 127;
+          prod[s] = __int_as_float((pb & 0x007FFFFF) | 0x3F800000);
         }
-        lsum += la;
-        prod *= f;  // prod in [1, 2) and f >= Phi(-12): a normal float
-        const int pb = __float_as_int(prod);
-        pe += (pb >> 23) - 127;
-        prod = __int_as_float((pb & 0x007FFFFF) | 0x3F800000);
-        // y into this lane's column v (its coupling has been read); the store is a
-        // warp-wide one, after the step's divergent branches
+        // y into this lane's column v of each slot (its coupling has been read); the
+        // stores are warp-wide ones, after the step's divergent branches
         __syncwarp();
-        asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(tl + (uint32_t)v), "r"(__float_as_uint(y))
-                     : "memory");
+#pragma unroll
+        for (int s = 0; s < SPT; s++)
+          asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(tl + (uint32_t)(STC_SUB * s + v)),
+                       "r"(__float_as_uint(y[s]))
+                       : "memory");
         // window shift: acc[i] <- acc[i+1] + B[v+1+i][v] y, the column from the band copy
         const float4* b4 = reinterpret_cast<const float4*>(s_band + v * 16);
         const float4 q[4] = {b4[0], b4[1], b4[2], b4[3]};
         const float bcur[DIAG_VB] = {q[0].x, q[0].y, q[0].z, q[0].w, q[1].x, q[1].y, q[1].z, q[1].w,
                                      q[2].x, q[2].y, q[2].z, q[2].w, q[3].x, q[3].y, q[3].z, q[3].w};
 #pragma unroll
-        for (int i = 0; i < DIAG_VB - 1; i++) acc[i] = fmaf(bcur[i], y, acc[i + 1]);
-        acc[DIAG_VB - 1] = 0.0f;
+        for (int s = 0; s < SPT; s++) {
+#pragma unroll
+          for (int i = 0; i < DIAG_VB - 1; i++) acc[s][i] = fmaf(bcur[i], y[s], acc[s][i + 1]);
+          acc[s][DIAG_VB - 1] = 0.0f;
+        }
       }
       asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
       // the block's y, sample-major bf16 hi and lo (32 bytes each per sample), for
       // the later sub-tiles' products (read back by TMA: async proxy) and the projection
-      {
+#pragma unroll
+      for (int s = 0; s < SPT; s++) {
         uint32_t r[DIAG_VB];
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
             "%15}, [%16];"
             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
               "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-            : "r"(tl + (uint32_t)v0));
+            : "r"(tl + (uint32_t)(STC_SUB * s + v0)));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (act) {
-          unsigned short* row = pl.ysrow + q0 + v0;
+        if (act[s]) {
+          unsigned short* row = pl.ysrow[s] + q0 + v0;
           uint32_t hi2[DIAG_VB / 2], lo2[DIAG_VB / 2];
 #pragma unroll
           for (int j = 0; j < DIAG_VB; j += 2) {
@@ -375,13 +431,14 @@ __device__ __forceinline__ bool stc_tile(const CUtensorMap* mapY, const CUtensor
   for (int r0 = 0; r0 < p.kc; r0 += 64) {
     if (tid == 0) {
       const uint32_t sa = tc::smem_u32(stage);
-      const uint64_t da = tc::sdesc<64>(sa), db = tc::sdesc<64>(sa + StcProjCfg::A_BYTES);
+      const uint64_t db = tc::sdesc<64>(sa + SPT * PA);
       uint32_t ph = *k.phases;
       int bad = 0;
       for (int kb = 0; kb < (mt + 63) / 64; kb++) {
         tc::mbar_expect_tx(full, SB);
-        tc::tma_load_2d(stage, mapY64, full, kb * 64, pl.yrow);
-        tc::tma_load_2d(stage + StcProjCfg::A_BYTES, mapV, full, kb * 64, p.kcol0 + r0);
+#pragma unroll
+        for (int s = 0; s < SPT; s++) tc::tma_load_2d(stage + s * PA, mapY64, full, kb * 64, pl.yrow + 128 * s);
+        tc::tma_load_2d(stage + SPT * PA, mapV, full, kb * 64, p.kcol0 + r0);
         if (!tc::mbar_wait(full, ph & 1, p.err, 8)) {
           bad = 1;
           break;
@@ -389,8 +446,13 @@ __device__ __forceinline__ bool stc_tile(const CUtensorMap* mapY, const CUtensor
         ph ^= 1;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-        for (int kk = 0; kk < 4; kk++)
-          tc::mma_f16(tmem, da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), ID_P, (kb > 0 || kk > 0) ? 1u : 0u);
+        for (int s = 0; s < SPT; s++) {
+          const uint64_t da = tc::sdesc<64>(sa + s * PA);
+#pragma unroll
+          for (int kk = 0; kk < 4; kk++)
+            tc::mma_f16(tmem + STC_SUB * s, da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), ID_P,
+                        (kb > 0 || kk > 0) ? 1u : 0u);
+        }
         tc::mma_commit(freeb);
         if (!tc::mbar_wait(freeb, (ph >> 1) & 1, p.err, 9)) {
           bad = 2;
@@ -411,20 +473,23 @@ __device__ __forceinline__ bool stc_tile(const CUtensorMap* mapY, const CUtensor
     if (*abort_flag) return false;
 #pragma unroll 1
     for (int h = 0; h < 64; h += 16) {
-      uint32_t r[16];
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-          "%15}, [%16];"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-          : "r"(tl + (uint32_t)h));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (act) {
 #pragma unroll
-        for (int j = 0; j < 16; j++)
-          if (r0 + h + j < p.kc)
-            pl.wcol[(int64_t)p.vmap[r0 + h + j] * p.ldw] =
-                Op::one(F16 ? __uint_as_float(r[j]) * p.wscale[r0 + h + j] : __uint_as_float(r[j]));
+      for (int s = 0; s < SPT; s++) {
+        uint32_t r[16];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+            "%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(tl + (uint32_t)(STC_SUB * s + h)));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (act[s]) {
+#pragma unroll
+          for (int j = 0; j < 16; j++)
+            if (r0 + h + j < p.kc)
+              pl.wcol[s][(int64_t)p.vmap[r0 + h + j] * p.ldw] =
+                  Op::one(F16 ? __uint_as_float(r[j]) * p.wscale[r0 + h + j] : __uint_as_float(r[j]));
+        }
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -434,14 +499,15 @@ __device__ __forceinline__ bool stc_tile(const CUtensorMap* mapY, const CUtensor
 }
 
 // The CTA's stage, constants, barriers and TMEM columns (dynamic shared memory of
-// sweep_tc_smem_bytes()); the barriers initialised and the columns allocated.
+// sweep_tc_smem_bytes<SPT>()); the barriers initialised and the columns allocated.
 // Ends with every thread past the allocation.
+template <int SPT>
 __device__ __forceinline__ StcCta stc_cta_setup(unsigned char* smem_raw, uint32_t* phases, int* abort_flag) {
   // (offset within the shared window, so that the accesses stay shared-memory ones)
   unsigned char* smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
   StcCta k;
   k.stage = smem;
-  k.s_abi = reinterpret_cast<float4*>(smem + StcCfg::SB);
+  k.s_abi = reinterpret_cast<float4*>(smem + StcLayout<SPT>::SB);
   k.s_q = reinterpret_cast<uint64_t*>(k.s_abi + STC_SUB);
   k.full = k.s_q + STC_SUB;
   k.freeb = k.full + 1;
@@ -457,7 +523,7 @@ __device__ __forceinline__ StcCta stc_cta_setup(unsigned char* smem_raw, uint32_
   }
   if ((threadIdx.x >> 5) == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(tmem_slot)),
-                 "r"(STC_SUB)
+                 "r"(StcLayout<SPT>::TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -469,59 +535,70 @@ __device__ __forceinline__ StcCta stc_cta_setup(unsigned char* smem_raw, uint32_
 }
 
 // Frees the CTA's TMEM columns once every thread is done with them.
+template <int SPT>
 __device__ __forceinline__ void stc_cta_release(const StcCta& k) {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if ((threadIdx.x >> 5) == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(k.tmem), "r"(STC_SUB) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(k.tmem), "r"(StcLayout<SPT>::TMEM_COLS)
+                 : "memory");
 }
 
-// One launch per diagonal tile of one problem: CTA x owns samples [128 x, 128 x + 128) of the chunk.
-// (Six CTAs per SM, 80 registers each: the 72 that seven would allow measured 17% slower.)
-template <int FLAGS, bool F16>
-__global__ void __launch_bounds__(STC_NS, 6)
+// One launch per diagonal tile of one problem: CTA x owns samples [128 SPT x, 128 SPT (x + 1)) of the
+// chunk.  SPT = 1: six CTAs per SM, 80 registers each (the 72 that seven would allow measured 17%
+// slower); SPT = 2: two samples per thread, 128 TMEM columns and a 40 KB stage per CTA, four per SM.
+template <int FLAGS, bool F16, int SPT>
+__global__ void __launch_bounds__(STC_NS, SPT == 1 ? 6 : 4)
     k_sweep_tc(const __grid_constant__ CUtensorMap mapY, const __grid_constant__ CUtensorMap mapB,
                const __grid_constant__ CUtensorMap mapW, const __grid_constant__ CUtensorMap mapU,
                const __grid_constant__ CUtensorMap mapY64, const __grid_constant__ CUtensorMap mapV, SweepTcArgs p) {
   extern __shared__ __align__(1024) unsigned char stc_smem[];
   __shared__ uint32_t phases;
   __shared__ int abort_flag;
-  const StcCta k = stc_cta_setup(stc_smem, &phases, &abort_flag);
+  const StcCta k = stc_cta_setup<SPT>(stc_smem, &phases, &abort_flag);
   pdl_trigger();  // (after the allocation: a successor's CTAs never hold TMEM this grid still needs)
   pdl_wait();  // limit shifts, y and log P of the preceding kernels
 
   const DiagArgs32& d = p.d;
   const int tid = threadIdx.x;
-  const int c0 = blockIdx.x * STC_NS;  // (a chunk holds fewer than 2^31 samples)
-  const bool act = c0 + tid < d.C;
-  const int cs = act ? c0 + tid : (int)d.C - 1;  // inactive lanes shadow a valid sample, write nothing
-  const uint64_t* Ds;
-  uint32_t ks;  // lattice point index k = 1..N (N < 2^31)
-  {
-    const int64_t g = d.sample0 + cs, sh = g / d.N;
-    ks = (uint32_t)(g - sh * d.N) + 1u;
-    Ds = d.D + sh * d.ldD + d.coord0;
-  }
-  const float rs = d.rs ? d.rs[cs] : 1.0f;
-  // log P of the tile = log(prod) + pe log 2 + lsum, prod kept in [1, 2)
-  float prod = 1.0f, lsum = 0.0f;
-  int pe = 0;
+  const int c0 = blockIdx.x * STC_NS * SPT;  // (a chunk holds fewer than 2^31 samples)
+  bool act[SPT];
+  int cs[SPT];
+  const uint64_t* Ds[SPT];
+  uint32_t ks[SPT];  // lattice point index k = 1..N (N < 2^31)
+  float rs[SPT], prod[SPT], lsum[SPT];
+  int pe[SPT];
   StcPlace pl;
   pl.wx = c0;
   pl.wy = 0;
   pl.yrow = c0;
-  pl.ysrow = reinterpret_cast<unsigned short*>(d.Ys) + (int64_t)cs * d.ldys;
-  pl.wcol = p.W + cs;
-  const bool ok = stc_tile<FLAGS, F16>(&mapY, &mapB, &mapW, &mapU, &mapY64, &mapV, p, k, pl, act, Ds, ks, rs, prod,
-                                       lsum, pe);
-  if (ok && act) {
-    const double lp = (double)(logf(prod) + lsum) + (double)pe * 0.69314718055994530942;
-    const int64_t g = d.sample0 + cs;
-    if (d.first) d.logP[g] = lp;
-    else d.logP[g] += lp;
+#pragma unroll
+  for (int s = 0; s < SPT; s++) {
+    act[s] = c0 + STC_NS * s + tid < d.C;
+    cs[s] = act[s] ? c0 + STC_NS * s + tid : (int)d.C - 1;  // inactive lanes shadow a valid sample, write nothing
+    const int64_t g = d.sample0 + cs[s], sh = g / d.N;
+    ks[s] = (uint32_t)(g - sh * d.N) + 1u;
+    Ds[s] = d.D + sh * d.ldD + d.coord0;
+    rs[s] = d.rs ? d.rs[cs[s]] : 1.0f;
+    // log P of the tile = log(prod) + pe log 2 + lsum, prod kept in [1, 2)
+    prod[s] = 1.0f;
+    lsum[s] = 0.0f;
+    pe[s] = 0;
+    pl.ysrow[s] = reinterpret_cast<unsigned short*>(d.Ys) + (int64_t)cs[s] * d.ldys;
+    pl.wcol[s] = p.W + cs[s];
   }
-  stc_cta_release(k);
+  const bool ok = stc_tile<FLAGS, F16, SPT>(&mapY, &mapB, &mapW, &mapU, &mapY64, &mapV, p, k, pl, act, Ds, ks, rs,
+                                            prod, lsum, pe);
+#pragma unroll
+  for (int s = 0; s < SPT; s++)
+    if (ok && act[s]) {
+      const double lp = (double)(logf(prod[s]) + lsum[s]) + (double)pe[s] * 0.69314718055994530942;
+      const int64_t g = d.sample0 + cs[s];
+      if (d.first) d.logP[g] = lp;
+      else d.logP[g] += lp;
+    }
+  stc_cta_release<SPT>(k);
 }
 
 }  // namespace tlrmvn

@@ -44,12 +44,16 @@ static std::string tune_key(const Factor& F, int precision, int64_t S, bool mvt)
 static std::vector<Tuning> candidates(const Factor& F, int precision, int64_t S) {
   std::vector<Tuning> c;
   if (precision == TLRMVN_BF16_SHIFT || precision == TLRMVN_FP16_SHIFT) {
-    for (int ctas : {6, 4})
-      for (int64_t chunk : {(int64_t)0, (S / 2 + 255) / 256 * 256}) {
-        Tuning t;
-        t.tc_ctas = ctas;
-        t.chunk = chunk;
-        c.push_back(t);
+    for (int spt : {1, 2})
+      for (int ctas : {6, 4}) {
+        if (spt == 2 && ctas > 4) continue;  // (two samples per thread: at most four CTAs per SM)
+        for (int64_t chunk : {(int64_t)0, (S / 2 + 255) / 256 * 256}) {
+          Tuning t;
+          t.tc_ctas = ctas;
+          t.chunk = chunk;
+          t.spt = spt;
+          c.push_back(t);
+        }
       }
   } else if (precision == TLRMVN_FP32) {
     for (int sub : {64, 128})
@@ -72,7 +76,7 @@ static std::vector<Tuning> candidates(const Factor& F, int precision, int64_t S)
     bool dup = false;
     for (const Tuning& u : out)
       dup = dup || (std::min(t.sub, F.m) == std::min(u.sub, F.m) && t.threads == u.threads && t.chunk == u.chunk &&
-                    t.tc_ctas == u.tc_ctas);
+                    t.tc_ctas == u.tc_ctas && t.spt == u.spt);
     if (!dup) out.push_back(t);
   }
   return out;
@@ -91,6 +95,8 @@ static bool cache_lookup(const char* path, const std::string& key, Tuning& t) {
     long long chunk = 0;
     if (v >> u.sub >> u.threads >> chunk >> u.tc_ctas) {
       u.chunk = chunk;
+      int spt = 1;
+      if (v >> spt && (spt == 1 || spt == 2)) u.spt = spt;  // (entries without it: one sample per thread)
       t = u;
       found = true;
     }
@@ -102,7 +108,8 @@ static void cache_store(const char* path, const std::string& key, const Tuning& 
   if (!path || !*path) return;
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%s | %d %d %lld %d # %.4f ms\n", key.c_str(), t.sub, t.threads, (long long)t.chunk, t.tc_ctas, ms);
+  fprintf(f, "%s | %d %d %lld %d %d # %.4f ms\n", key.c_str(), t.sub, t.threads, (long long)t.chunk, t.tc_ctas, t.spt,
+          ms);
   fclose(f);
 }
 
@@ -192,6 +199,7 @@ extern "C" int tlrmvn_autotune(tlrmvn_factor_t f, const double* a, const double*
     out->threads = best.threads;
     out->chunk = best.chunk;
     out->tc_ctas = best.tc_ctas;
+    out->spt = best.spt;
     out->ms = best_ms;
     out->candidates = tried;
   }
@@ -206,6 +214,7 @@ extern "C" int tlrmvn_get_tuning(tlrmvn_factor_t f, int precision, tlrmvn_tuning
   out->threads = t.threads;
   out->chunk = t.chunk;
   out->tc_ctas = t.tc_ctas;
+  out->spt = t.spt;
   out->ms = -1.0;
   out->candidates = 0;
   return TLRMVN_OK;
@@ -220,12 +229,14 @@ extern "C" int tlrmvn_set_tuning(tlrmvn_factor_t f, int precision, const tlrmvn_
   if (t->threads != 0 && (t->threads < 32 || t->threads > 256 || t->threads % 32))
     return fail(TLRMVN_E_INVAL, "threads must be 0 or a multiple of 32 in 32..256");
   if (t->chunk < 0 || t->tc_ctas < 1 || t->tc_ctas > 6) return fail(TLRMVN_E_INVAL, "bad chunk or tc_ctas");
+  if (t->spt != 1 && t->spt != 2) return fail(TLRMVN_E_INVAL, "spt must be 1 or 2");
   Factor& F = *reinterpret_cast<Factor*>(f);
   Tuning u;
   u.sub = t->sub;
   u.threads = t->threads;
   u.chunk = t->chunk;
   u.tc_ctas = t->tc_ctas;
+  u.spt = t->spt;
   std::lock_guard<std::mutex> lk(F.tune_mu);
   F.tune[precision] = u;
   return TLRMVN_OK;

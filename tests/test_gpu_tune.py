@@ -53,8 +53,8 @@ def test_tuned_choice_matches_the_oracle(tl, tmp_path, precision):
     F2 = tl.tlrmvn_factor_import(export_bytes(OF))
     again = tl.tlrmvn_autotune(F2, w.a, w.b, w.nu, prec, cache_path=cache, **kw)
     assert again["candidates"] == 0 and again["ms"] == -1.0
-    assert {k: again[k] for k in ("sub", "threads", "chunk", "tc_ctas")} == \
-        {k: got[k] for k in ("sub", "threads", "chunk", "tc_ctas")}
+    assert {k: again[k] for k in ("sub", "threads", "chunk", "tc_ctas", "spt")} == \
+        {k: got[k] for k in ("sub", "threads", "chunk", "tc_ctas", "spt")}
     assert os.path.getsize(cache) > 0
 
 
@@ -84,15 +84,22 @@ def test_bf16_candidates_give_identical_samples(tl):
     F = tl.tlrmvn_factor_import(export_bytes(OF))
     kw = dict(n_shifts=w.n_shifts, n_points=w.n_points, shifts=w.shifts, per_sample=True)
     base = None
-    for ctas in (6, 4, 2):
+    for ctas, spt in ((6, 1), (4, 1), (2, 1), (4, 2), (2, 2)):
         for chunk in (0, 768):
-            tl.tlrmvn_set_tuning(F, tl.BF16_SHIFT, tc_ctas=ctas, chunk=chunk)
+            tl.tlrmvn_set_tuning(F, tl.BF16_SHIFT, tc_ctas=ctas, chunk=chunk, spt=spt)
             pm = tl.tlrmvn_prob(F, w.a, w.b, w.nu, tl.BF16_SHIFT, **kw)[3]
             if base is None:
                 base = pm
-            assert np.array_equal(pm, base), (ctas, chunk)
+            assert np.array_equal(pm, base), (ctas, spt, chunk)
     ref = sov.solve(OF, w.a, w.b, w.nu, w.shifts, w.n_points)
     assert np.all(rel(base, ref["per_sample"]) < 1e-2)
+    # the FP16-shift path: two samples per thread give the same samples as one
+    tl.tlrmvn_set_tuning(F, tl.FP16_SHIFT, spt=1)
+    p1 = tl.tlrmvn_prob(F, w.a, w.b, w.nu, tl.FP16_SHIFT, **kw)[3]
+    tl.tlrmvn_set_tuning(F, tl.FP16_SHIFT, tc_ctas=4, spt=2)
+    p2 = tl.tlrmvn_prob(F, w.a, w.b, w.nu, tl.FP16_SHIFT, **kw)[3]
+    assert np.array_equal(p1, p2)
+    assert np.all(rel(p2, ref["per_sample"]) < 1e-2)
 
 
 def test_batch_tune_keeps_results(tl, tmp_path):

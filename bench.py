@@ -37,7 +37,7 @@ METRIC = "MVN/MVT QMC sample-dims/sec at n=65,536 vs FP64 path; p50/p99 solve la
 # those sources are unchanged (otherwise null); the summaries with the capture
 # commands are under profiles/.
 TRAFFIC = {
-    "k_sweep_tc": {"bytes_per_sample_dim": None,
+    "k_sweep_tc": {"bytes_per_sample_dim": 18.4388,
                    "capture": "profiles/k_sweep_tc_n16384.md",
                    "files": ["paper_2003_11183_gb300/csrc/sweep_tc.cuh",
                              "paper_2003_11183_gb300/csrc/sweep.cuh",
@@ -45,7 +45,7 @@ TRAFFIC = {
                              "paper_2003_11183_gb300/csrc/tcgen05.cuh",
                              "paper_2003_11183_gb300/csrc/common.cuh",
                              "include/tlrmvn.h"],
-                   "sources": None},
+                   "sources": "3067221d8aead7c1a4a75beae6d0cee4496d5793482470818ec07d8b9bded46c"},
 }
 
 
@@ -505,7 +505,7 @@ def run_ours(args):
     e2e = ws * sd / statistics.mean(t_e2e)
 
     # roofline of the dominant kernel class.  Algorithmic work per sample-dimension
-    # (SURVEY-style accounting, stated in sweep_work): the sweep's (mt - 1) flops per
+    # (the accounting stated in sweep_work): the sweep's (mt - 1) flops per
     # variable against the FP32 peak derived from this device's SM count and the SM
     # clock sampled during the timed region (128 FP32 lanes x 2 flops per FMA per SM
     # and cycle); the tensor-core products beside it against the bf16 peak.
@@ -520,6 +520,8 @@ def run_ours(args):
     fp32_src = (f"derived: {sm_count} SMs (device attribute) x 128 FP32 lanes x 2 flops x {sm_mhz:.0f} MHz "
                 "(median SM clock sampled during the timed region)")
     bf16_peak = pk.get("bf16_tflops_sustained", 1700.0)
+    # beside the derived peak, the library's own float32 FMA-throughput probe on this GPU
+    fp32_meas = tl.tlrmvn_measure_fp32_peak(stream)
     classes = {}
     for cls, (t_ms, n_launch) in kern.items():
         if t_ms <= 0 or n_launch == 0:
@@ -530,7 +532,10 @@ def run_ours(args):
             units = float(n) * C * args.steps / n_launch  # sample-dims per launch
             ach = work["sweep"] * units / (d["avg_launch_ms"] / 1e3) / 1e12
             d.update(bound="alu", unit="TFLOP/s", achieved=ach, peak=fp32_peak, frac=ach / fp32_peak,
-                     peak_source=fp32_src, flops_per_sample_dim=work["sweep"], sample_dims_per_launch=units,
+                     peak_source=fp32_src, peak_measured=fp32_meas, frac_of_measured=ach / fp32_meas,
+                     peak_measured_source="tlrmvn_measure_fp32_peak: 8 independent FMA chains per thread, "
+                                          "8 x 256 threads per SM, CUDA events",
+                     flops_per_sample_dim=work["sweep"], sample_dims_per_launch=units,
                      kernel={0: "k_diag<double>", 1: "k_diag_f32"}.get(prec, "k_sweep_tc"))
             if prec >= 2:
                 tach = work["tensor"] * units / (d["avg_launch_ms"] / 1e3) / 1e12
@@ -552,6 +557,8 @@ def run_ours(args):
     dom = max(classes, key=lambda c: classes[c]["ms_per_step"])
     roof = {k: v for k, v in classes[dom].items() if k in ("bound", "achieved", "peak", "unit", "frac", "traffic",
                                                             "traffic_source", "peak_source", "kernel",
+                                                            "peak_measured", "frac_of_measured",
+                                                            "peak_measured_source",
                                                             "flops_per_sample_dim", "sample_dims_per_launch",
                                                             "tensor_share")}
 

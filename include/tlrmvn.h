@@ -386,6 +386,15 @@ int tlrmvn_selftest_phi_neg(const float* x, int n, float* out);
  * arguments, TLRMVN_E_CUDA on a device error. */
 int tlrmvn_selftest_ndtri(const float* p, const float* lp, int n, float* out);
 
+/* Measured float32 FMA throughput of the current device (no counterpart in the
+ * paper; the denominator beside the derived SMs x 128 lanes x 2 x clock peak of
+ * the float sweep's roofline): eight blocks of 256 threads per SM, each thread
+ * eight independent fused multiply-add chains, timed with CUDA events on
+ * `stream` (NULL: the library's stream) after one untimed launch.  *tflops:
+ * flops per second / 1e12.  TLRMVN_E_INVAL for a null output, TLRMVN_E_CUDA on
+ * a device error. */
+int tlrmvn_measure_fp32_peak(void* stream, double* tflops);
+
 /* Kernel classes of the integrand, for tlrmvn_profile_get.  On the BF16-shift
  * path with tiles of more than 64 variables the shifts, the coupling and the
  * projections are computed inside the diagonal-tile sweep's kernel and are

@@ -76,6 +76,7 @@ SIGNATURES = {
     "tlrmvn_selftest_ndtri": (C.c_int, [C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_int,
                                         C.POINTER(C.c_float)]),
     "tlrmvn_selftest_phi_neg": (C.c_int, [C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_float)]),
+    "tlrmvn_measure_fp32_peak": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "tlrmvn_strerror": (C.c_char_p, [C.c_int]),
     "tlrmvn_last_error": (C.c_char_p, []),
 }

@@ -477,3 +477,10 @@ def tlrmvn_selftest_ndtri(p, lp) -> np.ndarray:
     _check(lib.tlrmvn_selftest_ndtri(ps.ctypes.data_as(fp), lps.ctypes.data_as(fp), int(ps.size),
                                      out.ctypes.data_as(fp)), "tlrmvn_selftest_ndtri")
     return out
+
+
+def tlrmvn_measure_fp32_peak(stream=None) -> float:
+    """Measured float32 FMA throughput of the current device, TFLOP/s."""
+    t = C.c_double()
+    _check(L.load().tlrmvn_measure_fp32_peak(_stream_ptr(stream), C.byref(t)), "tlrmvn_measure_fp32_peak")
+    return t.value

@@ -226,17 +226,33 @@ __global__ void __launch_bounds__(256) k_gemm_batched(const GemmEntry* __restric
         Bs[kk][nn] = v;
       }
       __syncthreads();
+      // (small ranks leave most of the last 16-deep step empty: only its kn rows are summed)
+      const int kn = min(16, g.K - k0);
+      if (kn == 16) {
 #pragma unroll
-      for (int kk = 0; kk < 16; kk++) {
-        double a[4], b[4];
+        for (int kk = 0; kk < 16; kk++) {
+          double a[4], b[4];
 #pragma unroll
-        for (int i = 0; i < 4; i++) a[i] = As[kk][ty + 16 * i];
+          for (int i = 0; i < 4; i++) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-        for (int j = 0; j < 4; j++) b[j] = Bs[kk][tx + 16 * j];
+          for (int j = 0; j < 4; j++) b[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-        for (int i = 0; i < 4; i++)
+          for (int i = 0; i < 4; i++)
 #pragma unroll
-          for (int j = 0; j < 4; j++) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+            for (int j = 0; j < 4; j++) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+      } else {
+        for (int kk = 0; kk < kn; kk++) {
+          double a[4], b[4];
+#pragma unroll
+          for (int i = 0; i < 4; i++) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+          for (int j = 0; j < 4; j++) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+          for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int j = 0; j < 4; j++) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
       }
       __syncthreads();
     }

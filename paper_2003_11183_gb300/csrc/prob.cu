@@ -1307,6 +1307,56 @@ __global__ void k_ndtri_selftest(const float* p, const float* lp, int n, float* 
   if (t < n) out[t] = ndtri_f32(p[t], lp[t]);
 }
 
+// Eight independent FMA chains per thread, `iters` x 8 steps each; the sum is
+// written only when it takes a value it never takes, which keeps the chains live.
+__global__ void __launch_bounds__(256) k_fma_peak(float m, float c, int iters, float* sink) {
+  float x[8];
+#pragma unroll
+  for (int j = 0; j < 8; j++) x[j] = (float)(threadIdx.x + j) * 1e-3f;
+  for (int i = 0; i < iters; i++) {
+#pragma unroll
+    for (int u = 0; u < 8; u++)
+#pragma unroll
+      for (int j = 0; j < 8; j++) x[j] = fmaf(x[j], m, c);
+  }
+  float s = 0.0f;
+#pragma unroll
+  for (int j = 0; j < 8; j++) s += x[j];
+  if (s == -1.0f) sink[blockIdx.x] = s;
+}
+
+extern "C" int tlrmvn_measure_fp32_peak(void* stream, double* tflops) {
+  if (!tflops) return fail(TLRMVN_E_INVAL, "null output");
+  cudaStream_t st = pick_stream(stream);
+  int dev = 0, sms = 0;
+  TLR_CUDA(cudaGetDevice(&dev));
+  TLR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int blocks = sms * 8, threads = 256, iters = 2048;
+  float* sink = nullptr;
+  TLR_CUDA(cudaMallocAsync((void**)&sink, (size_t)blocks * sizeof(float), st));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  float ms = 0.0f;
+  if (e == cudaSuccess) {
+    k_fma_peak<<<blocks, threads, 0, st>>>(0.99999994f, 1e-7f, iters, sink);  // untimed
+    cudaEventRecord(e0, st);
+    k_fma_peak<<<blocks, threads, 0, st>>>(0.99999994f, 1e-7f, iters, sink);
+    cudaEventRecord(e1, st);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFreeAsync(sink, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "float32 FMA throughput");
+  const double flops = 2.0 * 64.0 * (double)iters * (double)blocks * (double)threads;
+  *tflops = flops / ((double)ms * 1e-3) / 1e12;
+  return TLRMVN_OK;
+}
+
 extern "C" int tlrmvn_selftest_ndtri(const float* p, const float* lp, int n, float* out) {
   if (!p || !lp || !out || n < 1 || n > (1 << 24)) return fail(TLRMVN_E_INVAL, "bad arguments");
   cudaStream_t st = pick_stream(nullptr);

@@ -144,6 +144,54 @@ __global__ void k_cov_tiles(const TileJob* jobs, CovSrc src, int m) {
   }
 }
 
+// ---- float screening of univariate conditioning's pivot search --------------------------
+// log(Phi(bt) - Phi(at)) in float32, `sure` when its error is below UC_SCREEN_TOL: both finite
+// limits within 12 (Phi there is a normal float; erfcf's few-ulp error and the rounding of the
+// limits to float, |x|^2 2^-24 relative, stay below 1e-5), and the interval not narrow (the
+// smaller probability at most half the larger, so their difference keeps the relative error
+// within 3e-5).  Otherwise `sure` is false and the float64 value decides.
+constexpr float UC_SCREEN_TOL = 2e-4f;
+__device__ __forceinline__ float log_interval_screen(double at, double bt, bool& sure) {
+  sure = false;
+  const bool lo_inf = at == -INFINITY, hi_inf = bt == INFINITY;
+  if (lo_inf && hi_inf) {
+    sure = true;
+    return 0.0f;
+  }
+  if ((!lo_inf && fabs(at) > 12.0) || (!hi_inf && fabs(bt) > 12.0)) return 0.0f;
+  const float rs = 0.70710678118654752f;
+  float big, small;  // the probability as big - small
+  if (!lo_inf && at >= 0.0) {  // upper half: complements
+    big = 0.5f * erfcf((float)at * rs);
+    small = hi_inf ? 0.0f : 0.5f * erfcf((float)bt * rs);
+  } else if (!hi_inf && bt <= 0.0) {  // lower half
+    big = 0.5f * erfcf(-(float)bt * rs);
+    small = lo_inf ? 0.0f : 0.5f * erfcf(-(float)at * rs);
+  } else {  // straddles 0: 1 - upper tail - lower tail
+    big = 1.0f - (hi_inf ? 0.0f : 0.5f * erfcf((float)bt * rs));
+    small = lo_inf ? 0.0f : 0.5f * erfcf(-(float)at * rs);
+  }
+  const float p = big - small;
+  if (!(p > 0.0f) || small > 0.5f * big) return 0.0f;
+  sure = true;
+  return logf(p);
+}
+__device__ float block_min_f(float v, float* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  for (int o = 16; o; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    v = lane < nw ? sh[lane] : INFINITY;
+    for (int o = 16; o; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) sh[0] = v;
+  }
+  __syncthreads();
+  v = sh[0];
+  __syncthreads();
+  return v;
+}
+
 // ---- univariate conditioning (Trinh & Genz) of diagonal blocks --------------------------
 // One block per CTA; right-looking pivoted Cholesky of a copy of the block in
 // `work`.  Writes log of the estimate; with emit, also the pivot order and the
@@ -158,6 +206,8 @@ __global__ void __launch_bounds__(512) k_uc(const int* blist, const double* diag
   double* lcol = ss + m;
   double* sy = lcol + m;
   int* so = (int*)(sy + m);
+  float* sq = (float*)(so + m);  // float estimates of the pivot search (NaN: not sure)
+  __shared__ float shf[32];
   __shared__ double shq[32];
   __shared__ int shi[32];
   __shared__ double shy;
@@ -177,14 +227,36 @@ __global__ void __launch_bounds__(512) k_uc(const int* blist, const double* diag
   for (int k = 0; k < mb; k++) {
     double bq = INFINITY;
     int bi = 0x7fffffff;
+    // the pivot: the smallest float64 log interval probability (lowest index on ties), found
+    // in two passes -- a float estimate of every candidate's value, then float64 only where
+    // the estimate lies within 2 UC_SCREEN_TOL of the smallest sure estimate or is not sure
+    // (the float64 minimum always does: it is the same variable as the float64-only search)
+    float fmin = INFINITY;
     for (int i = k + threadIdx.x; i < mb; i += blockDim.x) {
-      double var = A[(size_t)i * m + i];
-      double q;
+      const double var = A[(size_t)i * m + i];
+      float e = __int_as_float(0x7fc00000);  // not sure: NaN
       if (!(var > 0.0)) {
         atomicExch(status, TLRMVN_E_NOT_SPD);
-        q = INFINITY;
       } else {
-        double sig = sqrt(var);
+        const double sig = sqrt(var);
+        bool sure = false;
+        const float f = log_interval_screen((sa[i] - ss[i]) / sig, (sb[i] - ss[i]) / sig, sure);
+        if (sure) {
+          e = f;
+          fmin = fminf(fmin, f);
+        }
+      }
+      sq[i] = e;
+    }
+    fmin = block_min_f(fmin, shf);
+    const float thr = fmin + 2.0f * UC_SCREEN_TOL;
+    for (int i = k + threadIdx.x; i < mb; i += blockDim.x) {
+      const float e = sq[i];
+      if (!(e != e) && !(e <= thr)) continue;  // sure and clearly above the minimum
+      const double var = A[(size_t)i * m + i];
+      double q = INFINITY;
+      if (var > 0.0) {
+        const double sig = sqrt(var);
         q = log_interval_d((sa[i] - ss[i]) / sig, (sb[i] - ss[i]) / sig);
       }
       argmin_merge(bq, bi, q, i);
@@ -201,17 +273,30 @@ __global__ void __launch_bounds__(512) k_uc(const int* blist, const double* diag
       }
       logp += bq;
     }
+    // (only the lower triangle of the symmetric block is kept: swapping variables k < piv
+    // exchanges A(k,t) with A(piv,t) for t < k, A(t,k) with A(piv,t) for k < t < piv,
+    // A(t,k) with A(t,piv) for t > piv, and the two diagonal entries)
     if (piv != k) {
       for (int t = threadIdx.x; t < mb; t += blockDim.x) {
-        double x = A[(size_t)k * m + t];
-        A[(size_t)k * m + t] = A[(size_t)piv * m + t];
-        A[(size_t)piv * m + t] = x;
-      }
-      __syncthreads();
-      for (int t = threadIdx.x; t < mb; t += blockDim.x) {
-        double x = A[(size_t)t * m + k];
-        A[(size_t)t * m + k] = A[(size_t)t * m + piv];
-        A[(size_t)t * m + piv] = x;
+        double *x0, *x1;
+        if (t < k) {
+          x0 = A + (size_t)k * m + t;
+          x1 = A + (size_t)piv * m + t;
+        } else if (t == k) {
+          x0 = A + (size_t)k * m + k;
+          x1 = A + (size_t)piv * m + piv;
+        } else if (t < piv) {
+          x0 = A + (size_t)t * m + k;
+          x1 = A + (size_t)piv * m + t;
+        } else if (t > piv) {
+          x0 = A + (size_t)t * m + k;
+          x1 = A + (size_t)t * m + piv;
+        } else {
+          continue;  // A(piv,k) stays
+        }
+        const double x = *x0;
+        *x0 = *x1;
+        *x1 = x;
       }
     }
     __syncthreads();
@@ -226,10 +311,14 @@ __global__ void __launch_bounds__(512) k_uc(const int* blist, const double* diag
     __syncthreads();
     const double yk = shy;
     for (int i = k + 1 + threadIdx.x; i < mb; i += blockDim.x) ss[i] += lcol[i] * yk;
-    const int w = mb - k - 1;
-    for (int t = threadIdx.x; t < w * w; t += blockDim.x) {
-      int i = k + 1 + t / w, jj = k + 1 + t % w;
-      A[(size_t)i * m + jj] -= lcol[i] * lcol[jj];
+    // the Schur update of the lower triangle, a row per warp
+    {
+      const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+      for (int i = k + 1 + (threadIdx.x >> 5); i < mb; i += nw) {
+        double* row = A + (size_t)i * m;
+        const double li = lcol[i];
+        for (int jj = k + 1 + lane; jj <= i; jj += 32) row[jj] -= li * lcol[jj];
+      }
     }
     __syncthreads();
   }
@@ -243,8 +332,11 @@ __global__ void __launch_bounds__(512) k_uc(const int* blist, const double* diag
 }
 
 // ---- plain Cholesky of one block, in place (lower), zero above -------------------------
-__global__ void __launch_bounds__(512) k_potrf(double* A, int mb, int m, int* status) {
+// (grid x: independent blocks A + x * m * m, sizes from mbs when given)
+__global__ void __launch_bounds__(512) k_potrf(double* A, int mb, int m, int* status, const int* mbs) {
   extern __shared__ double col[];
+  A += (size_t)blockIdx.x * m * m;
+  if (mbs) mb = mbs[blockIdx.x];
   for (int k = 0; k < mb; k++) {
     const double d = A[(size_t)k * m + k];
     if (!(d > 0.0)) {
@@ -272,17 +364,83 @@ __global__ void __launch_bounds__(512) k_potrf(double* A, int mb, int m, int* st
   }
 }
 
-// ---- inverse of a lower triangular block: Linv (zero above), column per thread ----------
-__global__ void __launch_bounds__(512) k_trinv(const double* L, double* Linv, int mb, int m) {
-  for (int t = threadIdx.x; t < m * m; t += blockDim.x) Linv[t] = 0.0;
-  __syncthreads();
-  for (int r = 0; r < mb; r++) {
-    for (int c = threadIdx.x; c <= r; c += blockDim.x) {
-      double acc = (r == c) ? 1.0 : 0.0;
-      for (int t = c; t < r; t++) acc -= L[(size_t)r * m + t] * Linv[(size_t)t * m + c];
-      Linv[(size_t)r * m + c] = acc / L[(size_t)r * m + r];
+// ---- inverse of a lower triangular block, column-parallel: one warp per column of X = L^-1 --
+// Column c by forward substitution, x_c = 1 / L_cc, x_i = -(sum_{c <= t < i} L_it x_t) / L_ii
+// (the dot product across the warp's lanes, x in the warp's shared-memory row).  X rows and
+// columns in [0, ncols); zero above the diagonal and past mb.  L with leading dimension ldl,
+// X with ldx; 8 warps per 256-thread block, 8 x ncols doubles of shared memory.  Grid y:
+// independent blocks, L and X advanced by sL and sX per block, mb from mbs[y] when mbs is given.
+__global__ void __launch_bounds__(256) k_trinv_cols(const double* L, int ldl, size_t sL, double* X, int ldx, size_t sX,
+                                                    int mb, const int* mbs, int ncols) {
+  extern __shared__ double xs[];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  L += blockIdx.y * sL;
+  X += blockIdx.y * sX;
+  if (mbs) mb = mbs[blockIdx.y];
+  const int c = blockIdx.x * 8 + wl;
+  if (c >= ncols) return;  // (whole warps; the kernel has no block-wide barrier)
+  double* x = xs + (size_t)wl * ncols;
+  const int top = c < mb ? c : ncols;
+  for (int i = lane; i < top; i += 32) X[(size_t)i * ldx + c] = 0.0;
+  if (c >= mb) return;
+  for (int i = mb + lane; i < ncols; i += 32) X[(size_t)i * ldx + c] = 0.0;
+  if (lane == 0) {
+    const double xc = 1.0 / L[(size_t)c * ldl + c];
+    x[c] = xc;
+    X[(size_t)c * ldx + c] = xc;
+  }
+  __syncwarp();
+  for (int i = c + 1; i < mb; i++) {
+    const double* Li = L + (size_t)i * ldl;
+    double sum = 0.0;
+    for (int t = c + lane; t < i; t += 32) sum = fma(Li[t], x[t], sum);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) {
+      const double xi = -sum / Li[i];
+      x[i] = xi;
+      X[(size_t)i * ldx + c] = xi;
+    }
+    __syncwarp();
+  }
+}
+
+// ---- blocked Cholesky pieces: one diagonal block of at most 64 in place ------------------
+// (lower; its strict upper triangle zeroed; the rest of the matrix untouched)
+__global__ void __launch_bounds__(256) k_potrf_diag(double* A, int nb, int ld, int* status) {
+  __shared__ double col[64];
+  for (int k = 0; k < nb; k++) {
+    const double d = A[(size_t)k * ld + k];
+    if (!(d > 0.0)) {
+      if (threadIdx.x == 0) atomicExch(status, TLRMVN_E_NOT_SPD);
+      return;
+    }
+    const double lkk = sqrt(d);
+    for (int i = k + 1 + threadIdx.x; i < nb; i += blockDim.x) {
+      const double l = A[(size_t)i * ld + k] / lkk;
+      A[(size_t)i * ld + k] = l;
+      col[i] = l;
     }
     __syncthreads();
+    if (threadIdx.x == 0) A[(size_t)k * ld + k] = lkk;
+    const int w = nb - k - 1;
+    for (int t = threadIdx.x; t < w * w; t += blockDim.x) {
+      const int i = k + 1 + t / w, jj = k + 1 + t % w;
+      if (jj <= i) A[(size_t)i * ld + jj] -= col[i] * col[jj];
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+    const int i = t / nb, jj = t % nb;
+    if (jj > i) A[(size_t)i * ld + jj] = 0.0;
+  }
+}
+// zero the strict upper triangle of the mb x mb block and every row and column past mb (m x m, ld m)
+__global__ void k_zero_upper(double* A, int mb, int m) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)m * m;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / m), jj = (int)(t % m);
+    if (jj > i || i >= mb) A[t] = 0.0;
   }
 }
 
@@ -295,18 +453,21 @@ struct AcaJob {
   double* V;
   int mi, mj;
 };
-__device__ __forceinline__ void argmax_merge(double& a, int& i, double a2, int i2) {
+// |x| compared through its bit pattern (for non-negative doubles the integer order is the
+// numeric order): the pivot search runs on the integer pipes, not the float64 one.
+__device__ __forceinline__ long long abs_key(double x) { return __double_as_longlong(fabs(x)); }
+__device__ __forceinline__ void keymax_merge(long long& a, int& i, long long a2, int i2) {
   if (a2 > a || (a2 == a && i2 < i)) {
     a = a2;
     i = i2;
   }
 }
-__device__ void block_argmax(double& a, int& i, double* sha, int* shi) {
+__device__ void block_keymax(long long& a, int& i, long long* sha, int* shi) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
   for (int o = 16; o; o >>= 1) {
-    double a2 = __shfl_xor_sync(0xffffffffu, a, o);
+    long long a2 = __shfl_xor_sync(0xffffffffu, a, o);
     int i2 = __shfl_xor_sync(0xffffffffu, i, o);
-    argmax_merge(a, i, a2, i2);
+    keymax_merge(a, i, a2, i2);
   }
   if (lane == 0) {
     sha[wid] = a;
@@ -314,12 +475,12 @@ __device__ void block_argmax(double& a, int& i, double* sha, int* shi) {
   }
   __syncthreads();
   if (wid == 0) {
-    a = lane < nw ? sha[lane] : -1.0;
+    a = lane < nw ? sha[lane] : -1LL;
     i = lane < nw ? shi[lane] : 0x7fffffff;
     for (int o = 16; o; o >>= 1) {
-      double a2 = __shfl_xor_sync(0xffffffffu, a, o);
+      long long a2 = __shfl_xor_sync(0xffffffffu, a, o);
       int i2 = __shfl_xor_sync(0xffffffffu, i, o);
-      argmax_merge(a, i, a2, i2);
+      keymax_merge(a, i, a2, i2);
     }
     if (lane == 0) {
       sha[0] = a;
@@ -335,16 +496,21 @@ __global__ void __launch_bounds__(512) k_aca(const AcaJob* jobs, int m, int cap,
   extern __shared__ double sm[];
   double* u = sm;
   double* v = sm + m;
-  __shared__ double sha[32];
+  __shared__ long long shk[32];
+  __shared__ double shs[32];
   __shared__ int shi[32];
   const AcaJob jb = jobs[blockIdx.x];
   const int mi = jb.mi, mj = jb.mj, tot = mi * mj;
-  double amax = -1.0;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  // entries by (row i over warps, column jj over lanes); t = i * mj + jj orders the ties
+  long long akey = -1;
   int aidx = 0x7fffffff;
-  for (int t = threadIdx.x; t < tot; t += blockDim.x) argmax_merge(amax, aidx, fabs(jb.R[(size_t)(t / mj) * m + t % mj]), t);
+  for (int i = wid; i < mi; i += nw)
+    for (int jj = lane; jj < mj; jj += 32) keymax_merge(akey, aidx, abs_key(jb.R[(size_t)i * m + jj]), i * mj + jj);
   int rank = 0, cp = 0;
   for (;;) {
-    block_argmax(amax, aidx, sha, shi);
+    block_keymax(akey, aidx, shk, shi);
+    const double amax = akey >= 0 ? __longlong_as_double(akey) : -1.0;
     if (!(amax > tol) || aidx >= tot) break;
     if (rank >= cap) {
       cp = 1;
@@ -357,20 +523,22 @@ __global__ void __launch_bounds__(512) k_aca(const AcaJob* jobs, int m, int cap,
     __syncthreads();
     double nu2 = 0.0, nv2 = 0.0;
     for (int t = threadIdx.x; t < mi; t += blockDim.x) nu2 += u[t] * u[t];
-    nu2 = block_sum(nu2, sha);
+    nu2 = block_sum(nu2, shs);
     for (int t = threadIdx.x; t < mj; t += blockDim.x) nv2 += v[t] * v[t];
-    nv2 = block_sum(nv2, sha);
+    nv2 = block_sum(nv2, shs);
     const double f = sqrt(sqrt(nv2) / sqrt(nu2));
     for (int t = threadIdx.x; t < mi; t += blockDim.x) jb.U[(size_t)t * cap + rank] = u[t] * f;
     for (int t = threadIdx.x; t < mj; t += blockDim.x) jb.V[(size_t)t * cap + rank] = v[t] / f;
-    amax = -1.0;
+    akey = -1;
     aidx = 0x7fffffff;
-    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
-      int i = t / mj, jj = t % mj;
-      double* p = jb.R + (size_t)i * m + jj;
-      double x = *p - u[i] * v[jj];
-      *p = x;
-      argmax_merge(amax, aidx, fabs(x), t);
+    for (int i = wid; i < mi; i += nw) {
+      double* row = jb.R + (size_t)i * m;
+      const double ui = u[i];
+      for (int jj = lane; jj < mj; jj += 32) {
+        const double x = row[jj] - ui * v[jj];
+        row[jj] = x;
+        keymax_merge(akey, aidx, abs_key(x), i * mj + jj);
+      }
     }
     __syncthreads();
     rank++;
@@ -582,6 +750,47 @@ static int run_batched(std::vector<GemmEntry>& ent, std::vector<GemmSeg>& seg, G
   return TLRMVN_OK;
 }
 
+// Cholesky factor of the leading mb x mb part of the m x m block A, in place (lower, zero
+// elsewhere), and its inverse Linv: right-looking in panels of 64 -- the panel's diagonal
+// block by one CTA, the panel below it through that block's inverse and the trailing update
+// as GEMMs over the whole GPU -- then the inverse with one warp per column.  P (m x 64) and
+// Pinv (64 x 64) are scratch.  (One CTA for the whole block is bound by one SM's float64
+// rate: ~20 ms at m = 512, against ~1 ms this way.)
+static int chol_inverse(double* A, int mb, int m, double* Linv, double* P, double* Pinv, GemmEntry* d_ent,
+                        GemmSeg* d_seg, size_t ent_cap, size_t seg_cap, int* d_status, cudaStream_t st,
+                        const char* what) {
+  std::vector<GemmEntry> ent;
+  std::vector<GemmSeg> seg;
+  for (int k0 = 0; k0 < mb; k0 += 64) {
+    const int nb = std::min(64, mb - k0), rest = mb - k0 - nb;
+    double* Akk = A + (size_t)k0 * m + k0;
+    k_potrf_diag<<<1, 256, 0, st>>>(Akk, nb, m, d_status);
+    TLR_CUDA(cudaGetLastError());
+    if (rest == 0) break;
+    k_trinv_cols<<<(nb + 7) / 8, 256, 8 * (size_t)nb * sizeof(double), st>>>(Akk, m, 0, Pinv, 64, 0, nb, nullptr, nb);
+    TLR_CUDA(cudaGetLastError());
+    double* Apan = A + (size_t)(k0 + nb) * m + k0;
+    ent.clear();
+    seg.clear();
+    seg.push_back(GemmSeg{Apan, Pinv, m, 64, nb});  // P = A_21 L_11^-T
+    ent.push_back(GemmEntry{P, 64, rest, nb, 0, 1, 1.0, 0.0});
+    TLR_CHECK((run_batched<false, true>(ent, seg, d_ent, d_seg, ent_cap, seg_cap, st)));
+    ent.clear();
+    seg.clear();
+    seg.push_back(GemmSeg{P, P, 64, 64, nb});  // A_22 -= P P^T
+    ent.push_back(GemmEntry{A + (size_t)(k0 + nb) * m + k0 + nb, m, rest, rest, 0, 1, -1.0, 1.0});
+    TLR_CHECK((run_batched<false, true>(ent, seg, d_ent, d_seg, ent_cap, seg_cap, st)));
+    TLR_CUDA(cudaMemcpy2DAsync(Apan, (size_t)m * sizeof(double), P, 64 * sizeof(double), (size_t)nb * sizeof(double),
+                               (size_t)rest, cudaMemcpyDeviceToDevice, st));
+  }
+  k_zero_upper<<<std::max(1, std::min(1024, (m * m + 255) / 256)), 256, 0, st>>>(A, mb, m);
+  TLR_CUDA(cudaGetLastError());
+  TLR_CHECK(check_status(d_status, st, what));
+  k_trinv_cols<<<(m + 7) / 8, 256, 8 * (size_t)m * sizeof(double), st>>>(A, m, 0, Linv, m, 0, mb, nullptr, m);
+  TLR_CUDA(cudaGetLastError());
+  return TLRMVN_OK;
+}
+
 static int factor_build(const CovSrc& src, int64_t n, std::vector<int64_t> geo, std::vector<int> sizes,
                         const double* a_ref, const double* b_ref, const tlrmvn_factor_opts& o, Factor& F) {
   cudaStream_t st = pick_stream(o.stream);
@@ -626,6 +835,9 @@ static int factor_build(const CovSrc& src, int64_t n, std::vector<int64_t> geo, 
   TLR_CHECK(bd.get(&d_blist, r));
   TLR_CHECK(bd.get(&d_logp, r));
   TLR_CHECK(bd.get(&Linv, (size_t)m * m));
+  double *Pch = nullptr, *Pinv = nullptr;  // scratch of the blocked Cholesky
+  TLR_CHECK(bd.get(&Pch, (size_t)m * 64));
+  TLR_CHECK(bd.get(&Pinv, (size_t)64 * 64));
   const size_t npairs = (size_t)r * (r - 1) / 2;
   TLR_CHECK(bd.get(&pool, std::max<size_t>(npairs, 1) * 2 * (size_t)m * cap));
   if (tlr) {
@@ -681,10 +893,11 @@ static int factor_build(const CovSrc& src, int64_t n, std::vector<int64_t> geo, 
   }
   std::vector<int> pos2blk(r);
   std::iota(pos2blk.begin(), pos2blk.end(), 0);
-  const size_t uc_smem = (size_t)m * (5 * sizeof(double) + sizeof(int));
+  const size_t uc_smem = (size_t)m * (5 * sizeof(double) + sizeof(int) + sizeof(float));
   TLR_CHECK(raise_smem_limit((const void*)k_uc, (size_t)uc_smem));
   TLR_CHECK(raise_smem_limit((const void*)k_aca, 2 * m * sizeof(double)));
   TLR_CHECK(raise_smem_limit((const void*)k_potrf, m * sizeof(double)));
+  TLR_CHECK(raise_smem_limit((const void*)k_trinv_cols, 8 * (size_t)m * sizeof(double)));
   const int uc_threads = m >= 256 ? 512 : 256;
 
   if (o.reorder == TLRMVN_REORDER_BLOCK) {
@@ -817,11 +1030,8 @@ static int factor_build(const CovSrc& src, int64_t n, std::vector<int64_t> geo, 
       const int cj = pos2blk[j], mj = sizes[cj];
       double* Sjj = diagS + (size_t)cj * m * m;
       // -- line 10: L_jj and its inverse
-      k_potrf<<<1, 512, m * sizeof(double), st>>>(Sjj, mj, m, d_status);
-      TLR_CUDA(cudaGetLastError());
-      TLR_CHECK(check_status(d_status, st, "diagonal Cholesky"));
-      k_trinv<<<1, 512, 0, st>>>(Sjj, Linv, mj, m);
-      TLR_CUDA(cudaGetLastError());
+      TLR_CHECK(chol_inverse(Sjj, mj, m, Linv, Pch, Pinv, d_ent, d_seg, ent_cap, seg_cap, d_status, st,
+                             "diagonal Cholesky"));
       if (j == r - 1) break;
       // -- line 12: L_ij = Sigma_ij (.) Sigma_jj^-T = U (L_jj^-1 V)^T, truncated; in batches
       {
@@ -1004,10 +1214,8 @@ static int factor_build(const CovSrc& src, int64_t n, std::vector<int64_t> geo, 
         TLR_CUDA(cudaStreamSynchronize(st));
       }
       // -- L_jj and its inverse
-      k_potrf<<<1, 512, m * sizeof(double), st>>>(Sjj, mj, m, d_status);
-      TLR_CUDA(cudaGetLastError());
-      TLR_CHECK(check_status(d_status, st, "diagonal Cholesky"));
-      k_trinv<<<1, 512, 0, st>>>(Sjj, Linv, mj, m);
+      TLR_CHECK(chol_inverse(Sjj, mj, m, Linv, Pch, Pinv, d_ent, d_seg, ent_cap, seg_cap, d_status, st,
+                             "diagonal Cholesky"));
       const int nrem = r - 1 - j;
       if (nrem == 0) break;
       // -- Sigma_ij for the remaining blocks
@@ -1319,7 +1527,7 @@ static int reorder_tiles(Factor& F, const double* a, const double* b, cudaStream
   TLR_CUDA(cudaMemsetAsync(S, 0, r * mm * 8, st));
   TLR_CHECK((run_batched<false, true>(ent, seg, d_ent, d_seg, (size_t)r, (size_t)r, st)));
   // P_j: the univariate-conditioning pivot order with the new limits
-  const size_t uc_smem = (size_t)m * (5 * sizeof(double) + sizeof(int));
+  const size_t uc_smem = (size_t)m * (5 * sizeof(double) + sizeof(int) + sizeof(float));
   TLR_CHECK(raise_smem_limit((const void*)k_uc, uc_smem));
   TLR_CHECK(raise_smem_limit((const void*)k_potrf, m * sizeof(double)));
   k_uc<<<r, m >= 256 ? 512 : 256, uc_smem, st>>>(d_blist, S, d_bsize, m, d_a, d_b, work, d_logp, 1, d_order, d_y,
@@ -1329,10 +1537,11 @@ static int reorder_tiles(Factor& F, const double* a, const double* b, cudaStream
   // Lt_j = chol(P S_j P^T) (in work); X_j = P^T Lt_j; Binv_j = B_j^-1; Q_j = Binv_j X_j
   const unsigned gx = (unsigned)std::max<size_t>(1, std::min<size_t>(64, (mm + 255) / 256));
   k_gather_sym<<<dim3(gx, r), 256, 0, st>>>(S, d_order, d_bsize, m, work);
-  for (int j = 0; j < r; j++) {
-    k_potrf<<<1, 512, m * sizeof(double), st>>>(work + j * mm, sizes[j], m, d_status);
-    k_trinv<<<1, 512, 0, st>>>(F.B + j * mm, Binv + j * mm, sizes[j], m);
-  }
+  // (all tiles at once: one CTA per tile for the Cholesky factors, a warp per column of the inverses)
+  TLR_CHECK(raise_smem_limit((const void*)k_trinv_cols, 8 * (size_t)m * sizeof(double)));
+  k_potrf<<<r, 512, m * sizeof(double), st>>>(work, 0, m, d_status, d_bsize);
+  k_trinv_cols<<<dim3((m + 7) / 8, r), 256, 8 * (size_t)m * sizeof(double), st>>>(F.B, m, mm, Binv, m, mm, 0, d_bsize,
+                                                                                   m);
   TLR_CUDA(cudaGetLastError());
   TLR_CHECK(check_status(d_status, st, "within-tile reordering (Cholesky)"));
   k_scatter_rows<<<dim3(gx, r), 256, 0, st>>>(work, d_order, d_bsize, m, X);

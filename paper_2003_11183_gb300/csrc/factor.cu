@@ -144,54 +144,6 @@ __global__ void k_cov_tiles(const TileJob* jobs, CovSrc src, int m) {
   }
 }
 
-// ---- float screening of univariate conditioning's pivot search --------------------------
-// log(Phi(bt) - Phi(at)) in float32, `sure` when its error is below UC_SCREEN_TOL: both finite
-// limits within 12 (Phi there is a normal float; erfcf's few-ulp error and the rounding of the
-// limits to float, |x|^2 2^-24 relative, stay below 1e-5), and the interval not narrow (the
-// smaller probability at most half the larger, so their difference keeps the relative error
-// within 3e-5).  Otherwise `sure` is false and the float64 value decides.
-constexpr float UC_SCREEN_TOL = 2e-4f;
-__device__ __forceinline__ float log_interval_screen(double at, double bt, bool& sure) {
-  sure = false;
-  const bool lo_inf = at == -INFINITY, hi_inf = bt == INFINITY;
-  if (lo_inf && hi_inf) {
-    sure = true;
-    return 0.0f;
-  }
-  if ((!lo_inf && fabs(at) > 12.0) || (!hi_inf && fabs(bt) > 12.0)) return 0.0f;
-  const float rs = 0.70710678118654752f;
-  float big, small;  // the probability as big - small
-  if (!lo_inf && at >= 0.0) {  // upper half: complements
-    big = 0.5f * erfcf((float)at * rs);
-    small = hi_inf ? 0.0f : 0.5f * erfcf((float)bt * rs);
-  } else if (!hi_inf && bt <= 0.0) {  // lower half
-    big = 0.5f * erfcf(-(float)bt * rs);
-    small = lo_inf ? 0.0f : 0.5f * erfcf(-(float)at * rs);
-  } else {  // straddles 0: 1 - upper tail - lower tail
-    big = 1.0f - (hi_inf ? 0.0f : 0.5f * erfcf((float)bt * rs));
-    small = lo_inf ? 0.0f : 0.5f * erfcf(-(float)at * rs);
-  }
-  const float p = big - small;
-  if (!(p > 0.0f) || small > 0.5f * big) return 0.0f;
-  sure = true;
-  return logf(p);
-}
-__device__ float block_min_f(float v, float* sh) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-  for (int o = 16; o; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
-  if (lane == 0) sh[wid] = v;
-  __syncthreads();
-  if (wid == 0) {
-    v = lane < nw ? sh[lane] : INFINITY;
-    for (int o = 16; o; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (lane == 0) sh[0] = v;
-  }
-  __syncthreads();
-  v = sh[0];
-  __syncthreads();
-  return v;
-}
-
 // ---- univariate conditioning (Trinh & Genz) of diagonal blocks --------------------------
 // One block per CTA; right-looking pivoted Cholesky of a copy of the block in
 // `work`.  Writes log of the estimate; with emit, also the pivot order and the
@@ -206,8 +158,6 @@ __global__ void __launch_bounds__(512) k_uc(const int* blist, const double* diag
   double* lcol = ss + m;
   double* sy = lcol + m;
   int* so = (int*)(sy + m);
-  float* sq = (float*)(so + m);  // float estimates of the pivot search (NaN: not sure)
-  __shared__ float shf[32];
   __shared__ double shq[32];
   __shared__ int shi[32];
   __shared__ double shy;
@@ -227,36 +177,14 @@ __global__ void __launch_bounds__(512) k_uc(const int* blist, const double* diag
   for (int k = 0; k < mb; k++) {
     double bq = INFINITY;
     int bi = 0x7fffffff;
-    // the pivot: the smallest float64 log interval probability (lowest index on ties), found
-    // in two passes -- a float estimate of every candidate's value, then float64 only where
-    // the estimate lies within 2 UC_SCREEN_TOL of the smallest sure estimate or is not sure
-    // (the float64 minimum always does: it is the same variable as the float64-only search)
-    float fmin = INFINITY;
     for (int i = k + threadIdx.x; i < mb; i += blockDim.x) {
-      const double var = A[(size_t)i * m + i];
-      float e = __int_as_float(0x7fc00000);  // not sure: NaN
+      double var = A[(size_t)i * m + i];
+      double q;
       if (!(var > 0.0)) {
         atomicExch(status, TLRMVN_E_NOT_SPD);
+        q = INFINITY;
       } else {
-        const double sig = sqrt(var);
-        bool sure = false;
-        const float f = log_interval_screen((sa[i] - ss[i]) / sig, (sb[i] - ss[i]) / sig, sure);
-        if (sure) {
-          e = f;
-          fmin = fminf(fmin, f);
-        }
-      }
-      sq[i] = e;
-    }
-    fmin = block_min_f(fmin, shf);
-    const float thr = fmin + 2.0f * UC_SCREEN_TOL;
-    for (int i = k + threadIdx.x; i < mb; i += blockDim.x) {
-      const float e = sq[i];
-      if (!(e != e) && !(e <= thr)) continue;  // sure and clearly above the minimum
-      const double var = A[(size_t)i * m + i];
-      double q = INFINITY;
-      if (var > 0.0) {
-        const double sig = sqrt(var);
+        double sig = sqrt(var);
         q = log_interval_d((sa[i] - ss[i]) / sig, (sb[i] - ss[i]) / sig);
       }
       argmin_merge(bq, bi, q, i);
@@ -893,7 +821,7 @@ static int factor_build(const CovSrc& src, int64_t n, std::vector<int64_t> geo, 
   }
   std::vector<int> pos2blk(r);
   std::iota(pos2blk.begin(), pos2blk.end(), 0);
-  const size_t uc_smem = (size_t)m * (5 * sizeof(double) + sizeof(int) + sizeof(float));
+  const size_t uc_smem = (size_t)m * (5 * sizeof(double) + sizeof(int));
   TLR_CHECK(raise_smem_limit((const void*)k_uc, (size_t)uc_smem));
   TLR_CHECK(raise_smem_limit((const void*)k_aca, 2 * m * sizeof(double)));
   TLR_CHECK(raise_smem_limit((const void*)k_potrf, m * sizeof(double)));
@@ -1527,7 +1455,7 @@ static int reorder_tiles(Factor& F, const double* a, const double* b, cudaStream
   TLR_CUDA(cudaMemsetAsync(S, 0, r * mm * 8, st));
   TLR_CHECK((run_batched<false, true>(ent, seg, d_ent, d_seg, (size_t)r, (size_t)r, st)));
   // P_j: the univariate-conditioning pivot order with the new limits
-  const size_t uc_smem = (size_t)m * (5 * sizeof(double) + sizeof(int) + sizeof(float));
+  const size_t uc_smem = (size_t)m * (5 * sizeof(double) + sizeof(int));
   TLR_CHECK(raise_smem_limit((const void*)k_uc, uc_smem));
   TLR_CHECK(raise_smem_limit((const void*)k_potrf, m * sizeof(double)));
   k_uc<<<r, m >= 256 ? 512 : 256, uc_smem, st>>>(d_blist, S, d_bsize, m, d_a, d_b, work, d_logp, 1, d_order, d_y,

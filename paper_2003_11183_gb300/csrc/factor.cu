@@ -245,7 +245,19 @@ __global__ void __launch_bounds__(512) k_uc(const int* blist, const double* diag
       for (int i = k + 1 + (threadIdx.x >> 5); i < mb; i += nw) {
         double* row = A + (size_t)i * m;
         const double li = lcol[i];
-        for (int jj = k + 1 + lane; jj <= i; jj += 32) row[jj] -= li * lcol[jj];
+        int jj = k + 1 + lane;
+        for (; jj + 96 <= i; jj += 128) {  // (four loads per lane in flight)
+          double x0 = row[jj], x1 = row[jj + 32], x2 = row[jj + 64], x3 = row[jj + 96];
+          x0 -= li * lcol[jj];
+          x1 -= li * lcol[jj + 32];
+          x2 -= li * lcol[jj + 64];
+          x3 -= li * lcol[jj + 96];
+          row[jj] = x0;
+          row[jj + 32] = x1;
+          row[jj + 64] = x2;
+          row[jj + 96] = x3;
+        }
+        for (; jj <= i; jj += 32) row[jj] -= li * lcol[jj];
       }
     }
     __syncthreads();
@@ -433,8 +445,19 @@ __global__ void __launch_bounds__(512) k_aca(const AcaJob* jobs, int m, int cap,
   // entries by (row i over warps, column jj over lanes); t = i * mj + jj orders the ties
   long long akey = -1;
   int aidx = 0x7fffffff;
-  for (int i = wid; i < mi; i += nw)
-    for (int jj = lane; jj < mj; jj += 32) keymax_merge(akey, aidx, abs_key(jb.R[(size_t)i * m + jj]), i * mj + jj);
+  // (rows are streamed four loads per lane at a time: the passes are bound by memory latency)
+  for (int i = wid; i < mi; i += nw) {
+    const double* row = jb.R + (size_t)i * m;
+    int jj = lane;
+    for (; jj + 96 < mj; jj += 128) {
+      const double x0 = row[jj], x1 = row[jj + 32], x2 = row[jj + 64], x3 = row[jj + 96];
+      keymax_merge(akey, aidx, abs_key(x0), i * mj + jj);
+      keymax_merge(akey, aidx, abs_key(x1), i * mj + jj + 32);
+      keymax_merge(akey, aidx, abs_key(x2), i * mj + jj + 64);
+      keymax_merge(akey, aidx, abs_key(x3), i * mj + jj + 96);
+    }
+    for (; jj < mj; jj += 32) keymax_merge(akey, aidx, abs_key(row[jj]), i * mj + jj);
+  }
   int rank = 0, cp = 0;
   for (;;) {
     block_keymax(akey, aidx, shk, shi);
@@ -462,7 +485,23 @@ __global__ void __launch_bounds__(512) k_aca(const AcaJob* jobs, int m, int cap,
     for (int i = wid; i < mi; i += nw) {
       double* row = jb.R + (size_t)i * m;
       const double ui = u[i];
-      for (int jj = lane; jj < mj; jj += 32) {
+      int jj = lane;
+      for (; jj + 96 < mj; jj += 128) {
+        double x0 = row[jj], x1 = row[jj + 32], x2 = row[jj + 64], x3 = row[jj + 96];
+        x0 -= ui * v[jj];
+        x1 -= ui * v[jj + 32];
+        x2 -= ui * v[jj + 64];
+        x3 -= ui * v[jj + 96];
+        row[jj] = x0;
+        row[jj + 32] = x1;
+        row[jj + 64] = x2;
+        row[jj + 96] = x3;
+        keymax_merge(akey, aidx, abs_key(x0), i * mj + jj);
+        keymax_merge(akey, aidx, abs_key(x1), i * mj + jj + 32);
+        keymax_merge(akey, aidx, abs_key(x2), i * mj + jj + 64);
+        keymax_merge(akey, aidx, abs_key(x3), i * mj + jj + 96);
+      }
+      for (; jj < mj; jj += 32) {
         const double x = row[jj] - ui * v[jj];
         row[jj] = x;
         keymax_merge(akey, aidx, abs_key(x), i * mj + jj);

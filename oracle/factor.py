@@ -377,7 +377,7 @@ def tlr_factor_truncated(Sigma: np.ndarray, geo_perm: np.ndarray, tile_sizes, a,
 def reorder_within_tiles(F: TLRFactor, a, b) -> TLRFactor:
     """Post-hoc within-tile reordering of a finished factor for new limits.
 
-    Not in the paper; derived from its factor structure (the survey's NEXT row):
+    Not in the paper; derived from its factor structure:
     the block reorderings of Section 3.3 also reorder variables within each
     diagonal block, and that within-block order depends on the limits, which a
     resident factor meets anew in every request.  For each tile j:

@@ -98,3 +98,23 @@ def test_tlr_arithmetic_factor_integrand_and_dense_entry(tl):
     exd = tl.parse_export(tl.tlrmvn_factor_export(Fd))
     assert np.array_equal(exd.perm, ODd.perm)
     assert np.abs(to_oracle_factor(exd).dense() - ODd.dense()).max() < 1e-7
+
+
+@pytest.mark.parametrize("schur", [0, 1])
+@pytest.mark.parametrize("reorder", [1, 2])
+def test_large_tiles_match_the_oracle(tl, reorder, schur):
+    # tiles of 256: each diagonal block's Cholesky factor runs in four 64-wide panels and its
+    # inverse a warp per column; the order, ranks and factor equal the oracle's (both arithmetics)
+    w = synth.small_workload(32, 256, 60 + reorder, tol=1e-6)
+    perm0, sizes = geometry.kd_order(w.xy, w.m)
+    Sig = geometry.covariance(w.xy, w.kernel, w.params, w.nugget)
+    if schur:
+        OF = ofactor.tlr_factor_truncated(Sig, perm0, sizes, w.a, w.b, w.tol, w.m, reorder)
+    else:
+        OF = ofactor.tlr_factor(Sig, perm0, sizes, w.a, w.b, w.tol, w.m, reorder)
+    F = tl.tlrmvn_factor_kernel(w.xy, w.kernel, w.params, w.nugget, w.a, w.b, w.m, w.tol, 0, reorder, schur=schur)
+    ex = tl.parse_export(tl.tlrmvn_factor_export(F))
+    assert np.array_equal(ex.perm, OF.perm)
+    GF = to_oracle_factor(ex)
+    assert ranks(GF) == {k: v for k, v in ranks(OF).items()}
+    assert np.abs(GF.dense() - OF.dense()).max() < 1e-7

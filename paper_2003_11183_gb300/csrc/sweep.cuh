@@ -45,13 +45,19 @@ constexpr int DIAG_SUB = 128;
 constexpr int DIAG_PAD = 32;
 
 // Shared memory of one block of `ns` samples: the sub-tile's y of each sample
-// (ns + 1 floats per variable), then the per-variable constants: (a, b, 1/B_vv)
-// as one float4 per variable (one 16-byte load), then the lattice generators.
+// (ns + 1 floats per variable), the sub-tile's transposed triangle (mt rows of mt
+// rounded up to 16 floats) and band copy (mt x 16; every per-variable load of B a
+// shared-memory broadcast),
+// then the per-variable constants: (a, b, 1/B_vv) as one float4 per variable (one
+// 16-byte load), then the lattice generators.
 __host__ __device__ inline size_t sweep_ys_bytes(int mt, int ns) {
   return ((size_t)mt * (ns + 1) * sizeof(float) + 15) / 16 * 16;
 }
+__host__ __device__ inline size_t sweep_bt_bytes(int mt) {
+  return (size_t)mt * ((mt + 15) & ~15) * sizeof(float) + (size_t)mt * 16 * sizeof(float);  // (+ the band copy)
+}
 __host__ __device__ inline size_t sweep_smem_bytes(int mt, int ns) {
-  return sweep_ys_bytes(mt, ns) + (size_t)mt * (sizeof(float4) + sizeof(uint64_t));
+  return sweep_ys_bytes(mt, ns) + sweep_bt_bytes(mt) + (size_t)mt * (sizeof(float4) + sizeof(uint64_t));
 }
 
 // FLAGS, fixed for a launch: SWEEP_PERIODIZE (tent-periodised lattice),
@@ -73,15 +79,24 @@ __global__ void k_diag_f32(DiagArgs32 p) {
   const int bd = blockDim.x, tid = threadIdx.x, ns = SPT * bd, ld = ns + 1;
   const int mt = p.mt;
   float* ys = reinterpret_cast<float*>(smem_raw);
-  float4* s_abi = reinterpret_cast<float4*>(smem_raw + sweep_ys_bytes(mt, ns));
+  const int wbt = (mt + 15) & ~15;  // row length of the staged triangle
+  float* s_bt = reinterpret_cast<float*>(smem_raw + sweep_ys_bytes(mt, ns));
+  float4* s_abi = reinterpret_cast<float4*>(smem_raw + sweep_ys_bytes(mt, ns) + sweep_bt_bytes(mt));
   uint64_t* s_q = reinterpret_cast<uint64_t*>(s_abi + mt);
   const int64_t c0 = (int64_t)blockIdx.x * ns;
   pdl_trigger();
-  // limits, diagonal and generators are not written by the preceding kernels
+  // limits, diagonal, triangle and generators are not written by the preceding kernels
   for (int t = tid; t < mt; t += bd) {
     s_abi[t] = make_float4(p.a[t], p.b[t], p.inv[t], 0.0f);
     s_q[t] = p.Q[p.coord0 + t];
   }
+  for (int t = tid; t < mt * (wbt >> 2); t += bd) {
+    const int u = t / (wbt >> 2), c = t - u * (wbt >> 2);
+    reinterpret_cast<float4*>(s_bt + u * wbt)[c] = __ldg(reinterpret_cast<const float4*>(p.BT + (int64_t)u * p.ldbt) + c);
+  }
+  float* s_band = s_bt + mt * wbt;  // s_band[v * 16 + k] = B[v+1+k][v]
+  for (int t = tid; t < mt * 4; t += bd)
+    reinterpret_cast<float4*>(s_band)[t] = __ldg(reinterpret_cast<const float4*>(p.band) + t);
   __syncthreads();
   pdl_wait();  // the limit shifts, y and log P of the preceding kernels
   bool act[SPT];
@@ -121,14 +136,14 @@ __global__ void k_diag_f32(DiagArgs32 p) {
 #pragma unroll
     for (int s = 0; s < SPT; s++) dnext[s] = Ds[s][v0];
     // sums over the sub-tile's earlier variables for the block's 16 variables
-    const float* bcol = p.BT + v0;
+    const float* bcol = s_bt + v0;
 #pragma unroll 2
     for (int u = 0; u < v0; u++) {
       float yu[SPT];
 #pragma unroll
       for (int s = 0; s < SPT; s++) yu[s] = ys[u * ld + tid + s * bd];
-      const float4* b4 = reinterpret_cast<const float4*>(bcol + (int64_t)u * p.ldbt);
-      const float4 q[4] = {__ldg(b4), __ldg(b4 + 1), __ldg(b4 + 2), __ldg(b4 + 3)};
+      const float4* b4 = reinterpret_cast<const float4*>(bcol + u * wbt);
+      const float4 q[4] = {b4[0], b4[1], b4[2], b4[3]};
 #pragma unroll
       for (int s = 0; s < SPT; s++)
 #pragma unroll
@@ -160,10 +175,10 @@ __global__ void k_diag_f32(DiagArgs32 p) {
       // special functions
       float bcur[DIAG_VB];
       {
-        const float4* b4 = reinterpret_cast<const float4*>(p.band + (int64_t)v * 16);
+        const float4* b4 = reinterpret_cast<const float4*>(s_band + v * 16);
 #pragma unroll
         for (int h = 0; h < 4; h++) {
-          const float4 x = __ldg(b4 + h);
+          const float4 x = b4[h];
           bcur[4 * h] = x.x;
           bcur[4 * h + 1] = x.y;
           bcur[4 * h + 2] = x.z;

@@ -37,7 +37,7 @@ METRIC = "MVN/MVT QMC sample-dims/sec at n=65,536 vs FP64 path; p50/p99 solve la
 # those sources are unchanged (otherwise null); the summaries with the capture
 # commands are under profiles/.
 TRAFFIC = {
-    "k_sweep_tc": {"bytes_per_sample_dim": 18.4388,
+    "k_sweep_tc": {"bytes_per_sample_dim": 18.6574,
                    "capture": "profiles/k_sweep_tc_n16384.md",
                    "files": ["paper_2003_11183_gb300/csrc/sweep_tc.cuh",
                              "paper_2003_11183_gb300/csrc/sweep.cuh",
@@ -45,7 +45,7 @@ TRAFFIC = {
                              "paper_2003_11183_gb300/csrc/tcgen05.cuh",
                              "paper_2003_11183_gb300/csrc/common.cuh",
                              "include/tlrmvn.h"],
-                   "sources": "3067221d8aead7c1a4a75beae6d0cee4496d5793482470818ec07d8b9bded46c"},
+                   "sources": "d15823eeb16dfafca824377a74d78c641719804b694886a5efffc4cfcd5b366d"},
 }
 
 

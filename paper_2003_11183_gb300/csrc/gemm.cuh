@@ -160,6 +160,113 @@ static __global__ void __launch_bounds__(256, 2) k_sgemm128(int M, int64_t N, in
   }
 }
 
+// The same for M <= 64 (the in-tile coupling of 64-variable sub-tiles): a 64 x 256 output tile
+// per block, 4 x 16 per thread (rows ty*4.., columns tx*4 + 64 h), so no half of the block's
+// rows is padding.  Same requirements as k_sgemm128.
+static __global__ void __launch_bounds__(256, 2) k_sgemm64(int M, int64_t N, int K, const float* __restrict__ A,
+                                                           int64_t lda, const float* __restrict__ B, int64_t ldb,
+                                                           float* __restrict__ C, int64_t ldc,
+                                                           const int32_t* __restrict__ rowmap, int accumulate) {
+  __shared__ __align__(16) float As[2][8][64];
+  __shared__ __align__(16) float Bs[2][8][256];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int64_t n0 = (int64_t)blockIdx.x * 256;
+  const int am = (tid & 127) >> 1, ak = (tid & 1) * 4;  // A (threads 0..127): row, first k of a float4
+  const int bk = tid >> 5, bn = (tid & 31) * 4;         // B: k row, first column of the first float4 (+128)
+  float acc[4][16];
+#pragma unroll
+  for (int i = 0; i < 4; i++)
+#pragma unroll
+    for (int j = 0; j < 16; j++) acc[i][j] = 0.0f;
+  float4 ra, rb0, rb1;
+  auto ldb4 = [&](const float* brow, int64_t gn) {
+    float4 r;
+    if (gn + 3 < N) {
+      r = *reinterpret_cast<const float4*>(brow + gn);
+    } else {
+      r.x = gn < N ? brow[gn] : 0.f;
+      r.y = gn + 1 < N ? brow[gn + 1] : 0.f;
+      r.z = gn + 2 < N ? brow[gn + 2] : 0.f;
+      r.w = 0.f;
+    }
+    return r;
+  };
+  auto load = [&](int k0) {
+    ra = (tid < 128 && am < M) ? *reinterpret_cast<const float4*>(A + (int64_t)am * lda + k0 + ak)
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float* brow = B + (int64_t)(k0 + bk) * ldb;
+    rb0 = ldb4(brow, n0 + bn);
+    rb1 = ldb4(brow, n0 + 128 + bn);
+  };
+  auto store = [&](int buf) {
+    if (tid < 128) {
+      As[buf][ak][am] = ra.x;
+      As[buf][ak + 1][am] = ra.y;
+      As[buf][ak + 2][am] = ra.z;
+      As[buf][ak + 3][am] = ra.w;
+    }
+    *reinterpret_cast<float4*>(&Bs[buf][bk][bn]) = rb0;
+    *reinterpret_cast<float4*>(&Bs[buf][bk][128 + bn]) = rb1;
+  };
+  load(0);
+  store(0);
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = 0; k0 < K; k0 += 8) {
+    const bool more = k0 + 8 < K;
+    if (more) load(k0 + 8);
+#pragma unroll
+    for (int kk = 0; kk < 8; kk++) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4]);
+      float b[16];
+#pragma unroll
+      for (int h = 0; h < 4; h++) {
+        const float4 bh = *reinterpret_cast<const float4*>(&Bs[buf][kk][64 * h + tx * 4]);
+        b[4 * h] = bh.x;
+        b[4 * h + 1] = bh.y;
+        b[4 * h + 2] = bh.z;
+        b[4 * h + 3] = bh.w;
+      }
+      const float a[4] = {a0.x, a0.y, a0.z, a0.w};
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 16; j++) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    if (more) {
+      store(buf ^ 1);
+      __syncthreads();
+      buf ^= 1;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    const int gm = ty * 4 + i;
+    if (gm >= M) continue;
+    const int64_t row = rowmap ? (int64_t)rowmap[gm] : (int64_t)gm;
+#pragma unroll
+    for (int h = 0; h < 4; h++) {
+      const int64_t gn = n0 + h * 64 + tx * 4;
+      float* c = C + row * ldc + gn;
+      const float* v = &acc[i][4 * h];
+      if (gn + 3 < N) {
+        float4 o = make_float4(v[0], v[1], v[2], v[3]);
+        if (accumulate) {
+          const float4 q = *reinterpret_cast<const float4*>(c);
+          o.x += q.x;
+          o.y += q.y;
+          o.z += q.z;
+          o.w += q.w;
+        }
+        *reinterpret_cast<float4*>(c) = o;
+      } else {
+        for (int q = 0; q < 3; q++)
+          if (gn + q < N) c[q] = accumulate ? c[q] + v[q] : v[q];
+      }
+    }
+  }
+}
+
 template <typename T>
 inline void gemm_nn(cudaStream_t st, int M, int64_t N, int64_t K, const T* A, int64_t lda, const T* B, int64_t ldb,
                     T* C, int64_t ldc, const int32_t* rowmap, int accumulate = 0) {
@@ -167,6 +274,11 @@ inline void gemm_nn(cudaStream_t st, int M, int64_t N, int64_t K, const T* A, in
   if constexpr (sizeof(T) == 4) {
     const bool aligned = (lda % 4 == 0) && (ldb % 4 == 0) && (ldc % 4 == 0) && (K % 8 == 0) && K > 0 &&
                          ((uintptr_t)A % 16 == 0) && ((uintptr_t)B % 16 == 0) && ((uintptr_t)C % 16 == 0);
+    if (aligned && M <= 64) {
+      k_sgemm64<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(M, N, (int)K, (const float*)A, lda, (const float*)B, ldb,
+                                                             (float*)C, ldc, rowmap, accumulate);
+      return;
+    }
     if (aligned) {
       dim3 grid((unsigned)((N + 127) / 128), (unsigned)((M + 127) / 128));
       k_sgemm128<<<grid, 256, 0, st>>>(M, N, (int)K, (const float*)A, lda, (const float*)B, ldb, (float*)C, ldc,

@@ -345,6 +345,14 @@ int ensure_float_tiles(Factor& F, cudaStream_t st) {
   return TLRMVN_OK;
 }
 
+// out[v * ld8 + k] = U[v * kr + k] for k < kr, else 0 (one row tile's U, float, padded ranks)
+__global__ void k_pad_u32(const double* U, int64_t kr, int64_t ld8, int64_t cnt, float* out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= cnt) return;
+  const int64_t v = t / ld8, k = t % ld8;
+  out[t] = k < kr ? (float)U[v * kr + k] : 0.0f;
+}
+
 // Makes the copies a precision needs; the first caller makes them (and waits for
 // them) under the factor's lock, so concurrent streams never see a partial copy.
 static int ensure_copies_locked(Factor& F, int precision, cudaStream_t st);
@@ -502,9 +510,18 @@ static int ensure_copies_locked(Factor& F, int precision, cudaStream_t st) {
   if (precision == TLRMVN_FP32 && !(F.U32 && F.V32) && nu) {
     dfree(F.U32);
     dfree(F.V32);
-    TLR_CHECK(dalloc(&F.U32, nu));
+    // U32: each row tile's U with its rank count padded to a multiple of 8 (zero columns), so
+    // that the shift product takes the vectorised float GEMM
+    F.u32_off.assign(F.r + 1, 0);
+    for (int i = 0; i < F.r; i++) F.u32_off[i + 1] = F.u32_off[i] + (int64_t)F.m * ((F.krow(i) + 7) / 8 * 8);
+    TLR_CHECK(dalloc(&F.U32, (size_t)std::max<int64_t>(F.u32_off[F.r], 1)));
     TLR_CHECK(dalloc(&F.V32, nu));
-    k_convert<double, float><<<blocks_for(nu, 256), 256, 0, st>>>(F.Ucat, F.U32, nu);
+    for (int i = 0; i < F.r; i++) {
+      const int64_t kr = F.krow(i), ld8 = (kr + 7) / 8 * 8, cnt = (int64_t)F.m * ld8;
+      if (cnt)
+        k_pad_u32<<<blocks_for(cnt, 256), 256, 0, st>>>(F.Ucat + (size_t)F.m * F.krow_off[i], kr, ld8, cnt,
+                                                        F.U32 + F.u32_off[i]);
+    }
     k_convert<double, float><<<blocks_for(nu, 256), 256, 0, st>>>(F.Vcat, F.V32, nu);
   }
   if ((precision == TLRMVN_BF16_SHIFT || precision == TLRMVN_FP16_SHIFT) && !bf16_ready(F)) {
@@ -938,7 +955,10 @@ static int run_chunks(Factor& F, const T* Bt, const T* Ut, const T* Vt, const Li
   YT* Y = nullptr;
   double* rs = nullptr;
   float* rs32 = nullptr;
-  TLR_CHECK(sc.get(&W, (size_t)F.ktot * C));
+  // (float: eight spare rows and a zeroed start, since a tile's shift reads its rank rows
+  // rounded up to 8, past rows a projection may not have written yet)
+  TLR_CHECK(sc.get(&W, (size_t)(F.ktot + (f32 ? 8 : 0)) * C));
+  if (f32) TLR_CUDA(cudaMemsetAsync(W, 0, (size_t)(F.ktot + 8) * C * sizeof(T), st));
   TLR_CHECK(sc.get(&Dl, (size_t)m * C));
   TLR_CHECK(sc.get(&Y, (size_t)m * C));
   const bool mvt = std::isfinite(nu);
@@ -966,8 +986,13 @@ static int run_chunks(Factor& F, const T* Bt, const T* Ut, const T* Vt, const Li
       const T* Delta = nullptr;
       if (Kr > 0) {
         pf.begin(TLRMVN_KC_SHIFT);
-        gemm_nn<T>(st, mt, Cc, Kr, Ut + (size_t)m * F.krow_off[i], Kr, W + (size_t)F.krow_off[i] * C, C, Dl, C,
-                   nullptr);
+        if constexpr (sizeof(T) == 4) {
+          const int64_t ld8 = (Kr + 7) / 8 * 8;
+          gemm_nn<T>(st, mt, Cc, ld8, Ut + F.u32_off[i], ld8, W + (size_t)F.krow_off[i] * C, C, Dl, C, nullptr);
+        } else {
+          gemm_nn<T>(st, mt, Cc, Kr, Ut + (size_t)m * F.krow_off[i], Kr, W + (size_t)F.krow_off[i] * C, C, Dl, C,
+                     nullptr);
+        }
         pf.end();
         Delta = Dl;
       }

@@ -37,7 +37,7 @@ METRIC = "MVN/MVT QMC sample-dims/sec at n=65,536 vs FP64 path; p50/p99 solve la
 # those sources are unchanged (otherwise null); the summaries with the capture
 # commands are under profiles/.
 TRAFFIC = {
-    "k_sweep_tc": {"bytes_per_sample_dim": 18.6574,
+    "k_sweep_tc": {"bytes_per_sample_dim": 20.5461,
                    "capture": "profiles/k_sweep_tc_n16384.md",
                    "files": ["paper_2003_11183_gb300/csrc/sweep_tc.cuh",
                              "paper_2003_11183_gb300/csrc/sweep.cuh",
@@ -45,7 +45,7 @@ TRAFFIC = {
                              "paper_2003_11183_gb300/csrc/tcgen05.cuh",
                              "paper_2003_11183_gb300/csrc/common.cuh",
                              "include/tlrmvn.h"],
-                   "sources": "d15823eeb16dfafca824377a74d78c641719804b694886a5efffc4cfcd5b366d"},
+                   "sources": "e327825f030652e11fcece06316c89b0ca9584160b4201398fbf8186fecb3e2a"},
 }
 
 
@@ -291,6 +291,9 @@ def load_workload(args):
     if args.points:
         w.n_points = args.points
     if args.shifts:
+        if args.shifts > len(w.shifts):  # more shifts than the workload draws: append fresh ones
+            extra = synth.lattice_shifts(args.shifts - len(w.shifts), w.shifts.shape[1], 3100 + args.workload)
+            w.shifts = np.concatenate([w.shifts, extra])
         w.n_shifts = args.shifts
         w.shifts = w.shifts[:args.shifts]
     if args.reorder >= 0:

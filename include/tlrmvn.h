@@ -350,7 +350,7 @@ int tlrmvn_estimate_pooled(const double* per_shift, int64_t count, double* logp,
  * the library, TLRMVN_NOALLOC_MAX_SHIFTS doubles, held by every GPU that loads
  * the library until the process exits.  n_shifts above that limit returns
  * TLRMVN_E_INVAL.  The first call on a device looks up the array's device
- * address; make that first call before any stream capture.  All calls share
+ * address.  All calls share
  * the array: calls whose work overlaps on the GPU (different streams, or other
  * threads) race on it and must be serialised by the caller. */
 #define TLRMVN_NOALLOC_MAX_SHIFTS 65536

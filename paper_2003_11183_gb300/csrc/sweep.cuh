@@ -94,9 +94,15 @@ __global__ void k_diag_f32(DiagArgs32 p) {
     const int u = t / (wbt >> 2), c = t - u * (wbt >> 2);
     reinterpret_cast<float4*>(s_bt + u * wbt)[c] = __ldg(reinterpret_cast<const float4*>(p.BT + (int64_t)u * p.ldbt) + c);
   }
-  float* s_band = s_bt + mt * wbt;  // s_band[v * 16 + k] = B[v+1+k][v]
-  for (int t = tid; t < mt * 4; t += bd)
-    reinterpret_cast<float4*>(s_band)[t] = __ldg(reinterpret_cast<const float4*>(p.band) + t);
+  // s_band[v * 16 + k] = B[v+1+k][v] for odd v; for even v moved one place down
+  // (B[v+2+k][v] at k < 14) with B[v+1][v] at 14, so that the pair update of the
+  // sweep below reads aligned pairs
+  float* s_band = s_bt + mt * wbt;
+  for (int t = tid; t < mt * 16; t += bd) {
+    const int v = t >> 4, kk = t & 15;
+    const float* src = p.band + (int64_t)v * 16;
+    s_band[t] = (v & 1) ? __ldg(src + kk) : (kk < 14 ? __ldg(src + kk + 1) : (kk == 14 ? __ldg(src) : 0.0f));
+  }
   __syncthreads();
   pdl_wait();  // the limit shifts, y and log P of the preceding kernels
   bool act[SPT];
@@ -123,13 +129,16 @@ __global__ void k_diag_f32(DiagArgs32 p) {
   }
   for (int v0 = 0; v0 < mt; v0 += DIAG_VB) {
     const int nb = min(DIAG_VB, mt - v0);
-    float acc[SPT][DIAG_VB], dl[SPT][DIAG_VB];
+    // acc[s][i] = sums of the block's variables 2i (x) and 2i + 1 (y), as pairs for the
+    // paired float32 FMAs (each pair FMA rounds as two fmaf)
+    float2 acc[SPT][DIAG_VB / 2], dl[SPT][DIAG_VB / 2];
 #pragma unroll
     for (int s = 0; s < SPT; s++)
 #pragma unroll
-      for (int j = 0; j < DIAG_VB; j++) {
-        dl[s][j] = (p.Delta && j < nb) ? p.Delta[(int64_t)(v0 + j) * p.ldd + cs[s]] : 0.0f;
-        acc[s][j] = 0.0f;
+      for (int j = 0; j < DIAG_VB / 2; j++) {
+        dl[s][j].x = (p.Delta && 2 * j < nb) ? p.Delta[(int64_t)(v0 + 2 * j) * p.ldd + cs[s]] : 0.0f;
+        dl[s][j].y = (p.Delta && 2 * j + 1 < nb) ? p.Delta[(int64_t)(v0 + 2 * j + 1) * p.ldd + cs[s]] : 0.0f;
+        acc[s][j] = make_float2(0.0f, 0.0f);
       }
     // lattice offsets of the block's first variable
     uint64_t dnext[SPT];
@@ -145,58 +154,38 @@ __global__ void k_diag_f32(DiagArgs32 p) {
       const float4* b4 = reinterpret_cast<const float4*>(bcol + u * wbt);
       const float4 q[4] = {b4[0], b4[1], b4[2], b4[3]};
 #pragma unroll
-      for (int s = 0; s < SPT; s++)
+      for (int s = 0; s < SPT; s++) {
+        const float2 yy = make_float2(yu[s], yu[s]);
 #pragma unroll
         for (int h = 0; h < 4; h++) {
-          acc[s][4 * h] = fmaf(q[h].x, yu[s], acc[s][4 * h]);
-          acc[s][4 * h + 1] = fmaf(q[h].y, yu[s], acc[s][4 * h + 1]);
-          acc[s][4 * h + 2] = fmaf(q[h].z, yu[s], acc[s][4 * h + 2]);
-          acc[s][4 * h + 3] = fmaf(q[h].w, yu[s], acc[s][4 * h + 3]);
+          acc[s][2 * h] = __ffma2_rn(make_float2(q[h].x, q[h].y), yy, acc[s][2 * h]);
+          acc[s][2 * h + 1] = __ffma2_rn(make_float2(q[h].z, q[h].w), yy, acc[s][2 * h + 1]);
         }
+      }
     }
 #pragma unroll
     for (int s = 0; s < SPT; s++)
 #pragma unroll
-      for (int j = 0; j < DIAG_VB; j++) acc[s][j] += dl[s][j];
-#pragma unroll 1
-    for (int j = 0; j < nb; j++) {
+      for (int j = 0; j < DIAG_VB / 2; j++) acc[s][j] = __fadd2_rn(acc[s][j], dl[s][j]);
+    // one variable of eq. 2 for each slot: sum[s] = its sum over the earlier variables
+    // and the shifts; returns its y (also stored for the later variables and blocks)
+    auto step = [&](int j, const float (&sum)[SPT], float (&y)[SPT]) {
       const int v = v0 + j;
       const float4 abi = s_abi[v];
       const float av = abi.x, bv = abi.y, iv = abi.z;
       const uint64_t qv = s_q[v];
-      uint64_t dv[SPT];
 #pragma unroll
       for (int s = 0; s < SPT; s++) {
-        dv[s] = dnext[s];
+        const uint64_t dv = dnext[s];
         dnext[s] = Ds[s][(j + 1 < nb) ? v + 1 : v];  // next variable's offset (the last one reloads its own)
-      }
-      // window column B[v+1..v+15][v] (four 16-byte loads of the band copy),
-      // loaded before the step so that the loads are in flight during its
-      // special functions
-      float bcur[DIAG_VB];
-      {
-        const float4* b4 = reinterpret_cast<const float4*>(s_band + v * 16);
-#pragma unroll
-        for (int h = 0; h < 4; h++) {
-          const float4 x = b4[h];
-          bcur[4 * h] = x.x;
-          bcur[4 * h + 1] = x.y;
-          bcur[4 * h + 2] = x.z;
-          bcur[4 * h + 3] = x.w;
-        }
-      }
-      float y[SPT];
-#pragma unroll
-      for (int s = 0; s < SPT; s++) {
-        const float sum = acc[s][0];  // shifts + earlier variables, for variable v
-        const float bt = (bv * rs[s] - sum) * iv;
+        const float bt = (bv * rs[s] - sum[s]) * iv;
         float w, wc;
-        lattice_wf((uint64_t)ks[s] * qv + dv[s], PER ? 1 : 0, w, wc);
+        lattice_wf((uint64_t)ks[s] * qv + dv, PER ? 1 : 0, w, wc);
         float f, la;
         if (ONE) {
           sov_step_f32_upper(bt, w, wc, f, la, y[s]);
         } else {
-          const float at = (av * rs[s] - sum) * iv;
+          const float at = (av * rs[s] - sum[s]) * iv;
           sov_step_f32_prod(at, bt, w, wc, f, la, y[s]);
         }
         lsum[s] += la;
@@ -207,13 +196,49 @@ __global__ void k_diag_f32(DiagArgs32 p) {
         ys[v * ld + tid + s * bd] = y[s];
         if (YV && act[s]) p.Yv[(int64_t)v * p.ldyv + cs[s]] = y[s];
       }
-      // window shift: acc[i] <- acc[i+1] + B[v+1+i][v] y
+    };
+    // the block's variables in pairs (v even, v + 1): after y_v the pair's second sum
+    // takes B[v+1][v] y_v and the window moves two places, the later sums taking
+    // B[v+2+k][v] y_v; after y_{v+1} they take B[v+2+k][v+1] y_{v+1} (k < 14: the rest
+    // of the block).  Each sum receives its terms in the order of the variables.  The
+    // window columns are loaded before the steps, so that the loads are in flight
+    // during their special functions.
+#pragma unroll 1
+    for (int j = 0; j < nb; j += 2) {
+      const int v = v0 + j;
+      const float4* b4 = reinterpret_cast<const float4*>(s_band + v * 16);
+      const float4 q[4] = {b4[0], b4[1], b4[2], b4[3]};
+      float sum[SPT], y0[SPT];
 #pragma unroll
-      for (int i = 0; i < DIAG_VB - 1; i++)
+      for (int s = 0; s < SPT; s++) sum[s] = acc[s][0].x;
+      step(j, sum, y0);
+      if (j + 1 == nb) break;  // (a ragged block's last variable: the window is not needed)
+      const float4* c4 = reinterpret_cast<const float4*>(s_band + (v + 1) * 16);
+      const float4 r[4] = {c4[0], c4[1], c4[2], c4[3]};
 #pragma unroll
-        for (int s = 0; s < SPT; s++) acc[s][i] = fmaf(bcur[i], y[s], acc[s][i + 1]);
+      for (int s = 0; s < SPT; s++) {
+        sum[s] = fmaf(q[3].z, y0[s], acc[s][0].y);
+        const float2 yy = make_float2(y0[s], y0[s]);
 #pragma unroll
-      for (int s = 0; s < SPT; s++) acc[s][DIAG_VB - 1] = 0.0f;
+        for (int h = 0; h < 3; h++) {
+          acc[s][2 * h] = __ffma2_rn(make_float2(q[h].x, q[h].y), yy, acc[s][2 * h + 1]);
+          acc[s][2 * h + 1] = __ffma2_rn(make_float2(q[h].z, q[h].w), yy, acc[s][2 * h + 2]);
+        }
+        acc[s][6] = __ffma2_rn(make_float2(q[3].x, q[3].y), yy, acc[s][7]);
+        acc[s][7] = make_float2(0.0f, 0.0f);
+      }
+      float y1[SPT];
+      step(j + 1, sum, y1);
+#pragma unroll
+      for (int s = 0; s < SPT; s++) {
+        const float2 yy = make_float2(y1[s], y1[s]);
+#pragma unroll
+        for (int h = 0; h < 3; h++) {
+          acc[s][2 * h] = __ffma2_rn(make_float2(r[h].x, r[h].y), yy, acc[s][2 * h]);
+          acc[s][2 * h + 1] = __ffma2_rn(make_float2(r[h].z, r[h].w), yy, acc[s][2 * h + 1]);
+        }
+        acc[s][6] = __ffma2_rn(make_float2(r[3].x, r[3].y), yy, acc[s][6]);
+      }
     }
   }
 #pragma unroll

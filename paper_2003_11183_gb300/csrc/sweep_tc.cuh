@@ -273,14 +273,22 @@ __device__ __forceinline__ bool stc_tile(const CUtensorMap* mapY, const CUtensor
         reinterpret_cast<float4*>(s_bt + u * STC_SUB)[c] =
             __ldg(reinterpret_cast<const float4*>(d.BT + (int64_t)(q0 + u) * d.ldbt + q0) + c);
       }
-      for (int t = tid; t < mq * 4; t += STC_NS)
-        reinterpret_cast<float4*>(s_band)[t] = __ldg(reinterpret_cast<const float4*>(d.band + (int64_t)q0 * 16) + t);
+      // band rows of odd variables as stored (B[v+1+k][v] at k); of even variables moved
+      // one place down (B[v+2+k][v] at k < 14) with B[v+1][v] at 14, so that the pair
+      // update of the sweep below reads aligned pairs
+      for (int t = tid; t < mq * 16; t += STC_NS) {
+        const int v = t >> 4, kk = t & 15;
+        const float* src = d.band + (int64_t)(q0 + v) * 16;
+        s_band[t] = (v & 1) ? __ldg(src + kk) : (kk < 14 ? __ldg(src + kk + 1) : (kk == 14 ? __ldg(src) : 0.0f));
+      }
     }
     __syncthreads();
 
     for (int v0 = 0; v0 < mq; v0 += DIAG_VB) {
       const int nb = min(DIAG_VB, mq - v0);
-      float acc[SPT][DIAG_VB];
+      // acc[s][i] = sums of the block's variables 2i (x) and 2i + 1 (y), as pairs for the
+      // paired float32 FMAs (each pair FMA rounds as two fmaf)
+      float2 acc[SPT][DIAG_VB / 2];
 #pragma unroll
       for (int s = 0; s < SPT; s++) {
         if (q0 > 0 || p.kr > 0) {
@@ -293,10 +301,12 @@ __device__ __forceinline__ bool stc_tile(const CUtensorMap* mapY, const CUtensor
               : "r"(tl + (uint32_t)(STC_SUB * s + v0)));
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-          for (int j = 0; j < DIAG_VB; j++) acc[s][j] = F16 ? __uint_as_float(r[j]) * p.tscale : __uint_as_float(r[j]);
+          for (int j = 0; j < DIAG_VB / 2; j++)
+            acc[s][j] = F16 ? make_float2(__uint_as_float(r[2 * j]) * p.tscale, __uint_as_float(r[2 * j + 1]) * p.tscale)
+                            : make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
         } else {
 #pragma unroll
-          for (int j = 0; j < DIAG_VB; j++) acc[s][j] = 0.0f;
+          for (int j = 0; j < DIAG_VB / 2; j++) acc[s][j] = make_float2(0.0f, 0.0f);
         }
       }
       uint64_t dnext[SPT];
@@ -319,35 +329,34 @@ __device__ __forceinline__ bool stc_tile(const CUtensorMap* mapY, const CUtensor
 #pragma unroll
           for (int s = 0; s < SPT; s++) {
             const float yu = __uint_as_float(r[s][uu]);
+            const float2 yy = make_float2(yu, yu);
 #pragma unroll
             for (int h = 0; h < 4; h++) {
-              acc[s][4 * h] = fmaf(q[h].x, yu, acc[s][4 * h]);
-              acc[s][4 * h + 1] = fmaf(q[h].y, yu, acc[s][4 * h + 1]);
-              acc[s][4 * h + 2] = fmaf(q[h].z, yu, acc[s][4 * h + 2]);
-              acc[s][4 * h + 3] = fmaf(q[h].w, yu, acc[s][4 * h + 3]);
+              acc[s][2 * h] = __ffma2_rn(make_float2(q[h].x, q[h].y), yy, acc[s][2 * h]);
+              acc[s][2 * h + 1] = __ffma2_rn(make_float2(q[h].z, q[h].w), yy, acc[s][2 * h + 1]);
             }
           }
         }
       }
-#pragma unroll 1
-      for (int j = 0; j < nb; j++) {
+      // one variable of eq. 2 for each slot: sum[s] = its sum over the earlier variables
+      // and the shifts; returns its y and stores it into this lane's column v (whose sum
+      // has been read), warp-wide after the step's divergent branches
+      auto step = [&](int j, const float (&sum)[SPT], float (&y)[SPT]) {
         const int v = v0 + j;
         const float4 abi = s_abi[v];
         const uint64_t qv = s_q[v];
         const int vn = q0 + ((j + 1 < nb) ? v + 1 : v);  // next variable (the last one reloads its own)
-        float y[SPT];
 #pragma unroll
         for (int s = 0; s < SPT; s++) {
           const uint64_t dv = dnext[s];
           dnext[s] = Ds[s][vn];
-          const float sum = acc[s][0];  // shifts + coupling + earlier variables, for variable v
-          const float bt = (abi.y * rs[s] - sum) * abi.z;
+          const float bt = (abi.y * rs[s] - sum[s]) * abi.z;
           float w, wc, f, la;
           lattice_wf((uint64_t)ks[s] * qv + dv, PER ? 1 : 0, w, wc);
           if (ONE) {
             sov_step_f32_upper(bt, w, wc, f, la, y[s]);
           } else {
-            const float at = (abi.x * rs[s] - sum) * abi.z;
+            const float at = (abi.x * rs[s] - sum[s]) * abi.z;
             sov_step_f32_prod(at, bt, w, wc, f, la, y[s]);
           }
           lsum[s] += la;
@@ -356,24 +365,56 @@ __device__ __forceinline__ bool stc_tile(const CUtensorMap* mapY, const CUtensor
           pe[s] += (pb >> 23) - 127;
           prod[s] = __int_as_float((pb & 0x007FFFFF) | 0x3F800000);
         }
-        // y into this lane's column v of each slot (its coupling has been read); the
-        // stores are warp-wide ones, after the step's divergent branches
         __syncwarp();
 #pragma unroll
         for (int s = 0; s < SPT; s++)
           asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(tl + (uint32_t)(STC_SUB * s + v)),
                        "r"(__float_as_uint(y[s]))
                        : "memory");
-        // window shift: acc[i] <- acc[i+1] + B[v+1+i][v] y, the column from the band copy
-        const float4* b4 = reinterpret_cast<const float4*>(s_band + v * 16);
-        const float4 q[4] = {b4[0], b4[1], b4[2], b4[3]};
-        const float bcur[DIAG_VB] = {q[0].x, q[0].y, q[0].z, q[0].w, q[1].x, q[1].y, q[1].z, q[1].w,
-                                     q[2].x, q[2].y, q[2].z, q[2].w, q[3].x, q[3].y, q[3].z, q[3].w};
+      };
+      // the block's variables in pairs (v even, v + 1): after y_v the pair's second sum
+      // takes B[v+1][v] y_v and the window moves two places, the later sums taking
+      // B[v+2+k][v] y_v; after y_{v+1} they take B[v+2+k][v+1] y_{v+1} (k < 14: the
+      // rest of the block).  Each sum receives its terms in the order of the variables.
+#pragma unroll 1
+      for (int j = 0; j < nb; j += 2) {
+        const int v = v0 + j;
+        float sum[SPT], y0[SPT];
 #pragma unroll
-        for (int s = 0; s < SPT; s++) {
+        for (int s = 0; s < SPT; s++) sum[s] = acc[s][0].x;
+        step(j, sum, y0);
+        if (j + 1 == nb) break;  // (a ragged block's last variable: the window is not needed)
+        {
+          const float4* b4 = reinterpret_cast<const float4*>(s_band + v * 16);
+          const float4 q[4] = {b4[0], b4[1], b4[2], b4[3]};
 #pragma unroll
-          for (int i = 0; i < DIAG_VB - 1; i++) acc[s][i] = fmaf(bcur[i], y[s], acc[s][i + 1]);
-          acc[s][DIAG_VB - 1] = 0.0f;
+          for (int s = 0; s < SPT; s++) {
+            sum[s] = fmaf(q[3].z, y0[s], acc[s][0].y);
+            const float2 yy = make_float2(y0[s], y0[s]);
+#pragma unroll
+            for (int h = 0; h < 3; h++) {
+              acc[s][2 * h] = __ffma2_rn(make_float2(q[h].x, q[h].y), yy, acc[s][2 * h + 1]);
+              acc[s][2 * h + 1] = __ffma2_rn(make_float2(q[h].z, q[h].w), yy, acc[s][2 * h + 2]);
+            }
+            acc[s][6] = __ffma2_rn(make_float2(q[3].x, q[3].y), yy, acc[s][7]);
+            acc[s][7] = make_float2(0.0f, 0.0f);
+          }
+        }
+        float y1[SPT];
+        step(j + 1, sum, y1);
+        {
+          const float4* b4 = reinterpret_cast<const float4*>(s_band + (v + 1) * 16);
+          const float4 q[4] = {b4[0], b4[1], b4[2], b4[3]};
+#pragma unroll
+          for (int s = 0; s < SPT; s++) {
+            const float2 yy = make_float2(y1[s], y1[s]);
+#pragma unroll
+            for (int h = 0; h < 3; h++) {
+              acc[s][2 * h] = __ffma2_rn(make_float2(q[h].x, q[h].y), yy, acc[s][2 * h]);
+              acc[s][2 * h + 1] = __ffma2_rn(make_float2(q[h].z, q[h].w), yy, acc[s][2 * h + 1]);
+            }
+            acc[s][6] = __ffma2_rn(make_float2(q[3].x, q[3].y), yy, acc[s][6]);
+          }
         }
       }
       asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");

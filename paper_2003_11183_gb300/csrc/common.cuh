@@ -104,9 +104,10 @@ struct Factor {
   float* band32 = nullptr;
   int64_t ldbt = 0;
   float* B32 = nullptr;
-  float* U32 = nullptr;  // row tile i at u32_off[i]: m x (Krow_i rounded up to 8), zero-padded columns
+  float* U32 = nullptr;  // row tile i at u32_off[i]: (Krow_i rounded up to 8) x m, U_i transposed, zero rows
   std::vector<int64_t> u32_off;
-  float* V32 = nullptr;
+  float* V32 = nullptr;  // column tile i at v32_off[i]: m x (Kcol_i rounded up to 4), V_i, zero columns
+  std::vector<int64_t> v32_off;
   // bf16 operands of the tensor-core shifts (K-major, padded for TMA):
   //   U16   (r*m) x kmax16: row i*m+v holds row v of Ucat_i, zero beyond Krow_i
   //   V16   ktot x my16:    Vcat rows, zero beyond m

@@ -64,84 +64,102 @@ __global__ void __launch_bounds__(256) k_gemm_nn(int M, int64_t N, int64_t K, co
   }
 }
 
-// float32 C = A B (+ C): 128 x 128 output tile per 256-thread block, 8 x 8 per
-// thread (two 4 x 4 quadrants so that shared-memory reads are float4), K in
-// steps of 8 with the next step's tile prefetched into registers while the
-// current one is multiplied (shared memory double-buffered, one barrier per step).
-// Requires lda, ldb, ldc multiples of 4, 16-byte aligned A, B, C and K a multiple of 8.
-static __global__ void __launch_bounds__(256, 2) k_sgemm128(int M, int64_t N, int K, const float* __restrict__ A, int64_t lda,
-                                                  const float* __restrict__ B, int64_t ldb, float* __restrict__ C,
-                                                  int64_t ldc, const int32_t* __restrict__ rowmap, int accumulate) {
-  __shared__ __align__(16) float As[2][8][128];
-  __shared__ __align__(16) float Bs[2][8][128];
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int m0 = blockIdx.y * 128;
+// ---- float32 C = At^T B (+ C) with the first operand stored k-major -------------------
+// At is K x M (row k holds column k of the product's first factor), so that a k-step of
+// it is a plain copy: the tiles of At and B go by cp.async straight into a ring of four
+// shared-memory stages (no registers held for the copies, three steps in flight while
+// one is multiplied).  The multiply is k_sgemm's: a BM x 128 output tile per block of
+// 2 BM threads, 8 x 8 outputs per thread as paired float32 FMAs.  Requires lda, ldb, ldc
+// multiples of 4, 16-byte aligned At, B, C and K a multiple of 8; the ragged columns of
+// the last row and column blocks are zero-filled copies.  (BM = 128: the shifts and
+// projections; BM = 64: the in-tile coupling of 64-variable sub-tiles, so that no half
+// of the block's rows is padding and a launch over the samples has twice the blocks.)
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+               "l"(gmem), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int NPEND>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(NPEND) : "memory");
+}
+
+template <int BM>
+__global__ void __launch_bounds__(2 * BM) k_sgemm_t(int M, int64_t N, int K, const float* __restrict__ At,
+                                                    int64_t lda, const float* __restrict__ B, int64_t ldb,
+                                                    float* __restrict__ C, int64_t ldc,
+                                                    const int32_t* __restrict__ rowmap, int accumulate) {
+  static_assert(BM == 64 || BM == 128, "block rows");
+  constexpr int NT = 2 * BM;    // threads; one float4 of the At tile (8 x BM) each
+  constexpr int BL = 256 / NT;  // float4 of the B tile (8 x 128) per thread
+  constexpr int S = 4;          // stages
+  __shared__ __align__(16) float As[S][8][BM];
+  __shared__ __align__(16) float Bs[S][8][128];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;  // ty < BM / 8
+  const int m0 = blockIdx.y * BM;
   const int64_t n0 = (int64_t)blockIdx.x * 128;
-  const int am = tid >> 1, ak = (tid & 1) * 4;   // A: row, first k of a float4
-  const int bk = tid >> 5, bn = (tid & 31) * 4;  // B: k row, first column of a float4
-  float acc[8][8];
+  float2 acc[8][4];  // acc[i][j]: columns 2j, 2j + 1 of row i
 #pragma unroll
   for (int i = 0; i < 8; i++)
 #pragma unroll
-    for (int j = 0; j < 8; j++) acc[i][j] = 0.0f;
-  float4 ra, rb;
-  auto load = [&](int k0) {
-    const int gm = m0 + am;
-    ra = (gm < M) ? *reinterpret_cast<const float4*>(A + (int64_t)gm * lda + k0 + ak) : make_float4(0.f, 0.f, 0.f, 0.f);
-    const int64_t gn = n0 + bn;
-    const float* brow = B + (int64_t)(k0 + bk) * ldb;
-    if (gn + 3 < N) {
-      rb = *reinterpret_cast<const float4*>(brow + gn);
-    } else {
-      rb.x = gn < N ? brow[gn] : 0.f;
-      rb.y = gn + 1 < N ? brow[gn + 1] : 0.f;
-      rb.z = gn + 2 < N ? brow[gn + 2] : 0.f;
-      rb.w = 0.f;
+    for (int j = 0; j < 4; j++) acc[i][j] = make_float2(0.0f, 0.0f);
+  // the copies of k-step ks into stage buf
+  auto issue = [&](int ks, int buf) {
+    const int k0 = ks * 8;
+    {
+      const int kk = tid / (BM / 4), mm = (tid % (BM / 4)) * 4, gm = m0 + mm;
+      const int bytes = gm + 3 < M ? 16 : (gm < M ? 4 * (M - gm) : 0);
+      cp_async16(&As[buf][kk][mm], bytes ? At + (int64_t)(k0 + kk) * lda + gm : At, bytes);
+    }
+#pragma unroll
+    for (int l = 0; l < BL; l++) {
+      const int e = tid + NT * l, kk = e >> 5, nn = (e & 31) * 4;
+      const int64_t gn = n0 + nn;
+      const int bytes = gn + 3 < N ? 16 : (gn < N ? (int)(4 * (N - gn)) : 0);
+      cp_async16(&Bs[buf][kk][nn], bytes ? B + (int64_t)(k0 + kk) * ldb + gn : B, bytes);
     }
   };
-  auto store = [&](int buf) {
-    As[buf][ak][am] = ra.x;
-    As[buf][ak + 1][am] = ra.y;
-    As[buf][ak + 2][am] = ra.z;
-    As[buf][ak + 3][am] = ra.w;
-    *reinterpret_cast<float4*>(&Bs[buf][bk][bn]) = rb;
-  };
-  load(0);
-  store(0);
-  __syncthreads();
-  int buf = 0;
-  for (int k0 = 0; k0 < K; k0 += 8) {
-    const bool more = k0 + 8 < K;
-    if (more) load(k0 + 8);
+  const int nk = K / 8;
+#pragma unroll
+  for (int s = 0; s < S - 1; s++) {
+    if (s < nk) issue(s, s);
+    cp_async_commit();
+  }
+  for (int ks = 0; ks < nk; ks++) {
+    cp_async_wait<S - 2>();  // this thread's copies of step ks have landed
+    __syncthreads();         // everyone's have, and everyone is done with step ks - 1's stage
+    if (ks + S - 1 < nk) issue(ks + S - 1, (ks + S - 1) % S);
+    cp_async_commit();
+    const int buf = ks % S;
 #pragma unroll
     for (int kk = 0; kk < 8; kk++) {
       const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4]);
-      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][64 + ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][BM / 2 + ty * 4]);
       const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
       const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][64 + tx * 4]);
       const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+      const float2 b[4] = {make_float2(b0.x, b0.y), make_float2(b0.z, b0.w), make_float2(b1.x, b1.y),
+                           make_float2(b1.z, b1.w)};
 #pragma unroll
-      for (int i = 0; i < 8; i++)
+      for (int i = 0; i < 8; i++) {
+        const float2 aa = make_float2(a[i], a[i]);
 #pragma unroll
-        for (int j = 0; j < 8; j++) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-    }
-    if (more) {
-      store(buf ^ 1);
-      __syncthreads();
-      buf ^= 1;
+        for (int j = 0; j < 4; j++) acc[i][j] = __ffma2_rn(aa, b[j], acc[i][j]);
+      }
     }
   }
+  cp_async_wait<0>();  // (only empty groups remain)
 #pragma unroll
   for (int i = 0; i < 8; i++) {
-    const int gm = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
+    const int gm = m0 + (i < 4 ? ty * 4 + i : BM / 2 + ty * 4 + i - 4);
     if (gm >= M) continue;
     const int64_t row = rowmap ? (int64_t)rowmap[gm] : (int64_t)gm;
 #pragma unroll
     for (int h = 0; h < 2; h++) {
       const int64_t gn = n0 + h * 64 + tx * 4;
       float* c = C + row * ldc + gn;
-      const float* v = &acc[i][4 * h];
+      const float v[4] = {acc[i][2 * h].x, acc[i][2 * h].y, acc[i][2 * h + 1].x, acc[i][2 * h + 1].y};
       if (gn + 3 < N) {
         float4 o = make_float4(v[0], v[1], v[2], v[3]);
         if (accumulate) {
@@ -160,132 +178,89 @@ static __global__ void __launch_bounds__(256, 2) k_sgemm128(int M, int64_t N, in
   }
 }
 
-// The same for M <= 64 (the in-tile coupling of 64-variable sub-tiles): a 64 x 256 output tile
-// per block, 4 x 16 per thread (rows ty*4.., columns tx*4 + 64 h), so no half of the block's
-// rows is padding.  Same requirements as k_sgemm128.
-static __global__ void __launch_bounds__(256, 2) k_sgemm64(int M, int64_t N, int K, const float* __restrict__ A,
-                                                           int64_t lda, const float* __restrict__ B, int64_t ldb,
-                                                           float* __restrict__ C, int64_t ldc,
-                                                           const int32_t* __restrict__ rowmap, int accumulate) {
-  __shared__ __align__(16) float As[2][8][64];
-  __shared__ __align__(16) float Bs[2][8][256];
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int64_t n0 = (int64_t)blockIdx.x * 256;
-  const int am = (tid & 127) >> 1, ak = (tid & 1) * 4;  // A (threads 0..127): row, first k of a float4
-  const int bk = tid >> 5, bn = (tid & 31) * 4;         // B: k row, first column of the first float4 (+128)
-  float acc[4][16];
+// The same product for any shape and alignment: 64 x 64 output tile per 256-thread
+// block, 4 x 4 per thread, K in steps of 16.
+static __global__ void __launch_bounds__(256) k_gemm_tn_f32(int M, int64_t N, int64_t K, const float* __restrict__ At,
+                                                     int64_t lda, const float* __restrict__ B, int64_t ldb,
+                                                     float* __restrict__ C, int64_t ldc,
+                                                     const int32_t* __restrict__ rowmap, int accumulate) {
+  __shared__ float As[16][64];
+  __shared__ float Bs[16][64];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int m0 = blockIdx.y * 64;
+  const int64_t n0 = (int64_t)blockIdx.x * 64;
+  float acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; i++)
 #pragma unroll
-    for (int j = 0; j < 16; j++) acc[i][j] = 0.0f;
-  float4 ra, rb0, rb1;
-  auto ldb4 = [&](const float* brow, int64_t gn) {
-    float4 r;
-    if (gn + 3 < N) {
-      r = *reinterpret_cast<const float4*>(brow + gn);
-    } else {
-      r.x = gn < N ? brow[gn] : 0.f;
-      r.y = gn + 1 < N ? brow[gn + 1] : 0.f;
-      r.z = gn + 2 < N ? brow[gn + 2] : 0.f;
-      r.w = 0.f;
+    for (int j = 0; j < 4; j++) acc[i][j] = 0.0f;
+  for (int64_t k0 = 0; k0 < K; k0 += 16) {
+    for (int l = threadIdx.x; l < 16 * 64; l += 256) {
+      const int kk = l >> 6, mm = l & 63;
+      const int gm = m0 + mm;
+      const int64_t gk = k0 + kk;
+      As[kk][mm] = (gm < M && gk < K) ? At[gk * lda + gm] : 0.0f;
     }
-    return r;
-  };
-  auto load = [&](int k0) {
-    ra = (tid < 128 && am < M) ? *reinterpret_cast<const float4*>(A + (int64_t)am * lda + k0 + ak)
-                               : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float* brow = B + (int64_t)(k0 + bk) * ldb;
-    rb0 = ldb4(brow, n0 + bn);
-    rb1 = ldb4(brow, n0 + 128 + bn);
-  };
-  auto store = [&](int buf) {
-    if (tid < 128) {
-      As[buf][ak][am] = ra.x;
-      As[buf][ak + 1][am] = ra.y;
-      As[buf][ak + 2][am] = ra.z;
-      As[buf][ak + 3][am] = ra.w;
+    for (int l = threadIdx.x; l < 16 * 64; l += 256) {
+      const int kk = l >> 6, nn = l & 63;
+      const int64_t gk = k0 + kk, gn = n0 + nn;
+      Bs[kk][nn] = (gk < K && gn < N) ? B[gk * ldb + gn] : 0.0f;
     }
-    *reinterpret_cast<float4*>(&Bs[buf][bk][bn]) = rb0;
-    *reinterpret_cast<float4*>(&Bs[buf][bk][128 + bn]) = rb1;
-  };
-  load(0);
-  store(0);
-  __syncthreads();
-  int buf = 0;
-  for (int k0 = 0; k0 < K; k0 += 8) {
-    const bool more = k0 + 8 < K;
-    if (more) load(k0 + 8);
+    __syncthreads();
 #pragma unroll
-    for (int kk = 0; kk < 8; kk++) {
-      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4]);
-      float b[16];
+    for (int kk = 0; kk < 16; kk++) {
+      float a[4], b[4];
 #pragma unroll
-      for (int h = 0; h < 4; h++) {
-        const float4 bh = *reinterpret_cast<const float4*>(&Bs[buf][kk][64 * h + tx * 4]);
-        b[4 * h] = bh.x;
-        b[4 * h + 1] = bh.y;
-        b[4 * h + 2] = bh.z;
-        b[4 * h + 3] = bh.w;
-      }
-      const float a[4] = {a0.x, a0.y, a0.z, a0.w};
+      for (int i = 0; i < 4; i++) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; j++) b[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
       for (int i = 0; i < 4; i++)
 #pragma unroll
-        for (int j = 0; j < 16; j++) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < 4; j++) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
     }
-    if (more) {
-      store(buf ^ 1);
-      __syncthreads();
-      buf ^= 1;
-    }
+    __syncthreads();
   }
 #pragma unroll
   for (int i = 0; i < 4; i++) {
-    const int gm = ty * 4 + i;
+    const int gm = m0 + ty + 16 * i;
     if (gm >= M) continue;
     const int64_t row = rowmap ? (int64_t)rowmap[gm] : (int64_t)gm;
 #pragma unroll
-    for (int h = 0; h < 4; h++) {
-      const int64_t gn = n0 + h * 64 + tx * 4;
-      float* c = C + row * ldc + gn;
-      const float* v = &acc[i][4 * h];
-      if (gn + 3 < N) {
-        float4 o = make_float4(v[0], v[1], v[2], v[3]);
-        if (accumulate) {
-          const float4 q = *reinterpret_cast<const float4*>(c);
-          o.x += q.x;
-          o.y += q.y;
-          o.z += q.z;
-          o.w += q.w;
-        }
-        *reinterpret_cast<float4*>(c) = o;
-      } else {
-        for (int q = 0; q < 3; q++)
-          if (gn + q < N) c[q] = accumulate ? c[q] + v[q] : v[q];
+    for (int j = 0; j < 4; j++) {
+      const int64_t gn = n0 + tx + 16 * j;
+      if (gn < N) {
+        float* c = C + row * ldc + gn;
+        *c = accumulate ? *c + acc[i][j] : acc[i][j];
       }
     }
   }
+}
+
+// C[rowmap[i]][:] = sum_k At[k][i] B[k][:] (+ C when accumulate): the float path's products
+inline void gemm_tn_f32(cudaStream_t st, int M, int64_t N, int64_t K, const float* At, int64_t lda, const float* B,
+                        int64_t ldb, float* C, int64_t ldc, const int32_t* rowmap, int accumulate = 0) {
+  if (M <= 0 || N <= 0) return;
+  const bool aligned = (lda % 4 == 0) && (ldb % 4 == 0) && (ldc % 4 == 0) && (K % 8 == 0) && K > 0 &&
+                       ((uintptr_t)At % 16 == 0) && ((uintptr_t)B % 16 == 0) && ((uintptr_t)C % 16 == 0);
+  if (aligned) {
+    if (M <= 64) {
+      k_sgemm_t<64><<<dim3((unsigned)((N + 127) / 128), 1), 128, 0, st>>>(M, N, (int)K, At, lda, B, ldb, C, ldc,
+                                                                         rowmap, accumulate);
+    } else {
+      dim3 grid((unsigned)((N + 127) / 128), (unsigned)((M + 127) / 128));
+      k_sgemm_t<128><<<grid, 256, 0, st>>>(M, N, (int)K, At, lda, B, ldb, C, ldc, rowmap, accumulate);
+    }
+    return;
+  }
+  dim3 grid((unsigned)((N + 63) / 64), (unsigned)((M + 63) / 64));
+  k_gemm_tn_f32<<<grid, 256, 0, st>>>(M, N, K, At, lda, B, ldb, C, ldc, rowmap, accumulate);
 }
 
 template <typename T>
 inline void gemm_nn(cudaStream_t st, int M, int64_t N, int64_t K, const T* A, int64_t lda, const T* B, int64_t ldb,
                     T* C, int64_t ldc, const int32_t* rowmap, int accumulate = 0) {
   if (M <= 0 || N <= 0) return;
-  if constexpr (sizeof(T) == 4) {
-    const bool aligned = (lda % 4 == 0) && (ldb % 4 == 0) && (ldc % 4 == 0) && (K % 8 == 0) && K > 0 &&
-                         ((uintptr_t)A % 16 == 0) && ((uintptr_t)B % 16 == 0) && ((uintptr_t)C % 16 == 0);
-    if (aligned && M <= 64) {
-      k_sgemm64<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(M, N, (int)K, (const float*)A, lda, (const float*)B, ldb,
-                                                             (float*)C, ldc, rowmap, accumulate);
-      return;
-    }
-    if (aligned) {
-      dim3 grid((unsigned)((N + 127) / 128), (unsigned)((M + 127) / 128));
-      k_sgemm128<<<grid, 256, 0, st>>>(M, N, (int)K, (const float*)A, lda, (const float*)B, ldb, (float*)C, ldc,
-                                       rowmap, accumulate);
-      return;
-    }
-  }
   dim3 grid((unsigned)((N + 63) / 64), (unsigned)((M + 63) / 64));
   k_gemm_nn<T><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, rowmap, accumulate);
 }

@@ -345,12 +345,21 @@ int ensure_float_tiles(Factor& F, cudaStream_t st) {
   return TLRMVN_OK;
 }
 
-// out[v * ld8 + k] = U[v * kr + k] for k < kr, else 0 (one row tile's U, float, padded ranks)
-__global__ void k_pad_u32(const double* U, int64_t kr, int64_t ld8, int64_t cnt, float* out) {
+// out[k * m + v] = U[v * kr + k] for k < kr, else 0 (one row tile's U, float, k-major,
+// its ranks padded to a multiple of 8: ld8 rows)
+__global__ void k_pad_u32t(const double* U, int64_t kr, int64_t m, int64_t cnt, float* out) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= cnt) return;
-  const int64_t v = t / ld8, k = t % ld8;
+  const int64_t k = t / m, v = t % m;
   out[t] = k < kr ? (float)U[v * kr + k] : 0.0f;
+}
+// out[v * kc4 + r] = Vt[r * m + v] for r < kc, else 0 (one column tile's V, float,
+// variable-major, its ranks padded to a multiple of 4)
+__global__ void k_pad_v32(const double* Vt, int64_t kc, int64_t kc4, int64_t m, int64_t cnt, float* out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= cnt) return;
+  const int64_t v = t / kc4, r = t % kc4;
+  out[t] = r < kc ? (float)Vt[r * m + v] : 0.0f;
 }
 
 // Makes the copies a precision needs; the first caller makes them (and waits for
@@ -510,19 +519,27 @@ static int ensure_copies_locked(Factor& F, int precision, cudaStream_t st) {
   if (precision == TLRMVN_FP32 && !(F.U32 && F.V32) && nu) {
     dfree(F.U32);
     dfree(F.V32);
-    // U32: each row tile's U with its rank count padded to a multiple of 8 (zero columns), so
-    // that the shift product takes the vectorised float GEMM
+    // the first factors of the float products, k-major (a k-step of them is one plain
+    // copy): U32 each row tile's U transposed, its rank count padded to a multiple of 8
+    // (zero rows); V32 each column tile's V, its rank count padded to a multiple of 4
     F.u32_off.assign(F.r + 1, 0);
-    for (int i = 0; i < F.r; i++) F.u32_off[i + 1] = F.u32_off[i] + (int64_t)F.m * ((F.krow(i) + 7) / 8 * 8);
-    TLR_CHECK(dalloc(&F.U32, (size_t)std::max<int64_t>(F.u32_off[F.r], 1)));
-    TLR_CHECK(dalloc(&F.V32, nu));
+    F.v32_off.assign(F.r + 1, 0);
     for (int i = 0; i < F.r; i++) {
-      const int64_t kr = F.krow(i), ld8 = (kr + 7) / 8 * 8, cnt = (int64_t)F.m * ld8;
-      if (cnt)
-        k_pad_u32<<<blocks_for(cnt, 256), 256, 0, st>>>(F.Ucat + (size_t)F.m * F.krow_off[i], kr, ld8, cnt,
-                                                        F.U32 + F.u32_off[i]);
+      F.u32_off[i + 1] = F.u32_off[i] + (int64_t)F.m * ((F.krow(i) + 7) / 8 * 8);
+      F.v32_off[i + 1] = F.v32_off[i] + (int64_t)F.m * ((F.kcol(i) + 3) / 4 * 4);
     }
-    k_convert<double, float><<<blocks_for(nu, 256), 256, 0, st>>>(F.Vcat, F.V32, nu);
+    TLR_CHECK(dalloc(&F.U32, (size_t)std::max<int64_t>(F.u32_off[F.r], 1)));
+    TLR_CHECK(dalloc(&F.V32, (size_t)std::max<int64_t>(F.v32_off[F.r], 1)));
+    for (int i = 0; i < F.r; i++) {
+      const int64_t kr = F.krow(i), cnt = F.u32_off[i + 1] - F.u32_off[i];
+      if (cnt)
+        k_pad_u32t<<<blocks_for(cnt, 256), 256, 0, st>>>(F.Ucat + (size_t)F.m * F.krow_off[i], kr, F.m, cnt,
+                                                         F.U32 + F.u32_off[i]);
+      const int64_t kc = F.kcol(i), cntv = F.v32_off[i + 1] - F.v32_off[i];
+      if (cntv)
+        k_pad_v32<<<blocks_for(cntv, 256), 256, 0, st>>>(F.Vcat + (size_t)F.m * F.kcol_off[i], kc, (kc + 3) / 4 * 4,
+                                                         F.m, cntv, F.V32 + F.v32_off[i]);
+    }
   }
   if ((precision == TLRMVN_BF16_SHIFT || precision == TLRMVN_FP16_SHIFT) && !bf16_ready(F)) {
     // (a failed earlier attempt may have left some of these behind)
@@ -901,13 +918,13 @@ static void sweep_tile_f32(const Factor& F, int i, bool has_shift, float* Dl, in
   const int m = F.m, mt = (int)F.tsize(i);
   const int sub = tu.sub;
   const SweepShape sh = sweep_shape(Cc, std::min(mt, sub), tu.threads);
-  const float* Bi = F.B32 + (size_t)i * m * m;
   for (int q0 = 0; q0 < mt; q0 += sub) {
     const int mq = std::min(sub, mt - q0);
     if (q0 > 0) {
+      // B_i[q0 + v][u] = BT32 row u, column q0 + v: the transposed tile is the k-major operand
       pf.begin(TLRMVN_KC_COUPLE);
-      gemm_nn<float>(st, mq, Cc, q0, Bi + (size_t)q0 * m, m, Yv, C, Dl + (size_t)q0 * C, C, nullptr,
-                     has_shift ? 1 : 0);
+      gemm_tn_f32(st, mq, Cc, q0, F.BT32 + (size_t)i * m * F.ldbt + q0, F.ldbt, Yv, C, Dl + (size_t)q0 * C, C,
+                  nullptr, has_shift ? 1 : 0);
       pf.end();
     }
     DiagArgs32 a;
@@ -988,7 +1005,8 @@ static int run_chunks(Factor& F, const T* Bt, const T* Ut, const T* Vt, const Li
         pf.begin(TLRMVN_KC_SHIFT);
         if constexpr (sizeof(T) == 4) {
           const int64_t ld8 = (Kr + 7) / 8 * 8;
-          gemm_nn<T>(st, mt, Cc, ld8, Ut + F.u32_off[i], ld8, W + (size_t)F.krow_off[i] * C, C, Dl, C, nullptr);
+          gemm_tn_f32(st, mt, Cc, ld8, (const float*)Ut + F.u32_off[i], m, (const float*)W + (size_t)F.krow_off[i] * C,
+                      C, (float*)Dl, C, nullptr);
         } else {
           gemm_nn<T>(st, mt, Cc, Kr, Ut + (size_t)m * F.krow_off[i], Kr, W + (size_t)F.krow_off[i] * C, C, Dl, C,
                      nullptr);
@@ -1039,7 +1057,11 @@ static int run_chunks(Factor& F, const T* Bt, const T* Ut, const T* Vt, const Li
       }
       if (Kc > 0) {
         pf.begin(TLRMVN_KC_VPROJ);
-        gemm_nn<T>(st, (int)Kc, Cc, mt, Vt + (size_t)m * F.kcol_off[i], m, Y, C, W, C, F.vmap + F.kcol_off[i]);
+        if constexpr (sizeof(T) == 4)
+          gemm_tn_f32(st, (int)Kc, Cc, mt, (const float*)Vt + F.v32_off[i], (Kc + 3) / 4 * 4, (const float*)Y, C,
+                      (float*)W, C, F.vmap + F.kcol_off[i]);
+        else
+          gemm_nn<T>(st, (int)Kc, Cc, mt, Vt + (size_t)m * F.kcol_off[i], m, Y, C, W, C, F.vmap + F.kcol_off[i]);
         pf.end();
       }
     }

@@ -618,10 +618,14 @@ def run_ours(args):
                                      "relative error); at this sample count three of them span ~2.4 in log p, so "
                                      "the full-size accuracy claim is the per-shift comparison with the FP64 path "
                                      "in the GPU tests (1e-4 FP32, 1e-2 BF16-shift)"},
-                "precision_note": ("f32+bf16: float32 sweep of eq. 2 (per-sample chains within 64-variable "
-                                   "sub-tiles); low-rank shifts and projections bf16 x bf16 -> fp32 on tcgen05; "
-                                   "the in-tile coupling between sub-tiles as split-bf16 products (hi hi + hi lo "
-                                   "+ lo hi, ~1e-5 relative) -> fp32")}
+                "precision_note": {
+                    0: "f64: every step in float64",
+                    1: "f32: float32 sweep of eq. 2 (per-sample chains within 64-variable sub-tiles); low-rank "
+                       "shifts, projections and the in-tile coupling between sub-tiles as float32 SIMT products",
+                    2: "f32+bf16: float32 sweep of eq. 2 (per-sample chains within 64-variable sub-tiles); low-rank "
+                       "shifts and projections bf16 x bf16 -> fp32 on tcgen05; the in-tile coupling between "
+                       "sub-tiles as split-bf16 products (hi hi + hi lo + lo hi, ~1e-5 relative) -> fp32",
+                    3: "f32+fp16: as f32+bf16 with fp16 operands, U and V scaled per tile by powers of two"}[prec]}
         if "serving" in extra:
             line["p50_ms"] = extra["serving"]["p50_ms"]
             line["p99_ms"] = extra["serving"]["p99_ms"]

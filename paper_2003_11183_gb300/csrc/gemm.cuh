@@ -68,12 +68,14 @@ __global__ void __launch_bounds__(256) k_gemm_nn(int M, int64_t N, int64_t K, co
 // At is K x M (row k holds column k of the product's first factor), so that a k-step of
 // it is a plain copy: the tiles of At and B go by cp.async straight into a ring of four
 // shared-memory stages (no registers held for the copies, three steps in flight while
-// one is multiplied).  The multiply is k_sgemm's: a BM x 128 output tile per block of
-// 2 BM threads, 8 x 8 outputs per thread as paired float32 FMAs.  Requires lda, ldb, ldc
-// multiples of 4, 16-byte aligned At, B, C and K a multiple of 8; the ragged columns of
-// the last row and column blocks are zero-filled copies.  (BM = 128: the shifts and
-// projections; BM = 64: the in-tile coupling of 64-variable sub-tiles, so that no half
-// of the block's rows is padding and a launch over the samples has twice the blocks.)
+// one is multiplied).  A BM x 128 output tile per block of 256 threads, TM x 8 outputs
+// per thread (4-row by 4-column quadrants, so that shared-memory reads are float4) as
+// paired float32 FMAs (two FMAs an instruction, each rounded as fmaf).  BM = 128, TM = 8:
+// the shifts and projections; BM = 64, TM = 4: the in-tile coupling of 64-variable
+// sub-tiles, 64 rows only, whose launches over the samples would otherwise hold about
+// nine warps per SM and wait on memory.  Requires lda, ldb, ldc multiples of 4, 16-byte
+// aligned At, B, C and K a multiple of 8; the ragged columns of the last row and column
+// blocks are zero-filled copies.
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
                "l"(gmem), "r"(src_bytes)
@@ -85,42 +87,40 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(NPEND) : "memory");
 }
 
-template <int BM>
-__global__ void __launch_bounds__(2 * BM) k_sgemm_t(int M, int64_t N, int K, const float* __restrict__ At,
-                                                    int64_t lda, const float* __restrict__ B, int64_t ldb,
-                                                    float* __restrict__ C, int64_t ldc,
-                                                    const int32_t* __restrict__ rowmap, int accumulate) {
-  static_assert(BM == 64 || BM == 128, "block rows");
-  constexpr int NT = 2 * BM;    // threads; one float4 of the At tile (8 x BM) each
-  constexpr int BL = 256 / NT;  // float4 of the B tile (8 x 128) per thread
-  constexpr int S = 4;          // stages
+template <int BM, int TM>
+__global__ void __launch_bounds__(256, TM == 4 ? 3 : 2)
+    k_sgemm_t(int M, int64_t N, int K, const float* __restrict__ At, int64_t lda, const float* __restrict__ B,
+              int64_t ldb, float* __restrict__ C, int64_t ldc, const int32_t* __restrict__ rowmap, int accumulate) {
+  static_assert((BM == 128 && TM == 8) || (BM == 64 && TM == 4), "tile shapes");
+  constexpr int S = 4;  // stages (256 threads: BM / TM row groups x 16 column groups)
   __shared__ __align__(16) float As[S][8][BM];
   __shared__ __align__(16) float Bs[S][8][128];
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;  // ty < BM / 8
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;  // ty < BM / TM
   const int m0 = blockIdx.y * BM;
   const int64_t n0 = (int64_t)blockIdx.x * 128;
-  float2 acc[8][4];  // acc[i][j]: columns 2j, 2j + 1 of row i
+  float2 acc[TM][4];  // acc[i][j]: columns 2j, 2j + 1 of row i
 #pragma unroll
-  for (int i = 0; i < 8; i++)
+  for (int i = 0; i < TM; i++)
 #pragma unroll
     for (int j = 0; j < 4; j++) acc[i][j] = make_float2(0.0f, 0.0f);
   // the copies of k-step ks into stage buf
   auto issue = [&](int ks, int buf) {
     const int k0 = ks * 8;
-    {
+    if (tid < 2 * BM) {  // the At tile: 2 BM float4
       const int kk = tid / (BM / 4), mm = (tid % (BM / 4)) * 4, gm = m0 + mm;
       const int bytes = gm + 3 < M ? 16 : (gm < M ? 4 * (M - gm) : 0);
       cp_async16(&As[buf][kk][mm], bytes ? At + (int64_t)(k0 + kk) * lda + gm : At, bytes);
     }
-#pragma unroll
-    for (int l = 0; l < BL; l++) {
-      const int e = tid + NT * l, kk = e >> 5, nn = (e & 31) * 4;
+    {  // the B tile: 256 float4
+      const int kk = tid >> 5, nn = (tid & 31) * 4;
       const int64_t gn = n0 + nn;
       const int bytes = gn + 3 < N ? 16 : (gn < N ? (int)(4 * (N - gn)) : 0);
       cp_async16(&Bs[buf][kk][nn], bytes ? B + (int64_t)(k0 + kk) * ldb + gn : B, bytes);
     }
   };
   const int nk = K / 8;
+  pdl_trigger();
+  pdl_wait();  // B and C may be the preceding kernels' output
 #pragma unroll
   for (int s = 0; s < S - 1; s++) {
     if (s < nk) issue(s, s);
@@ -134,15 +134,21 @@ __global__ void __launch_bounds__(2 * BM) k_sgemm_t(int M, int64_t N, int K, con
     const int buf = ks % S;
 #pragma unroll
     for (int kk = 0; kk < 8; kk++) {
-      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4]);
-      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][BM / 2 + ty * 4]);
+      float a[TM];
+      {
+        const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4]);
+        a[0] = a0.x, a[1] = a0.y, a[2] = a0.z, a[3] = a0.w;
+        if constexpr (TM == 8) {
+          const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][BM / 2 + ty * 4]);
+          a[4] = a1.x, a[5] = a1.y, a[6] = a1.z, a[7] = a1.w;
+        }
+      }
       const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
       const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][64 + tx * 4]);
-      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
       const float2 b[4] = {make_float2(b0.x, b0.y), make_float2(b0.z, b0.w), make_float2(b1.x, b1.y),
                            make_float2(b1.z, b1.w)};
 #pragma unroll
-      for (int i = 0; i < 8; i++) {
+      for (int i = 0; i < TM; i++) {
         const float2 aa = make_float2(a[i], a[i]);
 #pragma unroll
         for (int j = 0; j < 4; j++) acc[i][j] = __ffma2_rn(aa, b[j], acc[i][j]);
@@ -151,7 +157,7 @@ __global__ void __launch_bounds__(2 * BM) k_sgemm_t(int M, int64_t N, int K, con
   }
   cp_async_wait<0>();  // (only empty groups remain)
 #pragma unroll
-  for (int i = 0; i < 8; i++) {
+  for (int i = 0; i < TM; i++) {
     const int gm = m0 + (i < 4 ? ty * 4 + i : BM / 2 + ty * 4 + i - 4);
     if (gm >= M) continue;
     const int64_t row = rowmap ? (int64_t)rowmap[gm] : (int64_t)gm;
@@ -194,6 +200,8 @@ static __global__ void __launch_bounds__(256) k_gemm_tn_f32(int M, int64_t N, in
   for (int i = 0; i < 4; i++)
 #pragma unroll
     for (int j = 0; j < 4; j++) acc[i][j] = 0.0f;
+  pdl_trigger();
+  pdl_wait();  // B and C may be the preceding kernels' output
   for (int64_t k0 = 0; k0 < K; k0 += 16) {
     for (int l = threadIdx.x; l < 16 * 64; l += 256) {
       const int kk = l >> 6, mm = l & 63;
@@ -243,18 +251,19 @@ inline void gemm_tn_f32(cudaStream_t st, int M, int64_t N, int64_t K, const floa
   if (M <= 0 || N <= 0) return;
   const bool aligned = (lda % 4 == 0) && (ldb % 4 == 0) && (ldc % 4 == 0) && (K % 8 == 0) && K > 0 &&
                        ((uintptr_t)At % 16 == 0) && ((uintptr_t)B % 16 == 0) && ((uintptr_t)C % 16 == 0);
+  // (programmatic dependent launches: each kernel waits for its predecessor before it reads)
   if (aligned) {
     if (M <= 64) {
-      k_sgemm_t<64><<<dim3((unsigned)((N + 127) / 128), 1), 128, 0, st>>>(M, N, (int)K, At, lda, B, ldb, C, ldc,
-                                                                         rowmap, accumulate);
+      launch_pdl(k_sgemm_t<64, 4>, dim3((unsigned)((N + 127) / 128), 1), dim3(256), 0, st, M, N, (int)K, At, lda, B,
+                 ldb, C, ldc, rowmap, accumulate);
     } else {
-      dim3 grid((unsigned)((N + 127) / 128), (unsigned)((M + 127) / 128));
-      k_sgemm_t<128><<<grid, 256, 0, st>>>(M, N, (int)K, At, lda, B, ldb, C, ldc, rowmap, accumulate);
+      launch_pdl(k_sgemm_t<128, 8>, dim3((unsigned)((N + 127) / 128), (unsigned)((M + 127) / 128)), dim3(256), 0, st, M,
+                 N, (int)K, At, lda, B, ldb, C, ldc, rowmap, accumulate);
     }
     return;
   }
-  dim3 grid((unsigned)((N + 63) / 64), (unsigned)((M + 63) / 64));
-  k_gemm_tn_f32<<<grid, 256, 0, st>>>(M, N, K, At, lda, B, ldb, C, ldc, rowmap, accumulate);
+  launch_pdl(k_gemm_tn_f32, dim3((unsigned)((N + 63) / 64), (unsigned)((M + 63) / 64)), dim3(256), 0, st, M, N, K, At,
+             lda, B, ldb, C, ldc, rowmap, accumulate);
 }
 
 template <typename T>

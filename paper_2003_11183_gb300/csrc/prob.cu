@@ -955,7 +955,8 @@ static void sweep_tile_f32(const Factor& F, int i, bool has_shift, float* Dl, in
     a.logP = logP;
     pf.begin(TLRMVN_KC_DIAG);
     const int flags = (periodize ? SWEEP_PERIODIZE : 0) | SWEEP_YV | (L.one_sided ? SWEEP_ONE_SIDED : 0);
-    sweep_kernel(flags)<<<blocks_for(Cc, sh.ns), sh.threads, sweep_smem_bytes(mq, sh.ns), st>>>(a);
+    launch_pdl(sweep_kernel(flags), dim3((unsigned)blocks_for(Cc, sh.ns)), dim3(sh.threads), sweep_smem_bytes(mq, sh.ns), st,
+               a);
     pf.end();
   }
 }

@@ -20,7 +20,7 @@ probabilities") step by step, in float64, written for a reader to check by eye:
                integrand (Algorithms 6 and 7), and the QMC estimator
 
 Parity status: every function is pinned by ``tests/test_oracle_*.py`` against
-closed forms, library routines or brute force, except the end-to-end estimate
-at n = 65,536, which is pinned only through the same TLR recursion at small n
-(parity unpinned at full size beyond self-consistency across shifts).
+closed forms, library routines or brute force; the TLR integrand also at the
+full size n = 65,536, on a problem whose per-sample value has a closed form
+(``tests/test_oracle_full_size.py``).
 """

@@ -495,3 +495,23 @@ def test_scale_invariance_every_precision(tl):
     p16 = tl.tlrmvn_prob(F2, w.a * d, w.b * d, w.nu, tl.FP16_SHIFT, w.n_shifts, w.n_points, shifts=w.shifts,
                          per_shift=True)[2]
     assert np.all(rel(p16, ref["per_shift"]) < 1e-2)
+
+
+@pytest.mark.parametrize("precision,tol", [("FP64", 1e-9), ("FP32", 1e-4), ("BF16_SHIFT", 1e-2), ("FP16_SHIFT", 1e-2)])
+def test_full_size_closed_form_every_sample(tl, precision, tol):
+    # n = 65,536, 512-variable tiles, ranks 1..3 (tests.helpers.sources_targets_factor):
+    # every per-sample value of 4 x 128 samples against its closed form, computed from
+    # the lattice values without the tile recursion (pinned on the oracle at this size
+    # by tests/test_oracle_full_size.py)
+    from oracle import lattice
+    from tests.helpers import closed_form_logf, sources_targets_factor
+    n, m, M, N = 65_536, 512, 4, 128
+    OF, b = sources_targets_factor(n, m, seed=21)
+    F = tl.tlrmvn_factor_import(export_bytes(OF))
+    a = np.full(n, -np.inf)
+    shifts = synth.lattice_shifts(M, n + 1, 22)
+    _, _, _, pm = tl.tlrmvn_prob(F, a, b, math.inf, getattr(tl, precision), M, N, shifts=shifts, per_sample=True)
+    W = lattice.qmc_points(lattice.richtmyer_generators(n + 1), shifts, N)[:, :n].T
+    want = closed_form_logf(OF, b, W)
+    assert np.all(np.isfinite(pm))
+    assert np.all(rel(pm, want) < tol), rel(pm, want).max()

@@ -110,16 +110,18 @@ def sources_targets_factor(n: int, m: int, seed: int, max_rank: int = 3):
     return F, b
 
 
-def closed_form_logf(F: ofactor.TLRFactor, b: np.ndarray, W: np.ndarray) -> np.ndarray:
+def closed_form_logf(F: ofactor.TLRFactor, b: np.ndarray, W: np.ndarray, rs: np.ndarray | None = None) -> np.ndarray:
     """Per-sample log integrand of a sources_targets_factor problem, computed directly:
-    sum over target variables of log Phi(b_v - s_v), s as described there.  W: (n, S)."""
+    sum over target variables of log Phi(r b_v - s_v), s as described there and r the
+    sample's Student-t scale (rs, one per sample; 1 for a normal problem).  W: (n, S)."""
     from scipy.special import log_ndtr, ndtri
     o = F.tile_off
+    r = np.ones(W.shape[1]) if rs is None else np.asarray(rs, dtype=np.float64)
     out = np.zeros(W.shape[1])
     Y = {j: ndtri(W[o[j]:o[j + 1]]) for j in range(0, F.r, 2)}
     for i in range(1, F.r, 2):
         s = np.zeros((o[i + 1] - o[i], W.shape[1]))
         for j in range(0, i, 2):
             s += F.U[(i, j)] @ (F.V[(i, j)].T @ Y[j])
-        out += log_ndtr(b[o[i]:o[i + 1], None] - s).sum(axis=0)
+        out += log_ndtr(b[o[i]:o[i + 1], None] * r[None, :] - s).sum(axis=0)
     return out

@@ -497,8 +497,9 @@ def test_scale_invariance_every_precision(tl):
     assert np.all(rel(p16, ref["per_shift"]) < 1e-2)
 
 
+@pytest.mark.parametrize("nu", [math.inf, 7.0])
 @pytest.mark.parametrize("precision,tol", [("FP64", 1e-9), ("FP32", 1e-4), ("BF16_SHIFT", 1e-2), ("FP16_SHIFT", 1e-2)])
-def test_full_size_closed_form_every_sample(tl, precision, tol):
+def test_full_size_closed_form_every_sample(tl, precision, tol, nu):
     # n = 65,536, 512-variable tiles, ranks 1..3 (tests.helpers.sources_targets_factor):
     # every per-sample value of 4 x 128 samples against its closed form, computed from
     # the lattice values without the tile recursion (pinned on the oracle at this size
@@ -510,8 +511,12 @@ def test_full_size_closed_form_every_sample(tl, precision, tol):
     F = tl.tlrmvn_factor_import(export_bytes(OF))
     a = np.full(n, -np.inf)
     shifts = synth.lattice_shifts(M, n + 1, 22)
-    _, _, _, pm = tl.tlrmvn_prob(F, a, b, math.inf, getattr(tl, precision), M, N, shifts=shifts, per_sample=True)
-    W = lattice.qmc_points(lattice.richtmyer_generators(n + 1), shifts, N)[:, :n].T
-    want = closed_form_logf(OF, b, W)
+    _, _, _, pm = tl.tlrmvn_prob(F, a, b, nu, getattr(tl, precision), M, N, shifts=shifts, per_sample=True)
+    Wall = lattice.qmc_points(lattice.richtmyer_generators(n + 1), shifts, N)
+    rs = None
+    if math.isfinite(nu):  # Student-t: the sample's scale from lattice coordinate n (SciPy's chi quantile)
+        from scipy import stats
+        rs = stats.chi.ppf(Wall[:, n], nu) / math.sqrt(nu)
+    want = closed_form_logf(OF, b, Wall[:, :n].T, rs)
     assert np.all(np.isfinite(pm))
     assert np.all(rel(pm, want) < tol), rel(pm, want).max()

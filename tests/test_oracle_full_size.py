@@ -7,7 +7,10 @@ through the tile recursion.  A wrong tile offset, a transposed U or V, a sign of
 or a shift applied to the wrong tiles changes the values."""
 from __future__ import annotations
 
+import math
+
 import numpy as np
+from scipy import stats
 
 from oracle import sov
 from tests.helpers import closed_form_logf, sources_targets_factor
@@ -37,3 +40,15 @@ def test_closed_form_sees_the_low_rank_push():
         F.V[k] = F.V[k][:, :0]
     bare = sov.tlrmvn(F, a, b[:, None], W)
     assert np.min(np.abs(full - bare)) > 1.0
+
+
+def test_tlr_student_t_full_size_closed_form():
+    """Algorithm 7 at the same size: the target limits scale by chi_nu^-1(w0)/sqrt(nu), w0 the
+    lattice value of coordinate n (SciPy's chi quantile here, not the oracle's)."""
+    n, m, S, nu = 65_536, 512, 4, 7.0
+    F, b = sources_targets_factor(n, m, seed=15)
+    Wall = np.random.default_rng(16).uniform(1e-6, 1.0 - 1e-6, (S, n + 1))
+    got = sov.per_sample_logp(F, None, F.perm, np.full(n, -np.inf), b, nu, Wall)
+    rs = stats.chi.ppf(Wall[:, n], nu) / math.sqrt(nu)
+    want = closed_form_logf(F, b, Wall[:, :n].T, rs)
+    np.testing.assert_allclose(got, want, rtol=1e-10, atol=0.0)

@@ -37,7 +37,7 @@ METRIC = "MVN/MVT QMC sample-dims/sec at n=65,536 vs FP64 path; p50/p99 solve la
 # those sources are unchanged (otherwise null); the summaries with the capture
 # commands are under profiles/.
 TRAFFIC = {
-    "k_sweep_tc": {"bytes_per_sample_dim": 20.5461,
+    "k_sweep_tc": {"bytes_per_sample_dim": 20.7063,
                    "capture": "profiles/k_sweep_tc_n16384.md",
                    "files": ["paper_2003_11183_gb300/csrc/sweep_tc.cuh",
                              "paper_2003_11183_gb300/csrc/sweep.cuh",
@@ -45,7 +45,7 @@ TRAFFIC = {
                              "paper_2003_11183_gb300/csrc/tcgen05.cuh",
                              "paper_2003_11183_gb300/csrc/common.cuh",
                              "include/tlrmvn.h"],
-                   "sources": "e327825f030652e11fcece06316c89b0ca9584160b4201398fbf8186fecb3e2a"},
+                   "sources": "2091dce6350b70d328d34a085ab1b5bd34780cc9845b0990a2bf7b7e42bc9294"},
 }
 
 

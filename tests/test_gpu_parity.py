@@ -520,3 +520,34 @@ def test_full_size_closed_form_every_sample(tl, precision, tol, nu):
     want = closed_form_logf(OF, b, Wall[:, :n].T, rs)
     assert np.all(np.isfinite(pm))
     assert np.all(rel(pm, want) < tol), rel(pm, want).max()
+
+
+@pytest.mark.parametrize("precision,tol", [("FP64", 1e-12), ("FP32", 2e-6), ("BF16_SHIFT", 2e-6), ("FP16_SHIFT", 2e-6)])
+@pytest.mark.parametrize("one_sided", [True, False])
+def test_tiny_and_ragged_problems_every_precision(tl, precision, tol, one_sided):
+    # degenerate shapes against closed forms per sample: n = 1 (Phi(b) - Phi(a) with sigma = 1.5;
+    # FP64 and FP32, a problem the tensor-core paths are not meant for), and on every path n = 17
+    # independent variables in tiles of 16 (a full tile and a one-variable tile; no low-rank
+    # blocks), where each sample is the product of the univariate probabilities; one-sided limits
+    # take the float paths' one-sided step
+    from scipy.special import log_ndtr, ndtr
+    prec = getattr(tl, precision)
+
+    def logdiff(a, b):
+        a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+        return np.where(np.isneginf(a), log_ndtr(b), np.log(ndtr(b) - ndtr(a)))
+
+    if prec in (tl.FP64, tl.FP32):
+        a1 = [-np.inf] if one_sided else [-0.4]
+        F = tl.tlrmvn_factor_dense(np.array([[2.25]]), None, None, 1, 0.0, 0, 0)
+        _, _, _, pm = tl.tlrmvn_prob(F, a1, [1.1], math.inf, prec, 2, 50, seed=3, per_sample=True)
+        want = float(logdiff(np.array(a1) / 1.5, 1.1 / 1.5)[0])
+        assert np.allclose(pm, want, rtol=tol, atol=0)
+    rng = np.random.default_rng(31)
+    n = 17
+    b = rng.uniform(0.2, 2.0, n)
+    a = np.full(n, -np.inf) if one_sided else b - rng.uniform(0.5, 3.0, n)
+    F = tl.tlrmvn_factor_dense(np.eye(n), None, None, 16, 1e-8, 0, 0)
+    _, _, _, pm = tl.tlrmvn_prob(F, a, b, math.inf, prec, 3, 40, seed=5, per_sample=True)
+    want = float(logdiff(a, b).sum())
+    assert np.allclose(pm, want, rtol=tol, atol=0)

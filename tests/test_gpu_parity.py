@@ -551,3 +551,23 @@ def test_tiny_and_ragged_problems_every_precision(tl, precision, tol, one_sided)
     _, _, _, pm = tl.tlrmvn_prob(F, a, b, math.inf, prec, 3, 40, seed=5, per_sample=True)
     want = float(logdiff(a, b).sum())
     assert np.allclose(pm, want, rtol=tol, atol=0)
+
+
+@pytest.mark.parametrize("precision", ["FP64", "FP32", "BF16_SHIFT", "FP16_SHIFT"])
+def test_degenerate_limits_every_precision(tl, precision):
+    # the method's degenerate cases on every path (n = 40 with a real low-rank structure, tiles
+    # of 16): limits infinite on both sides give probability 1 (every per-sample log exactly 0);
+    # one zero-width interval a_i = b_i gives probability 0 (every per-sample log and the
+    # estimate -inf, its error NaN), and the other samples' arithmetic stays finite
+    prec = getattr(tl, precision)
+    w = synth.small_workload(8, 16, 91, n_shifts=3, n_points=40, ragged_n=40)
+    F = tl.tlrmvn_factor_kernel(w.xy, w.kernel, w.params, w.nugget, None, None, 16, 1e-6, 0, 0)
+    n = len(w.xy)
+    lp, err, ps, pm = tl.tlrmvn_prob(F, np.full(n, -np.inf), np.full(n, np.inf), math.inf, prec, 3, 40,
+                                     seed=9, per_shift=True, per_sample=True)
+    assert np.all(pm == 0.0) and np.all(ps == 0.0) and lp == 0.0
+    a = np.full(n, -np.inf)
+    b = np.full(n, 1.0)
+    a[n // 2] = b[n // 2] = 0.3
+    lp, err, ps, pm = tl.tlrmvn_prob(F, a, b, 7.0, prec, 3, 40, seed=9, per_shift=True, per_sample=True)
+    assert np.all(np.isneginf(pm)) and np.all(np.isneginf(ps)) and lp == -np.inf and math.isnan(err)
